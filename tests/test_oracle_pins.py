@@ -1,0 +1,314 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: published test vectors,
+closed forms, textbook/library routines run on the same input, brute force on tiny
+inputs, or invariants the paper states.  They are chosen so that a plausible slip (a
+dropped term, a wrong sign or index, a transposed operand) breaks at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import workloads as W
+from oracle.dense import cpqr, gepp, interp_decomp, lu_solve
+from oracle.gmres import gmres
+from oracle.nd import nested_dissection, separator_walk
+from oracle.philox import gaussian_f32, philox4x32_10, sketch_matrix
+from oracle.spalu import Elim, Options, Sparsify, factor, solve
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Published known-answer vectors of Philox4x32-10 (SC'11 / Random123)."""
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = philox4x32_10(*w[:4], *w[4:6])
+        assert [int(o) for o in out] == w[6:10]
+
+
+def test_gaussian_moments_and_independence():
+    n = 200_000
+    z = gaussian_f32(np.arange(n), 7, 3, 11, seed=12345).astype(np.float64)
+    assert abs(z.mean()) < 0.01
+    assert abs(z.var() - 1.0) < 0.01
+    assert abs(np.mean(z**4) - 3.0) < 0.06           # Gaussian kurtosis
+    z2 = gaussian_f32(np.arange(n), 7, 3, 12, seed=12345).astype(np.float64)
+    assert abs(np.corrcoef(z, z2)[0, 1]) < 0.01       # different segment -> independent
+
+
+def test_sketch_is_order_free():
+    """Entries depend on (row, node, half), not on the enumeration of far rows."""
+    nodes = np.array([5, 99, 17, 3000])
+    half = np.array([0, 1, 0, 1])
+    G = sketch_matrix(3, 4, 77, 6, nodes, half)
+    p = np.array([2, 0, 3, 1])
+    G2 = sketch_matrix(3, 4, 77, 6, nodes[p], half[p])
+    assert np.array_equal(G[:, p], G2)
+    G3 = sketch_matrix(3, 4, 77, 9, nodes, half)      # growing h keeps the first rows
+    assert np.array_equal(G3[:6], G)
+
+
+# ----------------------------------------------------------------------------- ND
+def _closed_form_counts(n):
+    q = (n + 1) // 16
+    leaves = q * q
+    return dict(N=n * n, leaves=leaves, L=2 * int(round(math.log2(q))), interior=225 * leaves,
+                separator=n * n - 225 * leaves, crossings=(q - 1) ** 2,
+                finest_segments=2 * q * (q - 1))
+
+
+@pytest.mark.parametrize("n", [15, 31, 63, 127, 255])
+def test_nd_geometry_matches_closed_form(n):
+    nd = nested_dissection(n, n)
+    cf = _closed_form_counts(n)
+    assert nd.L == cf["L"]
+    assert len(nd.leaves) == cf["leaves"]
+    assert sum(b.w * b.h for b in nd.leaves) == cf["interior"]
+    assert sum(s.size for l in nd.seps for _, s in nd.seps[l]) == cf["separator"]
+    if nd.L:
+        lev = nd.levels[nd.L]
+        assert len(lev.corners) == cf["crossings"]
+        assert len(lev.segments) == cf["finest_segments"]
+        assert all(s.nodes.size == 15 for s in lev.segments.values())
+
+
+@pytest.mark.parametrize("nx,ny", [(63, 63), (127, 31), (31, 127), (15, 15)])
+def test_nd_order_is_bijection_and_separates(nx, ny):
+    nd = nested_dissection(nx, ny)
+    assert np.array_equal(np.sort(nd.perm), np.arange(nx * ny))
+    # no stencil edge joins two different leaf interiors (Sec. 2.2)
+    owner = -np.ones(nx * ny, dtype=np.int64)
+    for i, b in enumerate(nd.leaves):
+        for y in range(b.y0, b.y1 + 1):
+            owner[b.x0 + nx * y: b.x1 + 1 + nx * y] = i
+    grid = owner.reshape(ny, nx)
+    a, b = grid[:, :-1], grid[:, 1:]
+    assert not np.any((a >= 0) & (b >= 0) & (a != b))
+    a, b = grid[:-1, :], grid[1:, :]
+    assert not np.any((a >= 0) & (b >= 0) & (a != b))
+    # leaves first, then separators level L..1
+    nI = sum(bx.w * bx.h for bx in nd.leaves)
+    assert np.all(owner[nd.perm[:nI]] >= 0) and np.all(owner[nd.perm[nI:]] < 0)
+
+
+@pytest.mark.parametrize("w,h", [(15, 31), (31, 15), (31, 31), (63, 31), (31, 63), (15, 63)])
+def test_degree_bias_walk_gives_straight_middle_line(w, h):
+    """The literal separator search of Sec. 3.1 (median centre, direction rule, Eq.
+    (degreebias) with theta=0.1) reproduces the straight middle cut on a grid box."""
+    xs, ys = np.meshgrid(np.arange(w), np.arange(h), indexing="xy")
+    coords = np.stack([xs.ravel(), ys.ravel()], axis=1).astype(float)
+    adj = []
+    for y in range(h):
+        for x in range(w):
+            nb = []
+            for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                if 0 <= x + dx < w and 0 <= y + dy < h:
+                    nb.append((x + dx) + w * (y + dy))
+            adj.append(nb)
+    sep = separator_walk(coords, adj)
+    if w < h:
+        expect = [x + w * ((h - 1) // 2) for x in range(w)]
+    else:
+        expect = [(w - 1) // 2 + w * y for y in range(h)]
+    assert sep == expect
+
+
+# ----------------------------------------------------------------------------- dense
+def test_gepp_reconstructs_and_pivots_lowest_on_ties():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((40, 40))
+    lu, piv = gepp(A)
+    L = np.tril(lu, -1) + np.eye(40)
+    U = np.triu(lu)
+    PA = A.copy()
+    for j, p in enumerate(piv):
+        PA[[j, p]] = PA[[p, j]]
+    assert np.allclose(L @ U, PA, atol=1e-12)
+    b = rng.standard_normal((40, 3))
+    assert np.allclose(lu_solve(lu, piv, b), np.linalg.solve(A, b), atol=1e-11)
+    T = np.array([[1.0, 2.0], [-1.0, 3.0]])          # |1| = |-1|: tie -> row 0
+    _, piv = gepp(T)
+    assert piv[0] == 0
+    _, piv = gepp(np.array([[0.5, 1.0], [-1.0, 3.0]]))
+    assert piv[0] == 1
+
+
+def test_cpqr_matches_lapack_pivoting():
+    """Businger-Golub pivots equal LAPACK's dgeqp3 (scipy) when norms are distinct."""
+    rng = np.random.default_rng(1)
+    for m, e in [(30, 12), (12, 30), (50, 50)]:
+        Y = rng.standard_normal((m, e)) * np.logspace(0, -3, e)[rng.permutation(e)]
+        perm, k, R = cpqr(Y, 0.0)
+        _, Rs, ps = scipy.linalg.qr(Y, pivoting=True, mode="economic")
+        kk = min(m, e)
+        assert k == kk
+        assert np.array_equal(perm[:kk], ps[:kk])
+        assert np.allclose(np.abs(np.diag(R[:kk, :kk])), np.abs(np.diag(Rs)[:kk]), rtol=1e-10)
+
+
+def test_interp_decomp_rank_and_error():
+    rng = np.random.default_rng(2)
+    m, e = 80, 40
+    U, _ = np.linalg.qr(rng.standard_normal((m, e)))
+    V, _ = np.linalg.qr(rng.standard_normal((e, e)))
+    s = 10.0 ** (-0.5 * np.arange(e))                  # sigma_i = 10^{-i/2}
+    B = (U * s) @ V.T
+    eps = 1e-6
+    perm, k, T = interp_decomp(B, eps)
+    true_rank = int(np.sum(s > eps * s[0]))
+    assert abs(k - true_rank) <= 2
+    err = np.linalg.norm(B[:, perm[k:]] - B[:, perm[:k]] @ T)
+    assert err <= 10 * eps * np.linalg.norm(B)
+    assert np.linalg.norm(T) <= math.sqrt(e * k * (e - k))   # bound of Eq. (norm(T))
+    perm0, k0, _ = interp_decomp(np.zeros((5, 4)), 1e-8)
+    assert k0 == 0
+
+
+# ----------------------------------------------------------------------------- whole method
+@pytest.mark.parametrize("kind", ["laplace", "diffusion", "helmholtz", "convdiff"])
+@pytest.mark.parametrize("n", [15, 31, 63])
+def test_eps0_equals_dense_solve(kind, n):
+    """With eps = 0 nothing is truncated: the method is exact block LU (special case)."""
+    P = W.make_problem(kind, n, seed=3, nrhs=2)
+    nd = nested_dissection(n, n)
+    F = factor(P.A, nd, Options(eps=0.0, symmetric=P.symmetric))
+    X = solve(F, P.B)
+    Xd = np.linalg.solve(P.A.to_dense(), P.B)
+    assert np.linalg.norm(X - Xd) <= 1e-11 * np.linalg.norm(Xd)
+
+
+def test_discrete_eigenfunction_closed_form():
+    """-Lap_h sin(p pi x) sin(q pi y) = lambda_pq (.) exactly on the grid."""
+    n = 63
+    h = 1.0 / (n + 1)
+    x = (np.arange(n) + 1) * h
+    p, q = 3, 5
+    f = np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x)).ravel()   # row = y, col = x
+    lam = 4 / h**2 * (np.sin(p * np.pi * h / 2) ** 2 + np.sin(q * np.pi * h / 2) ** 2)
+    A = W.laplace(n, n)
+    nd = nested_dissection(n, n)
+    u = solve(factor(A, nd, Options(eps=1e-8, symmetric=True)), f)
+    assert np.linalg.norm(u - f / lam) <= 1e-6 * np.linalg.norm(f / lam)
+    u0 = solve(factor(A, nd, Options(eps=0.0, symmetric=True)), f)
+    assert np.linalg.norm(u0 - f / lam) <= 1e-12 * np.linalg.norm(f / lam)
+
+
+def _manufactured_error(n, kind):
+    h = 1.0 / (n + 1)
+    x = (np.arange(n) + 1) * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    u = np.sin(np.pi * X) * np.sin(np.pi * Y)
+    if kind == "laplace":
+        A = W.laplace(n, n)
+        f = 2 * np.pi**2 * u
+        sym = True
+    elif kind == "diffusion":
+        xn = np.arange(n + 2) * h
+        Xn, Yn = np.meshgrid(xn, xn, indexing="xy")
+        A = W.diffusion(n, n, 1 + 0.5 * Xn**2 + 0.3 * Yn)
+        a = 1 + 0.5 * X**2 + 0.3 * Y
+        f = (2 * np.pi**2 * a * u - np.pi * X * np.cos(np.pi * X) * np.sin(np.pi * Y)
+             - 0.3 * np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y))
+        sym = True
+    else:
+        bx, by = 10.0, -6.0
+        A = W.convdiff(n, n, (bx, by))
+        f = (2 * np.pi**2 * u + bx * np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+             + by * np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y))
+        sym = False
+    nd = nested_dissection(n, n)
+    uh = solve(factor(A, nd, Options(eps=1e-11, symmetric=sym)), f.ravel())
+    return np.max(np.abs(uh - u.ravel()))
+
+
+@pytest.mark.parametrize("kind,order", [("laplace", 2), ("diffusion", 2), ("convdiff", 1)])
+def test_manufactured_solution_convergence_order(kind, order):
+    e1 = _manufactured_error(31, kind)
+    e2 = _manufactured_error(63, kind)
+    ratio = e1 / e2
+    assert 0.75 * 2**order < ratio < 1.3 * 2**order, ratio
+
+
+@pytest.mark.parametrize("kind", ["laplace", "diffusion", "convdiff"])
+def test_residual_tracks_eps(kind):
+    """R_es ~ eps with about one digit lost (Sec. 6.2); bound it by 1e3 eps."""
+    n = 127
+    P = W.make_problem(kind, n, seed=4, nrhs=1)
+    nd = nested_dissection(n, n)
+    eps = 1e-8
+    F = factor(P.A, nd, Options(eps=eps, symmetric=P.symmetric))
+    X = solve(F, P.B)
+    res = np.linalg.norm(P.B - P.A.matvec(X)) / np.linalg.norm(P.B)
+    assert res <= 1e3 * eps, res
+    ranks = [max(v["ranks"]) for v in F.stats["levels"].values()]
+    sizes = [v["e_max"] for v in F.stats["levels"].values()]
+    assert max(ranks) < 64 and max(sizes) < 80
+    # every sparsification transform has a moderate T (Eq. (norm(T)) as a loose bound)
+    for op in F.tape:
+        if isinstance(op, Sparsify):
+            e, k = op.sk.size + op.r.size, op.sk.size
+            assert np.linalg.norm(op.T) <= math.sqrt(e * k * (e - k)) + 1e-9
+
+
+def test_symmetric_input_gives_symmetric_inverse():
+    """L_t = U_t^T and symmetric LU blocks make the factored inverse symmetric (Sec. 4.4.2)."""
+    P = W.make_problem("diffusion", 63, seed=5, nrhs=1)
+    nd = nested_dissection(63, 63)
+    F = factor(P.A, nd, Options(eps=1e-6, symmetric=True))
+    rng = np.random.default_rng(0)
+    x, y = rng.standard_normal(P.A.n), rng.standard_normal(P.A.n)
+    a, b = y @ solve(F, x), x @ solve(F, y)
+    assert abs(a - b) <= 1e-10 * abs(a)
+    # and the non-symmetric problem does not give a symmetric inverse
+    Q = W.make_problem("convdiff", 63, seed=5, nrhs=1)
+    G = factor(Q.A, nd, Options(eps=1e-6, symmetric=False))
+    a, b = y @ solve(G, x), x @ solve(G, y)
+    assert abs(a - b) > 1e-6 * abs(a)
+
+
+def test_remainders_decoupled_from_neighbours():
+    """A_{r,n} = A_{n,r} = 0 after sparsification (Sec. 2.3.2): every remainder is
+    eliminated against its own skeleton only."""
+    P = W.make_problem("diffusion", 63, seed=6, nrhs=1)
+    nd = nested_dissection(63, 63)
+    F = factor(P.A, nd, Options(eps=1e-6, symmetric=True))
+    last_sparsify = {}
+    for i, op in enumerate(F.tape):
+        if isinstance(op, Sparsify):
+            last_sparsify[tuple(op.r.tolist())] = set(op.sk.tolist())
+        elif isinstance(op, Elim) and tuple(op.p.tolist()) in last_sparsify:
+            assert set(op.q.tolist()) == last_sparsify[tuple(op.p.tolist())]
+
+
+def test_gmres_refines_to_tolerance():
+    P = W.make_problem("diffusion", 63, seed=7, nrhs=1)
+    nd = nested_dissection(63, 63)
+    F = factor(P.A, nd, Options(eps=1e-4, symmetric=True))
+    b = P.B[:, 0]
+    x0 = solve(F, b)
+    r0 = np.linalg.norm(b - P.A.matvec(x0)) / np.linalg.norm(b)
+    x, it, rel = gmres(P.A.matvec, lambda v: solve(F, v), b, x0, m=30, tol=1e-10)
+    assert r0 > 1e-8 and rel <= 1e-10 and 1 <= it <= 30
+    xd = np.linalg.solve(P.A.to_dense(), b)
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
+
+
+def test_high_frequency_helmholtz_needs_refinement():
+    """At 10 points per wavelength the paper gives no accuracy claim (its Helmholtz runs use
+    k = sqrt(2)); the factor is still a strong preconditioner: GMRES reaches 1e-10."""
+    P = W.make_problem("helmholtz", 63, seed=4, nrhs=1)
+    nd = nested_dissection(63, 63)
+    F = factor(P.A, nd, Options(eps=1e-8, symmetric=True))
+    b = P.B[:, 0]
+    x0 = solve(F, b)
+    r0 = np.linalg.norm(b - P.A.matvec(x0)) / np.linalg.norm(b)
+    x, it, rel = gmres(P.A.matvec, lambda v: solve(F, v), b, x0, m=30, tol=1e-10)
+    assert r0 < 0.1 and rel <= 1e-10 and it <= 30, (r0, it, rel)
