@@ -1,0 +1,143 @@
+/*
+ * spalu.h - C ABI of the GB300 implementation of the recursive sparse LU ("spaLU") fast
+ * direct solver for 5-point finite-difference matrices on regular 2-D grids.
+ *
+ * The method (Zhu & Lai, arXiv 2408.14193):
+ *   - nested dissection of the grid into leaf boxes and separators (Sec. 2.2, Alg. 1);
+ *   - elimination of every leaf interior by LU, leaving the Schur complement on the
+ *     separators (Sec. 4.3, first step);
+ *   - for levels l = L..1: sparsification of every separator segment by an interpolative
+ *     decomposition of its sampled interaction block (Secs. 4.1-4.2, 4.5), elimination of
+ *     the redundant (remainder) unknowns, elimination of the level-l separators, and the
+ *     merge of the remaining skeletons into the segments of level l-1 (Sec. 4.3, Alg. 2);
+ *   - the tree-ordered forward / backward solve A ~= W~^{-1} V~^{-1} (Eq. (WV)).
+ *
+ * Conventions shared by every call:
+ *   - Grid: nx x ny interior nodes, natural index g = x + nx*y.  nx+1 and ny+1 must be
+ *     16 * 2^k (leaf boxes of 15 x 15 interior nodes with 1-wide separators).
+ *   - Matrix: CSR in natural order, int32 row pointers / column indices, float64 values,
+ *     device memory owned by the caller; its pattern must be the 5-point stencil (entries
+ *     only between grid neighbours and on the diagonal).
+ *   - Right-hand sides / solutions: float64, column-major, leading dimension ld >= N.
+ *   - Streams: every call enqueues on the given stream (NULL = legacy default stream);
+ *     calls that return results to the host synchronise that stream.
+ *   - Ownership: handles are created and destroyed by the library; all memory passed in
+ *     stays owned by the caller.  A handle is not safe for concurrent use from several
+ *     host threads.
+ *   - Errors: every call returns a status; the library never aborts, exits or traps on the
+ *     device.  Device-side failures (zero pivot, non-finite value) are reported through an
+ *     error word read by the host at the end of the call.
+ */
+#ifndef SPALU_H
+#define SPALU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* spalu_stream_t;          /* same type as cudaStream_t */
+typedef struct spalu_nd_s* spalu_nd_t;               /* opaque, library-owned */
+typedef struct spalu_factor_s* spalu_factor_t;       /* opaque, library-owned, owns device memory */
+
+typedef enum {
+  SPALU_OK = 0,
+  SPALU_ERR_ARG = -1,          /* invalid argument (sizes, pointers, grid shape) */
+  SPALU_ERR_ALLOC = -2,        /* device or host allocation failed */
+  SPALU_ERR_SINGULAR = -3,     /* an exactly zero pivot met in an LU */
+  SPALU_ERR_NOCONV = -4,       /* refinement did not reach the tolerance */
+  SPALU_ERR_TIMEOUT = -5,      /* a bounded device wait expired */
+  SPALU_ERR_CUDA = -6,         /* a CUDA runtime call failed */
+  SPALU_ERR_UNSUPPORTED = -7,  /* valid request this build does not implement */
+  SPALU_ERR_NONFINITE = -8,    /* a NaN or Inf appeared in the factor */
+  SPALU_ERR_STATE = -9         /* call made on a handle in the wrong state */
+} spalu_status;
+
+/* Options fixed at factor time. */
+typedef struct {
+  double eps_id;              /* ID tolerance, relative: stop at the first |R_kk| <= eps |R_11|
+                                 (Sec. 4.1).  0 = no sparsification (exact block LU). */
+  int precision;              /* 0 = FP64 throughout; 1 = mixed (FP32 Schur updates / solve,
+                                 FP64 pivoted LU and CPQR pivots/norms) */
+  int symmetric;              /* 1: caller asserts A = A^T and B = A_{n,i} is sampled;
+                                 0: B = [A_{n,i}; A_{i,n}^T] (Sec. 4.5, Eq. (ID [A_ni; A_in])) */
+  int p_oversample;           /* p of h = k + p (Sec. 4.2.3), default 5 */
+  int near_radius;            /* Chebyshev radius of the near field, default 2 */
+  int h0;                     /* first sketch size, default 16 */
+  unsigned long long seed;    /* key of the Philox4x32-10 stream of the sketch */
+  int gmres_m;                /* restart length of the refinement, default 30 */
+  int gmres_maxit;            /* total iteration cap of the refinement, default 200 */
+  double gmres_tol;           /* target ||b - A x|| / ||b||, default 1e-10 */
+} spalu_opts;
+
+/* Fill *o with the defaults listed above (eps_id = 1e-8, precision 0, symmetric 0). */
+void spalu_default_opts(spalu_opts* o);
+
+const char* spalu_status_string(spalu_status s);
+
+/* Nested dissection of an nx x ny grid (Alg. 1 on a regular grid, Sec. 3).
+ * leaf_pitch must be 16.  Builds the order I (Sec. 2.2) on the device and the level
+ * tables on the host.  *out receives a new handle (release with spalu_nd_destroy). */
+spalu_status spalu_nd_build_grid(int nx, int ny, int leaf_pitch, spalu_stream_t stream,
+                                 spalu_nd_t* out);
+
+/* Copy the ND order to host memory: perm[i] = grid node of the i-th unknown of order I,
+ * iperm[g] = position of node g (either pointer may be NULL).  levels[0] receives L and,
+ * for level l = 1..L, levels[8*l .. 8*l+7] = {bx, by, w, h, vertical_cut, nseg, ncorner,
+ * nsep} of the depth-l box tiling (levels may be NULL; cap = its length in ints).
+ * Synchronises the stream the handle was built on. */
+spalu_status spalu_nd_export(spalu_nd_t nd, int* perm, int* iperm, int* levels, int cap);
+
+/* Grid nodes of the finest-level segments (sides of leaf boxes), segment after segment in
+ * segment-id order, 15 each in increasing coordinate; nodes must hold 15 * nseg(L) ints. */
+spalu_status spalu_nd_export_segments(spalu_nd_t nd, int* nodes, int cap);
+
+void spalu_nd_destroy(spalu_nd_t nd);
+
+/* Allocate a factor for the grid of nd with options o (all device memory is allocated here,
+ * once).  nd must outlive the factor. */
+spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_factor_t* out);
+
+/* Numeric factorization (Alg. 2) of the CSR matrix (device pointers, natural order,
+ * nnz entries).  Enqueued on stream; synchronises it at the end to read the device
+ * error word. */
+spalu_status spalu_factor_numeric(spalu_factor_t f, const int* rowptr, const int* colind,
+                                  const double* val, int nnz, spalu_stream_t stream);
+
+/* Same, with rowptr / colind / val in host memory: the values are copied to the device
+ * inside the call (the pattern is copied only when it changed). */
+spalu_status spalu_factor_numeric_host(spalu_factor_t f, const int* rowptr, const int* colind,
+                                       const double* val, int nnz, spalu_stream_t stream);
+
+/* Direct solve X = V~ W~ B (Eq. (WV)) for nrhs columns (device pointers, column-major,
+ * leading dimension ld).  X may alias B.  Does not synchronise. */
+spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                         spalu_stream_t stream);
+
+/* Iterative refinement by right-preconditioned GMRES(m) with the factor as preconditioner
+ * and an FP64 residual with the last factored matrix: every column is iterated until
+ * ||b - A x|| <= tol ||b||.  X holds the initial guess on entry (e.g. from spalu_solve)
+ * and the result on exit.  iters (host, may be NULL) receives the largest iteration count
+ * over the columns, relres (host, nrhs entries, may be NULL) the final relative residuals.
+ * Returns SPALU_ERR_NOCONV when a column did not converge within gmres_maxit.
+ * Synchronises the stream. */
+spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                          int* iters, double* relres, spalu_stream_t stream);
+
+/* Host-memory variant of solve + refine: B and X are host arrays; the copies to and from
+ * the device happen inside the call.  refine = 0 returns the direct solve. */
+spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                              int refine, int* iters, double* relres, spalu_stream_t stream);
+
+/* JSON summary of the last factorization: per level the segment sizes and ranks, q~
+ * (Sec. 6), device bytes held.  Synchronises the factor's stream. */
+spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap);
+
+void spalu_factor_destroy(spalu_factor_t f);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPALU_H */

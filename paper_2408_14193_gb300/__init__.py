@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) implementation of the recursive sparse LU fast direct solver (spaLU).
+
+The compute path lives in the CUDA library built from ``csrc/`` into ``_build/libspalu.so``
+(C ABI: ``include/spalu.h``); ``spalu`` is a thin ctypes binding with the same names.
+"""
+from .spalu import (Factor, NestedDissection, Options, SpaluError, library_path, load_library,
+                    status_string)
+
+__all__ = ["Factor", "NestedDissection", "Options", "SpaluError", "library_path",
+           "load_library", "status_string"]

@@ -1,0 +1,668 @@
+// C ABI of the spaLU library: nested-dissection handle, factor handle (one device arena
+// planned from the grid), numeric factorization (Alg. 2), tree-ordered solve (Eq. (WV)) and
+// GMRES refinement.  See include/spalu.h for the contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "spalu_internal.h"
+
+using namespace spalu;
+
+struct spalu_nd_s {
+  int nx, ny, L;
+  std::vector<Geo> depth;   // depth 0..L tilings
+  std::vector<int> vcut;    // [1..L]
+  int* d_perm = nullptr;
+  int* d_iperm = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
+struct GmresWork {
+  int nrhs = 0, m = 0;
+  double* V = nullptr;      // (m+1) * N * nrhs
+  double* W = nullptr;      // N * nrhs
+  double* R = nullptr;      // N * nrhs
+  double* part = nullptr;   // partial sums
+  double* hcol = nullptr;   // device coefficients (m+2) * nrhs
+  double* vec = nullptr;    // nrhs scalars
+};
+
+struct spalu_factor_s {
+  spalu_nd_s* nd = nullptr;
+  spalu_opts o{};
+  int N = 0, nnz_cap = 0;
+  std::vector<LevelPlan> plan;   // [1..L]
+  std::vector<LevelDev> lev;     // [1..L]
+  LeafDev leaf{};
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  int* d_err = nullptr;
+  int* rowptr = nullptr;
+  int* colind = nullptr;
+  double* val = nullptr;
+  int nnz = 0;
+  bool factored = false;
+  cudaStream_t last_stream = nullptr;
+  GmresWork gw;
+  std::vector<int> host_rowptr_cache;
+};
+
+namespace {
+
+const int kPitch = 16;
+
+bool side_ok(int n) {
+  if (n < LEAF || (n + 1) % kPitch) return false;
+  int q = (n + 1) / kPitch;
+  return (q & (q - 1)) == 0;
+}
+
+#define CUDA_TRY(x)                                   \
+  do {                                                \
+    cudaError_t _e = (x);                             \
+    if (_e != cudaSuccess) return SPALU_ERR_CUDA;     \
+  } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Carver {
+  size_t off = 0;
+  char* base = nullptr;
+  template <class T>
+  T* take(size_t n) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+spalu_status read_err(spalu_factor_t f, cudaStream_t s) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h & ERR_SINGULAR) return SPALU_ERR_SINGULAR;
+  if (h & ERR_NONFINITE) return SPALU_ERR_NONFINITE;
+  if (h & ERR_TIMEOUT) return SPALU_ERR_TIMEOUT;
+  if (h & ERR_CAPACITY) return SPALU_ERR_UNSUPPORTED;
+  return SPALU_OK;
+}
+
+// ------------------------------------------------------------ GMRES helper kernels
+__global__ void spmv_residual_kernel(int n, const int* rowptr, const int* colind, const double* val,
+                                     const double* x, int ldx, const double* b, int ldb, double* y,
+                                     int ldy, int nrhs) {
+  long long tot = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % n), c = (int)(e / n);
+    double acc = 0.0;
+    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) acc += val[p] * x[colind[p] + (size_t)ldx * c];
+    y[r + (size_t)ldy * c] = b ? b[r + (size_t)ldb * c] - acc : acc;
+  }
+}
+
+// partial dot products: part[c * nb + blockIdx.x] (deterministic two-pass reduction)
+__global__ void dot_partial_kernel(int n, const double* x, int ldx, const double* y, int ldy,
+                                   double* part) {
+  __shared__ double red[32];
+  const int c = blockIdx.y;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s += x[i + (size_t)ldx * c] * y[i + (size_t)ldy * c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void dot_final_kernel(const double* part, int nb, double* out, int sq) {
+  const int c = blockIdx.x;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)c * nb + b];
+    out[c] = sq ? sqrt(s) : s;
+  }
+}
+
+// y[:, c] += alpha * coef[c] * x[:, c]
+__global__ void axpy_kernel(int n, int nrhs, double alpha, const double* coef, const double* x,
+                            int ldx, double* y, int ldy) {
+  long long tot = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % n), c = (int)(e / n);
+    y[r + (size_t)ldy * c] += alpha * coef[c] * x[r + (size_t)ldx * c];
+  }
+}
+
+// y[:, c] = x[:, c] / s[c] (zero when s[c] == 0)
+__global__ void scale_kernel(int n, int nrhs, const double* s, const double* x, int ldx, double* y,
+                             int ldy) {
+  long long tot = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % n), c = (int)(e / n);
+    double d = s[c];
+    y[r + (size_t)ldy * c] = d != 0.0 ? x[r + (size_t)ldx * c] / d : 0.0;
+  }
+}
+
+__global__ void copy_cols_kernel(int n, int nrhs, const double* x, int ldx, double* y, int ldy) {
+  long long tot = (long long)n * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % n), c = (int)(e / n);
+    y[r + (size_t)ldy * c] = x[r + (size_t)ldx * c];
+  }
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)std::max(1ll, b);
+}
+
+}  // namespace
+
+// ============================================================ public entry points
+extern "C" {
+
+void spalu_default_opts(spalu_opts* o) {
+  if (!o) return;
+  o->eps_id = 1e-8;
+  o->precision = 0;
+  o->symmetric = 0;
+  o->p_oversample = 5;
+  o->near_radius = 2;
+  o->h0 = 16;
+  o->seed = 0;
+  o->gmres_m = 30;
+  o->gmres_maxit = 200;
+  o->gmres_tol = 1e-10;
+}
+
+const char* spalu_status_string(spalu_status s) {
+  switch (s) {
+    case SPALU_OK: return "ok";
+    case SPALU_ERR_ARG: return "invalid argument";
+    case SPALU_ERR_ALLOC: return "allocation failed";
+    case SPALU_ERR_SINGULAR: return "zero pivot in an LU";
+    case SPALU_ERR_NOCONV: return "refinement did not converge";
+    case SPALU_ERR_TIMEOUT: return "bounded device wait expired";
+    case SPALU_ERR_CUDA: return "CUDA runtime error";
+    case SPALU_ERR_UNSUPPORTED: return "unsupported request";
+    case SPALU_ERR_NONFINITE: return "non-finite value in the factor";
+    case SPALU_ERR_STATE: return "handle in the wrong state";
+  }
+  return "unknown status";
+}
+
+spalu_status spalu_nd_build_grid(int nx, int ny, int leaf_pitch, spalu_stream_t stream,
+                                 spalu_nd_t* out) {
+  if (!out) return SPALU_ERR_ARG;
+  *out = nullptr;
+  if (leaf_pitch != kPitch) return SPALU_ERR_UNSUPPORTED;
+  if (!side_ok(nx) || !side_ok(ny)) return SPALU_ERR_ARG;
+  if ((long long)nx * ny > (1ll << 30)) return SPALU_ERR_UNSUPPORTED;
+  auto* nd = new spalu_nd_s();
+  nd->nx = nx;
+  nd->ny = ny;
+  nd->stream = (cudaStream_t)stream;
+  Geo g{1, 1, nx, ny};
+  nd->depth.push_back(g);
+  nd->vcut.push_back(0);
+  while (!(g.w == LEAF && g.h == LEAF)) {
+    Geo c = g;
+    if (g.w < g.h) { c.h = (g.h - 1) / 2; c.by = 2 * g.by; nd->vcut.push_back(0); }
+    else { c.w = (g.w - 1) / 2; c.bx = 2 * g.bx; nd->vcut.push_back(1); }
+    nd->depth.push_back(c);
+    g = c;
+  }
+  nd->L = (int)nd->depth.size() - 1;
+  size_t n = (size_t)nx * ny;
+  if (cudaMalloc(&nd->d_perm, n * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&nd->d_iperm, n * sizeof(int)) != cudaSuccess) {
+    cudaFree(nd->d_perm);
+    delete nd;
+    return SPALU_ERR_ALLOC;
+  }
+  launch_nd_perm(nx, ny, nd->L, nd->vcut.data(), nd->d_perm, nd->d_iperm, nd->stream);
+  if (cudaGetLastError() != cudaSuccess) {
+    spalu_nd_destroy(nd);
+    return SPALU_ERR_CUDA;
+  }
+  *out = nd;
+  return SPALU_OK;
+}
+
+spalu_status spalu_nd_export(spalu_nd_t nd, int* perm, int* iperm, int* levels, int cap) {
+  if (!nd) return SPALU_ERR_ARG;
+  size_t n = (size_t)nd->nx * nd->ny;
+  if (perm) CUDA_TRY(cudaMemcpyAsync(perm, nd->d_perm, n * sizeof(int), cudaMemcpyDeviceToHost, nd->stream));
+  if (iperm) CUDA_TRY(cudaMemcpyAsync(iperm, nd->d_iperm, n * sizeof(int), cudaMemcpyDeviceToHost, nd->stream));
+  CUDA_TRY(cudaStreamSynchronize(nd->stream));
+  if (levels) {
+    if (cap < 8 * (nd->L + 1)) return SPALU_ERR_ARG;
+    levels[0] = nd->L;
+    for (int l = 1; l <= nd->L; ++l) {
+      const Geo& g = nd->depth[l];
+      int* v = levels + 8 * l;
+      v[0] = g.bx; v[1] = g.by; v[2] = g.w; v[3] = g.h; v[4] = nd->vcut[l];
+      v[5] = g.nseg(); v[6] = g.ncorner(); v[7] = nd->depth[l - 1].nbox();
+    }
+  }
+  return SPALU_OK;
+}
+
+spalu_status spalu_nd_export_segments(spalu_nd_t nd, int* nodes, int cap) {
+  if (!nd || !nodes) return SPALU_ERR_ARG;
+  if (nd->L == 0) return SPALU_OK;
+  const Geo& g = nd->depth[nd->L];
+  if (cap < LEAF * g.nseg()) return SPALU_ERR_ARG;
+  for (int s = 0; s < g.nseg(); ++s)
+    for (int t = 0; t < LEAF; ++t) nodes[(size_t)s * LEAF + t] = g.seg_node(s, t, nd->nx);
+  return SPALU_OK;
+}
+
+void spalu_nd_destroy(spalu_nd_t nd) {
+  if (!nd) return;
+  cudaFree(nd->d_perm);
+  cudaFree(nd->d_iperm);
+  delete nd;
+}
+
+spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_factor_t* out) {
+  if (!nd || !o || !out) return SPALU_ERR_ARG;
+  *out = nullptr;
+  if (!(o->eps_id >= 0.0) || o->p_oversample < 0 || o->h0 < 1 || o->near_radius < 0 ||
+      o->gmres_m < 1 || o->gmres_maxit < 0)
+    return SPALU_ERR_ARG;
+  if (o->precision != 0) return SPALU_ERR_UNSUPPORTED;
+  auto* f = new spalu_factor_s();
+  f->nd = nd;
+  f->o = *o;
+  f->N = nd->nx * nd->ny;
+  f->nnz_cap = 5 * f->N;
+  const int L = nd->L;
+  f->plan.resize(L + 1);
+  f->lev.resize(L + 1);
+  // leading dimensions of the frontal stores per depth
+  std::vector<int> ldF(L + 1, 0);
+  for (int dd = 0; dd <= L; ++dd) {
+    const Geo& g = nd->depth[dd];
+    int sep = 0;
+    if (dd < L) sep = nd->vcut[dd + 1] ? g.h : g.w;
+    ldF[dd] = g.D() + sep;
+  }
+  for (int l = 1; l <= L; ++l) {
+    LevelPlan& p = f->plan[l];
+    p.l = l;
+    p.vcut = nd->vcut[l];
+    p.g = nd->depth[l];
+    p.gp = nd->depth[l - 1];
+    p.capS = p.g.cap();
+    p.ldF = ldF[l];
+    p.ldFp = ldF[l - 1];
+    p.sepcap = p.vcut ? p.gp.h : p.gp.w;
+    p.Ycap = 2 * 16 + std::max(o->h0, 2 * (p.capS + o->p_oversample));
+    size_t need = sparsify_smem_need(p.capS, o->symmetric, o->h0, o->p_oversample);
+    size_t lim = 160 * 1024;
+    size_t mn = sparsify_smem_min(p.capS, o->symmetric, o->h0, o->p_oversample);
+    p.spars_smem = std::min(need, std::max(lim, mn));
+    p.spars_global = need > p.spars_smem;
+  }
+  // plan the arena (two passes: sizes, then pointers)
+  for (int pass = 0; pass < 2; ++pass) {
+    Carver cv;
+    cv.base = pass ? f->arena : nullptr;
+    f->d_err = cv.take<int>(4);
+    f->rowptr = cv.take<int>(f->N + 1);
+    f->colind = cv.take<int>(f->nnz_cap);
+    f->val = cv.take<double>(f->nnz_cap);
+    const Geo& gl = nd->depth[L];
+    LeafDev& lf = f->leaf;
+    lf.nx = nd->nx; lf.ny = nd->ny; lf.L = L; lf.g = gl; lf.ldF = ldF[L];
+    lf.F = cv.take<double>((size_t)gl.nbox() * ldF[L] * ldF[L]);
+    lf.band = cv.take<double>((size_t)gl.nbox() * LDAB * NI);
+    lf.piv = cv.take<int>((size_t)gl.nbox() * NI);
+    std::vector<double*> Fst(L + 1, nullptr);
+    Fst[L] = lf.F;
+    for (int l = L; l >= 1; --l) {
+      const LevelPlan& p = f->plan[l];
+      LevelDev& d = f->lev[l];
+      const int nseg = p.g.nseg();
+      d.l = l; d.nx = nd->nx; d.ny = nd->ny; d.vcut = p.vcut;
+      d.g = p.g; d.gp = p.gp;
+      d.capS = p.capS; d.ldF = p.ldF; d.ldFp = p.ldFp; d.Ycap = p.Ycap; d.sepcap = p.sepcap;
+      d.cnt = cv.take<int>(nseg);
+      d.kk = cv.take<int>(nseg);
+      d.hs = cv.take<int>(nseg);
+      d.nodes = cv.take<int>((size_t)nseg * p.capS);
+      d.perm = cv.take<int>((size_t)nseg * p.capS);
+      d.piv = cv.take<int>((size_t)nseg * p.capS);
+      d.T = cv.take<double>((size_t)nseg * p.capS * p.capS);
+      d.Dm = cv.take<double>((size_t)nseg * p.capS * p.capS);
+      d.Yg = p.spars_global ? cv.take<double>((size_t)nseg * p.Ycap * p.capS) : nullptr;
+      Fst[l - 1] = cv.take<double>((size_t)p.gp.nbox() * p.ldFp * p.ldFp);
+      d.F = Fst[l];
+      d.Fp = Fst[l - 1];
+      d.ptab = cv.take<int>((size_t)p.gp.nbox() * p.ldFp * 8);
+      d.pcount = cv.take<int>((size_t)p.gp.nbox() * 2);
+      d.ppiv = cv.take<int>((size_t)p.gp.nbox() * p.sepcap);
+      d.eps = o->eps_id; d.symmetric = o->symmetric; d.p_over = o->p_oversample;
+      d.near_radius = o->near_radius; d.h0 = o->h0; d.seed = o->seed;
+    }
+    for (int l = L; l >= 1; --l) {
+      LevelDev& d = f->lev[l];
+      if (l > 1) { d.cnt_up = f->lev[l - 1].cnt; d.nodes_up = f->lev[l - 1].nodes; d.capS_up = f->lev[l - 1].capS; }
+      else { d.cnt_up = nullptr; d.nodes_up = nullptr; d.capS_up = 0; }
+    }
+    if (pass == 0) {
+      f->arena_bytes = align_up(cv.off, 256);
+      if (cudaMalloc(&f->arena, f->arena_bytes) != cudaSuccess) {
+        delete f;
+        return SPALU_ERR_ALLOC;
+      }
+    }
+  }
+  f->leaf.rowptr = f->rowptr;
+  f->leaf.colind = f->colind;
+  f->leaf.val = f->val;
+  f->leaf.err = f->d_err;
+  for (int l = 1; l <= L; ++l) f->lev[l].err = f->d_err;
+  *out = f;
+  return SPALU_OK;
+}
+
+static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
+  const int L = f->nd->L;
+  CUDA_TRY(cudaMemsetAsync(f->d_err, 0, sizeof(int), s));
+  if (L >= 1) launch_level_init_L(f->lev[L], s);
+  launch_leaf_factor(f->leaf, s);
+  for (int l = L; l >= 1; --l) {
+    launch_sparsify(f->lev[l], f->plan[l], s);
+    launch_merge(f->lev[l], f->plan[l], s);
+  }
+  CUDA_TRY(cudaGetLastError());
+  spalu_status st = read_err(f, s);
+  f->factored = (st == SPALU_OK);
+  f->last_stream = s;
+  return st;
+}
+
+spalu_status spalu_factor_numeric(spalu_factor_t f, const int* rowptr, const int* colind,
+                                  const double* val, int nnz, spalu_stream_t stream) {
+  if (!f || !rowptr || !colind || !val || nnz < 0 || nnz > f->nnz_cap) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  f->nnz = nnz;
+  CUDA_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (f->N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return factor_run(f, s);
+}
+
+spalu_status spalu_factor_numeric_host(spalu_factor_t f, const int* rowptr, const int* colind,
+                                       const double* val, int nnz, spalu_stream_t stream) {
+  if (!f || !rowptr || !colind || !val || nnz < 0 || nnz > f->nnz_cap) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool same = f->nnz == nnz && (int)f->host_rowptr_cache.size() == f->N + 1 &&
+              std::memcmp(f->host_rowptr_cache.data(), rowptr, (f->N + 1) * sizeof(int)) == 0;
+  f->nnz = nnz;
+  if (!same) {
+    CUDA_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (f->N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, s));
+    f->host_rowptr_cache.assign(rowptr, rowptr + f->N + 1);
+  }
+  CUDA_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+  return factor_run(f, s);
+}
+
+spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                         spalu_stream_t stream) {
+  if (!f || !B || !X || nrhs < 0 || ld < f->N) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  if (nrhs == 0) return SPALU_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = f->nd->L;
+  if (X != B)
+    CUDA_TRY(cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), B, (size_t)ld * sizeof(double),
+                               (size_t)f->N * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    int nc = std::min(32, nrhs - c0);
+    launch_leaf_solve_fwd(f->leaf, X + (size_t)ld * c0, nc, ld, s);
+  }
+  if (L >= 1) launch_sep_update_fwd(f->leaf, X, nrhs, ld, s);
+  for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], X, nrhs, ld, s);
+  for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], X, nrhs, ld, s);
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    int nc = std::min(32, nrhs - c0);
+    launch_leaf_solve_bwd(f->leaf, X + (size_t)ld * c0, nc, ld, nullptr, s);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return SPALU_OK;
+}
+
+static spalu_status gmres_alloc(spalu_factor_t f, int nrhs) {
+  GmresWork& w = f->gw;
+  const int m = f->o.gmres_m;
+  if (w.nrhs >= nrhs && w.m == m) return SPALU_OK;
+  cudaFree(w.V); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  w = GmresWork();
+  size_t N = f->N;
+  if (cudaMalloc(&w.V, sizeof(double) * (m + 1) * N * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.W, sizeof(double) * N * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.R, sizeof(double) * N * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.part, sizeof(double) * 1024 * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.hcol, sizeof(double) * (m + 2) * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.vec, sizeof(double) * 4 * nrhs) != cudaSuccess)
+    return SPALU_ERR_ALLOC;
+  w.nrhs = nrhs;
+  w.m = m;
+  return SPALU_OK;
+}
+
+// out[c] = <x_c, y_c> (or its square root) for nrhs columns, deterministic order
+static void dots(spalu_factor_t f, const double* x, int ldx, const double* y, int ldy, int nrhs,
+                 double* out, int sq, cudaStream_t s) {
+  const int nb = 512;
+  dim3 grid(nb, nrhs);
+  dot_partial_kernel<<<grid, 256, 0, s>>>(f->N, x, ldx, y, ldy, f->gw.part);
+  dot_final_kernel<<<nrhs, 32, 0, s>>>(f->gw.part, nb, out, sq);
+}
+
+spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                          int* iters, double* relres, spalu_stream_t stream) {
+  if (!f || !B || !X || nrhs < 0 || ld < f->N) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  if (nrhs == 0) return SPALU_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  spalu_status st = gmres_alloc(f, nrhs);
+  if (st != SPALU_OK) return st;
+  GmresWork& w = f->gw;
+  const int N = f->N, m = f->o.gmres_m;
+  const double tol = f->o.gmres_tol;
+  const int maxit = f->o.gmres_maxit;
+  const size_t ldv = (size_t)N;
+  auto Vj = [&](int j) { return w.V + (size_t)j * ldv * nrhs; };
+  std::vector<double> bn(nrhs), beta(nrhs), hh((size_t)(m + 2) * nrhs);
+  double* dvec = w.vec;   // [0, nrhs): norms; [nrhs, 2 nrhs): scratch
+  dots(f, B, ld, B, ld, nrhs, dvec, 1, s);
+  CUDA_TRY(cudaMemcpyAsync(bn.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  auto residual = [&]() -> spalu_status {
+    spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, X, ld, B, ld, w.R, (int)ldv, nrhs);
+    dots(f, w.R, (int)ldv, w.R, (int)ldv, nrhs, dvec, 1, s);
+    CUDA_TRY(cudaMemcpyAsync(beta.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SPALU_OK;
+  };
+  if ((st = residual()) != SPALU_OK) return st;
+  int it = 0;
+  auto done = [&](int c) { return bn[c] == 0.0 || beta[c] <= tol * bn[c]; };
+  std::vector<std::vector<double>> H(nrhs, std::vector<double>((size_t)(m + 1) * m, 0.0));
+  std::vector<std::vector<double>> cs(nrhs, std::vector<double>(m)), sn(nrhs, std::vector<double>(m)),
+      g(nrhs, std::vector<double>(m + 1));
+  std::vector<double> ycoef((size_t)m * nrhs);
+  while (it < maxit) {
+    bool all = true;
+    for (int c = 0; c < nrhs; ++c) all = all && done(c);
+    if (all) break;
+    // V_0 = r / beta (finished columns carry zeros)
+    std::vector<double> bsc(nrhs);
+    for (int c = 0; c < nrhs; ++c) bsc[c] = done(c) ? 0.0 : beta[c];
+    CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, bsc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    scale_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, dvec + nrhs, w.R, (int)ldv, Vj(0), (int)ldv);
+    for (int c = 0; c < nrhs; ++c) {
+      std::fill(H[c].begin(), H[c].end(), 0.0);
+      std::fill(g[c].begin(), g[c].end(), 0.0);
+      g[c][0] = bsc[c];
+    }
+    int jl = -1;
+    for (int j = 0; j < m; ++j) {
+      // W = A M^{-1} V_j
+      copy_cols_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, Vj(j), (int)ldv, w.W, (int)ldv);
+      if ((st = spalu_solve(f, w.W, w.W, nrhs, (int)ldv, stream)) != SPALU_OK) return st;
+      spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, w.W, (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, nrhs);
+      // modified Gram-Schmidt
+      for (int i = 0; i <= j; ++i) {
+        dots(f, Vj(j + 1), (int)ldv, Vj(i), (int)ldv, nrhs, w.hcol + (size_t)i * nrhs, 0, s);
+        axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, -1.0, w.hcol + (size_t)i * nrhs, Vj(i), (int)ldv, Vj(j + 1), (int)ldv);
+      }
+      dots(f, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv, nrhs, w.hcol + (size_t)(j + 1) * nrhs, 1, s);
+      scale_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, w.hcol + (size_t)(j + 1) * nrhs, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
+      CUDA_TRY(cudaMemcpyAsync(hh.data(), w.hcol, sizeof(double) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      ++it;
+      jl = j;
+      bool allc = true;
+      for (int c = 0; c < nrhs; ++c) {
+        double* Hc = H[c].data();
+        for (int i = 0; i <= j; ++i) Hc[i + (m + 1) * j] = hh[(size_t)i * nrhs + c];
+        Hc[(j + 1) + (m + 1) * j] = hh[(size_t)(j + 1) * nrhs + c];
+        for (int i = 0; i < j; ++i) {
+          double a = Hc[i + (m + 1) * j], b = Hc[i + 1 + (m + 1) * j];
+          Hc[i + (m + 1) * j] = cs[c][i] * a + sn[c][i] * b;
+          Hc[i + 1 + (m + 1) * j] = -sn[c][i] * a + cs[c][i] * b;
+        }
+        double a = Hc[j + (m + 1) * j], b = Hc[j + 1 + (m + 1) * j];
+        double den = std::hypot(a, b);
+        cs[c][j] = den == 0.0 ? 1.0 : a / den;
+        sn[c][j] = den == 0.0 ? 0.0 : b / den;
+        Hc[j + (m + 1) * j] = den;
+        Hc[j + 1 + (m + 1) * j] = 0.0;
+        g[c][j + 1] = -sn[c][j] * g[c][j];
+        g[c][j] = cs[c][j] * g[c][j];
+        if (!(done(c) || std::fabs(g[c][j + 1]) <= tol * bn[c])) allc = false;
+      }
+      if (allc || it >= maxit) break;
+    }
+    // y from the triangular system, U = V y, X += M^{-1} U
+    const int kdim = jl + 1;
+    for (int c = 0; c < nrhs; ++c) {
+      double* Hc = H[c].data();
+      for (int i = kdim - 1; i >= 0; --i) {
+        double sum = g[c][i];
+        for (int q = i + 1; q < kdim; ++q) sum -= Hc[i + (m + 1) * q] * ycoef[(size_t)q * nrhs + c];
+        ycoef[(size_t)i * nrhs + c] = (done(c) || Hc[i + (m + 1) * i] == 0.0) ? 0.0 : sum / Hc[i + (m + 1) * i];
+      }
+    }
+    CUDA_TRY(cudaMemsetAsync(w.W, 0, sizeof(double) * ldv * nrhs, s));
+    CUDA_TRY(cudaMemcpyAsync(w.hcol, ycoef.data(), sizeof(double) * kdim * nrhs, cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < kdim; ++i)
+      axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, w.hcol + (size_t)i * nrhs, Vj(i), (int)ldv, w.W, (int)ldv);
+    if ((st = spalu_solve(f, w.W, w.W, nrhs, (int)ldv, stream)) != SPALU_OK) return st;
+    std::vector<double> ones(nrhs, 1.0);
+    CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, ones.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, dvec + nrhs, w.W, (int)ldv, X, ld);
+    if ((st = residual()) != SPALU_OK) return st;
+  }
+  bool conv = true;
+  for (int c = 0; c < nrhs; ++c) {
+    if (relres) relres[c] = bn[c] == 0.0 ? 0.0 : beta[c] / bn[c];
+    conv = conv && done(c);
+  }
+  if (iters) *iters = it;
+  CUDA_TRY(cudaGetLastError());
+  return conv ? SPALU_OK : SPALU_ERR_NOCONV;
+}
+
+spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                              int refine, int* iters, double* relres, spalu_stream_t stream) {
+  if (!f || !B || !X || nrhs < 0 || ld < f->N) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  double *dB = nullptr, *dX = nullptr;
+  size_t bytes = sizeof(double) * (size_t)f->N * nrhs;
+  if (cudaMallocAsync(&dB, bytes, s) != cudaSuccess || cudaMallocAsync(&dX, bytes, s) != cudaSuccess)
+    return SPALU_ERR_ALLOC;
+  spalu_status st = SPALU_OK;
+  if (cudaMemcpy2DAsync(dB, (size_t)f->N * sizeof(double), B, (size_t)ld * sizeof(double),
+                        (size_t)f->N * sizeof(double), nrhs, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    st = SPALU_ERR_CUDA;
+  if (st == SPALU_OK) st = spalu_solve(f, dB, dX, nrhs, f->N, stream);
+  if (st == SPALU_OK && refine) st = spalu_refine(f, dB, dX, nrhs, f->N, iters, relres, stream);
+  spalu_status st2 = SPALU_OK;
+  if (st == SPALU_OK || st == SPALU_ERR_NOCONV) {
+    if (cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), dX, (size_t)f->N * sizeof(double),
+                          (size_t)f->N * sizeof(double), nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st2 = SPALU_ERR_CUDA;
+  }
+  cudaFreeAsync(dB, s);
+  cudaFreeAsync(dX, s);
+  return st != SPALU_OK ? st : st2;
+}
+
+spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
+  if (!f || !json || cap == 0) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  const int L = f->nd->L;
+  std::string out = "{\"L\": " + std::to_string(L) + ", \"arena_bytes\": " + std::to_string(f->arena_bytes) + ", \"levels\": [";
+  double qt = 0.0;
+  for (int l = 1; l <= L; ++l) {
+    const LevelDev& d = f->lev[l];
+    int n = d.g.nseg();
+    std::vector<int> cnt(n), kk(n), hs(n);
+    CUDA_TRY(cudaMemcpy(cnt.data(), d.cnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(kk.data(), d.kk, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(hs.data(), d.hs, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    int emax = 0, kmax = 0;
+    long long esum = 0, ksum = 0;
+    for (int i = 0; i < n; ++i) {
+      emax = std::max(emax, cnt[i]);
+      kmax = std::max(kmax, kk[i]);
+      esum += cnt[i];
+      ksum += kk[i];
+    }
+    if (emax > 0) qt = std::max(qt, (double)kmax / emax);
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld}",
+                  l == 1 ? "" : ", ", l, n, emax, kmax, esum, ksum);
+    out += buf;
+  }
+  char buf[64];
+  std::snprintf(buf, sizeof buf, "], \"q_tilde\": %.6f}", qt);
+  out += buf;
+  if (out.size() + 1 > cap) return SPALU_ERR_ARG;
+  std::memcpy(json, out.c_str(), out.size() + 1);
+  return SPALU_OK;
+}
+
+void spalu_factor_destroy(spalu_factor_t f) {
+  if (!f) return;
+  cudaFree(f->arena);
+  GmresWork& w = f->gw;
+  cudaFree(w.V); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  delete f;
+}
+
+}  // extern "C"

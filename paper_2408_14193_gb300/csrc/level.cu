@@ -1,0 +1,1166 @@
+// One level of the spaLU factorization (Sec. 4.3, Alg. 2, l = L..1) and its solve.
+//
+// Data model: the Schur complement A^(l) is the sum over the depth-l boxes of dense
+// "frontal" blocks over each box's boundary unknowns (its four sides and corners); a side
+// shared by two boxes is one segment.  Per level:
+//   sparsify_kernel   one CTA per segment: hybrid sketch Y = [B_N; G B_F / sqrt(h)] of
+//                     B = [A_{n,i}; A_{i,n}^T] (Eqs. (Phi), (ID [A_ni; A_in])), column-pivoted
+//                     QR and T = R_1^{-1} R_2 (Eqs. (RRQR 1), (RRQR 2)), the transform of the
+//                     segment's own block by U_t, L_t (Eq. (UtALt)), LU of the remainder and
+//                     its Schur update onto the skeleton (Eq. (L^-1 * A * U^-1)).
+//   merge_*_kernels   one parent (depth l-1 box) at a time: extend-add of its two children
+//                     restricted to skeletons (the permutation E_(l)), LU of the level-l
+//                     separator's skeleton block and the Schur update onto the parent's
+//                     boundary, which is the parent's frontal for level l-1.
+// The neighbour couplings of a remainder are dropped (they are O(eps) after the
+// transform), and the couplings between skeletons are unchanged by the transforms, so only
+// the segment's own diagonal block is transformed.
+#include <cfloat>
+#include <cmath>
+
+#include "spalu_internal.h"
+
+namespace spalu {
+namespace {
+
+constexpr int NEAR_MAX = 16;      // near unknowns per segment (the geometry gives <= 10)
+constexpr int RUN_MAX = 16;
+constexpr int SK_CHUNK = 16;      // far unknowns per chunk of the sketch product
+constexpr double TIE_RTOL = 1e-12;
+
+// ------------------------------------------------------------ Philox4x32-10 (SC'11)
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+// Entry of the sampling matrix G: counter (r, node, 2l+t, sid), key = seed; float32
+// Box-Muller from the first two words, u = odd multiple of 2^-24.
+__device__ __forceinline__ float sketch_gauss(unsigned long long seed, int l, int sid, int r, int node, int t) {
+  uint32_t c[4] = {(uint32_t)r, (uint32_t)node, (uint32_t)(2 * l + t), (uint32_t)sid};
+  philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+  float u1 = (float)(((c[0] >> 9) << 1) | 1u) * 0x1p-24f;
+  float u2 = (float)(((c[1] >> 9) << 1) | 1u) * 0x1p-24f;
+  float rad = sqrtf(-2.0f * logf(u1));
+  float ang = 6.283185307179586f * u2;
+  return rad * cosf(ang);
+}
+
+// ------------------------------------------------------------ neighbour runs of a segment
+struct Run {
+  int p1, p2, len, ref;   // positions in box 1 / box 2 (-1: absent), count, seg id or -2-node
+};
+
+struct SegCtx {
+  int sid, e, b1, b2, s1, s2;   // boxes (b1 = lower/left owner) and position of the segment
+  int horiz, line, lo, hi;      // geometric extent
+  int nrun, nb;
+  Run run[RUN_MAX];
+};
+
+__device__ void seg_context(const LevelDev& d, int sid, SegCtx& S) {
+  const Geo g = d.g;
+  int I1, J1, I2, J2;
+  S.sid = sid;
+  S.e = d.cnt[sid];
+  if (sid < g.nh()) {
+    int I = sid % g.bx, J = sid / g.bx + 1;
+    I1 = I; J1 = J - 1; I2 = I; J2 = J;
+    S.s1 = g.side_pos(SIDE_TOP);
+    S.s2 = g.side_pos(SIDE_BOTTOM);
+    S.horiz = 1;
+    S.line = J * (g.h + 1) - 1;
+    S.lo = I * (g.w + 1);
+    S.hi = S.lo + g.w - 1;
+  } else {
+    int t = sid - g.nh();
+    int I = t % (g.bx - 1) + 1, J = t / (g.bx - 1);
+    I1 = I - 1; J1 = J; I2 = I; J2 = J;
+    S.s1 = g.side_pos(SIDE_RIGHT);
+    S.s2 = g.side_pos(SIDE_LEFT);
+    S.horiz = 0;
+    S.line = I * (g.w + 1) - 1;
+    S.lo = J * (g.h + 1);
+    S.hi = S.lo + g.h - 1;
+  }
+  S.b1 = I1 + g.bx * J1;
+  S.b2 = I2 + g.bx * J2;
+  const int skip1 = S.horiz ? SIDE_TOP : SIDE_RIGHT;
+  const int skip2 = S.horiz ? SIDE_BOTTOM : SIDE_LEFT;
+  int n = 0, nb = 0;
+  for (int side = 0; side < 4; ++side) {
+    if (side == skip1) continue;
+    int sg = g.box_side(I1, J1, side);
+    if (sg >= 0) { S.run[n] = {g.side_pos(side), -1, d.cnt[sg], sg}; nb += S.run[n].len; ++n; }
+  }
+  for (int side = 0; side < 4; ++side) {
+    if (side == skip2) continue;
+    int sg = g.box_side(I2, J2, side);
+    if (sg >= 0) { S.run[n] = {-1, g.side_pos(side), d.cnt[sg], sg}; nb += S.run[n].len; ++n; }
+  }
+  // shared corners: horizontal (b1 below b2): b1.TL = b2.BL, b1.TR = b2.BR;
+  //                 vertical (b1 left of b2):  b1.BR = b2.BL, b1.TR = b2.TL
+  for (int c = 0; c < 4; ++c) {
+    int cid = g.box_corner(I1, J1, c);
+    if (cid < 0) continue;
+    int c2 = -1;
+    if (S.horiz) { if (c == C_TL) c2 = C_BL; else if (c == C_TR) c2 = C_BR; }
+    else { if (c == C_BR) c2 = C_BL; else if (c == C_TR) c2 = C_TL; }
+    S.run[n] = {g.corner_pos(c), c2 >= 0 ? g.corner_pos(c2) : -1, 1, -2 - g.junction_node(cid, d.nx)};
+    ++nb; ++n;
+  }
+  for (int c = 0; c < 4; ++c) {
+    int cid = g.box_corner(I2, J2, c);
+    if (cid < 0) continue;
+    bool shared = S.horiz ? (c == C_BL || c == C_BR) : (c == C_BL || c == C_TL);
+    if (shared) continue;
+    S.run[n] = {-1, g.corner_pos(c), 1, -2 - g.junction_node(cid, d.nx)};
+    ++nb; ++n;
+  }
+  S.nrun = n;
+  S.nb = nb;
+}
+
+__device__ __forceinline__ void locate(const SegCtx& S, int f, int& r, int& i) {
+  r = 0;
+  while (f >= S.run[r].len) { f -= S.run[r].len; ++r; }
+  i = f;
+}
+
+__device__ __forceinline__ int run_node(const LevelDev& d, const Run& R, int i) {
+  return R.ref >= 0 ? d.nodes[(size_t)R.ref * d.capS + i] : (-2 - R.ref);
+}
+
+__device__ __forceinline__ int cheb(const SegCtx& S, int node, int nx) {
+  int x = node % nx, y = node / nx;
+  int a = S.horiz ? y : x, b = S.horiz ? x : y;
+  int da = abs(a - S.line);
+  int db = max(0, max(S.lo - b, b - S.hi));
+  return max(da, db);
+}
+
+// B entry for neighbour f (run r, element i), half t (0: A[v, s_c], 1: A[s_c, v]), column c
+__device__ __forceinline__ double bval(const LevelDev& d, const SegCtx& S, const double* F1,
+                                       const double* F2, const Run& R, int i, int t, int c) {
+  const size_t ld = d.ldF;
+  double v = 0.0;
+  if (R.p1 >= 0) {
+    int p = R.p1 + i;
+    v += t == 0 ? F1[p + ld * (S.s1 + c)] : F1[(S.s1 + c) + ld * p];
+  }
+  if (R.p2 >= 0) {
+    int p = R.p2 + i;
+    v += t == 0 ? F2[p + ld * (S.s2 + c)] : F2[(S.s2 + c) + ld * p];
+  }
+  return v;
+}
+
+// ------------------------------------------------------------ block reductions
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------ column-pivoted QR
+// Businger-Golub Householder QR with column pivoting of Y (m x e, ld ldy), stopped at the
+// first step i with |R_ii| <= eps |R_00|.  perm receives the column order; on exit the
+// first k rows of Y hold [R_1 R_2] in the permuted order.  Returns k.
+__device__ int block_cpqr(double* Y, int ldy, int m, int e, double eps, int* perm, double* vn1,
+                          double* vn2, double* red, int* shi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < e; j += blockDim.x) perm[j] = j;
+  if (m == 0 || e == 0) { __syncthreads(); return 0; }
+  // initial column norms (one warp per column)
+  for (int j = warp; j < e; j += nw) {
+    double s = 0.0;
+    for (int r = lane; r < m; r += 32) { double v = Y[r + (size_t)ldy * j]; s += v * v; }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) { vn1[j] = sqrt(s); vn2[j] = vn1[j]; }
+  }
+  __syncthreads();
+  const double tol3z = sqrt(DBL_EPSILON);
+  const int kmax = min(m, e);
+  double ref = 0.0;
+  int k = kmax;
+  for (int i = 0; i < kmax; ++i) {
+    if (warp == 0) {          // pivot: largest norm, near-ties -> lowest index
+      double mx = -1.0;
+      for (int j = i + lane; j < e; j += 32) mx = fmax(mx, vn1[j]);
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int best = e;
+      for (int j = i + lane; j < e; j += 32)
+        if (vn1[j] >= mx * (1.0 - TIE_RTOL) && j < best) best = j;
+      for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+      if (lane == 0) shi[0] = best;
+    }
+    __syncthreads();
+    const int p = shi[0];
+    if (p != i) {
+      for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        double a = Y[r + (size_t)ldy * i];
+        Y[r + (size_t)ldy * i] = Y[r + (size_t)ldy * p];
+        Y[r + (size_t)ldy * p] = a;
+      }
+      if (threadIdx.x == 0) {
+        int t = perm[i]; perm[i] = perm[p]; perm[p] = t;
+        double a = vn1[i]; vn1[i] = vn1[p]; vn1[p] = a;
+        a = vn2[i]; vn2[i] = vn2[p]; vn2[p] = a;
+      }
+    }
+    __syncthreads();
+    double s = 0.0;
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) { double v = Y[r + (size_t)ldy * i]; s += v * v; }
+    const double normx = sqrt(block_sum(s, red));
+    if (i == 0) ref = normx;
+    if (ref == 0.0) { k = 0; break; }
+    if (normx <= eps * ref || normx == 0.0) { k = i; break; }
+    const double x0 = Y[i + (size_t)ldy * i];
+    const double alpha = x0 >= 0.0 ? -normx : normx;
+    const double v0 = x0 - alpha;
+    const double vv = v0 * v0 + (normx * normx - x0 * x0);
+    // apply H = I - 2 v v^T / (v^T v) to columns i+1..e-1 (one warp per column)
+    for (int j = i + 1 + warp; j < e; j += nw) {
+      double* yj = Y + (size_t)ldy * j;
+      const double* yi = Y + (size_t)ldy * i;
+      double dot = (lane == 0) ? v0 * yj[i] : 0.0;
+      for (int r = i + 1 + lane; r < m; r += 32) dot += yi[r] * yj[r];
+      for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      const double coef = 2.0 * dot / vv;
+      if (lane == 0) yj[i] -= coef * v0;
+      for (int r = i + 1 + lane; r < m; r += 32) yj[r] -= coef * yi[r];
+      __syncwarp();
+      // norm downdate with the recomputation guard
+      double nv = vn1[j];
+      if (nv != 0.0) {
+        double q = fabs(yj[i]) / nv;
+        double temp = fmax(1.0 - q * q, 0.0);
+        double r2 = nv / vn2[j];
+        double temp2 = temp * r2 * r2;
+        if (temp2 <= tol3z) {
+          double ss = 0.0;
+          for (int r = i + 1 + lane; r < m; r += 32) ss += yj[r] * yj[r];
+          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          if (lane == 0) { vn1[j] = sqrt(ss); vn2[j] = vn1[j]; }
+        } else if (lane == 0) {
+          vn1[j] = nv * sqrt(temp);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) Y[i + (size_t)ldy * i] = alpha;
+    __syncthreads();
+  }
+  __syncthreads();
+  return k;
+}
+
+// T (k x (e-k), ld ldt) = R_1^{-1} R_2 from the R held in Y (ld ldy)
+__device__ void block_interp(const double* Y, int ldy, int k, int e, double* T, int ldt) {
+  for (int j = threadIdx.x; j < e - k; j += blockDim.x) {
+    for (int a = k - 1; a >= 0; --a) {
+      double s = Y[a + (size_t)ldy * (k + j)];
+      for (int b = a + 1; b < k; ++b) s -= Y[a + (size_t)ldy * b] * T[b + (size_t)ldt * j];
+      T[a + (size_t)ldt * j] = s / Y[a + (size_t)ldy * a];
+    }
+  }
+  __syncthreads();
+}
+
+// LU with partial pivoting of the n x n block of A at (r0, r0) (ld lda), with the row
+// operations carried over columns [0, ncol); the multipliers are stored below the diagonal.
+// Returns false on an exactly zero pivot.
+__device__ bool block_gepp(double* A, int lda, int r0, int n, int ncol, int* piv, int* shi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    const int cj = r0 + j;
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = n;
+      for (int r = j + lane; r < n; r += 32) {
+        double v = fabs(A[(r0 + r) + (size_t)lda * cj]);
+        if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { shi[0] = bi; shi[1] = best == 0.0; piv[j] = bi; }
+    }
+    __syncthreads();
+    const int p = shi[0];
+    if (shi[1]) { ok = false; __syncthreads(); continue; }
+    if (p != j) {
+      for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        if (c >= r0 && c < cj) continue;
+        double a = A[(r0 + j) + (size_t)lda * c];
+        A[(r0 + j) + (size_t)lda * c] = A[(r0 + p) + (size_t)lda * c];
+        A[(r0 + p) + (size_t)lda * c] = a;
+      }
+      __syncthreads();
+    }
+    const double pv = A[(r0 + j) + (size_t)lda * cj];
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[(r0 + r) + (size_t)lda * cj] /= pv;
+    __syncthreads();
+    const int nr = n - j - 1;
+    const int nc = ncol - 1;   // every column but cj
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      int r = j + 1 + e % nr;
+      int c = e / nr;
+      if (c >= cj) ++c;
+      // columns of the already-factored part of the block (r0 <= c < cj) hold multipliers
+      if (c >= r0 && c < cj) continue;
+      A[(r0 + r) + (size_t)lda * c] -= A[(r0 + r) + (size_t)lda * cj] * A[(r0 + j) + (size_t)lda * c];
+    }
+    __syncthreads();
+  }
+  return ok;
+}
+
+// ------------------------------------------------------------ sparsify: one CTA per segment
+__global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_bytes) {
+  extern __shared__ double sm[];
+  __shared__ SegCtx S;
+  __shared__ double red[40];
+  __shared__ int shi[8];
+  __shared__ int nearlist[NEAR_MAX];
+  __shared__ int nnear_sh, nfar_sh;
+
+  const int sid = blockIdx.x;
+  if (threadIdx.x == 0) seg_context(d, sid, S);
+  __syncthreads();
+  const int e = S.e;
+  const int capS = d.capS;
+  int* perm_out = d.perm + (size_t)sid * capS;
+  if (e == 0) {
+    if (threadIdx.x == 0) { d.kk[sid] = 0; d.hs[sid] = 0; }
+    return;
+  }
+  const size_t ld = d.ldF;
+  const double* F1 = d.F + (size_t)S.b1 * ld * ld;
+  const double* F2 = d.F + (size_t)S.b2 * ld * ld;
+  const int halves = d.symmetric ? 1 : 2;
+
+  // eps == 0: no sparsification, the whole segment is skeleton
+  if (d.eps == 0.0) {
+    double* Dg = d.Dm + (size_t)sid * capS * capS;
+    for (int x = threadIdx.x; x < e * e; x += blockDim.x) {
+      int a = x % e, b = x / e;
+      Dg[a + (size_t)capS * b] = F1[(S.s1 + a) + ld * (S.s1 + b)] + F2[(S.s2 + a) + ld * (S.s2 + b)];
+    }
+    for (int j = threadIdx.x; j < e; j += blockDim.x) perm_out[j] = j;
+    if (threadIdx.x == 0) { d.kk[sid] = e; d.hs[sid] = 0; }
+    return;
+  }
+
+  // near / far split of the neighbours (ordered scan, warp 0)
+  if (threadIdx.x < 32) {
+    int lane = threadIdx.x, nn = 0;
+    for (int base = 0; base < S.nb; base += 32) {
+      int f = base + lane;
+      bool isnear = false;
+      if (f < S.nb) {
+        int r, i;
+        locate(S, f, r, i);
+        isnear = cheb(S, run_node(d, S.run[r], i), d.nx) <= d.near_radius;
+      }
+      unsigned msk = __ballot_sync(0xffffffffu, isnear);
+      int pos = nn + __popc(msk & ((1u << lane) - 1u));
+      if (isnear && pos < NEAR_MAX) nearlist[pos] = f;
+      nn += __popc(msk);
+    }
+    if (lane == 0) {
+      if (nn > NEAR_MAX) atomicOr(d.err, ERR_CAPACITY);
+      nnear_sh = min(nn, NEAR_MAX);
+      nfar_sh = S.nb - nn;
+    }
+  }
+  __syncthreads();
+  const int nnear = nnear_sh;
+  const int nN = halves * nnear;
+  const int nF = halves * nfar_sh;
+  const int hcap = max(d.h0, 2 * (e + d.p_over));
+  const int hmax = min(nF, hcap);
+  const int mmax = nN + hmax;
+
+  // working storage: vectors and sketch chunks in shared memory; Y, D, T too when they
+  // fit, else in the global scratch of this segment
+  const size_t small = 2 * (size_t)e + (size_t)e + 1;          // vn1, vn2, perm + piv (ints)
+  const size_t per_ch = (size_t)halves * (e + hmax);            // Bc + Gc per chunk row
+  const size_t ydt = (size_t)mmax * e + 2 * (size_t)e * e;
+  const size_t avail = (size_t)smem_bytes / sizeof(double);
+  int ch = SK_CHUNK;
+  bool in_smem = small + ch * per_ch + ydt <= avail;
+  if (!in_smem) {
+    size_t room = avail > small ? avail - small : 0;
+    ch = (int)min((size_t)SK_CHUNK, room / (per_ch > 0 ? per_ch : 1));
+    if (ch < 1) { ch = 1; if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); }
+  }
+  double *Y, *Dw, *Tw, *Bc, *Gc, *vn1, *vn2;
+  int *perm, *piv;
+  int ldy, ldd, ldt;
+  {
+    double* q = sm;
+    vn1 = q; q += e;
+    vn2 = q; q += e;
+    perm = reinterpret_cast<int*>(q);
+    piv = perm + e;
+    q += (e + 1);
+    Bc = q; q += (size_t)halves * ch * e;
+    Gc = q; q += (size_t)hmax * halves * ch;
+    if (in_smem) {
+      Y = q; q += (size_t)mmax * e; ldy = mmax;
+      Dw = q; q += (size_t)e * e; ldd = e;
+      Tw = q; q += (size_t)e * e; ldt = e;
+    } else {
+      Y = d.Yg + (size_t)sid * d.Ycap * capS; ldy = d.Ycap;
+      Dw = d.Dm + (size_t)sid * capS * capS; ldd = capS;
+      Tw = d.T + (size_t)sid * capS * capS; ldt = capS;
+    }
+  }
+  if (!in_smem && (mmax > d.Ycap || d.Yg == nullptr)) {   // no room: report, touch nothing
+    if (threadIdx.x == 0) { atomicOr(d.err, ERR_CAPACITY); d.kk[sid] = 0; d.hs[sid] = 0; }
+    return;
+  }
+
+  // ---- adaptive sketch + ID (Sec. 4.2.3; h = k + p with k unknown: double h until k <= h - p)
+  int h = (nF <= d.h0) ? nF : d.h0;
+  int k = 0;
+  while (true) {
+    const bool full = (h >= nF);
+    const int hh = full ? nF : h;
+    const int m = nN + hh;
+    // near rows
+    for (int x = threadIdx.x; x < nN * e; x += blockDim.x) {
+      int row = x % nN, c = x / nN;
+      int t = row / nnear, a = row % nnear;
+      int r, i;
+      locate(S, nearlist[a], r, i);
+      Y[row + (size_t)ldy * c] = bval(d, S, F1, F2, S.run[r], i, t, c);
+    }
+    if (full) {
+      // Phi = I on the far block: far rows in the enumeration order of the neighbours;
+      // position of far neighbour f = f minus the near ones before it
+      for (int f = threadIdx.x; f < S.nb; f += blockDim.x) {
+        int before = 0;
+        bool isnear = false;
+        for (int a = 0; a < nnear; ++a) {
+          if (nearlist[a] < f) ++before;
+          if (nearlist[a] == f) isnear = true;
+        }
+        if (isnear) continue;
+        int j = f - before;
+        int r, i;
+        locate(S, f, r, i);
+        for (int t = 0; t < halves; ++t)
+          for (int c = 0; c < e; ++c)
+            Y[(nN + t * nfar_sh + j) + (size_t)ldy * c] = bval(d, S, F1, F2, S.run[r], i, t, c);
+      }
+    } else {
+      for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] = 0.0;
+      __syncthreads();
+      // Y_F = G B_F, chunks of SK_CHUNK neighbours (near ones get zero weight)
+      for (int f0 = 0; f0 < S.nb; f0 += ch) {
+        const int nc = min(ch, S.nb - f0);
+        const int rows = halves * nc;
+        for (int x = threadIdx.x; x < rows * e; x += blockDim.x) {
+          int row = x % rows, c = x / rows;
+          int t = row / nc, jj = row % nc;
+          int r, i;
+          locate(S, f0 + jj, r, i);
+          Bc[row + (size_t)rows * c] = bval(d, S, F1, F2, S.run[r], i, t, c);
+        }
+        for (int x = threadIdx.x; x < hh * rows; x += blockDim.x) {
+          int rr = x % hh, row = x / hh;
+          int t = row / nc, jj = row % nc;
+          int f = f0 + jj;
+          bool isnear = false;
+          for (int a = 0; a < nnear; ++a) isnear |= (nearlist[a] == f);
+          double gv = 0.0;
+          if (!isnear) {
+            int r, i;
+            locate(S, f, r, i);
+            gv = (double)sketch_gauss(d.seed, d.l, sid, rr, run_node(d, S.run[r], i), t);
+          }
+          Gc[rr + (size_t)hh * row] = gv;
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < hh * e; x += blockDim.x) {
+          int rr = x % hh, c = x / hh;
+          double acc = 0.0;
+          for (int row = 0; row < rows; ++row) acc += Gc[rr + (size_t)hh * row] * Bc[row + (size_t)rows * c];
+          Y[(nN + rr) + (size_t)ldy * c] += acc;
+        }
+        __syncthreads();
+      }
+      const double sc = 1.0 / sqrt((double)hh);
+      for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
+    }
+    __syncthreads();
+    k = block_cpqr(Y, ldy, m, e, d.eps, perm, vn1, vn2, red, shi);
+    if (!full && k > h - d.p_over && h < nF) {
+      h = min(2 * h, nF);
+      __syncthreads();
+      continue;
+    }
+    break;
+  }
+  const int r = e - k;
+  block_interp(Y, ldy, k, e, Tw, ldt);
+
+  // ---- transformed diagonal block in [skeleton | remainder] order (Eq. (UtALt))
+  for (int x = threadIdx.x; x < e * e; x += blockDim.x) {
+    int a = x % e, b = x / e;
+    int pa = perm[a], pb = perm[b];
+    Dw[a + (size_t)ldd * b] = F1[(S.s1 + pa) + ld * (S.s1 + pb)] + F2[(S.s2 + pa) + ld * (S.s2 + pb)];
+  }
+  __syncthreads();
+  if (k > 0 && r > 0) {
+    // column operation: D[:, k:] -= D[:, :k] T
+    for (int x = threadIdx.x; x < e * r; x += blockDim.x) {
+      int a = x % e, b = x / e;
+      double s = 0.0;
+      for (int c = 0; c < k; ++c) s += Dw[a + (size_t)ldd * c] * Tw[c + (size_t)ldt * b];
+      Dw[a + (size_t)ldd * (k + b)] -= s;
+    }
+    __syncthreads();
+    // row operation: D[k:, :] -= T^T D[:k, :]
+    for (int x = threadIdx.x; x < r * e; x += blockDim.x) {
+      int a = x % r, b = x / r;
+      double s = 0.0;
+      for (int c = 0; c < k; ++c) s += Tw[c + (size_t)ldt * a] * Dw[c + (size_t)ldd * b];
+      Dw[(k + a) + (size_t)ldd * b] -= s;
+    }
+    __syncthreads();
+  }
+  // ---- eliminate the remainder: LU(A_rr) with W = L^{-1} P A_rk, Z = A_kr U^{-1},
+  //      A_kk -= Z W  (Eq. (L^-1 * A * U^-1) for the segments of level l)
+  if (r > 0) {
+    bool ok = block_gepp(Dw, ldd, k, r, e, piv, shi);
+    if (!ok && threadIdx.x == 0) atomicOr(d.err, ERR_SINGULAR);
+    if (k > 0) {
+      for (int a = threadIdx.x; a < k; a += blockDim.x) {     // Z = A_kr U^{-1}, row by row
+        for (int j = 0; j < r; ++j) {
+          double s = Dw[a + (size_t)ldd * (k + j)];
+          for (int i2 = 0; i2 < j; ++i2) s -= Dw[a + (size_t)ldd * (k + i2)] * Dw[(k + i2) + (size_t)ldd * (k + j)];
+          Dw[a + (size_t)ldd * (k + j)] = s / Dw[(k + j) + (size_t)ldd * (k + j)];
+        }
+      }
+      __syncthreads();
+      for (int x = threadIdx.x; x < k * k; x += blockDim.x) {
+        int a = x % k, b = x / k;
+        double s = 0.0;
+        for (int j = 0; j < r; ++j) s += Dw[a + (size_t)ldd * (k + j)] * Dw[(k + j) + (size_t)ldd * b];
+        Dw[a + (size_t)ldd * b] -= s;
+      }
+      __syncthreads();
+    }
+  }
+  // ---- outputs
+  if (in_smem) {
+    double* Dg = d.Dm + (size_t)sid * capS * capS;
+    double* Tg = d.T + (size_t)sid * capS * capS;
+    for (int x = threadIdx.x; x < e * e; x += blockDim.x) Dg[(x % e) + (size_t)capS * (x / e)] = Dw[x];
+    for (int x = threadIdx.x; x < k * r; x += blockDim.x) Tg[(x % k) + (size_t)capS * (x / k)] = Tw[(x % k) + (size_t)ldt * (x / k)];
+  }
+  for (int j = threadIdx.x; j < e; j += blockDim.x) perm_out[j] = perm[j];
+  for (int j = threadIdx.x; j < r; j += blockDim.x) d.piv[(size_t)sid * capS + j] = piv[j];
+  if (threadIdx.x == 0) { d.kk[sid] = k; d.hs[sid] = h; }
+}
+
+// ------------------------------------------------------------ level-L segment tables
+__global__ void level_init_L_kernel(LevelDev d) {
+  const int nseg = d.g.nseg();
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nseg * LEAF; x += gridDim.x * blockDim.x) {
+    int sid = x / LEAF, t = x % LEAF;
+    d.nodes[(size_t)sid * d.capS + t] = d.g.seg_node(sid, t, d.nx);
+    if (t == 0) d.cnt[sid] = LEAF;
+  }
+}
+
+// ------------------------------------------------------------ merge (Sec. 4.3, E_(l))
+// Table entry per unknown of the parent's extended block [dP | p]:
+//   [0] position in the parent block, [1..3] (position, side, skeleton index) in child 1,
+//   [4..6] the same in child 2 (-1 when absent; side 4 = corner), [7] grid node.
+constexpr int TABW = 8;
+
+struct ParentCtx {
+  int Ip, Jp, c1, c2, I1, J1, I2, J2, sep, kp;
+};
+
+__device__ void parent_ctx(const LevelDev& d, int P, ParentCtx& C) {
+  C.Ip = P % d.gp.bx;
+  C.Jp = P / d.gp.bx;
+  if (d.vcut) { C.I1 = 2 * C.Ip; C.J1 = C.Jp; C.I2 = 2 * C.Ip + 1; C.J2 = C.Jp; }
+  else { C.I1 = C.Ip; C.J1 = 2 * C.Jp; C.I2 = C.Ip; C.J2 = 2 * C.Jp + 1; }
+  C.c1 = C.I1 + d.g.bx * C.J1;
+  C.c2 = C.I2 + d.g.bx * C.J2;
+  C.sep = d.g.box_side(C.I1, C.J1, d.vcut ? SIDE_RIGHT : SIDE_TOP);
+  C.kp = d.kk[C.sep];
+}
+
+// Unknowns of a child side restricted to its skeleton, appended to the table.
+__device__ int add_side(const LevelDev& d, int* tab, int n, int posM, int child, int I, int J,
+                        int side, int node_seg_dummy) {
+  (void)node_seg_dummy;
+  int sg = d.g.box_side(I, J, side);
+  if (sg < 0) return n;
+  int k = d.kk[sg];
+  for (int t = 0; t < k; ++t) {
+    int* e = tab + (size_t)(n + t) * TABW;
+    int pc = d.g.side_pos(side) + d.perm[(size_t)sg * d.capS + t];
+    e[0] = posM + t;
+    e[1] = e[2] = e[3] = e[4] = e[5] = e[6] = -1;
+    e[child == 1 ? 1 : 4] = pc;
+    e[child == 1 ? 2 : 5] = side;
+    e[child == 1 ? 3 : 6] = t;
+    e[7] = d.nodes[(size_t)sg * d.capS + d.perm[(size_t)sg * d.capS + t]];
+  }
+  return n + k;
+}
+
+__device__ int add_corner(const LevelDev& d, int* tab, int n, int posM, int I1, int J1, int c1,
+                          int I2, int J2, int c2) {
+  int cid = c1 >= 0 ? d.g.box_corner(I1, J1, c1) : d.g.box_corner(I2, J2, c2);
+  if (cid < 0) return n;
+  int* e = tab + (size_t)n * TABW;
+  e[0] = posM;
+  e[1] = c1 >= 0 ? d.g.corner_pos(c1) : -1;
+  e[2] = c1 >= 0 ? 4 : -1;
+  e[3] = 0;
+  e[4] = c2 >= 0 ? d.g.corner_pos(c2) : -1;
+  e[5] = c2 >= 0 ? 4 : -1;
+  e[6] = 0;
+  e[7] = d.g.junction_node(cid, d.nx);
+  return n + 1;
+}
+
+__global__ void merge_table_kernel(LevelDev d) {
+  const int P = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  ParentCtx C;
+  parent_ctx(d, P, C);
+  int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
+  const Geo gp = d.gp;
+  const int Dp = gp.D();
+  int n = 0;
+  // sides of P (merged or inherited), then its corners, then the separator skeleton
+  for (int side = 0; side < 4; ++side) {
+    if (gp.bx * gp.by > 1 && gp.box_side(C.Ip, C.Jp, side) < 0) continue;
+    if (gp.bx * gp.by == 1) continue;
+    int pos = gp.side_pos(side);
+    bool split = d.vcut ? (side == SIDE_BOTTOM || side == SIDE_TOP) : (side == SIDE_LEFT || side == SIDE_RIGHT);
+    if (!split) {
+      // inherited from one child
+      int child = d.vcut ? (side == SIDE_LEFT ? 1 : 2) : (side == SIDE_BOTTOM ? 1 : 2);
+      int I = child == 1 ? C.I1 : C.I2, J = child == 1 ? C.J1 : C.J2;
+      n = add_side(d, tab, n, pos, child, I, J, side, 0);
+    } else {
+      int n0 = n;
+      n = add_side(d, tab, n, pos, 1, C.I1, C.J1, side, 0);
+      int k1 = n - n0;
+      // junction: vertical cut: bottom -> b1.BR = b2.BL, top -> b1.TR = b2.TL;
+      //           horizontal cut: left -> b1.TL = b2.BL, right -> b1.TR = b2.BR
+      int jc1, jc2;
+      if (d.vcut) { jc1 = side == SIDE_BOTTOM ? C_BR : C_TR; jc2 = side == SIDE_BOTTOM ? C_BL : C_TL; }
+      else { jc1 = side == SIDE_LEFT ? C_TL : C_TR; jc2 = side == SIDE_LEFT ? C_BL : C_BR; }
+      n = add_corner(d, tab, n, pos + k1, C.I1, C.J1, jc1, C.I2, C.J2, jc2);
+      int n1 = n;
+      n = add_side(d, tab, n, pos + (n1 - n0), 2, C.I2, C.J2, side, 0);
+    }
+  }
+  if (gp.bx * gp.by > 1) {
+    for (int c = 0; c < 4; ++c) {
+      if (gp.box_corner(C.Ip, C.Jp, c) < 0) continue;
+      // vertical cut: BL,TL from b1; BR,TR from b2.  horizontal: BL,BR from b1; TL,TR from b2
+      bool from1 = d.vcut ? (c == C_BL || c == C_TL) : (c == C_BL || c == C_BR);
+      if (from1) n = add_corner(d, tab, n, gp.corner_pos(c), C.I1, C.J1, c, 0, 0, -1);
+      else n = add_corner(d, tab, n, gp.corner_pos(c), 0, 0, -1, C.I2, C.J2, c);
+    }
+  }
+  const int ndP = n;
+  // separator skeleton: side RIGHT/TOP of child 1 (owner) = LEFT/BOTTOM of child 2
+  {
+    int s1 = d.vcut ? SIDE_RIGHT : SIDE_TOP, s2 = d.vcut ? SIDE_LEFT : SIDE_BOTTOM;
+    int sg = C.sep;
+    for (int t = 0; t < C.kp; ++t) {
+      int* e = tab + (size_t)(n + t) * TABW;
+      int q = d.perm[(size_t)sg * d.capS + t];
+      e[0] = Dp + t;
+      e[1] = d.g.side_pos(s1) + q; e[2] = s1; e[3] = t;
+      e[4] = d.g.side_pos(s2) + q; e[5] = s2; e[6] = t;
+      e[7] = d.nodes[(size_t)sg * d.capS + q];
+    }
+    n += C.kp;
+  }
+  d.pcount[2 * P] = ndP;
+  d.pcount[2 * P + 1] = C.kp;
+}
+
+// M[a][b] = sum over the children holding both unknowns of the child's block, where the
+// block of a segment with itself is its eliminated skeleton block A_ss' (held by the owner
+// child: the segment is that child's TOP or RIGHT side) and zero in the other child.
+__global__ void merge_assemble_kernel(LevelDev d) {
+  const int P = blockIdx.y;
+  const int nM = d.pcount[2 * P] + d.pcount[2 * P + 1];
+  const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
+  ParentCtx C;
+  parent_ctx(d, P, C);
+  const size_t ld = d.ldF, ldp = d.ldFp;
+  const double* F1 = d.F + (size_t)C.c1 * ld * ld;
+  const double* F2 = d.F + (size_t)C.c2 * ld * ld;
+  double* M = d.Fp + (size_t)P * ldp * ldp;
+  const long long tot = (long long)nM * nM;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < tot;
+       x += (long long)gridDim.x * blockDim.x) {
+    int a = (int)(x % nM), b = (int)(x / nM);
+    const int* ea = tab + (size_t)a * TABW;
+    const int* eb = tab + (size_t)b * TABW;
+    double v = 0.0;
+    for (int ch = 0; ch < 2; ++ch) {
+      int pa = ea[1 + 3 * ch], pb = eb[1 + 3 * ch];
+      if (pa < 0 || pb < 0) continue;
+      int sa = ea[2 + 3 * ch], sb = eb[2 + 3 * ch];
+      if (sa == sb && sa < 4) {
+        if (sa == SIDE_TOP || sa == SIDE_RIGHT) {
+          int I = ch == 0 ? C.I1 : C.I2, J = ch == 0 ? C.J1 : C.J2;
+          int sg = d.g.box_side(I, J, sa);
+          v += d.Dm[(size_t)sg * d.capS * d.capS + ea[3 + 3 * ch] + (size_t)d.capS * eb[3 + 3 * ch]];
+        }
+      } else {
+        const double* Fc = ch == 0 ? F1 : F2;
+        v += Fc[pa + ld * pb];
+      }
+    }
+    M[ea[0] + ldp * eb[0]] = v;
+  }
+}
+
+// LU of the separator block with the row operations over every column (W = L^{-1} P A_pd),
+// then Z = A_dp U^{-1}.
+__global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
+  __shared__ int shi[4];
+  const int P = blockIdx.x;
+  const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
+  if (kp == 0) return;
+  const int nM = ndP + kp;
+  const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
+  const size_t ldp = d.ldFp;
+  double* M = d.Fp + (size_t)P * ldp * ldp;
+  const int Dp = d.gp.D();
+  int* piv = d.ppiv + (size_t)P * d.sepcap;
+  bool ok = true;
+  for (int j = 0; j < kp; ++j) {
+    const int cj = Dp + j;
+    if (threadIdx.x < 32) {
+      int lane = threadIdx.x;
+      double best = -1.0;
+      int bi = kp;
+      for (int r = j + lane; r < kp; r += 32) {
+        double v = fabs(M[(Dp + r) + ldp * cj]);
+        if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { shi[0] = bi; shi[1] = best == 0.0; piv[j] = bi; }
+    }
+    __syncthreads();
+    const int p = shi[0];
+    if (shi[1]) { ok = false; __syncthreads(); continue; }
+    if (p != j) {
+      for (int c = threadIdx.x; c < nM; c += blockDim.x) {
+        const int pc = tab[(size_t)c * TABW];
+        if (pc >= Dp && pc < cj) continue;
+        size_t col = ldp * pc;
+        double a = M[(Dp + j) + col];
+        M[(Dp + j) + col] = M[(Dp + p) + col];
+        M[(Dp + p) + col] = a;
+      }
+      __syncthreads();
+    }
+    const double pv = M[(Dp + j) + ldp * cj];
+    for (int r = j + 1 + threadIdx.x; r < kp; r += blockDim.x) M[(Dp + r) + ldp * cj] /= pv;
+    __syncthreads();
+    const int nr = kp - j - 1;
+    // update rows j+1.. over columns: the separator columns j+1..kp-1 and every dP column
+    const int ncols = (kp - j - 1) + ndP;
+    for (int x = threadIdx.x; x < nr * ncols; x += blockDim.x) {
+      int r = j + 1 + x % nr, cc = x / nr;
+      int col = cc < kp - j - 1 ? (Dp + j + 1 + cc) : tab[(size_t)(cc - (kp - j - 1)) * TABW];
+      M[(Dp + r) + ldp * col] -= M[(Dp + r) + ldp * cj] * M[(Dp + j) + ldp * col];
+    }
+    __syncthreads();
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(d.err, ERR_SINGULAR);
+  // Z = A_dp U^{-1}: each dP row solved left to right
+  for (int a = threadIdx.x; a < ndP; a += blockDim.x) {
+    size_t row = tab[(size_t)a * TABW];
+    for (int j = 0; j < kp; ++j) {
+      double s = M[row + ldp * (Dp + j)];
+      for (int i = 0; i < j; ++i) s -= M[row + ldp * (Dp + i)] * M[(Dp + i) + ldp * (Dp + j)];
+      M[row + ldp * (Dp + j)] = s / M[(Dp + j) + ldp * (Dp + j)];
+    }
+  }
+}
+
+// Schur update of the parent's boundary block: M[dP, dP] -= Z W (FP64, 64 x 64 tiles)
+__global__ void __launch_bounds__(256) merge_schur_kernel(LevelDev d) {
+  __shared__ double Zs[64][17];
+  __shared__ double Ws[16][65];
+  __shared__ int ra[64], cb[64];
+  const int P = blockIdx.z;
+  const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
+  if (kp == 0 || ndP == 0) return;
+  const int tiles = (ndP + 63) / 64;
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti >= tiles || tj >= tiles) return;
+  const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
+  const size_t ldp = d.ldFp;
+  double* M = d.Fp + (size_t)P * ldp * ldp;
+  const int Dp = d.gp.D();
+  for (int x = threadIdx.x; x < 64; x += blockDim.x) {
+    int a = ti * 64 + x, b = tj * 64 + x;
+    ra[x] = a < ndP ? tab[(size_t)a * TABW] : -1;
+    cb[x] = b < ndP ? tab[(size_t)b * TABW] : -1;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;   // 16 x 16 threads, 4 x 4 each
+  double acc[4][4] = {};
+  for (int j0 = 0; j0 < kp; j0 += 16) {
+    for (int x = threadIdx.x; x < 64 * 16; x += blockDim.x) {
+      int i = x % 64, j = x / 64;
+      Zs[i][j] = (ra[i] >= 0 && j0 + j < kp) ? M[ra[i] + ldp * (Dp + j0 + j)] : 0.0;
+      int c = x % 64, jj = x / 64;
+      Ws[jj][c] = (cb[c] >= 0 && j0 + jj < kp) ? M[(Dp + j0 + jj) + ldp * cb[c]] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      double z[4], w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { z[u] = Zs[ty * 4 + u][j]; w[u] = Ws[j][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += z[u] * w[v];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int i = ty * 4 + u, c = tx * 4 + v;
+      if (ra[i] >= 0 && cb[c] >= 0) M[ra[i] + ldp * cb[c]] -= acc[u][v];
+    }
+}
+
+// Level-(l-1) segment tables: counts and grid nodes (merged sides: [skel 1, junction, skel 2]).
+__global__ void seg_merge_kernel(LevelDev d) {
+  const Geo gp = d.gp, g = d.g;
+  const int sidp = blockIdx.x;
+  const bool horiz = sidp < gp.nh();
+  int Ip, Jp;
+  if (horiz) { Ip = sidp % gp.bx; Jp = sidp / gp.bx + 1; }
+  else { int t = sidp - gp.nh(); Ip = t % (gp.bx - 1) + 1; Jp = t / (gp.bx - 1); }
+  int* out = d.nodes_up + (size_t)sidp * d.capS_up;
+  bool split = d.vcut ? horiz : !horiz;
+  int cs1, cs2 = -1, jn = -1;
+  if (!split) {
+    // horizontal cut at level l: hs_p(Ip,Jp) -> hs(Ip, 2Jp); vertical cut: vs_p(Ip,Jp) -> vs(2Ip, Jp)
+    if (horiz) cs1 = Ip + g.bx * (2 * Jp - 1);
+    else cs1 = g.nh() + (2 * Ip - 1) + (g.bx - 1) * Jp;
+  } else if (horiz) {   // vertical cut: hs_p(Ip,Jp) -> hs(2Ip,Jp), c(2Ip+1,Jp), hs(2Ip+1,Jp)
+    cs1 = 2 * Ip + g.bx * (Jp - 1);
+    cs2 = 2 * Ip + 1 + g.bx * (Jp - 1);
+    jn = g.junction_node((2 * Ip + 1 - 1) + (g.bx - 1) * (Jp - 1), d.nx);
+  } else {              // horizontal cut: vs_p(Ip,Jp) -> vs(Ip,2Jp), c(Ip,2Jp+1), vs(Ip,2Jp+1)
+    cs1 = g.nh() + (Ip - 1) + (g.bx - 1) * (2 * Jp);
+    cs2 = g.nh() + (Ip - 1) + (g.bx - 1) * (2 * Jp + 1);
+    jn = g.junction_node((Ip - 1) + (g.bx - 1) * (2 * Jp + 1 - 1), d.nx);
+  }
+  const int k1 = d.kk[cs1];
+  for (int t = threadIdx.x; t < k1; t += blockDim.x)
+    out[t] = d.nodes[(size_t)cs1 * d.capS + d.perm[(size_t)cs1 * d.capS + t]];
+  int n = k1;
+  if (cs2 >= 0) {
+    if (threadIdx.x == 0) out[n] = jn;
+    ++n;
+    const int k2 = d.kk[cs2];
+    for (int t = threadIdx.x; t < k2; t += blockDim.x)
+      out[n + t] = d.nodes[(size_t)cs2 * d.capS + d.perm[(size_t)cs2 * d.capS + t]];
+    n += k2;
+  }
+  if (threadIdx.x == 0) d.cnt_up[sidp] = n;
+}
+
+// ------------------------------------------------------------ solve
+// Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
+// Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
+__global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, double* X, int nrhs, int ld, int bwd) {
+  extern __shared__ double sm[];
+  const int sid = blockIdx.x;
+  const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
+  if (r == 0 || e == 0) return;
+  const int capS = d.capS;
+  const int* perm = d.perm + (size_t)sid * capS;
+  const int* nodes = d.nodes + (size_t)sid * capS;
+  const int* piv = d.piv + (size_t)sid * capS;
+  const double* T = d.T + (size_t)sid * capS * capS;
+  const double* Dm = d.Dm + (size_t)sid * capS * capS;
+  double* v = sm;   // e x nrhs: [skeleton | remainder] order
+  for (int x = threadIdx.x; x < e * nrhs; x += blockDim.x) {
+    int a = x % e, c = x / e;
+    v[x] = X[nodes[perm[a]] + (size_t)ld * c];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (!bwd) {
+    for (int x = threadIdx.x; x < r * nrhs; x += blockDim.x) {
+      int a = x % r, c = x / r;
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s += T[q + (size_t)capS * a] * v[q + e * c];
+      v[k + a + e * c] -= s;
+    }
+    __syncthreads();
+    for (int c = warp; c < nrhs; c += nw) {   // y = L^{-1} P b_r
+      double* y = v + k + e * c;
+      for (int j = 0; j < r; ++j) {
+        int p = piv[j];
+        __syncwarp();
+        if (p != j && lane == 0) { double t = y[j]; y[j] = y[p]; y[p] = t; }
+        __syncwarp();
+        double yj = y[j];
+        for (int i = j + 1 + lane; i < r; i += 32) y[i] -= Dm[(k + i) + (size_t)capS * (k + j)] * yj;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < k * nrhs; x += blockDim.x) {
+      int a = x % k, c = x / k;
+      double s = 0.0;
+      for (int j = 0; j < r; ++j) s += Dm[a + (size_t)capS * (k + j)] * v[k + j + e * c];
+      v[a + e * c] -= s;
+    }
+  } else {
+    for (int x = threadIdx.x; x < r * nrhs; x += blockDim.x) {
+      int a = x % r, c = x / r;
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s += Dm[(k + a) + (size_t)capS * q] * v[q + e * c];
+      v[k + a + e * c] -= s;
+    }
+    __syncthreads();
+    for (int c = warp; c < nrhs; c += nw) {   // x_r = U^{-1} (.)
+      double* y = v + k + e * c;
+      for (int j = r - 1; j >= 0; --j) {
+        __syncwarp();
+        double yj = y[j] / Dm[(k + j) + (size_t)capS * (k + j)];
+        __syncwarp();
+        if (lane == 0) y[j] = yj;
+        for (int i = lane; i < j; i += 32) y[i] -= Dm[(k + i) + (size_t)capS * (k + j)] * yj;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < k * nrhs; x += blockDim.x) {
+      int a = x % k, c = x / k;
+      double s = 0.0;
+      for (int j = 0; j < r; ++j) s += T[a + (size_t)capS * j] * v[k + j + e * c];
+      v[a + e * c] -= s;
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < e * nrhs; x += blockDim.x) {
+    int a = x % e, c = x / e;
+    X[nodes[perm[a]] + (size_t)ld * c] = v[x];
+  }
+}
+
+// Separator of each parent: forward y_p = L^{-1} P b_p, b_dP -= Z y_p (parents of one colour
+// at a time: two parents of the same colour share no boundary unknown); backward
+// x_p = U^{-1} (y_p - W x_dP).
+__global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, double* X, int nrhs, int ld, int bwd, int colour) {
+  extern __shared__ double sm[];
+  const int P = blockIdx.x;
+  const int Ip = P % d.gp.bx, Jp = P / d.gp.bx;
+  if (!bwd && ((Ip & 1) + 2 * (Jp & 1)) != colour) return;
+  const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
+  if (kp == 0) return;
+  const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
+  const size_t ldp = d.ldFp;
+  const double* M = d.Fp + (size_t)P * ldp * ldp;
+  const int Dp = d.gp.D();
+  const int* piv = d.ppiv + (size_t)P * d.sepcap;
+  double* y = sm;   // kp x nrhs
+  for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
+    int a = x % kp, c = x / kp;
+    y[x] = X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (!bwd) {
+    for (int c = warp; c < nrhs; c += nw) {
+      double* yy = y + kp * c;
+      for (int j = 0; j < kp; ++j) {
+        int p = piv[j];
+        __syncwarp();
+        if (p != j && lane == 0) { double t = yy[j]; yy[j] = yy[p]; yy[p] = t; }
+        __syncwarp();
+        double yj = yy[j];
+        for (int i = j + 1 + lane; i < kp; i += 32) yy[i] -= M[(Dp + i) + ldp * (Dp + j)] * yj;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < ndP * nrhs; x += blockDim.x) {
+      int a = x % ndP, c = x / ndP;
+      size_t row = tab[(size_t)a * TABW];
+      double s = 0.0;
+      for (int j = 0; j < kp; ++j) s += M[row + ldp * (Dp + j)] * y[j + kp * c];
+      X[tab[(size_t)a * TABW + 7] + (size_t)ld * c] -= s;
+    }
+  } else {
+    for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
+      int a = x % kp, c = x / kp;
+      double s = 0.0;
+      for (int b = 0; b < ndP; ++b)
+        s += M[(Dp + a) + ldp * tab[(size_t)b * TABW]] * X[tab[(size_t)b * TABW + 7] + (size_t)ld * c];
+      y[x] -= s;
+    }
+    __syncthreads();
+    for (int c = warp; c < nrhs; c += nw) {
+      double* yy = y + kp * c;
+      for (int j = kp - 1; j >= 0; --j) {
+        __syncwarp();
+        double yj = yy[j] / M[(Dp + j) + ldp * (Dp + j)];
+        __syncwarp();
+        if (lane == 0) yy[j] = yj;
+        for (int i = lane; i < j; i += 32) yy[i] -= M[(Dp + i) + ldp * (Dp + j)] * yj;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
+    int a = x % kp, c = x / kp;
+    X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] = y[x];
+  }
+}
+
+}  // namespace
+
+size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over) {
+  const size_t halves = symmetric ? 1 : 2;
+  const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
+  const size_t mmax = halves * NEAR_MAX + hcap;
+  const size_t need = 3 * (size_t)e + 1 + SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e;
+  return need * sizeof(double);
+}
+
+size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over) {
+  const size_t halves = symmetric ? 1 : 2;
+  const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
+  return (3 * (size_t)e + 1 + halves * (e + hcap)) * sizeof(double);
+}
+
+void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
+  int n = d.g.nseg() * LEAF;
+  if (n == 0) return;
+  level_init_L_kernel<<<(n + 255) / 256, 256, 0, s>>>(d);
+}
+
+void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
+  if (d.g.nseg() == 0) return;
+  int smem = (int)p.spars_smem;
+  cudaFuncSetAttribute(sparsify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  sparsify_kernel<<<d.g.nseg(), 256, smem, s>>>(d, smem);
+}
+
+void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
+  const int np = d.gp.nbox();
+  merge_table_kernel<<<np, 32, 0, s>>>(d);
+  {
+    long long nmax = (long long)p.ldFp;
+    int gx = (int)((nmax * nmax + 255) / 256);
+    if (gx > 256) gx = 256;
+    dim3 grid(gx, np);
+    merge_assemble_kernel<<<grid, 256, 0, s>>>(d);
+  }
+  merge_panel_kernel<<<np, 256, 0, s>>>(d);
+  {
+    int tiles = (p.ldFp + 63) / 64;
+    dim3 grid(tiles, tiles, np);
+    merge_schur_kernel<<<grid, 256, 0, s>>>(d);
+  }
+  if (d.l > 1 && d.gp.nseg() > 0) seg_merge_kernel<<<d.gp.nseg(), 128, 0, s>>>(d);
+}
+
+static int col_chunk(size_t per_col_bytes) {
+  size_t lim = 96 * 1024;
+  int c = (int)(lim / (per_col_bytes > 0 ? per_col_bytes : 1));
+  return c < 1 ? 1 : c;
+}
+
+void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
+  if (d.g.nseg() > 0) {
+    int cc = col_chunk(sizeof(double) * d.capS);
+    for (int c0 = 0; c0 < nrhs; c0 += cc) {
+      int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
+      size_t smem = sizeof(double) * (size_t)d.capS * nc;
+      cudaFuncSetAttribute(seg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      seg_solve_kernel<<<d.g.nseg(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 0);
+    }
+  }
+  int cc = col_chunk(sizeof(double) * d.sepcap);
+  for (int c0 = 0; c0 < nrhs; c0 += cc) {
+    int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
+    size_t smem = sizeof(double) * (size_t)d.sepcap * nc;
+    cudaFuncSetAttribute(sep_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int colour = 0; colour < 4; ++colour)
+      sep_solve_kernel<<<d.gp.nbox(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 0, colour);
+  }
+}
+
+void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
+  int cc = col_chunk(sizeof(double) * d.sepcap);
+  for (int c0 = 0; c0 < nrhs; c0 += cc) {
+    int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
+    size_t smem = sizeof(double) * (size_t)d.sepcap * nc;
+    cudaFuncSetAttribute(sep_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sep_solve_kernel<<<d.gp.nbox(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 1, 0);
+  }
+  if (d.g.nseg() > 0) {
+    int cc2 = col_chunk(sizeof(double) * d.capS);
+    for (int c0 = 0; c0 < nrhs; c0 += cc2) {
+      int nc = nrhs - c0 < cc2 ? nrhs - c0 : cc2;
+      size_t smem = sizeof(double) * (size_t)d.capS * nc;
+      cudaFuncSetAttribute(seg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      seg_solve_kernel<<<d.g.nseg(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 1);
+    }
+  }
+}
+
+}  // namespace spalu

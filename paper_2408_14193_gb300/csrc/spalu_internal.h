@@ -1,0 +1,164 @@
+// Internal declarations of the spaLU CUDA library (not part of the C ABI).
+//
+// Geometry of the nested dissection on an nx x ny grid (Sec. 2.2, Alg. 1 on a regular
+// grid): the boxes of depth d tile the grid in bx x by boxes of w x h interior nodes,
+// separated by 1-wide lines.  Box (I, J) covers x in [I(w+1), I(w+1)+w-1] and y in
+// [J(h+1), J(h+1)+h-1].  The level-l separators split every depth-(l-1) box into its two
+// depth-l children (vertical cut when the parent is at least as wide as tall).
+//
+// Level-l objects (Sec. 2.3.1, Sec. 3.2), all derived from the depth-l tiling:
+//   horizontal segment hs(I,J), 0<=I<bx, 1<=J<by:  sid = I + bx (J-1);
+//       line y = J(h+1)-1, below it box (I,J-1) (its owner, the side is that box's TOP),
+//       above it box (I,J) (its BOTTOM);
+//   vertical segment vs(I,J), 1<=I<bx, 0<=J<by:    sid = nh + (I-1) + (bx-1) J;
+//       line x = I(w+1)-1, left box (I-1,J) (owner, its RIGHT side), right box (I,J) (LEFT);
+//   junction c(I,J), 1<=I<bx, 1<=J<by: node (I(w+1)-1, J(h+1)-1), id (I-1)+(bx-1)(J-1).
+//
+// Frontal layout of a depth-d box (position of each boundary unknown in its dense block):
+//   BOTTOM [0,w)  TOP [w,2w)  LEFT [2w,2w+h)  RIGHT [2w+h,2w+2h)  corners BL,BR,TL,TR at
+//   2w+2h+{0,1,2,3}.  The root (depth 0) has no boundary unknowns (D = 0).  A side holds
+//   cnt <= its length unknowns at the start of its range.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spalu.h"
+
+namespace spalu {
+
+enum { SIDE_BOTTOM = 0, SIDE_TOP = 1, SIDE_LEFT = 2, SIDE_RIGHT = 3 };
+enum { C_BL = 0, C_BR = 1, C_TL = 2, C_TR = 3 };
+
+// device error word bits
+enum { ERR_SINGULAR = 1, ERR_NONFINITE = 2, ERR_CAPACITY = 4, ERR_TIMEOUT = 8 };
+
+struct Geo {
+  int bx, by, w, h;
+  __host__ __device__ int nbox() const { return bx * by; }
+  __host__ __device__ int nh() const { return bx * (by - 1); }
+  __host__ __device__ int nv() const { return (bx - 1) * by; }
+  __host__ __device__ int nseg() const { return nh() + nv(); }
+  __host__ __device__ int ncorner() const { return (bx - 1) * (by - 1); }
+  __host__ __device__ int D() const { return (bx * by == 1) ? 0 : 2 * w + 2 * h + 4; }
+  __host__ __device__ int side_pos(int side) const {
+    return side == SIDE_BOTTOM ? 0 : side == SIDE_TOP ? w : side == SIDE_LEFT ? 2 * w : 2 * w + h;
+  }
+  __host__ __device__ int corner_pos(int c) const { return 2 * w + 2 * h + c; }
+  __host__ __device__ int side_len(int side) const { return side < 2 ? w : h; }
+  __host__ __device__ int cap() const { return w > h ? w : h; }
+  // segment id of a side of box (I,J), or -1 when the side lies on the domain boundary
+  __host__ __device__ int box_side(int I, int J, int side) const {
+    switch (side) {
+      case SIDE_BOTTOM: return J >= 1 ? I + bx * (J - 1) : -1;
+      case SIDE_TOP: return J + 1 < by ? I + bx * J : -1;
+      case SIDE_LEFT: return I >= 1 ? nh() + (I - 1) + (bx - 1) * J : -1;
+      default: return I + 1 < bx ? nh() + I + (bx - 1) * J : -1;
+    }
+  }
+  // junction id of a corner of box (I,J), or -1 on the boundary
+  __host__ __device__ int box_corner(int I, int J, int c) const {
+    int ci = I + (c & 1), cj = J + (c >> 1);
+    if (ci < 1 || ci >= bx || cj < 1 || cj >= by) return -1;
+    return (ci - 1) + (bx - 1) * (cj - 1);
+  }
+  __host__ __device__ int junction_node(int cid, int nx) const {
+    int ci = cid % (bx - 1) + 1, cj = cid / (bx - 1) + 1;
+    return (ci * (w + 1) - 1) + nx * (cj * (h + 1) - 1);
+  }
+  // node of the t-th grid point of segment sid (geometric order, increasing coordinate)
+  __host__ __device__ int seg_node(int sid, int t, int nx) const {
+    if (sid < nh()) {
+      int I = sid % bx, J = sid / bx + 1;
+      return (I * (w + 1) + t) + nx * (J * (h + 1) - 1);
+    }
+    int s = sid - nh();
+    int I = s % (bx - 1) + 1, J = s / (bx - 1);
+    return (I * (w + 1) - 1) + nx * (J * (h + 1) + t);
+  }
+};
+
+struct LevelPlan {          // host-side description of level l (1..L)
+  int l;
+  int vcut;                 // level-l cut is vertical (children left/right)
+  Geo g;                    // depth-l tiling (boxes whose sides are the level-l segments)
+  Geo gp;                   // depth-(l-1) tiling (parents)
+  int capS;                 // segment capacity at level l = max(w, h)
+  int ldF;                  // leading dimension of the depth-l frontal store
+  int ldFp;                 // leading dimension of the depth-(l-1) frontal store
+  int sepcap;               // length of a level-l separator
+  int Ycap;                 // rows of the per-segment sketch buffer
+  size_t spars_smem;        // dynamic shared memory of the sparsify kernel
+  int spars_global;         // 1 when the worst case needs global scratch
+};
+
+// Device view of one level, passed by value to the kernels.
+struct LevelDev {
+  int l, nx, ny, vcut;
+  Geo g, gp;
+  int capS, ldF, ldFp, Ycap, sepcap;
+  double* F;        // depth-l frontals: nbox * ldF * ldF
+  double* Fp;       // depth-(l-1) frontals (merge target): gp.nbox * ldFp * ldFp
+  int* cnt;         // [nseg] unknowns per segment before compression
+  int* kk;          // [nseg] skeleton size
+  int* hs;          // [nseg] final sketch size (statistics)
+  int* nodes;       // [nseg * capS] grid nodes in pre-ID order
+  int* perm;        // [nseg * capS] column order of the ID (first kk = skeleton)
+  int* piv;         // [nseg * capS] pivots of the remainder LU
+  double* T;        // [nseg * capS * capS] interpolation matrices, k x (e-k), ld capS
+  double* Dm;       // [nseg * capS * capS] [A_ss' | Z ; W | LU(A_rr)], ld capS
+  double* Yg;       // global sketch scratch (nseg * Ycap * capS) or null
+  int* ptab;        // merge tables: gp.nbox * ldFp * 8 ints
+  int* pcount;      // [gp.nbox * 2]: unknowns of dP, skeleton size of the separator
+  int* ppiv;        // [gp.nbox * sepcap] pivots of the separator LU
+  int* cnt_up;      // level-(l-1) segment counts (merge target) or null at l = 1
+  int* nodes_up;    // level-(l-1) segment nodes or null
+  int capS_up;
+  // options
+  double eps;
+  int symmetric, p_over, near_radius, h0;
+  unsigned long long seed;
+  int* err;
+};
+
+struct LeafDev {
+  int nx, ny, L;
+  Geo g;            // depth-L tiling (leaf boxes, 15 x 15)
+  int ldF;          // = g.D()
+  double* F;        // depth-L frontals
+  double* band;     // [nbox * LDAB * 225] band LU of the leaf interiors
+  int* piv;         // [nbox * 225]
+  const int* rowptr;
+  const int* colind;
+  const double* val;
+  int* err;
+};
+
+constexpr int LEAF = 15;
+constexpr int NI = LEAF * LEAF;        // interior unknowns of a leaf
+constexpr int KL = LEAF;               // lower bandwidth of the leaf matrix (natural order)
+constexpr int KU = LEAF;               // upper bandwidth
+constexpr int LDAB = 2 * KL + KU + 1;  // band storage rows (LAPACK layout with pivot fill)
+
+// launch helpers (defined in the .cu files)
+void launch_leaf_factor(const LeafDev& d, cudaStream_t s);
+void launch_level_init_L(const LevelDev& d, cudaStream_t s);
+void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
+void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
+
+struct SolveLevel {           // device pointers the solve needs for one level
+  LevelDev d;
+};
+void launch_leaf_solve_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s);
+void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s);
+void launch_leaf_solve_bwd(const LeafDev& d, double* X, int nrhs, int ld, double* tmp,
+                           cudaStream_t s);
+void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s);
+void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s);
+
+size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over);
+size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over);
+
+void launch_nd_perm(int nx, int ny, int L, const int* vcut_host, int* d_perm, int* d_iperm,
+                    cudaStream_t s);
+
+}  // namespace spalu

@@ -1,0 +1,236 @@
+"""ctypes binding of the spaLU C ABI (include/spalu.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; device arrays are passed as torch CUDA
+tensors (their data pointers) together with the current torch CUDA stream.  There is no
+CPU fallback: when the library is missing, loading fails with an error that says so.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+SPALU_OK = 0
+_STATUS = {
+    0: "ok", -1: "invalid argument", -2: "allocation failed", -3: "zero pivot in an LU",
+    -4: "refinement did not converge", -5: "bounded device wait expired", -6: "CUDA runtime error",
+    -7: "unsupported request", -8: "non-finite value in the factor", -9: "handle in the wrong state",
+}
+
+
+class SpaluError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+def status_string(s: int) -> str:
+    return _STATUS.get(int(s), "unknown status")
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libspalu.so")
+
+
+class Options(ctypes.Structure):
+    """Mirror of spalu_opts."""
+    _fields_ = [
+        ("eps_id", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("symmetric", ctypes.c_int),
+        ("p_oversample", ctypes.c_int),
+        ("near_radius", ctypes.c_int),
+        ("h0", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+        ("gmres_m", ctypes.c_int),
+        ("gmres_maxit", ctypes.c_int),
+        ("gmres_tol", ctypes.c_double),
+    ]
+
+    @classmethod
+    def default(cls, **kw) -> "Options":
+        o = cls()
+        load_library().spalu_default_opts(ctypes.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise AttributeError(k)
+            setattr(o, k, v)
+        return o
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# (name, restype, argtypes) of every entry point declared in include/spalu.h
+SIGNATURES = [
+    ("spalu_default_opts", None, [_P]),
+    ("spalu_status_string", ctypes.c_char_p, [_I]),
+    ("spalu_nd_build_grid", _I, [_I, _I, _I, _P, _P]),
+    ("spalu_nd_export", _I, [_P, _P, _P, _P, _I]),
+    ("spalu_nd_export_segments", _I, [_P, _P, _I]),
+    ("spalu_nd_destroy", None, [_P]),
+    ("spalu_factor_create", _I, [_P, _P, _P]),
+    ("spalu_factor_numeric", _I, [_P, _P, _P, _P, _I, _P]),
+    ("spalu_factor_numeric_host", _I, [_P, _P, _P, _P, _I, _P]),
+    ("spalu_solve", _I, [_P, _P, _P, _I, _I, _P]),
+    ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    ("spalu_solve_host", _I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    ("spalu_stats", _I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    ("spalu_factor_destroy", None, [_P]),
+]
+
+
+def load_library(path: str | None = None):
+    """Load the CUDA library (building is done by __graft_entry__.build or build.py)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(
+            f"spaLU CUDA library not found at {p}: build it first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(status: int, where: str):
+    if status != SPALU_OK:
+        raise SpaluError(status, where)
+
+
+def _dev_ptr(t, dtype):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA tensor of {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class NestedDissection:
+    """spalu_nd_build_grid: nested dissection of an nx x ny grid (leaf pitch 16)."""
+
+    def __init__(self, nx: int, ny: int | None = None, leaf_pitch: int = 16, stream=None):
+        self.lib = load_library()
+        self.nx = nx
+        self.ny = nx if ny is None else ny
+        h = ctypes.c_void_p()
+        _check(self.lib.spalu_nd_build_grid(nx, self.ny, leaf_pitch, _stream_ptr(stream), ctypes.byref(h)),
+               "spalu_nd_build_grid")
+        self.handle = h
+
+    def export(self):
+        n = self.nx * self.ny
+        perm = np.empty(n, dtype=np.int32)
+        iperm = np.empty(n, dtype=np.int32)
+        levels = np.zeros(8 * 64, dtype=np.int32)
+        _check(self.lib.spalu_nd_export(self.handle, perm.ctypes.data, iperm.ctypes.data,
+                                        levels.ctypes.data, levels.size), "spalu_nd_export")
+        L = int(levels[0])
+        table = levels[8: 8 * (L + 1)].reshape(L, 8) if L else np.zeros((0, 8), np.int32)
+        return perm, iperm, L, table
+
+    def finest_segments(self, nseg: int) -> np.ndarray:
+        out = np.empty(15 * nseg, dtype=np.int32)
+        _check(self.lib.spalu_nd_export_segments(self.handle, out.ctypes.data, out.size),
+               "spalu_nd_export_segments")
+        return out.reshape(nseg, 15)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.lib.spalu_nd_destroy(h)
+            self.handle = None
+
+
+class Factor:
+    """spalu_factor_create / _numeric / spalu_solve / spalu_refine on one grid."""
+
+    def __init__(self, nd: NestedDissection, opts: Options | None = None, **kw):
+        self.lib = load_library()
+        self.nd = nd
+        self.opts = opts if opts is not None else Options.default(**kw)
+        h = ctypes.c_void_p()
+        _check(self.lib.spalu_factor_create(nd.handle, ctypes.byref(self.opts), ctypes.byref(h)),
+               "spalu_factor_create")
+        self.handle = h
+        self.N = nd.nx * nd.ny
+
+    def factor(self, rowptr, colind, val, stream=None):
+        """Numeric factorization of a device CSR matrix (torch int32/int32/float64)."""
+        import torch
+        _check(self.lib.spalu_factor_numeric(self.handle, _dev_ptr(rowptr, torch.int32),
+                                             _dev_ptr(colind, torch.int32), _dev_ptr(val, torch.float64),
+                                             int(val.numel()), _stream_ptr(stream)),
+               "spalu_factor_numeric")
+
+    def factor_host(self, rowptr: np.ndarray, colind: np.ndarray, val: np.ndarray, stream=None):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        colind = np.ascontiguousarray(colind, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        _check(self.lib.spalu_factor_numeric_host(self.handle, rowptr.ctypes.data, colind.ctypes.data,
+                                                  val.ctypes.data, int(val.size), _stream_ptr(stream)),
+               "spalu_factor_numeric_host")
+
+    def solve(self, B, X=None, stream=None):
+        """X = spaLU^{-1} B for a device float64 tensor B of shape (N,) or (nrhs, N) laid
+        out column by column (row k of the tensor is right-hand side k)."""
+        import torch
+        if X is None:
+            X = torch.empty_like(B)
+        nrhs = 1 if B.dim() == 1 else B.shape[0]
+        _check(self.lib.spalu_solve(self.handle, _dev_ptr(B, torch.float64), _dev_ptr(X, torch.float64),
+                                    nrhs, self.N, _stream_ptr(stream)), "spalu_solve")
+        return X
+
+    def refine(self, B, X, stream=None, check=True):
+        """GMRES refinement of X in place; returns (iterations, relative residuals)."""
+        import torch
+        nrhs = 1 if B.dim() == 1 else B.shape[0]
+        it = ctypes.c_int(0)
+        rel = np.zeros(nrhs)
+        st = self.lib.spalu_refine(self.handle, _dev_ptr(B, torch.float64), _dev_ptr(X, torch.float64),
+                                   nrhs, self.N, ctypes.byref(it), rel.ctypes.data, _stream_ptr(stream))
+        if check:
+            _check(st, "spalu_refine")
+        return it.value, rel
+
+    def solve_host(self, B: np.ndarray, refine: bool = False, stream=None):
+        """Host arrays in and out (copies inside the call); B has shape (nrhs, N)."""
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        nrhs = 1 if B.ndim == 1 else B.shape[0]
+        X = np.empty_like(B)
+        it = ctypes.c_int(0)
+        rel = np.zeros(nrhs)
+        _check(self.lib.spalu_solve_host(self.handle, B.ctypes.data, X.ctypes.data, nrhs, self.N,
+                                         1 if refine else 0, ctypes.byref(it), rel.ctypes.data,
+                                         _stream_ptr(stream)), "spalu_solve_host")
+        return X, it.value, rel
+
+    def stats(self) -> dict:
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(self.lib.spalu_stats(self.handle, buf, len(buf)), "spalu_stats")
+        return json.loads(buf.value.decode())
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.lib.spalu_factor_destroy(h)
+            self.handle = None

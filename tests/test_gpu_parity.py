@@ -1,0 +1,180 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded inputs.
+
+Bars: integer tables (ND order, segment node lists) bit-exact; FP64 solutions within a
+relative 1e-6 of the oracle's at eps_ID = 1e-8 (skeleton choices may differ at pivot
+ties); eps_ID = 0 (exact block LU) within 1e-11 of a dense solve; refinement to a relative
+residual <= 1e-10 checked by a CPU residual.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.nd import nested_dissection
+from oracle.spalu import Options as OOpts, factor as ofactor, solve as osolve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _dev(P):
+    d = torch.device("cuda:0")
+    A = P.A
+    return (torch.from_numpy(A.indptr).to(d), torch.from_numpy(A.indices).to(d),
+            torch.from_numpy(A.data).to(d), torch.from_numpy(np.ascontiguousarray(P.B.T)).to(d))
+
+
+def _gpu_solve(P, eps, nx=None, ny=None, refine=False, symmetric=None):
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    nx = nx or P.nx
+    ny = ny or P.ny
+    rp, ci, va, B = _dev(P)
+    nd = NestedDissection(nx, ny)
+    sym = P.symmetric if symmetric is None else symmetric
+    f = Factor(nd, eps_id=eps, symmetric=1 if sym else 0)
+    f.factor(rp, ci, va)
+    X = f.solve(B)
+    info = None
+    if refine:
+        info = f.refine(B, X)
+    torch.cuda.synchronize()
+    return X.cpu().numpy().T, f, info
+
+
+# ------------------------------------------------------------------ ND tables, bit-exact
+@pytest.mark.parametrize("nx,ny", [(15, 15), (31, 31), (63, 63), (127, 31), (31, 127), (255, 255),
+                                   (1023, 1023)])
+def test_nd_order_bit_exact(nx, ny):
+    from paper_2408_14193_gb300 import NestedDissection
+    nd = NestedDissection(nx, ny)
+    perm, iperm, L, table = nd.export()
+    ond = nested_dissection(nx, ny)
+    assert L == ond.L
+    assert np.array_equal(perm.astype(np.int64), ond.perm)
+    assert np.array_equal(iperm[perm], np.arange(nx * ny))
+    for l in range(1, L + 1):
+        lev = ond.levels[l]
+        bx, by, w, h, vc, nseg, ncor, nsep = table[l - 1]
+        assert (w, h) == (lev.boxes[0].w, lev.boxes[0].h)
+        assert nseg == len(lev.segments) and ncor == len(lev.corners) and nsep == len(lev.separators)
+    if L:
+        segs = nd.finest_segments(int(table[L - 1][5]))
+        for s in ond.levels[L].segments.values():
+            assert np.array_equal(segs[s.sid].astype(np.int64), s.nodes)
+
+
+# ------------------------------------------------------------------ exact special case
+@pytest.mark.parametrize("kind,n", [("laplace", 15), ("diffusion", 31), ("convdiff", 31),
+                                    ("helmholtz", 63), ("diffusion", 63)])
+def test_eps0_equals_dense_solve(kind, n):
+    P = W.make_problem(kind, n, seed=21, nrhs=3)
+    X, _, _ = _gpu_solve(P, 0.0)
+    Xd = np.linalg.solve(P.A.to_dense(), P.B)
+    assert np.linalg.norm(X - Xd) <= 1e-11 * np.linalg.norm(Xd)
+
+
+# ------------------------------------------------------------------ FP64 parity with the oracle
+@pytest.mark.parametrize("kind,n,nrhs", [("laplace", 127, 1), ("diffusion", 127, 4),
+                                         ("convdiff", 127, 2), ("diffusion", 255, 2),
+                                         ("helmholtz", 63, 2)])
+def test_fp64_matches_oracle(kind, n, nrhs):
+    P = W.make_problem(kind, n, seed=22, nrhs=nrhs)
+    X, f, _ = _gpu_solve(P, 1e-8)
+    F = ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-8, symmetric=P.symmetric))
+    Xo = osolve(F, P.B)
+    rel = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    assert rel <= 1e-6, rel
+    # rank statistics agree level by level (pivot ties may move a rank by one)
+    st = f.stats()
+    for lv in st["levels"]:
+        o = F.stats["levels"][lv["level"]]
+        assert lv["e_max"] == o["e_max"] or abs(lv["e_max"] - o["e_max"]) <= 2
+        assert abs(lv["k_max"] - o["k_max"]) <= 2
+
+
+@pytest.mark.parametrize("nx,ny", [(127, 31), (31, 63)])
+def test_rectangular_grids(nx, ny):
+    P = W.make_problem("diffusion", nx, seed=23, nrhs=2, ny=ny)
+    X, _, _ = _gpu_solve(P, 1e-8, nx=nx, ny=ny)
+    Xo = osolve(ofactor(P.A, nested_dissection(nx, ny), OOpts(eps=1e-8, symmetric=True)), P.B)
+    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+
+
+def test_nonsymmetric_flag_on_symmetric_matrix():
+    """Stacked ID on a symmetric matrix gives the same solution as the symmetric ID."""
+    P = W.make_problem("diffusion", 63, seed=24, nrhs=1)
+    X1, _, _ = _gpu_solve(P, 1e-8, symmetric=True)
+    X2, _, _ = _gpu_solve(P, 1e-8, symmetric=False)
+    Xd = np.linalg.solve(P.A.to_dense(), P.B)
+    for X in (X1, X2):
+        assert np.linalg.norm(X - Xd) <= 1e-5 * np.linalg.norm(Xd)
+
+
+# ------------------------------------------------------------------ refinement
+@pytest.mark.parametrize("kind,n,eps", [("diffusion", 127, 1e-6), ("convdiff", 127, 1e-6),
+                                        ("helmholtz", 127, 1e-8)])
+def test_refine_reaches_tolerance(kind, n, eps):
+    P = W.make_problem(kind, n, seed=25, nrhs=3)
+    X, f, (it, rel) = _gpu_solve(P, eps, refine=True)
+    res = np.linalg.norm(P.B - P.A.matvec(X), axis=0) / np.linalg.norm(P.B, axis=0)
+    assert np.all(res <= 1e-10), res
+    assert np.all(rel <= 1e-10)
+    assert it >= 1
+
+
+# ------------------------------------------------------------------ API edge cases
+def test_solve_aliasing_and_host_entry_points():
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    P = W.make_problem("laplace", 63, seed=26, nrhs=2)
+    rp, ci, va, B = _dev(P)
+    nd = NestedDissection(63)
+    f = Factor(nd, eps_id=1e-8, symmetric=1)
+    f.factor(rp, ci, va)
+    X = f.solve(B)
+    Y = B.clone()
+    f.solve(Y, Y)                                   # X may alias B
+    torch.cuda.synchronize()
+    assert torch.equal(X, Y)
+    g = Factor(nd, eps_id=1e-8, symmetric=1)
+    g.factor_host(P.A.indptr, P.A.indices, P.A.data)
+    Xh, it, rel = g.solve_host(np.ascontiguousarray(P.B.T), refine=True)
+    res = np.linalg.norm(P.B - P.A.matvec(Xh.T), axis=0) / np.linalg.norm(P.B, axis=0)
+    assert np.all(res <= 1e-10)
+
+
+def test_errors_are_reported_not_raised_on_device():
+    from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError
+    nd = NestedDissection(31)
+    f = Factor(nd, eps_id=1e-8)
+    B = torch.zeros(31 * 31, dtype=torch.float64, device="cuda")
+    with pytest.raises(SpaluError):
+        f.solve(B)                                 # not factored yet -> state error
+    # a zero row makes a leaf interior block singular
+    P = W.make_problem("laplace", 31, seed=27)
+    A = P.A
+    val = A.data.copy()
+    r = 5 + 31 * 5
+    val[A.indptr[r]:A.indptr[r + 1]] = 0.0
+    rp, ci, _, _ = _dev(P)
+    with pytest.raises(SpaluError) as e:
+        f.factor(rp, ci, torch.from_numpy(val).cuda())
+    assert e.value.status == -3
+
+
+def test_full_size_diffusion_1023_refined():
+    """The 1023 x 1023 variable-coefficient problem (16 RHS) at full size: ND order
+    bit-exact (above) and the refined residual checked on the CPU."""
+    P = W.make_problem("diffusion", 1023, seed=1, nrhs=16)
+    X, f, (it, rel) = _gpu_solve(P, 1e-8, refine=True)
+    res = np.linalg.norm(P.B - P.A.matvec(X), axis=0) / np.linalg.norm(P.B, axis=0)
+    assert np.all(res <= 1e-10), res
+    st = f.stats()
+    assert st["L"] == 12 and st["q_tilde"] <= 1.0
