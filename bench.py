@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: factor + solve DOF/s of the spaLU fast direct solver on one GB300.
+
+Step = one numeric factorization of the 1023 x 1023 variable-coefficient diffusion matrix
+(a = exp(GRF), squared-exponential covariance with length 0.05, variance 1), the direct
+solve of 16 standard-normal right-hand sides and GMRES refinement of every column to a
+relative residual <= 1e-10.  value = N / (T_factor + T_solve+refine), summed over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank factors its own instance (seed + rank): the problems are
+independent, so there is no data-path collective and scaling is weak.  --impl reference
+times the CPU oracle (the plain FP64 restatement of the method) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+# the CPU oracle leg is reported as single-threaded: keep numpy's BLAS on one thread
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+METRIC = "factor+solve DOF/s at N≈1M, mixed+learned vs plain FP64 GPU @1e-10 residual"
+N_SIDE = 1023
+NRHS = 16
+EPS_ID = 1e-8
+FP64_FLOP_PER_CLK_SM = 4          # 2 FP64 FMA per clock per SM on GB300
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def leaf_algorithmic_flops() -> float:
+    """FP64 FLOPs of one leaf elimination: band LU of the 225 x 225 interior (bandwidths
+    15/15, no pivot fill) and 60 band solves for the Schur complement onto the sides."""
+    n, b = 225, 15
+    lu = 0.0
+    solves = 0.0
+    for j in range(n):
+        km = min(b, n - 1 - j)
+        lu += km + 2.0 * km * km
+        solves += 2.0 * km + 1.0 + 2.0 * min(b, j)
+    return lu + 60.0 * solves
+
+
+def peaks() -> dict:
+    p = {"hbm_gbs": None, "bf16_tflops": None}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p.update({k: m.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "sm_max_mhz")})
+    except OSError:
+        pass
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: str):
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "-i", gpu,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.out.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(n: int, nrhs: int, seed: int = 1):
+    """Factor + solve + GMRES refinement of one instance with the CPU oracle; returns
+    (DOF/s, seconds, relres max, cores used)."""
+    import numpy as np
+
+    import workloads as W
+    from oracle.gmres import gmres
+    from oracle.nd import nested_dissection
+    from oracle.spalu import Options, factor, solve
+    P = W.make_problem("diffusion", n, seed=seed, nrhs=nrhs)
+    nd = nested_dissection(n, n)
+    t0 = time.perf_counter()
+    F = factor(P.A, nd, Options(eps=EPS_ID, symmetric=True))
+    X = solve(F, P.B)
+    rel = []
+    for c in range(nrhs):
+        x, _, r = gmres(P.A.matvec, lambda v: solve(F, v), P.B[:, c], X[:, c], m=30, tol=1e-10)
+        X[:, c] = x
+        rel.append(r)
+    t = time.perf_counter() - t0
+    return n * n / t, t, max(rel), 1
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.ref_n
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, t, rel, cores = oracle_sample(n, NRHS, seed=1 + i)
+        if i >= args.warmup:
+            times.append(t)
+    tot = sum(times)
+    value = args.steps * n * n / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"diffusion {n}x{n} a=exp(GRF l=0.05 var=1), {NRHS} normal RHS, "
+                               f"eps_ID={EPS_ID}, GMRES to 1e-10 (bounded sample of the "
+                               f"{N_SIDE}x{N_SIDE} workload)", "N": n * n, "nrhs": NRHS},
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n}x{n} instance of the same problem family, {NRHS} RHS, "
+                                   "factor + solve + GMRES per step"},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import workloads as W
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local if torch.cuda.device_count() > local else 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    ge.build()
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    from paper_2408_14193_gb300.spalu import kernel_launches
+
+    P = W.make_problem("diffusion", N_SIDE, seed=1 + rank, nrhs=NRHS)
+    N = P.A.n
+    A = P.A
+    rp = torch.from_numpy(A.indptr).to(dev)
+    ci = torch.from_numpy(A.indices).to(dev)
+    va = torch.from_numpy(A.data).to(dev)
+    B = torch.from_numpy(np.ascontiguousarray(P.B.T)).to(dev)
+    X = torch.empty_like(B)
+    nd = NestedDissection(N_SIDE)
+    f = Factor(nd, eps_id=EPS_ID, symmetric=1, precision=0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        f.factor(rp, ci, va)
+        f.solve(B, X)
+        it, rel = f.refine(B, X)
+        return it, rel
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", "") or "")
+    gpu_id = ("GPU-" + gpu_id) if gpu_id and not gpu_id.startswith("GPU-") else (gpu_id or str(local))
+    f.set_timing(True)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    l0 = kernel_launches()
+    ms = 0.0
+    iters, rels = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, rel = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        iters.append(it)
+        rels.append(float(np.max(rel)))
+    torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    st = f.stats()
+    f.set_timing(False)
+
+    # end to end through the host-memory entry points (pinned host buffers)
+    val_h = torch.from_numpy(A.data).pin_memory().numpy()
+    rp_h = torch.from_numpy(A.indptr).pin_memory().numpy()
+    ci_h = torch.from_numpy(A.indices).pin_memory().numpy()
+    B_h = torch.from_numpy(np.ascontiguousarray(P.B.T)).pin_memory().numpy()
+    g = Factor(nd, eps_id=EPS_ID, symmetric=1, precision=0)
+    g.factor_host(rp_h, ci_h, val_h)
+    g.solve_host(B_h, refine=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_rel = 0.0
+    for _ in range(args.steps):
+        g.factor_host(rp_h, ci_h, val_h)
+        Xh, _, rel = g.solve_host(B_h, refine=True)
+        e2e_rel = max(e2e_rel, float(np.max(rel)))
+    e2e_s = time.perf_counter() - t0
+    del g
+
+    tmax = ms
+    if pg:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tmax, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        pg.destroy_process_group()
+        return 0
+    value = ws * args.steps * N / (tmax / 1e3)
+    e2e_value = ws * args.steps * N / e2e_s
+
+    # roofline of the dominant single-kernel phase (FP64 ALU bound)
+    tms, tcount = st["timing_ms"], st["timing_count"]
+    single = {k: v for k, v in tms.items() if k == "leaf_factor" or k.startswith("sparsify_l")}
+    dom = max(single, key=single.get)
+    dur_ms = tms[dom] / tcount[dom]
+    nleaf = ((N_SIDE + 1) // 16) ** 2
+    smhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    peak_tf = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    roof = None
+    if dom == "leaf_factor":
+        flops = nleaf * leaf_algorithmic_flops()
+        ach = flops / (dur_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach / peak_tf, "traffic": None, "kernel": "leaf_factor_kernel",
+                "launch_ms": dur_ms, "peak_note": "FP64 FMA: 152 SMs x 4 FLOP/clk x 2070 MHz (derived)"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak_tf, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": dom, "launch_ms": dur_ms}
+
+    phases = {k: round(v / args.steps, 4) for k, v in sorted(tms.items())}
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        v, t, rel, cores = oracle_sample(args.cpu_n, NRHS)
+        cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+               "sample": f"one {args.cpu_n}x{args.cpu_n} instance of the same family, {NRHS} RHS, "
+                         f"factor + solve + GMRES to 1e-10 ({t:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"diffusion {N_SIDE}x{N_SIDE} a=exp(GRF l=0.05 var=1), {NRHS} normal "
+                               f"RHS, eps_ID={EPS_ID}, plain FP64, GMRES to 1e-10",
+                   "N": N, "nrhs": NRHS, "precision": "fp64", "learned_ranks": False,
+                   "l2": "256 MB flush between steps; factor working set > L2"},
+        "relres_max": max(rels), "gmres_iters": max(iters),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "DOF/s",
+                "h2d_bytes_per_step": int(A.data.nbytes + P.B.nbytes),
+                "d2h_bytes_per_step": int(P.B.nbytes), "relres_max": e2e_rel},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "phase_ms_per_step": phases,
+        "factor_stats": {"q_tilde": st["q_tilde"], "levels": st["levels"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-n", type=int, default=255, dest="cpu_n")
+    ap.add_argument("--ref-n", type=int, default=127, dest="ref_n")
+    ap.add_argument("--no-cpu", action="store_true", dest="no_cpu")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -134,6 +134,17 @@ spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int 
  * (Sec. 6), device bytes held.  Synchronises the factor's stream. */
 spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap);
 
+/* Per-phase timing: with on != 0, every later factor / solve / refine call on f records a
+ * pair of CUDA events around each of its kernel phases on the stream it launches on;
+ * spalu_stats then reports, per phase name, the summed milliseconds and the count of
+ * recorded intervals ("timing_ms", "timing_count").  Calling it resets the sums.
+ * Off by default (no events are recorded). */
+spalu_status spalu_set_timing(spalu_factor_t f, int on);
+
+/* Number of CUDA kernels this library has launched so far in the calling process, over all
+ * handles (a diagnostic counter; never reset). */
+unsigned long long spalu_kernel_launches(void);
+
 void spalu_factor_destroy(spalu_factor_t f);
 
 #ifdef __cplusplus

@@ -2,7 +2,9 @@
 // planned from the grid), numeric factorization (Alg. 2), tree-ordered solve (Eq. (WV)) and
 // GMRES refinement.  See include/spalu.h for the contract of every entry point.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -31,6 +33,53 @@ struct GmresWork {
   double* vec = nullptr;    // nrhs scalars
 };
 
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void spalu::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct PhaseTimer {
+  bool on = false;
+  struct Rec { std::string name; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, double> ms;
+  std::map<std::string, long long> count;
+  cudaEvent_t take() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // open an interval on stream s; returns its index (or -1 when timing is off)
+  int begin(const std::string& name, cudaStream_t s) {
+    if (!on) return -1;
+    Rec r{name, take(), take()};
+    cudaEventRecord(r.a, s);
+    recs.push_back(r);
+    return (int)recs.size() - 1;
+  }
+  void end(int i, cudaStream_t s) {
+    if (i >= 0) cudaEventRecord(recs[i].b, s);
+  }
+  // fold the finished intervals into the sums
+  void collect() {
+    for (auto& r : recs) {
+      float t = 0.f;
+      cudaEventSynchronize(r.b);
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) { ms[r.name] += t; count[r.name] += 1; }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  void reset() { collect(); ms.clear(); count.clear(); }
+  ~PhaseTimer() {
+    for (auto& r : recs) { pool.push_back(r.a); pool.push_back(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct spalu_factor_s {
   spalu_nd_s* nd = nullptr;
   spalu_opts o{};
@@ -49,6 +98,7 @@ struct spalu_factor_s {
   cudaStream_t last_stream = nullptr;
   GmresWork gw;
   std::vector<int> host_rowptr_cache;
+  PhaseTimer timer;
 };
 
 namespace {
@@ -386,13 +436,22 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
 
 static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   const int L = f->nd->L;
+  PhaseTimer& tm = f->timer;
+  int t_all = tm.begin("factor", s);
   CUDA_TRY(cudaMemsetAsync(f->d_err, 0, sizeof(int), s));
   if (L >= 1) launch_level_init_L(f->lev[L], s);
+  int t = tm.begin("leaf_factor", s);
   launch_leaf_factor(f->leaf, s);
+  tm.end(t, s);
   for (int l = L; l >= 1; --l) {
+    t = tm.begin("sparsify_l" + std::to_string(l), s);
     launch_sparsify(f->lev[l], f->plan[l], s);
+    tm.end(t, s);
+    t = tm.begin("merge_l" + std::to_string(l), s);
     launch_merge(f->lev[l], f->plan[l], s);
+    tm.end(t, s);
   }
+  tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());
   spalu_status st = read_err(f, s);
   f->factored = (st == SPALU_OK);
@@ -434,20 +493,29 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
   if (nrhs == 0) return SPALU_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int L = f->nd->L;
+  PhaseTimer& tm = f->timer;
+  int t_all = tm.begin("solve", s);
   if (X != B)
     CUDA_TRY(cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), B, (size_t)ld * sizeof(double),
                                (size_t)f->N * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
+  int t = tm.begin("leaf_solve_fwd", s);
   for (int c0 = 0; c0 < nrhs; c0 += 32) {
     int nc = std::min(32, nrhs - c0);
     launch_leaf_solve_fwd(f->leaf, X + (size_t)ld * c0, nc, ld, s);
   }
   if (L >= 1) launch_sep_update_fwd(f->leaf, X, nrhs, ld, s);
+  tm.end(t, s);
+  t = tm.begin("level_solve", s);
   for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], X, nrhs, ld, s);
   for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], X, nrhs, ld, s);
+  tm.end(t, s);
+  t = tm.begin("leaf_solve_bwd", s);
   for (int c0 = 0; c0 < nrhs; c0 += 32) {
     int nc = std::min(32, nrhs - c0);
     launch_leaf_solve_bwd(f->leaf, X + (size_t)ld * c0, nc, ld, nullptr, s);
   }
+  tm.end(t, s);
+  tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());
   return SPALU_OK;
 }
@@ -476,12 +544,26 @@ static void dots(spalu_factor_t f, const double* x, int ldx, const double* y, in
                  double* out, int sq, cudaStream_t s) {
   const int nb = 512;
   dim3 grid(nb, nrhs);
+  note_launch();
   dot_partial_kernel<<<grid, 256, 0, s>>>(f->N, x, ldx, y, ldy, f->gw.part);
+  note_launch();
   dot_final_kernel<<<nrhs, 32, 0, s>>>(f->gw.part, nb, out, sq);
 }
 
+static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                                int* iters, double* relres, spalu_stream_t stream);
+
 spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
                           int* iters, double* relres, spalu_stream_t stream) {
+  if (!f) return SPALU_ERR_ARG;
+  int t = f->timer.begin("refine", (cudaStream_t)stream);
+  spalu_status st = refine_impl(f, B, X, nrhs, ld, iters, relres, stream);
+  f->timer.end(t, (cudaStream_t)stream);
+  return st;
+}
+
+static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
+                                int* iters, double* relres, spalu_stream_t stream) {
   if (!f || !B || !X || nrhs < 0 || ld < f->N) return SPALU_ERR_ARG;
   if (!f->factored) return SPALU_ERR_STATE;
   if (nrhs == 0) return SPALU_OK;
@@ -499,6 +581,7 @@ spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs
   dots(f, B, ld, B, ld, nrhs, dvec, 1, s);
   CUDA_TRY(cudaMemcpyAsync(bn.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
   auto residual = [&]() -> spalu_status {
+    note_launch();
     spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, X, ld, B, ld, w.R, (int)ldv, nrhs);
     dots(f, w.R, (int)ldv, w.R, (int)ldv, nrhs, dvec, 1, s);
     CUDA_TRY(cudaMemcpyAsync(beta.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
@@ -520,6 +603,7 @@ spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs
     std::vector<double> bsc(nrhs);
     for (int c = 0; c < nrhs; ++c) bsc[c] = done(c) ? 0.0 : beta[c];
     CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, bsc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    note_launch();
     scale_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, dvec + nrhs, w.R, (int)ldv, Vj(0), (int)ldv);
     for (int c = 0; c < nrhs; ++c) {
       std::fill(H[c].begin(), H[c].end(), 0.0);
@@ -529,15 +613,19 @@ spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs
     int jl = -1;
     for (int j = 0; j < m; ++j) {
       // W = A M^{-1} V_j
+      note_launch();
       copy_cols_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, Vj(j), (int)ldv, w.W, (int)ldv);
       if ((st = spalu_solve(f, w.W, w.W, nrhs, (int)ldv, stream)) != SPALU_OK) return st;
+      note_launch();
       spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, w.W, (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, nrhs);
       // modified Gram-Schmidt
       for (int i = 0; i <= j; ++i) {
         dots(f, Vj(j + 1), (int)ldv, Vj(i), (int)ldv, nrhs, w.hcol + (size_t)i * nrhs, 0, s);
+        note_launch();
         axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, -1.0, w.hcol + (size_t)i * nrhs, Vj(i), (int)ldv, Vj(j + 1), (int)ldv);
       }
       dots(f, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv, nrhs, w.hcol + (size_t)(j + 1) * nrhs, 1, s);
+      note_launch();
       scale_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, w.hcol + (size_t)(j + 1) * nrhs, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
       CUDA_TRY(cudaMemcpyAsync(hh.data(), w.hcol, sizeof(double) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
@@ -577,11 +665,14 @@ spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs
     }
     CUDA_TRY(cudaMemsetAsync(w.W, 0, sizeof(double) * ldv * nrhs, s));
     CUDA_TRY(cudaMemcpyAsync(w.hcol, ycoef.data(), sizeof(double) * kdim * nrhs, cudaMemcpyHostToDevice, s));
-    for (int i = 0; i < kdim; ++i)
+    for (int i = 0; i < kdim; ++i) {
+      note_launch();
       axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, w.hcol + (size_t)i * nrhs, Vj(i), (int)ldv, w.W, (int)ldv);
+    }
     if ((st = spalu_solve(f, w.W, w.W, nrhs, (int)ldv, stream)) != SPALU_OK) return st;
     std::vector<double> ones(nrhs, 1.0);
     CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, ones.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    note_launch();
     axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, dvec + nrhs, w.W, (int)ldv, X, ld);
     if ((st = residual()) != SPALU_OK) return st;
   }
@@ -650,12 +741,39 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
     out += buf;
   }
   char buf[64];
-  std::snprintf(buf, sizeof buf, "], \"q_tilde\": %.6f}", qt);
+  std::snprintf(buf, sizeof buf, "], \"q_tilde\": %.6f", qt);
   out += buf;
+  f->timer.collect();
+  out += ", \"timing_ms\": {";
+  bool first = true;
+  for (auto& kv : f->timer.ms) {
+    char b2[160];
+    std::snprintf(b2, sizeof b2, "%s\"%s\": %.6f", first ? "" : ", ", kv.first.c_str(), kv.second);
+    out += b2;
+    first = false;
+  }
+  out += "}, \"timing_count\": {";
+  first = true;
+  for (auto& kv : f->timer.count) {
+    char b2[160];
+    std::snprintf(b2, sizeof b2, "%s\"%s\": %lld", first ? "" : ", ", kv.first.c_str(), kv.second);
+    out += b2;
+    first = false;
+  }
+  out += "}}";
   if (out.size() + 1 > cap) return SPALU_ERR_ARG;
   std::memcpy(json, out.c_str(), out.size() + 1);
   return SPALU_OK;
 }
+
+spalu_status spalu_set_timing(spalu_factor_t f, int on) {
+  if (!f) return SPALU_ERR_ARG;
+  f->timer.reset();
+  f->timer.on = on != 0;
+  return SPALU_OK;
+}
+
+unsigned long long spalu_kernel_launches(void) { return g_launches.load(); }
 
 void spalu_factor_destroy(spalu_factor_t f) {
   if (!f) return;

@@ -317,6 +317,7 @@ static size_t leaf_factor_smem() {
 void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
   size_t smem = leaf_factor_smem();
   cudaFuncSetAttribute(leaf_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
   leaf_factor_kernel<<<d.g.nbox(), 256, smem, s>>>(d);
 }
 
@@ -327,6 +328,7 @@ static size_t leaf_solve_smem(int nrhs) {
 void launch_leaf_solve_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
   size_t smem = leaf_solve_smem(nrhs);
   cudaFuncSetAttribute(leaf_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
   leaf_solve_kernel<<<d.g.nbox(), 256, smem, s>>>(d, X, nrhs, ld, 0, nullptr);
 }
 
@@ -335,12 +337,14 @@ void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaSt
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
+  note_launch();
   sep_update_fwd_kernel<<<blocks, 256, 0, s>>>(d, X, nrhs, ld);
 }
 
 void launch_leaf_solve_bwd(const LeafDev& d, double* X, int nrhs, int ld, double* tmp, cudaStream_t s) {
   size_t smem = leaf_solve_smem(nrhs);
   cudaFuncSetAttribute(leaf_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
   leaf_solve_kernel<<<d.g.nbox(), 256, smem, s>>>(d, X, nrhs, ld, 1, tmp);
 }
 

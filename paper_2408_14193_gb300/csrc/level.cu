@@ -1089,6 +1089,7 @@ size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over) {
 void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
   int n = d.g.nseg() * LEAF;
   if (n == 0) return;
+  note_launch();
   level_init_L_kernel<<<(n + 255) / 256, 256, 0, s>>>(d);
 }
 
@@ -1096,26 +1097,34 @@ void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   if (d.g.nseg() == 0) return;
   int smem = (int)p.spars_smem;
   cudaFuncSetAttribute(sparsify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  note_launch();
   sparsify_kernel<<<d.g.nseg(), 256, smem, s>>>(d, smem);
 }
 
 void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   const int np = d.gp.nbox();
+  note_launch();
   merge_table_kernel<<<np, 32, 0, s>>>(d);
   {
     long long nmax = (long long)p.ldFp;
     int gx = (int)((nmax * nmax + 255) / 256);
     if (gx > 256) gx = 256;
     dim3 grid(gx, np);
+    note_launch();
     merge_assemble_kernel<<<grid, 256, 0, s>>>(d);
   }
+  note_launch();
   merge_panel_kernel<<<np, 256, 0, s>>>(d);
   {
     int tiles = (p.ldFp + 63) / 64;
     dim3 grid(tiles, tiles, np);
+    note_launch();
     merge_schur_kernel<<<grid, 256, 0, s>>>(d);
   }
-  if (d.l > 1 && d.gp.nseg() > 0) seg_merge_kernel<<<d.gp.nseg(), 128, 0, s>>>(d);
+  if (d.l > 1 && d.gp.nseg() > 0) {
+    note_launch();
+    seg_merge_kernel<<<d.gp.nseg(), 128, 0, s>>>(d);
+  }
 }
 
 static int col_chunk(size_t per_col_bytes) {
@@ -1131,6 +1140,7 @@ void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cuda
       int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
       size_t smem = sizeof(double) * (size_t)d.capS * nc;
       cudaFuncSetAttribute(seg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      note_launch();
       seg_solve_kernel<<<d.g.nseg(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 0);
     }
   }
@@ -1139,8 +1149,10 @@ void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cuda
     int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
     size_t smem = sizeof(double) * (size_t)d.sepcap * nc;
     cudaFuncSetAttribute(sep_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    for (int colour = 0; colour < 4; ++colour)
+    for (int colour = 0; colour < 4; ++colour) {
+      note_launch();
       sep_solve_kernel<<<d.gp.nbox(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 0, colour);
+    }
   }
 }
 
@@ -1150,6 +1162,7 @@ void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cuda
     int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
     size_t smem = sizeof(double) * (size_t)d.sepcap * nc;
     cudaFuncSetAttribute(sep_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
     sep_solve_kernel<<<d.gp.nbox(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 1, 0);
   }
   if (d.g.nseg() > 0) {
@@ -1158,6 +1171,7 @@ void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cuda
       int nc = nrhs - c0 < cc2 ? nrhs - c0 : cc2;
       size_t smem = sizeof(double) * (size_t)d.capS * nc;
       cudaFuncSetAttribute(seg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      note_launch();
       seg_solve_kernel<<<d.g.nseg(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 1);
     }
   }

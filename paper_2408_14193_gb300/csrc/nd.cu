@@ -109,6 +109,7 @@ void launch_nd_perm(int nx, int ny, int L, const int* vcut_host, int* d_perm, in
   long long n = (long long)nx * ny;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
+  note_launch();
   nd_perm_kernel<<<blocks, 256, 0, s>>>(P, d_perm, d_iperm);
 }
 

@@ -139,6 +139,9 @@ constexpr int KL = LEAF;               // lower bandwidth of the leaf matrix (na
 constexpr int KU = LEAF;               // upper bandwidth
 constexpr int LDAB = 2 * KL + KU + 1;  // band storage rows (LAPACK layout with pivot fill)
 
+// Kernels launched by this library in this process (diagnostics, spalu_kernel_launches).
+void note_launch();
+
 // launch helpers (defined in the .cu files)
 void launch_leaf_factor(const LeafDev& d, cudaStream_t s);
 void launch_level_init_L(const LevelDev& d, cudaStream_t s);

@@ -82,6 +82,8 @@ SIGNATURES = [
     ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     ("spalu_solve_host", _I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_stats", _I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    ("spalu_set_timing", _I, [_P, _I]),
+    ("spalu_kernel_launches", ctypes.c_ulonglong, []),
     ("spalu_factor_destroy", None, [_P]),
 ]
 
@@ -104,6 +106,10 @@ def load_library(path: str | None = None):
     if path is None:
         _LIB = lib
     return lib
+
+
+def kernel_launches() -> int:
+    return int(load_library().spalu_kernel_launches())
 
 
 def _stream_ptr(stream=None):
@@ -223,6 +229,9 @@ class Factor:
                                          1 if refine else 0, ctypes.byref(it), rel.ctypes.data,
                                          _stream_ptr(stream)), "spalu_solve_host")
         return X, it.value, rel
+
+    def set_timing(self, on: bool = True):
+        _check(self.lib.spalu_set_timing(self.handle, 1 if on else 0), "spalu_set_timing")
 
     def stats(self) -> dict:
         buf = ctypes.create_string_buffer(1 << 16)
