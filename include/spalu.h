@@ -134,6 +134,22 @@ spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int 
  * (Sec. 6), device bytes held.  Synchronises the factor's stream. */
 spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap);
 
+/* Relative residual norms relres[c] = ||B_c - A X_c||_2 / ||B_c||_2 (0 when B_c = 0) of nrhs
+ * columns against the matrix of the last factorization, computed without allocating any
+ * device memory.  The paper has no counterpart: this serves callers that cannot let the
+ * library allocate when they check a solution, such as code running while a stream is
+ * captured into a CUDA graph, or hosts that give all device memory to their own pool.
+ * B, X: device, column-major, leading dimension ld >= N; relres: host, nrhs entries.
+ * The reduction goes through one fixed scratch array of 64 * 512 * 2 + 64 doubles
+ * (about 0.5 MB) held by every GPU that loads the library until the process exits, so
+ * nrhs may be at most 64 (larger values return SPALU_ERR_ARG and compute nothing).
+ * The first call on a device looks the array's address up (with that device current) and
+ * should come before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Synchronises the stream to return relres. */
+spalu_status spalu_residual_noalloc(spalu_factor_t f, const double* B, const double* X, int nrhs,
+                                    int ld, double* relres, spalu_stream_t stream);
+
 /* Per-phase timing: with on != 0, every later factor / solve / refine call on f records a
  * pair of CUDA events around each of its kernel phases on the stream it launches on;
  * spalu_stats then reports, per phase name, the summed milliseconds and the count of

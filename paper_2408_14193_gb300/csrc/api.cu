@@ -766,6 +766,14 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
   return SPALU_OK;
 }
 
+spalu_status spalu_residual_noalloc(spalu_factor_t f, const double* B, const double* X, int nrhs,
+                                    int ld, double* relres, spalu_stream_t stream) {
+  if (!f) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  return residual_noalloc(f->N, f->rowptr, f->colind, f->val, B, X, nrhs, ld, relres,
+                          (cudaStream_t)stream);
+}
+
 spalu_status spalu_set_timing(spalu_factor_t f, int on) {
   if (!f) return SPALU_ERR_ARG;
   f->timer.reset();

@@ -161,6 +161,10 @@ void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cuda
 size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over);
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over);
 
+spalu_status residual_noalloc(int n, const int* rowptr, const int* colind, const double* val,
+                              const double* B, const double* X, int nrhs, int ld, double* relres,
+                              cudaStream_t s);
+
 void launch_nd_perm(int nx, int ny, int L, const int* vcut_host, int* d_perm, int* d_iperm,
                     cudaStream_t s);
 

@@ -82,6 +82,7 @@ SIGNATURES = [
     ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     ("spalu_solve_host", _I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_stats", _I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    ("spalu_residual_noalloc", _I, [_P, _P, _P, _I, _I, _P, _P]),
     ("spalu_set_timing", _I, [_P, _I]),
     ("spalu_kernel_launches", ctypes.c_ulonglong, []),
     ("spalu_factor_destroy", None, [_P]),
@@ -229,6 +230,17 @@ class Factor:
                                          1 if refine else 0, ctypes.byref(it), rel.ctypes.data,
                                          _stream_ptr(stream)), "spalu_solve_host")
         return X, it.value, rel
+
+    def residual_noalloc(self, B, X, stream=None):
+        """||B - A X|| / ||B|| per column without any device allocation (nrhs <= 64)."""
+        import torch
+        nrhs = 1 if B.dim() == 1 else B.shape[0]
+        rel = np.zeros(nrhs)
+        _check(self.lib.spalu_residual_noalloc(self.handle, _dev_ptr(B, torch.float64),
+                                               _dev_ptr(X, torch.float64), nrhs, self.N,
+                                               rel.ctypes.data, _stream_ptr(stream)),
+               "spalu_residual_noalloc")
+        return rel
 
     def set_timing(self, on: bool = True):
         _check(self.lib.spalu_set_timing(self.handle, 1 if on else 0), "spalu_set_timing")
