@@ -53,6 +53,13 @@ def leaf_algorithmic_flops() -> float:
     return lu + 60.0 * solves
 
 
+def leaf_solve_flops_per_rhs() -> float:
+    """FP64 FLOPs of one leaf solve sweep pair for one right-hand side: L (bandwidth 15) and
+    U (bandwidth 15, reciprocal pivots)."""
+    n, b = 225, 15
+    return sum(2.0 * min(b, n - 1 - j) + 1.0 + 2.0 * min(b, j) for j in range(n))
+
+
 def peaks() -> dict:
     p = {"hbm_gbs": None, "bf16_tflops": None}
     try:
@@ -172,6 +179,33 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
+def _roofline(st, steps):
+    """Roofline of the dominant kernel: candidates are the phases holding launches of one
+    kernel only; achieved = algorithmic FP64 FLOP per launch / launch time."""
+    tms, tcount = st["timing_ms"], st["timing_count"]
+    nleaf = ((N_SIDE + 1) // 16) ** 2
+    peak_tf = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    cand = {}
+    if "leaf_factor" in tms:
+        cand["leaf_factor_kernel"] = (tms["leaf_factor"], tcount["leaf_factor"], nleaf * leaf_algorithmic_flops())
+    if "leaf_solve_fwd" in tms:
+        t = tms["leaf_solve_fwd"] + tms.get("leaf_solve_bwd", 0.0)
+        c = tcount["leaf_solve_fwd"] + tcount.get("leaf_solve_bwd", 0)
+        cand["leaf_solve_kernel"] = (t, c, nleaf * NRHS * leaf_solve_flops_per_rhs())
+    spars = {k: v for k, v in tms.items() if k.startswith("sparsify_l")}
+    if spars:
+        k = max(spars, key=spars.get)
+        cand["sparsify_kernel (" + k.split("_")[1] + ")"] = (spars[k], tcount[k], None)
+    dom = max(cand, key=lambda k: cand[k][0])
+    tot, cnt, flops = cand[dom]
+    dur_ms = tot / cnt
+    ach = flops / (dur_ms / 1e3) / 1e12 if flops else None
+    return {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": (ach / peak_tf) if ach else None, "traffic": None, "kernel": dom,
+            "launch_ms": dur_ms, "share_of_step": tot / steps,
+            "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2070 MHz"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -198,58 +232,71 @@ def run_ours(args):
     va = torch.from_numpy(A.data).to(dev)
     B = torch.from_numpy(np.ascontiguousarray(P.B.T)).to(dev)
     X = torch.empty_like(B)
+    t_nd = time.perf_counter()
     nd = NestedDissection(N_SIDE)
-    f = Factor(nd, eps_id=EPS_ID, symmetric=1, precision=0)
+    torch.cuda.synchronize()
+    nd_s = time.perf_counter() - t_nd
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-
-    def step():
-        f.factor(rp, ci, va)
-        f.solve(B, X)
-        it, rel = f.refine(B, X)
-        return it, rel
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
     props = torch.cuda.get_device_properties(dev)
     gpu_id = str(getattr(props, "uuid", "") or "")
     gpu_id = ("GPU-" + gpu_id) if gpu_id and not gpu_id.startswith("GPU-") else (gpu_id or str(local))
-    f.set_timing(True)
-    sampler = ClockSampler(gpu_id)
-    time.sleep(0.3)
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    l0 = kernel_launches()
-    ms = 0.0
-    iters, rels = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, rel = step()
-        e1.record(stream)
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
-        iters.append(it)
-        rels.append(float(np.max(rel)))
-    torch.cuda.synchronize()
-    launches = kernel_launches() - l0
-    if pg:
-        pg.barrier()
-    clocks = sampler.stop()
-    st = f.stats()
-    f.set_timing(False)
 
-    # end to end through the host-memory entry points (pinned host buffers)
+    def measure(prec, eps, sample_clocks):
+        f = Factor(nd, eps_id=eps, symmetric=1, precision=prec)
+
+        def step():
+            f.factor(rp, ci, va)
+            f.solve(B, X)
+            return f.refine(B, X)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        f.set_timing(True)
+        sampler = ClockSampler(gpu_id) if sample_clocks else None
+        time.sleep(0.3)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        l0 = kernel_launches()
+        ms = 0.0
+        iters, rels = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, rel = step()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            iters.append(it)
+            rels.append(float(np.max(rel)))
+        torch.cuda.synchronize()
+        launches = kernel_launches() - l0
+        if pg:
+            pg.barrier()
+        clocks = sampler.stop() if sampler else None
+        st = f.stats()
+        f.set_timing(False)
+        del f
+        if pg:
+            t = torch.tensor([ms], dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t[0])
+        return {"ms": ms, "iters": max(iters), "relres": max(rels), "launches": launches,
+                "st": st, "clocks": clocks}
+
+    head = measure(1, args.mixed_eps, True)       # mixed precision: the headline path
+    base = measure(0, EPS_ID, False)              # plain FP64 GPU form
+
+    # end to end through the host-memory entry points (pinned host buffers), headline path
     val_h = torch.from_numpy(A.data).pin_memory().numpy()
     rp_h = torch.from_numpy(A.indptr).pin_memory().numpy()
     ci_h = torch.from_numpy(A.indices).pin_memory().numpy()
     B_h = torch.from_numpy(np.ascontiguousarray(P.B.T)).pin_memory().numpy()
-    g = Factor(nd, eps_id=EPS_ID, symmetric=1, precision=0)
+    g = Factor(nd, eps_id=args.mixed_eps, symmetric=1, precision=1)
     g.factor_host(rp_h, ci_h, val_h)
     g.solve_host(B_h, refine=True)
     torch.cuda.synchronize()
@@ -261,60 +308,49 @@ def run_ours(args):
         e2e_rel = max(e2e_rel, float(np.max(rel)))
     e2e_s = time.perf_counter() - t0
     del g
-
-    tmax = ms
     if pg:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64)
+        t = torch.tensor([e2e_s], dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        tmax, e2e_s = float(t[0]), float(t[1])
+        e2e_s = float(t[0])
     if rank != 0:
         pg.destroy_process_group()
         return 0
-    value = ws * args.steps * N / (tmax / 1e3)
+    value = ws * args.steps * N / (head["ms"] / 1e3)
+    base_value = ws * args.steps * N / (base["ms"] / 1e3)
     e2e_value = ws * args.steps * N / e2e_s
 
-    # roofline of the dominant single-kernel phase (FP64 ALU bound)
-    tms, tcount = st["timing_ms"], st["timing_count"]
-    single = {k: v for k, v in tms.items() if k == "leaf_factor" or k.startswith("sparsify_l")}
-    dom = max(single, key=single.get)
-    dur_ms = tms[dom] / tcount[dom]
-    nleaf = ((N_SIDE + 1) // 16) ** 2
-    smhz = clocks.get("sm_mhz") or SM_MAX_MHZ
-    peak_tf = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
-    roof = None
-    if dom == "leaf_factor":
-        flops = nleaf * leaf_algorithmic_flops()
-        ach = flops / (dur_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach / peak_tf, "traffic": None, "kernel": "leaf_factor_kernel",
-                "launch_ms": dur_ms, "peak_note": "FP64 FMA: 152 SMs x 4 FLOP/clk x 2070 MHz (derived)"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": peak_tf, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "kernel": dom, "launch_ms": dur_ms}
-
-    phases = {k: round(v / args.steps, 4) for k, v in sorted(tms.items())}
     cpu = None
     if ws == 1 and not args.no_cpu:
         v, t, rel, cores = oracle_sample(args.cpu_n, NRHS)
         cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
                "sample": f"one {args.cpu_n}x{args.cpu_n} instance of the same family, {NRHS} RHS, "
                          f"factor + solve + GMRES to 1e-10 ({t:.1f} s)"}
+    st = head["st"]
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"diffusion {N_SIDE}x{N_SIDE} a=exp(GRF l=0.05 var=1), {NRHS} normal "
-                               f"RHS, eps_ID={EPS_ID}, plain FP64, GMRES to 1e-10",
-                   "N": N, "nrhs": NRHS, "precision": "fp64", "learned_ranks": False,
+                               f"RHS, mixed precision (FP32 factors and solve, FP64 leaf LU and "
+                               f"QR pivots/norms), eps_ID={args.mixed_eps}, GMRES (FP64 residual) "
+                               f"to 1e-10",
+                   "N": N, "nrhs": NRHS, "precision": "mixed", "eps_id": args.mixed_eps,
+                   "learned_ranks": False,
                    "l2": "256 MB flush between steps; factor working set > L2"},
-        "relres_max": max(rels), "gmres_iters": max(iters),
-        "clocks": clocks,
+        "relres_max": head["relres"], "gmres_iters": head["iters"],
+        "fp64_plain": {"value": base_value, "unit": "DOF/s", "ms_per_step": base["ms"] / args.steps,
+                       "eps_id": EPS_ID, "relres_max": base["relres"], "gmres_iters": base["iters"],
+                       "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(base["st"]["timing_ms"].items())},
+                       "roofline": _roofline(base["st"], args.steps)},
+        "speedup_vs_fp64": value / base_value,
+        "nd_build_s": nd_s,
+        "clocks": head["clocks"],
         "e2e": {"value": e2e_value, "unit": "DOF/s",
                 "h2d_bytes_per_step": int(A.data.nbytes + P.B.nbytes),
                 "d2h_bytes_per_step": int(P.B.nbytes), "relres_max": e2e_rel},
-        "gpu_launches": int(launches),
-        "roofline": roof,
-        "phase_ms_per_step": phases,
+        "gpu_launches": int(head["launches"]),
+        "roofline": _roofline(st, args.steps),
+        "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(st["timing_ms"].items())},
         "factor_stats": {"q_tilde": st["q_tilde"], "levels": st["levels"]},
         "cpu_baseline": cpu,
     }
@@ -333,6 +369,7 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=255, dest="cpu_n")
     ap.add_argument("--ref-n", type=int, default=127, dest="ref_n")
     ap.add_argument("--no-cpu", action="store_true", dest="no_cpu")
+    ap.add_argument("--mixed-eps", type=float, default=1e-6, dest="mixed_eps")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

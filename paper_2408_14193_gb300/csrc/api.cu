@@ -99,6 +99,7 @@ struct spalu_factor_s {
   GmresWork gw;
   std::vector<int> host_rowptr_cache;
   PhaseTimer timer;
+  int kumax = 30;            // upper bandwidth of the leaf U factors (read after each factor)
 };
 
 namespace {
@@ -337,7 +338,8 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   if (!(o->eps_id >= 0.0) || o->p_oversample < 0 || o->h0 < 1 || o->near_radius < 0 ||
       o->gmres_m < 1 || o->gmres_maxit < 0)
     return SPALU_ERR_ARG;
-  if (o->precision != 0) return SPALU_ERR_UNSUPPORTED;
+  if (o->precision != 0 && o->precision != 1) return SPALU_ERR_ARG;
+  if (leaf_init_tables() != cudaSuccess) return SPALU_ERR_CUDA;
   auto* f = new spalu_factor_s();
   f->nd = nd;
   f->o = *o;
@@ -365,9 +367,10 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     p.ldFp = ldF[l - 1];
     p.sepcap = p.vcut ? p.gp.h : p.gp.w;
     p.Ycap = 2 * 16 + std::max(o->h0, 2 * (p.capS + o->p_oversample));
-    size_t need = sparsify_smem_need(p.capS, o->symmetric, o->h0, o->p_oversample);
+    const int tb = o->precision == 1 ? 4 : 8;
+    size_t need = sparsify_smem_need(p.capS, o->symmetric, o->h0, o->p_oversample, tb);
     size_t lim = 160 * 1024;
-    size_t mn = sparsify_smem_min(p.capS, o->symmetric, o->h0, o->p_oversample);
+    size_t mn = sparsify_smem_min(p.capS, o->symmetric, o->h0, o->p_oversample, tb);
     p.spars_smem = std::min(need, std::max(lim, mn));
     p.spars_global = need > p.spars_smem;
   }
@@ -382,10 +385,16 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     const Geo& gl = nd->depth[L];
     LeafDev& lf = f->leaf;
     lf.nx = nd->nx; lf.ny = nd->ny; lf.L = L; lf.g = gl; lf.ldF = ldF[L];
-    lf.F = cv.take<double>((size_t)gl.nbox() * ldF[L] * ldF[L]);
-    lf.band = cv.take<double>((size_t)gl.nbox() * LDAB * NI);
+    const bool f32 = o->precision == 1;
+    auto real = [&](size_t n) -> void* { return f32 ? (void*)cv.take<float>(n) : (void*)cv.take<double>(n); };
+    lf.fp32 = f32 ? 1 : 0;
+    lf.F = real((size_t)gl.nbox() * ldF[L] * ldF[L]);
+    lf.band = real((size_t)gl.nbox() * LDAB * NI);
+    lf.invd = real((size_t)gl.nbox() * NI);
+    lf.ybuf = real((size_t)gl.nbox() * NI * 64);
     lf.piv = cv.take<int>((size_t)gl.nbox() * NI);
-    std::vector<double*> Fst(L + 1, nullptr);
+    lf.kumax = cv.take<int>(4);
+    std::vector<void*> Fst(L + 1, nullptr);
     Fst[L] = lf.F;
     for (int l = L; l >= 1; --l) {
       const LevelPlan& p = f->plan[l];
@@ -400,10 +409,13 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
       d.nodes = cv.take<int>((size_t)nseg * p.capS);
       d.perm = cv.take<int>((size_t)nseg * p.capS);
       d.piv = cv.take<int>((size_t)nseg * p.capS);
-      d.T = cv.take<double>((size_t)nseg * p.capS * p.capS);
-      d.Dm = cv.take<double>((size_t)nseg * p.capS * p.capS);
-      d.Yg = p.spars_global ? cv.take<double>((size_t)nseg * p.Ycap * p.capS) : nullptr;
-      Fst[l - 1] = cv.take<double>((size_t)p.gp.nbox() * p.ldFp * p.ldFp);
+      d.fp32 = f32 ? 1 : 0;
+      d.T = real((size_t)nseg * p.capS * p.capS);
+      d.Dm = real((size_t)nseg * p.capS * p.capS);
+      d.Dinv = real((size_t)nseg * p.capS);
+      d.Yg = p.spars_global ? real((size_t)nseg * p.Ycap * p.capS) : nullptr;
+      Fst[l - 1] = real((size_t)p.gp.nbox() * p.ldFp * p.ldFp);
+      d.Pinv = real((size_t)p.gp.nbox() * p.sepcap);
       d.F = Fst[l];
       d.Fp = Fst[l - 1];
       d.ptab = cv.take<int>((size_t)p.gp.nbox() * p.ldFp * 8);
@@ -439,6 +451,7 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   PhaseTimer& tm = f->timer;
   int t_all = tm.begin("factor", s);
   CUDA_TRY(cudaMemsetAsync(f->d_err, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(f->leaf.kumax, 0, sizeof(int), s));
   if (L >= 1) launch_level_init_L(f->lev[L], s);
   int t = tm.begin("leaf_factor", s);
   launch_leaf_factor(f->leaf, s);
@@ -454,6 +467,9 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());
   spalu_status st = read_err(f, s);
+  int ku = 30;
+  if (cudaMemcpy(&ku, f->leaf.kumax, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SPALU_ERR_CUDA;
+  f->kumax = ku;
   f->factored = (st == SPALU_OK);
   f->last_stream = s;
   return st;
@@ -499,10 +515,9 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
     CUDA_TRY(cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), B, (size_t)ld * sizeof(double),
                                (size_t)f->N * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
   int t = tm.begin("leaf_solve_fwd", s);
-  for (int c0 = 0; c0 < nrhs; c0 += 32) {
-    int nc = std::min(32, nrhs - c0);
-    launch_leaf_solve_fwd(f->leaf, X + (size_t)ld * c0, nc, ld, s);
-  }
+  launch_leaf_solve(f->leaf, X, nrhs, ld, 0, f->kumax, s);
+  tm.end(t, s);
+  t = tm.begin("sep_update", s);
   if (L >= 1) launch_sep_update_fwd(f->leaf, X, nrhs, ld, s);
   tm.end(t, s);
   t = tm.begin("level_solve", s);
@@ -510,10 +525,7 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
   for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], X, nrhs, ld, s);
   tm.end(t, s);
   t = tm.begin("leaf_solve_bwd", s);
-  for (int c0 = 0; c0 < nrhs; c0 += 32) {
-    int nc = std::min(32, nrhs - c0);
-    launch_leaf_solve_bwd(f->leaf, X + (size_t)ld * c0, nc, ld, nullptr, s);
-  }
+  launch_leaf_solve(f->leaf, X, nrhs, ld, 1, f->kumax, s);
   tm.end(t, s);
   tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());

@@ -1,14 +1,20 @@
 // Leaf-interior elimination (Sec. 4.3, first step: L_(L+1)^{-1} A U_(L+1)^{-1} = diag(I, A^(L)))
 // and the leaf part of the tree-ordered solve (Eq. (WV)).
 //
-// One CTA per leaf box.  The 225 x 225 interior block A_II is banded in the natural
-// in-leaf order (x fastest): lower and upper bandwidth 15.  Gaussian elimination with
-// partial pivoting (pivot = largest |a_ij| in the column, ties -> lowest row) is done in
-// LAPACK band storage (kl = ku = 15, 46 rows incl. the fill of the row interchanges),
-// which performs exactly the operations of dense partial-pivoting LU on the nonzeros.
-// The Schur complement S_b = A_dI A_II^{-1} A_Id onto the 60 side unknowns needs
-// A_II^{-1} only at the ring of interior nodes next to the sides, because every side
-// unknown couples to exactly one interior node; it is formed from 60 band solves.
+// The 225 x 225 interior block A_II of a 15 x 15 leaf is banded in the natural in-leaf order
+// (x fastest, lower and upper bandwidth 15).  Gaussian elimination with partial pivoting
+// (pivot = largest |a_ij| in the column, ties -> lowest row) runs in LAPACK band storage
+// (kl = ku = 15, 46 rows incl. the fill of the row interchanges) in FP64: it performs exactly
+// the operations of dense partial-pivoting LU on the nonzeros.  The Schur complement
+// S_b = A_dI A_II^{-1} A_Id onto the 60 side unknowns needs A_II^{-1} only at the ring of
+// interior nodes next to the sides (every side unknown couples to one interior node), so it
+// comes from 60 solves with unit right-hand sides.
+//
+// GB300 mapping: FP64 runs at 2 FMA per clock per SM, so every FP64 warp instruction must
+// carry 32 useful lanes.  The solves therefore give one thread to one (leaf, right-hand side)
+// column and sweep the band with a register window (the interchanges stay inside it); the
+// reciprocal pivots are stored once, and the upper sweep runs at the bandwidth the
+// interchanges actually produced (15 when there were none).
 #include <cstdio>
 
 #include "spalu_internal.h"
@@ -18,12 +24,13 @@ namespace {
 
 constexpr int KV = KL + KU;   // row of the diagonal in band storage
 constexpr int NQ = 4 * LEAF;  // side unknowns of a leaf
-constexpr int RHS_CHUNK = 16; // right-hand sides per pass of the Schur solves
+constexpr int LPC = 2;        // leaves per CTA of the factor kernel
+constexpr int FTH = 128;      // threads of the factor kernel (64 per leaf)
+constexpr int QL = 64;        // column slots per leaf in the sweep buffer (60 used by the factor)
 
 __device__ __forceinline__ double& ab(double* AB, int i, int j) { return AB[(KV + i - j) + LDAB * j]; }
 
-// Position of grid node (vx, vy) in the frontal layout of the leaf box at (x0, y0), or -1.
-__device__ int leaf_frontal_pos(int vx, int vy, int x0, int y0) {
+__device__ __forceinline__ int leaf_frontal_pos(int vx, int vy, int x0, int y0) {
   const int w = LEAF;
   if (vy == y0 - 1 && vx >= x0 && vx < x0 + w) return vx - x0;                  // bottom
   if (vy == y0 + w && vx >= x0 && vx < x0 + w) return w + vx - x0;              // top
@@ -36,9 +43,9 @@ __device__ int leaf_frontal_pos(int vx, int vy, int x0, int y0) {
   return -1;
 }
 
-// side unknown q (0..59, sides BOTTOM, TOP, LEFT, RIGHT of 15 each): its grid node and
-// the local index of its single interior neighbour.
-__device__ void side_unknown(int q, int x0, int y0, int* vx, int* vy, int* m) {
+// side unknown q (0..59: BOTTOM, TOP, LEFT, RIGHT, 15 each): grid node and the local index of
+// its interior neighbour
+__device__ __forceinline__ void side_unknown(int q, int x0, int y0, int* vx, int* vy, int* m) {
   int s = q / LEAF, t = q % LEAF;
   switch (s) {
     case SIDE_BOTTOM: *vx = x0 + t; *vy = y0 - 1; *m = t; break;
@@ -48,175 +55,238 @@ __device__ void side_unknown(int q, int x0, int y0, int* vx, int* vy, int* m) {
   }
 }
 
-__device__ double csr_entry(const int* rowptr, const int* colind, const double* val, int r, int c) {
+__device__ __forceinline__ double csr_entry(const int* rowptr, const int* colind, const double* val, int r, int c) {
   for (int p = rowptr[r]; p < rowptr[r + 1]; ++p)
     if (colind[p] == c) return val[p];
   return 0.0;
 }
 
-// Band GEPP (the dgbtf2 sequence) by the whole CTA; multipliers stay in their column.
-__device__ bool band_gepp(double* AB, int* piv, int* sh_int) {
-  int ju = 0;
-  bool ok = true;
+// side unknowns ordered by the position of their interior neighbour (so that the solves of
+// one warp can start late: L^{-1} P e_m vanishes above row m - 15)
+__constant__ int c_qorder[NQ];
+__constant__ int c_qstart[2];   // first sweep step of the two solve warps of a leaf
+
+template <typename T>
+struct Band {                   // read-only view of one leaf's factors in precision T
+  const T* ab;                  // LDAB x NI
+  const int* piv;
+  const T* invd;
+  __device__ __forceinline__ T l(int r, int j) const { return ab[(KV + r) + LDAB * j]; }   // L(j+r, j)
+  __device__ __forceinline__ T u(int r, int j) const { return ab[(KV - r) + LDAB * j]; }   // U(j-r, j)
+};
+
+// Forward sweep y = L^{-1} P x for one column held by this thread.  in(j) gives x_j,
+// out(j, y) receives y_j for j = j0..NI-1 (x_j = 0 for j < j0 is assumed).
+template <typename T, class In, class Out>
+__device__ __forceinline__ void sweep_L(const Band<T>& B, int j0, In in, Out out) {
+  T W[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) W[r] = (j0 + r < NI) ? in(j0 + r) : T(0);
+  for (int t0 = 0; j0 + t0 < NI; t0 += 16) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int j = j0 + t0 + u;
+      if (j < NI) {
+        const int dsw = B.piv[j] - j;   // 0..15: the interchange stays in the window
+        T a = W[u], b = a;
+#pragma unroll
+        for (int r = 1; r < 16; ++r)
+          if (r == dsw) { b = W[(u + r) & 15]; W[(u + r) & 15] = a; }
+        W[u] = b;
+#pragma unroll
+        for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= B.l(r, j) * b;
+        out(j, b);
+        W[u] = (j + 16 < NI) ? in(j + 16) : T(0);
+      }
+    }
+  }
+}
+
+// Backward sweep x = U^{-1} y (upper bandwidth < KUW) for one column: in(j) gives y_j,
+// out(j, x) receives x_j for j = NI-1 .. 0.
+template <typename T, int KUW, class In, class Out>
+__device__ __forceinline__ void sweep_U(const Band<T>& B, In in, Out out) {
+  T V[KUW];
+#pragma unroll
+  for (int r = 0; r < KUW; ++r) V[r] = (NI - 1 - r >= 0) ? in(NI - 1 - r) : T(0);
+  constexpr int RMAX = KUW - 1 < KV ? KUW - 1 : KV;
+  for (int t0 = 0; t0 < NI; t0 += KUW) {
+#pragma unroll
+    for (int u = 0; u < KUW; ++u) {
+      const int t = t0 + u;
+      if (t < NI) {
+        const int j = NI - 1 - t;
+        const T x = V[u] * B.invd[j];
+        out(j, x);
+#pragma unroll
+        for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= B.u(r, j) * x;
+        V[u] = (j - KUW >= 0) ? in(j - KUW) : T(0);
+      }
+    }
+  }
+}
+
+// Band GEPP (the dgbtf2 sequence) of one leaf by a group of 64 threads (tid 0..63); all
+// threads of the CTA execute the same barriers.  Returns the upper bandwidth reached.
+__device__ int band_gepp_pair(double* AB, int* piv, int tid, volatile int* sh, bool& ok) {
+  int ju = 0, kureach = KU;
+  const int lane = tid & 31;
   for (int j = 0; j < NI; ++j) {
     const int km = min(KL, NI - 1 - j);
-    if (threadIdx.x < 32) {                       // pivot search: warp 0
+    if (tid < 32) {
       double best = -1.0;
       int bi = 0;
-      for (int r = threadIdx.x; r <= km; r += 32) {
-        double v = fabs(ab(AB, j + r, j));
-        if (v > best) { best = v; bi = r; }
-      }
+      if (lane <= km) { best = fabs(ab(AB, j + lane, j)); bi = lane; }
       for (int o = 16; o > 0; o >>= 1) {
         double ob = __shfl_down_sync(0xffffffffu, best, o);
         int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (threadIdx.x == 0) {
-        sh_int[0] = bi;
+      if (lane == 0) {
+        sh[0] = bi;
+        sh[1] = (best == 0.0) ? 1 : 0;
         piv[j] = j + bi;
-        sh_int[1] = (best == 0.0) ? 1 : 0;
       }
     }
     __syncthreads();
-    const int jp = sh_int[0];
-    if (sh_int[1]) { ok = false; __syncthreads(); continue; }
-    ju = max(ju, min(j + KU + jp, NI - 1));
-    if (jp != 0) {
-      for (int c = j + threadIdx.x; c <= ju; c += blockDim.x) {
+    const int jp = sh[0];
+    const bool zero = sh[1] != 0;
+    if (zero) ok = false;
+    const int juj = min(j + KU + jp, NI - 1);
+    ju = max(ju, juj);
+    kureach = max(kureach, ju - j);
+    if (!zero && jp != 0) {
+      for (int c = j + tid; c <= ju; c += 64) {
         double a = ab(AB, j, c), b = ab(AB, j + jp, c);
         ab(AB, j, c) = b;
         ab(AB, j + jp, c) = a;
       }
-      __syncthreads();
-    }
-    const double piv_v = ab(AB, j, j);
-    for (int r = 1 + threadIdx.x; r <= km; r += blockDim.x) ab(AB, j + r, j) /= piv_v;
-    __syncthreads();
-    // rank-1 update of rows j+1..j+km, columns j+1..ju
-    const int ncol = ju - j;
-    for (int e = threadIdx.x; e < km * ncol; e += blockDim.x) {
-      int r = 1 + e % km, c = j + 1 + e / km;
-      ab(AB, j + r, c) -= ab(AB, j + r, j) * ab(AB, j, c);
     }
     __syncthreads();
-  }
-  return ok;
-}
-
-// Solve with the band LU for ncol columns X (ld NI), one warp per column.
-__device__ void band_solve_cols(const double* AB, const int* piv, double* X, int ncol) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int q = warp; q < ncol; q += nw) {
-    double* x = X + (size_t)q * NI;
-    for (int j = 0; j < NI; ++j) {                 // L: interchanges then unit lower
-      int p = piv[j];
-      if (p != j) {
-        __syncwarp();
-        if (lane == 0) { double t = x[j]; x[j] = x[p]; x[p] = t; }
+    if (!zero) {
+      const double pv = ab(AB, j, j);
+      if (tid < km) ab(AB, j + 1 + tid, j) /= pv;
+    }
+    __syncthreads();
+    if (!zero) {
+      const int ncol = ju - j;
+      for (int e = tid; e < km * ncol; e += 64) {
+        int r = 1 + e % km, c = j + 1 + e / km;
+        ab(AB, j + r, c) -= ab(AB, j + r, j) * ab(AB, j, c);
       }
-      __syncwarp();
-      double xj = x[j];
-      int km = min(KL, NI - 1 - j);
-      if (lane < km) x[j + 1 + lane] -= ab(const_cast<double*>(AB), j + 1 + lane, j) * xj;
     }
-    __syncwarp();
-    for (int j = NI - 1; j >= 0; --j) {            // U: upper bandwidth KL+KU
-      __syncwarp();
-      double xj = x[j] / ab(const_cast<double*>(AB), j, j);
-      __syncwarp();
-      if (lane == 0) x[j] = xj;
-      int i0 = max(0, j - KV);
-      for (int i = i0 + lane; i < j; i += 32) x[i] -= ab(const_cast<double*>(AB), i, j) * xj;
-    }
-    __syncwarp();
+    __syncthreads();
   }
+  return min(kureach, KV);
 }
 
-__global__ void __launch_bounds__(256) leaf_factor_kernel(LeafDev d) {
+template <typename T>
+__global__ void __launch_bounds__(FTH) leaf_factor_kernel(LeafDev d) {
   extern __shared__ double sm[];
-  double* AB = sm;                                   // LDAB * NI
-  double* X = AB + LDAB * NI;                        // NI * RHS_CHUNK
-  double* qa = X + NI * RHS_CHUNK;                   // NQ: A[q, m_q]
-  double* qc = qa + NQ;                              // NQ: A[m_q, q]
-  int* piv = reinterpret_cast<int*>(qc + NQ);        // NI
-  int* qm = piv + NI;                                // NQ: interior neighbour (local index)
-  int* qex = qm + NQ;                                // NQ: side exists
-  int* sh_int = qex + NQ;                            // scratch
-
-  const int b = blockIdx.x;
+  __shared__ int shv[LPC][4];
+  __shared__ double qa[LPC][NQ], qc[LPC][NQ];
+  __shared__ int qm[LPC][NQ], qex[LPC][NQ];
+  const int sub = threadIdx.x / 64;                 // which leaf of the pair
+  const int tid = threadIdx.x % 64;
+  const int b = blockIdx.x * LPC + sub;
+  const int nbox = d.g.nbox();
+  const bool live = b < nbox;
+  double* AB = sm + (size_t)sub * LDAB * NI;
+  int* piv = reinterpret_cast<int*>(sm + (size_t)LPC * LDAB * NI) + sub * NI;
   const Geo g = d.g;
-  const int I = b % g.bx, J = b / g.bx;
+  const int I = live ? b % g.bx : 0, J = live ? b / g.bx : 0;
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
-  double* F = d.F + (size_t)b * d.ldF * d.ldF;
+  T* F = reinterpret_cast<T*>(d.F) + (size_t)(live ? b : 0) * d.ldF * d.ldF;
   const int D = g.D();
 
-  for (int i = threadIdx.x; i < LDAB * NI; i += blockDim.x) AB[i] = 0.0;
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x) F[(e % D) + (size_t)d.ldF * (e / D)] = 0.0;
+  for (int i = tid; i < LDAB * NI; i += 64) AB[i] = 0.0;
+  if (live)
+    for (int e = tid; e < D * D; e += 64) F[(e % D) + (size_t)d.ldF * (e / D)] = T(0);
   __syncthreads();
-  for (int i = threadIdx.x; i < NI; i += blockDim.x) {
-    int row = (x0 + i % LEAF) + nx * (y0 + i / LEAF);
-    for (int p = d.rowptr[row]; p < d.rowptr[row + 1]; ++p) {
-      int c = d.colind[p];
-      int cx = c % nx - x0, cy = c / nx - y0;
-      if (cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF) ab(AB, i, cx + LEAF * cy) += d.val[p];
+  if (live) {
+    for (int i = tid; i < NI; i += 64) {
+      int row = (x0 + i % LEAF) + nx * (y0 + i / LEAF);
+      for (int p = d.rowptr[row]; p < d.rowptr[row + 1]; ++p) {
+        int c = d.colind[p];
+        int cx = c % nx - x0, cy = c / nx - y0;
+        if (cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF) ab(AB, i, cx + LEAF * cy) += d.val[p];
+      }
     }
-  }
-  for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
-    int vx, vy, m;
-    side_unknown(q, x0, y0, &vx, &vy, &m);
-    bool exists = vx >= 0 && vx < nx && vy >= 0 && vy < d.ny;
-    qm[q] = m;
-    qex[q] = exists ? 1 : 0;
-    double a = 0.0, c = 0.0;
-    if (exists) {
-      int node = vx + nx * vy;
-      int mnode = (x0 + m % LEAF) + nx * (y0 + m / LEAF);
-      a = csr_entry(d.rowptr, d.colind, d.val, node, mnode);
-      c = csr_entry(d.rowptr, d.colind, d.val, mnode, node);
+    for (int q = tid; q < NQ; q += 64) {
+      int vx, vy, m;
+      side_unknown(q, x0, y0, &vx, &vy, &m);
+      bool exists = vx >= 0 && vx < nx && vy >= 0 && vy < d.ny;
+      qm[sub][q] = m;
+      qex[sub][q] = exists ? 1 : 0;
+      double a = 0.0, c = 0.0;
+      if (exists) {
+        int node = vx + nx * vy;
+        int mnode = (x0 + m % LEAF) + nx * (y0 + m / LEAF);
+        a = csr_entry(d.rowptr, d.colind, d.val, node, mnode);
+        c = csr_entry(d.rowptr, d.colind, d.val, mnode, node);
+      }
+      qa[sub][q] = a;
+      qc[sub][q] = c;
     }
-    qa[q] = a;
-    qc[q] = c;
+  } else {
+    // an empty leaf slot: a unit diagonal keeps the shared elimination finite
+    for (int i = tid; i < NI; i += 64) ab(AB, i, i) = 1.0;
   }
   __syncthreads();
 
-  const bool ok = band_gepp(AB, piv, sh_int);
-  if (!ok && threadIdx.x == 0) atomicOr(d.err, ERR_SINGULAR);
+  bool ok = true;
+  const int kureach = band_gepp_pair(AB, piv, tid, shv[sub], ok);
+  if (live && !ok && tid == 0) atomicOr(d.err, ERR_SINGULAR);
 
-  // F[i][q] = -A[i, m_i] (A_II^{-1})[m_i, m_q] A[m_q, q]: the Schur complement S_b
-  for (int q0 = 0; q0 < NQ; q0 += RHS_CHUNK) {
-    const int nc = min(RHS_CHUNK, NQ - q0);
-    for (int e = threadIdx.x; e < NI * nc; e += blockDim.x) X[e] = 0.0;
-    __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += blockDim.x)
-      if (qex[q0 + c]) X[(size_t)c * NI + qm[q0 + c]] = qc[q0 + c];
-    __syncthreads();
-    if (ok) band_solve_cols(AB, piv, X, nc);
-    __syncthreads();
-    for (int e = threadIdx.x; e < NQ * nc; e += blockDim.x) {
-      int i = e % NQ, c = e / NQ;
-      if (qex[i] && qex[q0 + c]) F[i + (size_t)d.ldF * (q0 + c)] = -qa[i] * X[(size_t)c * NI + qm[i]];
+  // factors kept for the solve, in precision T, plus the reciprocal pivots
+  T* bandg = reinterpret_cast<T*>(d.band) + (size_t)(live ? b : 0) * LDAB * NI;
+  T* invg = reinterpret_cast<T*>(d.invd) + (size_t)(live ? b : 0) * NI;
+  if (live) {
+    for (int i = tid; i < LDAB * NI; i += 64) bandg[i] = (T)AB[i];
+    for (int i = tid; i < NI; i += 64) {
+      d.piv[(size_t)b * NI + i] = piv[i];
+      invg[i] = (T)(1.0 / ab(AB, i, i));
     }
-    __syncthreads();
+    if (tid == 0) atomicMax(d.kumax, kureach);
   }
+  __syncthreads();
+  const bool active = live && ok;     // no early exit: every thread reaches every barrier
 
+  // Schur complement: one thread per side unknown q (lanes sorted by interior neighbour)
+  if (active && tid < NQ) {
+    const int q = c_qorder[tid];
+    const int j0 = c_qstart[tid >> 5];
+    Band<T> Bd{bandg, d.piv + (size_t)b * NI, invg};
+    T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
+    const int mq = qm[sub][q];
+    const T cq = qex[sub][q] ? (T)qc[sub][q] : T(0);
+    sweep_L<T>(Bd, j0, [&](int j) { return j == mq ? cq : T(0); },
+               [&](int j, T y) { yb[(size_t)j * QL + tid] = y; });
+    const size_t ldF = d.ldF;
+    auto yin = [&](int j) { return j < j0 ? T(0) : yb[(size_t)j * QL + tid]; };
+    auto ring_out = [&](int j, T x) {
+      const int lx = j % LEAF, ly = j / LEAF;
+      if (ly == 0 && qex[sub][lx]) F[lx + ldF * q] = -(T)qa[sub][lx] * x;
+      if (ly == LEAF - 1 && qex[sub][LEAF + lx]) F[(LEAF + lx) + ldF * q] = -(T)qa[sub][LEAF + lx] * x;
+      if (lx == 0 && qex[sub][2 * LEAF + ly]) F[(2 * LEAF + ly) + ldF * q] = -(T)qa[sub][2 * LEAF + ly] * x;
+      if (lx == LEAF - 1 && qex[sub][3 * LEAF + ly]) F[(3 * LEAF + ly) + ldF * q] = -(T)qa[sub][3 * LEAF + ly] * x;
+    };
+    if (kureach <= 15) sweep_U<T, 16>(Bd, yin, ring_out);   // no interchange widened U
+    else sweep_U<T, 32>(Bd, yin, ring_out);
+  }
+  __syncthreads();
   // original couplings owned by this box: its TOP and RIGHT sides (it is their lower /
   // left box) with their end junctions, and the diagonal of its BL junction.
-  //   task 0..14  : TOP side row      -> TOP, TL, TR
-  //   task 15..29 : RIGHT side row    -> RIGHT, BR, TR
-  //   task 30     : TL junction row   -> TOP
-  //   task 31     : TR junction row   -> TOP, RIGHT
-  //   task 32     : BR junction row   -> RIGHT
-  //   task 33     : BL junction row   -> BL
-  const int tk = threadIdx.x;
-  if (tk < 2 * LEAF + 4) {
+  //   task 0..14 TOP row -> TOP, TL, TR   15..29 RIGHT row -> RIGHT, BR, TR
+  //   30 TL row -> TOP   31 TR row -> TOP, RIGHT   32 BR row -> RIGHT   33 BL row -> BL
+  if (active && tid < 2 * LEAF + 4) {
     int vx, vy;
-    if (tk < LEAF) { vx = x0 + tk; vy = y0 + LEAF; }
-    else if (tk < 2 * LEAF) { vx = x0 + LEAF; vy = y0 + tk - LEAF; }
-    else if (tk == 30) { vx = x0 - 1; vy = y0 + LEAF; }
-    else if (tk == 31) { vx = x0 + LEAF; vy = y0 + LEAF; }
-    else if (tk == 32) { vx = x0 + LEAF; vy = y0 - 1; }
+    if (tid < LEAF) { vx = x0 + tid; vy = y0 + LEAF; }
+    else if (tid < 2 * LEAF) { vx = x0 + LEAF; vy = y0 + tid - LEAF; }
+    else if (tid == 30) { vx = x0 - 1; vy = y0 + LEAF; }
+    else if (tid == 31) { vx = x0 + LEAF; vy = y0 + LEAF; }
+    else if (tid == 32) { vx = x0 + LEAF; vy = y0 - 1; }
     else { vx = x0 - 1; vy = y0 - 1; }
     if (vx >= 0 && vx < nx && vy >= 0 && vy < d.ny) {
       const int row = vx + nx * vy;
@@ -228,62 +298,58 @@ __global__ void __launch_bounds__(256) leaf_factor_kernel(LeafDev d) {
         const bool on_top = pj >= LEAF && pj < 2 * LEAF;
         const bool on_right = pj >= 3 * LEAF && pj < 4 * LEAF;
         bool take;
-        if (tk < LEAF) take = on_top || pj == 4 * LEAF + C_TL || pj == 4 * LEAF + C_TR;
-        else if (tk < 2 * LEAF) take = on_right || pj == 4 * LEAF + C_BR || pj == 4 * LEAF + C_TR;
-        else if (tk == 30) take = on_top;
-        else if (tk == 31) take = on_top || on_right;
-        else if (tk == 32) take = on_right;
+        if (tid < LEAF) take = on_top || pj == 4 * LEAF + C_TL || pj == 4 * LEAF + C_TR;
+        else if (tid < 2 * LEAF) take = on_right || pj == 4 * LEAF + C_BR || pj == 4 * LEAF + C_TR;
+        else if (tid == 30) take = on_top;
+        else if (tid == 31) take = on_top || on_right;
+        else if (tid == 32) take = on_right;
         else take = (pj == pi);
-        if (take) F[pi + (size_t)d.ldF * pj] += d.val[p];
+        if (take) F[pi + (size_t)d.ldF * pj] += (T)d.val[p];
       }
     }
   }
-  // keep the band LU and pivots for the solve
-  double* band = d.band + (size_t)b * LDAB * NI;
-  for (int i = threadIdx.x; i < LDAB * NI; i += blockDim.x) band[i] = AB[i];
-  for (int i = threadIdx.x; i < NI; i += blockDim.x) d.piv[(size_t)b * NI + i] = piv[i];
 }
 
 // ---------------------------------------------------------------- solve
-// Forward (leaf part of W~): t = A_II^{-1} b_I stored in X[I]; the side unknowns are
-// updated afterwards by sep_update_fwd_kernel (b_d -= A_dI t).
-__global__ void leaf_solve_kernel(LeafDev d, double* X, int nrhs, int ld, int bwd, const double* tmp) {
-  extern __shared__ double sm[];
-  double* AB = sm;
-  double* x = AB + LDAB * NI;         // NI * nrhs
-  int* piv = reinterpret_cast<int*>(x + (size_t)NI * nrhs);
-  const int b = blockIdx.x;
+// One thread per (leaf, right-hand side).  Forward (leaf part of W~): X[I] <- A_II^{-1} X[I];
+// the side unknowns are updated afterwards by sep_update_fwd_kernel.  Backward (leaf part of
+// V~): X[I] <- X[I] - A_II^{-1} (A_Id x_d).  The intermediate L^{-1} P b goes through ybuf.
+template <typename T, int KUW>
+__global__ void __launch_bounds__(128) leaf_solve_kernel(LeafDev d, double* X, int nrhs, int ld, int bwd) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nbox = d.g.nbox();
+  if (gid >= (long long)nbox * nrhs) return;
+  const int b = (int)(gid / nrhs), c = (int)(gid % nrhs);
   const int I = b % d.g.bx, J = b / d.g.bx;
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
-  const double* band = d.band + (size_t)b * LDAB * NI;
-  for (int i = threadIdx.x; i < LDAB * NI; i += blockDim.x) AB[i] = band[i];
-  for (int i = threadIdx.x; i < NI; i += blockDim.x) piv[i] = d.piv[(size_t)b * NI + i];
-  for (int e = threadIdx.x; e < NI * nrhs; e += blockDim.x) {
-    int i = e % NI, c = e / NI;
-    int node = (x0 + i % LEAF) + nx * (y0 + i / LEAF);
-    double v;
-    if (!bwd) {
-      v = X[node + (size_t)ld * c];
-    } else {
-      // b_I <- A_Id x_d  (couplings to side unknowns)
-      v = 0.0;
-      for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
-        int cc = d.colind[p];
-        int cx = cc % nx - x0, cy = cc / nx - y0;
-        if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += d.val[p] * X[cc + (size_t)ld * c];
+  Band<T> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
+             reinterpret_cast<const T*>(d.invd) + (size_t)b * NI};
+  T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
+  double* Xc = X + (size_t)ld * c;
+  auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
+  if (!bwd) {
+    sweep_L<T>(Bd, 0, [&](int j) { return (T)Xc[node_of(j)]; },
+               [&](int j, T y) { yb[(size_t)j * QL + c] = y; });
+    sweep_U<T, KUW>(Bd, [&](int j) { return yb[(size_t)j * QL + c]; },
+                    [&](int j, T x) { Xc[node_of(j)] = (double)x; });
+  } else {
+    auto coupling = [&](int j) {
+      const int node = node_of(j);
+      T v = T(0);
+      const int lx = j % LEAF, ly = j / LEAF;
+      if (lx == 0 || ly == 0 || lx == LEAF - 1 || ly == LEAF - 1) {
+        for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
+          const int cc = d.colind[p];
+          const int cx = cc % nx - x0, cy = cc / nx - y0;
+          if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)(d.val[p] * Xc[cc]);
+        }
       }
-    }
-    x[e] = v;
-  }
-  __syncthreads();
-  band_solve_cols(AB, piv, x, nrhs);
-  __syncthreads();
-  for (int e = threadIdx.x; e < NI * nrhs; e += blockDim.x) {
-    int i = e % NI, c = e / NI;
-    int node = (x0 + i % LEAF) + nx * (y0 + i / LEAF);
-    if (!bwd) X[node + (size_t)ld * c] = x[e];
-    else X[node + (size_t)ld * c] -= x[e];         // x_I = t - A_II^{-1} A_Id x_d
+      return v;
+    };
+    sweep_L<T>(Bd, 0, coupling, [&](int j, T y) { yb[(size_t)j * QL + c] = y; });
+    sweep_U<T, KUW>(Bd, [&](int j) { return yb[(size_t)j * QL + c]; },
+                    [&](int j, T x) { Xc[node_of(j)] -= (double)x; });
   }
 }
 
@@ -308,28 +374,69 @@ __global__ void sep_update_fwd_kernel(LeafDev d, double* X, int nrhs, int ld) {
   }
 }
 
+// side unknowns sorted by the in-leaf index of their interior neighbour, and the first
+// sweep step of each of the two warps that solve for them
+void qorder_tables(int* ord, int* start) {
+  int m[NQ];
+  for (int q = 0; q < NQ; ++q) {
+    int s = q / LEAF, t = q % LEAF;
+    m[q] = s == SIDE_BOTTOM ? t : s == SIDE_TOP ? t + LEAF * (LEAF - 1) : s == SIDE_LEFT ? LEAF * t : LEAF * t + LEAF - 1;
+    ord[q] = q;
+  }
+  for (int a = 1; a < NQ; ++a)
+    for (int b2 = a; b2 > 0 && (m[ord[b2]] < m[ord[b2 - 1]] || (m[ord[b2]] == m[ord[b2 - 1]] && ord[b2] < ord[b2 - 1])); --b2) {
+      int t = ord[b2]; ord[b2] = ord[b2 - 1]; ord[b2 - 1] = t;
+    }
+  for (int w = 0; w < 2; ++w) {
+    int mn = NI;
+    for (int l = 32 * w; l < 32 * w + 32 && l < NQ; ++l) mn = m[ord[l]] < mn ? m[ord[l]] : mn;
+    start[w] = mn - KL > 0 ? mn - KL : 0;
+  }
+}
+
 }  // namespace
 
-static size_t leaf_factor_smem() {
-  return sizeof(double) * (LDAB * NI + NI * RHS_CHUNK + 2 * NQ) + sizeof(int) * (NI + 2 * NQ + 8);
+size_t leaf_factor_smem() {
+  return sizeof(double) * (size_t)LPC * LDAB * NI + sizeof(int) * (LPC * NI + 2);
+}
+
+cudaError_t leaf_init_tables() {
+  int ord[NQ], start[2];
+  qorder_tables(ord, start);
+  cudaError_t e = cudaMemcpyToSymbol(c_qorder, ord, sizeof(ord));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_qstart, start, sizeof(start));
+  return e;
 }
 
 void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
   size_t smem = leaf_factor_smem();
-  cudaFuncSetAttribute(leaf_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  note_launch();
-  leaf_factor_kernel<<<d.g.nbox(), 256, smem, s>>>(d);
+  int grid = (d.g.nbox() + LPC - 1) / LPC;
+  if (d.fp32) {
+    cudaFuncSetAttribute(leaf_factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    leaf_factor_kernel<float><<<grid, FTH, smem, s>>>(d);
+  } else {
+    cudaFuncSetAttribute(leaf_factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    leaf_factor_kernel<double><<<grid, FTH, smem, s>>>(d);
+  }
 }
 
-static size_t leaf_solve_smem(int nrhs) {
-  return sizeof(double) * (LDAB * NI + (size_t)NI * nrhs) + sizeof(int) * NI;
+template <typename T>
+static void leaf_solve_launch(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s) {
+  long long n = (long long)d.g.nbox() * nrhs;
+  int grid = (int)((n + 127) / 128);
+  note_launch();
+  if (kumax <= 15) leaf_solve_kernel<T, 16><<<grid, 128, 0, s>>>(d, X, nrhs, ld, bwd);
+  else leaf_solve_kernel<T, 32><<<grid, 128, 0, s>>>(d, X, nrhs, ld, bwd);
 }
 
-void launch_leaf_solve_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
-  size_t smem = leaf_solve_smem(nrhs);
-  cudaFuncSetAttribute(leaf_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  note_launch();
-  leaf_solve_kernel<<<d.g.nbox(), 256, smem, s>>>(d, X, nrhs, ld, 0, nullptr);
+void launch_leaf_solve(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s) {
+  for (int c0 = 0; c0 < nrhs; c0 += QL) {
+    int nc = nrhs - c0 < QL ? nrhs - c0 : QL;
+    if (d.fp32) leaf_solve_launch<float>(d, X + (size_t)ld * c0, nc, ld, bwd, kumax, s);
+    else leaf_solve_launch<double>(d, X + (size_t)ld * c0, nc, ld, bwd, kumax, s);
+  }
 }
 
 void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
@@ -339,13 +446,6 @@ void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaSt
   if (blocks < 1) blocks = 1;
   note_launch();
   sep_update_fwd_kernel<<<blocks, 256, 0, s>>>(d, X, nrhs, ld);
-}
-
-void launch_leaf_solve_bwd(const LeafDev& d, double* X, int nrhs, int ld, double* tmp, cudaStream_t s) {
-  size_t smem = leaf_solve_smem(nrhs);
-  cudaFuncSetAttribute(leaf_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  note_launch();
-  leaf_solve_kernel<<<d.g.nbox(), 256, smem, s>>>(d, X, nrhs, ld, 1, tmp);
 }
 
 }  // namespace spalu

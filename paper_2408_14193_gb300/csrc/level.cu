@@ -15,6 +15,12 @@
 // The neighbour couplings of a remainder are dropped (they are O(eps) after the
 // transform), and the couplings between skeletons are unchanged by the transforms, so only
 // the segment's own diagonal block is transformed.
+//
+// Every kernel is templated on the working precision T (double; float in mixed mode).
+// Column norms, pivots and the truncation test of the column-pivoted QR stay in FP64.
+// GB300 runs FP64 at 2 FMA per clock per SM, so per-column scalars (Householder coefficients,
+// norm downdates) are computed once for 32 columns at a time (one lane per column) and
+// divisions are replaced by stored reciprocals.
 #include <cfloat>
 #include <cmath>
 
@@ -26,6 +32,7 @@ namespace {
 constexpr int NEAR_MAX = 16;      // near unknowns per segment (the geometry gives <= 10)
 constexpr int RUN_MAX = 16;
 constexpr int SK_CHUNK = 16;      // far unknowns per chunk of the sketch product
+constexpr int NW = 8;             // warps per CTA of the sparsify kernel
 constexpr double TIE_RTOL = 1e-12;
 
 // ------------------------------------------------------------ Philox4x32-10 (SC'11)
@@ -146,11 +153,12 @@ __device__ __forceinline__ int cheb(const SegCtx& S, int node, int nx) {
   return max(da, db);
 }
 
-// B entry for neighbour f (run r, element i), half t (0: A[v, s_c], 1: A[s_c, v]), column c
-__device__ __forceinline__ double bval(const LevelDev& d, const SegCtx& S, const double* F1,
-                                       const double* F2, const Run& R, int i, int t, int c) {
+// B entry for neighbour (run R, element i), half t (0: A[v, s_c], 1: A[s_c, v]), column c
+template <typename T>
+__device__ __forceinline__ T bval(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2,
+                                  const Run& R, int i, int t, int c) {
   const size_t ld = d.ldF;
-  double v = 0.0;
+  T v = T(0);
   if (R.p1 >= 0) {
     int p = R.p1 + i;
     v += t == 0 ? F1[p + ld * (S.s1 + c)] : F1[(S.s1 + c) + ld * p];
@@ -162,38 +170,29 @@ __device__ __forceinline__ double bval(const LevelDev& d, const SegCtx& S, const
   return v;
 }
 
-// ------------------------------------------------------------ block reductions
-__device__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    double s = lane < nw ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red[32] = s;
-  }
-  __syncthreads();
-  double r = red[32];
-  __syncthreads();
-  return r;
-}
+// non-negative doubles order like their bit patterns
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 // ------------------------------------------------------------ column-pivoted QR
-// Businger-Golub Householder QR with column pivoting of Y (m x e, ld ldy), stopped at the
-// first step i with |R_ii| <= eps |R_00|.  perm receives the column order; on exit the
-// first k rows of Y hold [R_1 R_2] in the permuted order.  Returns k.
-__device__ int block_cpqr(double* Y, int ldy, int m, int e, double eps, int* perm, double* vn1,
-                          double* vn2, double* red, int* shi) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Businger-Golub Householder QR with column pivoting of Y (m x e, ld ldy, precision T),
+// stopped at the first step i with |R_ii| <= eps |R_00|.  Norms, pivot choice and the
+// truncation test in FP64; Householder products in T.  perm receives the column order; on
+// exit the first k rows of Y hold [R_1 R_2] in the permuted order.  Returns k.
+// sh: >= NW*32 + 3*64 doubles of shared scratch; flags: >= e ints.
+template <typename T>
+__device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1,
+                          double* vn2, double* sh, int* flags, int* shi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* part = sh;                    // [NW][32] partial dots
+  T* coef = reinterpret_cast<T*>(sh + NW * 32);   // [64]
+  double* scal = sh + NW * 32 + 64;     // alpha, v0, c2, normx
   for (int j = threadIdx.x; j < e; j += blockDim.x) perm[j] = j;
   if (m == 0 || e == 0) { __syncthreads(); return 0; }
-  // initial column norms (one warp per column)
-  for (int j = warp; j < e; j += nw) {
+  // initial column norms (one warp per column, FP64 accumulation)
+  for (int j = warp; j < e; j += NW) {
     double s = 0.0;
-    for (int r = lane; r < m; r += 32) { double v = Y[r + (size_t)ldy * j]; s += v * v; }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    for (int r = lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * j]; s += v * v; }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) { vn1[j] = sqrt(s); vn2[j] = vn1[j]; }
   }
   __syncthreads();
@@ -203,12 +202,13 @@ __device__ int block_cpqr(double* Y, int ldy, int m, int e, double eps, int* per
   int k = kmax;
   for (int i = 0; i < kmax; ++i) {
     if (warp == 0) {          // pivot: largest norm, near-ties -> lowest index
-      double mx = -1.0;
-      for (int j = i + lane; j < e; j += 32) mx = fmax(mx, vn1[j]);
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      long long mx = -1;
+      for (int j = i + lane; j < e; j += 32) mx = max(mx, dbits(vn1[j]));
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const long long thr = dbits(__longlong_as_double(mx) * (1.0 - TIE_RTOL));
       int best = e;
       for (int j = i + lane; j < e; j += 32)
-        if (vn1[j] >= mx * (1.0 - TIE_RTOL) && j < best) best = j;
+        if (dbits(vn1[j]) >= thr && j < best) best = j;
       for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
       if (lane == 0) shi[0] = best;
     }
@@ -216,7 +216,7 @@ __device__ int block_cpqr(double* Y, int ldy, int m, int e, double eps, int* per
     const int p = shi[0];
     if (p != i) {
       for (int r = threadIdx.x; r < m; r += blockDim.x) {
-        double a = Y[r + (size_t)ldy * i];
+        T a = Y[r + (size_t)ldy * i];
         Y[r + (size_t)ldy * i] = Y[r + (size_t)ldy * p];
         Y[r + (size_t)ldy * p] = a;
       }
@@ -225,70 +225,114 @@ __device__ int block_cpqr(double* Y, int ldy, int m, int e, double eps, int* per
         double a = vn1[i]; vn1[i] = vn1[p]; vn1[p] = a;
         a = vn2[i]; vn2[i] = vn2[p]; vn2[p] = a;
       }
+      __syncthreads();
     }
-    __syncthreads();
-    double s = 0.0;
-    for (int r = i + threadIdx.x; r < m; r += blockDim.x) { double v = Y[r + (size_t)ldy * i]; s += v * v; }
-    const double normx = sqrt(block_sum(s, red));
-    if (i == 0) ref = normx;
-    if (ref == 0.0) { k = 0; break; }
-    if (normx <= eps * ref || normx == 0.0) { k = i; break; }
-    const double x0 = Y[i + (size_t)ldy * i];
-    const double alpha = x0 >= 0.0 ? -normx : normx;
-    const double v0 = x0 - alpha;
-    const double vv = v0 * v0 + (normx * normx - x0 * x0);
-    // apply H = I - 2 v v^T / (v^T v) to columns i+1..e-1 (one warp per column)
-    for (int j = i + 1 + warp; j < e; j += nw) {
-      double* yj = Y + (size_t)ldy * j;
-      const double* yi = Y + (size_t)ldy * i;
-      double dot = (lane == 0) ? v0 * yj[i] : 0.0;
-      for (int r = i + 1 + lane; r < m; r += 32) dot += yi[r] * yj[r];
-      for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-      const double coef = 2.0 * dot / vv;
-      if (lane == 0) yj[i] -= coef * v0;
-      for (int r = i + 1 + lane; r < m; r += 32) yj[r] -= coef * yi[r];
-      __syncwarp();
-      // norm downdate with the recomputation guard
-      double nv = vn1[j];
-      if (nv != 0.0) {
-        double q = fabs(yj[i]) / nv;
-        double temp = fmax(1.0 - q * q, 0.0);
-        double r2 = nv / vn2[j];
-        double temp2 = temp * r2 * r2;
-        if (temp2 <= tol3z) {
-          double ss = 0.0;
-          for (int r = i + 1 + lane; r < m; r += 32) ss += yj[r] * yj[r];
-          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-          if (lane == 0) { vn1[j] = sqrt(ss); vn2[j] = vn1[j]; }
-        } else if (lane == 0) {
-          vn1[j] = nv * sqrt(temp);
-        }
+    // Householder vector of column i: FP64 norm, scalars by one thread
+    if (warp == 0) {
+      double s = 0.0;
+      for (int r = i + lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * i]; s += v * v; }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        const double normx = sqrt(s);
+        const double x0 = (double)Y[i + (size_t)ldy * i];
+        const double alpha = x0 >= 0.0 ? -normx : normx;
+        const double v0 = x0 - alpha;
+        const double vv = v0 * v0 + (s - x0 * x0);
+        scal[0] = alpha;
+        scal[1] = v0;
+        scal[2] = vv > 0.0 ? 2.0 / vv : 0.0;
+        scal[3] = normx;
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) Y[i + (size_t)ldy * i] = alpha;
+    const double normx = scal[3];
+    if (i == 0) ref = normx;
+    if (ref == 0.0) { k = 0; break; }
+    if (normx <= eps * ref || normx == 0.0) { k = i; break; }
+    const T v0 = (T)scal[1];
+    const T c2 = (T)scal[2];
+    const int ncol = e - i - 1;
+    // dots of v with the trailing columns: lanes over columns, warps over rows
+    for (int cg = 0; cg < ncol; cg += 32) {
+      const int j = i + 1 + cg + lane;
+      T acc = T(0);
+      if (j < e) {
+        const T* yj = Y + (size_t)ldy * j;
+        const T* yi = Y + (size_t)ldy * i;
+        if (warp == 0) acc = v0 * yj[i];
+        for (int r = i + 1 + warp; r < m; r += NW) acc += yi[r] * yj[r];
+      }
+      part[warp * 32 + lane] = (double)acc;
+      __syncthreads();
+      if (warp == 0 && j < e) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += part[w * 32 + lane];
+        coef[(cg + lane) & 63] = (T)s * c2;
+      }
+      __syncthreads();
+      // update of this group of trailing columns
+      if (j < e) {
+        const T cj = coef[(cg + lane) & 63];
+        T* yj = Y + (size_t)ldy * j;
+        const T* yi = Y + (size_t)ldy * i;
+        if (warp == 0) yj[i] -= cj * v0;
+        for (int r = i + 1 + warp; r < m; r += NW) yj[r] -= cj * yi[r];
+      }
+      __syncthreads();
+    }
+    // FP64 norm downdates, one lane per column; the guarded recomputations afterwards
+    if (warp == 0) {
+      for (int j = i + 1 + lane; j < e; j += 32) {
+        const double nv = vn1[j];
+        int fl = 0;
+        if (nv != 0.0) {
+          const double q = fabs((double)Y[i + (size_t)ldy * j]) / nv;
+          const double temp = fmax(1.0 - q * q, 0.0);
+          const double r2 = nv / vn2[j];
+          const double temp2 = temp * r2 * r2;
+          if (temp2 <= tol3z) fl = 1;
+          else vn1[j] = nv * sqrt(temp);
+        }
+        flags[j] = fl;
+      }
+    }
+    __syncthreads();
+    for (int j = i + 1 + warp; j < e; j += NW) {
+      if (!flags[j]) continue;
+      double s = 0.0;
+      for (int r = i + 1 + lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * j]; s += v * v; }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) { vn1[j] = sqrt(s); vn2[j] = vn1[j]; }
+    }
+    if (threadIdx.x == 0) Y[i + (size_t)ldy * i] = (T)scal[0];
     __syncthreads();
   }
   __syncthreads();
   return k;
 }
 
-// T (k x (e-k), ld ldt) = R_1^{-1} R_2 from the R held in Y (ld ldy)
-__device__ void block_interp(const double* Y, int ldy, int k, int e, double* T, int ldt) {
+// T (k x (e-k), ld ldt) = R_1^{-1} R_2 from the R held in Y (ld ldy); rinv: >= k scratch
+template <typename T>
+__device__ void block_interp(const T* Y, int ldy, int k, int e, T* Tm, int ldt, T* rinv) {
+  for (int a = threadIdx.x; a < k; a += blockDim.x) rinv[a] = T(1) / Y[a + (size_t)ldy * a];
+  __syncthreads();
   for (int j = threadIdx.x; j < e - k; j += blockDim.x) {
     for (int a = k - 1; a >= 0; --a) {
-      double s = Y[a + (size_t)ldy * (k + j)];
-      for (int b = a + 1; b < k; ++b) s -= Y[a + (size_t)ldy * b] * T[b + (size_t)ldt * j];
-      T[a + (size_t)ldt * j] = s / Y[a + (size_t)ldy * a];
+      T s = Y[a + (size_t)ldy * (k + j)];
+      for (int b = a + 1; b < k; ++b) s -= Y[a + (size_t)ldy * b] * Tm[b + (size_t)ldt * j];
+      Tm[a + (size_t)ldt * j] = s * rinv[a];
     }
   }
   __syncthreads();
 }
 
 // LU with partial pivoting of the n x n block of A at (r0, r0) (ld lda), with the row
-// operations carried over columns [0, ncol); the multipliers are stored below the diagonal.
-// Returns false on an exactly zero pivot.
-__device__ bool block_gepp(double* A, int lda, int r0, int n, int ncol, int* piv, int* shi) {
+// operations carried over columns [0, ncol) outside the factored block; multipliers are
+// stored below the diagonal and not interchanged afterwards (the solve interleaves
+// interchanges and eliminations).  inv receives the reciprocal pivots.  Returns false on an
+// exactly zero pivot.
+template <typename T>
+__device__ bool block_gepp(T* A, int lda, int r0, int n, int ncol, int* piv, T* inv, int* shi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   bool ok = true;
   for (int j = 0; j < n; ++j) {
@@ -297,7 +341,7 @@ __device__ bool block_gepp(double* A, int lda, int r0, int n, int ncol, int* piv
       double best = -1.0;
       int bi = n;
       for (int r = j + lane; r < n; r += 32) {
-        double v = fabs(A[(r0 + r) + (size_t)lda * cj]);
+        double v = fabs((double)A[(r0 + r) + (size_t)lda * cj]);
         if (v > best || (v == best && r < bi)) { best = v; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -309,18 +353,19 @@ __device__ bool block_gepp(double* A, int lda, int r0, int n, int ncol, int* piv
     }
     __syncthreads();
     const int p = shi[0];
-    if (shi[1]) { ok = false; __syncthreads(); continue; }
+    if (shi[1]) { ok = false; if (threadIdx.x == 0) inv[j] = T(0); __syncthreads(); continue; }
     if (p != j) {
       for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
         if (c >= r0 && c < cj) continue;
-        double a = A[(r0 + j) + (size_t)lda * c];
+        T a = A[(r0 + j) + (size_t)lda * c];
         A[(r0 + j) + (size_t)lda * c] = A[(r0 + p) + (size_t)lda * c];
         A[(r0 + p) + (size_t)lda * c] = a;
       }
       __syncthreads();
     }
-    const double pv = A[(r0 + j) + (size_t)lda * cj];
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[(r0 + r) + (size_t)lda * cj] /= pv;
+    const T ipv = T(1) / A[(r0 + j) + (size_t)lda * cj];
+    if (threadIdx.x == 0) inv[j] = ipv;
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[(r0 + r) + (size_t)lda * cj] *= ipv;
     __syncthreads();
     const int nr = n - j - 1;
     const int nc = ncol - 1;   // every column but cj
@@ -328,8 +373,7 @@ __device__ bool block_gepp(double* A, int lda, int r0, int n, int ncol, int* piv
       int r = j + 1 + e % nr;
       int c = e / nr;
       if (c >= cj) ++c;
-      // columns of the already-factored part of the block (r0 <= c < cj) hold multipliers
-      if (c >= r0 && c < cj) continue;
+      if (c >= r0 && c < cj) continue;   // multipliers of earlier steps
       A[(r0 + r) + (size_t)lda * c] -= A[(r0 + r) + (size_t)lda * cj] * A[(r0 + j) + (size_t)lda * c];
     }
     __syncthreads();
@@ -338,10 +382,11 @@ __device__ bool block_gepp(double* A, int lda, int r0, int n, int ncol, int* piv
 }
 
 // ------------------------------------------------------------ sparsify: one CTA per segment
-__global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_bytes) {
+template <typename T>
+__global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_bytes) {
   extern __shared__ double sm[];
   __shared__ SegCtx S;
-  __shared__ double red[40];
+  __shared__ double shr[NW * 32 + 3 * 64];
   __shared__ int shi[8];
   __shared__ int nearlist[NEAR_MAX];
   __shared__ int nnear_sh, nfar_sh;
@@ -357,13 +402,15 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
     return;
   }
   const size_t ld = d.ldF;
-  const double* F1 = d.F + (size_t)S.b1 * ld * ld;
-  const double* F2 = d.F + (size_t)S.b2 * ld * ld;
+  const T* F1 = static_cast<const T*>(d.F) + (size_t)S.b1 * ld * ld;
+  const T* F2 = static_cast<const T*>(d.F) + (size_t)S.b2 * ld * ld;
+  T* Dg = static_cast<T*>(d.Dm) + (size_t)sid * capS * capS;
+  T* Tg = static_cast<T*>(d.T) + (size_t)sid * capS * capS;
+  T* Ig = static_cast<T*>(d.Dinv) + (size_t)sid * capS;
   const int halves = d.symmetric ? 1 : 2;
 
   // eps == 0: no sparsification, the whole segment is skeleton
   if (d.eps == 0.0) {
-    double* Dg = d.Dm + (size_t)sid * capS * capS;
     for (int x = threadIdx.x; x < e * e; x += blockDim.x) {
       int a = x % e, b = x / e;
       Dg[a + (size_t)capS * b] = F1[(S.s1 + a) + ld * (S.s1 + b)] + F2[(S.s2 + a) + ld * (S.s2 + b)];
@@ -404,38 +451,42 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
   const int mmax = nN + hmax;
 
   // working storage: vectors and sketch chunks in shared memory; Y, D, T too when they
-  // fit, else in the global scratch of this segment
-  const size_t small = 2 * (size_t)e + (size_t)e + 1;          // vn1, vn2, perm + piv (ints)
-  const size_t per_ch = (size_t)halves * (e + hmax);            // Bc + Gc per chunk row
-  const size_t ydt = (size_t)mmax * e + 2 * (size_t)e * e;
-  const size_t avail = (size_t)smem_bytes / sizeof(double);
+  // fit, else the global scratch of this segment
+  const size_t TD = sizeof(T);
+  const size_t small_b = (2 * (size_t)e) * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * TD + 64;
+  const size_t per_ch_b = (size_t)halves * (e + hmax) * TD;
+  const size_t ydt_b = ((size_t)mmax * e + 2 * (size_t)e * e) * TD;
   int ch = SK_CHUNK;
-  bool in_smem = small + ch * per_ch + ydt <= avail;
+  bool in_smem = small_b + ch * per_ch_b + ydt_b <= (size_t)smem_bytes;
   if (!in_smem) {
-    size_t room = avail > small ? avail - small : 0;
-    ch = (int)min((size_t)SK_CHUNK, room / (per_ch > 0 ? per_ch : 1));
+    size_t room = (size_t)smem_bytes > small_b ? (size_t)smem_bytes - small_b : 0;
+    ch = (int)min((size_t)SK_CHUNK, room / (per_ch_b > 0 ? per_ch_b : 1));
     if (ch < 1) { ch = 1; if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); }
   }
-  double *Y, *Dw, *Tw, *Bc, *Gc, *vn1, *vn2;
-  int *perm, *piv;
+  T *Y, *Dw, *Tw, *Bc, *Gc, *rinv;
+  double *vn1, *vn2;
+  int *perm, *piv, *flags;
   int ldy, ldd, ldt;
   {
-    double* q = sm;
-    vn1 = q; q += e;
-    vn2 = q; q += e;
-    perm = reinterpret_cast<int*>(q);
-    piv = perm + e;
-    q += (e + 1);
-    Bc = q; q += (size_t)halves * ch * e;
-    Gc = q; q += (size_t)hmax * halves * ch;
+    char* q = reinterpret_cast<char*>(sm);
+    vn1 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
+    vn2 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
+    perm = reinterpret_cast<int*>(q); q += (size_t)e * 4;
+    piv = reinterpret_cast<int*>(q); q += (size_t)e * 4;
+    flags = reinterpret_cast<int*>(q); q += ((size_t)e + 4) * 4;
+    q = reinterpret_cast<char*>(((uintptr_t)q + 15) & ~(uintptr_t)15);
+    rinv = reinterpret_cast<T*>(q); q += (size_t)e * TD;
+    q = reinterpret_cast<char*>(((uintptr_t)q + 15) & ~(uintptr_t)15);
+    Bc = reinterpret_cast<T*>(q); q += (size_t)halves * ch * e * TD;
+    Gc = reinterpret_cast<T*>(q); q += (size_t)hmax * halves * ch * TD;
     if (in_smem) {
-      Y = q; q += (size_t)mmax * e; ldy = mmax;
-      Dw = q; q += (size_t)e * e; ldd = e;
-      Tw = q; q += (size_t)e * e; ldt = e;
+      Y = reinterpret_cast<T*>(q); q += (size_t)mmax * e * TD; ldy = mmax;
+      Dw = reinterpret_cast<T*>(q); q += (size_t)e * e * TD; ldd = e;
+      Tw = reinterpret_cast<T*>(q); q += (size_t)e * e * TD; ldt = e;
     } else {
-      Y = d.Yg + (size_t)sid * d.Ycap * capS; ldy = d.Ycap;
-      Dw = d.Dm + (size_t)sid * capS * capS; ldd = capS;
-      Tw = d.T + (size_t)sid * capS * capS; ldt = capS;
+      Y = static_cast<T*>(d.Yg) + (size_t)sid * d.Ycap * capS; ldy = d.Ycap;
+      Dw = Dg; ldd = capS;
+      Tw = Tg; ldt = capS;
     }
   }
   if (!in_smem && (mmax > d.Ycap || d.Yg == nullptr)) {   // no room: report, touch nothing
@@ -456,7 +507,7 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
       int t = row / nnear, a = row % nnear;
       int r, i;
       locate(S, nearlist[a], r, i);
-      Y[row + (size_t)ldy * c] = bval(d, S, F1, F2, S.run[r], i, t, c);
+      Y[row + (size_t)ldy * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
     }
     if (full) {
       // Phi = I on the far block: far rows in the enumeration order of the neighbours;
@@ -474,12 +525,12 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
         locate(S, f, r, i);
         for (int t = 0; t < halves; ++t)
           for (int c = 0; c < e; ++c)
-            Y[(nN + t * nfar_sh + j) + (size_t)ldy * c] = bval(d, S, F1, F2, S.run[r], i, t, c);
+            Y[(nN + t * nfar_sh + j) + (size_t)ldy * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
       }
     } else {
-      for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] = 0.0;
+      for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] = T(0);
       __syncthreads();
-      // Y_F = G B_F, chunks of SK_CHUNK neighbours (near ones get zero weight)
+      // Y_F = G B_F, chunks of neighbours (near ones get zero weight)
       for (int f0 = 0; f0 < S.nb; f0 += ch) {
         const int nc = min(ch, S.nb - f0);
         const int rows = halves * nc;
@@ -488,7 +539,7 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
           int t = row / nc, jj = row % nc;
           int r, i;
           locate(S, f0 + jj, r, i);
-          Bc[row + (size_t)rows * c] = bval(d, S, F1, F2, S.run[r], i, t, c);
+          Bc[row + (size_t)rows * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
         }
         for (int x = threadIdx.x; x < hh * rows; x += blockDim.x) {
           int rr = x % hh, row = x / hh;
@@ -496,28 +547,28 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
           int f = f0 + jj;
           bool isnear = false;
           for (int a = 0; a < nnear; ++a) isnear |= (nearlist[a] == f);
-          double gv = 0.0;
+          T gv = T(0);
           if (!isnear) {
             int r, i;
             locate(S, f, r, i);
-            gv = (double)sketch_gauss(d.seed, d.l, sid, rr, run_node(d, S.run[r], i), t);
+            gv = (T)sketch_gauss(d.seed, d.l, sid, rr, run_node(d, S.run[r], i), t);
           }
           Gc[rr + (size_t)hh * row] = gv;
         }
         __syncthreads();
         for (int x = threadIdx.x; x < hh * e; x += blockDim.x) {
           int rr = x % hh, c = x / hh;
-          double acc = 0.0;
+          T acc = T(0);
           for (int row = 0; row < rows; ++row) acc += Gc[rr + (size_t)hh * row] * Bc[row + (size_t)rows * c];
           Y[(nN + rr) + (size_t)ldy * c] += acc;
         }
         __syncthreads();
       }
-      const double sc = 1.0 / sqrt((double)hh);
+      const T sc = (T)(1.0 / sqrt((double)hh));
       for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
     }
     __syncthreads();
-    k = block_cpqr(Y, ldy, m, e, d.eps, perm, vn1, vn2, red, shi);
+    k = block_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
     if (!full && k > h - d.p_over && h < nF) {
       h = min(2 * h, nF);
       __syncthreads();
@@ -526,7 +577,7 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
     break;
   }
   const int r = e - k;
-  block_interp(Y, ldy, k, e, Tw, ldt);
+  block_interp<T>(Y, ldy, k, e, Tw, ldt, rinv);
 
   // ---- transformed diagonal block in [skeleton | remainder] order (Eq. (UtALt))
   for (int x = threadIdx.x; x < e * e; x += blockDim.x) {
@@ -539,7 +590,7 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
     // column operation: D[:, k:] -= D[:, :k] T
     for (int x = threadIdx.x; x < e * r; x += blockDim.x) {
       int a = x % e, b = x / e;
-      double s = 0.0;
+      T s = T(0);
       for (int c = 0; c < k; ++c) s += Dw[a + (size_t)ldd * c] * Tw[c + (size_t)ldt * b];
       Dw[a + (size_t)ldd * (k + b)] -= s;
     }
@@ -547,7 +598,7 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
     // row operation: D[k:, :] -= T^T D[:k, :]
     for (int x = threadIdx.x; x < r * e; x += blockDim.x) {
       int a = x % r, b = x / r;
-      double s = 0.0;
+      T s = T(0);
       for (int c = 0; c < k; ++c) s += Tw[c + (size_t)ldt * a] * Dw[c + (size_t)ldd * b];
       Dw[(k + a) + (size_t)ldd * b] -= s;
     }
@@ -556,20 +607,20 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
   // ---- eliminate the remainder: LU(A_rr) with W = L^{-1} P A_rk, Z = A_kr U^{-1},
   //      A_kk -= Z W  (Eq. (L^-1 * A * U^-1) for the segments of level l)
   if (r > 0) {
-    bool ok = block_gepp(Dw, ldd, k, r, e, piv, shi);
+    bool ok = block_gepp<T>(Dw, ldd, k, r, e, piv, rinv, shi);
     if (!ok && threadIdx.x == 0) atomicOr(d.err, ERR_SINGULAR);
     if (k > 0) {
       for (int a = threadIdx.x; a < k; a += blockDim.x) {     // Z = A_kr U^{-1}, row by row
         for (int j = 0; j < r; ++j) {
-          double s = Dw[a + (size_t)ldd * (k + j)];
+          T s = Dw[a + (size_t)ldd * (k + j)];
           for (int i2 = 0; i2 < j; ++i2) s -= Dw[a + (size_t)ldd * (k + i2)] * Dw[(k + i2) + (size_t)ldd * (k + j)];
-          Dw[a + (size_t)ldd * (k + j)] = s / Dw[(k + j) + (size_t)ldd * (k + j)];
+          Dw[a + (size_t)ldd * (k + j)] = s * rinv[j];
         }
       }
       __syncthreads();
       for (int x = threadIdx.x; x < k * k; x += blockDim.x) {
         int a = x % k, b = x / k;
-        double s = 0.0;
+        T s = T(0);
         for (int j = 0; j < r; ++j) s += Dw[a + (size_t)ldd * (k + j)] * Dw[(k + j) + (size_t)ldd * b];
         Dw[a + (size_t)ldd * b] -= s;
       }
@@ -578,13 +629,14 @@ __global__ void __launch_bounds__(256) sparsify_kernel(LevelDev d, int smem_byte
   }
   // ---- outputs
   if (in_smem) {
-    double* Dg = d.Dm + (size_t)sid * capS * capS;
-    double* Tg = d.T + (size_t)sid * capS * capS;
     for (int x = threadIdx.x; x < e * e; x += blockDim.x) Dg[(x % e) + (size_t)capS * (x / e)] = Dw[x];
     for (int x = threadIdx.x; x < k * r; x += blockDim.x) Tg[(x % k) + (size_t)capS * (x / k)] = Tw[(x % k) + (size_t)ldt * (x / k)];
   }
   for (int j = threadIdx.x; j < e; j += blockDim.x) perm_out[j] = perm[j];
-  for (int j = threadIdx.x; j < r; j += blockDim.x) d.piv[(size_t)sid * capS + j] = piv[j];
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    d.piv[(size_t)sid * capS + j] = piv[j];
+    Ig[j] = rinv[j];
+  }
   if (threadIdx.x == 0) { d.kk[sid] = k; d.hs[sid] = h; }
 }
 
@@ -620,9 +672,7 @@ __device__ void parent_ctx(const LevelDev& d, int P, ParentCtx& C) {
 }
 
 // Unknowns of a child side restricted to its skeleton, appended to the table.
-__device__ int add_side(const LevelDev& d, int* tab, int n, int posM, int child, int I, int J,
-                        int side, int node_seg_dummy) {
-  (void)node_seg_dummy;
+__device__ int add_side(const LevelDev& d, int* tab, int n, int posM, int child, int I, int J, int side) {
   int sg = d.g.box_side(I, J, side);
   if (sg < 0) return n;
   int k = d.kk[sg];
@@ -663,21 +713,20 @@ __global__ void merge_table_kernel(LevelDev d) {
   int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
   const Geo gp = d.gp;
   const int Dp = gp.D();
+  const bool root = gp.bx * gp.by == 1;
   int n = 0;
   // sides of P (merged or inherited), then its corners, then the separator skeleton
-  for (int side = 0; side < 4; ++side) {
-    if (gp.bx * gp.by > 1 && gp.box_side(C.Ip, C.Jp, side) < 0) continue;
-    if (gp.bx * gp.by == 1) continue;
+  for (int side = 0; side < 4 && !root; ++side) {
+    if (gp.box_side(C.Ip, C.Jp, side) < 0) continue;
     int pos = gp.side_pos(side);
     bool split = d.vcut ? (side == SIDE_BOTTOM || side == SIDE_TOP) : (side == SIDE_LEFT || side == SIDE_RIGHT);
     if (!split) {
-      // inherited from one child
       int child = d.vcut ? (side == SIDE_LEFT ? 1 : 2) : (side == SIDE_BOTTOM ? 1 : 2);
       int I = child == 1 ? C.I1 : C.I2, J = child == 1 ? C.J1 : C.J2;
-      n = add_side(d, tab, n, pos, child, I, J, side, 0);
+      n = add_side(d, tab, n, pos, child, I, J, side);
     } else {
       int n0 = n;
-      n = add_side(d, tab, n, pos, 1, C.I1, C.J1, side, 0);
+      n = add_side(d, tab, n, pos, 1, C.I1, C.J1, side);
       int k1 = n - n0;
       // junction: vertical cut: bottom -> b1.BR = b2.BL, top -> b1.TR = b2.TL;
       //           horizontal cut: left -> b1.TL = b2.BL, right -> b1.TR = b2.BR
@@ -686,17 +735,15 @@ __global__ void merge_table_kernel(LevelDev d) {
       else { jc1 = side == SIDE_LEFT ? C_TL : C_TR; jc2 = side == SIDE_LEFT ? C_BL : C_BR; }
       n = add_corner(d, tab, n, pos + k1, C.I1, C.J1, jc1, C.I2, C.J2, jc2);
       int n1 = n;
-      n = add_side(d, tab, n, pos + (n1 - n0), 2, C.I2, C.J2, side, 0);
+      n = add_side(d, tab, n, pos + (n1 - n0), 2, C.I2, C.J2, side);
     }
   }
-  if (gp.bx * gp.by > 1) {
-    for (int c = 0; c < 4; ++c) {
-      if (gp.box_corner(C.Ip, C.Jp, c) < 0) continue;
-      // vertical cut: BL,TL from b1; BR,TR from b2.  horizontal: BL,BR from b1; TL,TR from b2
-      bool from1 = d.vcut ? (c == C_BL || c == C_TL) : (c == C_BL || c == C_BR);
-      if (from1) n = add_corner(d, tab, n, gp.corner_pos(c), C.I1, C.J1, c, 0, 0, -1);
-      else n = add_corner(d, tab, n, gp.corner_pos(c), 0, 0, -1, C.I2, C.J2, c);
-    }
+  for (int c = 0; c < 4 && !root; ++c) {
+    if (gp.box_corner(C.Ip, C.Jp, c) < 0) continue;
+    // vertical cut: BL,TL from b1; BR,TR from b2.  horizontal: BL,BR from b1; TL,TR from b2
+    bool from1 = d.vcut ? (c == C_BL || c == C_TL) : (c == C_BL || c == C_BR);
+    if (from1) n = add_corner(d, tab, n, gp.corner_pos(c), C.I1, C.J1, c, 0, 0, -1);
+    else n = add_corner(d, tab, n, gp.corner_pos(c), 0, 0, -1, C.I2, C.J2, c);
   }
   const int ndP = n;
   // separator skeleton: side RIGHT/TOP of child 1 (owner) = LEFT/BOTTOM of child 2
@@ -720,6 +767,7 @@ __global__ void merge_table_kernel(LevelDev d) {
 // M[a][b] = sum over the children holding both unknowns of the child's block, where the
 // block of a segment with itself is its eliminated skeleton block A_ss' (held by the owner
 // child: the segment is that child's TOP or RIGHT side) and zero in the other child.
+template <typename T>
 __global__ void merge_assemble_kernel(LevelDev d) {
   const int P = blockIdx.y;
   const int nM = d.pcount[2 * P] + d.pcount[2 * P + 1];
@@ -727,16 +775,17 @@ __global__ void merge_assemble_kernel(LevelDev d) {
   ParentCtx C;
   parent_ctx(d, P, C);
   const size_t ld = d.ldF, ldp = d.ldFp;
-  const double* F1 = d.F + (size_t)C.c1 * ld * ld;
-  const double* F2 = d.F + (size_t)C.c2 * ld * ld;
-  double* M = d.Fp + (size_t)P * ldp * ldp;
+  const T* F1 = static_cast<const T*>(d.F) + (size_t)C.c1 * ld * ld;
+  const T* F2 = static_cast<const T*>(d.F) + (size_t)C.c2 * ld * ld;
+  const T* Dm = static_cast<const T*>(d.Dm);
+  T* M = static_cast<T*>(d.Fp) + (size_t)P * ldp * ldp;
   const long long tot = (long long)nM * nM;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < tot;
        x += (long long)gridDim.x * blockDim.x) {
     int a = (int)(x % nM), b = (int)(x / nM);
     const int* ea = tab + (size_t)a * TABW;
     const int* eb = tab + (size_t)b * TABW;
-    double v = 0.0;
+    T v = T(0);
     for (int ch = 0; ch < 2; ++ch) {
       int pa = ea[1 + 3 * ch], pb = eb[1 + 3 * ch];
       if (pa < 0 || pb < 0) continue;
@@ -745,10 +794,10 @@ __global__ void merge_assemble_kernel(LevelDev d) {
         if (sa == SIDE_TOP || sa == SIDE_RIGHT) {
           int I = ch == 0 ? C.I1 : C.I2, J = ch == 0 ? C.J1 : C.J2;
           int sg = d.g.box_side(I, J, sa);
-          v += d.Dm[(size_t)sg * d.capS * d.capS + ea[3 + 3 * ch] + (size_t)d.capS * eb[3 + 3 * ch]];
+          v += Dm[(size_t)sg * d.capS * d.capS + ea[3 + 3 * ch] + (size_t)d.capS * eb[3 + 3 * ch]];
         }
       } else {
-        const double* Fc = ch == 0 ? F1 : F2;
+        const T* Fc = ch == 0 ? F1 : F2;
         v += Fc[pa + ld * pb];
       }
     }
@@ -758,6 +807,7 @@ __global__ void merge_assemble_kernel(LevelDev d) {
 
 // LU of the separator block with the row operations over every column (W = L^{-1} P A_pd),
 // then Z = A_dp U^{-1}.
+template <typename T>
 __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
   __shared__ int shi[4];
   const int P = blockIdx.x;
@@ -766,7 +816,8 @@ __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
   const int nM = ndP + kp;
   const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
   const size_t ldp = d.ldFp;
-  double* M = d.Fp + (size_t)P * ldp * ldp;
+  T* M = static_cast<T*>(d.Fp) + (size_t)P * ldp * ldp;
+  T* inv = static_cast<T*>(d.Pinv) + (size_t)P * d.sepcap;
   const int Dp = d.gp.D();
   int* piv = d.ppiv + (size_t)P * d.sepcap;
   bool ok = true;
@@ -777,7 +828,7 @@ __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
       double best = -1.0;
       int bi = kp;
       for (int r = j + lane; r < kp; r += 32) {
-        double v = fabs(M[(Dp + r) + ldp * cj]);
+        double v = fabs((double)M[(Dp + r) + ldp * cj]);
         if (v > best || (v == best && r < bi)) { best = v; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -789,20 +840,21 @@ __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
     }
     __syncthreads();
     const int p = shi[0];
-    if (shi[1]) { ok = false; __syncthreads(); continue; }
+    if (shi[1]) { ok = false; if (threadIdx.x == 0) inv[j] = T(0); __syncthreads(); continue; }
     if (p != j) {
       for (int c = threadIdx.x; c < nM; c += blockDim.x) {
         const int pc = tab[(size_t)c * TABW];
         if (pc >= Dp && pc < cj) continue;
         size_t col = ldp * pc;
-        double a = M[(Dp + j) + col];
+        T a = M[(Dp + j) + col];
         M[(Dp + j) + col] = M[(Dp + p) + col];
         M[(Dp + p) + col] = a;
       }
       __syncthreads();
     }
-    const double pv = M[(Dp + j) + ldp * cj];
-    for (int r = j + 1 + threadIdx.x; r < kp; r += blockDim.x) M[(Dp + r) + ldp * cj] /= pv;
+    const T ipv = T(1) / M[(Dp + j) + ldp * cj];
+    if (threadIdx.x == 0) inv[j] = ipv;
+    for (int r = j + 1 + threadIdx.x; r < kp; r += blockDim.x) M[(Dp + r) + ldp * cj] *= ipv;
     __syncthreads();
     const int nr = kp - j - 1;
     // update rows j+1.. over columns: the separator columns j+1..kp-1 and every dP column
@@ -819,17 +871,18 @@ __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
   for (int a = threadIdx.x; a < ndP; a += blockDim.x) {
     size_t row = tab[(size_t)a * TABW];
     for (int j = 0; j < kp; ++j) {
-      double s = M[row + ldp * (Dp + j)];
+      T s = M[row + ldp * (Dp + j)];
       for (int i = 0; i < j; ++i) s -= M[row + ldp * (Dp + i)] * M[(Dp + i) + ldp * (Dp + j)];
-      M[row + ldp * (Dp + j)] = s / M[(Dp + j) + ldp * (Dp + j)];
+      M[row + ldp * (Dp + j)] = s * inv[j];
     }
   }
 }
 
-// Schur update of the parent's boundary block: M[dP, dP] -= Z W (FP64, 64 x 64 tiles)
+// Schur update of the parent's boundary block: M[dP, dP] -= Z W (64 x 64 tiles)
+template <typename T>
 __global__ void __launch_bounds__(256) merge_schur_kernel(LevelDev d) {
-  __shared__ double Zs[64][17];
-  __shared__ double Ws[16][65];
+  __shared__ T Zs[64][17];
+  __shared__ T Ws[16][65];
   __shared__ int ra[64], cb[64];
   const int P = blockIdx.z;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
@@ -839,7 +892,7 @@ __global__ void __launch_bounds__(256) merge_schur_kernel(LevelDev d) {
   if (ti >= tiles || tj >= tiles) return;
   const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
   const size_t ldp = d.ldFp;
-  double* M = d.Fp + (size_t)P * ldp * ldp;
+  T* M = static_cast<T*>(d.Fp) + (size_t)P * ldp * ldp;
   const int Dp = d.gp.D();
   for (int x = threadIdx.x; x < 64; x += blockDim.x) {
     int a = ti * 64 + x, b = tj * 64 + x;
@@ -848,18 +901,18 @@ __global__ void __launch_bounds__(256) merge_schur_kernel(LevelDev d) {
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;   // 16 x 16 threads, 4 x 4 each
-  double acc[4][4] = {};
+  T acc[4][4] = {};
   for (int j0 = 0; j0 < kp; j0 += 16) {
     for (int x = threadIdx.x; x < 64 * 16; x += blockDim.x) {
       int i = x % 64, j = x / 64;
-      Zs[i][j] = (ra[i] >= 0 && j0 + j < kp) ? M[ra[i] + ldp * (Dp + j0 + j)] : 0.0;
+      Zs[i][j] = (ra[i] >= 0 && j0 + j < kp) ? M[ra[i] + ldp * (Dp + j0 + j)] : T(0);
       int c = x % 64, jj = x / 64;
-      Ws[jj][c] = (cb[c] >= 0 && j0 + jj < kp) ? M[(Dp + j0 + jj) + ldp * cb[c]] : 0.0;
+      Ws[jj][c] = (cb[c] >= 0 && j0 + jj < kp) ? M[(Dp + j0 + jj) + ldp * cb[c]] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      double z[4], w[4];
+      T z[4], w[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) { z[u] = Zs[ty * 4 + u][j]; w[u] = Ws[j][tx * 4 + u]; }
 #pragma unroll
@@ -920,8 +973,10 @@ __global__ void seg_merge_kernel(LevelDev d) {
 // ------------------------------------------------------------ solve
 // Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
+template <typename T>
 __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, double* X, int nrhs, int ld, int bwd) {
-  extern __shared__ double sm[];
+  extern __shared__ double smd[];
+  T* v = reinterpret_cast<T*>(smd);   // e x nrhs: [skeleton | remainder] order
   const int sid = blockIdx.x;
   const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
   if (r == 0 || e == 0) return;
@@ -929,31 +984,31 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, double* X, i
   const int* perm = d.perm + (size_t)sid * capS;
   const int* nodes = d.nodes + (size_t)sid * capS;
   const int* piv = d.piv + (size_t)sid * capS;
-  const double* T = d.T + (size_t)sid * capS * capS;
-  const double* Dm = d.Dm + (size_t)sid * capS * capS;
-  double* v = sm;   // e x nrhs: [skeleton | remainder] order
+  const T* Tm = static_cast<const T*>(d.T) + (size_t)sid * capS * capS;
+  const T* Dm = static_cast<const T*>(d.Dm) + (size_t)sid * capS * capS;
+  const T* inv = static_cast<const T*>(d.Dinv) + (size_t)sid * capS;
   for (int x = threadIdx.x; x < e * nrhs; x += blockDim.x) {
     int a = x % e, c = x / e;
-    v[x] = X[nodes[perm[a]] + (size_t)ld * c];
+    v[x] = (T)X[nodes[perm[a]] + (size_t)ld * c];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   if (!bwd) {
     for (int x = threadIdx.x; x < r * nrhs; x += blockDim.x) {
       int a = x % r, c = x / r;
-      double s = 0.0;
-      for (int q = 0; q < k; ++q) s += T[q + (size_t)capS * a] * v[q + e * c];
+      T s = T(0);
+      for (int q = 0; q < k; ++q) s += Tm[q + (size_t)capS * a] * v[q + e * c];
       v[k + a + e * c] -= s;
     }
     __syncthreads();
     for (int c = warp; c < nrhs; c += nw) {   // y = L^{-1} P b_r
-      double* y = v + k + e * c;
+      T* y = v + k + e * c;
       for (int j = 0; j < r; ++j) {
         int p = piv[j];
         __syncwarp();
-        if (p != j && lane == 0) { double t = y[j]; y[j] = y[p]; y[p] = t; }
+        if (p != j && lane == 0) { T t = y[j]; y[j] = y[p]; y[p] = t; }
         __syncwarp();
-        double yj = y[j];
+        T yj = y[j];
         for (int i = j + 1 + lane; i < r; i += 32) y[i] -= Dm[(k + i) + (size_t)capS * (k + j)] * yj;
       }
       __syncwarp();
@@ -961,23 +1016,23 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, double* X, i
     __syncthreads();
     for (int x = threadIdx.x; x < k * nrhs; x += blockDim.x) {
       int a = x % k, c = x / k;
-      double s = 0.0;
+      T s = T(0);
       for (int j = 0; j < r; ++j) s += Dm[a + (size_t)capS * (k + j)] * v[k + j + e * c];
       v[a + e * c] -= s;
     }
   } else {
     for (int x = threadIdx.x; x < r * nrhs; x += blockDim.x) {
       int a = x % r, c = x / r;
-      double s = 0.0;
+      T s = T(0);
       for (int q = 0; q < k; ++q) s += Dm[(k + a) + (size_t)capS * q] * v[q + e * c];
       v[k + a + e * c] -= s;
     }
     __syncthreads();
     for (int c = warp; c < nrhs; c += nw) {   // x_r = U^{-1} (.)
-      double* y = v + k + e * c;
+      T* y = v + k + e * c;
       for (int j = r - 1; j >= 0; --j) {
         __syncwarp();
-        double yj = y[j] / Dm[(k + j) + (size_t)capS * (k + j)];
+        const T yj = y[j] * inv[j];
         __syncwarp();
         if (lane == 0) y[j] = yj;
         for (int i = lane; i < j; i += 32) y[i] -= Dm[(k + i) + (size_t)capS * (k + j)] * yj;
@@ -987,23 +1042,25 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, double* X, i
     __syncthreads();
     for (int x = threadIdx.x; x < k * nrhs; x += blockDim.x) {
       int a = x % k, c = x / k;
-      double s = 0.0;
-      for (int j = 0; j < r; ++j) s += T[a + (size_t)capS * j] * v[k + j + e * c];
+      T s = T(0);
+      for (int j = 0; j < r; ++j) s += Tm[a + (size_t)capS * j] * v[k + j + e * c];
       v[a + e * c] -= s;
     }
   }
   __syncthreads();
   for (int x = threadIdx.x; x < e * nrhs; x += blockDim.x) {
     int a = x % e, c = x / e;
-    X[nodes[perm[a]] + (size_t)ld * c] = v[x];
+    X[nodes[perm[a]] + (size_t)ld * c] = (double)v[x];
   }
 }
 
 // Separator of each parent: forward y_p = L^{-1} P b_p, b_dP -= Z y_p (parents of one colour
 // at a time: two parents of the same colour share no boundary unknown); backward
 // x_p = U^{-1} (y_p - W x_dP).
+template <typename T>
 __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, double* X, int nrhs, int ld, int bwd, int colour) {
-  extern __shared__ double sm[];
+  extern __shared__ double smd[];
+  T* y = reinterpret_cast<T*>(smd);   // kp x nrhs
   const int P = blockIdx.x;
   const int Ip = P % d.gp.bx, Jp = P / d.gp.bx;
   if (!bwd && ((Ip & 1) + 2 * (Jp & 1)) != colour) return;
@@ -1011,25 +1068,25 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, double* X, i
   if (kp == 0) return;
   const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
   const size_t ldp = d.ldFp;
-  const double* M = d.Fp + (size_t)P * ldp * ldp;
+  const T* M = static_cast<const T*>(d.Fp) + (size_t)P * ldp * ldp;
+  const T* inv = static_cast<const T*>(d.Pinv) + (size_t)P * d.sepcap;
   const int Dp = d.gp.D();
   const int* piv = d.ppiv + (size_t)P * d.sepcap;
-  double* y = sm;   // kp x nrhs
   for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
     int a = x % kp, c = x / kp;
-    y[x] = X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c];
+    y[x] = (T)X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   if (!bwd) {
     for (int c = warp; c < nrhs; c += nw) {
-      double* yy = y + kp * c;
+      T* yy = y + kp * c;
       for (int j = 0; j < kp; ++j) {
         int p = piv[j];
         __syncwarp();
-        if (p != j && lane == 0) { double t = yy[j]; yy[j] = yy[p]; yy[p] = t; }
+        if (p != j && lane == 0) { T t = yy[j]; yy[j] = yy[p]; yy[p] = t; }
         __syncwarp();
-        double yj = yy[j];
+        T yj = yy[j];
         for (int i = j + 1 + lane; i < kp; i += 32) yy[i] -= M[(Dp + i) + ldp * (Dp + j)] * yj;
       }
       __syncwarp();
@@ -1038,24 +1095,24 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, double* X, i
     for (int x = threadIdx.x; x < ndP * nrhs; x += blockDim.x) {
       int a = x % ndP, c = x / ndP;
       size_t row = tab[(size_t)a * TABW];
-      double s = 0.0;
+      T s = T(0);
       for (int j = 0; j < kp; ++j) s += M[row + ldp * (Dp + j)] * y[j + kp * c];
-      X[tab[(size_t)a * TABW + 7] + (size_t)ld * c] -= s;
+      X[tab[(size_t)a * TABW + 7] + (size_t)ld * c] -= (double)s;
     }
   } else {
     for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
       int a = x % kp, c = x / kp;
-      double s = 0.0;
+      T s = T(0);
       for (int b = 0; b < ndP; ++b)
-        s += M[(Dp + a) + ldp * tab[(size_t)b * TABW]] * X[tab[(size_t)b * TABW + 7] + (size_t)ld * c];
+        s += M[(Dp + a) + ldp * tab[(size_t)b * TABW]] * (T)X[tab[(size_t)b * TABW + 7] + (size_t)ld * c];
       y[x] -= s;
     }
     __syncthreads();
     for (int c = warp; c < nrhs; c += nw) {
-      double* yy = y + kp * c;
+      T* yy = y + kp * c;
       for (int j = kp - 1; j >= 0; --j) {
         __syncwarp();
-        double yj = yy[j] / M[(Dp + j) + ldp * (Dp + j)];
+        const T yj = yy[j] * inv[j];
         __syncwarp();
         if (lane == 0) yy[j] = yj;
         for (int i = lane; i < j; i += 32) yy[i] -= M[(Dp + i) + ldp * (Dp + j)] * yj;
@@ -1066,24 +1123,24 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, double* X, i
   __syncthreads();
   for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
     int a = x % kp, c = x / kp;
-    X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] = y[x];
+    X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] = (double)y[x];
   }
 }
 
 }  // namespace
 
-size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over) {
+size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes) {
   const size_t halves = symmetric ? 1 : 2;
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
   const size_t mmax = halves * NEAR_MAX + hcap;
-  const size_t need = 3 * (size_t)e + 1 + SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e;
-  return need * sizeof(double);
+  const size_t small_b = 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
+  return small_b + (SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e) * tbytes;
 }
 
-size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over) {
+size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes) {
   const size_t halves = symmetric ? 1 : 2;
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
-  return (3 * (size_t)e + 1 + halves * (e + hcap)) * sizeof(double);
+  return 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64 + halves * (e + hcap) * tbytes;
 }
 
 void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
@@ -1093,15 +1150,22 @@ void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
   level_init_L_kernel<<<(n + 255) / 256, 256, 0, s>>>(d);
 }
 
-void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
-  if (d.g.nseg() == 0) return;
+template <typename T>
+static void sparsify_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   int smem = (int)p.spars_smem;
-  cudaFuncSetAttribute(sparsify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(sparsify_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   note_launch();
-  sparsify_kernel<<<d.g.nseg(), 256, smem, s>>>(d, smem);
+  sparsify_kernel<T><<<d.g.nseg(), NW * 32, smem, s>>>(d, smem);
 }
 
-void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
+void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
+  if (d.g.nseg() == 0) return;
+  if (d.fp32) sparsify_launch<float>(d, p, s);
+  else sparsify_launch<double>(d, p, s);
+}
+
+template <typename T>
+static void merge_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   const int np = d.gp.nbox();
   note_launch();
   merge_table_kernel<<<np, 32, 0, s>>>(d);
@@ -1111,20 +1175,25 @@ void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
     if (gx > 256) gx = 256;
     dim3 grid(gx, np);
     note_launch();
-    merge_assemble_kernel<<<grid, 256, 0, s>>>(d);
+    merge_assemble_kernel<T><<<grid, 256, 0, s>>>(d);
   }
   note_launch();
-  merge_panel_kernel<<<np, 256, 0, s>>>(d);
+  merge_panel_kernel<T><<<np, 256, 0, s>>>(d);
   {
     int tiles = (p.ldFp + 63) / 64;
     dim3 grid(tiles, tiles, np);
     note_launch();
-    merge_schur_kernel<<<grid, 256, 0, s>>>(d);
+    merge_schur_kernel<T><<<grid, 256, 0, s>>>(d);
   }
   if (d.l > 1 && d.gp.nseg() > 0) {
     note_launch();
     seg_merge_kernel<<<d.gp.nseg(), 128, 0, s>>>(d);
   }
+}
+
+void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
+  if (d.fp32) merge_launch<float>(d, p, s);
+  else merge_launch<double>(d, p, s);
 }
 
 static int col_chunk(size_t per_col_bytes) {
@@ -1133,48 +1202,44 @@ static int col_chunk(size_t per_col_bytes) {
   return c < 1 ? 1 : c;
 }
 
-void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
-  if (d.g.nseg() > 0) {
-    int cc = col_chunk(sizeof(double) * d.capS);
-    for (int c0 = 0; c0 < nrhs; c0 += cc) {
-      int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
-      size_t smem = sizeof(double) * (size_t)d.capS * nc;
-      cudaFuncSetAttribute(seg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      note_launch();
-      seg_solve_kernel<<<d.g.nseg(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 0);
-    }
-  }
-  int cc = col_chunk(sizeof(double) * d.sepcap);
+template <typename T>
+static void level_solve(const LevelDev& d, double* X, int nrhs, int ld, int bwd, cudaStream_t s) {
+  const int cc = col_chunk(sizeof(T) * (size_t)(d.capS > d.sepcap ? d.capS : d.sepcap));
   for (int c0 = 0; c0 < nrhs; c0 += cc) {
-    int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
-    size_t smem = sizeof(double) * (size_t)d.sepcap * nc;
-    cudaFuncSetAttribute(sep_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    for (int colour = 0; colour < 4; ++colour) {
+    const int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
+    double* Xc = X + (size_t)ld * c0;
+    const size_t seg_smem = sizeof(T) * (size_t)d.capS * nc;
+    const size_t sep_smem = sizeof(T) * (size_t)d.sepcap * nc;
+    cudaFuncSetAttribute(seg_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
+    cudaFuncSetAttribute(sep_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sep_smem);
+    if (!bwd) {
+      if (d.g.nseg() > 0) {
+        note_launch();
+        seg_solve_kernel<T><<<d.g.nseg(), 256, seg_smem, s>>>(d, Xc, nc, ld, 0);
+      }
+      for (int colour = 0; colour < 4; ++colour) {
+        note_launch();
+        sep_solve_kernel<T><<<d.gp.nbox(), 256, sep_smem, s>>>(d, Xc, nc, ld, 0, colour);
+      }
+    } else {
       note_launch();
-      sep_solve_kernel<<<d.gp.nbox(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 0, colour);
+      sep_solve_kernel<T><<<d.gp.nbox(), 256, sep_smem, s>>>(d, Xc, nc, ld, 1, 0);
+      if (d.g.nseg() > 0) {
+        note_launch();
+        seg_solve_kernel<T><<<d.g.nseg(), 256, seg_smem, s>>>(d, Xc, nc, ld, 1);
+      }
     }
   }
 }
 
+void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
+  if (d.fp32) level_solve<float>(d, X, nrhs, ld, 0, s);
+  else level_solve<double>(d, X, nrhs, ld, 0, s);
+}
+
 void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
-  int cc = col_chunk(sizeof(double) * d.sepcap);
-  for (int c0 = 0; c0 < nrhs; c0 += cc) {
-    int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
-    size_t smem = sizeof(double) * (size_t)d.sepcap * nc;
-    cudaFuncSetAttribute(sep_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launch();
-    sep_solve_kernel<<<d.gp.nbox(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 1, 0);
-  }
-  if (d.g.nseg() > 0) {
-    int cc2 = col_chunk(sizeof(double) * d.capS);
-    for (int c0 = 0; c0 < nrhs; c0 += cc2) {
-      int nc = nrhs - c0 < cc2 ? nrhs - c0 : cc2;
-      size_t smem = sizeof(double) * (size_t)d.capS * nc;
-      cudaFuncSetAttribute(seg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      note_launch();
-      seg_solve_kernel<<<d.g.nseg(), 256, smem, s>>>(d, X + (size_t)ld * c0, nc, ld, 1);
-    }
-  }
+  if (d.fp32) level_solve<float>(d, X, nrhs, ld, 1, s);
+  else level_solve<double>(d, X, nrhs, ld, 1, s);
 }
 
 }  // namespace spalu

@@ -94,19 +94,22 @@ struct LevelPlan {          // host-side description of level l (1..L)
 // Device view of one level, passed by value to the kernels.
 struct LevelDev {
   int l, nx, ny, vcut;
+  int fp32;         // real arrays below hold FP32 (mixed mode) instead of FP64
   Geo g, gp;
   int capS, ldF, ldFp, Ycap, sepcap;
-  double* F;        // depth-l frontals: nbox * ldF * ldF
-  double* Fp;       // depth-(l-1) frontals (merge target): gp.nbox * ldFp * ldFp
+  void* F;          // depth-l frontals: nbox * ldF * ldF
+  void* Fp;         // depth-(l-1) frontals (merge target): gp.nbox * ldFp * ldFp
   int* cnt;         // [nseg] unknowns per segment before compression
   int* kk;          // [nseg] skeleton size
   int* hs;          // [nseg] final sketch size (statistics)
   int* nodes;       // [nseg * capS] grid nodes in pre-ID order
   int* perm;        // [nseg * capS] column order of the ID (first kk = skeleton)
   int* piv;         // [nseg * capS] pivots of the remainder LU
-  double* T;        // [nseg * capS * capS] interpolation matrices, k x (e-k), ld capS
-  double* Dm;       // [nseg * capS * capS] [A_ss' | Z ; W | LU(A_rr)], ld capS
-  double* Yg;       // global sketch scratch (nseg * Ycap * capS) or null
+  void* T;          // [nseg * capS * capS] interpolation matrices, k x (e-k), ld capS
+  void* Dm;         // [nseg * capS * capS] [A_ss' | Z ; W | LU(A_rr)], ld capS
+  void* Dinv;       // [nseg * capS] reciprocal pivots of U(A_rr)
+  void* Yg;         // global sketch scratch (nseg * Ycap * capS) or null
+  void* Pinv;       // [gp.nbox * sepcap] reciprocal pivots of the separator U
   int* ptab;        // merge tables: gp.nbox * ldFp * 8 ints
   int* pcount;      // [gp.nbox * 2]: unknowns of dP, skeleton size of the separator
   int* ppiv;        // [gp.nbox * sepcap] pivots of the separator LU
@@ -122,11 +125,15 @@ struct LevelDev {
 
 struct LeafDev {
   int nx, ny, L;
+  int fp32;         // factors, frontals and solves in FP32 (the LU itself stays FP64)
   Geo g;            // depth-L tiling (leaf boxes, 15 x 15)
   int ldF;          // = g.D()
-  double* F;        // depth-L frontals
-  double* band;     // [nbox * LDAB * 225] band LU of the leaf interiors
+  void* F;          // depth-L frontals (FP64 or FP32)
+  void* band;       // [nbox * LDAB * 225] band LU of the leaf interiors (FP64 or FP32)
+  void* invd;       // [nbox * 225] reciprocal pivots of U
+  void* ybuf;       // [nbox * 225 * 64] intermediate vectors of the band sweeps
   int* piv;         // [nbox * 225]
+  int* kumax;       // largest upper bandwidth of U produced by the interchanges
   const int* rowptr;
   const int* colind;
   const double* val;
@@ -151,15 +158,14 @@ void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
 struct SolveLevel {           // device pointers the solve needs for one level
   LevelDev d;
 };
-void launch_leaf_solve_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s);
+cudaError_t leaf_init_tables();
+void launch_leaf_solve(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s);
 void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s);
-void launch_leaf_solve_bwd(const LeafDev& d, double* X, int nrhs, int ld, double* tmp,
-                           cudaStream_t s);
 void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s);
 void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s);
 
-size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over);
-size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over);
+size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes);
+size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes);
 
 spalu_status residual_noalloc(int n, const int* rowptr, const int* colind, const double* val,
                               const double* B, const double* X, int nrhs, int ld, double* relres,

@@ -178,3 +178,31 @@ def test_full_size_diffusion_1023_refined():
     assert np.all(res <= 1e-10), res
     st = f.stats()
     assert st["L"] == 12 and st["q_tilde"] <= 1.0
+
+
+# ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("kind,n,eps", [("diffusion", 127, 1e-6), ("diffusion", 255, 1e-6),
+                                        ("convdiff", 127, 1e-6), ("laplace", 127, 1e-6),
+                                        ("helmholtz", 63, 1e-6)])
+def test_mixed_precision_refined(kind, n, eps):
+    """Mixed mode (FP32 factors / solve, FP64 leaf LU, FP64 QR pivots and norms) refined by
+    GMRES with an FP64 residual to 1e-10; the direct solve's error against the FP64 oracle
+    at the same tolerance is stated (printed) and bounded."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    P = W.make_problem(kind, n, seed=28, nrhs=2)
+    rp, ci, va, B = _dev(P)
+    nd = NestedDissection(n)
+    f = Factor(nd, eps_id=eps, symmetric=1 if P.symmetric else 0, precision=1)
+    f.factor(rp, ci, va)
+    X = f.solve(B)
+    torch.cuda.synchronize()
+    x0 = X.cpu().numpy().T
+    Xo = osolve(ofactor(P.A, nested_dissection(n, n), OOpts(eps=eps, symmetric=P.symmetric)), P.B)
+    err = np.linalg.norm(x0 - Xo) / np.linalg.norm(Xo)
+    print(f"mixed {kind} {n}: direct-solve error vs FP64 oracle {err:.2e}")
+    assert err <= 1e-2
+    it, rel = f.refine(B, X)
+    torch.cuda.synchronize()
+    x = X.cpu().numpy().T
+    res = np.linalg.norm(P.B - P.A.matvec(x), axis=0) / np.linalg.norm(P.B, axis=0)
+    assert np.all(res <= 1e-10), res
