@@ -100,6 +100,8 @@ struct spalu_factor_s {
   std::vector<int> host_rowptr_cache;
   PhaseTimer timer;
   int kumax = 30;            // upper bandwidth of the leaf U factors (read after each factor)
+  int* d_lmax = nullptr;     // [4 * (L + 1)] per-level maxima {e, kp, |dP|, -} (factor kernels)
+  std::vector<SolveCaps> caps;   // [1..L] solve-kernel capacities from the last factor
 };
 
 namespace {
@@ -196,16 +198,15 @@ __global__ void axpy_kernel(int n, int nrhs, double alpha, const double* coef, c
   }
 }
 
-// y[:, c] = x[:, c] / s[c] (zero when s[c] == 0)
+// y[:, c] = x[:, c] / s[c] (zero when s[c] == 0); blockIdx.y = column, one reciprocal per thread
 __global__ void scale_kernel(int n, int nrhs, const double* s, const double* x, int ldx, double* y,
                              int ldy) {
-  long long tot = (long long)n * nrhs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(e % n), c = (int)(e / n);
-    double d = s[c];
-    y[r + (size_t)ldy * c] = d != 0.0 ? x[r + (size_t)ldx * c] / d : 0.0;
-  }
+  const int c = blockIdx.y;
+  const double d = s[c];
+  const double di = d != 0.0 ? 1.0 / d : 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x)
+    y[r + (size_t)ldy * c] = x[r + (size_t)ldx * c] * di;
 }
 
 __global__ void copy_cols_kernel(int n, int nrhs, const double* x, int ldx, double* y, int ldy) {
@@ -379,6 +380,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     Carver cv;
     cv.base = pass ? f->arena : nullptr;
     f->d_err = cv.take<int>(4);
+    f->d_lmax = cv.take<int>((size_t)4 * (L + 1));
     f->rowptr = cv.take<int>(f->N + 1);
     f->colind = cv.take<int>(f->nnz_cap);
     f->val = cv.take<double>(f->nnz_cap);
@@ -441,7 +443,11 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   f->leaf.colind = f->colind;
   f->leaf.val = f->val;
   f->leaf.err = f->d_err;
-  for (int l = 1; l <= L; ++l) f->lev[l].err = f->d_err;
+  for (int l = 1; l <= L; ++l) {
+    f->lev[l].err = f->d_err;
+    f->lev[l].lmax = f->d_lmax + 4 * l;
+  }
+  f->caps.resize(L + 1);
   *out = f;
   return SPALU_OK;
 }
@@ -452,6 +458,7 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   int t_all = tm.begin("factor", s);
   CUDA_TRY(cudaMemsetAsync(f->d_err, 0, sizeof(int), s));
   CUDA_TRY(cudaMemsetAsync(f->leaf.kumax, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(f->d_lmax, 0, sizeof(int) * 4 * (L + 1), s));
   if (L >= 1) launch_level_init_L(f->lev[L], s);
   int t = tm.begin("leaf_factor", s);
   launch_leaf_factor(f->leaf, s);
@@ -470,6 +477,12 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   int ku = 30;
   if (cudaMemcpy(&ku, f->leaf.kumax, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SPALU_ERR_CUDA;
   f->kumax = ku;
+  std::vector<int> lm((size_t)4 * (L + 1));
+  if (cudaMemcpy(lm.data(), f->d_lmax, sizeof(int) * lm.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SPALU_ERR_CUDA;
+  // the solve kernels hold a segment's (or separator's) right-hand-side block in shared memory
+  for (int l = 1; l <= L && st == SPALU_OK; ++l)
+    if (!level_solve_caps(f->lev[l], lm.data() + 4 * l, &f->caps[l])) st = SPALU_ERR_UNSUPPORTED;
   f->factored = (st == SPALU_OK);
   f->last_stream = s;
   return st;
@@ -521,8 +534,8 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
   if (L >= 1) launch_sep_update_fwd(f->leaf, X, nrhs, ld, s);
   tm.end(t, s);
   t = tm.begin("level_solve", s);
-  for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], X, nrhs, ld, s);
-  for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], X, nrhs, ld, s);
+  for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], f->caps[l], X, nrhs, ld, s);
+  for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], f->caps[l], X, nrhs, ld, s);
   tm.end(t, s);
   t = tm.begin("leaf_solve_bwd", s);
   launch_leaf_solve(f->leaf, X, nrhs, ld, 1, f->kumax, s);
@@ -616,7 +629,7 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     for (int c = 0; c < nrhs; ++c) bsc[c] = done(c) ? 0.0 : beta[c];
     CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, bsc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     note_launch();
-    scale_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, dvec + nrhs, w.R, (int)ldv, Vj(0), (int)ldv);
+    scale_kernel<<<dim3(grid_for(N) / nrhs + 1, nrhs), 256, 0, s>>>(N, nrhs, dvec + nrhs, w.R, (int)ldv, Vj(0), (int)ldv);
     for (int c = 0; c < nrhs; ++c) {
       std::fill(H[c].begin(), H[c].end(), 0.0);
       std::fill(g[c].begin(), g[c].end(), 0.0);
@@ -638,7 +651,7 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
       }
       dots(f, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv, nrhs, w.hcol + (size_t)(j + 1) * nrhs, 1, s);
       note_launch();
-      scale_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, w.hcol + (size_t)(j + 1) * nrhs, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
+      scale_kernel<<<dim3(grid_for(N) / nrhs + 1, nrhs), 256, 0, s>>>(N, nrhs, w.hcol + (size_t)(j + 1) * nrhs, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
       CUDA_TRY(cudaMemcpyAsync(hh.data(), w.hcol, sizeof(double) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
       ++it;
@@ -748,8 +761,8 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
     }
     if (emax > 0) qt = std::max(qt, (double)kmax / emax);
     char buf[256];
-    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld}",
-                  l == 1 ? "" : ", ", l, n, emax, kmax, esum, ksum);
+    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld, \"sep_k_max\": %d}",
+                  l == 1 ? "" : ", ", l, n, emax, kmax, esum, ksum, f->caps[l].yrows);
     out += buf;
   }
   char buf[64];

@@ -66,19 +66,24 @@ __device__ __forceinline__ double csr_entry(const int* rowptr, const int* colind
 __constant__ int c_qorder[NQ];
 __constant__ int c_qstart[2];   // first sweep step of the two solve warps of a leaf
 
-template <typename T>
-struct Band {                   // read-only view of one leaf's factors in precision T
-  const T* ab;                  // LDAB x NI
-  const int* piv;
-  const T* invd;
-  __device__ __forceinline__ T l(int r, int j) const { return ab[(KV + r) + LDAB * j]; }   // L(j+r, j)
-  __device__ __forceinline__ T u(int r, int j) const { return ab[(KV - r) + LDAB * j]; }   // U(j-r, j)
+// Read-only view of one leaf's factors in precision T: RO = true reads global memory through
+// the read-only path (factors written by an earlier kernel); false reads plain (shared) memory.
+template <typename T, bool RO>
+struct Band {
+  const T* __restrict__ ab;     // LDAB x NI
+  const int* __restrict__ piv;
+  const T* __restrict__ invd;
+  __device__ __forceinline__ T ld(const T* q) const { if constexpr (RO) return __ldg(q); else return *q; }
+  __device__ __forceinline__ T l(int r, int j) const { return ld(ab + (KV + r) + LDAB * j); }   // L(j+r, j)
+  __device__ __forceinline__ T u(int r, int j) const { return ld(ab + (KV - r) + LDAB * j); }   // U(j-r, j)
+  __device__ __forceinline__ int p(int j) const { if constexpr (RO) return __ldg(piv + j); else return piv[j]; }
+  __device__ __forceinline__ T dinv(int j) const { return ld(invd + j); }
 };
 
 // Forward sweep y = L^{-1} P x for one column held by this thread.  in(j) gives x_j,
 // out(j, y) receives y_j for j = j0..NI-1 (x_j = 0 for j < j0 is assumed).
-template <typename T, class In, class Out>
-__device__ __forceinline__ void sweep_L(const Band<T>& B, int j0, In in, Out out) {
+template <typename T, class BandT, class In, class Out>
+__device__ __forceinline__ void sweep_L(const BandT& B, int j0, In in, Out out) {
   T W[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) W[r] = (j0 + r < NI) ? in(j0 + r) : T(0);
@@ -87,7 +92,7 @@ __device__ __forceinline__ void sweep_L(const Band<T>& B, int j0, In in, Out out
     for (int u = 0; u < 16; ++u) {
       const int j = j0 + t0 + u;
       if (j < NI) {
-        const int dsw = B.piv[j] - j;   // 0..15: the interchange stays in the window
+        const int dsw = B.p(j) - j;     // 0..15: the interchange stays in the window
         T a = W[u], b = a;
 #pragma unroll
         for (int r = 1; r < 16; ++r)
@@ -104,8 +109,8 @@ __device__ __forceinline__ void sweep_L(const Band<T>& B, int j0, In in, Out out
 
 // Backward sweep x = U^{-1} y (upper bandwidth < KUW) for one column: in(j) gives y_j,
 // out(j, x) receives x_j for j = NI-1 .. 0.
-template <typename T, int KUW, class In, class Out>
-__device__ __forceinline__ void sweep_U(const Band<T>& B, In in, Out out) {
+template <typename T, int KUW, class BandT, class In, class Out>
+__device__ __forceinline__ void sweep_U(const BandT& B, In in, Out out) {
   T V[KUW];
 #pragma unroll
   for (int r = 0; r < KUW; ++r) V[r] = (NI - 1 - r >= 0) ? in(NI - 1 - r) : T(0);
@@ -116,7 +121,7 @@ __device__ __forceinline__ void sweep_U(const Band<T>& B, In in, Out out) {
       const int t = t0 + u;
       if (t < NI) {
         const int j = NI - 1 - t;
-        const T x = V[u] * B.invd[j];
+        const T x = V[u] * B.dinv(j);
         out(j, x);
 #pragma unroll
         for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= B.u(r, j) * x;
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(FTH) leaf_factor_kernel(LeafDev d) {
   __shared__ int shv[LPC][4];
   __shared__ double qa[LPC][NQ], qc[LPC][NQ];
   __shared__ int qm[LPC][NQ], qex[LPC][NQ];
+  __shared__ double sinv[LPC * NI];
   const int sub = threadIdx.x / 64;                 // which leaf of the pair
   const int tid = threadIdx.x % 64;
   const int b = blockIdx.x * LPC + sub;
@@ -242,22 +248,35 @@ __global__ void __launch_bounds__(FTH) leaf_factor_kernel(LeafDev d) {
   // factors kept for the solve, in precision T, plus the reciprocal pivots
   T* bandg = reinterpret_cast<T*>(d.band) + (size_t)(live ? b : 0) * LDAB * NI;
   T* invg = reinterpret_cast<T*>(d.invd) + (size_t)(live ? b : 0) * NI;
+  T* invs = reinterpret_cast<T*>(sinv) + sub * NI;
+  for (int i = tid; i < NI; i += 64) invs[i] = (T)(1.0 / ab(AB, i, i));
   if (live) {
     for (int i = tid; i < LDAB * NI; i += 64) bandg[i] = (T)AB[i];
     for (int i = tid; i < NI; i += 64) {
       d.piv[(size_t)b * NI + i] = piv[i];
-      invg[i] = (T)(1.0 / ab(AB, i, i));
+      invg[i] = invs[i];
     }
     if (tid == 0) atomicMax(d.kumax, kureach);
   }
   __syncthreads();
+  // the band in precision T for the sweeps, converted in place (front of the same buffer)
+  T* ABt = reinterpret_cast<T*>(AB);
+  if constexpr (sizeof(T) < sizeof(double)) {
+    for (int c0 = 0; c0 < LDAB * NI; c0 += 64) {
+      const int i = c0 + tid;
+      const double v = i < LDAB * NI ? AB[i] : 0.0;
+      __syncthreads();
+      if (i < LDAB * NI) ABt[i] = (T)v;
+      __syncthreads();
+    }
+  }
   const bool active = live && ok;     // no early exit: every thread reaches every barrier
 
   // Schur complement: one thread per side unknown q (lanes sorted by interior neighbour)
   if (active && tid < NQ) {
     const int q = c_qorder[tid];
     const int j0 = c_qstart[tid >> 5];
-    Band<T> Bd{bandg, d.piv + (size_t)b * NI, invg};
+    Band<T, false> Bd{ABt, piv, invs};
     T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
     const int mq = qm[sub][q];
     const T cq = qex[sub][q] ? (T)qc[sub][q] : T(0);
@@ -323,8 +342,8 @@ __global__ void __launch_bounds__(128) leaf_solve_kernel(LeafDev d, double* X, i
   const int I = b % d.g.bx, J = b / d.g.bx;
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
-  Band<T> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
-             reinterpret_cast<const T*>(d.invd) + (size_t)b * NI};
+  Band<T, true> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
+                   reinterpret_cast<const T*>(d.invd) + (size_t)b * NI};
   T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
   double* Xc = X + (size_t)ld * c;
   auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };

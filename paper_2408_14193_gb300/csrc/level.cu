@@ -34,6 +34,7 @@ constexpr int RUN_MAX = 16;
 constexpr int SK_CHUNK = 16;      // far unknowns per chunk of the sketch product
 constexpr int NW = 8;             // warps per CTA of the sparsify kernel
 constexpr double TIE_RTOL = 1e-12;
+constexpr int RSTAGE = 96;        // triangular blocks up to this order are staged in shared memory
 
 // ------------------------------------------------------------ Philox4x32-10 (SC'11)
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -175,25 +176,31 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 
 // ------------------------------------------------------------ column-pivoted QR
 // Businger-Golub Householder QR with column pivoting of Y (m x e, ld ldy, precision T),
-// stopped at the first step i with |R_ii| <= eps |R_00|.  Norms, pivot choice and the
-// truncation test in FP64; Householder products in T.  perm receives the column order; on
-// exit the first k rows of Y hold [R_1 R_2] in the permuted order.  Returns k.
-// sh: >= NW*32 + 3*64 doubles of shared scratch; flags: >= e ints.
+// stopped at the first step i with |R_ii| <= eps |R_00|.  Column norms are tracked and
+// downdated in FP64 (with the Drmac-Bujanovic recomputation guard) and the pivot is chosen
+// from them; the Householder products and their column sums run in T.  perm receives the
+// column order; on exit the first k rows of Y hold [R_1 R_2] in the permuted order.
+// Returns k.  sh: >= NW*32 + 3*64 doubles of shared scratch; flags, ivn2: >= e entries.
 template <typename T>
 __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1,
-                          double* vn2, double* sh, int* flags, int* shi) {
+                          double* vn2, double* ivn2, double* sh, int* flags, int* shi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* part = sh;                    // [NW][32] partial dots
-  T* coef = reinterpret_cast<T*>(sh + NW * 32);   // [64]
-  double* scal = sh + NW * 32 + 64;     // alpha, v0, c2, normx
+  T* part = reinterpret_cast<T*>(sh);                   // [NW][32] partial dots
+  T* coef = reinterpret_cast<T*>(sh + NW * 32);         // [64]
+  double* scal = sh + NW * 32 + 64;                     // alpha, v0, c2, normx
   for (int j = threadIdx.x; j < e; j += blockDim.x) perm[j] = j;
   if (m == 0 || e == 0) { __syncthreads(); return 0; }
-  // initial column norms (one warp per column, FP64 accumulation)
+  // initial column norms (one warp per column)
   for (int j = warp; j < e; j += NW) {
-    double s = 0.0;
-    for (int r = lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * j]; s += v * v; }
+    T s = T(0);
+    for (int r = lane; r < m; r += 32) { T v = Y[r + (size_t)ldy * j]; s += v * v; }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) { vn1[j] = sqrt(s); vn2[j] = vn1[j]; }
+    if (lane == 0) {
+      const double nv = sqrt((double)s);
+      vn1[j] = nv;
+      vn2[j] = nv;
+      ivn2[j] = nv > 0.0 ? 1.0 / nv : 0.0;
+    }
   }
   __syncthreads();
   const double tol3z = sqrt(DBL_EPSILON);
@@ -201,7 +208,11 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
   double ref = 0.0;
   int k = kmax;
   for (int i = 0; i < kmax; ++i) {
-    if (warp == 0) {          // pivot: largest norm, near-ties -> lowest index
+    // the per-step scalar tasks rotate over the warps (and CTAs), so that the FP64 work of
+    // co-resident CTAs does not pile up on one SM sub-partition
+    const int wp = (i + blockIdx.x) % NW, wh = (i + 1 + blockIdx.x) % NW;
+    const int wr = (i + 2 + blockIdx.x) % NW, wd = (i + 3 + blockIdx.x) % NW;
+    if (warp == wp) {         // pivot: largest norm, near-ties -> lowest index
       long long mx = -1;
       for (int j = i + lane; j < e; j += 32) mx = max(mx, dbits(vn1[j]));
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -224,24 +235,25 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
         int t = perm[i]; perm[i] = perm[p]; perm[p] = t;
         double a = vn1[i]; vn1[i] = vn1[p]; vn1[p] = a;
         a = vn2[i]; vn2[i] = vn2[p]; vn2[p] = a;
+        a = ivn2[i]; ivn2[i] = ivn2[p]; ivn2[p] = a;
       }
       __syncthreads();
     }
-    // Householder vector of column i: FP64 norm, scalars by one thread
-    if (warp == 0) {
-      double s = 0.0;
-      for (int r = i + lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * i]; s += v * v; }
+    // Householder vector of column i (scalars by one thread)
+    if (warp == wh) {
+      T s = T(0);
+      for (int r = i + lane; r < m; r += 32) { T v = Y[r + (size_t)ldy * i]; s += v * v; }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) {
-        const double normx = sqrt(s);
-        const double x0 = (double)Y[i + (size_t)ldy * i];
-        const double alpha = x0 >= 0.0 ? -normx : normx;
-        const double v0 = x0 - alpha;
-        const double vv = v0 * v0 + (s - x0 * x0);
-        scal[0] = alpha;
-        scal[1] = v0;
-        scal[2] = vv > 0.0 ? 2.0 / vv : 0.0;
-        scal[3] = normx;
+        const T normx = sqrt(s);
+        const T x0 = Y[i + (size_t)ldy * i];
+        const T alpha = x0 >= T(0) ? -normx : normx;
+        const T v0 = x0 - alpha;
+        const T vv = v0 * v0 + (s - x0 * x0);
+        scal[0] = (double)alpha;
+        scal[1] = (double)v0;
+        scal[2] = vv > T(0) ? (double)(T(2) / vv) : 0.0;
+        scal[3] = (double)normx;
       }
     }
     __syncthreads();
@@ -252,7 +264,7 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
     const T v0 = (T)scal[1];
     const T c2 = (T)scal[2];
     const int ncol = e - i - 1;
-    // dots of v with the trailing columns: lanes over columns, warps over rows
+    // dots of v with the trailing columns (lanes over columns, warps over rows), then update
     for (int cg = 0; cg < ncol; cg += 32) {
       const int j = i + 1 + cg + lane;
       T acc = T(0);
@@ -262,17 +274,16 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
         if (warp == 0) acc = v0 * yj[i];
         for (int r = i + 1 + warp; r < m; r += NW) acc += yi[r] * yj[r];
       }
-      part[warp * 32 + lane] = (double)acc;
+      part[warp * 32 + lane] = acc;
       __syncthreads();
-      if (warp == 0 && j < e) {
-        double s = 0.0;
+      if (warp == wr && j < e) {
+        T s = T(0);
         for (int w = 0; w < NW; ++w) s += part[w * 32 + lane];
-        coef[(cg + lane) & 63] = (T)s * c2;
+        coef[lane] = s * c2;
       }
       __syncthreads();
-      // update of this group of trailing columns
       if (j < e) {
-        const T cj = coef[(cg + lane) & 63];
+        const T cj = coef[lane];
         T* yj = Y + (size_t)ldy * j;
         const T* yi = Y + (size_t)ldy * i;
         if (warp == 0) yj[i] -= cj * v0;
@@ -281,14 +292,15 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
       __syncthreads();
     }
     // FP64 norm downdates, one lane per column; the guarded recomputations afterwards
-    if (warp == 0) {
+    if (warp == wd) {
       for (int j = i + 1 + lane; j < e; j += 32) {
         const double nv = vn1[j];
         int fl = 0;
         if (nv != 0.0) {
-          const double q = fabs((double)Y[i + (size_t)ldy * j]) / nv;
+          const double inv = 1.0 / nv;
+          const double q = fabs((double)Y[i + (size_t)ldy * j]) * inv;
           const double temp = fmax(1.0 - q * q, 0.0);
-          const double r2 = nv / vn2[j];
+          const double r2 = nv * ivn2[j];
           const double temp2 = temp * r2 * r2;
           if (temp2 <= tol3z) fl = 1;
           else vn1[j] = nv * sqrt(temp);
@@ -302,7 +314,12 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
       double s = 0.0;
       for (int r = i + 1 + lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * j]; s += v * v; }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) { vn1[j] = sqrt(s); vn2[j] = vn1[j]; }
+      if (lane == 0) {
+        const double nv = sqrt(s);
+        vn1[j] = nv;
+        vn2[j] = nv;
+        ivn2[j] = nv > 0.0 ? 1.0 / nv : 0.0;
+      }
     }
     if (threadIdx.x == 0) Y[i + (size_t)ldy * i] = (T)scal[0];
     __syncthreads();
@@ -397,6 +414,7 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
   const int e = S.e;
   const int capS = d.capS;
   int* perm_out = d.perm + (size_t)sid * capS;
+  if (threadIdx.x == 0) atomicMax(d.lmax, e);
   if (e == 0) {
     if (threadIdx.x == 0) { d.kk[sid] = 0; d.hs[sid] = 0; }
     return;
@@ -453,7 +471,7 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
   // working storage: vectors and sketch chunks in shared memory; Y, D, T too when they
   // fit, else the global scratch of this segment
   const size_t TD = sizeof(T);
-  const size_t small_b = (2 * (size_t)e) * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * TD + 64;
+  const size_t small_b = (3 * (size_t)e) * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * TD + 64;
   const size_t per_ch_b = (size_t)halves * (e + hmax) * TD;
   const size_t ydt_b = ((size_t)mmax * e + 2 * (size_t)e * e) * TD;
   int ch = SK_CHUNK;
@@ -464,13 +482,14 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
     if (ch < 1) { ch = 1; if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); }
   }
   T *Y, *Dw, *Tw, *Bc, *Gc, *rinv;
-  double *vn1, *vn2;
+  double *vn1, *vn2, *ivn2;
   int *perm, *piv, *flags;
   int ldy, ldd, ldt;
   {
     char* q = reinterpret_cast<char*>(sm);
     vn1 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
     vn2 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
+    ivn2 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
     perm = reinterpret_cast<int*>(q); q += (size_t)e * 4;
     piv = reinterpret_cast<int*>(q); q += (size_t)e * 4;
     flags = reinterpret_cast<int*>(q); q += ((size_t)e + 4) * 4;
@@ -568,7 +587,7 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
       for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
     }
     __syncthreads();
-    k = block_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
+    k = block_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, ivn2, shr, flags, shi);
     if (!full && k > h - d.p_over && h < nF) {
       h = min(2 * h, nF);
       __syncthreads();
@@ -762,6 +781,8 @@ __global__ void merge_table_kernel(LevelDev d) {
   }
   d.pcount[2 * P] = ndP;
   d.pcount[2 * P + 1] = C.kp;
+  atomicMax(d.lmax + 1, C.kp);
+  atomicMax(d.lmax + 2, ndP);
 }
 
 // M[a][b] = sum over the children holding both unknowns of the child's block, where the
@@ -971,84 +992,158 @@ __global__ void seg_merge_kernel(LevelDev d) {
 }
 
 // ------------------------------------------------------------ solve
+constexpr int SC = 16;      // right-hand sides per solve pass (register accumulators per thread)
+constexpr int DCAP = 512;   // parent boundaries up to this size are staged in shared memory
+
+// out(a, acc) for a < nout with acc[c] = sum_j A(a, j) v[j + ldv c], c < SC: one thread per
+// output row, the matrix row read once (coalesced across rows for column-major panels) and
+// reused for all right-hand sides, which are read from shared memory by broadcast.
+template <typename T, class Row, class Out>
+__device__ __forceinline__ void gemv_rows(int nout, int nin, Row row, size_t sj, const T* v, int ldv, Out out) {
+  for (int a = threadIdx.x; a < nout; a += blockDim.x) {
+    T acc[SC];
+#pragma unroll
+    for (int c = 0; c < SC; ++c) acc[c] = T(0);
+    const T* Aa = row(a);   // global or shared memory: plain (generic) loads
+#pragma unroll 4
+    for (int j = 0; j < nin; ++j) {
+      const T w = Aa[j * sj];
+#pragma unroll
+      for (int c = 0; c < SC; ++c) acc[c] += w * v[j + ldv * c];
+    }
+    out(a, acc);
+  }
+}
+
+// Triangular sweeps on the SC columns held in shared memory (one warp per column).
+template <typename T>
+__device__ __forceinline__ void lower_sweep(T* y, int ldy, int n, const T* LU, size_t ldl, const int* pv, int nc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    T* yy = y + (size_t)ldy * c;
+    for (int j = 0; j < n; ++j) {
+      const int p = pv[j];
+      __syncwarp();
+      if (p != j && lane == 0) { T t = yy[j]; yy[j] = yy[p]; yy[p] = t; }
+      __syncwarp();
+      const T yj = yy[j];
+      for (int i = j + 1 + lane; i < n; i += 32) yy[i] -= LU[i + ldl * j] * yj;
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void upper_sweep(T* y, int ldy, int n, const T* LU, size_t ldl, const T* iv, int nc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    T* yy = y + (size_t)ldy * c;
+    for (int j = n - 1; j >= 0; --j) {
+      __syncwarp();
+      const T yj = yy[j] * iv[j];
+      __syncwarp();
+      if (lane == 0) yy[j] = yj;
+      for (int i = lane; i < j; i += 32) yy[i] -= LU[i + ldl * j] * yj;
+    }
+    __syncwarp();
+  }
+}
+
+
+template <typename T>
+__device__ __forceinline__ void gather_panel(T* dst, int nr, int ncl, const T* src, size_t ldsrc,
+                                             const int* rowidx, size_t colbase) {
+  // dst[i + nr * j] = src[rowidx(i) + ldsrc * (colbase + j)]; independent loads, coalesced per column
+  for (int x = threadIdx.x; x < nr * ncl; x += blockDim.x) {
+    const int i = x % nr, j = x / nr;
+    dst[x] = src[(size_t)rowidx[i] + ldsrc * (colbase + j)];
+  }
+}
+
 // Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
 template <typename T>
-__global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, double* X, int nrhs, int ld, int bwd) {
+__global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd) {
   extern __shared__ double smd[];
-  T* v = reinterpret_cast<T*>(smd);   // e x nrhs: [skeleton | remainder] order
   const int sid = blockIdx.x;
   const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
   if (r == 0 || e == 0) return;
+  if (e > cap.vrows) { if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); return; }
   const int capS = d.capS;
+  T* v = reinterpret_cast<T*>(smd);                      // e x SC, [skeleton | remainder]
+  T* LUsm = v + (size_t)cap.vrows * SC;                  // r x r LU (when r <= lucap)
+  T* Psm = LUsm + (size_t)cap.lucap * cap.lucap;         // two k x r panels (when k r <= pcap)
+  T* invs = Psm + 2 * (size_t)cap.pcap;
+  int* pivs = reinterpret_cast<int*>(invs + cap.lucap);
+  const bool staged = r <= cap.lucap;
+  const bool pstaged = (size_t)k * r <= (size_t)cap.pcap;
   const int* perm = d.perm + (size_t)sid * capS;
   const int* nodes = d.nodes + (size_t)sid * capS;
   const int* piv = d.piv + (size_t)sid * capS;
   const T* Tm = static_cast<const T*>(d.T) + (size_t)sid * capS * capS;
-  const T* Dm = static_cast<const T*>(d.Dm) + (size_t)sid * capS * capS;
+  const T* Dg = static_cast<const T*>(d.Dm) + (size_t)sid * capS * capS;
   const T* inv = static_cast<const T*>(d.Dinv) + (size_t)sid * capS;
-  for (int x = threadIdx.x; x < e * nrhs; x += blockDim.x) {
+  for (int x = threadIdx.x; x < e * SC; x += blockDim.x) {
     int a = x % e, c = x / e;
-    v[x] = (T)X[nodes[perm[a]] + (size_t)ld * c];
+    v[x] = c < nc ? (T)X[nodes[perm[a]] + (size_t)ld * c] : T(0);
+  }
+  if (staged) {
+    for (int x = threadIdx.x; x < r * r; x += blockDim.x)
+      LUsm[x] = Dg[(k + x % r) + (size_t)capS * (k + x / r)];
+    for (int x = threadIdx.x; x < r; x += blockDim.x) { invs[x] = inv[x]; pivs[x] = piv[x]; }
+  }
+  // panels: T (k x r, ld capS) and Z = D[0:k, k:e] (forward) or W = D[k:e, 0:k] (backward)
+  T* Ts = Psm;              // k x r, ld k
+  T* Ps = Psm + cap.pcap;   // forward: Z as k x r (ld k); backward: W as r x k (ld r)
+  if (pstaged && k > 0) {
+    for (int x = threadIdx.x; x < k * r; x += blockDim.x) {
+      const int i = x % k, j = x / k;
+      Ts[x] = Tm[i + (size_t)capS * j];
+      if (!bwd) Ps[x] = Dg[i + (size_t)capS * (k + j)];
+    }
+    if (bwd)
+      for (int x = threadIdx.x; x < r * k; x += blockDim.x) Ps[x] = Dg[(k + x % r) + (size_t)capS * (x / r)];
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const T* LUs = staged ? LUsm : Dg + k + (size_t)capS * k;
+  const size_t ldl = staged ? (size_t)r : (size_t)capS;
+  const T* ivs = staged ? invs : inv;
+  const int* pvs = staged ? pivs : piv;
+  const T* Tp = pstaged ? Ts : Tm;
+  const size_t ldt = pstaged ? (size_t)k : (size_t)capS;
+  T* vs = v;          // skeleton part
+  T* vr = v + k;      // remainder part
   if (!bwd) {
-    for (int x = threadIdx.x; x < r * nrhs; x += blockDim.x) {
-      int a = x % r, c = x / r;
-      T s = T(0);
-      for (int q = 0; q < k; ++q) s += Tm[q + (size_t)capS * a] * v[q + e * c];
-      v[k + a + e * c] -= s;
+    if (k > 0) {      // b_r -= T^T b_s: row a of T^T is column a of T
+      gemv_rows<T>(r, k, [&](int a) { return Tp + ldt * a; }, 1, vs, e,
+                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vr[a + e * c] -= acc[c]; });
+      __syncthreads();
     }
+    lower_sweep<T>(vr, e, r, LUs, ldl, pvs, nc);
     __syncthreads();
-    for (int c = warp; c < nrhs; c += nw) {   // y = L^{-1} P b_r
-      T* y = v + k + e * c;
-      for (int j = 0; j < r; ++j) {
-        int p = piv[j];
-        __syncwarp();
-        if (p != j && lane == 0) { T t = y[j]; y[j] = y[p]; y[p] = t; }
-        __syncwarp();
-        T yj = y[j];
-        for (int i = j + 1 + lane; i < r; i += 32) y[i] -= Dm[(k + i) + (size_t)capS * (k + j)] * yj;
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < k * nrhs; x += blockDim.x) {
-      int a = x % k, c = x / k;
-      T s = T(0);
-      for (int j = 0; j < r; ++j) s += Dm[a + (size_t)capS * (k + j)] * v[k + j + e * c];
-      v[a + e * c] -= s;
+    if (k > 0) {      // b_s -= Z y_r
+      const T* Zp = pstaged ? Ps : Dg + (size_t)capS * k;
+      const size_t ldz = pstaged ? (size_t)k : (size_t)capS;
+      gemv_rows<T>(k, r, [&](int a) { return Zp + a; }, ldz, vr, e,
+                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vs[a + e * c] -= acc[c]; });
     }
   } else {
-    for (int x = threadIdx.x; x < r * nrhs; x += blockDim.x) {
-      int a = x % r, c = x / r;
-      T s = T(0);
-      for (int q = 0; q < k; ++q) s += Dm[(k + a) + (size_t)capS * q] * v[q + e * c];
-      v[k + a + e * c] -= s;
+    if (k > 0) {      // y_r -= W x_s
+      const T* Wp = pstaged ? Ps : Dg + k;
+      const size_t ldw = pstaged ? (size_t)r : (size_t)capS;
+      gemv_rows<T>(r, k, [&](int a) { return Wp + a; }, ldw, vs, e,
+                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vr[a + e * c] -= acc[c]; });
+      __syncthreads();
     }
+    upper_sweep<T>(vr, e, r, LUs, ldl, ivs, nc);
     __syncthreads();
-    for (int c = warp; c < nrhs; c += nw) {   // x_r = U^{-1} (.)
-      T* y = v + k + e * c;
-      for (int j = r - 1; j >= 0; --j) {
-        __syncwarp();
-        const T yj = y[j] * inv[j];
-        __syncwarp();
-        if (lane == 0) y[j] = yj;
-        for (int i = lane; i < j; i += 32) y[i] -= Dm[(k + i) + (size_t)capS * (k + j)] * yj;
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < k * nrhs; x += blockDim.x) {
-      int a = x % k, c = x / k;
-      T s = T(0);
-      for (int j = 0; j < r; ++j) s += Tm[a + (size_t)capS * j] * v[k + j + e * c];
-      v[a + e * c] -= s;
+    if (k > 0) {      // x_s -= T x_r
+      gemv_rows<T>(k, r, [&](int a) { return Tp + a; }, ldt, vr, e,
+                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vs[a + e * c] -= acc[c]; });
     }
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < e * nrhs; x += blockDim.x) {
+  for (int x = threadIdx.x; x < e * nc; x += blockDim.x) {
     int a = x % e, c = x / e;
     X[nodes[perm[a]] + (size_t)ld * c] = (double)v[x];
   }
@@ -1058,70 +1153,109 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, double* X, i
 // at a time: two parents of the same colour share no boundary unknown); backward
 // x_p = U^{-1} (y_p - W x_dP).
 template <typename T>
-__global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, double* X, int nrhs, int ld, int bwd, int colour) {
+__global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd, int colour) {
   extern __shared__ double smd[];
-  T* y = reinterpret_cast<T*>(smd);   // kp x nrhs
   const int P = blockIdx.x;
   const int Ip = P % d.gp.bx, Jp = P / d.gp.bx;
   if (!bwd && ((Ip & 1) + 2 * (Jp & 1)) != colour) return;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
   if (kp == 0) return;
+  if (kp > cap.yrows) { if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); return; }
   const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
   const size_t ldp = d.ldFp;
   const T* M = static_cast<const T*>(d.Fp) + (size_t)P * ldp * ldp;
   const T* inv = static_cast<const T*>(d.Pinv) + (size_t)P * d.sepcap;
   const int Dp = d.gp.D();
   const int* piv = d.ppiv + (size_t)P * d.sepcap;
-  for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
+  const int ub = cap.lucap * cap.lucap > cap.qcap ? cap.lucap * cap.lucap : cap.qcap;
+  T* y = reinterpret_cast<T*>(smd);                     // kp x SC
+  T* U = y + (size_t)cap.yrows * SC;                    // union: LU block / panel
+  T* xd = U + ub;                                       // drows x SC (backward)
+  T* invs = xd + (size_t)cap.drows * SC;
+  int* pivs = reinterpret_cast<int*>(invs + cap.lucap);
+  int* rows_sm = pivs + cap.lucap;                      // 2 * drows
+  const bool staged = kp <= cap.lucap;
+  const bool dstage = ndP <= cap.drows;
+  const bool pstaged = dstage && (size_t)ndP * kp <= (size_t)cap.qcap;
+  if (dstage) {
+    for (int x = threadIdx.x; x < ndP; x += blockDim.x) {
+      rows_sm[x] = tab[(size_t)x * TABW];
+      rows_sm[cap.drows + x] = tab[(size_t)x * TABW + 7];
+    }
+  }
+  __syncthreads();          // rows_sm is read by other threads below
+  auto rowpos = [&](int a) { return dstage ? rows_sm[a] : tab[(size_t)a * TABW]; };
+  auto rownode = [&](int a) { return dstage ? rows_sm[cap.drows + a] : tab[(size_t)a * TABW + 7]; };
+  for (int x = threadIdx.x; x < kp * SC; x += blockDim.x) {
     int a = x % kp, c = x / kp;
-    y[x] = (T)X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c];
+    y[x] = c < nc ? (T)X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] : T(0);
   }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (staged) for (int x = threadIdx.x; x < kp; x += blockDim.x) { invs[x] = inv[x]; pivs[x] = piv[x]; }
+  const size_t ldl = staged ? (size_t)kp : ldp;
+  const T* ivs = staged ? invs : inv;
+  const int* pvs = staged ? pivs : piv;
   if (!bwd) {
-    for (int c = warp; c < nrhs; c += nw) {
-      T* yy = y + kp * c;
-      for (int j = 0; j < kp; ++j) {
-        int p = piv[j];
-        __syncwarp();
-        if (p != j && lane == 0) { T t = yy[j]; yy[j] = yy[p]; yy[p] = t; }
-        __syncwarp();
-        T yj = yy[j];
-        for (int i = j + 1 + lane; i < kp; i += 32) yy[i] -= M[(Dp + i) + ldp * (Dp + j)] * yj;
-      }
-      __syncwarp();
-    }
+    if (staged)
+      for (int x = threadIdx.x; x < kp * kp; x += blockDim.x) U[x] = M[(Dp + x % kp) + ldp * (Dp + x / kp)];
     __syncthreads();
-    for (int x = threadIdx.x; x < ndP * nrhs; x += blockDim.x) {
-      int a = x % ndP, c = x / ndP;
-      size_t row = tab[(size_t)a * TABW];
-      T s = T(0);
-      for (int j = 0; j < kp; ++j) s += M[row + ldp * (Dp + j)] * y[j + kp * c];
-      X[tab[(size_t)a * TABW + 7] + (size_t)ld * c] -= (double)s;
+    lower_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
+    __syncthreads();
+    // b_dP -= Z y_p, Z = M[dP rows, separator columns]
+    if (pstaged) {
+      gather_panel<T>(U, ndP, kp, M, ldp, rows_sm, Dp);
+      __syncthreads();
     }
+    gemv_rows<T>(ndP, kp,
+                 [&](int a) { return pstaged ? U + a : M + rowpos(a) + ldp * Dp; },
+                 pstaged ? (size_t)ndP : ldp, y, kp,
+                 [&](int a, const T* acc) {
+                   double* xa = X + rownode(a);
+                   for (int c = 0; c < nc; ++c) xa[(size_t)ld * c] -= (double)acc[c];
+                 });
   } else {
-    for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
-      int a = x % kp, c = x / kp;
-      T s = T(0);
-      for (int b = 0; b < ndP; ++b)
-        s += M[(Dp + a) + ldp * tab[(size_t)b * TABW]] * (T)X[tab[(size_t)b * TABW + 7] + (size_t)ld * c];
-      y[x] -= s;
+    if (dstage) {
+      for (int x = threadIdx.x; x < ndP * SC; x += blockDim.x) {
+        int b = x % ndP, c = x / ndP;
+        xd[x] = c < nc ? (T)X[rows_sm[cap.drows + b] + (size_t)ld * c] : T(0);
+      }
+    }
+    // W^T panel: Wt[b + ndP j] = M[(Dp + j) + ldp * pos(b)]
+    if (pstaged)
+      for (int x = threadIdx.x; x < ndP * kp; x += blockDim.x) {
+        const int j = x % kp, b = x / kp;
+        U[b + (size_t)ndP * j] = M[(Dp + j) + ldp * rows_sm[b]];
+      }
+    __syncthreads();
+    // y_p -= W x_dP
+    for (int a = threadIdx.x; a < kp; a += blockDim.x) {
+      T acc[SC];
+#pragma unroll
+      for (int c = 0; c < SC; ++c) acc[c] = T(0);
+      if (pstaged) {
+        const T* Wa = U + (size_t)ndP * a;
+#pragma unroll 4
+        for (int b = 0; b < ndP; ++b) {
+          const T w = Wa[b];
+#pragma unroll
+          for (int c = 0; c < SC; ++c) acc[c] += w * xd[b + ndP * c];
+        }
+      } else {
+        for (int b = 0; b < ndP; ++b) {
+          const T w = M[(Dp + a) + ldp * rowpos(b)];
+          const int nb = rownode(b);
+          for (int c = 0; c < nc; ++c) acc[c] += w * (T)X[nb + (size_t)ld * c];
+        }
+      }
+      for (int c = 0; c < SC; ++c) y[a + kp * c] -= acc[c];
     }
     __syncthreads();
-    for (int c = warp; c < nrhs; c += nw) {
-      T* yy = y + kp * c;
-      for (int j = kp - 1; j >= 0; --j) {
-        __syncwarp();
-        const T yj = yy[j] * inv[j];
-        __syncwarp();
-        if (lane == 0) yy[j] = yj;
-        for (int i = lane; i < j; i += 32) yy[i] -= M[(Dp + i) + ldp * (Dp + j)] * yj;
-      }
-      __syncwarp();
-    }
+    if (staged)
+      for (int x = threadIdx.x; x < kp * kp; x += blockDim.x) U[x] = M[(Dp + x % kp) + ldp * (Dp + x / kp)];
+    __syncthreads();
+    upper_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, ivs, nc);
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < kp * nrhs; x += blockDim.x) {
+  for (int x = threadIdx.x; x < kp * nc; x += blockDim.x) {
     int a = x % kp, c = x / kp;
     X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] = (double)y[x];
   }
@@ -1133,14 +1267,14 @@ size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes) 
   const size_t halves = symmetric ? 1 : 2;
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
   const size_t mmax = halves * NEAR_MAX + hcap;
-  const size_t small_b = 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
+  const size_t small_b = 3 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
   return small_b + (SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e) * tbytes;
 }
 
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes) {
   const size_t halves = symmetric ? 1 : 2;
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
-  return 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64 + halves * (e + hcap) * tbytes;
+  return 3 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64 + halves * (e + hcap) * tbytes;
 }
 
 void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
@@ -1196,50 +1330,73 @@ void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   else merge_launch<double>(d, p, s);
 }
 
-static int col_chunk(size_t per_col_bytes) {
-  size_t lim = 96 * 1024;
-  int c = (int)(lim / (per_col_bytes > 0 ? per_col_bytes : 1));
-  return c < 1 ? 1 : c;
+bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
+  auto mn = [](long long a, long long b) { return a < b ? a : b; };
+  auto mx = [](long long a, long long b) { return a > b ? a : b; };
+  const long long TB = d.fp32 ? 4 : 8, budget = 200 * 1024;
+  SolveCaps sc{};
+  sc.vrows = (int)mx(lmax[0], 1);
+  sc.yrows = (int)mx(lmax[1], 1);
+  sc.drows = (int)mn(lmax[2], DCAP);
+  sc.lucap = (int)mn(mx(lmax[0], lmax[1]), RSTAGE);
+  long long seg_fixed = 0, sep_fixed = 0;
+  for (;;) {
+    // segment: v, LU block, reciprocal pivots, pivots (panels come on top)
+    seg_fixed = TB * ((long long)sc.vrows * SC + (long long)sc.lucap * sc.lucap + sc.lucap) + 4LL * sc.lucap + 16;
+    // separator: y, xd, reciprocal pivots, pivots, boundary rows (the LU block / panel union on top)
+    sep_fixed = TB * ((long long)sc.yrows * SC + (long long)sc.drows * SC + sc.lucap) +
+                4LL * (sc.lucap + 2 * sc.drows) + 16;
+    const long long lu = TB * (long long)sc.lucap * sc.lucap;
+    if (seg_fixed <= budget && sep_fixed + lu <= budget) break;
+    if (sc.lucap > 8) sc.lucap /= 2;
+    else if (sc.lucap > 0) sc.lucap = 0;
+    else if (sc.drows > 0) sc.drows /= 2;
+    else return false;              // the right-hand-side blocks alone exceed the budget
+  }
+  // a segment panel is k x r <= (e/2)^2; a separator panel |dP| x kp
+  sc.pcap = (int)mx(0, mn((long long)(sc.vrows / 2 + 1) * (sc.vrows / 2 + 1), (budget - seg_fixed) / (2 * TB)));
+  sc.qcap = (int)mx(0, mn((long long)sc.drows * sc.yrows, (budget - sep_fixed) / TB));
+  sc.seg_smem = (size_t)(seg_fixed + 2 * TB * sc.pcap);
+  sc.sep_smem = (size_t)(sep_fixed + TB * mx((long long)sc.lucap * sc.lucap, sc.qcap));
+  *out = sc;
+  return true;
 }
 
 template <typename T>
-static void level_solve(const LevelDev& d, double* X, int nrhs, int ld, int bwd, cudaStream_t s) {
-  const int cc = col_chunk(sizeof(T) * (size_t)(d.capS > d.sepcap ? d.capS : d.sepcap));
-  for (int c0 = 0; c0 < nrhs; c0 += cc) {
-    const int nc = nrhs - c0 < cc ? nrhs - c0 : cc;
+static void level_solve(const LevelDev& d, const SolveCaps& sc, double* X, int nrhs, int ld, int bwd, cudaStream_t s) {
+  cudaFuncSetAttribute(seg_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.seg_smem);
+  cudaFuncSetAttribute(sep_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.sep_smem);
+  for (int c0 = 0; c0 < nrhs; c0 += SC) {
+    const int nc = nrhs - c0 < SC ? nrhs - c0 : SC;
     double* Xc = X + (size_t)ld * c0;
-    const size_t seg_smem = sizeof(T) * (size_t)d.capS * nc;
-    const size_t sep_smem = sizeof(T) * (size_t)d.sepcap * nc;
-    cudaFuncSetAttribute(seg_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
-    cudaFuncSetAttribute(sep_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sep_smem);
     if (!bwd) {
       if (d.g.nseg() > 0) {
         note_launch();
-        seg_solve_kernel<T><<<d.g.nseg(), 256, seg_smem, s>>>(d, Xc, nc, ld, 0);
+        seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, ld, 0);
       }
       for (int colour = 0; colour < 4; ++colour) {
         note_launch();
-        sep_solve_kernel<T><<<d.gp.nbox(), 256, sep_smem, s>>>(d, Xc, nc, ld, 0, colour);
+        sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, ld, 0, colour);
       }
     } else {
       note_launch();
-      sep_solve_kernel<T><<<d.gp.nbox(), 256, sep_smem, s>>>(d, Xc, nc, ld, 1, 0);
+      sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, ld, 1, 0);
       if (d.g.nseg() > 0) {
         note_launch();
-        seg_solve_kernel<T><<<d.g.nseg(), 256, seg_smem, s>>>(d, Xc, nc, ld, 1);
+        seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, ld, 1);
       }
     }
   }
 }
 
-void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
-  if (d.fp32) level_solve<float>(d, X, nrhs, ld, 0, s);
-  else level_solve<double>(d, X, nrhs, ld, 0, s);
+void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s) {
+  if (d.fp32) level_solve<float>(d, c, X, nrhs, ld, 0, s);
+  else level_solve<double>(d, c, X, nrhs, ld, 0, s);
 }
 
-void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
-  if (d.fp32) level_solve<float>(d, X, nrhs, ld, 1, s);
-  else level_solve<double>(d, X, nrhs, ld, 1, s);
+void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s) {
+  if (d.fp32) level_solve<float>(d, c, X, nrhs, ld, 1, s);
+  else level_solve<double>(d, c, X, nrhs, ld, 1, s);
 }
 
 }  // namespace spalu

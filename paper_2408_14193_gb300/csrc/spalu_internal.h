@@ -121,6 +121,20 @@ struct LevelDev {
   int symmetric, p_over, near_radius, h0;
   unsigned long long seed;
   int* err;
+  int* lmax;        // [3] largest segment size e, separator skeleton kp and parent boundary
+                    // count |dP| met at this level (atomicMax by the factor kernels)
+};
+
+// Shared-memory capacities of the solve kernels of one level, set by the host from the
+// largest sizes the factor met at that level.
+struct SolveCaps {
+  int vrows;     // segment: rows of the right-hand-side block (>= every e of the level)
+  int lucap;     // order up to which a triangular block is staged
+  int pcap;      // segment: elements of each of the two staged panels
+  int qcap;      // separator: elements of the staged boundary panel
+  int drows;     // separator: parent-boundary rows staged
+  int yrows;     // separator: skeleton rows of the right-hand-side block (>= every kp)
+  size_t seg_smem, sep_smem;
 };
 
 struct LeafDev {
@@ -155,14 +169,14 @@ void launch_level_init_L(const LevelDev& d, cudaStream_t s);
 void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
 void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
 
-struct SolveLevel {           // device pointers the solve needs for one level
-  LevelDev d;
-};
 cudaError_t leaf_init_tables();
 void launch_leaf_solve(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s);
 void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s);
-void launch_level_solve_fwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s);
-void launch_level_solve_bwd(const LevelDev& d, double* X, int nrhs, int ld, cudaStream_t s);
+// Capacities for the level-solve kernels from the level maxima {e, kp, |dP|}; false when
+// the right-hand-side blocks alone do not fit in shared memory.
+bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out);
+void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
+void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
 
 size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes);
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes);
