@@ -40,6 +40,7 @@ extern "C" {
 typedef struct CUstream_st* spalu_stream_t;          /* same type as cudaStream_t */
 typedef struct spalu_nd_s* spalu_nd_t;               /* opaque, library-owned */
 typedef struct spalu_factor_s* spalu_factor_t;       /* opaque, library-owned, owns device memory */
+typedef struct spalu_predictor_s* spalu_predictor_t; /* opaque, library-owned, owns device memory */
 
 typedef enum {
   SPALU_OK = 0,
@@ -130,8 +131,10 @@ spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs
 spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
                               int refine, int* iters, double* relres, spalu_stream_t stream);
 
-/* JSON summary of the last factorization: per level the segment sizes and ranks, q~
- * (Sec. 6), device bytes held.  Synchronises the factor's stream. */
+/* JSON summary of the last factorization: per level the segment sizes and ranks, the
+ * largest separator skeleton, the number of IDs computed ("passes"), of predicted one-pass
+ * IDs and of those that fell back to the adaptive schedule; q~ (Sec. 6); device bytes
+ * held.  Synchronises the factor's stream. */
 spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap);
 
 /* Relative residual norms relres[c] = ||B_c - A X_c||_2 / ||B_c||_2 (0 when B_c = 0) of nrhs
@@ -162,6 +165,73 @@ spalu_status spalu_set_timing(spalu_factor_t f, int on);
 unsigned long long spalu_kernel_launches(void);
 
 void spalu_factor_destroy(spalu_factor_t f);
+
+/* ------------------------------------------------------------------------------------
+ * Learned rank predictor.  No counterpart in the paper: the paper finds the rank k of each
+ * segment's ID adaptively (Sec. 4.2.3, sketch size h = k + p with p = 5 and k unknown until
+ * the ID is done).  A 16 -> 64 (ReLU) -> 2 network predicts log2(1 + k) and log2 of the
+ * one-pass sketch size from 16 features of the segment; the factorization then sketches
+ * once with that size and keeps the ID only if k <= h - p and the measured error
+ * ||B_r - B_s T||_F <= 10 eps ||B||_F holds on the exact B, else it continues with the
+ * adaptive doubling.  Features, targets and rules are fixed as follows (row layouts are
+ * float32, row-major):
+ *   features  0 L - l, 1 log2 e, 2 log2(1 + neighbours), 3 near neighbours,
+ *             4 log2(1 + far neighbours), 5-7 min - mean, max - mean, std of log|A_uu| over
+ *             the segment's nodes u, 8 mean log(|A_uu| / sum_{j!=u} |A_uj|), 9 mean
+ *             |row sum| / |A_uu|, 10 mean relative asymmetry of the row's off-diagonal
+ *             entries, 11-15 log10 of |R_jj| / |R_00| (j = 1, 2, 3, 5, 7, floored at
+ *             1e-16) minus log10 eps, from the column-pivoted QR of an 8-row probe sketch
+ *             (the first 8 rows of the sketch matrix) of the far rows;
+ *   targets   y0 = log2(1 + k), y1 = log2(min(far rows, k + p));
+ *   sketch    h = max(ceil(2^o1 (1 + margin)), ceil((2^o0 - 1)(1 + margin)) + p), clamped
+ *             to [1, min(far rows, max(h0, 2 (e + p)))];
+ *   applies   to segments whose far rows exceed max(h0, 8).
+ * Parameter vector (float32, SPALU_PRED_NPARAM): W1 (64 x 16 row-major) | b1 (64) |
+ * W2 (2 x 64) | b2 (2).  Inference rounds the standardised features, the parameters and
+ * the hidden activations to bfloat16 and accumulates in float32. */
+#define SPALU_PRED_NFEAT 16
+#define SPALU_PRED_NPARAM 1218
+
+/* Create a predictor from host parameters (copied); standardisation starts as mean 0,
+ * scale 1.  Errors: SPALU_ERR_ARG (null), SPALU_ERR_ALLOC, SPALU_ERR_CUDA. */
+spalu_status spalu_predictor_create(const float* params, spalu_predictor_t* out);
+/* Copy the FP32 parameters to host memory (SPALU_PRED_NPARAM floats); synchronises. */
+spalu_status spalu_predictor_get_params(spalu_predictor_t p, float* params, spalu_stream_t stream);
+/* Feature standardisation z = (x - mu) * isd: set from / copy to host arrays of 16 floats. */
+spalu_status spalu_predictor_set_norm(spalu_predictor_t p, const float* mu, const float* isd,
+                                      spalu_stream_t stream);
+spalu_status spalu_predictor_get_norm(spalu_predictor_t p, float* mu, float* isd, spalu_stream_t stream);
+/* Fit the standardisation on device rows X (n x 16): mu = column means, isd = 1 / population
+ * standard deviation (1 where it is below 1e-6). */
+spalu_status spalu_predictor_fit_norm(spalu_predictor_t p, const float* X, int n, spalu_stream_t stream);
+/* FP32 loss sum (o - y)^2 / (2n) over device rows X (n x 16), Y (n x 2) and its gradient
+ * (host, SPALU_PRED_NPARAM floats, may be NULL); synchronises. */
+spalu_status spalu_predictor_loss_grad(spalu_predictor_t p, const float* X, const float* Y, int n,
+                                       float* loss, float* grad, spalu_stream_t stream);
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) over consecutive batches of
+ * `batch` rows, `epochs` times, on the device; the step count and moments persist in the
+ * handle across calls.  One epoch is captured once as a CUDA graph and replayed.  loss
+ * (host, may be NULL) receives the loss of the trained parameters over all rows, which
+ * synchronises the stream.  X and Y must stay valid and unchanged between calls that reuse
+ * them. */
+spalu_status spalu_predictor_train(spalu_predictor_t p, const float* X, const float* Y, int n, int epochs,
+                                   int batch, float lr, float* loss, spalu_stream_t stream);
+/* BF16 inference of device rows X (n x 16) into device out (n x 2). */
+spalu_status spalu_predictor_infer(spalu_predictor_t p, const float* X, int n, float* out,
+                                   spalu_stream_t stream);
+void spalu_predictor_destroy(spalu_predictor_t p);
+
+/* Predictor mode of the next factorizations of f: 0 off (adaptive ID), 1 record (adaptive ID;
+ * the features and ranks of the segments it applies to are kept for
+ * spalu_factor_export_training), 2 predict (one-pass sketch from p with the given margin,
+ * adaptive fallback).  p must outlive its use by f.  Errors: SPALU_ERR_ARG. */
+spalu_status spalu_factor_set_predictor(spalu_factor_t f, spalu_predictor_t p, int mode, double margin);
+/* Rows recorded by the last factorization (mode 1), levels L..1, segments in id order:
+ * features into device X (cap x 16), targets into device Y (cap x 2); *n_out receives the
+ * number of rows recorded (rows beyond cap are not written).  SPALU_ERR_STATE when the last
+ * factorization did not record. */
+spalu_status spalu_factor_export_training(spalu_factor_t f, float* X, float* Y, int cap, int* n_out,
+                                          spalu_stream_t stream);
 
 #ifdef __cplusplus
 }

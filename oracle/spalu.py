@@ -37,6 +37,7 @@ import numpy as np
 from .dense import gepp, interp_decomp, lu_solve
 from .nd import NestedDissection, box_corners, chebyshev_to_segment, _sides
 from .philox import sketch_matrix
+from . import predictor as pred
 
 
 @dataclass
@@ -47,6 +48,11 @@ class Options:
     near_radius: int = 2
     h0: int = 16
     seed: int = 0
+    # learned rank predictor (not in the paper; see oracle/predictor.py): a dict with
+    # "params", "mu", "isd" and optionally "margin"; and a list that receives one
+    # (features, k, far rows, e, l) tuple per segment the predictor applies to
+    predictor: dict | None = None
+    record: list | None = None
 
 
 @dataclass
@@ -180,6 +186,7 @@ def factor(A, nd: NestedDissection, opts: Options = Options()) -> Factor:
         seg_g = {k: ("S", l, k) for k in keys}
         ids = {}
         e_max, k_max = 0, 0
+        cnt = {"passes": 0, "fallbacks": 0, "predicted": 0}
         # 1. one ID per segment, all from A^(l) as it stands (Eqs. (RRQR sample), (ID [A_ni; A_in]))
         for key in keys:
             g = seg_g[key]
@@ -190,9 +197,10 @@ def factor(A, nd: NestedDissection, opts: Options = Options()) -> Factor:
                 k_max = max(k_max, e)
                 continue
             nbr = _neighbour_groups(lev.segments[key], l, nx, nd.ny, nodes)
-            ids[key] = _segment_id(blk, g, key, nbr, nodes, l, lev.segments[key].sid, nx, opts)
+            ids[key] = _segment_id(blk, g, key, nbr, nodes, l, lev.segments[key].sid, nx, opts,
+                                   A, L, cnt)
             k_max = max(k_max, ids[key][1])
-        stats["levels"][l] = {"e_max": e_max, "k_max": k_max,
+        stats["levels"][l] = {"e_max": e_max, "k_max": k_max, **cnt,
                               "ranks": [int(ids[k][1]) for k in keys],
                               "sizes": [int(nodes[seg_g[k]].size) for k in keys]}
 
@@ -282,8 +290,11 @@ def _neighbour_groups(seg, l, nx, ny, nodes):
     return out
 
 
-def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options):
-    """Sampled ID of one segment (Secs. 4.1-4.2, 4.5): returns (perm, k, T)."""
+def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0, cnt=None):
+    """Sampled ID of one segment (Secs. 4.1-4.2, 4.5): returns (perm, k, T).  With a
+    predictor, the first sketch has the predicted size and is kept only if it passes the
+    measured-error test; otherwise the adaptive schedule continues."""
+    cnt = cnt if cnt is not None else {"passes": 0, "fallbacks": 0, "predicted": 0}
     e = nodes[g].size
     rows_n, rows_t, labels = [], [], []
     for gn in nbr:
@@ -315,19 +326,50 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options):
     def ident():
         return interp_decomp(np.vstack([BN, BF]), opts.eps)
 
+    cnt["passes"] += 1
     if nF <= opts.h0:
         return ident()
+    p = opts.p_oversample
     h = min(nF, opts.h0)
+    use_pred = (opts.predictor is not None or opts.record is not None) and A is not None \
+        and nF > max(opts.h0, pred.PROBE)
+    predicted = False
+    if use_pred:
+        probe = sketch_matrix(opts.seed, l, sid, pred.PROBE, f_nodes, f_half) @ BF
+        x = pred.features(A, L, l, nodes[g], int(vlab.size), int(near.sum()), int((~near).sum()), probe,
+                          opts.eps)
+        if opts.predictor is not None:
+            pr = opts.predictor
+            o = pred.infer_bf16(pr["params"], pr["mu"], pr["isd"], x[None, :])[0]
+            h = pred.sketch_size(o, nF, e, p, opts.h0, pr.get("margin", pred.MARGIN))
+            predicted = True
+            cnt["predicted"] += 1
+    Bx = Bn if opts.symmetric else np.vstack([Bn, Bt])      # the exact B of Eq. (ID [A_ni; A_in])
     while True:
         if h >= nF:
-            return ident()
+            res = ident()
+            break
         G = sketch_matrix(opts.seed, l, sid, h, f_nodes, f_half)
         Y = np.vstack([BN, (G @ BF) / math.sqrt(h)])
         perm, k, T = interp_decomp(Y, opts.eps)
-        if k > h - opts.p_oversample and h < nF:
-            h = min(2 * h, nF)
+        if predicted:
+            predicted = False
+            if k <= h - p and pred.id_error_ok(Bx, perm, k, T, opts.eps):
+                res = (perm, k, T)
+                break
+            cnt["fallbacks"] += 1
+            cnt["passes"] += 1
+            h = min(2 * h, nF, max(opts.h0, 2 * (e + p)))
             continue
-        return perm, k, T
+        if k > h - p and h < nF:
+            cnt["passes"] += 1
+            h = min(2 * h, nF, max(opts.h0, 2 * (e + p)))   # binds only after a prediction
+            continue
+        res = (perm, k, T)
+        break
+    if use_pred and opts.record is not None:
+        opts.record.append((x, int(res[1]), int(nF), int(e), int(l)))
+    return res
 
 
 def _eliminate(blk: _Blocks, p, nodes, tape):

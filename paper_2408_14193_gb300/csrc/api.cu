@@ -37,6 +37,7 @@ namespace {
 std::atomic<unsigned long long> g_launches{0};
 }
 void spalu::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static void note_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 struct PhaseTimer {
   bool on = false;
@@ -100,8 +101,30 @@ struct spalu_factor_s {
   std::vector<int> host_rowptr_cache;
   PhaseTimer timer;
   int kumax = 30;            // upper bandwidth of the leaf U factors (read after each factor)
-  int* d_lmax = nullptr;     // [4 * (L + 1)] per-level maxima {e, kp, |dP|, -} (factor kernels)
+  int* d_lstat = nullptr;    // [LS_N * (L + 1)] per-level counters (factor kernels)
+  std::vector<int> lstat;    // host copy after the last factor
   std::vector<SolveCaps> caps;   // [1..L] solve-kernel capacities from the last factor
+  int* d_tgt_all = nullptr;  // recorded targets of all levels (4 ints per segment)
+  int* d_count = nullptr;    // export row counter
+  size_t tgt_ints = 0;
+  spalu_predictor_t pred = nullptr;
+  int pred_mode = PRED_OFF;
+};
+
+struct spalu_predictor_s {
+  float* params = nullptr;   // FP32 master parameters
+  float* m = nullptr;        // Adam moments
+  float* v = nullptr;
+  float* grad = nullptr;     // PRED_NPARAM + 1 (last: sum of squared residuals)
+  float* partial = nullptr;  // PRED_MAXBLK x (PRED_NPARAM + 1)
+  int* step = nullptr;       // Adam step counter
+  PredDev* dev = nullptr;    // inference copy (standardisation + bfloat16 parameters)
+  cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  cudaGraphExec_t epoch = nullptr;     // captured training epoch
+  const float* g_X = nullptr;          // the arguments the epoch graph was captured with
+  const float* g_Y = nullptr;
+  int g_n = 0, g_batch = 0;
+  float g_lr = 0.f;
 };
 
 namespace {
@@ -380,7 +403,15 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     Carver cv;
     cv.base = pass ? f->arena : nullptr;
     f->d_err = cv.take<int>(4);
-    f->d_lmax = cv.take<int>((size_t)4 * (L + 1));
+    f->d_lstat = cv.take<int>((size_t)LS_N * (L + 1));
+    {
+      size_t nt = 0;
+      for (int l = 1; l <= L; ++l) nt += (size_t)f->plan[l].g.nseg() * 4;
+      f->tgt_ints = nt;
+      f->d_tgt_all = cv.take<int>(nt > 0 ? nt : 1);
+    }
+    size_t tgt_off = 0;
+    f->d_count = cv.take<int>(1);
     f->rowptr = cv.take<int>(f->N + 1);
     f->colind = cv.take<int>(f->nnz_cap);
     f->val = cv.take<double>(f->nnz_cap);
@@ -425,6 +456,11 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
       d.ppiv = cv.take<int>((size_t)p.gp.nbox() * p.sepcap);
       d.eps = o->eps_id; d.symmetric = o->symmetric; d.p_over = o->p_oversample;
       d.near_radius = o->near_radius; d.h0 = o->h0; d.seed = o->seed;
+      d.L = L;
+      d.pred_mode = PRED_OFF; d.pred_margin = 0.35; d.pred = nullptr;
+      d.feat = cv.take<float>((size_t)nseg * PRED_NFEAT);
+      d.tgt = f->d_tgt_all ? f->d_tgt_all + tgt_off : nullptr;
+      tgt_off += (size_t)nseg * 4;
     }
     for (int l = L; l >= 1; --l) {
       LevelDev& d = f->lev[l];
@@ -445,7 +481,10 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   f->leaf.err = f->d_err;
   for (int l = 1; l <= L; ++l) {
     f->lev[l].err = f->d_err;
-    f->lev[l].lmax = f->d_lmax + 4 * l;
+    f->lev[l].lstat = f->d_lstat + LS_N * l;
+    f->lev[l].rowptr = f->rowptr;
+    f->lev[l].colind = f->colind;
+    f->lev[l].val = f->val;
   }
   f->caps.resize(L + 1);
   *out = f;
@@ -458,7 +497,9 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   int t_all = tm.begin("factor", s);
   CUDA_TRY(cudaMemsetAsync(f->d_err, 0, sizeof(int), s));
   CUDA_TRY(cudaMemsetAsync(f->leaf.kumax, 0, sizeof(int), s));
-  CUDA_TRY(cudaMemsetAsync(f->d_lmax, 0, sizeof(int) * 4 * (L + 1), s));
+  CUDA_TRY(cudaMemsetAsync(f->d_lstat, 0, sizeof(int) * LS_N * (L + 1), s));
+  if (f->pred_mode == PRED_RECORD && f->tgt_ints)
+    CUDA_TRY(cudaMemsetAsync(f->d_tgt_all, 0, sizeof(int) * f->tgt_ints, s));
   if (L >= 1) launch_level_init_L(f->lev[L], s);
   int t = tm.begin("leaf_factor", s);
   launch_leaf_factor(f->leaf, s);
@@ -477,12 +518,12 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   int ku = 30;
   if (cudaMemcpy(&ku, f->leaf.kumax, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SPALU_ERR_CUDA;
   f->kumax = ku;
-  std::vector<int> lm((size_t)4 * (L + 1));
-  if (cudaMemcpy(lm.data(), f->d_lmax, sizeof(int) * lm.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+  f->lstat.assign((size_t)LS_N * (L + 1), 0);
+  if (cudaMemcpy(f->lstat.data(), f->d_lstat, sizeof(int) * f->lstat.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
     return SPALU_ERR_CUDA;
   // the solve kernels hold a segment's (or separator's) right-hand-side block in shared memory
   for (int l = 1; l <= L && st == SPALU_OK; ++l)
-    if (!level_solve_caps(f->lev[l], lm.data() + 4 * l, &f->caps[l])) st = SPALU_ERR_UNSUPPORTED;
+    if (!level_solve_caps(f->lev[l], f->lstat.data() + LS_N * l, &f->caps[l])) st = SPALU_ERR_UNSUPPORTED;
   f->factored = (st == SPALU_OK);
   f->last_stream = s;
   return st;
@@ -760,9 +801,11 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
       ksum += kk[i];
     }
     if (emax > 0) qt = std::max(qt, (double)kmax / emax);
-    char buf[256];
-    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld, \"sep_k_max\": %d}",
-                  l == 1 ? "" : ", ", l, n, emax, kmax, esum, ksum, f->caps[l].yrows);
+    char buf[512];
+    const int* ls = f->lstat.data() + LS_N * l;
+    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld, \"sep_k_max\": %d, \"passes\": %d, \"fallbacks\": %d, \"predicted\": %d}",
+                  l == 1 ? "" : ", ", l, n, emax, kmax, esum, ksum, ls[LS_KPMAX], ls[LS_PASSES],
+                  ls[LS_FALLBACK], ls[LS_PREDICTED]);
     out += buf;
   }
   char buf[64];
@@ -807,6 +850,172 @@ spalu_status spalu_set_timing(spalu_factor_t f, int on) {
 }
 
 unsigned long long spalu_kernel_launches(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------- learned rank predictor
+void spalu_predictor_destroy(spalu_predictor_t p) {
+  if (!p) return;
+  if (p->epoch) cudaGraphExecDestroy(p->epoch);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  cudaFree(p->params); cudaFree(p->m); cudaFree(p->v); cudaFree(p->grad); cudaFree(p->partial);
+  cudaFree(p->step); cudaFree(p->dev);
+  delete p;
+}
+
+spalu_status spalu_predictor_create(const float* params, spalu_predictor_t* out) {
+  if (!params || !out) return SPALU_ERR_ARG;
+  *out = nullptr;
+  auto* p = new spalu_predictor_s();
+  const size_t np = PRED_NPARAM;
+  if (cudaMalloc(&p->params, np * 4) != cudaSuccess || cudaMalloc(&p->m, np * 4) != cudaSuccess ||
+      cudaMalloc(&p->v, np * 4) != cudaSuccess || cudaMalloc(&p->grad, (np + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&p->partial, (size_t)PRED_MAXBLK * (np + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&p->step, sizeof(int)) != cudaSuccess || cudaMalloc(&p->dev, sizeof(PredDev)) != cudaSuccess) {
+    spalu_predictor_destroy(p);
+    return SPALU_ERR_ALLOC;
+  }
+  PredDev h{};
+  for (int i = 0; i < PRED_NFEAT; ++i) { h.mu[i] = 0.0f; h.isd[i] = 1.0f; }
+  bool ok = cudaMemcpy(p->params, params, np * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemset(p->m, 0, np * 4) == cudaSuccess && cudaMemset(p->v, 0, np * 4) == cudaSuccess &&
+            cudaMemset(p->step, 0, sizeof(int)) == cudaSuccess &&
+            cudaMemcpy(p->dev, &h, sizeof(PredDev), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok) {
+    launch_pred_to_bf16(p->params, p->dev, nullptr);
+    ok = cudaStreamSynchronize(nullptr) == cudaSuccess;
+  }
+  if (!ok) {
+    spalu_predictor_destroy(p);
+    return SPALU_ERR_CUDA;
+  }
+  *out = p;
+  return SPALU_OK;
+}
+
+spalu_status spalu_predictor_get_params(spalu_predictor_t p, float* params, spalu_stream_t stream) {
+  if (!p || !params) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(params, p->params, PRED_NPARAM * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return SPALU_OK;
+}
+
+spalu_status spalu_predictor_set_norm(spalu_predictor_t p, const float* mu, const float* isd,
+                                      spalu_stream_t stream) {
+  if (!p || !mu || !isd) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(p->dev->mu, mu, PRED_NFEAT * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(p->dev->isd, isd, PRED_NFEAT * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return SPALU_OK;
+}
+
+spalu_status spalu_predictor_get_norm(spalu_predictor_t p, float* mu, float* isd, spalu_stream_t stream) {
+  if (!p || !mu || !isd) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(mu, p->dev->mu, PRED_NFEAT * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(isd, p->dev->isd, PRED_NFEAT * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return SPALU_OK;
+}
+
+spalu_status spalu_predictor_fit_norm(spalu_predictor_t p, const float* X, int n, spalu_stream_t stream) {
+  if (!p || !X || n < 1) return SPALU_ERR_ARG;
+  launch_pred_fit_norm(X, n, p->dev, (cudaStream_t)stream);
+  CUDA_TRY(cudaGetLastError());
+  return SPALU_OK;
+}
+
+spalu_status spalu_predictor_loss_grad(spalu_predictor_t p, const float* X, const float* Y, int n,
+                                       float* loss, float* grad, spalu_stream_t stream) {
+  if (!p || !X || !Y || n < 1 || !loss) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_pred_grad(p->params, p->dev, X, Y, 0, n, p->partial, p->grad, nullptr, s);
+  std::vector<float> g(PRED_NPARAM + 1);
+  CUDA_TRY(cudaMemcpyAsync(g.data(), p->grad, g.size() * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *loss = g[PRED_NPARAM] / (2.0f * n);
+  if (grad) std::memcpy(grad, g.data(), PRED_NPARAM * 4);
+  return SPALU_OK;
+}
+
+spalu_status spalu_predictor_train(spalu_predictor_t p, const float* X, const float* Y, int n, int epochs,
+                                   int batch, float lr, float* loss, spalu_stream_t stream) {
+  if (!p || !X || !Y || n < 1 || epochs < 0 || batch < 1 || !(lr > 0.0f)) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nbatch = (n + batch - 1) / batch;
+  // one epoch (gradient, reduction and Adam per batch) is captured once as a CUDA graph and
+  // replayed; it is recaptured when the data, sizes or learning rate change
+  if (!p->epoch || p->g_X != X || p->g_Y != Y || p->g_n != n || p->g_batch != batch || p->g_lr != lr) {
+    if (p->epoch) { cudaGraphExecDestroy(p->epoch); p->epoch = nullptr; }
+    if (!p->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    const unsigned long long l0 = g_launches.load();
+    CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int b = 0; b < nbatch; ++b) {
+      const int r0 = b * batch, nb = std::min(batch, n - r0);
+      launch_pred_grad(p->params, p->dev, X, Y, r0, nb, p->partial, p->grad, p->step, p->cap_stream);
+      launch_pred_adam(p->params, p->m, p->v, p->grad, p->step, lr, p->dev, p->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+    const long long captured = (long long)(g_launches.load() - l0);
+    note_launches(-captured);                      // nothing ran during the capture
+    if (ce != cudaSuccess) return SPALU_ERR_CUDA;
+    ce = cudaGraphInstantiate(&p->epoch, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { p->epoch = nullptr; return SPALU_ERR_CUDA; }
+    p->g_X = X; p->g_Y = Y; p->g_n = n; p->g_batch = batch; p->g_lr = lr;
+  }
+  for (int e = 0; e < epochs; ++e) {
+    CUDA_TRY(cudaGraphLaunch(p->epoch, s));
+    note_launches(3LL * nbatch);
+  }
+  if (loss) {
+    launch_pred_grad(p->params, p->dev, X, Y, 0, n, p->partial, p->grad, nullptr, s);
+    float l2 = 0.0f;
+    CUDA_TRY(cudaMemcpyAsync(&l2, p->grad + PRED_NPARAM, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *loss = l2 / (2.0f * n);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return SPALU_OK;
+}
+
+spalu_status spalu_predictor_infer(spalu_predictor_t p, const float* X, int n, float* out,
+                                   spalu_stream_t stream) {
+  if (!p || !X || !out || n < 0) return SPALU_ERR_ARG;
+  launch_pred_infer(p->dev, X, n, out, (cudaStream_t)stream);
+  CUDA_TRY(cudaGetLastError());
+  return SPALU_OK;
+}
+
+spalu_status spalu_factor_set_predictor(spalu_factor_t f, spalu_predictor_t p, int mode, double margin) {
+  if (!f || mode < PRED_OFF || mode > PRED_PREDICT || !(margin >= 0.0)) return SPALU_ERR_ARG;
+  if (mode == PRED_PREDICT && !p) return SPALU_ERR_ARG;
+  f->pred = p;
+  f->pred_mode = mode;
+  for (int l = 1; l <= f->nd->L; ++l) {
+    f->lev[l].pred_mode = mode;
+    f->lev[l].pred_margin = margin;
+    f->lev[l].pred = p ? p->dev : nullptr;
+  }
+  return SPALU_OK;
+}
+
+spalu_status spalu_factor_export_training(spalu_factor_t f, float* X, float* Y, int cap, int* n_out,
+                                          spalu_stream_t stream) {
+  if (!f || !X || !Y || cap < 0 || !n_out) return SPALU_ERR_ARG;
+  if (!f->factored || f->pred_mode != PRED_RECORD) return SPALU_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemsetAsync(f->d_count, 0, sizeof(int), s));
+  for (int l = f->nd->L; l >= 1; --l)
+    launch_pred_export(f->lev[l].feat, f->lev[l].tgt, f->lev[l].g.nseg(), f->o.p_oversample, X, Y, cap,
+                       f->d_count, s);
+  int n = 0;
+  CUDA_TRY(cudaMemcpyAsync(&n, f->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *n_out = n;
+  return SPALU_OK;
+}
 
 void spalu_factor_destroy(spalu_factor_t f) {
   if (!f) return;

@@ -24,6 +24,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "pred_infer.cuh"
 #include "spalu_internal.h"
 
 namespace spalu {
@@ -398,6 +399,197 @@ __device__ bool block_gepp(T* A, int lda, int r0, int n, int ncol, int* piv, T* 
   return ok;
 }
 
+
+// ------------------------------------------------------------ block reductions (FP64)
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ double block_minmax(double v, double* red, bool mx) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = mx ? fmax(v, w) : fmin(v, w);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = red[0];
+  for (int w = 1; w < nw; ++w) s = mx ? fmax(s, red[w]) : fmin(s, red[w]);
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------------------ far-row sketch
+// Yr[rr, c] = sum over far neighbour rows f of G[rr, f] B_F[f, c] for rr < hh (unscaled),
+// neighbours taken in chunks of ch (near ones get zero weight).  Yr has leading dimension ldy.
+template <typename T>
+__device__ void sketch_far(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, int sid,
+                           int halves, int nnear, const int* nearlist, int e, int hh, T* Yr, int ldy,
+                           T* Bc, T* Gc, int ch) {
+  for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Yr[(x % hh) + (size_t)ldy * (x / hh)] = T(0);
+  __syncthreads();
+  for (int f0 = 0; f0 < S.nb; f0 += ch) {
+    const int nc = min(ch, S.nb - f0);
+    const int rows = halves * nc;
+    for (int x = threadIdx.x; x < rows * e; x += blockDim.x) {
+      int row = x % rows, c = x / rows;
+      int t = row / nc, jj = row % nc;
+      int r, i;
+      locate(S, f0 + jj, r, i);
+      Bc[row + (size_t)rows * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
+    }
+    for (int x = threadIdx.x; x < hh * rows; x += blockDim.x) {
+      int rr = x % hh, row = x / hh;
+      int t = row / nc, jj = row % nc;
+      int f = f0 + jj;
+      bool isnear = false;
+      for (int a = 0; a < nnear; ++a) isnear |= (nearlist[a] == f);
+      T gv = T(0);
+      if (!isnear) {
+        int r, i;
+        locate(S, f, r, i);
+        gv = (T)sketch_gauss(d.seed, d.l, sid, rr, run_node(d, S.run[r], i), t);
+      }
+      Gc[rr + (size_t)hh * row] = gv;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < hh * e; x += blockDim.x) {
+      int rr = x % hh, c = x / hh;
+      T acc = T(0);
+      for (int row = 0; row < rows; ++row) acc += Gc[rr + (size_t)hh * row] * Bc[row + (size_t)rows * c];
+      Yr[rr + (size_t)ldy * c] += acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ learned rank predictor
+// (no counterpart in the paper; the definitions are those of the oracle's predictor module)
+__device__ __forceinline__ double csr_entry(const LevelDev& d, int u, int v) {
+  double a = 0.0;
+  for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p)
+    if (d.colind[p] == v) a += d.val[p];
+  return a;
+}
+
+// Features of segment sid into xf[16] (shared).  Y holds the column-pivoted QR of the probe
+// (R on its first kp rows).  red: >= NW doubles of shared scratch.
+template <typename T>
+__device__ void segment_features(const LevelDev& d, const SegCtx& S, int sid, int e, int nnear,
+                                 int nfar, const T* Y, int ldy, int kp, float* xf, double* red) {
+  const int* nodes = d.nodes + (size_t)sid * d.capS;
+  double lmin = 1e300, lmax = -1e300, lsum = 0.0, dsum = 0.0, ssum = 0.0, asum = 0.0;
+  for (int t = threadIdx.x; t < e; t += blockDim.x) {
+    const int u = nodes[t];
+    double dd = 0.0, off = 0.0, rs = 0.0, num = 0.0, den = 0.0;
+    for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p) {
+      const int j = d.colind[p];
+      const double a = d.val[p];
+      rs += a;
+      if (j == u) { dd += a; continue; }
+      off += fabs(a);
+      const double aj = csr_entry(d, j, u);
+      num += fabs(a - aj);
+      den += fabs(a) + fabs(aj);
+    }
+    dd = fabs(dd);
+    const double ld = dd > 0.0 ? log(dd) : log(1e-300);
+    lmin = fmin(lmin, ld);
+    lmax = fmax(lmax, ld);
+    lsum += ld;
+    dsum += (off > 0.0 && dd > 0.0) ? log(dd / off) : 0.0;
+    ssum += dd > 0.0 ? fabs(rs) / dd : 0.0;
+    asum += den > 0.0 ? num / den : 0.0;
+  }
+  lmin = block_minmax(lmin, red, false);
+  lmax = block_minmax(lmax, red, true);
+  const double mean = block_sum(lsum, red) / e;
+  dsum = block_sum(dsum, red);
+  ssum = block_sum(ssum, red);
+  asum = block_sum(asum, red);
+  double vsum = 0.0;                      // second pass: population variance of log d
+  for (int t = threadIdx.x; t < e; t += blockDim.x) {
+    const int u = nodes[t];
+    double dd = 0.0;
+    for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p)
+      if (d.colind[p] == u) dd += d.val[p];
+    dd = fabs(dd);
+    const double ld = dd > 0.0 ? log(dd) : log(1e-300);
+    vsum += (ld - mean) * (ld - mean);
+  }
+  vsum = block_sum(vsum, red);
+  if (threadIdx.x == 0) {
+    xf[0] = (float)(d.L - d.l);
+    xf[1] = (float)log2((double)e);
+    xf[2] = (float)log2(1.0 + S.nb);
+    xf[3] = (float)nnear;
+    xf[4] = (float)log2(1.0 + nfar);
+    xf[5] = (float)(lmin - mean);
+    xf[6] = (float)(lmax - mean);
+    xf[7] = (float)sqrt(vsum / e);
+    xf[8] = (float)(dsum / e);
+    xf[9] = (float)(ssum / e);
+    xf[10] = (float)(asum / e);
+    const double le = log10(d.eps);
+    const int nd = min(PRED_PROBE, e);
+    const double r0 = kp > 0 ? fabs((double)Y[0]) : 0.0;
+    const int js[5] = {1, 2, 3, 5, 7};
+    for (int q = 0; q < 5; ++q) {
+      const int j = js[q];
+      double v;
+      if (j >= nd || r0 == 0.0) v = -16.0 - le;
+      else {
+        const double rj = j < kp ? fabs((double)Y[j + (size_t)ldy * j]) : 0.0;
+        v = log10(fmax(rj / r0, 1e-16)) - le;
+      }
+      xf[11 + q] = (float)v;
+    }
+  }
+  __syncthreads();
+}
+
+// Measured ID error test ||B_r - B_s T||_F <= 10 eps ||B||_F on the exact B (all neighbour
+// rows, both halves of a non-symmetric B), chunked through Bc.
+template <typename T>
+__device__ bool id_error_ok(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, int halves,
+                            int e, int k, const int* perm, const T* Tw, int ldt, T* Bc, int ch, double* red) {
+  const int r = e - k;
+  double num = 0.0, den = 0.0;
+  for (int f0 = 0; f0 < S.nb; f0 += ch) {
+    const int nc = min(ch, S.nb - f0);
+    const int rows = halves * nc;
+    for (int x = threadIdx.x; x < rows * e; x += blockDim.x) {
+      int row = x % rows, c = x / rows;
+      int t = row / nc, jj = row % nc;
+      int ri, i;
+      locate(S, f0 + jj, ri, i);
+      const T v = bval<T>(d, S, F1, F2, S.run[ri], i, t, c);
+      Bc[row + (size_t)rows * c] = v;
+      den += (double)v * (double)v;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < rows * r; x += blockDim.x) {
+      int row = x % rows, j = x / rows;
+      T s = Bc[row + (size_t)rows * perm[k + j]];
+      for (int a = 0; a < k; ++a) s -= Bc[row + (size_t)rows * perm[a]] * Tw[a + (size_t)ldt * j];
+      num += (double)s * (double)s;
+    }
+    __syncthreads();
+  }
+  num = block_sum(num, red);
+  den = block_sum(den, red);
+  return sqrt(num) <= 10.0 * d.eps * sqrt(den);
+}
+
 // ------------------------------------------------------------ sparsify: one CTA per segment
 template <typename T>
 __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_bytes) {
@@ -414,7 +606,7 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
   const int e = S.e;
   const int capS = d.capS;
   int* perm_out = d.perm + (size_t)sid * capS;
-  if (threadIdx.x == 0) atomicMax(d.lmax, e);
+  if (threadIdx.x == 0) atomicMax(d.lstat + LS_EMAX, e);
   if (e == 0) {
     if (threadIdx.x == 0) { d.kk[sid] = 0; d.hs[sid] = 0; }
     return;
@@ -513,9 +705,31 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
     return;
   }
 
-  // ---- adaptive sketch + ID (Sec. 4.2.3; h = k + p with k unknown: double h until k <= h - p)
+  // ---- learned rank predictor (not in the paper): features from an 8-row probe of the
+  //      far rows, then the network's one-pass sketch size (PRED_PREDICT) or a training
+  //      record of the features and the adaptive rank (PRED_RECORD)
+  __shared__ float xf[PRED_NFEAT], zs[PRED_NFEAT], hid[PRED_NHID], pout[PRED_NOUT];
+  const bool use_pred = d.pred_mode != PRED_OFF && nF > max(d.h0, PRED_PROBE);
   int h = (nF <= d.h0) ? nF : d.h0;
+  bool predicted = false;
+  if (use_pred) {
+    sketch_far<T>(d, S, F1, F2, sid, halves, nnear, nearlist, e, PRED_PROBE, Y, ldy, Bc, Gc, ch);
+    const int kp = block_cpqr<T>(Y, ldy, PRED_PROBE, e, 0.0, perm, vn1, vn2, ivn2, shr, flags, shi);
+    segment_features<T>(d, S, sid, e, nnear, nfar_sh, Y, ldy, kp, xf, shr);
+    if (d.pred_mode == PRED_RECORD) {
+      if (threadIdx.x < PRED_NFEAT) d.feat[(size_t)sid * PRED_NFEAT + threadIdx.x] = xf[threadIdx.x];
+    } else {
+      mlp_infer_block(*d.pred, xf, zs, hid, pout);
+      h = pred_sketch_size(pout, nF, e, d.p_over, d.h0, d.pred_margin);
+      predicted = true;
+    }
+  }
+
+  // ---- adaptive sketch + ID (Sec. 4.2.3; h = k + p with k unknown: double h until k <= h - p)
   int k = 0;
+  int passes = 0;
+  bool fellback = false, have_t = false;
+  const bool was_predicted = predicted;
   while (true) {
     const bool full = (h >= nF);
     const int hh = full ? nF : h;
@@ -547,56 +761,48 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
             Y[(nN + t * nfar_sh + j) + (size_t)ldy * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
       }
     } else {
-      for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] = T(0);
-      __syncthreads();
       // Y_F = G B_F, chunks of neighbours (near ones get zero weight)
-      for (int f0 = 0; f0 < S.nb; f0 += ch) {
-        const int nc = min(ch, S.nb - f0);
-        const int rows = halves * nc;
-        for (int x = threadIdx.x; x < rows * e; x += blockDim.x) {
-          int row = x % rows, c = x / rows;
-          int t = row / nc, jj = row % nc;
-          int r, i;
-          locate(S, f0 + jj, r, i);
-          Bc[row + (size_t)rows * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
-        }
-        for (int x = threadIdx.x; x < hh * rows; x += blockDim.x) {
-          int rr = x % hh, row = x / hh;
-          int t = row / nc, jj = row % nc;
-          int f = f0 + jj;
-          bool isnear = false;
-          for (int a = 0; a < nnear; ++a) isnear |= (nearlist[a] == f);
-          T gv = T(0);
-          if (!isnear) {
-            int r, i;
-            locate(S, f, r, i);
-            gv = (T)sketch_gauss(d.seed, d.l, sid, rr, run_node(d, S.run[r], i), t);
-          }
-          Gc[rr + (size_t)hh * row] = gv;
-        }
-        __syncthreads();
-        for (int x = threadIdx.x; x < hh * e; x += blockDim.x) {
-          int rr = x % hh, c = x / hh;
-          T acc = T(0);
-          for (int row = 0; row < rows; ++row) acc += Gc[rr + (size_t)hh * row] * Bc[row + (size_t)rows * c];
-          Y[(nN + rr) + (size_t)ldy * c] += acc;
-        }
-        __syncthreads();
-      }
+      sketch_far<T>(d, S, F1, F2, sid, halves, nnear, nearlist, e, hh, Y + nN, ldy, Bc, Gc, ch);
       const T sc = (T)(1.0 / sqrt((double)hh));
       for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
     }
     __syncthreads();
     k = block_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, ivn2, shr, flags, shi);
+    ++passes;
+    if (predicted) {          // the one-pass ID stands if it passes the measured-error test
+      predicted = false;
+      if (full) break;
+      bool ok = k <= h - d.p_over;
+      if (ok) {
+        block_interp<T>(Y, ldy, k, e, Tw, ldt, rinv);
+        have_t = true;
+        ok = id_error_ok<T>(d, S, F1, F2, halves, e, k, perm, Tw, ldt, Bc, ch, shr);
+      }
+      if (ok) break;
+      fellback = true;
+      have_t = false;
+      h = min(2 * h, hmax);     // hmax = min(|F|, max(h0, 2(e+p))): k <= e < hmax - p
+      __syncthreads();
+      continue;
+    }
     if (!full && k > h - d.p_over && h < nF) {
-      h = min(2 * h, nF);
+      h = min(2 * h, hmax);     // never binds without a prediction (h < 2(k+p))
       __syncthreads();
       continue;
     }
     break;
   }
+  if (threadIdx.x == 0) {
+    atomicAdd(d.lstat + LS_PASSES, passes);
+    if (fellback) atomicAdd(d.lstat + LS_FALLBACK, 1);
+    if (was_predicted) atomicAdd(d.lstat + LS_PREDICTED, 1);
+    if (use_pred && d.pred_mode == PRED_RECORD) {
+      int* tg = d.tgt + (size_t)sid * 4;
+      tg[0] = k; tg[1] = nF; tg[2] = 1; tg[3] = passes;
+    }
+  }
   const int r = e - k;
-  block_interp<T>(Y, ldy, k, e, Tw, ldt, rinv);
+  if (!have_t) block_interp<T>(Y, ldy, k, e, Tw, ldt, rinv);
 
   // ---- transformed diagonal block in [skeleton | remainder] order (Eq. (UtALt))
   for (int x = threadIdx.x; x < e * e; x += blockDim.x) {
@@ -781,8 +987,8 @@ __global__ void merge_table_kernel(LevelDev d) {
   }
   d.pcount[2 * P] = ndP;
   d.pcount[2 * P + 1] = C.kp;
-  atomicMax(d.lmax + 1, C.kp);
-  atomicMax(d.lmax + 2, ndP);
+  atomicMax(d.lstat + LS_KPMAX, C.kp);
+  atomicMax(d.lstat + LS_DPMAX, ndP);
 }
 
 // M[a][b] = sum over the children holding both unknowns of the child's block, where the
@@ -1331,6 +1537,7 @@ void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
 }
 
 bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
+  // lmax: the level counters, LS_EMAX / LS_KPMAX / LS_DPMAX first
   auto mn = [](long long a, long long b) { return a < b ? a : b; };
   auto mx = [](long long a, long long b) { return a > b ? a : b; };
   const long long TB = d.fp32 ? 4 : 8, budget = 200 * 1024;

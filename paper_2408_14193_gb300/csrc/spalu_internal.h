@@ -19,6 +19,7 @@
 //   2w+2h+{0,1,2,3}.  The root (depth 0) has no boundary unknowns (D = 0).  A side holds
 //   cnt <= its length unknowns at the start of its range.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,6 +32,29 @@ enum { C_BL = 0, C_BR = 1, C_TL = 2, C_TR = 3 };
 
 // device error word bits
 enum { ERR_SINGULAR = 1, ERR_NONFINITE = 2, ERR_CAPACITY = 4, ERR_TIMEOUT = 8 };
+
+// ---- learned rank predictor (no counterpart in the paper): 16 features -> 64 ReLU -> 2
+constexpr int PRED_NFEAT = 16;
+constexpr int PRED_NHID = 64;
+constexpr int PRED_NOUT = 2;
+constexpr int PRED_NPARAM = PRED_NHID * PRED_NFEAT + PRED_NHID + PRED_NOUT * PRED_NHID + PRED_NOUT;
+constexpr int PRED_PROBE = 8;          // rows of the probe sketch behind features 11-15
+constexpr int PRED_MAXBLK = 256;       // blocks of the training gradient kernel
+constexpr int PRED_OFF_B1 = PRED_NHID * PRED_NFEAT;
+constexpr int PRED_OFF_W2 = PRED_OFF_B1 + PRED_NHID;
+constexpr int PRED_OFF_B2 = PRED_OFF_W2 + PRED_NOUT * PRED_NHID;
+// predictor modes of a factorization
+enum { PRED_OFF = 0, PRED_RECORD = 1, PRED_PREDICT = 2 };
+// per-level counters (int) written by the factor kernels
+enum { LS_EMAX = 0, LS_KPMAX = 1, LS_DPMAX = 2, LS_PASSES = 3, LS_FALLBACK = 4, LS_PREDICTED = 5, LS_N = 8 };
+
+// Inference copy of the network: feature standardisation and bfloat16 parameters
+// (W1 64x16 row-major | b1 | W2 2x64 | b2).
+struct PredDev {
+  float mu[PRED_NFEAT];
+  float isd[PRED_NFEAT];
+  __nv_bfloat16 wb[PRED_NPARAM];
+};
 
 struct Geo {
   int bx, by, w, h;
@@ -121,8 +145,17 @@ struct LevelDev {
   int symmetric, p_over, near_radius, h0;
   unsigned long long seed;
   int* err;
-  int* lmax;        // [3] largest segment size e, separator skeleton kp and parent boundary
-                    // count |dP| met at this level (atomicMax by the factor kernels)
+  int* lstat;       // [LS_N] counters of this level (maxima of e, kp, |dP|; ID passes, ...)
+  int L;            // number of levels of the dissection
+  // learned rank predictor
+  int pred_mode;            // PRED_OFF / PRED_RECORD / PRED_PREDICT
+  double pred_margin;
+  const PredDev* pred;      // device copy of the network (PRED_PREDICT)
+  float* feat;              // [nseg * 16] features (PRED_RECORD)
+  int* tgt;                 // [nseg * 4] {k, far rows, valid, ID passes} (PRED_RECORD)
+  const int* rowptr;        // original matrix (features 5-10)
+  const int* colind;
+  const double* val;
 };
 
 // Shared-memory capacities of the solve kernels of one level, set by the host from the
@@ -174,9 +207,19 @@ void launch_leaf_solve(const LeafDev& d, double* X, int nrhs, int ld, int bwd, i
 void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s);
 // Capacities for the level-solve kernels from the level maxima {e, kp, |dP|}; false when
 // the right-hand-side blocks alone do not fit in shared memory.
-bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out);
+bool level_solve_caps(const LevelDev& d, const int* lstat, SolveCaps* out);
 void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
 void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
+
+void launch_pred_fit_norm(const float* X, int n, PredDev* P, cudaStream_t s);
+void launch_pred_grad(const float* params, const PredDev* P, const float* X, const float* Y, int r0, int nb,
+                      float* partial, float* grad, int* step, cudaStream_t s);
+void launch_pred_adam(float* params, float* m, float* v, const float* grad, const int* step, float lr,
+                      PredDev* P, cudaStream_t s);
+void launch_pred_to_bf16(const float* params, PredDev* P, cudaStream_t s);
+void launch_pred_infer(const PredDev* P, const float* X, int n, float* out, cudaStream_t s);
+void launch_pred_export(const float* feat, const int* tgt, int nseg, int p, float* X, float* Y, int cap,
+                        int* count, cudaStream_t s);
 
 size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes);
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes);

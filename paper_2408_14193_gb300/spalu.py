@@ -86,7 +86,22 @@ SIGNATURES = [
     ("spalu_set_timing", _I, [_P, _I]),
     ("spalu_kernel_launches", ctypes.c_ulonglong, []),
     ("spalu_factor_destroy", None, [_P]),
+    ("spalu_predictor_create", _I, [_P, _P]),
+    ("spalu_predictor_get_params", _I, [_P, _P, _P]),
+    ("spalu_predictor_set_norm", _I, [_P, _P, _P, _P]),
+    ("spalu_predictor_get_norm", _I, [_P, _P, _P, _P]),
+    ("spalu_predictor_fit_norm", _I, [_P, _P, _I, _P]),
+    ("spalu_predictor_loss_grad", _I, [_P, _P, _P, _I, _P, _P, _P]),
+    ("spalu_predictor_train", _I, [_P, _P, _P, _I, _I, _I, ctypes.c_float, _P, _P]),
+    ("spalu_predictor_infer", _I, [_P, _P, _I, _P, _P]),
+    ("spalu_predictor_destroy", None, [_P]),
+    ("spalu_factor_set_predictor", _I, [_P, _P, _I, ctypes.c_double]),
+    ("spalu_factor_export_training", _I, [_P, _P, _P, _I, _P, _P]),
 ]
+
+PRED_NFEAT = 16
+PRED_NPARAM = 1218
+PRED_MODES = {"off": 0, "record": 1, "predict": 2}
 
 
 def load_library(path: str | None = None):
@@ -245,6 +260,27 @@ class Factor:
     def set_timing(self, on: bool = True):
         _check(self.lib.spalu_set_timing(self.handle, 1 if on else 0), "spalu_set_timing")
 
+    def set_predictor(self, predictor: "Predictor | None", mode: str = "predict", margin: float = 0.35):
+        """spalu_factor_set_predictor: mode "off", "record" or "predict" for the next factor."""
+        self._pred = predictor             # keep it alive while the factor may use it
+        _check(self.lib.spalu_factor_set_predictor(self.handle, predictor.handle if predictor else None,
+                                                   PRED_MODES[mode], float(margin)),
+               "spalu_factor_set_predictor")
+
+    def export_training(self, cap: int | None = None, stream=None):
+        """spalu_factor_export_training: (X, Y) device float32 tensors of the recorded rows."""
+        import torch
+        if cap is None:
+            cap = sum(lv["nseg"] for lv in self.stats()["levels"])
+        X = torch.empty((max(cap, 1), PRED_NFEAT), dtype=torch.float32, device="cuda")
+        Y = torch.empty((max(cap, 1), 2), dtype=torch.float32, device="cuda")
+        n = ctypes.c_int(0)
+        _check(self.lib.spalu_factor_export_training(self.handle, _dev_ptr(X, torch.float32),
+                                                     _dev_ptr(Y, torch.float32), int(cap), ctypes.byref(n),
+                                                     _stream_ptr(stream)), "spalu_factor_export_training")
+        m = min(n.value, cap)
+        return X[:m], Y[:m]
+
     def stats(self) -> dict:
         buf = ctypes.create_string_buffer(1 << 16)
         _check(self.lib.spalu_stats(self.handle, buf, len(buf)), "spalu_stats")
@@ -254,4 +290,75 @@ class Factor:
         h = getattr(self, "handle", None)
         if h:
             self.lib.spalu_factor_destroy(h)
+            self.handle = None
+
+
+class Predictor:
+    """spalu_predictor_*: the learned rank predictor (16 -> 64 ReLU -> 2; BF16 inference,
+    FP32 training with Adam, all on the device)."""
+
+    def __init__(self, params: np.ndarray):
+        self.lib = load_library()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != PRED_NPARAM:
+            raise ValueError(f"expected {PRED_NPARAM} parameters")
+        h = ctypes.c_void_p()
+        _check(self.lib.spalu_predictor_create(p.ctypes.data, ctypes.byref(h)), "spalu_predictor_create")
+        self.handle = h
+
+    def params(self, stream=None) -> np.ndarray:
+        out = np.empty(PRED_NPARAM, dtype=np.float32)
+        _check(self.lib.spalu_predictor_get_params(self.handle, out.ctypes.data, _stream_ptr(stream)),
+               "spalu_predictor_get_params")
+        return out
+
+    def set_norm(self, mu, isd, stream=None):
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        isd = np.ascontiguousarray(isd, dtype=np.float32)
+        _check(self.lib.spalu_predictor_set_norm(self.handle, mu.ctypes.data, isd.ctypes.data,
+                                                 _stream_ptr(stream)), "spalu_predictor_set_norm")
+
+    def norm(self, stream=None):
+        mu = np.empty(PRED_NFEAT, dtype=np.float32)
+        isd = np.empty(PRED_NFEAT, dtype=np.float32)
+        _check(self.lib.spalu_predictor_get_norm(self.handle, mu.ctypes.data, isd.ctypes.data,
+                                                 _stream_ptr(stream)), "spalu_predictor_get_norm")
+        return mu, isd
+
+    def fit_norm(self, X, stream=None):
+        import torch
+        _check(self.lib.spalu_predictor_fit_norm(self.handle, _dev_ptr(X, torch.float32), int(X.shape[0]),
+                                                 _stream_ptr(stream)), "spalu_predictor_fit_norm")
+
+    def loss_grad(self, X, Y, stream=None):
+        import torch
+        loss = ctypes.c_float(0.0)
+        g = np.empty(PRED_NPARAM, dtype=np.float32)
+        _check(self.lib.spalu_predictor_loss_grad(self.handle, _dev_ptr(X, torch.float32),
+                                                  _dev_ptr(Y, torch.float32), int(X.shape[0]),
+                                                  ctypes.byref(loss), g.ctypes.data, _stream_ptr(stream)),
+               "spalu_predictor_loss_grad")
+        return loss.value, g
+
+    def train(self, X, Y, epochs: int, batch: int = 256, lr: float = 1e-3, stream=None) -> float:
+        import torch
+        loss = ctypes.c_float(0.0)
+        _check(self.lib.spalu_predictor_train(self.handle, _dev_ptr(X, torch.float32),
+                                              _dev_ptr(Y, torch.float32), int(X.shape[0]), int(epochs),
+                                              int(batch), float(lr), ctypes.byref(loss), _stream_ptr(stream)),
+               "spalu_predictor_train")
+        return loss.value
+
+    def infer(self, X, stream=None):
+        import torch
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _check(self.lib.spalu_predictor_infer(self.handle, _dev_ptr(X, torch.float32), int(X.shape[0]),
+                                              _dev_ptr(out, torch.float32), _stream_ptr(stream)),
+               "spalu_predictor_infer")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.lib.spalu_predictor_destroy(h)
             self.handle = None
