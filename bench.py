@@ -5,6 +5,9 @@ Step = one numeric factorization of the 1023 x 1023 variable-coefficient diffusi
 (a = exp(GRF), squared-exponential covariance with length 0.05, variance 1), the direct
 solve of 16 standard-normal right-hand sides and GMRES refinement of every column to a
 relative residual <= 1e-10.  value = N / (T_factor + T_solve+refine), summed over ranks.
+The headline path is mixed precision with the learned rank predictor, trained on the GPU
+before the timed region from adaptive-ID records of smaller problems (n <= 511); the plain
+FP64 form (adaptive ID) is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,9 +38,13 @@ METRIC = "factor+solve DOF/s at N≈1M, mixed+learned vs plain FP64 GPU @1e-10 r
 N_SIDE = 1023
 NRHS = 16
 EPS_ID = 1e-8
-FP64_FLOP_PER_CLK_SM = 4          # 2 FP64 FMA per clock per SM on GB300
+FP64_FLOP_PER_CLK_SM = 4          # 2 FP64 FMA per clock per SM on GB300 (measured: 1.19 TFLOP/s)
+FP32_FLOP_PER_CLK_SM = 256        # 128 FP32 lanes x FMA per clock per SM
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+# training problems of the predictor (kind, n, seed): the families of the method at n <= 511
+TRAIN_SET = [("diffusion", 255, 101), ("diffusion", 255, 102), ("diffusion", 511, 103),
+             ("laplace", 255, 104), ("helmholtz", 255, 105), ("convdiff", 255, 106)]
 
 
 def leaf_algorithmic_flops() -> float:
@@ -179,31 +186,99 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
-def _roofline(st, steps):
-    """Roofline of the dominant kernel: candidates are the phases holding launches of one
-    kernel only; achieved = algorithmic FP64 FLOP per launch / launch time."""
+def _leaf_flops_split():
+    """(FP64 FLOPs of the band LU, FLOPs of the 60 band solves) of one leaf elimination."""
+    n, b = 225, 15
+    lu = sum(min(b, n - 1 - j) + 2.0 * min(b, n - 1 - j) ** 2 for j in range(n))
+    return lu, leaf_algorithmic_flops() - lu
+
+
+def _roofline(st, steps, fp32: bool, hbm_gbs: float):
+    """Roofline of the dominant kernel among those timed alone in a phase (the leaf
+    elimination, the leaf solve sweeps): achieved = algorithmic work per launch / average
+    launch time.  The leaf elimination is bound by the FP64 pipe (its band LU) plus, in mixed
+    mode, the FP32 pipe (its band solves); the leaf solve by HBM (factor bytes + vectors)."""
     tms, tcount = st["timing_ms"], st["timing_count"]
     nleaf = ((N_SIDE + 1) // 16) ** 2
-    peak_tf = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    clk = SM_MAX_MHZ * 1e6
+    p64 = N_SM * FP64_FLOP_PER_CLK_SM * clk
+    p32 = N_SM * FP32_FLOP_PER_CLK_SM * clk
     cand = {}
     if "leaf_factor" in tms:
-        cand["leaf_factor_kernel"] = (tms["leaf_factor"], tcount["leaf_factor"], nleaf * leaf_algorithmic_flops())
+        lu, sv = _leaf_flops_split()
+        t_roof = nleaf * (lu / p64 + sv / (p32 if fp32 else p64))
+        cand["leaf_factor_kernel"] = ("alu", tms["leaf_factor"], tcount["leaf_factor"],
+                                      nleaf * (lu + sv), t_roof)
     if "leaf_solve_fwd" in tms:
         t = tms["leaf_solve_fwd"] + tms.get("leaf_solve_bwd", 0.0)
         c = tcount["leaf_solve_fwd"] + tcount.get("leaf_solve_bwd", 0)
-        cand["leaf_solve_kernel"] = (t, c, nleaf * NRHS * leaf_solve_flops_per_rhs())
-    spars = {k: v for k, v in tms.items() if k.startswith("sparsify_l")}
-    if spars:
-        k = max(spars, key=spars.get)
-        cand["sparsify_kernel (" + k.split("_")[1] + ")"] = (spars[k], tcount[k], None)
-    dom = max(cand, key=lambda k: cand[k][0])
-    tot, cnt, flops = cand[dom]
-    dur_ms = tot / cnt
-    ach = flops / (dur_ms / 1e3) / 1e12 if flops else None
-    return {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-            "frac": (ach / peak_tf) if ach else None, "traffic": None, "kernel": dom,
-            "launch_ms": dur_ms, "share_of_step": tot / steps,
-            "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2070 MHz"}
+        tb = 4 if fp32 else 8
+        # per launch (one sweep pair, all 16 right-hand sides): the band factor, pivots and
+        # reciprocal pivots once, the interior unknowns read and written
+        byts = nleaf * (46 * 225 * tb + 225 * 4 + 225 * tb) + 2 * 8 * nleaf * 225 * NRHS
+        cand["leaf_solve_kernel"] = ("hbm", t, c, byts, byts / (hbm_gbs * 1e9))
+    dom = max(cand, key=lambda k: cand[k][1])
+    bound, tot, cnt, work, t_roof = cand[dom]
+    dur_s = tot / cnt / 1e3
+    if bound == "hbm":
+        ach = work / dur_s / 1e9
+        peak, unit, src = hbm_gbs, "GB/s", "measured (MEASURED_PEAKS.json hbm_gbs)"
+    else:
+        ach = work / dur_s / 1e12
+        peak = work / t_roof / 1e12
+        unit = "TFLOP/s"
+        src = ("derived: FP64 band LU at 152 SMs x 4 FLOP/clk x 2070 MHz" +
+               (" + FP32 band solves at 152 x 256 FLOP/clk x 2070 MHz" if fp32 else ""))
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "traffic": None, "kernel": dom, "launch_ms": dur_s * 1e3, "share_of_step_ms": tot / steps,
+            "peak_source": src}
+
+
+def _nvtx(push: bool):
+    try:
+        import torch
+        if push:
+            torch.cuda.nvtx.range_push("step")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+def train_predictor(dev, prec, eps, epochs: int = 200):
+    """Record adaptive-ID rows on TRAIN_SET (same precision and eps as the timed path), fit
+    the standardisation and train the network on the GPU; returns (predictor, info)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from oracle import predictor as opr
+    from paper_2408_14193_gb300 import Factor, NestedDissection, Predictor
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xs, Ys = [], []
+    for kind, n, seed in TRAIN_SET:
+        P = W.make_problem(kind, n, seed=seed, nrhs=1)
+        f = Factor(NestedDissection(n), eps_id=eps, symmetric=1 if P.symmetric else 0, precision=prec)
+        f.set_predictor(None, "record")
+        f.factor(torch.from_numpy(P.A.indptr).to(dev), torch.from_numpy(P.A.indices).to(dev),
+                 torch.from_numpy(P.A.data).to(dev))
+        X, Y = f.export_training()
+        Xs.append(X)
+        Ys.append(Y)
+    X = torch.cat(Xs).contiguous()
+    Y = torch.cat(Ys).contiguous()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    p = Predictor(opr.init_params(0))
+    p.fit_norm(X)
+    loss0, _ = p.loss_grad(X, Y)
+    loss = p.train(X, Y, epochs=epochs, batch=256, lr=3e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return p, {"rows": int(X.shape[0]), "record_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3),
+               "epochs": epochs, "batch": 256, "loss_initial": loss0, "loss_final": loss,
+               "problems": [f"{k} {n}x{n}" for k, n, _ in TRAIN_SET]}
 
 
 def run_ours(args):
@@ -242,8 +317,10 @@ def run_ours(args):
     gpu_id = str(getattr(props, "uuid", "") or "")
     gpu_id = ("GPU-" + gpu_id) if gpu_id and not gpu_id.startswith("GPU-") else (gpu_id or str(local))
 
-    def measure(prec, eps, sample_clocks):
+    def measure(prec, eps, sample_clocks, pred=None):
         f = Factor(nd, eps_id=eps, symmetric=1, precision=prec)
+        if pred is not None:
+            f.set_predictor(pred, "predict")
 
         def step():
             f.factor(rp, ci, va)
@@ -266,9 +343,11 @@ def run_ours(args):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            _nvtx(True)                           # the timed kernels (for profiler filters)
             e0.record(stream)
             it, rel = step()
             e1.record(stream)
+            _nvtx(False)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
             iters.append(it)
@@ -288,12 +367,14 @@ def run_ours(args):
         return {"ms": ms, "iters": max(iters), "relres": max(rels), "launches": launches,
                 "st": st, "clocks": clocks}
 
-    head = measure(1, args.mixed_eps, True)       # mixed precision: the headline path
+    pred, pred_info = train_predictor(dev, 1, args.mixed_eps, args.pred_epochs)
+    head = measure(1, args.mixed_eps, True, pred)  # mixed precision + learned ranks: the headline
     if args.only_mixed:                           # profiling runs: the headline path alone
         print(json.dumps({"ms_per_step": head["ms"] / args.steps, "relres_max": head["relres"],
                           "gmres_iters": head["iters"]}), flush=True)
         return 0
     base = measure(0, EPS_ID, False)              # plain FP64 GPU form
+    noml = measure(1, args.mixed_eps, False)      # ablation: mixed precision, adaptive ID
 
     # end to end through the host-memory entry points (pinned host buffers), headline path
     val_h = torch.from_numpy(A.data).pin_memory().numpy()
@@ -301,6 +382,7 @@ def run_ours(args):
     ci_h = torch.from_numpy(A.indices).pin_memory().numpy()
     B_h = torch.from_numpy(np.ascontiguousarray(P.B.T)).pin_memory().numpy()
     g = Factor(nd, eps_id=args.mixed_eps, symmetric=1, precision=1)
+    g.set_predictor(pred, "predict")
     g.factor_host(rp_h, ci_h, val_h)
     g.solve_host(B_h, refine=True)
     torch.cuda.synchronize()
@@ -321,6 +403,9 @@ def run_ours(args):
         return 0
     value = ws * args.steps * N / (head["ms"] / 1e3)
     base_value = ws * args.steps * N / (base["ms"] / 1e3)
+    noml_value = ws * args.steps * N / (noml["ms"] / 1e3)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs") or 6800.0
     e2e_value = ws * args.steps * N / e2e_s
 
     cpu = None
@@ -339,13 +424,19 @@ def run_ours(args):
                                f"QR pivots/norms), eps_ID={args.mixed_eps}, GMRES (FP64 residual) "
                                f"to 1e-10",
                    "N": N, "nrhs": NRHS, "precision": "mixed", "eps_id": args.mixed_eps,
-                   "learned_ranks": False,
+                   "learned_ranks": True,
                    "l2": "256 MB flush between steps; factor working set > L2"},
         "relres_max": head["relres"], "gmres_iters": head["iters"],
         "fp64_plain": {"value": base_value, "unit": "DOF/s", "ms_per_step": base["ms"] / args.steps,
                        "eps_id": EPS_ID, "relres_max": base["relres"], "gmres_iters": base["iters"],
                        "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(base["st"]["timing_ms"].items())},
-                       "roofline": _roofline(base["st"], args.steps)},
+                       "roofline": _roofline(base["st"], args.steps, False, hbm)},
+        "mixed_adaptive": {"value": noml_value, "unit": "DOF/s", "ms_per_step": noml["ms"] / args.steps,
+                           "relres_max": noml["relres"], "gmres_iters": noml["iters"],
+                           "id_passes": sum(lv["passes"] for lv in noml["st"]["levels"])},
+        "predictor": dict(pred_info, id_passes=sum(lv["passes"] for lv in st["levels"]),
+                          predicted=sum(lv["predicted"] for lv in st["levels"]),
+                          fallbacks=sum(lv["fallbacks"] for lv in st["levels"])),
         "speedup_vs_fp64": value / base_value,
         "nd_build_s": nd_s,
         "clocks": head["clocks"],
@@ -353,7 +444,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(A.data.nbytes + P.B.nbytes),
                 "d2h_bytes_per_step": int(P.B.nbytes), "relres_max": e2e_rel},
         "gpu_launches": int(head["launches"]),
-        "roofline": _roofline(st, args.steps),
+        "roofline": _roofline(st, args.steps, True, hbm),
         "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(st["timing_ms"].items())},
         "factor_stats": {"q_tilde": st["q_tilde"], "levels": st["levels"]},
         "cpu_baseline": cpu,
@@ -374,6 +465,7 @@ def main():
     ap.add_argument("--ref-n", type=int, default=127, dest="ref_n")
     ap.add_argument("--no-cpu", action="store_true", dest="no_cpu")
     ap.add_argument("--mixed-eps", type=float, default=1e-6, dest="mixed_eps")
+    ap.add_argument("--pred-epochs", type=int, default=200, dest="pred_epochs")
     ap.add_argument("--only-mixed", action="store_true", dest="only_mixed",
                     help="time the mixed-precision path only (for profiler runs)")
     args = ap.parse_args()

@@ -185,7 +185,7 @@ void spalu_factor_destroy(spalu_factor_t f);
  *   targets   y0 = log2(1 + k), y1 = log2(min(far rows, k + p));
  *   sketch    h = max(ceil(2^o1 (1 + margin)), ceil((2^o0 - 1)(1 + margin)) + p), clamped
  *             to [1, min(far rows, max(h0, 2 (e + p)))];
- *   applies   to segments whose far rows exceed max(h0, 8).
+ *   applies   to segments whose far rows exceed max(h0, 8) and with e <= 128.
  * Parameter vector (float32, SPALU_PRED_NPARAM): W1 (64 x 16 row-major) | b1 (64) |
  * W2 (2 x 64) | b2 (2).  Inference rounds the standardised features, the parameters and
  * the hidden activations to bfloat16 and accumulates in float32. */

@@ -332,7 +332,7 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0,
     p = opts.p_oversample
     h = min(nF, opts.h0)
     use_pred = (opts.predictor is not None or opts.record is not None) and A is not None \
-        and nF > max(opts.h0, pred.PROBE)
+        and nF > max(opts.h0, pred.PROBE) and e <= pred.EMAX
     predicted = False
     if use_pred:
         probe = sketch_matrix(opts.seed, l, sid, pred.PROBE, f_nodes, f_half) @ BF

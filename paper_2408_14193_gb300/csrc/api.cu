@@ -106,6 +106,7 @@ struct spalu_factor_s {
   std::vector<SolveCaps> caps;   // [1..L] solve-kernel capacities from the last factor
   int* d_tgt_all = nullptr;  // recorded targets of all levels (4 ints per segment)
   int* d_count = nullptr;    // export row counter
+  float4* d_nstat = nullptr; // per-node matrix statistics (predictor features)
   size_t tgt_ints = 0;
   spalu_predictor_t pred = nullptr;
   int pred_mode = PRED_OFF;
@@ -412,6 +413,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     }
     size_t tgt_off = 0;
     f->d_count = cv.take<int>(1);
+    f->d_nstat = cv.take<float4>((size_t)f->N);
     f->rowptr = cv.take<int>(f->N + 1);
     f->colind = cv.take<int>(f->nnz_cap);
     f->val = cv.take<double>(f->nnz_cap);
@@ -441,6 +443,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
       d.hs = cv.take<int>(nseg);
       d.nodes = cv.take<int>((size_t)nseg * p.capS);
       d.perm = cv.take<int>((size_t)nseg * p.capS);
+      d.snodes = cv.take<int>((size_t)nseg * p.capS);
       d.piv = cv.take<int>((size_t)nseg * p.capS);
       d.fp32 = f32 ? 1 : 0;
       d.T = real((size_t)nseg * p.capS * p.capS);
@@ -485,6 +488,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     f->lev[l].rowptr = f->rowptr;
     f->lev[l].colind = f->colind;
     f->lev[l].val = f->val;
+    f->lev[l].nstat = f->d_nstat;
   }
   f->caps.resize(L + 1);
   *out = f;
@@ -501,6 +505,7 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   if (f->pred_mode == PRED_RECORD && f->tgt_ints)
     CUDA_TRY(cudaMemsetAsync(f->d_tgt_all, 0, sizeof(int) * f->tgt_ints, s));
   if (L >= 1) launch_level_init_L(f->lev[L], s);
+  if (f->pred_mode != PRED_OFF) launch_node_stats(f->rowptr, f->colind, f->val, f->N, f->d_nstat, s);
   int t = tm.begin("leaf_factor", s);
   launch_leaf_factor(f->leaf, s);
   tm.end(t, s);

@@ -413,21 +413,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-__device__ __forceinline__ double block_minmax(double v, double* red, bool mx) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = mx ? fmax(v, w) : fmin(v, w);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = red[0];
-  for (int w = 1; w < nw; ++w) s = mx ? fmax(s, red[w]) : fmin(s, red[w]);
-  __syncthreads();
-  return s;
-}
-
 // ------------------------------------------------------------ far-row sketch
 // Yr[rr, c] = sum over far neighbour rows f of G[rr, f] B_F[f, c] for rr < hh (unscaled),
 // neighbours taken in chunks of ch (near ones get zero weight).  Yr has leading dimension ldy.
@@ -474,116 +459,187 @@ __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const T* F1, cons
 
 // ------------------------------------------------------------ learned rank predictor
 // (no counterpart in the paper; the definitions are those of the oracle's predictor module)
-__device__ __forceinline__ double csr_entry(const LevelDev& d, int u, int v) {
-  double a = 0.0;
-  for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p)
-    if (d.colind[p] == v) a += d.val[p];
-  return a;
+// Probe sketch Y8[r + PRED_PROBE c] = sum over the far rows of G[r, row] B[row, c], r < 8: the
+// first PRED_PROBE rows of the sketch matrix of this segment, unscaled.  Warps take rows in
+// turn; lanes hold columns lane + 32 q of a 64-column chunk in registers; the warps' sums meet
+// in Y8 (zeroed by the caller) through shared-memory atomics.
+template <typename T>
+__device__ void probe_sketch(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, int sid,
+                             int halves, int nnear, const int* nearlist, int e, T* Y8) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nrows = halves * S.nb;
+  for (int c0 = 0; c0 < e; c0 += 64) {
+    T acc[2][PRED_PROBE];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < PRED_PROBE; ++r) acc[q][r] = T(0);
+    for (int row = warp; row < nrows; row += nw) {
+      const int f = row % S.nb, t = row / S.nb;
+      bool isnear = false;
+      for (int a = 0; a < nnear; ++a) isnear |= (nearlist[a] == f);
+      if (isnear) continue;                                  // warp-uniform
+      int ri, i;
+      locate(S, f, ri, i);
+      const T g = lane < PRED_PROBE ? (T)sketch_gauss(d.seed, d.l, sid, lane, run_node(d, S.run[ri], i), t) : T(0);
+      T b[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int c = c0 + 32 * q + lane;
+        b[q] = c < e ? bval<T>(d, S, F1, F2, S.run[ri], i, t, c) : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < PRED_PROBE; ++r) {
+        const T gr = __shfl_sync(0xffffffffu, g, r);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[q][r] += gr * b[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c = c0 + 32 * q + lane;
+      if (c < e)
+#pragma unroll
+        for (int r = 0; r < PRED_PROBE; ++r) atomicAdd(&Y8[r + PRED_PROBE * c], acc[q][r]);
+    }
+  }
 }
 
-// Features of segment sid into xf[16] (shared).  Y holds the column-pivoted QR of the probe
-// (R on its first kp rows).  red: >= NW doubles of shared scratch.
+// Features of segment sid into xf[16] (shared), needs >= 2 warps; every thread calls it.
+// Warp 0: column-pivoted QR of the probe Y8 (PRED_PROBE x e, pitch PRED_PROBE, overwritten)
+// by Gram-Schmidt with exactly recomputed column norms, lane c owning columns c + 32 q; the
+// pivot is the largest norm, near-ties (relative 1e-12) to the lowest column.  Warp 1: the
+// coefficient statistics of the segment's nodes from the per-node table.
 template <typename T>
-__device__ void segment_features(const LevelDev& d, const SegCtx& S, int sid, int e, int nnear,
-                                 int nfar, const T* Y, int ldy, int kp, float* xf, double* red) {
-  const int* nodes = d.nodes + (size_t)sid * d.capS;
-  double lmin = 1e300, lmax = -1e300, lsum = 0.0, dsum = 0.0, ssum = 0.0, asum = 0.0;
-  for (int t = threadIdx.x; t < e; t += blockDim.x) {
-    const int u = nodes[t];
-    double dd = 0.0, off = 0.0, rs = 0.0, num = 0.0, den = 0.0;
-    for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p) {
-      const int j = d.colind[p];
-      const double a = d.val[p];
-      rs += a;
-      if (j == u) { dd += a; continue; }
-      off += fabs(a);
-      const double aj = csr_entry(d, j, u);
-      num += fabs(a - aj);
-      den += fabs(a) + fabs(aj);
-    }
-    dd = fabs(dd);
-    const double ld = dd > 0.0 ? log(dd) : log(1e-300);
-    lmin = fmin(lmin, ld);
-    lmax = fmax(lmax, ld);
-    lsum += ld;
-    dsum += (off > 0.0 && dd > 0.0) ? log(dd / off) : 0.0;
-    ssum += dd > 0.0 ? fabs(rs) / dd : 0.0;
-    asum += den > 0.0 ? num / den : 0.0;
-  }
-  lmin = block_minmax(lmin, red, false);
-  lmax = block_minmax(lmax, red, true);
-  const double mean = block_sum(lsum, red) / e;
-  dsum = block_sum(dsum, red);
-  ssum = block_sum(ssum, red);
-  asum = block_sum(asum, red);
-  double vsum = 0.0;                      // second pass: population variance of log d
-  for (int t = threadIdx.x; t < e; t += blockDim.x) {
-    const int u = nodes[t];
-    double dd = 0.0;
-    for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p)
-      if (d.colind[p] == u) dd += d.val[p];
-    dd = fabs(dd);
-    const double ld = dd > 0.0 ? log(dd) : log(1e-300);
-    vsum += (ld - mean) * (ld - mean);
-  }
-  vsum = block_sum(vsum, red);
-  if (threadIdx.x == 0) {
-    xf[0] = (float)(d.L - d.l);
-    xf[1] = (float)log2((double)e);
-    xf[2] = (float)log2(1.0 + S.nb);
-    xf[3] = (float)nnear;
-    xf[4] = (float)log2(1.0 + nfar);
-    xf[5] = (float)(lmin - mean);
-    xf[6] = (float)(lmax - mean);
-    xf[7] = (float)sqrt(vsum / e);
-    xf[8] = (float)(dsum / e);
-    xf[9] = (float)(ssum / e);
-    xf[10] = (float)(asum / e);
-    const double le = log10(d.eps);
+__device__ void probe_features(const LevelDev& d, int sid, int e, int nnear, int nfar, int nb,
+                               T* Y8, float* xf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
     const int nd = min(PRED_PROBE, e);
-    const double r0 = kp > 0 ? fabs((double)Y[0]) : 0.0;
-    const int js[5] = {1, 2, 3, 5, 7};
-    for (int q = 0; q < 5; ++q) {
-      const int j = js[q];
-      double v;
-      if (j >= nd || r0 == 0.0) v = -16.0 - le;
-      else {
-        const double rj = j < kp ? fabs((double)Y[j + (size_t)ldy * j]) : 0.0;
-        v = log10(fmax(rj / r0, 1e-16)) - le;
+    double rd[PRED_PROBE];
+#pragma unroll
+    for (int i = 0; i < PRED_PROBE; ++i) rd[i] = 0.0;
+    unsigned used = 0;                                       // bit q: column lane + 32 q pivoted
+    for (int i = 0; i < nd; ++i) {
+      double mx = 0.0;
+      int best = 1 << 30;
+      for (int q = 0, c = lane; c < e; ++q, c += 32) {
+        if (used >> q & 1) continue;
+        double sq = 0.0;
+        for (int r = 0; r < PRED_PROBE; ++r) sq += (double)Y8[r + PRED_PROBE * c] * (double)Y8[r + PRED_PROBE * c];
+        mx = fmax(mx, sqrt(sq));
       }
-      xf[11 + q] = (float)v;
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (mx <= 0.0) break;
+      const double thr = mx * (1.0 - TIE_RTOL);
+      for (int q = 0, c = lane; c < e; ++q, c += 32) {
+        if (used >> q & 1) continue;
+        double sq = 0.0;
+        for (int r = 0; r < PRED_PROBE; ++r) sq += (double)Y8[r + PRED_PROBE * c] * (double)Y8[r + PRED_PROBE * c];
+        if (sqrt(sq) >= thr) best = min(best, c);
+      }
+      for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+      T v[PRED_PROBE];
+      double pn = 0.0;
+#pragma unroll
+      for (int r = 0; r < PRED_PROBE; ++r) {
+        v[r] = Y8[r + PRED_PROBE * best];
+        pn += (double)v[r] * (double)v[r];
+      }
+      pn = sqrt(pn);
+      rd[i] = pn;
+      const T inv = (T)(1.0 / pn);
+#pragma unroll
+      for (int r = 0; r < PRED_PROBE; ++r) v[r] *= inv;
+      if ((best & 31) == lane) used |= 1u << (best >> 5);
+      __syncwarp();
+      for (int q = 0, c = lane; c < e; ++q, c += 32) {
+        if (used >> q & 1) continue;
+        T* col = Y8 + PRED_PROBE * c;
+        T dot = T(0);
+#pragma unroll
+        for (int r = 0; r < PRED_PROBE; ++r) dot += v[r] * col[r];
+#pragma unroll
+        for (int r = 0; r < PRED_PROBE; ++r) col[r] -= dot * v[r];
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const double le = log10(d.eps);
+      const int js[5] = {1, 2, 3, 5, 7};
+      for (int q = 0; q < 5; ++q) {
+        const int j = js[q];
+        double val;
+        if (j >= nd || rd[0] == 0.0) val = -16.0 - le;
+        else val = log10(fmax(rd[j] / rd[0], 1e-16)) - le;
+        xf[11 + q] = (float)val;
+      }
+    }
+  } else if (warp == 1) {
+    const int* nodes = d.nodes + (size_t)sid * d.capS;
+    double lmin = 1e300, lmax = -1e300, lsum = 0.0, dsum = 0.0, ssum = 0.0, asum = 0.0;
+    for (int t = lane; t < e; t += 32) {
+      const float4 st = d.nstat[nodes[t]];
+      lmin = fmin(lmin, (double)st.x);
+      lmax = fmax(lmax, (double)st.x);
+      lsum += st.x;
+      dsum += st.y;
+      ssum += st.z;
+      asum += st.w;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+      lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+      lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+      asum += __shfl_xor_sync(0xffffffffu, asum, o);
+    }
+    const double mean = lsum / e;
+    double vsum = 0.0;
+    for (int t = lane; t < e; t += 32) {
+      const double dv = (double)d.nstat[nodes[t]].x - mean;
+      vsum += dv * dv;
+    }
+    for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+    if (lane == 0) {
+      xf[0] = (float)(d.L - d.l);
+      xf[1] = (float)log2((double)e);
+      xf[2] = (float)log2(1.0 + nb);
+      xf[3] = (float)nnear;
+      xf[4] = (float)log2(1.0 + nfar);
+      xf[5] = (float)(lmin - mean);
+      xf[6] = (float)(lmax - mean);
+      xf[7] = (float)sqrt(vsum / e);
+      xf[8] = (float)(dsum / e);
+      xf[9] = (float)(ssum / e);
+      xf[10] = (float)(asum / e);
     }
   }
   __syncthreads();
 }
 
 // Measured ID error test ||B_r - B_s T||_F <= 10 eps ||B||_F on the exact B (all neighbour
-// rows, both halves of a non-symmetric B), chunked through Bc.
+// rows, both halves of a non-symmetric B): one thread per row of B, entries read directly.
 template <typename T>
 __device__ bool id_error_ok(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, int halves,
-                            int e, int k, const int* perm, const T* Tw, int ldt, T* Bc, int ch, double* red) {
+                            int e, int k, const int* perm, const T* Tw, int ldt, double* red) {
   const int r = e - k;
   double num = 0.0, den = 0.0;
-  for (int f0 = 0; f0 < S.nb; f0 += ch) {
-    const int nc = min(ch, S.nb - f0);
-    const int rows = halves * nc;
-    for (int x = threadIdx.x; x < rows * e; x += blockDim.x) {
-      int row = x % rows, c = x / rows;
-      int t = row / nc, jj = row % nc;
-      int ri, i;
-      locate(S, f0 + jj, ri, i);
-      const T v = bval<T>(d, S, F1, F2, S.run[ri], i, t, c);
-      Bc[row + (size_t)rows * c] = v;
-      den += (double)v * (double)v;
+  for (int row = threadIdx.x; row < halves * S.nb; row += blockDim.x) {
+    const int f = row % S.nb, t = row / S.nb;
+    int ri, i;
+    locate(S, f, ri, i);
+    const Run& R = S.run[ri];
+    for (int c = 0; c < e; ++c) {
+      const double v = (double)bval<T>(d, S, F1, F2, R, i, t, c);
+      den += v * v;
     }
-    __syncthreads();
-    for (int x = threadIdx.x; x < rows * r; x += blockDim.x) {
-      int row = x % rows, j = x / rows;
-      T s = Bc[row + (size_t)rows * perm[k + j]];
-      for (int a = 0; a < k; ++a) s -= Bc[row + (size_t)rows * perm[a]] * Tw[a + (size_t)ldt * j];
+    for (int j = 0; j < r; ++j) {
+      T s = bval<T>(d, S, F1, F2, R, i, t, perm[k + j]);
+      for (int a = 0; a < k; ++a) s -= bval<T>(d, S, F1, F2, R, i, t, perm[a]) * Tw[a + (size_t)ldt * j];
       num += (double)s * (double)s;
     }
-    __syncthreads();
   }
   num = block_sum(num, red);
   den = block_sum(den, red);
@@ -592,7 +648,7 @@ __device__ bool id_error_ok(const LevelDev& d, const SegCtx& S, const T* F1, con
 
 // ------------------------------------------------------------ sparsify: one CTA per segment
 template <typename T>
-__global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_bytes) {
+__global__ void __launch_bounds__(NW * 32, 4) sparsify_kernel(LevelDev d, int smem_bytes) {
   extern __shared__ double sm[];
   __shared__ SegCtx S;
   __shared__ double shr[NW * 32 + 3 * 64];
@@ -625,7 +681,10 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
       int a = x % e, b = x / e;
       Dg[a + (size_t)capS * b] = F1[(S.s1 + a) + ld * (S.s1 + b)] + F2[(S.s2 + a) + ld * (S.s2 + b)];
     }
-    for (int j = threadIdx.x; j < e; j += blockDim.x) perm_out[j] = j;
+    for (int j = threadIdx.x; j < e; j += blockDim.x) {
+      perm_out[j] = j;
+      d.snodes[(size_t)sid * capS + j] = d.nodes[(size_t)sid * capS + j];
+    }
     if (threadIdx.x == 0) { d.kk[sid] = e; d.hs[sid] = 0; }
     return;
   }
@@ -709,13 +768,15 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
   //      far rows, then the network's one-pass sketch size (PRED_PREDICT) or a training
   //      record of the features and the adaptive rank (PRED_RECORD)
   __shared__ float xf[PRED_NFEAT], zs[PRED_NFEAT], hid[PRED_NHID], pout[PRED_NOUT];
-  const bool use_pred = d.pred_mode != PRED_OFF && nF > max(d.h0, PRED_PROBE);
+  const bool use_pred = d.pred_mode != PRED_OFF && nF > max(d.h0, PRED_PROBE) && e <= PRED_EMAX;
   int h = (nF <= d.h0) ? nF : d.h0;
   bool predicted = false;
   if (use_pred) {
-    sketch_far<T>(d, S, F1, F2, sid, halves, nnear, nearlist, e, PRED_PROBE, Y, ldy, Bc, Gc, ch);
-    const int kp = block_cpqr<T>(Y, ldy, PRED_PROBE, e, 0.0, perm, vn1, vn2, ivn2, shr, flags, shi);
-    segment_features<T>(d, S, sid, e, nnear, nfar_sh, Y, ldy, kp, xf, shr);
+    for (int x = threadIdx.x; x < PRED_PROBE * e; x += blockDim.x) Y[x] = T(0);   // Y8, pitch 8
+    __syncthreads();
+    probe_sketch<T>(d, S, F1, F2, sid, halves, nnear, nearlist, e, Y);
+    __syncthreads();
+    probe_features<T>(d, sid, e, nnear, nfar_sh, S.nb, Y, xf);
     if (d.pred_mode == PRED_RECORD) {
       if (threadIdx.x < PRED_NFEAT) d.feat[(size_t)sid * PRED_NFEAT + threadIdx.x] = xf[threadIdx.x];
     } else {
@@ -776,7 +837,7 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
       if (ok) {
         block_interp<T>(Y, ldy, k, e, Tw, ldt, rinv);
         have_t = true;
-        ok = id_error_ok<T>(d, S, F1, F2, halves, e, k, perm, Tw, ldt, Bc, ch, shr);
+        ok = id_error_ok<T>(d, S, F1, F2, halves, e, k, perm, Tw, ldt, shr);
       }
       if (ok) break;
       fellback = true;
@@ -857,7 +918,10 @@ __global__ void __launch_bounds__(NW * 32) sparsify_kernel(LevelDev d, int smem_
     for (int x = threadIdx.x; x < e * e; x += blockDim.x) Dg[(x % e) + (size_t)capS * (x / e)] = Dw[x];
     for (int x = threadIdx.x; x < k * r; x += blockDim.x) Tg[(x % k) + (size_t)capS * (x / k)] = Tw[(x % k) + (size_t)ldt * (x / k)];
   }
-  for (int j = threadIdx.x; j < e; j += blockDim.x) perm_out[j] = perm[j];
+  for (int j = threadIdx.x; j < e; j += blockDim.x) {
+    perm_out[j] = perm[j];
+    d.snodes[(size_t)sid * capS + j] = d.nodes[(size_t)sid * capS + perm[j]];
+  }
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     d.piv[(size_t)sid * capS + j] = piv[j];
     Ig[j] = rinv[j];
@@ -1283,15 +1347,14 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, SolveCaps ca
   int* pivs = reinterpret_cast<int*>(invs + cap.lucap);
   const bool staged = r <= cap.lucap;
   const bool pstaged = (size_t)k * r <= (size_t)cap.pcap;
-  const int* perm = d.perm + (size_t)sid * capS;
-  const int* nodes = d.nodes + (size_t)sid * capS;
+  const int* snodes = d.snodes + (size_t)sid * capS;     // nodes in [skeleton | remainder] order
   const int* piv = d.piv + (size_t)sid * capS;
   const T* Tm = static_cast<const T*>(d.T) + (size_t)sid * capS * capS;
   const T* Dg = static_cast<const T*>(d.Dm) + (size_t)sid * capS * capS;
   const T* inv = static_cast<const T*>(d.Dinv) + (size_t)sid * capS;
   for (int x = threadIdx.x; x < e * SC; x += blockDim.x) {
     int a = x % e, c = x / e;
-    v[x] = c < nc ? (T)X[nodes[perm[a]] + (size_t)ld * c] : T(0);
+    v[x] = c < nc ? (T)X[snodes[a] + (size_t)ld * c] : T(0);
   }
   if (staged) {
     for (int x = threadIdx.x; x < r * r; x += blockDim.x)
@@ -1351,19 +1414,17 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, SolveCaps ca
   __syncthreads();
   for (int x = threadIdx.x; x < e * nc; x += blockDim.x) {
     int a = x % e, c = x / e;
-    X[nodes[perm[a]] + (size_t)ld * c] = (double)v[x];
+    X[snodes[a] + (size_t)ld * c] = (double)v[x];
   }
 }
 
-// Separator of each parent: forward y_p = L^{-1} P b_p, b_dP -= Z y_p (parents of one colour
-// at a time: two parents of the same colour share no boundary unknown); backward
-// x_p = U^{-1} (y_p - W x_dP).
+// Separator of each parent: forward y_p = L^{-1} P b_p, then b_dP -= Z y_p added atomically
+// (a boundary unknown is shared by up to four parents; the order of their contributions is
+// not fixed); backward x_p = U^{-1} (y_p - W x_dP).
 template <typename T>
-__global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd, int colour) {
+__global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd) {
   extern __shared__ double smd[];
   const int P = blockIdx.x;
-  const int Ip = P % d.gp.bx, Jp = P / d.gp.bx;
-  if (!bwd && ((Ip & 1) + 2 * (Jp & 1)) != colour) return;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
   if (kp == 0) return;
   if (kp > cap.yrows) { if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); return; }
@@ -1382,14 +1443,14 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps ca
   int* rows_sm = pivs + cap.lucap;                      // 2 * drows
   const bool staged = kp <= cap.lucap;
   const bool dstage = ndP <= cap.drows;
-  const bool pstaged = dstage && (size_t)ndP * kp <= (size_t)cap.qcap;
+  const int ldw = ndP | 1;                              // odd pitch of the staged W^T panel
+  const bool pstaged = dstage && (size_t)ldw * kp <= (size_t)cap.qcap;
   if (dstage) {
     for (int x = threadIdx.x; x < ndP; x += blockDim.x) {
       rows_sm[x] = tab[(size_t)x * TABW];
       rows_sm[cap.drows + x] = tab[(size_t)x * TABW + 7];
     }
   }
-  __syncthreads();          // rows_sm is read by other threads below
   auto rowpos = [&](int a) { return dstage ? rows_sm[a] : tab[(size_t)a * TABW]; };
   auto rownode = [&](int a) { return dstage ? rows_sm[cap.drows + a] : tab[(size_t)a * TABW + 7]; };
   for (int x = threadIdx.x; x < kp * SC; x += blockDim.x) {
@@ -1400,10 +1461,13 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps ca
   const size_t ldl = staged ? (size_t)kp : ldp;
   const T* ivs = staged ? invs : inv;
   const int* pvs = staged ? pivs : piv;
-  if (!bwd) {
+  auto stage_lu = [&]() {
     if (staged)
       for (int x = threadIdx.x; x < kp * kp; x += blockDim.x) U[x] = M[(Dp + x % kp) + ldp * (Dp + x / kp)];
-    __syncthreads();
+  };
+  if (!bwd) stage_lu();
+  __syncthreads();          // rows_sm, y (and the LU block) are read by other threads below
+  if (!bwd) {
     lower_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
     __syncthreads();
     // b_dP -= Z y_p, Z = M[dP rows, separator columns]
@@ -1416,7 +1480,7 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps ca
                  pstaged ? (size_t)ndP : ldp, y, kp,
                  [&](int a, const T* acc) {
                    double* xa = X + rownode(a);
-                   for (int c = 0; c < nc; ++c) xa[(size_t)ld * c] -= (double)acc[c];
+                   for (int c = 0; c < nc; ++c) atomicAdd(xa + (size_t)ld * c, -(double)acc[c]);
                  });
   } else {
     if (dstage) {
@@ -1425,38 +1489,32 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps ca
         xd[x] = c < nc ? (T)X[rows_sm[cap.drows + b] + (size_t)ld * c] : T(0);
       }
     }
-    // W^T panel: Wt[b + ndP j] = M[(Dp + j) + ldp * pos(b)]
+    T* Wt = U;                                            // W^T panel, pitch ldw
     if (pstaged)
       for (int x = threadIdx.x; x < ndP * kp; x += blockDim.x) {
         const int j = x % kp, b = x / kp;
-        U[b + (size_t)ndP * j] = M[(Dp + j) + ldp * rows_sm[b]];
+        Wt[b + (size_t)ldw * j] = M[(Dp + j) + ldp * rows_sm[b]];
       }
     __syncthreads();
-    // y_p -= W x_dP
-    for (int a = threadIdx.x; a < kp; a += blockDim.x) {
-      T acc[SC];
-#pragma unroll
-      for (int c = 0; c < SC; ++c) acc[c] = T(0);
+    // y_p -= W x_dP, one thread per (row a, right-hand side c)
+    for (int x = threadIdx.x; x < kp * nc; x += blockDim.x) {
+      const int a = x % kp, c = x / kp;
+      T acc = T(0);
       if (pstaged) {
-        const T* Wa = U + (size_t)ndP * a;
+        const T* wa = Wt + (size_t)ldw * a;
+        const T* xc = xd + (size_t)ndP * c;
 #pragma unroll 4
-        for (int b = 0; b < ndP; ++b) {
-          const T w = Wa[b];
-#pragma unroll
-          for (int c = 0; c < SC; ++c) acc[c] += w * xd[b + ndP * c];
-        }
+        for (int b = 0; b < ndP; ++b) acc += wa[b] * xc[b];
+      } else if (dstage) {
+        const T* xc = xd + (size_t)ndP * c;
+        for (int b = 0; b < ndP; ++b) acc += M[(Dp + a) + ldp * rows_sm[b]] * xc[b];
       } else {
-        for (int b = 0; b < ndP; ++b) {
-          const T w = M[(Dp + a) + ldp * rowpos(b)];
-          const int nb = rownode(b);
-          for (int c = 0; c < nc; ++c) acc[c] += w * (T)X[nb + (size_t)ld * c];
-        }
+        for (int b = 0; b < ndP; ++b) acc += M[(Dp + a) + ldp * rowpos(b)] * (T)X[rownode(b) + (size_t)ld * c];
       }
-      for (int c = 0; c < SC; ++c) y[a + kp * c] -= acc[c];
+      y[a + kp * c] -= acc;
     }
     __syncthreads();
-    if (staged)
-      for (int x = threadIdx.x; x < kp * kp; x += blockDim.x) U[x] = M[(Dp + x % kp) + ldp * (Dp + x / kp)];
+    stage_lu();             // the panel is consumed: U takes the LU block
     __syncthreads();
     upper_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, ivs, nc);
   }
@@ -1466,6 +1524,7 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps ca
     X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] = (double)y[x];
   }
 }
+
 
 }  // namespace
 
@@ -1562,7 +1621,7 @@ bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
   }
   // a segment panel is k x r <= (e/2)^2; a separator panel |dP| x kp
   sc.pcap = (int)mx(0, mn((long long)(sc.vrows / 2 + 1) * (sc.vrows / 2 + 1), (budget - seg_fixed) / (2 * TB)));
-  sc.qcap = (int)mx(0, mn((long long)sc.drows * sc.yrows, (budget - sep_fixed) / TB));
+  sc.qcap = (int)mx(0, mn((long long)(sc.drows | 1) * sc.yrows, (budget - sep_fixed) / TB));
   sc.seg_smem = (size_t)(seg_fixed + 2 * TB * sc.pcap);
   sc.sep_smem = (size_t)(sep_fixed + TB * mx((long long)sc.lucap * sc.lucap, sc.qcap));
   *out = sc;
@@ -1576,22 +1635,20 @@ static void level_solve(const LevelDev& d, const SolveCaps& sc, double* X, int n
   for (int c0 = 0; c0 < nrhs; c0 += SC) {
     const int nc = nrhs - c0 < SC ? nrhs - c0 : SC;
     double* Xc = X + (size_t)ld * c0;
-    if (!bwd) {
-      if (d.g.nseg() > 0) {
-        note_launch();
-        seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, ld, 0);
-      }
-      for (int colour = 0; colour < 4; ++colour) {
-        note_launch();
-        sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, ld, 0, colour);
-      }
-    } else {
+    auto seg_go = [&](int dir) {
       note_launch();
-      sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, ld, 1, 0);
-      if (d.g.nseg() > 0) {
-        note_launch();
-        seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, ld, 1);
-      }
+      seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, ld, dir);
+    };
+    auto sep_go = [&](int dir) {
+      note_launch();
+      sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, ld, dir);
+    };
+    if (!bwd) {
+      if (d.g.nseg() > 0) seg_go(0);
+      sep_go(0);
+    } else {
+      sep_go(1);
+      if (d.g.nseg() > 0) seg_go(1);
     }
   }
 }

@@ -22,6 +22,35 @@ namespace {
 constexpr int GW = 8;                  // warps per block of the gradient kernel
 constexpr int NACC = PRED_NPARAM + 1;  // gradient entries + the loss sum
 
+// Per grid node u of the original matrix (features 5-10 of the segments): log d_u with
+// d_u = |A_uu|, log(d_u / s_u) with s_u = sum_{j != u} |A_uj|, |sum_j A_uj| / d_u, and
+// sum_{j!=u} |A_uj - A_ju| / sum_{j!=u} (|A_uj| + |A_ju|); computed in FP64, stored as float.
+__global__ void node_stats_kernel(const int* __restrict__ rowptr, const int* __restrict__ colind,
+                                  const double* __restrict__ val, int n, float4* __restrict__ out) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    double dd = 0.0, off = 0.0, rs = 0.0, num = 0.0, den = 0.0;
+    for (int p = rowptr[u]; p < rowptr[u + 1]; ++p) {
+      const int j = colind[p];
+      const double a = val[p];
+      rs += a;
+      if (j == u) { dd += a; continue; }
+      off += fabs(a);
+      double aj = 0.0;
+      for (int q = rowptr[j]; q < rowptr[j + 1]; ++q)
+        if (colind[q] == u) aj += val[q];
+      num += fabs(a - aj);
+      den += fabs(a) + fabs(aj);
+    }
+    dd = fabs(dd);
+    float4 r;
+    r.x = (float)(dd > 0.0 ? log(dd) : log(1e-300));
+    r.y = (float)((off > 0.0 && dd > 0.0) ? log(dd / off) : 0.0);
+    r.z = (float)(dd > 0.0 ? fabs(rs) / dd : 0.0);
+    r.w = (float)(den > 0.0 ? num / den : 0.0);
+    out[u] = r;
+  }
+}
+
 __global__ void pred_fit_norm_kernel(const float* X, int n, PredDev* P) {
   __shared__ double red[32];
   const int col = blockIdx.x;
@@ -207,6 +236,15 @@ __global__ void __launch_bounds__(1024) pred_export_kernel(const float* __restri
 int pred_grad_blocks(int nb) {
   int g = (nb + GW * 8 - 1) / (GW * 8);
   return g < 1 ? 1 : (g > PRED_MAXBLK ? PRED_MAXBLK : g);
+}
+
+void launch_node_stats(const int* rowptr, const int* colind, const double* val, int n, float4* out,
+                       cudaStream_t s) {
+  if (n <= 0) return;
+  int g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  note_launch();
+  node_stats_kernel<<<g, 256, 0, s>>>(rowptr, colind, val, n, out);
 }
 
 void launch_pred_fit_norm(const float* X, int n, PredDev* P, cudaStream_t s) {

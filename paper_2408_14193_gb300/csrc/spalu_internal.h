@@ -40,6 +40,7 @@ constexpr int PRED_NOUT = 2;
 constexpr int PRED_NPARAM = PRED_NHID * PRED_NFEAT + PRED_NHID + PRED_NOUT * PRED_NHID + PRED_NOUT;
 constexpr int PRED_PROBE = 8;          // rows of the probe sketch behind features 11-15
 constexpr int PRED_MAXBLK = 256;       // blocks of the training gradient kernel
+constexpr int PRED_EMAX = 128;         // largest segment the predictor serves
 constexpr int PRED_OFF_B1 = PRED_NHID * PRED_NFEAT;
 constexpr int PRED_OFF_W2 = PRED_OFF_B1 + PRED_NHID;
 constexpr int PRED_OFF_B2 = PRED_OFF_W2 + PRED_NOUT * PRED_NHID;
@@ -128,6 +129,7 @@ struct LevelDev {
   int* hs;          // [nseg] final sketch size (statistics)
   int* nodes;       // [nseg * capS] grid nodes in pre-ID order
   int* perm;        // [nseg * capS] column order of the ID (first kk = skeleton)
+  int* snodes;      // [nseg * capS] grid nodes in the ID order (nodes[perm[a]]), for the solve
   int* piv;         // [nseg * capS] pivots of the remainder LU
   void* T;          // [nseg * capS * capS] interpolation matrices, k x (e-k), ld capS
   void* Dm;         // [nseg * capS * capS] [A_ss' | Z ; W | LU(A_rr)], ld capS
@@ -156,6 +158,7 @@ struct LevelDev {
   const int* rowptr;        // original matrix (features 5-10)
   const int* colind;
   const double* val;
+  const float4* nstat;      // per grid node {log|A_uu|, log(|A_uu|/off), |row sum|/|A_uu|, asymmetry}
 };
 
 // Shared-memory capacities of the solve kernels of one level, set by the host from the
@@ -211,6 +214,8 @@ bool level_solve_caps(const LevelDev& d, const int* lstat, SolveCaps* out);
 void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
 void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
 
+void launch_node_stats(const int* rowptr, const int* colind, const double* val, int n, float4* out,
+                       cudaStream_t s);
 void launch_pred_fit_norm(const float* X, int n, PredDev* P, cudaStream_t s);
 void launch_pred_grad(const float* params, const PredDev* P, const float* X, const float* Y, int r0, int nb,
                       float* partial, float* grad, int* step, cudaStream_t s);

@@ -142,7 +142,9 @@ def test_solve_aliasing_and_host_entry_points():
     Y = B.clone()
     f.solve(Y, Y)                                   # X may alias B
     torch.cuda.synchronize()
-    assert torch.equal(X, Y)
+    # separator updates of shared boundary unknowns are atomic additions, so two solves agree
+    # to rounding, not bit for bit
+    assert torch.linalg.norm(X - Y) <= 1e-12 * torch.linalg.norm(X)
     g = Factor(nd, eps_id=1e-8, symmetric=1)
     g.factor_host(P.A.indptr, P.A.indices, P.A.data)
     Xh, it, rel = g.solve_host(np.ascontiguousarray(P.B.T), refine=True)
