@@ -177,14 +177,15 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 
 // ------------------------------------------------------------ column-pivoted QR
 // Businger-Golub Householder QR with column pivoting of Y (m x e, ld ldy, precision T),
-// stopped at the first step i with |R_ii| <= eps |R_00|.  Column norms are tracked and
-// downdated in FP64 (with the Drmac-Bujanovic recomputation guard) and the pivot is chosen
-// from them; the Householder products and their column sums run in T.  perm receives the
-// column order; on exit the first k rows of Y hold [R_1 R_2] in the permuted order.
-// Returns k.  sh: >= NW*32 + 3*64 doubles of shared scratch; flags, ivn2: >= e entries.
+// stopped at the first step i with |R_ii| <= eps |R_00|.  Squared column norms are tracked
+// and downdated in FP64 — s <- s - R_ij^2, recomputed when s <= sqrt(eps_64) s_ref (the
+// Drmac-Bujanovic guard written for squared norms: no division or square root per column and
+// step) — and the pivot is chosen from them; the Householder products and their column sums
+// run in T.  perm receives the column order; on exit the first k rows of Y hold [R_1 R_2] in
+// the permuted order.  Returns k.  sh: >= NW*32 + 3*64 doubles of shared scratch; flags: >= e.
 template <typename T>
 __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1,
-                          double* vn2, double* ivn2, double* sh, int* flags, int* shi) {
+                          double* vn2, double* sh, int* flags, int* shi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* part = reinterpret_cast<T*>(sh);                   // [NW][32] partial dots
   T* coef = reinterpret_cast<T*>(sh + NW * 32);         // [64]
@@ -197,14 +198,13 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
     for (int r = lane; r < m; r += 32) { T v = Y[r + (size_t)ldy * j]; s += v * v; }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
-      const double nv = sqrt((double)s);
-      vn1[j] = nv;
-      vn2[j] = nv;
-      ivn2[j] = nv > 0.0 ? 1.0 / nv : 0.0;
+      vn1[j] = (double)s;
+      vn2[j] = (double)s;
     }
   }
   __syncthreads();
   const double tol3z = sqrt(DBL_EPSILON);
+  const double tie = (1.0 - TIE_RTOL) * (1.0 - TIE_RTOL);   // on squared norms
   const int kmax = min(m, e);
   double ref = 0.0;
   int k = kmax;
@@ -217,7 +217,7 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
       long long mx = -1;
       for (int j = i + lane; j < e; j += 32) mx = max(mx, dbits(vn1[j]));
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      const long long thr = dbits(__longlong_as_double(mx) * (1.0 - TIE_RTOL));
+      const long long thr = dbits(__longlong_as_double(mx) * tie);
       int best = e;
       for (int j = i + lane; j < e; j += 32)
         if (dbits(vn1[j]) >= thr && j < best) best = j;
@@ -236,7 +236,6 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
         int t = perm[i]; perm[i] = perm[p]; perm[p] = t;
         double a = vn1[i]; vn1[i] = vn1[p]; vn1[p] = a;
         a = vn2[i]; vn2[i] = vn2[p]; vn2[p] = a;
-        a = ivn2[i]; ivn2[i] = ivn2[p]; ivn2[p] = a;
       }
       __syncthreads();
     }
@@ -292,19 +291,16 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
       }
       __syncthreads();
     }
-    // FP64 norm downdates, one lane per column; the guarded recomputations afterwards
+    // FP64 downdates of the squared norms, one lane per column; guarded recomputations after
     if (warp == wd) {
       for (int j = i + 1 + lane; j < e; j += 32) {
-        const double nv = vn1[j];
+        const double sq = vn1[j];
         int fl = 0;
-        if (nv != 0.0) {
-          const double inv = 1.0 / nv;
-          const double q = fabs((double)Y[i + (size_t)ldy * j]) * inv;
-          const double temp = fmax(1.0 - q * q, 0.0);
-          const double r2 = nv * ivn2[j];
-          const double temp2 = temp * r2 * r2;
-          if (temp2 <= tol3z) fl = 1;
-          else vn1[j] = nv * sqrt(temp);
+        if (sq != 0.0) {
+          const double rij = (double)Y[i + (size_t)ldy * j];
+          const double sn = fmax(sq - rij * rij, 0.0);
+          if (sn <= tol3z * vn2[j]) fl = 1;
+          else vn1[j] = sn;
         }
         flags[j] = fl;
       }
@@ -316,10 +312,8 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
       for (int r = i + 1 + lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * j]; s += v * v; }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) {
-        const double nv = sqrt(s);
-        vn1[j] = nv;
-        vn2[j] = nv;
-        ivn2[j] = nv > 0.0 ? 1.0 / nv : 0.0;
+        vn1[j] = s;
+        vn2[j] = s;
       }
     }
     if (threadIdx.x == 0) Y[i + (size_t)ldy * i] = (T)scal[0];
@@ -722,7 +716,7 @@ __global__ void __launch_bounds__(NW * 32, 4) sparsify_kernel(LevelDev d, int sm
   // working storage: vectors and sketch chunks in shared memory; Y, D, T too when they
   // fit, else the global scratch of this segment
   const size_t TD = sizeof(T);
-  const size_t small_b = (3 * (size_t)e) * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * TD + 64;
+  const size_t small_b = (2 * (size_t)e) * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * TD + 64;
   const size_t per_ch_b = (size_t)halves * (e + hmax) * TD;
   const size_t ydt_b = ((size_t)mmax * e + 2 * (size_t)e * e) * TD;
   int ch = SK_CHUNK;
@@ -733,14 +727,13 @@ __global__ void __launch_bounds__(NW * 32, 4) sparsify_kernel(LevelDev d, int sm
     if (ch < 1) { ch = 1; if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); }
   }
   T *Y, *Dw, *Tw, *Bc, *Gc, *rinv;
-  double *vn1, *vn2, *ivn2;
+  double *vn1, *vn2;
   int *perm, *piv, *flags;
   int ldy, ldd, ldt;
   {
     char* q = reinterpret_cast<char*>(sm);
     vn1 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
     vn2 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
-    ivn2 = reinterpret_cast<double*>(q); q += (size_t)e * 8;
     perm = reinterpret_cast<int*>(q); q += (size_t)e * 4;
     piv = reinterpret_cast<int*>(q); q += (size_t)e * 4;
     flags = reinterpret_cast<int*>(q); q += ((size_t)e + 4) * 4;
@@ -828,7 +821,7 @@ __global__ void __launch_bounds__(NW * 32, 4) sparsify_kernel(LevelDev d, int sm
       for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
     }
     __syncthreads();
-    k = block_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, ivn2, shr, flags, shi);
+    k = block_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
     ++passes;
     if (predicted) {          // the one-pass ID stands if it passes the measured-error test
       predicted = false;
@@ -1532,14 +1525,14 @@ size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes) 
   const size_t halves = symmetric ? 1 : 2;
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
   const size_t mmax = halves * NEAR_MAX + hcap;
-  const size_t small_b = 3 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
+  const size_t small_b = 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
   return small_b + (SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e) * tbytes;
 }
 
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes) {
   const size_t halves = symmetric ? 1 : 2;
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
-  return 3 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64 + halves * (e + hcap) * tbytes;
+  return 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64 + halves * (e + hcap) * tbytes;
 }
 
 void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
