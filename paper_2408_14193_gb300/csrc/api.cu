@@ -25,7 +25,8 @@ struct spalu_nd_s {
 
 struct GmresWork {
   int nrhs = 0, m = 0;
-  double* V = nullptr;      // (m+1) * N * nrhs
+  double* V = nullptr;      // (m+1) * N * nrhs   Krylov basis
+  double* Z = nullptr;      // m * N * nrhs       M^{-1} V_j, kept for the update (no final solve)
   double* W = nullptr;      // N * nrhs
   double* R = nullptr;      // N * nrhs
   double* part = nullptr;   // partial sums
@@ -231,15 +232,6 @@ __global__ void scale_kernel(int n, int nrhs, const double* s, const double* x, 
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x)
     y[r + (size_t)ldy * c] = x[r + (size_t)ldx * c] * di;
-}
-
-__global__ void copy_cols_kernel(int n, int nrhs, const double* x, int ldx, double* y, int ldy) {
-  long long tot = (long long)n * nrhs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(e % n), c = (int)(e / n);
-    y[r + (size_t)ldy * c] = x[r + (size_t)ldx * c];
-  }
 }
 
 int grid_for(long long n) {
@@ -595,10 +587,11 @@ static spalu_status gmres_alloc(spalu_factor_t f, int nrhs) {
   GmresWork& w = f->gw;
   const int m = f->o.gmres_m;
   if (w.nrhs >= nrhs && w.m == m) return SPALU_OK;
-  cudaFree(w.V); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
   w = GmresWork();
   size_t N = f->N;
   if (cudaMalloc(&w.V, sizeof(double) * (m + 1) * N * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.Z, sizeof(double) * (size_t)m * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.W, sizeof(double) * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.R, sizeof(double) * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.part, sizeof(double) * 1024 * nrhs) != cudaSuccess ||
@@ -647,6 +640,7 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
   const int maxit = f->o.gmres_maxit;
   const size_t ldv = (size_t)N;
   auto Vj = [&](int j) { return w.V + (size_t)j * ldv * nrhs; };
+  auto Zj = [&](int j) { return w.Z + (size_t)j * ldv * nrhs; };
   std::vector<double> bn(nrhs), beta(nrhs), hh((size_t)(m + 2) * nrhs);
   double* dvec = w.vec;   // [0, nrhs): norms; [nrhs, 2 nrhs): scratch
   dots(f, B, ld, B, ld, nrhs, dvec, 1, s);
@@ -683,12 +677,10 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     }
     int jl = -1;
     for (int j = 0; j < m; ++j) {
-      // W = A M^{-1} V_j
+      // Z_j = M^{-1} V_j (kept), V_{j+1} = A Z_j
+      if ((st = spalu_solve(f, Vj(j), Zj(j), nrhs, (int)ldv, stream)) != SPALU_OK) return st;
       note_launch();
-      copy_cols_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, Vj(j), (int)ldv, w.W, (int)ldv);
-      if ((st = spalu_solve(f, w.W, w.W, nrhs, (int)ldv, stream)) != SPALU_OK) return st;
-      note_launch();
-      spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, w.W, (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, nrhs);
+      spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, Zj(j), (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, nrhs);
       // modified Gram-Schmidt
       for (int i = 0; i <= j; ++i) {
         dots(f, Vj(j + 1), (int)ldv, Vj(i), (int)ldv, nrhs, w.hcol + (size_t)i * nrhs, 0, s);
@@ -734,17 +726,12 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
         ycoef[(size_t)i * nrhs + c] = (done(c) || Hc[i + (m + 1) * i] == 0.0) ? 0.0 : sum / Hc[i + (m + 1) * i];
       }
     }
-    CUDA_TRY(cudaMemsetAsync(w.W, 0, sizeof(double) * ldv * nrhs, s));
+    // X += M^{-1} V y = sum_i y_i Z_i
     CUDA_TRY(cudaMemcpyAsync(w.hcol, ycoef.data(), sizeof(double) * kdim * nrhs, cudaMemcpyHostToDevice, s));
     for (int i = 0; i < kdim; ++i) {
       note_launch();
-      axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, w.hcol + (size_t)i * nrhs, Vj(i), (int)ldv, w.W, (int)ldv);
+      axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, w.hcol + (size_t)i * nrhs, Zj(i), (int)ldv, X, ld);
     }
-    if ((st = spalu_solve(f, w.W, w.W, nrhs, (int)ldv, stream)) != SPALU_OK) return st;
-    std::vector<double> ones(nrhs, 1.0);
-    CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, ones.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-    note_launch();
-    axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, dvec + nrhs, w.W, (int)ldv, X, ld);
     if ((st = residual()) != SPALU_OK) return st;
   }
   bool conv = true;
@@ -1026,7 +1013,7 @@ void spalu_factor_destroy(spalu_factor_t f) {
   if (!f) return;
   cudaFree(f->arena);
   GmresWork& w = f->gw;
-  cudaFree(w.V); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
   delete f;
 }
 

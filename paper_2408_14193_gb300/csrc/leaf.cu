@@ -94,10 +94,12 @@ __device__ __forceinline__ void sweep_L(const BandT& B, int j0, In in, Out out) 
       if (j < NI) {
         const int dsw = B.p(j) - j;     // 0..15: the interchange stays in the window
         T a = W[u], b = a;
+        if (__any_sync(__activemask(), dsw != 0)) {   // skipped when no lane interchanges
 #pragma unroll
-        for (int r = 1; r < 16; ++r)
-          if (r == dsw) { b = W[(u + r) & 15]; W[(u + r) & 15] = a; }
-        W[u] = b;
+          for (int r = 1; r < 16; ++r)
+            if (r == dsw) { b = W[(u + r) & 15]; W[(u + r) & 15] = a; }
+          W[u] = b;
+        }
 #pragma unroll
         for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= B.l(r, j) * b;
         out(j, b);
@@ -333,60 +335,205 @@ __global__ void __launch_bounds__(FTH) leaf_factor_kernel(LeafDev d) {
 // One thread per (leaf, right-hand side).  Forward (leaf part of W~): X[I] <- A_II^{-1} X[I];
 // the side unknowns are updated afterwards by sep_update_fwd_kernel.  Backward (leaf part of
 // V~): X[I] <- X[I] - A_II^{-1} (A_Id x_d).  The intermediate L^{-1} P b goes through ybuf.
-template <typename T, int KUW>
-__global__ void __launch_bounds__(128) leaf_solve_kernel(LeafDev d, double* X, int nrhs, int ld, int bwd) {
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// One thread per (leaf, right-hand side slot), LPB leaves x 16 slots per CTA.  The band
+// columns of the next block of steps (16 for L, KUW for U) are copied into a double-buffered
+// shared-memory stage with cp.async while the current block is swept, so the sequential
+// sweeps read their factor entries from shared memory without waiting on L2.
+constexpr int SLOT = 16;   // right-hand-side slots per leaf and launch
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
+  if constexpr (sizeof(T) == 8) cp_async8(smem, gmem); else cp_async4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename T, int KUW, int LPB>
+__global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, double* X, int nrhs, int ld, int bwd) {
+  extern __shared__ double lsm[];
+  constexpr int LST = SLOT * SLOT;                    // L stage per leaf: 16 columns x 16 (r = 1..15)
+  constexpr int UST = KUW * KUW;                      // U stage per leaf: KUW columns x KUW (r = 0 -> 1/U_jj)
+  constexpr int RMAX = KUW - 1 < KV ? KUW - 1 : KV;
+  T* stg = reinterpret_cast<T*>(lsm);                 // 2 buffers
   const int nbox = d.g.nbox();
-  if (gid >= (long long)nbox * nrhs) return;
-  const int b = (int)(gid / nrhs), c = (int)(gid % nrhs);
-  const int I = b % d.g.bx, J = b / d.g.bx;
+  const int sub = threadIdx.x / SLOT, c = threadIdx.x % SLOT;
+  const int b0 = blockIdx.x * LPB;
+  const int b = b0 + sub;
+  const bool active = b < nbox && c < nrhs;
+  const int bb = b < nbox ? b : nbox - 1;
+  const T* gband = reinterpret_cast<const T*>(d.band);
+  const T* ginv = reinterpret_cast<const T*>(d.invd);
+  const size_t bufL = (size_t)LPB * (LST + SLOT);     // values + pivots (pivots stored as T slots)
+  const size_t bufU = (size_t)LPB * UST;
+  const size_t bufsz = bufL > bufU ? bufL : bufU;
+  const int I = bb % d.g.bx, J = bb / d.g.bx;
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
-  Band<T, true> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
-                   reinterpret_cast<const T*>(d.invd) + (size_t)b * NI};
-  T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
+  T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)bb * NI * QL;
   double* Xc = X + (size_t)ld * c;
   auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
-  if (!bwd) {
-    sweep_L<T>(Bd, 0, [&](int j) { return (T)Xc[node_of(j)]; },
-               [&](int j, T y) { yb[(size_t)j * QL + c] = y; });
-    sweep_U<T, KUW>(Bd, [&](int j) { return yb[(size_t)j * QL + c]; },
-                    [&](int j, T x) { Xc[node_of(j)] = (double)x; });
-  } else {
-    auto coupling = [&](int j) {
+
+  // ---- L sweep: y = L^{-1} P x, blocks of 16 steps
+  auto issue_L = [&](int blk, int buf) {
+    T* S = stg + (size_t)buf * bufsz;
+    const int j0 = blk * SLOT;
+    for (int x = threadIdx.x; x < LPB * SLOT * (SLOT - 1); x += blockDim.x) {
+      const int sl = x / (SLOT * (SLOT - 1)), rem = x % (SLOT * (SLOT - 1));
+      const int u = rem / (SLOT - 1), r = rem % (SLOT - 1) + 1;
+      const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
+      if (j0 + u < NI) cp_async_t(S + (size_t)sl * LST + u * SLOT + r, gband + (size_t)lb * LDAB * NI + (KV + r) + LDAB * (j0 + u));
+    }
+    int* P = reinterpret_cast<int*>(S + (size_t)LPB * LST);
+    for (int x = threadIdx.x; x < LPB * SLOT; x += blockDim.x) {
+      const int sl = x / SLOT, u = x % SLOT;
+      const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
+      if (j0 + u < NI) cp_async4(P + x, d.piv + (size_t)lb * NI + j0 + u);
+    }
+    cp_async_commit();
+  };
+  const int nbl = (NI + SLOT - 1) / SLOT;
+  T W[16];
+  if (active) {
+    if (!bwd) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) W[r] = (T)Xc[node_of(r)];
+    } else {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) W[r] = T(0);
+    }
+  }
+  auto coupling = [&](int j) {            // (A_Id x_d)_j for the backward sweep
+    T v = T(0);
+    const int lx = j % LEAF, ly = j / LEAF;
+    if (lx == 0 || ly == 0 || lx == LEAF - 1 || ly == LEAF - 1) {
       const int node = node_of(j);
-      T v = T(0);
-      const int lx = j % LEAF, ly = j / LEAF;
-      if (lx == 0 || ly == 0 || lx == LEAF - 1 || ly == LEAF - 1) {
-        for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
-          const int cc = d.colind[p];
-          const int cx = cc % nx - x0, cy = cc / nx - y0;
-          if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)(d.val[p] * Xc[cc]);
+      for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
+        const int cc = d.colind[p];
+        const int cx = cc % nx - x0, cy = cc / nx - y0;
+        if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)(d.val[p] * Xc[cc]);
+      }
+    }
+    return v;
+  };
+  if (active && bwd) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) W[r] = coupling(r);
+  }
+  issue_L(0, 0);
+  for (int blk = 0; blk < nbl; ++blk) {
+    if (blk + 1 < nbl) { issue_L(blk + 1, (blk + 1) & 1); cp_async_wait<1>(); }
+    else cp_async_wait<0>();
+    __syncthreads();
+    const T* S = stg + (size_t)(blk & 1) * bufsz + (size_t)sub * LST;
+    const int* P = reinterpret_cast<const int*>(stg + (size_t)(blk & 1) * bufsz + (size_t)LPB * LST) + sub * SLOT;
+    if (active) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int j = blk * SLOT + u;
+        if (j < NI) {
+          const int dsw = P[u] - j;
+          T a = W[u], bv = a;
+          if (__any_sync(__activemask(), dsw != 0)) {
+#pragma unroll
+            for (int r = 1; r < 16; ++r)
+              if (r == dsw) { bv = W[(u + r) & 15]; W[(u + r) & 15] = a; }
+            W[u] = bv;
+          }
+#pragma unroll
+          for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= S[u * SLOT + r] * bv;
+          yb[(size_t)j * QL + c] = bv;
+          W[u] = (j + 16 < NI) ? (!bwd ? (T)Xc[node_of(j + 16)] : coupling(j + 16)) : T(0);
         }
       }
-      return v;
-    };
-    sweep_L<T>(Bd, 0, coupling, [&](int j, T y) { yb[(size_t)j * QL + c] = y; });
-    sweep_U<T, KUW>(Bd, [&](int j) { return yb[(size_t)j * QL + c]; },
-                    [&](int j, T x) { Xc[node_of(j)] -= (double)x; });
+    }
+    __syncthreads();
+  }
+
+  // ---- U sweep: x = U^{-1} y, blocks of KUW steps from the bottom
+  auto issue_U = [&](int blk, int buf) {
+    T* S = stg + (size_t)buf * bufsz;
+    const int t0 = blk * KUW;
+    for (int x = threadIdx.x; x < LPB * KUW * KUW; x += blockDim.x) {
+      const int sl = x / (KUW * KUW), rem = x % (KUW * KUW);
+      const int u = rem / KUW, r = rem % KUW;
+      const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
+      const int j = NI - 1 - (t0 + u);
+      if (j >= 0 && r <= RMAX) {
+        if (r == 0) cp_async_t(S + x, ginv + (size_t)lb * NI + j);
+        else cp_async_t(S + x, gband + (size_t)lb * LDAB * NI + (KV - r) + LDAB * j);
+      }
+    }
+    cp_async_commit();
+  };
+  const int nbu = (NI + KUW - 1) / KUW;
+  T V[KUW];
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < KUW; ++r) V[r] = (NI - 1 - r >= 0) ? yb[(size_t)(NI - 1 - r) * QL + c] : T(0);
+  }
+  issue_U(0, 0);
+  for (int blk = 0; blk < nbu; ++blk) {
+    if (blk + 1 < nbu) { issue_U(blk + 1, (blk + 1) & 1); cp_async_wait<1>(); }
+    else cp_async_wait<0>();
+    __syncthreads();
+    const T* S = stg + (size_t)(blk & 1) * bufsz + (size_t)sub * UST;
+    if (active) {
+#pragma unroll
+      for (int u = 0; u < KUW; ++u) {
+        const int t = blk * KUW + u;
+        if (t < NI) {
+          const int j = NI - 1 - t;
+          const T x = V[u] * S[u * KUW];
+          if (!bwd) Xc[node_of(j)] = (double)x;
+          else Xc[node_of(j)] -= (double)x;
+#pragma unroll
+          for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= S[u * KUW + r] * x;
+          V[u] = (j - KUW >= 0) ? yb[(size_t)(j - KUW) * QL + c] : T(0);
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
-// b_u -= sum over interior neighbours j of A_uj t_j, for every separator node u.
+// b_u -= sum over interior neighbours j of A_uj t_j, for every separator node u.  One thread
+// per (separator node, right-hand side); separator nodes are enumerated in closed form: the
+// R full separator rows (y = 16 r + 15) first, then the C separator columns (x = 16 q + 15) of
+// the remaining rows.
 __global__ void sep_update_fwd_kernel(LeafDev d, double* X, int nrhs, int ld) {
   const int nx = d.nx, ny = d.ny;
-  const long long n = (long long)nx * ny;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * nrhs;
+  const int R = (ny + 1) / (LEAF + 1) - 1, C = (nx + 1) / (LEAF + 1) - 1;
+  const long long nrow = (long long)R * nx;
+  const long long nsep = nrow + (long long)(ny - R) * C;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nsep * nrhs;
        e += (long long)gridDim.x * blockDim.x) {
-    int u = (int)(e % n), c = (int)(e / n);
-    int ux = u % nx, uy = u / nx;
-    bool sep = ((ux + 1) % (LEAF + 1) == 0) || ((uy + 1) % (LEAF + 1) == 0);
-    if (!sep) continue;
+    const long long sidx = e % nsep;
+    const int c = (int)(e / nsep);
+    int ux, uy;
+    if (sidx < nrow) {
+      uy = (int)(sidx / nx) * (LEAF + 1) + LEAF;
+      ux = (int)(sidx % nx);
+    } else {
+      const long long t = sidx - nrow;
+      const int yy = (int)(t / C);
+      ux = (int)(t % C) * (LEAF + 1) + LEAF;
+      uy = (yy / LEAF) * (LEAF + 1) + yy % LEAF;
+    }
+    const int u = ux + nx * uy;
     double acc = 0.0;
     for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p) {
-      int v = d.colind[p];
-      int vx = v % nx, vy = v / nx;
-      bool vsep = ((vx + 1) % (LEAF + 1) == 0) || ((vy + 1) % (LEAF + 1) == 0);
+      const int v = d.colind[p];
+      const int vx = v % nx, vy = v / nx;
+      const bool vsep = ((vx + 1) % (LEAF + 1) == 0) || ((vy + 1) % (LEAF + 1) == 0);
       if (!vsep) acc += d.val[p] * X[v + (size_t)ld * c];
     }
     X[u + (size_t)ld * c] -= acc;
@@ -441,25 +588,33 @@ void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
   }
 }
 
-template <typename T>
-static void leaf_solve_launch(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s) {
-  long long n = (long long)d.g.nbox() * nrhs;
-  int grid = (int)((n + 127) / 128);
+template <typename T, int KUW, int LPB>
+static void leaf_solve_go(const LeafDev& d, double* X, int nrhs, int ld, int bwd, cudaStream_t s) {
+  const size_t bufL = (size_t)LPB * (SLOT * SLOT + SLOT), bufU = (size_t)LPB * KUW * KUW;
+  const size_t smem = 2 * sizeof(T) * (bufL > bufU ? bufL : bufU);
+  cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launch();
-  if (kumax <= 15) leaf_solve_kernel<T, 16><<<grid, 128, 0, s>>>(d, X, nrhs, ld, bwd);
-  else leaf_solve_kernel<T, 32><<<grid, 128, 0, s>>>(d, X, nrhs, ld, bwd);
+  leaf_solve_kernel<T, KUW, LPB><<<(d.g.nbox() + LPB - 1) / LPB, LPB * SLOT, smem, s>>>(d, X, nrhs, ld, bwd);
 }
 
 void launch_leaf_solve(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s) {
-  for (int c0 = 0; c0 < nrhs; c0 += QL) {
-    int nc = nrhs - c0 < QL ? nrhs - c0 : QL;
-    if (d.fp32) leaf_solve_launch<float>(d, X + (size_t)ld * c0, nc, ld, bwd, kumax, s);
-    else leaf_solve_launch<double>(d, X + (size_t)ld * c0, nc, ld, bwd, kumax, s);
+  for (int c0 = 0; c0 < nrhs; c0 += SLOT) {
+    const int nc = nrhs - c0 < SLOT ? nrhs - c0 : SLOT;
+    double* Xc = X + (size_t)ld * c0;
+    if (d.fp32) {
+      if (kumax <= 15) leaf_solve_go<float, 16, 8>(d, Xc, nc, ld, bwd, s);
+      else leaf_solve_go<float, 32, 8>(d, Xc, nc, ld, bwd, s);
+    } else {
+      if (kumax <= 15) leaf_solve_go<double, 16, 4>(d, Xc, nc, ld, bwd, s);
+      else leaf_solve_go<double, 32, 4>(d, Xc, nc, ld, bwd, s);
+    }
   }
 }
 
 void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
-  long long n = (long long)d.nx * d.ny * nrhs;
+  const int R = (d.ny + 1) / (LEAF + 1) - 1, C = (d.nx + 1) / (LEAF + 1) - 1;
+  long long n = ((long long)R * d.nx + (long long)(d.ny - R) * C) * nrhs;
+  if (n <= 0) return;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;

@@ -33,7 +33,8 @@ namespace {
 constexpr int NEAR_MAX = 16;      // near unknowns per segment (the geometry gives <= 10)
 constexpr int RUN_MAX = 16;
 constexpr int SK_CHUNK = 16;      // far unknowns per chunk of the sketch product
-constexpr int NW = 8;             // warps per CTA of the sparsify kernel
+constexpr int NW = 8;             // warps per CTA of the sparsify kernel (segments with e > 32)
+constexpr int NW_SMALL = 2;       // ... and for levels whose segments have at most 16 unknowns
 constexpr double TIE_RTOL = 1e-12;
 constexpr int RSTAGE = 96;        // triangular blocks up to this order are staged in shared memory
 
@@ -182,18 +183,19 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 // Drmac-Bujanovic guard written for squared norms: no division or square root per column and
 // step) — and the pivot is chosen from them; the Householder products and their column sums
 // run in T.  perm receives the column order; on exit the first k rows of Y hold [R_1 R_2] in
-// the permuted order.  Returns k.  sh: >= NW*32 + 3*64 doubles of shared scratch; flags: >= e.
-template <typename T>
+// the permuted order.  Returns k.  sh: >= NWT*32 + 3*64 doubles of shared scratch; flags: >= e.
+// NWT = warps of the CTA.
+template <typename T, int NWT>
 __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1,
                           double* vn2, double* sh, int* flags, int* shi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* part = reinterpret_cast<T*>(sh);                   // [NW][32] partial dots
-  T* coef = reinterpret_cast<T*>(sh + NW * 32);         // [64]
-  double* scal = sh + NW * 32 + 64;                     // alpha, v0, c2, normx
+  T* part = reinterpret_cast<T*>(sh);                   // [NWT][32] partial dots
+  T* coef = reinterpret_cast<T*>(sh + NWT * 32);         // [64]
+  double* scal = sh + NWT * 32 + 64;                     // alpha, v0, c2, normx
   for (int j = threadIdx.x; j < e; j += blockDim.x) perm[j] = j;
   if (m == 0 || e == 0) { __syncthreads(); return 0; }
   // initial column norms (one warp per column)
-  for (int j = warp; j < e; j += NW) {
+  for (int j = warp; j < e; j += NWT) {
     T s = T(0);
     for (int r = lane; r < m; r += 32) { T v = Y[r + (size_t)ldy * j]; s += v * v; }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -211,8 +213,8 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
   for (int i = 0; i < kmax; ++i) {
     // the per-step scalar tasks rotate over the warps (and CTAs), so that the FP64 work of
     // co-resident CTAs does not pile up on one SM sub-partition
-    const int wp = (i + blockIdx.x) % NW, wh = (i + 1 + blockIdx.x) % NW;
-    const int wr = (i + 2 + blockIdx.x) % NW, wd = (i + 3 + blockIdx.x) % NW;
+    const int wp = (i + blockIdx.x) % NWT, wh = (i + 1 + blockIdx.x) % NWT;
+    const int wr = (i + 2 + blockIdx.x) % NWT, wd = (i + 3 + blockIdx.x) % NWT;
     if (warp == wp) {         // pivot: largest norm, near-ties -> lowest index
       long long mx = -1;
       for (int j = i + lane; j < e; j += 32) mx = max(mx, dbits(vn1[j]));
@@ -272,13 +274,13 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
         const T* yj = Y + (size_t)ldy * j;
         const T* yi = Y + (size_t)ldy * i;
         if (warp == 0) acc = v0 * yj[i];
-        for (int r = i + 1 + warp; r < m; r += NW) acc += yi[r] * yj[r];
+        for (int r = i + 1 + warp; r < m; r += NWT) acc += yi[r] * yj[r];
       }
       part[warp * 32 + lane] = acc;
       __syncthreads();
       if (warp == wr && j < e) {
         T s = T(0);
-        for (int w = 0; w < NW; ++w) s += part[w * 32 + lane];
+        for (int w = 0; w < NWT; ++w) s += part[w * 32 + lane];
         coef[lane] = s * c2;
       }
       __syncthreads();
@@ -287,7 +289,7 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
         T* yj = Y + (size_t)ldy * j;
         const T* yi = Y + (size_t)ldy * i;
         if (warp == 0) yj[i] -= cj * v0;
-        for (int r = i + 1 + warp; r < m; r += NW) yj[r] -= cj * yi[r];
+        for (int r = i + 1 + warp; r < m; r += NWT) yj[r] -= cj * yi[r];
       }
       __syncthreads();
     }
@@ -306,7 +308,7 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
       }
     }
     __syncthreads();
-    for (int j = i + 1 + warp; j < e; j += NW) {
+    for (int j = i + 1 + warp; j < e; j += NWT) {
       if (!flags[j]) continue;
       double s = 0.0;
       for (int r = i + 1 + lane; r < m; r += 32) { double v = (double)Y[r + (size_t)ldy * j]; s += v * v; }
@@ -641,11 +643,11 @@ __device__ bool id_error_ok(const LevelDev& d, const SegCtx& S, const T* F1, con
 }
 
 // ------------------------------------------------------------ sparsify: one CTA per segment
-template <typename T>
-__global__ void __launch_bounds__(NW * 32, 4) sparsify_kernel(LevelDev d, int smem_bytes) {
+template <typename T, int NWT>
+__global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(LevelDev d, int smem_bytes) {
   extern __shared__ double sm[];
   __shared__ SegCtx S;
-  __shared__ double shr[NW * 32 + 3 * 64];
+  __shared__ double shr[NWT * 32 + 3 * 64];
   __shared__ int shi[8];
   __shared__ int nearlist[NEAR_MAX];
   __shared__ int nnear_sh, nfar_sh;
@@ -821,7 +823,7 @@ __global__ void __launch_bounds__(NW * 32, 4) sparsify_kernel(LevelDev d, int sm
       for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
     }
     __syncthreads();
-    k = block_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
+    k = block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
     ++passes;
     if (predicted) {          // the one-pass ID stands if it passes the measured-error test
       predicted = false;
@@ -1258,23 +1260,20 @@ __global__ void seg_merge_kernel(LevelDev d) {
 constexpr int SC = 16;      // right-hand sides per solve pass (register accumulators per thread)
 constexpr int DCAP = 512;   // parent boundaries up to this size are staged in shared memory
 
-// out(a, acc) for a < nout with acc[c] = sum_j A(a, j) v[j + ldv c], c < SC: one thread per
-// output row, the matrix row read once (coalesced across rows for column-major panels) and
-// reused for all right-hand sides, which are read from shared memory by broadcast.
+// out(a, c, acc) for a < nout, c < nc with acc = sum_j A(a, j) v[j + ldv c]: one thread per
+// (row, right-hand side) pair, so that short products (a few rows, as in the finest levels)
+// still spread over the CTA; v is read from shared memory, A from shared or global memory.
 template <typename T, class Row, class Out>
-__device__ __forceinline__ void gemv_rows(int nout, int nin, Row row, size_t sj, const T* v, int ldv, Out out) {
-  for (int a = threadIdx.x; a < nout; a += blockDim.x) {
-    T acc[SC];
-#pragma unroll
-    for (int c = 0; c < SC; ++c) acc[c] = T(0);
+__device__ __forceinline__ void gemv_pairs(int nout, int nin, Row row, size_t sj, const T* v, int ldv, int nc,
+                                           Out out) {
+  for (int x = threadIdx.x; x < nout * nc; x += blockDim.x) {
+    const int a = x % nout, c = x / nout;
     const T* Aa = row(a);   // global or shared memory: plain (generic) loads
+    const T* vc = v + (size_t)ldv * c;
+    T acc = T(0);
 #pragma unroll 4
-    for (int j = 0; j < nin; ++j) {
-      const T w = Aa[j * sj];
-#pragma unroll
-      for (int c = 0; c < SC; ++c) acc[c] += w * v[j + ldv * c];
-    }
-    out(a, acc);
+    for (int j = 0; j < nin; ++j) acc += Aa[j * sj] * vc[j];
+    out(a, c, acc);
   }
 }
 
@@ -1326,7 +1325,7 @@ __device__ __forceinline__ void gather_panel(T* dst, int nr, int ncl, const T* s
 // Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
 template <typename T>
-__global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd) {
+__global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd) {
   extern __shared__ double smd[];
   const int sid = blockIdx.x;
   const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
@@ -1377,8 +1376,8 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, SolveCaps ca
   T* vr = v + k;      // remainder part
   if (!bwd) {
     if (k > 0) {      // b_r -= T^T b_s: row a of T^T is column a of T
-      gemv_rows<T>(r, k, [&](int a) { return Tp + ldt * a; }, 1, vs, e,
-                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vr[a + e * c] -= acc[c]; });
+      gemv_pairs<T>(r, k, [&](int a) { return Tp + ldt * a; }, 1, vs, e, nc,
+                    [&](int a, int c, T acc) { vr[a + e * c] -= acc; });
       __syncthreads();
     }
     lower_sweep<T>(vr, e, r, LUs, ldl, pvs, nc);
@@ -1386,22 +1385,22 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, SolveCaps ca
     if (k > 0) {      // b_s -= Z y_r
       const T* Zp = pstaged ? Ps : Dg + (size_t)capS * k;
       const size_t ldz = pstaged ? (size_t)k : (size_t)capS;
-      gemv_rows<T>(k, r, [&](int a) { return Zp + a; }, ldz, vr, e,
-                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vs[a + e * c] -= acc[c]; });
+      gemv_pairs<T>(k, r, [&](int a) { return Zp + a; }, ldz, vr, e, nc,
+                    [&](int a, int c, T acc) { vs[a + e * c] -= acc; });
     }
   } else {
     if (k > 0) {      // y_r -= W x_s
       const T* Wp = pstaged ? Ps : Dg + k;
       const size_t ldw = pstaged ? (size_t)r : (size_t)capS;
-      gemv_rows<T>(r, k, [&](int a) { return Wp + a; }, ldw, vs, e,
-                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vr[a + e * c] -= acc[c]; });
+      gemv_pairs<T>(r, k, [&](int a) { return Wp + a; }, ldw, vs, e, nc,
+                    [&](int a, int c, T acc) { vr[a + e * c] -= acc; });
       __syncthreads();
     }
     upper_sweep<T>(vr, e, r, LUs, ldl, ivs, nc);
     __syncthreads();
     if (k > 0) {      // x_s -= T x_r
-      gemv_rows<T>(k, r, [&](int a) { return Tp + a; }, ldt, vr, e,
-                   [&](int a, const T* acc) { for (int c = 0; c < SC; ++c) vs[a + e * c] -= acc[c]; });
+      gemv_pairs<T>(k, r, [&](int a) { return Tp + a; }, ldt, vr, e, nc,
+                    [&](int a, int c, T acc) { vs[a + e * c] -= acc; });
     }
   }
   __syncthreads();
@@ -1415,7 +1414,7 @@ __global__ void __launch_bounds__(256) seg_solve_kernel(LevelDev d, SolveCaps ca
 // (a boundary unknown is shared by up to four parents; the order of their contributions is
 // not fixed); backward x_p = U^{-1} (y_p - W x_dP).
 template <typename T>
-__global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd) {
+__global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps cap, double* X, int nc, int ld, int bwd) {
   extern __shared__ double smd[];
   const int P = blockIdx.x;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
@@ -1468,13 +1467,10 @@ __global__ void __launch_bounds__(256) sep_solve_kernel(LevelDev d, SolveCaps ca
       gather_panel<T>(U, ndP, kp, M, ldp, rows_sm, Dp);
       __syncthreads();
     }
-    gemv_rows<T>(ndP, kp,
-                 [&](int a) { return pstaged ? U + a : M + rowpos(a) + ldp * Dp; },
-                 pstaged ? (size_t)ndP : ldp, y, kp,
-                 [&](int a, const T* acc) {
-                   double* xa = X + rownode(a);
-                   for (int c = 0; c < nc; ++c) atomicAdd(xa + (size_t)ld * c, -(double)acc[c]);
-                 });
+    gemv_pairs<T>(ndP, kp,
+                  [&](int a) { return pstaged ? U + a : M + rowpos(a) + ldp * Dp; },
+                  pstaged ? (size_t)ndP : ldp, y, kp, nc,
+                  [&](int a, int c, T acc) { atomicAdd(X + rownode(a) + (size_t)ld * c, -(double)acc); });
   } else {
     if (dstage) {
       for (int x = threadIdx.x; x < ndP * SC; x += blockDim.x) {
@@ -1545,9 +1541,14 @@ void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
 template <typename T>
 static void sparsify_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   int smem = (int)p.spars_smem;
-  cudaFuncSetAttribute(sparsify_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   note_launch();
-  sparsify_kernel<T><<<d.g.nseg(), NW * 32, smem, s>>>(d, smem);
+  if (d.capS <= 16) {       // finest segments: two warps each, many segments per SM
+    cudaFuncSetAttribute(sparsify_kernel<T, NW_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    sparsify_kernel<T, NW_SMALL><<<d.g.nseg(), NW_SMALL * 32, smem, s>>>(d, smem);
+  } else {
+    cudaFuncSetAttribute(sparsify_kernel<T, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    sparsify_kernel<T, NW><<<d.g.nseg(), NW * 32, smem, s>>>(d, smem);
+  }
 }
 
 void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
