@@ -453,6 +453,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
       d.near_radius = o->near_radius; d.h0 = o->h0; d.seed = o->seed;
       d.L = L;
       d.pred_mode = PRED_OFF; d.pred_margin = 0.35; d.pred = nullptr;
+      d.log10eps = o->eps_id > 0.0 ? std::log10(o->eps_id) : -16.0;
       d.feat = cv.take<float>((size_t)nseg * PRED_NFEAT);
       d.tgt = f->d_tgt_all ? f->d_tgt_all + tgt_off : nullptr;
       tgt_off += (size_t)nseg * 4;

@@ -173,6 +173,53 @@ __device__ __forceinline__ T bval(const LevelDev& d, const SegCtx& S, const T* F
   return v;
 }
 
+// Neighbour table of a segment (shared memory, built once per segment when it has at most
+// NB_MAX neighbours): grid node, positions in the frontal blocks of box 1 / box 2 (-1 when
+// absent) and the near flag of neighbour f.  Without the table the same values come from the
+// runs.
+constexpr int NB_MAX = 512;
+struct NbrTab {
+  const int* node;
+  const short* p1;
+  const short* p2;
+  const unsigned char* nearf;
+  bool on;
+};
+struct Nbr {
+  int node, p1, p2;
+  bool nearf;
+};
+
+__device__ __forceinline__ Nbr nbr_get(const LevelDev& d, const SegCtx& S, const NbrTab& tb, int f) {
+  Nbr q;
+  if (tb.on) {
+    q.node = tb.node[f];
+    q.p1 = tb.p1[f];
+    q.p2 = tb.p2[f];
+    q.nearf = tb.nearf[f] != 0;
+  } else {
+    int r, i;
+    locate(S, f, r, i);
+    const Run& R = S.run[r];
+    q.node = run_node(d, R, i);
+    q.p1 = R.p1 >= 0 ? R.p1 + i : -1;
+    q.p2 = R.p2 >= 0 ? R.p2 + i : -1;
+    q.nearf = cheb(S, q.node, d.nx) <= d.near_radius;
+  }
+  return q;
+}
+
+// B entry of neighbour q, half t, column c (as bval)
+template <typename T>
+__device__ __forceinline__ T bval_q(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, const Nbr& q,
+                                    int t, int c) {
+  const size_t ld = d.ldF;
+  T v = T(0);
+  if (q.p1 >= 0) v += t == 0 ? F1[q.p1 + ld * (S.s1 + c)] : F1[(S.s1 + c) + ld * q.p1];
+  if (q.p2 >= 0) v += t == 0 ? F2[q.p2 + ld * (S.s2 + c)] : F2[(S.s2 + c) + ld * q.p2];
+  return v;
+}
+
 // non-negative doubles order like their bit patterns
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
@@ -412,10 +459,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // ------------------------------------------------------------ far-row sketch
 // Yr[rr, c] = sum over far neighbour rows f of G[rr, f] B_F[f, c] for rr < hh (unscaled),
 // neighbours taken in chunks of ch (near ones get zero weight).  Yr has leading dimension ldy.
-template <typename T>
-__device__ void sketch_far(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, int sid,
-                           int halves, int nnear, const int* nearlist, int e, int hh, T* Yr, int ldy,
-                           T* Bc, T* Gc, int ch) {
+template <typename T, class BGet>
+__device__ void sketch_far(const LevelDev& d, const SegCtx& S, const NbrTab& tb, BGet bget,
+                           int sid, int halves, int e, int hh, T* Yr, int ldy, T* Bc, T* Gc, int ch) {
   for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Yr[(x % hh) + (size_t)ldy * (x / hh)] = T(0);
   __syncthreads();
   for (int f0 = 0; f0 < S.nb; f0 += ch) {
@@ -424,23 +470,13 @@ __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const T* F1, cons
     for (int x = threadIdx.x; x < rows * e; x += blockDim.x) {
       int row = x % rows, c = x / rows;
       int t = row / nc, jj = row % nc;
-      int r, i;
-      locate(S, f0 + jj, r, i);
-      Bc[row + (size_t)rows * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
+      Bc[row + (size_t)rows * c] = bget(t, f0 + jj, c);
     }
     for (int x = threadIdx.x; x < hh * rows; x += blockDim.x) {
       int rr = x % hh, row = x / hh;
       int t = row / nc, jj = row % nc;
-      int f = f0 + jj;
-      bool isnear = false;
-      for (int a = 0; a < nnear; ++a) isnear |= (nearlist[a] == f);
-      T gv = T(0);
-      if (!isnear) {
-        int r, i;
-        locate(S, f, r, i);
-        gv = (T)sketch_gauss(d.seed, d.l, sid, rr, run_node(d, S.run[r], i), t);
-      }
-      Gc[rr + (size_t)hh * row] = gv;
+      const Nbr q = nbr_get(d, S, tb, f0 + jj);
+      Gc[rr + (size_t)hh * row] = q.nearf ? T(0) : (T)sketch_gauss(d.seed, d.l, sid, rr, q.node, t);
     }
     __syncthreads();
     for (int x = threadIdx.x; x < hh * e; x += blockDim.x) {
@@ -459,49 +495,58 @@ __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const T* F1, cons
 // first PRED_PROBE rows of the sketch matrix of this segment, unscaled.  Warps take rows in
 // turn; lanes hold columns lane + 32 q of a 64-column chunk in registers; the warps' sums meet
 // in Y8 (zeroed by the caller) through shared-memory atomics.
-template <typename T>
-__device__ void probe_sketch(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, int sid,
-                             int halves, int nnear, const int* nearlist, int e, T* Y8) {
+template <typename T, class BGet>
+__device__ void probe_sketch(const LevelDev& d, const SegCtx& S, const NbrTab& tb, BGet bget,
+                             int sid, int halves, int e, T* Y8) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nrows = halves * S.nb;
+  const int ro = lane >> 3, r8 = lane & 7;                 // lane: row ro of a group of 4, probe row r8
   for (int c0 = 0; c0 < e; c0 += 64) {
     T acc[2][PRED_PROBE];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int r = 0; r < PRED_PROBE; ++r) acc[q][r] = T(0);
-    for (int row = warp; row < nrows; row += nw) {
-      const int f = row % S.nb, t = row / S.nb;
-      bool isnear = false;
-      for (int a = 0; a < nnear; ++a) isnear |= (nearlist[a] == f);
-      if (isnear) continue;                                  // warp-uniform
-      int ri, i;
-      locate(S, f, ri, i);
-      const T g = lane < PRED_PROBE ? (T)sketch_gauss(d.seed, d.l, sid, lane, run_node(d, S.run[ri], i), t) : T(0);
-      T b[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int c = c0 + 32 * q + lane;
-        b[q] = c < e ? bval<T>(d, S, F1, F2, S.run[ri], i, t, c) : T(0);
+    for (int g0 = 4 * warp; g0 < nrows; g0 += 4 * nw) {
+      const int row = g0 + ro;
+      Nbr q{0, -1, -1, true};
+      int t = 0;
+      if (row < nrows) {
+        t = row / S.nb;
+        q = nbr_get(d, S, tb, row % S.nb);
       }
+      const T g = q.nearf ? T(0) : (T)sketch_gauss(d.seed, d.l, sid, r8, q.node, t);
 #pragma unroll
-      for (int r = 0; r < PRED_PROBE; ++r) {
-        const T gr = __shfl_sync(0xffffffffu, g, r);
+      for (int rr = 0; rr < 4; ++rr) {
+        const int src = 8 * rr;
+        if (__shfl_sync(0xffffffffu, (int)q.nearf, src)) continue;   // near or past the end
+        const int rowr = g0 + rr, tr = rowr / S.nb, fr = rowr % S.nb;
+        T b[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) acc[q][r] += gr * b[q];
+        for (int qc = 0; qc < 2; ++qc) {
+          const int c = c0 + 32 * qc + lane;
+          b[qc] = c < e ? bget(tr, fr, c) : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < PRED_PROBE; ++r) {
+          const T gr = __shfl_sync(0xffffffffu, g, src + r);
+#pragma unroll
+          for (int qc = 0; qc < 2; ++qc) acc[qc][r] += gr * b[qc];
+        }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int c = c0 + 32 * q + lane;
+    for (int qc = 0; qc < 2; ++qc) {
+      const int c = c0 + 32 * qc + lane;
       if (c < e)
 #pragma unroll
-        for (int r = 0; r < PRED_PROBE; ++r) atomicAdd(&Y8[r + PRED_PROBE * c], acc[q][r]);
+        for (int r = 0; r < PRED_PROBE; ++r) atomicAdd(&Y8[r + PRED_PROBE * c], acc[qc][r]);
     }
   }
 }
 
 // Features of segment sid into xf[16] (shared), needs >= 2 warps; every thread calls it.
+// Arithmetic in the factor's precision T (features are inputs of a BF16 network).
 // Warp 0: column-pivoted QR of the probe Y8 (PRED_PROBE x e, pitch PRED_PROBE, overwritten)
 // by Gram-Schmidt with exactly recomputed column norms, lane c owning columns c + 32 q; the
 // pivot is the largest norm, near-ties (relative 1e-12) to the lowest column.  Warp 1: the
@@ -512,39 +557,43 @@ __device__ void probe_features(const LevelDev& d, int sid, int e, int nnear, int
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp == 0) {
     const int nd = min(PRED_PROBE, e);
-    double rd[PRED_PROBE];
+    T rd[PRED_PROBE];
 #pragma unroll
-    for (int i = 0; i < PRED_PROBE; ++i) rd[i] = 0.0;
+    for (int i = 0; i < PRED_PROBE; ++i) rd[i] = T(0);
     unsigned used = 0;                                       // bit q: column lane + 32 q pivoted
+    T sq[4];
     for (int i = 0; i < nd; ++i) {
-      double mx = 0.0;
+      T mx = T(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = lane + 32 * q;
+        sq[q] = T(-1);
+        if (c < e && !(used >> q & 1)) {
+          T a = T(0);
+#pragma unroll
+          for (int r = 0; r < PRED_PROBE; ++r) a += Y8[r + PRED_PROBE * c] * Y8[r + PRED_PROBE * c];
+          sq[q] = a;
+          mx = a > mx ? a : mx;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) { const T w = __shfl_xor_sync(0xffffffffu, mx, o); mx = w > mx ? w : mx; }
+      if (!(mx > T(0))) break;
+      const T thr = mx * (T)((1.0 - TIE_RTOL) * (1.0 - TIE_RTOL));
       int best = 1 << 30;
-      for (int q = 0, c = lane; c < e; ++q, c += 32) {
-        if (used >> q & 1) continue;
-        double sq = 0.0;
-        for (int r = 0; r < PRED_PROBE; ++r) sq += (double)Y8[r + PRED_PROBE * c] * (double)Y8[r + PRED_PROBE * c];
-        mx = fmax(mx, sqrt(sq));
-      }
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (mx <= 0.0) break;
-      const double thr = mx * (1.0 - TIE_RTOL);
-      for (int q = 0, c = lane; c < e; ++q, c += 32) {
-        if (used >> q & 1) continue;
-        double sq = 0.0;
-        for (int r = 0; r < PRED_PROBE; ++r) sq += (double)Y8[r + PRED_PROBE * c] * (double)Y8[r + PRED_PROBE * c];
-        if (sqrt(sq) >= thr) best = min(best, c);
-      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (sq[q] >= thr) best = min(best, lane + 32 * q);
       for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
       T v[PRED_PROBE];
-      double pn = 0.0;
+      T pn = T(0);
 #pragma unroll
       for (int r = 0; r < PRED_PROBE; ++r) {
         v[r] = Y8[r + PRED_PROBE * best];
-        pn += (double)v[r] * (double)v[r];
+        pn += v[r] * v[r];
       }
       pn = sqrt(pn);
       rd[i] = pn;
-      const T inv = (T)(1.0 / pn);
+      const T inv = T(1) / pn;
 #pragma unroll
       for (int r = 0; r < PRED_PROBE; ++r) v[r] *= inv;
       if ((best & 31) == lane) used |= 1u << (best >> 5);
@@ -560,56 +609,60 @@ __device__ void probe_features(const LevelDev& d, int sid, int e, int nnear, int
       }
       __syncwarp();
     }
-    if (lane == 0) {
-      const double le = log10(d.eps);
+    if (lane < 5) {                                          // one decay ratio per lane
       const int js[5] = {1, 2, 3, 5, 7};
-      for (int q = 0; q < 5; ++q) {
-        const int j = js[q];
-        double val;
-        if (j >= nd || rd[0] == 0.0) val = -16.0 - le;
-        else val = log10(fmax(rd[j] / rd[0], 1e-16)) - le;
-        xf[11 + q] = (float)val;
+      const int j = js[lane];
+      const T le = (T)d.log10eps;
+      T val;
+      if (j >= nd || rd[0] == T(0)) val = T(-16) - le;
+      else {
+        T rj = rd[0];
+#pragma unroll
+        for (int q = 1; q < PRED_PROBE; ++q) if (q == j) rj = rd[q];
+        const T ratio = rj / rd[0];
+        val = log10(ratio > T(1e-16) ? ratio : T(1e-16)) - le;
       }
+      xf[11 + lane] = (float)val;
     }
   } else if (warp == 1) {
     const int* nodes = d.nodes + (size_t)sid * d.capS;
-    double lmin = 1e300, lmax = -1e300, lsum = 0.0, dsum = 0.0, ssum = 0.0, asum = 0.0;
+    float lmin = 3.0e38f, lmax = -3.0e38f, lsum = 0.f, dsum = 0.f, ssum = 0.f, asum = 0.f;
     for (int t = lane; t < e; t += 32) {
       const float4 st = d.nstat[nodes[t]];
-      lmin = fmin(lmin, (double)st.x);
-      lmax = fmax(lmax, (double)st.x);
+      lmin = fminf(lmin, st.x);
+      lmax = fmaxf(lmax, st.x);
       lsum += st.x;
       dsum += st.y;
       ssum += st.z;
       asum += st.w;
     }
     for (int o = 16; o > 0; o >>= 1) {
-      lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-      lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+      lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+      lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
       lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
       dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
       ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
       asum += __shfl_xor_sync(0xffffffffu, asum, o);
     }
-    const double mean = lsum / e;
-    double vsum = 0.0;
+    const float mean = lsum / e;
+    float vsum = 0.f;
     for (int t = lane; t < e; t += 32) {
-      const double dv = (double)d.nstat[nodes[t]].x - mean;
+      const float dv = d.nstat[nodes[t]].x - mean;
       vsum += dv * dv;
     }
     for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
     if (lane == 0) {
       xf[0] = (float)(d.L - d.l);
-      xf[1] = (float)log2((double)e);
-      xf[2] = (float)log2(1.0 + nb);
+      xf[1] = log2f((float)e);
+      xf[2] = log2f(1.0f + nb);
       xf[3] = (float)nnear;
-      xf[4] = (float)log2(1.0 + nfar);
-      xf[5] = (float)(lmin - mean);
-      xf[6] = (float)(lmax - mean);
-      xf[7] = (float)sqrt(vsum / e);
-      xf[8] = (float)(dsum / e);
-      xf[9] = (float)(ssum / e);
-      xf[10] = (float)(asum / e);
+      xf[4] = log2f(1.0f + nfar);
+      xf[5] = lmin - mean;
+      xf[6] = lmax - mean;
+      xf[7] = sqrtf(vsum / e);
+      xf[8] = dsum / e;
+      xf[9] = ssum / e;
+      xf[10] = asum / e;
     }
   }
   __syncthreads();
@@ -617,29 +670,26 @@ __device__ void probe_features(const LevelDev& d, int sid, int e, int nnear, int
 
 // Measured ID error test ||B_r - B_s T||_F <= 10 eps ||B||_F on the exact B (all neighbour
 // rows, both halves of a non-symmetric B): one thread per row of B, entries read directly.
-template <typename T>
-__device__ bool id_error_ok(const LevelDev& d, const SegCtx& S, const T* F1, const T* F2, int halves,
-                            int e, int k, const int* perm, const T* Tw, int ldt, double* red) {
+template <typename T, class BGet>
+__device__ bool id_error_ok(const SegCtx& S, BGet bget, int halves, int e, int k, const int* perm,
+                            const T* Tw, int ldt, double eps, double* red) {
   const int r = e - k;
-  double num = 0.0, den = 0.0;
+  T num = T(0), den = T(0);                 // per-thread sums in T, the block sum in FP64
   for (int row = threadIdx.x; row < halves * S.nb; row += blockDim.x) {
     const int f = row % S.nb, t = row / S.nb;
-    int ri, i;
-    locate(S, f, ri, i);
-    const Run& R = S.run[ri];
     for (int c = 0; c < e; ++c) {
-      const double v = (double)bval<T>(d, S, F1, F2, R, i, t, c);
+      const T v = bget(t, f, c);
       den += v * v;
     }
     for (int j = 0; j < r; ++j) {
-      T s = bval<T>(d, S, F1, F2, R, i, t, perm[k + j]);
-      for (int a = 0; a < k; ++a) s -= bval<T>(d, S, F1, F2, R, i, t, perm[a]) * Tw[a + (size_t)ldt * j];
-      num += (double)s * (double)s;
+      T s = bget(t, f, perm[k + j]);
+      for (int a = 0; a < k; ++a) s -= bget(t, f, perm[a]) * Tw[a + (size_t)ldt * j];
+      num += s * s;
     }
   }
-  num = block_sum(num, red);
-  den = block_sum(den, red);
-  return sqrt(num) <= 10.0 * d.eps * sqrt(den);
+  const double nsum = block_sum((double)num, red);
+  const double dsum = block_sum((double)den, red);
+  return sqrt(nsum) <= 10.0 * eps * sqrt(dsum);
 }
 
 // ------------------------------------------------------------ sparsify: one CTA per segment
@@ -707,6 +757,21 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
       nfar_sh = S.nb - nn;
     }
   }
+  // neighbour table (all threads)
+  __shared__ int tb_node[NB_MAX];
+  __shared__ short tb_p1[NB_MAX], tb_p2[NB_MAX];
+  __shared__ unsigned char tb_nf[NB_MAX];
+  const NbrTab tb{tb_node, tb_p1, tb_p2, tb_nf, S.nb <= NB_MAX};
+  if (tb.on) {
+    const NbrTab none{nullptr, nullptr, nullptr, nullptr, false};
+    for (int f = threadIdx.x; f < S.nb; f += blockDim.x) {
+      const Nbr q = nbr_get(d, S, none, f);
+      tb_node[f] = q.node;
+      tb_p1[f] = (short)q.p1;
+      tb_p2[f] = (short)q.p2;
+      tb_nf[f] = q.nearf ? 1 : 0;
+    }
+  }
   __syncthreads();
   const int nnear = nnear_sh;
   const int nN = halves * nnear;
@@ -728,7 +793,8 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     ch = (int)min((size_t)SK_CHUNK, room / (per_ch_b > 0 ? per_ch_b : 1));
     if (ch < 1) { ch = 1; if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY); }
   }
-  T *Y, *Dw, *Tw, *Bc, *Gc, *rinv;
+  T *Y, *Dw, *Tw, *Bc, *Gc, *rinv, *Bs;
+  bool bstage;
   double *vn1, *vn2;
   int *perm, *piv, *flags;
   int ldy, ldd, ldt;
@@ -753,11 +819,27 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
       Dw = Dg; ldd = capS;
       Tw = Tg; ldt = capS;
     }
+    // the segment's B block (every neighbour row, e columns) in what is left, when it fits
+    q = reinterpret_cast<char*>(((uintptr_t)q + 15) & ~(uintptr_t)15);
+    Bs = reinterpret_cast<T*>(q);
+    bstage = (size_t)(q - reinterpret_cast<char*>(sm)) + (size_t)halves * S.nb * e * TD <= (size_t)smem_bytes;
   }
   if (!in_smem && (mmax > d.Ycap || d.Yg == nullptr)) {   // no room: report, touch nothing
     if (threadIdx.x == 0) { atomicOr(d.err, ERR_CAPACITY); d.kk[sid] = 0; d.hs[sid] = 0; }
     return;
   }
+  // B staged once (all loads in flight) for the near rows, every sketch pass, the probe and
+  // the error test; otherwise each reads the frontal blocks through the neighbour table
+  if (bstage) {
+    for (int x = threadIdx.x; x < halves * S.nb * e; x += blockDim.x) {
+      const int row = x / e, c = x % e;
+      Bs[x] = bval_q<T>(d, S, F1, F2, nbr_get(d, S, tb, row % S.nb), row / S.nb, c);
+    }
+    __syncthreads();
+  }
+  auto bget = [&](int t, int f, int c) -> T {
+    return bstage ? Bs[((size_t)t * S.nb + f) * e + c] : bval_q<T>(d, S, F1, F2, nbr_get(d, S, tb, f), t, c);
+  };
 
   // ---- learned rank predictor (not in the paper): features from an 8-row probe of the
   //      far rows, then the network's one-pass sketch size (PRED_PREDICT) or a training
@@ -769,7 +851,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
   if (use_pred) {
     for (int x = threadIdx.x; x < PRED_PROBE * e; x += blockDim.x) Y[x] = T(0);   // Y8, pitch 8
     __syncthreads();
-    probe_sketch<T>(d, S, F1, F2, sid, halves, nnear, nearlist, e, Y);
+    probe_sketch<T>(d, S, tb, bget, sid, halves, e, Y);
     __syncthreads();
     probe_features<T>(d, sid, e, nnear, nfar_sh, S.nb, Y, xf);
     if (d.pred_mode == PRED_RECORD) {
@@ -794,9 +876,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     for (int x = threadIdx.x; x < nN * e; x += blockDim.x) {
       int row = x % nN, c = x / nN;
       int t = row / nnear, a = row % nnear;
-      int r, i;
-      locate(S, nearlist[a], r, i);
-      Y[row + (size_t)ldy * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
+      Y[row + (size_t)ldy * c] = bget(t, nearlist[a], c);
     }
     if (full) {
       // Phi = I on the far block: far rows in the enumeration order of the neighbours;
@@ -810,15 +890,13 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
         }
         if (isnear) continue;
         int j = f - before;
-        int r, i;
-        locate(S, f, r, i);
         for (int t = 0; t < halves; ++t)
           for (int c = 0; c < e; ++c)
-            Y[(nN + t * nfar_sh + j) + (size_t)ldy * c] = bval<T>(d, S, F1, F2, S.run[r], i, t, c);
+            Y[(nN + t * nfar_sh + j) + (size_t)ldy * c] = bget(t, f, c);
       }
     } else {
       // Y_F = G B_F, chunks of neighbours (near ones get zero weight)
-      sketch_far<T>(d, S, F1, F2, sid, halves, nnear, nearlist, e, hh, Y + nN, ldy, Bc, Gc, ch);
+      sketch_far<T>(d, S, tb, bget, sid, halves, e, hh, Y + nN, ldy, Bc, Gc, ch);
       const T sc = (T)(1.0 / sqrt((double)hh));
       for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
     }
@@ -832,7 +910,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
       if (ok) {
         block_interp<T>(Y, ldy, k, e, Tw, ldt, rinv);
         have_t = true;
-        ok = id_error_ok<T>(d, S, F1, F2, halves, e, k, perm, Tw, ldt, shr);
+        ok = id_error_ok<T>(S, bget, halves, e, k, perm, Tw, ldt, d.eps, shr);
       }
       if (ok) break;
       fellback = true;
@@ -1522,7 +1600,9 @@ size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes) 
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
   const size_t mmax = halves * NEAR_MAX + hcap;
   const size_t small_b = 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
-  return small_b + (SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e) * tbytes;
+  // segments of at most 32 unknowns also stage their B block (<= 6 sides of e + 8 corners)
+  const size_t bs = e <= 32 ? halves * (6 * (size_t)e + 8) * e + 4 : 0;
+  return small_b + (SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e + bs) * tbytes;
 }
 
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes) {

@@ -152,6 +152,7 @@ struct LevelDev {
   // learned rank predictor
   int pred_mode;            // PRED_OFF / PRED_RECORD / PRED_PREDICT
   double pred_margin;
+  double log10eps;          // log10(eps) (features 11-15)
   const PredDev* pred;      // device copy of the network (PRED_PREDICT)
   float* feat;              // [nseg * 16] features (PRED_RECORD)
   int* tgt;                 // [nseg * 4] {k, far rows, valid, ID passes} (PRED_RECORD)
