@@ -421,6 +421,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     lf.ybuf = real((size_t)gl.nbox() * NI * 64);
     lf.piv = cv.take<int>((size_t)gl.nbox() * NI);
     lf.kumax = cv.take<int>(4);
+    lf.kur = cv.take<int>((size_t)gl.nbox());
     std::vector<void*> Fst(L + 1, nullptr);
     Fst[L] = lf.F;
     for (int l = L; l >= 1; --l) {

@@ -28,8 +28,6 @@ constexpr int LPC = 2;        // leaves per CTA of the factor kernel
 constexpr int FTH = 128;      // threads of the factor kernel (64 per leaf)
 constexpr int QL = 64;        // column slots per leaf in the sweep buffer (60 used by the factor)
 
-__device__ __forceinline__ double& ab(double* AB, int i, int j) { return AB[(KV + i - j) + LDAB * j]; }
-
 __device__ __forceinline__ int leaf_frontal_pos(int vx, int vy, int x0, int y0) {
   const int w = LEAF;
   if (vy == y0 - 1 && vx >= x0 && vx < x0 + w) return vx - x0;                  // bottom
@@ -133,152 +131,147 @@ __device__ __forceinline__ void sweep_U(const BandT& B, In in, Out out) {
   }
 }
 
-// Band GEPP (the dgbtf2 sequence) of one leaf by a group of 64 threads (tid 0..63); all
-// threads of the CTA execute the same barriers.  Returns the upper bandwidth reached.
-__device__ int band_gepp_pair(double* AB, int* piv, int tid, volatile int* sh, bool& ok) {
+// ---- leaf factorization, kernel A: band LU (the dgbtf2 sequence: pivot = largest |entry| of
+// the column inside the band, ties -> lowest row; interchanges applied to the columns the U
+// factor can reach; multipliers scaled by the reciprocal pivot) of one leaf per 64-thread
+// CTA, in FP64, on a sliding window of WS band columns in shared memory: column c sits in
+// slot c mod WS; after step j column j is final, goes to global memory in precision T and its
+// slot is refilled with column j + WS assembled from the CSR (first touched at step j + 2).
+// Also zeroes the leaf's frontal block and records the upper bandwidth reached.
+constexpr int WS = 32;       // window columns (> KV)
+constexpr int LUT = 64;      // threads per leaf LU
+
+template <typename T>
+__global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
+  __shared__ double W[LDAB * WS];
+  __shared__ int sh[2];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const Geo g = d.g;
+  const int I = b % g.bx, J = b / g.bx;
+  const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
+  const int nx = d.nx;
+  {
+    T* F = reinterpret_cast<T*>(d.F) + (size_t)b * d.ldF * d.ldF;
+    const int D = g.D();
+    for (int e = tid; e < D * D; e += LUT) F[(e % D) + (size_t)d.ldF * (e / D)] = T(0);
+  }
+  T* bandg = reinterpret_cast<T*>(d.band) + (size_t)b * LDAB * NI;
+  T* invg = reinterpret_cast<T*>(d.invd) + (size_t)b * NI;
+  int* pivg = d.piv + (size_t)b * NI;
+  auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
+  // band row r of column c of A_II from the CSR: A(i, c), i = c + r - KV (5-point stencil)
+  auto assemble = [&](int r, int c) -> double {
+    const int i = c + r - KV;
+    if (c >= NI || i < 0 || i >= NI) return 0.0;
+    const int di = i - c;
+    const bool adj = di == 0 || di == LEAF || di == -LEAF || ((di == 1 || di == -1) && i / LEAF == c / LEAF);
+    if (!adj) return 0.0;
+    return csr_entry(d.rowptr, d.colind, d.val, node_of(i), node_of(c));
+  };
+  auto w = [&](int i, int c) -> double& { return W[(KV + i - c) + LDAB * (c & (WS - 1))]; };
+  for (int x = tid; x < LDAB * WS; x += LUT) W[x] = assemble(x % LDAB, x / LDAB);
+  __syncthreads();
   int ju = 0, kureach = KU;
-  const int lane = tid & 31;
+  bool ok = true;
+  const int ur = 1 + (tid & 15), ucg = tid >> 4;       // rank-1 update: row, column group
   for (int j = 0; j < NI; ++j) {
     const int km = min(KL, NI - 1 - j);
-    if (tid < 32) {
-      double best = -1.0;
+    if (tid < 32) {           // pivot: |entries| compared as bit patterns (no FP64 arithmetic)
+      long long best = -1;
       int bi = 0;
-      if (lane <= km) { best = fabs(ab(AB, j + lane, j)); bi = lane; }
+      if (lane <= km) { best = __double_as_longlong(w(j + lane, j)) & 0x7fffffffffffffffll; bi = lane; }
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, o);
-        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        const long long ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (lane == 0) {
         sh[0] = bi;
-        sh[1] = (best == 0.0) ? 1 : 0;
-        piv[j] = j + bi;
+        sh[1] = best == 0 ? 1 : 0;
+        pivg[j] = j + bi;
       }
     }
     __syncthreads();
     const int jp = sh[0];
     const bool zero = sh[1] != 0;
     if (zero) ok = false;
-    const int juj = min(j + KU + jp, NI - 1);
-    ju = max(ju, juj);
+    ju = max(ju, min(j + KU + jp, NI - 1));
     kureach = max(kureach, ju - j);
-    if (!zero && jp != 0) {
-      for (int c = j + tid; c <= ju; c += 64) {
-        double a = ab(AB, j, c), b = ab(AB, j + jp, c);
-        ab(AB, j, c) = b;
-        ab(AB, j + jp, c) = a;
+    if (!zero && jp != 0)
+      for (int c = j + tid; c <= ju; c += LUT) {
+        const double a = w(j, c);
+        w(j, c) = w(j + jp, c);
+        w(j + jp, c) = a;
       }
+    __syncthreads();
+    if (tid < 32) {           // one reciprocal per pivot; multipliers scaled by it
+      const double rp = zero ? 0.0 : 1.0 / w(j, j);
+      if (!zero && tid < km) w(j + 1 + tid, j) *= rp;
+      if (tid == 0) invg[j] = (T)rp;
     }
     __syncthreads();
-    if (!zero) {
-      const double pv = ab(AB, j, j);
-      if (tid < km) ab(AB, j + 1 + tid, j) /= pv;
+    if (!zero && ur <= km) {
+      const double m = w(j + ur, j);
+      for (int c = j + 1 + ucg; c <= ju; c += LUT / 16) w(j + ur, c) -= m * w(j, c);
     }
     __syncthreads();
-    if (!zero) {
-      const int ncol = ju - j;
-      for (int e = tid; e < km * ncol; e += 64) {
-        int r = 1 + e % km, c = j + 1 + e / km;
-        ab(AB, j + r, c) -= ab(AB, j + r, j) * ab(AB, j, c);
-      }
+    if (tid < LDAB) {         // column j is final: store it, refill its slot with column j + WS
+      double& slot = W[tid + LDAB * (j & (WS - 1))];
+      bandg[tid + LDAB * j] = (T)slot;
+      slot = assemble(tid, j + WS);
     }
-    __syncthreads();
   }
-  return min(kureach, KV);
+  if (!ok && tid == 0) atomicOr(d.err, ERR_SINGULAR);
+  if (tid == 0) {
+    const int ku = min(kureach, KV);
+    d.kur[b] = ku;
+    atomicMax(d.kumax, ku);
+  }
 }
 
+// ---- leaf factorization, kernel B: the Schur complement onto the sides from the ring of
+// A_II^{-1} (one thread per side unknown q: a band solve with the unit vector of its interior
+// neighbour, the factor read from global memory), then the original couplings this box owns.
+// Two leaves per 128-thread CTA.
 template <typename T>
-__global__ void __launch_bounds__(FTH) leaf_factor_kernel(LeafDev d) {
-  extern __shared__ double sm[];
-  __shared__ int shv[LPC][4];
+__global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
   __shared__ double qa[LPC][NQ], qc[LPC][NQ];
   __shared__ int qm[LPC][NQ], qex[LPC][NQ];
-  __shared__ double sinv[LPC * NI];
-  const int sub = threadIdx.x / 64;                 // which leaf of the pair
+  const int sub = threadIdx.x / 64;
   const int tid = threadIdx.x % 64;
   const int b = blockIdx.x * LPC + sub;
   const int nbox = d.g.nbox();
   const bool live = b < nbox;
-  double* AB = sm + (size_t)sub * LDAB * NI;
-  int* piv = reinterpret_cast<int*>(sm + (size_t)LPC * LDAB * NI) + sub * NI;
   const Geo g = d.g;
   const int I = live ? b % g.bx : 0, J = live ? b / g.bx : 0;
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
   T* F = reinterpret_cast<T*>(d.F) + (size_t)(live ? b : 0) * d.ldF * d.ldF;
-  const int D = g.D();
-
-  for (int i = tid; i < LDAB * NI; i += 64) AB[i] = 0.0;
-  if (live)
-    for (int e = tid; e < D * D; e += 64) F[(e % D) + (size_t)d.ldF * (e / D)] = T(0);
-  __syncthreads();
   if (live) {
-    for (int i = tid; i < NI; i += 64) {
-      int row = (x0 + i % LEAF) + nx * (y0 + i / LEAF);
-      for (int p = d.rowptr[row]; p < d.rowptr[row + 1]; ++p) {
-        int c = d.colind[p];
-        int cx = c % nx - x0, cy = c / nx - y0;
-        if (cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF) ab(AB, i, cx + LEAF * cy) += d.val[p];
-      }
-    }
     for (int q = tid; q < NQ; q += 64) {
       int vx, vy, m;
       side_unknown(q, x0, y0, &vx, &vy, &m);
-      bool exists = vx >= 0 && vx < nx && vy >= 0 && vy < d.ny;
+      const bool exists = vx >= 0 && vx < nx && vy >= 0 && vy < d.ny;
       qm[sub][q] = m;
       qex[sub][q] = exists ? 1 : 0;
       double a = 0.0, c = 0.0;
       if (exists) {
-        int node = vx + nx * vy;
-        int mnode = (x0 + m % LEAF) + nx * (y0 + m / LEAF);
+        const int node = vx + nx * vy;
+        const int mnode = (x0 + m % LEAF) + nx * (y0 + m / LEAF);
         a = csr_entry(d.rowptr, d.colind, d.val, node, mnode);
         c = csr_entry(d.rowptr, d.colind, d.val, mnode, node);
       }
       qa[sub][q] = a;
       qc[sub][q] = c;
     }
-  } else {
-    // an empty leaf slot: a unit diagonal keeps the shared elimination finite
-    for (int i = tid; i < NI; i += 64) ab(AB, i, i) = 1.0;
   }
   __syncthreads();
-
-  bool ok = true;
-  const int kureach = band_gepp_pair(AB, piv, tid, shv[sub], ok);
-  if (live && !ok && tid == 0) atomicOr(d.err, ERR_SINGULAR);
-
-  // factors kept for the solve, in precision T, plus the reciprocal pivots
-  T* bandg = reinterpret_cast<T*>(d.band) + (size_t)(live ? b : 0) * LDAB * NI;
-  T* invg = reinterpret_cast<T*>(d.invd) + (size_t)(live ? b : 0) * NI;
-  T* invs = reinterpret_cast<T*>(sinv) + sub * NI;
-  for (int i = tid; i < NI; i += 64) invs[i] = (T)(1.0 / ab(AB, i, i));
-  if (live) {
-    for (int i = tid; i < LDAB * NI; i += 64) bandg[i] = (T)AB[i];
-    for (int i = tid; i < NI; i += 64) {
-      d.piv[(size_t)b * NI + i] = piv[i];
-      invg[i] = invs[i];
-    }
-    if (tid == 0) atomicMax(d.kumax, kureach);
-  }
-  __syncthreads();
-  // the band in precision T for the sweeps, converted in place (front of the same buffer)
-  T* ABt = reinterpret_cast<T*>(AB);
-  if constexpr (sizeof(T) < sizeof(double)) {
-    for (int c0 = 0; c0 < LDAB * NI; c0 += 64) {
-      const int i = c0 + tid;
-      const double v = i < LDAB * NI ? AB[i] : 0.0;
-      __syncthreads();
-      if (i < LDAB * NI) ABt[i] = (T)v;
-      __syncthreads();
-    }
-  }
-  const bool active = live && ok;     // no early exit: every thread reaches every barrier
-
-  // Schur complement: one thread per side unknown q (lanes sorted by interior neighbour)
-  if (active && tid < NQ) {
+  if (live && tid < NQ) {
     const int q = c_qorder[tid];
     const int j0 = c_qstart[tid >> 5];
-    Band<T, false> Bd{ABt, piv, invs};
+    Band<T, true> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
+                     reinterpret_cast<const T*>(d.invd) + (size_t)b * NI};
     T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
     const int mq = qm[sub][q];
     const T cq = qex[sub][q] ? (T)qc[sub][q] : T(0);
@@ -293,10 +286,11 @@ __global__ void __launch_bounds__(FTH) leaf_factor_kernel(LeafDev d) {
       if (lx == 0 && qex[sub][2 * LEAF + ly]) F[(2 * LEAF + ly) + ldF * q] = -(T)qa[sub][2 * LEAF + ly] * x;
       if (lx == LEAF - 1 && qex[sub][3 * LEAF + ly]) F[(3 * LEAF + ly) + ldF * q] = -(T)qa[sub][3 * LEAF + ly] * x;
     };
-    if (kureach <= 15) sweep_U<T, 16>(Bd, yin, ring_out);   // no interchange widened U
+    if (d.kur[b] <= 15) sweep_U<T, 16>(Bd, yin, ring_out);   // no interchange widened U
     else sweep_U<T, 32>(Bd, yin, ring_out);
   }
   __syncthreads();
+  const bool active = live;
   // original couplings owned by this box: its TOP and RIGHT sides (it is their lower /
   // left box) with their end junctions, and the diagonal of its BL junction.
   //   task 0..14 TOP row -> TOP, TL, TR   15..29 RIGHT row -> RIGHT, BR, TR
@@ -562,9 +556,6 @@ void qorder_tables(int* ord, int* start) {
 
 }  // namespace
 
-size_t leaf_factor_smem() {
-  return sizeof(double) * (size_t)LPC * LDAB * NI + sizeof(int) * (LPC * NI + 2);
-}
 
 cudaError_t leaf_init_tables() {
   int ord[NQ], start[2];
@@ -575,17 +566,13 @@ cudaError_t leaf_init_tables() {
 }
 
 void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
-  size_t smem = leaf_factor_smem();
-  int grid = (d.g.nbox() + LPC - 1) / LPC;
-  if (d.fp32) {
-    cudaFuncSetAttribute(leaf_factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launch();
-    leaf_factor_kernel<float><<<grid, FTH, smem, s>>>(d);
-  } else {
-    cudaFuncSetAttribute(leaf_factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launch();
-    leaf_factor_kernel<double><<<grid, FTH, smem, s>>>(d);
-  }
+  const int nbox = d.g.nbox();
+  note_launch();
+  if (d.fp32) leaf_lu_kernel<float><<<nbox, LUT, 0, s>>>(d);
+  else leaf_lu_kernel<double><<<nbox, LUT, 0, s>>>(d);
+  note_launch();
+  if (d.fp32) leaf_schur_kernel<float><<<(nbox + LPC - 1) / LPC, FTH, 0, s>>>(d);
+  else leaf_schur_kernel<double><<<(nbox + LPC - 1) / LPC, FTH, 0, s>>>(d);
 }
 
 template <typename T, int KUW, int LPB>

@@ -185,6 +185,7 @@ struct LeafDev {
   void* ybuf;       // [nbox * 225 * 64] intermediate vectors of the band sweeps
   int* piv;         // [nbox * 225]
   int* kumax;       // largest upper bandwidth of U produced by the interchanges
+  int* kur;         // [nbox] upper bandwidth of each leaf's U
   const int* rowptr;
   const int* colind;
   const double* val;
