@@ -186,6 +186,11 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the same
+# workload, keyed by (kernel, mixed precision); a kernel missing here reports null traffic
+PROFILED_TRAFFIC = {}
+
+
 def _leaf_flops_split():
     """(FP64 FLOPs of the band LU, FLOPs of the 60 band solves) of one leaf elimination."""
     n, b = 225, 15
@@ -194,29 +199,42 @@ def _leaf_flops_split():
 
 
 def _roofline(st, steps, fp32: bool, hbm_gbs: float):
-    """Roofline of the dominant kernel among those timed alone in a phase (the leaf
-    elimination, the leaf solve sweeps): achieved = algorithmic work per launch / average
-    launch time.  The leaf elimination is bound by the FP64 pipe (its band LU) plus, in mixed
-    mode, the FP32 pipe (its band solves); the leaf solve by HBM (factor bytes + vectors)."""
+    """Roofline of the dominant kernel among those timed alone in a phase: achieved =
+    algorithmic work per launch / average launch time.
+
+    * leaf_factor (leaf_lu_kernel + leaf_schur_kernel): bound by the FP64 pipe (band LU) plus,
+      in mixed mode, the FP32 pipe (band solves);
+    * leaf_solve_kernel (forward band sweeps, one launch = 4096 leaves x 16 right-hand sides):
+      HBM bytes = the L multipliers (15 per column), U rows (15 superdiagonals and the
+      reciprocal pivot), the pivots, and the 225 interior values read and written;
+    * leaf_bwd_g_kernel (mixed backward step): the FP32 A_II^{-1} A_Id (225 x 60), the 60 side
+      values gathered and the 225 interior values read and written;
+      in FP64 the backward step is the band sweep again, with the side couplings."""
     tms, tcount = st["timing_ms"], st["timing_count"]
     nleaf = ((N_SIDE + 1) // 16) ** 2
     clk = SM_MAX_MHZ * 1e6
     p64 = N_SM * FP64_FLOP_PER_CLK_SM * clk
     p32 = N_SM * FP32_FLOP_PER_CLK_SM * clk
+    tb = 4 if fp32 else 8                  # factors and solve vectors share the precision
+    sweep = 225 * (15 + 15 + 1) * tb + 225 * 4 + 2 * 225 * NRHS * tb
     cand = {}
     if "leaf_factor" in tms:
         lu, sv = _leaf_flops_split()
         t_roof = nleaf * (lu / p64 + sv / (p32 if fp32 else p64))
-        cand["leaf_factor_kernel"] = ("alu", tms["leaf_factor"], tcount["leaf_factor"],
-                                      nleaf * (lu + sv), t_roof)
+        cand["leaf_lu_kernel+leaf_schur_kernel"] = ("alu", tms["leaf_factor"], tcount["leaf_factor"],
+                                                    nleaf * (lu + sv), t_roof)
     if "leaf_solve_fwd" in tms:
-        t = tms["leaf_solve_fwd"] + tms.get("leaf_solve_bwd", 0.0)
-        c = tcount["leaf_solve_fwd"] + tcount.get("leaf_solve_bwd", 0)
-        tb = 4 if fp32 else 8
-        # per launch (one sweep pair, all 16 right-hand sides): the band factor, pivots and
-        # reciprocal pivots once, the interior unknowns read and written
-        byts = nleaf * (46 * 225 * tb + 225 * 4 + 225 * tb) + 2 * 8 * nleaf * 225 * NRHS
-        cand["leaf_solve_kernel"] = ("hbm", t, c, byts, byts / (hbm_gbs * 1e9))
+        byts = nleaf * sweep
+        cand["leaf_solve_kernel"] = ("hbm", tms["leaf_solve_fwd"], tcount["leaf_solve_fwd"], byts,
+                                     byts / (hbm_gbs * 1e9))
+    if "leaf_solve_bwd" in tms:
+        if fp32:
+            byts = nleaf * (225 * 60 * 4 + 60 * NRHS * 4 + 2 * 225 * NRHS * 4)
+            name = "leaf_bwd_g_kernel"
+        else:
+            byts = nleaf * sweep
+            name = "leaf_solve_kernel(backward)"
+        cand[name] = ("hbm", tms["leaf_solve_bwd"], tcount["leaf_solve_bwd"], byts, byts / (hbm_gbs * 1e9))
     dom = max(cand, key=lambda k: cand[k][1])
     bound, tot, cnt, work, t_roof = cand[dom]
     dur_s = tot / cnt / 1e3
@@ -229,9 +247,10 @@ def _roofline(st, steps, fp32: bool, hbm_gbs: float):
         unit = "TFLOP/s"
         src = ("derived: FP64 band LU at 152 SMs x 4 FLOP/clk x 2070 MHz" +
                (" + FP32 band solves at 152 x 256 FLOP/clk x 2070 MHz" if fp32 else ""))
+    traffic = PROFILED_TRAFFIC.get((dom, fp32))
     return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-            "traffic": None, "kernel": dom, "launch_ms": dur_s * 1e3, "share_of_step_ms": tot / steps,
-            "peak_source": src}
+            "traffic": traffic, "kernel": dom, "algorithmic_bytes" if bound == "hbm" else "algorithmic_flops": work,
+            "launch_ms": dur_s * 1e3, "share_of_step_ms": tot / steps, "peak_source": src}
 
 
 def _nvtx(push: bool):

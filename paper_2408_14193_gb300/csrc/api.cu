@@ -27,7 +27,7 @@ struct GmresWork {
   int nrhs = 0, m = 0;
   double* V = nullptr;      // (m+1) * N * nrhs   Krylov basis
   double* Z = nullptr;      // m * N * nrhs       M^{-1} V_j, kept for the update (no final solve)
-  double* W = nullptr;      // N * nrhs
+  unsigned* cnt = nullptr;  // ticket counters of the column sums, one per column chunk
   double* R = nullptr;      // N * nrhs
   double* part = nullptr;   // partial sums
   double* hcol = nullptr;   // device coefficients (m+2) * nrhs
@@ -95,8 +95,11 @@ struct spalu_factor_s {
   int* rowptr = nullptr;
   int* colind = nullptr;
   double* val = nullptr;
+  float* fval = nullptr;     // FP32 copy of val (mixed path: the solve's separator update)
   int nnz = 0;
   bool factored = false;
+  float* xf = nullptr;       // FP32 solve vector of the mixed path, N x xf_cols
+  int xf_cols = 0;
   cudaStream_t last_stream = nullptr;
   GmresWork gw;
   std::vector<int> host_rowptr_cache;
@@ -171,55 +174,122 @@ spalu_status read_err(spalu_factor_t f, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ GMRES helper kernels
-__global__ void spmv_residual_kernel(int n, const int* rowptr, const int* colind, const double* val,
-                                     const double* x, int ldx, const double* b, int ldb, double* y,
-                                     int ldy, int nrhs) {
-  long long tot = (long long)n * nrhs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(e % n), c = (int)(e / n);
-    double acc = 0.0;
-    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) acc += val[p] * x[colind[p] + (size_t)ldx * c];
-    y[r + (size_t)ldy * c] = b ? b[r + (size_t)ldb * c] - acc : acc;
-  }
-}
+// Vector kernels over N rows x nrhs columns: one thread per row and RC columns (blockIdx.y =
+// column chunk), so a row of the CSR matrix is read once per chunk.  Column sums are
+// deterministic: each block writes one partial per column, and the last block of a chunk to
+// finish (ticket counter, reset by that block) adds the partials in block order.
+constexpr int RC = 8;
+constexpr int VB = 256;                  // threads per block of the vector kernels
+constexpr int VNB = 1024;                // most blocks per column chunk (partial buffer width)
 
-// partial dot products: part[c * nb + blockIdx.x] (deterministic two-pass reduction)
-__global__ void dot_partial_kernel(int n, const double* x, int ldx, const double* y, int ldy,
-                                   double* part) {
-  __shared__ double red[32];
-  const int c = blockIdx.y;
-  double s = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    s += x[i + (size_t)ldx * c] * y[i + (size_t)ldy * c];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+static_assert(VB == 32 * RC, "one warp per column of a chunk in the block sums");
+__device__ void column_sums(double (&s)[RC], int c0, int nrhs, double* part, unsigned* cnt,
+                            double* out, int sq) {
+  __shared__ double red[RC][VB];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;   // warp k sums column c0 + k
+  const int nb = gridDim.x;
+  const bool valid = c0 + k < nrhs;
+#pragma unroll
+  for (int i = 0; i < RC; ++i) red[i][threadIdx.x] = s[i];
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = t;
+  double t = 0.0;
+#pragma unroll
+  for (int m = 0; m < VB / 32; ++m) t += red[k][lane + 32 * m];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0 && valid) {
+    part[(size_t)(c0 + k) * nb + blockIdx.x] = t;
+    __threadfence();
   }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(cnt + blockIdx.y, 1u) == (unsigned)(nb - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  t = 0.0;
+  if (valid)
+    for (int i = lane; i < nb; i += 32) t += __ldcg(part + (size_t)(c0 + k) * nb + i);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0 && valid) out[c0 + k] = sq ? sqrt(t) : t;
+  if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
-__global__ void dot_final_kernel(const double* part, int nb, double* out, int sq) {
-  const int c = blockIdx.x;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(size_t)c * nb + b];
-    out[c] = sq ? sqrt(s) : s;
+// y = b - A x (b null: y = A x); when part is set, out[c] = <y_c, d_c> (d null: ||y_c||, sq)
+__global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int* rowptr, const int* colind,
+                                                  const double* val, const double* x, int ldx,
+                                                  const double* b, int ldb, double* y, int ldy,
+                                                  const double* d, int ldd, double* part,
+                                                  unsigned* cnt, double* out, int sq) {
+  const int c0 = blockIdx.y * RC;
+  const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
+  double s[RC];
+#pragma unroll
+  for (int k = 0; k < RC; ++k) s[k] = 0.0;
+  for (long long r = blockIdx.x * (long long)VB + threadIdx.x; r < n; r += (long long)gridDim.x * VB) {
+    double acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+    const int p1 = rowptr[r + 1];
+    for (int p = rowptr[r]; p < p1; ++p) {
+      const int col = colind[p];
+      const double v = val[p];
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < nc) acc[k] += v * x[col + (size_t)ldx * (c0 + k)];
+    }
+#pragma unroll
+    for (int k = 0; k < RC; ++k)
+      if (k < nc) {
+        const double yv = b ? b[r + (size_t)ldb * (c0 + k)] - acc[k] : acc[k];
+        y[r + (size_t)ldy * (c0 + k)] = yv;
+        s[k] += yv * (d ? d[r + (size_t)ldd * (c0 + k)] : yv);
+      }
   }
+  if (part) column_sums(s, c0, nrhs, part, cnt, out, sq);
 }
 
-// y[:, c] += alpha * coef[c] * x[:, c]
-__global__ void axpy_kernel(int n, int nrhs, double alpha, const double* coef, const double* x,
-                            int ldx, double* y, int ldy) {
-  long long tot = (long long)n * nrhs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(e % n), c = (int)(e / n);
-    y[r + (size_t)ldy * c] += alpha * coef[c] * x[r + (size_t)ldx * c];
+// One modified Gram-Schmidt pass: w_c -= h_c p_c (skipped when p is null), then
+// out[c] = <w_c, q_c> (q null: ||w_c||, sq)
+__global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const double* h, const double* p, int ldp,
+                                                 double* w, int ldw, const double* q, int ldq,
+                                                 double* part, unsigned* cnt, double* out, int sq) {
+  const int c0 = blockIdx.y * RC;
+  const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
+  double s[RC], hc[RC];
+#pragma unroll
+  for (int k = 0; k < RC; ++k) {
+    s[k] = 0.0;
+    hc[k] = (p && k < nc) ? h[c0 + k] : 0.0;
+  }
+  for (long long r = blockIdx.x * (long long)VB + threadIdx.x; r < n; r += (long long)gridDim.x * VB) {
+#pragma unroll
+    for (int k = 0; k < RC; ++k)
+      if (k < nc) {
+        double wv = w[r + (size_t)ldw * (c0 + k)];
+        if (p) {
+          wv -= hc[k] * p[r + (size_t)ldp * (c0 + k)];
+          w[r + (size_t)ldw * (c0 + k)] = wv;
+        }
+        s[k] += wv * (q ? q[r + (size_t)ldq * (c0 + k)] : wv);
+      }
+  }
+  column_sums(s, c0, nrhs, part, cnt, out, sq);
+}
+
+// X_c += sum_i y[i][c] Z_i,c for i = 0..k-1, in that order (Z_i = Z + i * ldz * nrhs)
+__global__ void __launch_bounds__(VB, 4) combine_kernel(int n, int nrhs, int k, const double* y,
+                                                     const double* Z, size_t ldz, double* X, int ldx) {
+  const int c0 = blockIdx.y * RC;
+  const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
+  for (long long r = blockIdx.x * (long long)VB + threadIdx.x; r < n; r += (long long)gridDim.x * VB) {
+#pragma unroll
+    for (int kk = 0; kk < RC; ++kk)
+      if (kk < nc) {
+        const int c = c0 + kk;
+        double xv = X[r + (size_t)ldx * c];
+        for (int i = 0; i < k; ++i) xv += y[(size_t)i * nrhs + c] * Z[(size_t)i * ldz * nrhs + r + ldz * c];
+        X[r + (size_t)ldx * c] = xv;
+      }
   }
 }
 
@@ -232,6 +302,17 @@ __global__ void scale_kernel(int n, int nrhs, const double* s, const double* x, 
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x)
     y[r + (size_t)ldy * c] = x[r + (size_t)ldx * c] * di;
+}
+
+// dst[:, c] = src[:, c] in the other precision (round to nearest), n rows, nc columns
+template <typename S, typename D>
+__global__ void convert_kernel(long long n, int nc, const S* src, int lds, D* dst, int ldd) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * nc;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % n;
+    const int c = (int)(e / n);
+    dst[r + (size_t)ldd * c] = (D)src[r + (size_t)lds * c];
+  }
 }
 
 int grid_for(long long n) {
@@ -409,6 +490,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     f->rowptr = cv.take<int>(f->N + 1);
     f->colind = cv.take<int>(f->nnz_cap);
     f->val = cv.take<double>(f->nnz_cap);
+    f->fval = o->precision == 1 ? cv.take<float>(f->nnz_cap) : nullptr;
     const Geo& gl = nd->depth[L];
     LeafDev& lf = f->leaf;
     lf.nx = nd->nx; lf.ny = nd->ny; lf.L = L; lf.g = gl; lf.ldF = ldF[L];
@@ -419,6 +501,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     lf.band = real((size_t)gl.nbox() * LDAB * NI);
     lf.invd = real((size_t)gl.nbox() * NI);
     lf.ybuf = real((size_t)gl.nbox() * NI * 64);
+    lf.G = f32 ? (void*)cv.take<float>((size_t)gl.nbox() * NI * 4 * LEAF) : nullptr;
     lf.piv = cv.take<int>((size_t)gl.nbox() * NI);
     lf.kumax = cv.take<int>(4);
     lf.kur = cv.take<int>((size_t)gl.nbox());
@@ -475,6 +558,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   f->leaf.rowptr = f->rowptr;
   f->leaf.colind = f->colind;
   f->leaf.val = f->val;
+  f->leaf.fval = f->fval;
   f->leaf.err = f->d_err;
   for (int l = 1; l <= L; ++l) {
     f->lev[l].err = f->d_err;
@@ -499,6 +583,10 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   if (f->pred_mode == PRED_RECORD && f->tgt_ints)
     CUDA_TRY(cudaMemsetAsync(f->d_tgt_all, 0, sizeof(int) * f->tgt_ints, s));
   if (L >= 1) launch_level_init_L(f->lev[L], s);
+  if (f->fval && f->nnz > 0) {
+    note_launch();
+    convert_kernel<double, float><<<grid_for(f->nnz), 256, 0, s>>>(f->nnz, 1, f->val, 0, f->fval, 0);
+  }
   if (f->pred_mode != PRED_OFF) launch_node_stats(f->rowptr, f->colind, f->val, f->N, f->d_nstat, s);
   int t = tm.begin("leaf_factor", s);
   launch_leaf_factor(f->leaf, s);
@@ -562,24 +650,46 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
   if (nrhs == 0) return SPALU_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int L = f->nd->L;
+  const int N = f->N;
   PhaseTimer& tm = f->timer;
   int t_all = tm.begin("solve", s);
-  if (X != B)
+  // the mixed path solves on an FP32 copy (ld = N): every kernel of the solve reads and writes
+  // the precision of the factors, and B and X are converted once each
+  void* W = X;
+  int ldw = ld;
+  if (f->leaf.fp32) {
+    if (f->xf_cols < nrhs) {
+      cudaFree(f->xf);
+      f->xf = nullptr;
+      f->xf_cols = 0;
+      if (cudaMalloc(&f->xf, sizeof(float) * (size_t)N * nrhs) != cudaSuccess) return SPALU_ERR_ALLOC;
+      f->xf_cols = nrhs;
+    }
+    note_launch();
+    convert_kernel<double, float><<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, B, ld, f->xf, N);
+    W = f->xf;
+    ldw = N;
+  } else if (X != B) {
     CUDA_TRY(cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), B, (size_t)ld * sizeof(double),
-                               (size_t)f->N * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
+                               (size_t)N * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
+  }
   int t = tm.begin("leaf_solve_fwd", s);
-  launch_leaf_solve(f->leaf, X, nrhs, ld, 0, f->kumax, s);
+  launch_leaf_solve(f->leaf, W, nrhs, ldw, 0, f->kumax, s);
   tm.end(t, s);
   t = tm.begin("sep_update", s);
-  if (L >= 1) launch_sep_update_fwd(f->leaf, X, nrhs, ld, s);
+  if (L >= 1) launch_sep_update_fwd(f->leaf, W, nrhs, ldw, s);
   tm.end(t, s);
   t = tm.begin("level_solve", s);
-  for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], f->caps[l], X, nrhs, ld, s);
-  for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], f->caps[l], X, nrhs, ld, s);
+  for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], f->caps[l], W, nrhs, ldw, s);
+  for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], f->caps[l], W, nrhs, ldw, s);
   tm.end(t, s);
   t = tm.begin("leaf_solve_bwd", s);
-  launch_leaf_solve(f->leaf, X, nrhs, ld, 1, f->kumax, s);
+  launch_leaf_solve(f->leaf, W, nrhs, ldw, 1, f->kumax, s);
   tm.end(t, s);
+  if (f->leaf.fp32) {
+    note_launch();
+    convert_kernel<float, double><<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, f->xf, N, X, ld);
+  }
   tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());
   return SPALU_OK;
@@ -589,14 +699,15 @@ static spalu_status gmres_alloc(spalu_factor_t f, int nrhs) {
   GmresWork& w = f->gw;
   const int m = f->o.gmres_m;
   if (w.nrhs >= nrhs && w.m == m) return SPALU_OK;
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
   w = GmresWork();
   size_t N = f->N;
   if (cudaMalloc(&w.V, sizeof(double) * (m + 1) * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.Z, sizeof(double) * (size_t)m * N * nrhs) != cudaSuccess ||
-      cudaMalloc(&w.W, sizeof(double) * N * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.cnt, sizeof(unsigned) * ((nrhs + RC - 1) / RC)) != cudaSuccess ||
+      cudaMemset(w.cnt, 0, sizeof(unsigned) * ((nrhs + RC - 1) / RC)) != cudaSuccess ||
       cudaMalloc(&w.R, sizeof(double) * N * nrhs) != cudaSuccess ||
-      cudaMalloc(&w.part, sizeof(double) * 1024 * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.part, sizeof(double) * VNB * nrhs) != cudaSuccess ||
       cudaMalloc(&w.hcol, sizeof(double) * (m + 2) * nrhs) != cudaSuccess ||
       cudaMalloc(&w.vec, sizeof(double) * 4 * nrhs) != cudaSuccess)
     return SPALU_ERR_ALLOC;
@@ -605,15 +716,38 @@ static spalu_status gmres_alloc(spalu_factor_t f, int nrhs) {
   return SPALU_OK;
 }
 
-// out[c] = <x_c, y_c> (or its square root) for nrhs columns, deterministic order
-static void dots(spalu_factor_t f, const double* x, int ldx, const double* y, int ldy, int nrhs,
-                 double* out, int sq, cudaStream_t s) {
-  const int nb = 512;
-  dim3 grid(nb, nrhs);
+// about four blocks per SM in all: few blocks keep the per-block column sums (FP64 adds, slow
+// on this part) small next to the streamed work
+static dim3 vec_grid(int n, int nrhs) {
+  static const int nsm = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  const int nch = (nrhs + RC - 1) / RC;
+  int nb = 4 * nsm / nch;
+  const int need = (n + VB - 1) / VB;
+  nb = nb < need ? nb : need;
+  nb = nb < VNB ? nb : VNB;
+  return dim3(nb > 0 ? nb : 1, nch);
+}
+
+// w -= h p (p null: w unchanged), out[c] = <w_c, q_c> (q null: ||w_c||, sq)
+static void vec_mgs(spalu_factor_t f, int nrhs, const double* h, const double* p, int ldp, double* w,
+                    int ldw, const double* q, int ldq, double* out, int sq, cudaStream_t s) {
   note_launch();
-  dot_partial_kernel<<<grid, 256, 0, s>>>(f->N, x, ldx, y, ldy, f->gw.part);
+  mgs_kernel<<<vec_grid(f->N, nrhs), VB, 0, s>>>(f->N, nrhs, h, p, ldp, w, ldw, q, ldq, f->gw.part,
+                                                 f->gw.cnt, out, sq);
+}
+
+// y = b - A x (b null: A x); out set: out[c] = <y_c, d_c> (d null: ||y_c||, sq)
+static void vec_spmv(spalu_factor_t f, int nrhs, const double* x, int ldx, const double* b, int ldb,
+                     double* y, int ldy, const double* d, int ldd, double* out, int sq, cudaStream_t s) {
   note_launch();
-  dot_final_kernel<<<nrhs, 32, 0, s>>>(f->gw.part, nb, out, sq);
+  spmv_kernel<<<vec_grid(f->N, nrhs), VB, 0, s>>>(f->N, nrhs, f->rowptr, f->colind, f->val, x, ldx, b, ldb,
+                                                  y, ldy, d, ldd, out ? f->gw.part : nullptr, f->gw.cnt,
+                                                  out, sq);
 }
 
 static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
@@ -645,12 +779,10 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
   auto Zj = [&](int j) { return w.Z + (size_t)j * ldv * nrhs; };
   std::vector<double> bn(nrhs), beta(nrhs), hh((size_t)(m + 2) * nrhs);
   double* dvec = w.vec;   // [0, nrhs): norms; [nrhs, 2 nrhs): scratch
-  dots(f, B, ld, B, ld, nrhs, dvec, 1, s);
+  vec_mgs(f, nrhs, nullptr, nullptr, 0, const_cast<double*>(B), ld, nullptr, 0, dvec, 1, s);
   CUDA_TRY(cudaMemcpyAsync(bn.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
   auto residual = [&]() -> spalu_status {
-    note_launch();
-    spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, X, ld, B, ld, w.R, (int)ldv, nrhs);
-    dots(f, w.R, (int)ldv, w.R, (int)ldv, nrhs, dvec, 1, s);
+    vec_spmv(f, nrhs, X, ld, B, ld, w.R, (int)ldv, nullptr, 0, dvec, 1, s);
     CUDA_TRY(cudaMemcpyAsync(beta.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SPALU_OK;
@@ -681,15 +813,12 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     for (int j = 0; j < m; ++j) {
       // Z_j = M^{-1} V_j (kept), V_{j+1} = A Z_j
       if ((st = spalu_solve(f, Vj(j), Zj(j), nrhs, (int)ldv, stream)) != SPALU_OK) return st;
-      note_launch();
-      spmv_residual_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, f->rowptr, f->colind, f->val, Zj(j), (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, nrhs);
-      // modified Gram-Schmidt
-      for (int i = 0; i <= j; ++i) {
-        dots(f, Vj(j + 1), (int)ldv, Vj(i), (int)ldv, nrhs, w.hcol + (size_t)i * nrhs, 0, s);
-        note_launch();
-        axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, -1.0, w.hcol + (size_t)i * nrhs, Vj(i), (int)ldv, Vj(j + 1), (int)ldv);
-      }
-      dots(f, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv, nrhs, w.hcol + (size_t)(j + 1) * nrhs, 1, s);
+      // modified Gram-Schmidt, each subtraction fused with the next inner product:
+      // h_0 = <A Z_j, V_0> in the product's pass, then w -= h_{i-1} V_{i-1}, h_i = <w, V_i>
+      vec_spmv(f, nrhs, Zj(j), (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, Vj(0), (int)ldv, w.hcol, 0, s);
+      for (int i = 1; i <= j + 1; ++i)
+        vec_mgs(f, nrhs, w.hcol + (size_t)(i - 1) * nrhs, Vj(i - 1), (int)ldv, Vj(j + 1), (int)ldv,
+                i <= j ? Vj(i) : nullptr, (int)ldv, w.hcol + (size_t)i * nrhs, i > j, s);
       note_launch();
       scale_kernel<<<dim3(grid_for(N) / nrhs + 1, nrhs), 256, 0, s>>>(N, nrhs, w.hcol + (size_t)(j + 1) * nrhs, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
       CUDA_TRY(cudaMemcpyAsync(hh.data(), w.hcol, sizeof(double) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
@@ -730,10 +859,8 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     }
     // X += M^{-1} V y = sum_i y_i Z_i
     CUDA_TRY(cudaMemcpyAsync(w.hcol, ycoef.data(), sizeof(double) * kdim * nrhs, cudaMemcpyHostToDevice, s));
-    for (int i = 0; i < kdim; ++i) {
-      note_launch();
-      axpy_kernel<<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, 1.0, w.hcol + (size_t)i * nrhs, Zj(i), (int)ldv, X, ld);
-    }
+    note_launch();
+    combine_kernel<<<vec_grid(N, nrhs), VB, 0, s>>>(N, nrhs, kdim, w.hcol, w.Z, ldv, X, ld);
     if ((st = residual()) != SPALU_OK) return st;
   }
   bool conv = true;
@@ -1014,8 +1141,9 @@ spalu_status spalu_factor_export_training(spalu_factor_t f, float* X, float* Y, 
 void spalu_factor_destroy(spalu_factor_t f) {
   if (!f) return;
   cudaFree(f->arena);
+  cudaFree(f->xf);
   GmresWork& w = f->gw;
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.W); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
   delete f;
 }
 

@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
     Band<T, true> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
                      reinterpret_cast<const T*>(d.invd) + (size_t)b * NI};
     T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
+    T* Gb = d.G ? reinterpret_cast<T*>(d.G) + (size_t)b * NI * NQ : nullptr;
     const int mq = qm[sub][q];
     const T cq = qex[sub][q] ? (T)qc[sub][q] : T(0);
     sweep_L<T>(Bd, j0, [&](int j) { return j == mq ? cq : T(0); },
@@ -280,6 +281,7 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
     const size_t ldF = d.ldF;
     auto yin = [&](int j) { return j < j0 ? T(0) : yb[(size_t)j * QL + tid]; };
     auto ring_out = [&](int j, T x) {
+      if (Gb) Gb[(size_t)j * NQ + q] = x;                   // column q of A_II^{-1} A_Id
       const int lx = j % LEAF, ly = j / LEAF;
       if (ly == 0 && qex[sub][lx]) F[lx + ldF * q] = -(T)qa[sub][lx] * x;
       if (ly == LEAF - 1 && qex[sub][LEAF + lx]) F[(LEAF + lx) + ldF * q] = -(T)qa[sub][LEAF + lx] * x;
@@ -351,10 +353,35 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <typename T, int KUW, int LPB>
-__global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, double* X, int nrhs, int ld, int bwd) {
+// 16 consecutive values of shared memory (16-byte aligned) into registers, 128-bit loads
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(p)[i];
+      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const double2 q = reinterpret_cast<const double2*>(p)[i];
+      v[2 * i] = q.x; v[2 * i + 1] = q.y;
+    }
+  }
+}
+
+// Band sweeps of LPB leaves x 16 right-hand sides per CTA, thread (leaf, rhs): forward
+// x_I = U^{-1} L^{-1} P b_I; backward x_I -= U^{-1} L^{-1} P (A_Id x_d).  The factors of the
+// next block of 16 (L) or KUW (U) steps are staged by cp.async while the current block runs,
+// a half-warp per band column; in the FP32 forward L sweep each thread also stages its own
+// right-hand-side rows one block ahead (the FP64 variant loads them directly: its shared
+// memory would otherwise cost resident CTAs).
+template <typename T, int KUW, int LPB, bool bwd>
+__global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X, int nrhs, int ld) {
   extern __shared__ double lsm[];
-  constexpr int LST = SLOT * SLOT;                    // L stage per leaf: 16 columns x 16 (r = 1..15)
+  constexpr int NT = LPB * SLOT;
+  constexpr int LST = SLOT * SLOT;                    // L stage per leaf: 16 columns x 16 (L(j+r, j) at r - 1)
   constexpr int UST = KUW * KUW;                      // U stage per leaf: KUW columns x KUW (r = 0 -> 1/U_jj)
   constexpr int RMAX = KUW - 1 < KV ? KUW - 1 : KV;
   T* stg = reinterpret_cast<T*>(lsm);                 // 2 buffers
@@ -366,31 +393,47 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
   const int bb = b < nbox ? b : nbox - 1;
   const T* gband = reinterpret_cast<const T*>(d.band);
   const T* ginv = reinterpret_cast<const T*>(d.invd);
-  const size_t bufL = (size_t)LPB * (LST + SLOT);     // values + pivots (pivots stored as T slots)
-  const size_t bufU = (size_t)LPB * UST;
-  const size_t bufsz = bufL > bufU ? bufL : bufU;
+  constexpr size_t bufL = (size_t)LPB * (LST + SLOT); // values + pivots (pivots stored as T slots)
+  constexpr size_t bufU = (size_t)LPB * UST;
+  constexpr size_t bufsz = bufL > bufU ? bufL : bufU;
   const int I = bb % d.g.bx, J = bb / d.g.bx;
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
   T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)bb * NI * QL;
-  double* Xc = X + (size_t)ld * c;
+  T* Xc = X + (size_t)ld * c;
   auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
+  constexpr bool XPF = !bwd && sizeof(T) == 4;       // stage the right-hand-side rows
+  T* xst = stg + 2 * bufsz + (size_t)threadIdx.x * 2 * SLOT;   // own rows, 2 x 16
 
   // ---- L sweep: y = L^{-1} P x, blocks of 16 steps
   auto issue_L = [&](int blk, int buf) {
     T* S = stg + (size_t)buf * bufsz;
     const int j0 = blk * SLOT;
-    for (int x = threadIdx.x; x < LPB * SLOT * (SLOT - 1); x += blockDim.x) {
-      const int sl = x / (SLOT * (SLOT - 1)), rem = x % (SLOT * (SLOT - 1));
-      const int u = rem / (SLOT - 1), r = rem % (SLOT - 1) + 1;
-      const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
-      if (j0 + u < NI) cp_async_t(S + (size_t)sl * LST + u * SLOT + r, gband + (size_t)lb * LDAB * NI + (KV + r) + LDAB * (j0 + u));
+    {
+      // half-warps over band columns (col = leaf * 16 + u), lane r < 15 copies L(j+1+r, j):
+      // contiguous in the band, so each half-warp reads one run of 15 values
+      const int r = threadIdx.x & 15;
+#pragma unroll 4
+      for (int col = threadIdx.x >> 4; col < LPB * SLOT; col += NT / 16) {
+        const int sl = col / SLOT, u = col % SLOT;
+        const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
+        if (j0 + u < NI) {
+          if (r < SLOT - 1)
+            cp_async_t(S + (size_t)sl * LST + u * SLOT + r, gband + (size_t)lb * LDAB * NI + (KV + 1 + r) + (size_t)LDAB * (j0 + u));
+          else
+            cp_async4(reinterpret_cast<int*>(S + (size_t)LPB * LST) + col, d.piv + (size_t)lb * NI + j0 + u);
+        }
+      }
     }
-    int* P = reinterpret_cast<int*>(S + (size_t)LPB * LST);
-    for (int x = threadIdx.x; x < LPB * SLOT; x += blockDim.x) {
-      const int sl = x / SLOT, u = x % SLOT;
-      const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
-      if (j0 + u < NI) cp_async4(P + x, d.piv + (size_t)lb * NI + j0 + u);
+    if (XPF && active) {                              // rows j0 + 16 .. j0 + 31 of this thread's rhs
+      T* xs = xst + (buf & 1) * SLOT;
+      int j = j0 + SLOT;
+      int lx = j % LEAF, node = node_of(j);
+#pragma unroll
+      for (int u = 0; u < SLOT; ++u, ++j) {
+        if (j < NI) cp_async_t(xs + u, Xc + node);
+        if (++lx == LEAF) { lx = 0; node += nx - (LEAF - 1); } else ++node;
+      }
     }
     cp_async_commit();
   };
@@ -399,7 +442,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
   if (active) {
     if (!bwd) {
 #pragma unroll
-      for (int r = 0; r < 16; ++r) W[r] = (T)Xc[node_of(r)];
+      for (int r = 0; r < 16; ++r) W[r] = Xc[node_of(r)];
     } else {
 #pragma unroll
       for (int r = 0; r < 16; ++r) W[r] = T(0);
@@ -413,7 +456,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
       for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
         const int cc = d.colind[p];
         const int cx = cc % nx - x0, cy = cc / nx - y0;
-        if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)(d.val[p] * Xc[cc]);
+        if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)d.val[p] * Xc[cc];
       }
     }
     return v;
@@ -429,6 +472,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
     __syncthreads();
     const T* S = stg + (size_t)(blk & 1) * bufsz + (size_t)sub * LST;
     const int* P = reinterpret_cast<const int*>(stg + (size_t)(blk & 1) * bufsz + (size_t)LPB * LST) + sub * SLOT;
+    const T* xs = xst + (blk & 1) * SLOT;
     if (active) {
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
@@ -442,10 +486,18 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
               if (r == dsw) { bv = W[(u + r) & 15]; W[(u + r) & 15] = a; }
             W[u] = bv;
           }
+          T lv[16];
+          lds_vec(S + u * SLOT, lv);
 #pragma unroll
-          for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= S[u * SLOT + r] * bv;
+          for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= lv[r - 1] * bv;
           yb[(size_t)j * QL + c] = bv;
-          W[u] = (j + 16 < NI) ? (!bwd ? (T)Xc[node_of(j + 16)] : coupling(j + 16)) : T(0);
+          T nv = T(0);
+          if (j + 16 < NI) {
+            if constexpr (XPF) nv = xs[u];
+            else if constexpr (!bwd) nv = Xc[node_of(j + 16)];
+            else nv = coupling(j + 16);
+          }
+          W[u] = nv;
         }
       }
     }
@@ -456,14 +508,18 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
   auto issue_U = [&](int blk, int buf) {
     T* S = stg + (size_t)buf * bufsz;
     const int t0 = blk * KUW;
-    for (int x = threadIdx.x; x < LPB * KUW * KUW; x += blockDim.x) {
-      const int sl = x / (KUW * KUW), rem = x % (KUW * KUW);
-      const int u = rem / KUW, r = rem % KUW;
+    // half-warps over band columns; lane r copies 1/U_jj (r = 0) or U(j-r, j) (r <= RMAX)
+    const int r0 = threadIdx.x & 15;
+#pragma unroll 4
+    for (int cr = threadIdx.x >> 4; cr < LPB * KUW * (KUW / 16); cr += NT / 16) {
+      const int col = cr / (KUW / 16), r = r0 + 16 * (cr % (KUW / 16));
+      const int sl = col / KUW, u = col % KUW;
       const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
       const int j = NI - 1 - (t0 + u);
       if (j >= 0 && r <= RMAX) {
-        if (r == 0) cp_async_t(S + x, ginv + (size_t)lb * NI + j);
-        else cp_async_t(S + x, gband + (size_t)lb * LDAB * NI + (KV - r) + LDAB * j);
+        T* dst = S + (size_t)sl * UST + u * KUW + r;
+        if (r == 0) cp_async_t(dst, ginv + (size_t)lb * NI + j);
+        else cp_async_t(dst, gband + (size_t)lb * LDAB * NI + (KV - r) + (size_t)LDAB * j);
       }
     }
     cp_async_commit();
@@ -486,11 +542,13 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
         const int t = blk * KUW + u;
         if (t < NI) {
           const int j = NI - 1 - t;
-          const T x = V[u] * S[u * KUW];
-          if (!bwd) Xc[node_of(j)] = (double)x;
-          else Xc[node_of(j)] -= (double)x;
+          T uv[KUW];
+          lds_vec(S + u * KUW, uv);
+          const T x = V[u] * uv[0];
+          if (!bwd) Xc[node_of(j)] = x;
+          else Xc[node_of(j)] -= x;
 #pragma unroll
-          for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= S[u * KUW + r] * x;
+          for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= uv[r] * x;
           V[u] = (j - KUW >= 0) ? yb[(size_t)(j - KUW) * QL + c] : T(0);
         }
       }
@@ -499,11 +557,72 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, doubl
   }
 }
 
+// Backward leaf step of the mixed path: x_I -= G x_d with G = A_II^{-1} A_Id (FP32, stored by
+// the factorization) and x_d the 60 side unknowns of the leaf.  One leaf per CTA: G is staged
+// in shared memory by cp.async while x_d is gathered, then thread j forms row j of G x_d for
+// all right-hand sides of the chunk (up to 16) and updates the interior unknown j.
+constexpr int GTH = 256;
+constexpr int GRC = 16;                          // right-hand sides per launch
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+
+__global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X, int nrhs, int ld) {
+  extern __shared__ float4 gsm4[];
+  float* Gs = reinterpret_cast<float*>(gsm4);    // NI x NQ
+  float* xd = Gs + NI * NQ;                      // NQ x GRC
+  const int b = blockIdx.x;
+  const float* Gg = reinterpret_cast<const float*>(d.G) + (size_t)b * NI * NQ;
+  for (int i = threadIdx.x; i < NI * NQ / 4; i += GTH) cp_async16(Gs + 4 * i, Gg + 4 * i);
+  cp_async_commit();
+  const int I = b % d.g.bx, J = b / d.g.bx;
+  const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
+  const int nx = d.nx;
+  for (int i = threadIdx.x; i < NQ * GRC; i += GTH) {
+    const int q = i / GRC, c = i % GRC;
+    int vx, vy, m;
+    side_unknown(q, x0, y0, &vx, &vy, &m);
+    const bool ex = c < nrhs && vx >= 0 && vx < nx && vy >= 0 && vy < d.ny;
+    xd[i] = ex ? X[(vx + nx * vy) + (size_t)ld * c] : 0.f;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j >= NI) return;
+  float acc[GRC];
+#pragma unroll
+  for (int c = 0; c < GRC; ++c) acc[c] = 0.f;
+  const float4* gr = reinterpret_cast<const float4*>(Gs + j * NQ);
+  const float4* x4 = reinterpret_cast<const float4*>(xd);
+#pragma unroll 3
+  for (int k = 0; k < NQ / 4; ++k) {
+    const float4 g = gr[k];
+    const float gq[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+#pragma unroll
+      for (int c4 = 0; c4 < GRC / 4; ++c4) {
+        const float4 v = x4[(4 * k + t) * (GRC / 4) + c4];
+        acc[4 * c4 + 0] += gq[t] * v.x;
+        acc[4 * c4 + 1] += gq[t] * v.y;
+        acc[4 * c4 + 2] += gq[t] * v.z;
+        acc[4 * c4 + 3] += gq[t] * v.w;
+      }
+    }
+  }
+  const size_t node = (size_t)(x0 + j % LEAF) + (size_t)nx * (y0 + j / LEAF);
+#pragma unroll
+  for (int c = 0; c < GRC; ++c)
+    if (c < nrhs) X[node + (size_t)ld * c] -= acc[c];
+}
+
 // b_u -= sum over interior neighbours j of A_uj t_j, for every separator node u.  One thread
 // per (separator node, right-hand side); separator nodes are enumerated in closed form: the
 // R full separator rows (y = 16 r + 15) first, then the C separator columns (x = 16 q + 15) of
 // the remaining rows.
-__global__ void sep_update_fwd_kernel(LeafDev d, double* X, int nrhs, int ld) {
+template <typename T>
+__global__ void sep_update_fwd_kernel(LeafDev d, T* X, int nrhs, int ld) {
   const int nx = d.nx, ny = d.ny;
   const int R = (ny + 1) / (LEAF + 1) - 1, C = (nx + 1) / (LEAF + 1) - 1;
   const long long nrow = (long long)R * nx;
@@ -523,12 +642,16 @@ __global__ void sep_update_fwd_kernel(LeafDev d, double* X, int nrhs, int ld) {
       uy = (yy / LEAF) * (LEAF + 1) + yy % LEAF;
     }
     const int u = ux + nx * uy;
-    double acc = 0.0;
+    T acc = T(0);
     for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p) {
       const int v = d.colind[p];
       const int vx = v % nx, vy = v / nx;
       const bool vsep = ((vx + 1) % (LEAF + 1) == 0) || ((vy + 1) % (LEAF + 1) == 0);
-      if (!vsep) acc += d.val[p] * X[v + (size_t)ld * c];
+      if (!vsep) {
+        T a;
+        if constexpr (sizeof(T) == 4) a = d.fval[p]; else a = d.val[p];
+        acc += a * X[v + (size_t)ld * c];
+      }
     }
     X[u + (size_t)ld * c] -= acc;
   }
@@ -576,29 +699,47 @@ void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
 }
 
 template <typename T, int KUW, int LPB>
-static void leaf_solve_go(const LeafDev& d, double* X, int nrhs, int ld, int bwd, cudaStream_t s) {
+static void leaf_solve_go(const LeafDev& d, T* X, int nrhs, int ld, int bwd, cudaStream_t s) {
   const size_t bufL = (size_t)LPB * (SLOT * SLOT + SLOT), bufU = (size_t)LPB * KUW * KUW;
-  const size_t smem = 2 * sizeof(T) * (bufL > bufU ? bufL : bufU);
-  cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool xpf = !bwd && sizeof(T) == 4;
+  const size_t smem = sizeof(T) * (2 * (bufL > bufU ? bufL : bufU) + (xpf ? (size_t)LPB * SLOT * 2 * SLOT : 0));
+  const int grid = (d.g.nbox() + LPB - 1) / LPB;
   note_launch();
-  leaf_solve_kernel<T, KUW, LPB><<<(d.g.nbox() + LPB - 1) / LPB, LPB * SLOT, smem, s>>>(d, X, nrhs, ld, bwd);
+  if (!bwd) {
+    cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    leaf_solve_kernel<T, KUW, LPB, false><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, ld);
+  } else {
+    cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    leaf_solve_kernel<T, KUW, LPB, true><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, ld);
+  }
 }
 
-void launch_leaf_solve(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s) {
+void launch_leaf_solve(const LeafDev& d, void* Xv, int nrhs, int ld, int bwd, int kumax, cudaStream_t s) {
+  if (bwd && d.fp32 && d.G) {
+    const int smem = (int)(sizeof(float) * (NI * NQ + NQ * GRC));
+    cudaFuncSetAttribute(leaf_bwd_g_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    for (int c0 = 0; c0 < nrhs; c0 += GRC) {
+      const int nc = nrhs - c0 < GRC ? nrhs - c0 : GRC;
+      note_launch();
+      leaf_bwd_g_kernel<<<d.g.nbox(), GTH, smem, s>>>(d, static_cast<float*>(Xv) + (size_t)ld * c0, nc, ld);
+    }
+    return;
+  }
   for (int c0 = 0; c0 < nrhs; c0 += SLOT) {
     const int nc = nrhs - c0 < SLOT ? nrhs - c0 : SLOT;
-    double* Xc = X + (size_t)ld * c0;
     if (d.fp32) {
+      float* Xc = static_cast<float*>(Xv) + (size_t)ld * c0;
       if (kumax <= 15) leaf_solve_go<float, 16, 8>(d, Xc, nc, ld, bwd, s);
       else leaf_solve_go<float, 32, 8>(d, Xc, nc, ld, bwd, s);
     } else {
+      double* Xc = static_cast<double*>(Xv) + (size_t)ld * c0;
       if (kumax <= 15) leaf_solve_go<double, 16, 4>(d, Xc, nc, ld, bwd, s);
       else leaf_solve_go<double, 32, 4>(d, Xc, nc, ld, bwd, s);
     }
   }
 }
 
-void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s) {
+void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, int ld, cudaStream_t s) {
   const int R = (d.ny + 1) / (LEAF + 1) - 1, C = (d.nx + 1) / (LEAF + 1) - 1;
   long long n = ((long long)R * d.nx + (long long)(d.ny - R) * C) * nrhs;
   if (n <= 0) return;
@@ -606,7 +747,8 @@ void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaSt
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
   note_launch();
-  sep_update_fwd_kernel<<<blocks, 256, 0, s>>>(d, X, nrhs, ld);
+  if (d.fp32) sep_update_fwd_kernel<float><<<blocks, 256, 0, s>>>(d, static_cast<float*>(X), nrhs, ld);
+  else sep_update_fwd_kernel<double><<<blocks, 256, 0, s>>>(d, static_cast<double*>(X), nrhs, ld);
 }
 
 }  // namespace spalu

@@ -183,12 +183,15 @@ struct LeafDev {
   void* band;       // [nbox * LDAB * 225] band LU of the leaf interiors (FP64 or FP32)
   void* invd;       // [nbox * 225] reciprocal pivots of U
   void* ybuf;       // [nbox * 225 * 64] intermediate vectors of the band sweeps
+  void* G;          // [nbox * 225 * 60] FP32 A_II^{-1} A_Id per leaf (row-major, column = side
+                    // unknown); set in the mixed path only, where it replaces the backward sweeps
   int* piv;         // [nbox * 225]
   int* kumax;       // largest upper bandwidth of U produced by the interchanges
   int* kur;         // [nbox] upper bandwidth of each leaf's U
   const int* rowptr;
   const int* colind;
   const double* val;
+  const float* fval;  // FP32 copy of val (mixed path)
   int* err;
 };
 
@@ -201,20 +204,21 @@ constexpr int LDAB = 2 * KL + KU + 1;  // band storage rows (LAPACK layout with 
 // Kernels launched by this library in this process (diagnostics, spalu_kernel_launches).
 void note_launch();
 
-// launch helpers (defined in the .cu files)
+// launch helpers (defined in the .cu files).  The solve launchers take the vector in the
+// precision of the factors: float in the mixed path, double otherwise.
 void launch_leaf_factor(const LeafDev& d, cudaStream_t s);
 void launch_level_init_L(const LevelDev& d, cudaStream_t s);
 void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
 void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
 
 cudaError_t leaf_init_tables();
-void launch_leaf_solve(const LeafDev& d, double* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s);
-void launch_sep_update_fwd(const LeafDev& d, double* X, int nrhs, int ld, cudaStream_t s);
+void launch_leaf_solve(const LeafDev& d, void* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s);
+void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, int ld, cudaStream_t s);
 // Capacities for the level-solve kernels from the level maxima {e, kp, |dP|}; false when
 // the right-hand-side blocks alone do not fit in shared memory.
 bool level_solve_caps(const LevelDev& d, const int* lstat, SolveCaps* out);
-void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
-void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, double* X, int nrhs, int ld, cudaStream_t s);
+void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, int ld, cudaStream_t s);
+void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, int ld, cudaStream_t s);
 
 void launch_node_stats(const int* rowptr, const int* colind, const double* val, int n, float4* out,
                        cudaStream_t s);
