@@ -315,6 +315,40 @@ __global__ void convert_kernel(long long n, int nc, const S* src, int lds, D* ds
   }
 }
 
+// Column-major FP64 vectors <-> chunk-interleaved FP32 (chunk k = right-hand sides 16k..16k+15,
+// 16 consecutive values per grid node), through a 64-node x 16-column tile in shared memory so
+// that both sides are read and written in whole sectors.  grid = (ceil(n / 64), chunks).
+constexpr int CT = 64;
+__global__ void __launch_bounds__(256) to_chunked_kernel(int n, int nrhs, const double* B, int ldb, float* xf) {
+  __shared__ float tile[16][CT + 1];
+  const int u0 = blockIdx.x * CT, k = blockIdx.y;
+  for (int i = threadIdx.x; i < 16 * CT; i += 256) {
+    const int cc = i / CT, uu = i % CT, c = 16 * k + cc;
+    tile[cc][uu] = (u0 + uu < n && c < nrhs) ? (float)B[(size_t)(u0 + uu) + (size_t)ldb * c] : 0.f;
+  }
+  __syncthreads();
+  float* dst = xf + ((size_t)k * n + u0) * 16;
+  for (int i = threadIdx.x; i < 16 * CT; i += 256) {
+    const int uu = i / 16, cc = i % 16;
+    if (u0 + uu < n) dst[i] = tile[cc][uu];
+  }
+}
+
+__global__ void __launch_bounds__(256) from_chunked_kernel(int n, int nrhs, const float* xf, double* X, int ldx) {
+  __shared__ float tile[16][CT + 1];
+  const int u0 = blockIdx.x * CT, k = blockIdx.y;
+  const float* src = xf + ((size_t)k * n + u0) * 16;
+  for (int i = threadIdx.x; i < 16 * CT; i += 256) {
+    const int uu = i / 16, cc = i % 16;
+    if (u0 + uu < n) tile[cc][uu] = src[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 16 * CT; i += 256) {
+    const int cc = i / CT, uu = i % CT, c = 16 * k + cc;
+    if (u0 + uu < n && c < nrhs) X[(size_t)(u0 + uu) + (size_t)ldx * c] = (double)tile[cc][uu];
+  }
+}
+
 int grid_for(long long n) {
   long long b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -653,42 +687,45 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
   const int N = f->N;
   PhaseTimer& tm = f->timer;
   int t_all = tm.begin("solve", s);
-  // the mixed path solves on an FP32 copy (ld = N): every kernel of the solve reads and writes
-  // the precision of the factors, and B and X are converted once each
+  // the mixed path solves on an FP32 copy, 16 right-hand sides interleaved per grid node:
+  // every kernel of the solve reads and writes the precision of the factors, a node's values
+  // for one chunk share sectors, and B and X are converted once each
   void* W = X;
-  int ldw = ld;
+  VecLayout lay{1, ld, 16LL * ld};
+  const int nch = (nrhs + 15) / 16;
+  const dim3 cgrid((N + CT - 1) / CT, nch);
   if (f->leaf.fp32) {
-    if (f->xf_cols < nrhs) {
+    if (f->xf_cols < 16 * nch) {
       cudaFree(f->xf);
       f->xf = nullptr;
       f->xf_cols = 0;
-      if (cudaMalloc(&f->xf, sizeof(float) * (size_t)N * nrhs) != cudaSuccess) return SPALU_ERR_ALLOC;
-      f->xf_cols = nrhs;
+      if (cudaMalloc(&f->xf, sizeof(float) * (size_t)N * 16 * nch) != cudaSuccess) return SPALU_ERR_ALLOC;
+      f->xf_cols = 16 * nch;
     }
     note_launch();
-    convert_kernel<double, float><<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, B, ld, f->xf, N);
+    to_chunked_kernel<<<cgrid, 256, 0, s>>>(N, nrhs, B, ld, f->xf);
     W = f->xf;
-    ldw = N;
+    lay = VecLayout{16, 1, 16LL * N};
   } else if (X != B) {
     CUDA_TRY(cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), B, (size_t)ld * sizeof(double),
                                (size_t)N * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
   }
   int t = tm.begin("leaf_solve_fwd", s);
-  launch_leaf_solve(f->leaf, W, nrhs, ldw, 0, f->kumax, s);
+  launch_leaf_solve(f->leaf, W, nrhs, lay, 0, f->kumax, s);
   tm.end(t, s);
   t = tm.begin("sep_update", s);
-  if (L >= 1) launch_sep_update_fwd(f->leaf, W, nrhs, ldw, s);
+  if (L >= 1) launch_sep_update_fwd(f->leaf, W, nrhs, lay, s);
   tm.end(t, s);
   t = tm.begin("level_solve", s);
-  for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], f->caps[l], W, nrhs, ldw, s);
-  for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], f->caps[l], W, nrhs, ldw, s);
+  for (int l = L; l >= 1; --l) launch_level_solve_fwd(f->lev[l], f->caps[l], W, nrhs, lay, s);
+  for (int l = 1; l <= L; ++l) launch_level_solve_bwd(f->lev[l], f->caps[l], W, nrhs, lay, s);
   tm.end(t, s);
   t = tm.begin("leaf_solve_bwd", s);
-  launch_leaf_solve(f->leaf, W, nrhs, ldw, 1, f->kumax, s);
+  launch_leaf_solve(f->leaf, W, nrhs, lay, 1, f->kumax, s);
   tm.end(t, s);
   if (f->leaf.fp32) {
     note_launch();
-    convert_kernel<float, double><<<grid_for((long long)N * nrhs), 256, 0, s>>>(N, nrhs, f->xf, N, X, ld);
+    from_chunked_kernel<<<cgrid, 256, 0, s>>>(N, nrhs, f->xf, X, ld);
   }
   tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());

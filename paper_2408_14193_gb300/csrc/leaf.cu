@@ -378,7 +378,7 @@ __device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
 // right-hand-side rows one block ahead (the FP64 variant loads them directly: its shared
 // memory would otherwise cost resident CTAs).
 template <typename T, int KUW, int LPB, bool bwd>
-__global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X, int nrhs, int ld) {
+__global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) {
   extern __shared__ double lsm[];
   constexpr int NT = LPB * SLOT;
   constexpr int LST = SLOT * SLOT;                    // L stage per leaf: 16 columns x 16 (L(j+r, j) at r - 1)
@@ -400,8 +400,10 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
   T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)bb * NI * QL;
-  T* Xc = X + (size_t)ld * c;
+  T* Xc = X + (size_t)c * lay.cs;
+  const long long rs = lay.rs;
   auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
+  auto xat = [&](int node) -> T& { return Xc[(size_t)(node * rs)]; };
   constexpr bool XPF = !bwd && sizeof(T) == 4;       // stage the right-hand-side rows
   T* xst = stg + 2 * bufsz + (size_t)threadIdx.x * 2 * SLOT;   // own rows, 2 x 16
 
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
       int lx = j % LEAF, node = node_of(j);
 #pragma unroll
       for (int u = 0; u < SLOT; ++u, ++j) {
-        if (j < NI) cp_async_t(xs + u, Xc + node);
+        if (j < NI) cp_async_t(xs + u, &xat(node));
         if (++lx == LEAF) { lx = 0; node += nx - (LEAF - 1); } else ++node;
       }
     }
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
   if (active) {
     if (!bwd) {
 #pragma unroll
-      for (int r = 0; r < 16; ++r) W[r] = Xc[node_of(r)];
+      for (int r = 0; r < 16; ++r) W[r] = xat(node_of(r));
     } else {
 #pragma unroll
       for (int r = 0; r < 16; ++r) W[r] = T(0);
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
       for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
         const int cc = d.colind[p];
         const int cx = cc % nx - x0, cy = cc / nx - y0;
-        if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)d.val[p] * Xc[cc];
+        if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)d.val[p] * xat(cc);
       }
     }
     return v;
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
           T nv = T(0);
           if (j + 16 < NI) {
             if constexpr (XPF) nv = xs[u];
-            else if constexpr (!bwd) nv = Xc[node_of(j + 16)];
+            else if constexpr (!bwd) nv = xat(node_of(j + 16));
             else nv = coupling(j + 16);
           }
           W[u] = nv;
@@ -545,8 +547,8 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
           T uv[KUW];
           lds_vec(S + u * KUW, uv);
           const T x = V[u] * uv[0];
-          if (!bwd) Xc[node_of(j)] = x;
-          else Xc[node_of(j)] -= x;
+          if (!bwd) xat(node_of(j)) = x;
+          else xat(node_of(j)) -= x;
 #pragma unroll
           for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= uv[r] * x;
           V[u] = (j - KUW >= 0) ? yb[(size_t)(j - KUW) * QL + c] : T(0);
@@ -568,7 +570,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
 
-__global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X, int nrhs, int ld) {
+__global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X, int nrhs, VecLayout lay) {
   extern __shared__ float4 gsm4[];
   float* Gs = reinterpret_cast<float*>(gsm4);    // NI x NQ
   float* xd = Gs + NI * NQ;                      // NQ x GRC
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X,
     int vx, vy, m;
     side_unknown(q, x0, y0, &vx, &vy, &m);
     const bool ex = c < nrhs && vx >= 0 && vx < nx && vy >= 0 && vy < d.ny;
-    xd[i] = ex ? X[(vx + nx * vy) + (size_t)ld * c] : 0.f;
+    xd[i] = ex ? X[lay.at(vx + nx * vy, c)] : 0.f;
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -611,10 +613,10 @@ __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X,
       }
     }
   }
-  const size_t node = (size_t)(x0 + j % LEAF) + (size_t)nx * (y0 + j / LEAF);
+  const int node = (x0 + j % LEAF) + nx * (y0 + j / LEAF);
 #pragma unroll
   for (int c = 0; c < GRC; ++c)
-    if (c < nrhs) X[node + (size_t)ld * c] -= acc[c];
+    if (c < nrhs) X[lay.at(node, c)] -= acc[c];
 }
 
 // b_u -= sum over interior neighbours j of A_uj t_j, for every separator node u.  One thread
@@ -622,15 +624,17 @@ __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X,
 // R full separator rows (y = 16 r + 15) first, then the C separator columns (x = 16 q + 15) of
 // the remaining rows.
 template <typename T>
-__global__ void sep_update_fwd_kernel(LeafDev d, T* X, int nrhs, int ld) {
+__global__ void sep_update_fwd_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) {
   const int nx = d.nx, ny = d.ny;
   const int R = (ny + 1) / (LEAF + 1) - 1, C = (nx + 1) / (LEAF + 1) - 1;
   const long long nrow = (long long)R * nx;
   const long long nsep = nrow + (long long)(ny - R) * C;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nsep * nrhs;
        e += (long long)gridDim.x * blockDim.x) {
-    const long long sidx = e % nsep;
-    const int c = (int)(e / nsep);
+    // consecutive threads: consecutive nodes (column-major vectors) or right-hand sides
+    const bool cin = lay.cs == 1;
+    const long long sidx = cin ? e / nrhs : e % nsep;
+    const int c = (int)(cin ? e % nrhs : e / nsep);
     int ux, uy;
     if (sidx < nrow) {
       uy = (int)(sidx / nx) * (LEAF + 1) + LEAF;
@@ -650,10 +654,10 @@ __global__ void sep_update_fwd_kernel(LeafDev d, T* X, int nrhs, int ld) {
       if (!vsep) {
         T a;
         if constexpr (sizeof(T) == 4) a = d.fval[p]; else a = d.val[p];
-        acc += a * X[v + (size_t)ld * c];
+        acc += a * X[lay.atc(v, c)];
       }
     }
-    X[u + (size_t)ld * c] -= acc;
+    X[lay.atc(u, c)] -= acc;
   }
 }
 
@@ -699,7 +703,7 @@ void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
 }
 
 template <typename T, int KUW, int LPB>
-static void leaf_solve_go(const LeafDev& d, T* X, int nrhs, int ld, int bwd, cudaStream_t s) {
+static void leaf_solve_go(const LeafDev& d, T* X, int nrhs, VecLayout lay, int bwd, cudaStream_t s) {
   const size_t bufL = (size_t)LPB * (SLOT * SLOT + SLOT), bufU = (size_t)LPB * KUW * KUW;
   const bool xpf = !bwd && sizeof(T) == 4;
   const size_t smem = sizeof(T) * (2 * (bufL > bufU ? bufL : bufU) + (xpf ? (size_t)LPB * SLOT * 2 * SLOT : 0));
@@ -707,39 +711,39 @@ static void leaf_solve_go(const LeafDev& d, T* X, int nrhs, int ld, int bwd, cud
   note_launch();
   if (!bwd) {
     cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    leaf_solve_kernel<T, KUW, LPB, false><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, ld);
+    leaf_solve_kernel<T, KUW, LPB, false><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, lay);
   } else {
     cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    leaf_solve_kernel<T, KUW, LPB, true><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, ld);
+    leaf_solve_kernel<T, KUW, LPB, true><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, lay);
   }
 }
 
-void launch_leaf_solve(const LeafDev& d, void* Xv, int nrhs, int ld, int bwd, int kumax, cudaStream_t s) {
+void launch_leaf_solve(const LeafDev& d, void* Xv, int nrhs, VecLayout lay, int bwd, int kumax, cudaStream_t s) {
   if (bwd && d.fp32 && d.G) {
     const int smem = (int)(sizeof(float) * (NI * NQ + NQ * GRC));
     cudaFuncSetAttribute(leaf_bwd_g_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     for (int c0 = 0; c0 < nrhs; c0 += GRC) {
       const int nc = nrhs - c0 < GRC ? nrhs - c0 : GRC;
       note_launch();
-      leaf_bwd_g_kernel<<<d.g.nbox(), GTH, smem, s>>>(d, static_cast<float*>(Xv) + (size_t)ld * c0, nc, ld);
+      leaf_bwd_g_kernel<<<d.g.nbox(), GTH, smem, s>>>(d, static_cast<float*>(Xv) + (size_t)(c0 / GRC) * lay.chunk, nc, lay);
     }
     return;
   }
   for (int c0 = 0; c0 < nrhs; c0 += SLOT) {
     const int nc = nrhs - c0 < SLOT ? nrhs - c0 : SLOT;
     if (d.fp32) {
-      float* Xc = static_cast<float*>(Xv) + (size_t)ld * c0;
-      if (kumax <= 15) leaf_solve_go<float, 16, 8>(d, Xc, nc, ld, bwd, s);
-      else leaf_solve_go<float, 32, 8>(d, Xc, nc, ld, bwd, s);
+      float* Xc = static_cast<float*>(Xv) + (size_t)(c0 / SLOT) * lay.chunk;
+      if (kumax <= 15) leaf_solve_go<float, 16, 8>(d, Xc, nc, lay, bwd, s);
+      else leaf_solve_go<float, 32, 8>(d, Xc, nc, lay, bwd, s);
     } else {
-      double* Xc = static_cast<double*>(Xv) + (size_t)ld * c0;
-      if (kumax <= 15) leaf_solve_go<double, 16, 4>(d, Xc, nc, ld, bwd, s);
-      else leaf_solve_go<double, 32, 4>(d, Xc, nc, ld, bwd, s);
+      double* Xc = static_cast<double*>(Xv) + (size_t)(c0 / SLOT) * lay.chunk;
+      if (kumax <= 15) leaf_solve_go<double, 16, 4>(d, Xc, nc, lay, bwd, s);
+      else leaf_solve_go<double, 32, 4>(d, Xc, nc, lay, bwd, s);
     }
   }
 }
 
-void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, int ld, cudaStream_t s) {
+void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, VecLayout lay, cudaStream_t s) {
   const int R = (d.ny + 1) / (LEAF + 1) - 1, C = (d.nx + 1) / (LEAF + 1) - 1;
   long long n = ((long long)R * d.nx + (long long)(d.ny - R) * C) * nrhs;
   if (n <= 0) return;
@@ -747,8 +751,8 @@ void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, int ld, cudaStre
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
   note_launch();
-  if (d.fp32) sep_update_fwd_kernel<float><<<blocks, 256, 0, s>>>(d, static_cast<float*>(X), nrhs, ld);
-  else sep_update_fwd_kernel<double><<<blocks, 256, 0, s>>>(d, static_cast<double*>(X), nrhs, ld);
+  if (d.fp32) sep_update_fwd_kernel<float><<<blocks, 256, 0, s>>>(d, static_cast<float*>(X), nrhs, lay);
+  else sep_update_fwd_kernel<double><<<blocks, 256, 0, s>>>(d, static_cast<double*>(X), nrhs, lay);
 }
 
 }  // namespace spalu

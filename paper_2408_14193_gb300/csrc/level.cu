@@ -1403,7 +1403,7 @@ __device__ __forceinline__ void gather_panel(T* dst, int nr, int ncl, const T* s
 // Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
 template <typename T>
-__global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, int ld, int bwd) {
+__global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
   extern __shared__ double smd[];
   const int sid = blockIdx.x;
   const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
@@ -1424,7 +1424,7 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
   const T* inv = static_cast<const T*>(d.Dinv) + (size_t)sid * capS;
   for (int x = threadIdx.x; x < e * SC; x += blockDim.x) {
     int a = x % e, c = x / e;
-    v[x] = c < nc ? X[snodes[a] + (size_t)ld * c] : T(0);
+    v[x] = c < nc ? X[lay.at(snodes[a], c)] : T(0);
   }
   if (staged) {
     for (int x = threadIdx.x; x < r * r; x += blockDim.x)
@@ -1484,7 +1484,7 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
   __syncthreads();
   for (int x = threadIdx.x; x < e * nc; x += blockDim.x) {
     int a = x % e, c = x / e;
-    X[snodes[a] + (size_t)ld * c] = v[x];
+    X[lay.at(snodes[a], c)] = v[x];
   }
 }
 
@@ -1492,7 +1492,7 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
 // (a boundary unknown is shared by up to four parents; the order of their contributions is
 // not fixed); backward x_p = U^{-1} (y_p - W x_dP).
 template <typename T>
-__global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, int ld, int bwd) {
+__global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
   extern __shared__ double smd[];
   const int P = blockIdx.x;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
@@ -1525,7 +1525,7 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
   auto rownode = [&](int a) { return dstage ? rows_sm[cap.drows + a] : tab[(size_t)a * TABW + 7]; };
   for (int x = threadIdx.x; x < kp * SC; x += blockDim.x) {
     int a = x % kp, c = x / kp;
-    y[x] = c < nc ? X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] : T(0);
+    y[x] = c < nc ? X[lay.at(tab[(size_t)(ndP + a) * TABW + 7], c)] : T(0);
   }
   if (staged) for (int x = threadIdx.x; x < kp; x += blockDim.x) { invs[x] = inv[x]; pivs[x] = piv[x]; }
   const size_t ldl = staged ? (size_t)kp : ldp;
@@ -1548,12 +1548,12 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
     gemv_pairs<T>(ndP, kp,
                   [&](int a) { return pstaged ? U + a : M + rowpos(a) + ldp * Dp; },
                   pstaged ? (size_t)ndP : ldp, y, kp, nc,
-                  [&](int a, int c, T acc) { atomicAdd(X + rownode(a) + (size_t)ld * c, -acc); });
+                  [&](int a, int c, T acc) { atomicAdd(X + lay.at(rownode(a), c), -acc); });
   } else {
     if (dstage) {
       for (int x = threadIdx.x; x < ndP * SC; x += blockDim.x) {
         int b = x % ndP, c = x / ndP;
-        xd[x] = c < nc ? X[rows_sm[cap.drows + b] + (size_t)ld * c] : T(0);
+        xd[x] = c < nc ? X[lay.at(rows_sm[cap.drows + b], c)] : T(0);
       }
     }
     T* Wt = U;                                            // W^T panel, pitch ldw
@@ -1576,7 +1576,7 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
         const T* xc = xd + (size_t)ndP * c;
         for (int b = 0; b < ndP; ++b) acc += M[(Dp + a) + ldp * rows_sm[b]] * xc[b];
       } else {
-        for (int b = 0; b < ndP; ++b) acc += M[(Dp + a) + ldp * rowpos(b)] * X[rownode(b) + (size_t)ld * c];
+        for (int b = 0; b < ndP; ++b) acc += M[(Dp + a) + ldp * rowpos(b)] * X[lay.at(rownode(b), c)];
       }
       y[a + kp * c] -= acc;
     }
@@ -1588,7 +1588,7 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
   __syncthreads();
   for (int x = threadIdx.x; x < kp * nc; x += blockDim.x) {
     int a = x % kp, c = x / kp;
-    X[tab[(size_t)(ndP + a) * TABW + 7] + (size_t)ld * c] = y[x];
+    X[lay.at(tab[(size_t)(ndP + a) * TABW + 7], c)] = y[x];
   }
 }
 
@@ -1703,19 +1703,19 @@ bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
 }
 
 template <typename T>
-static void level_solve(const LevelDev& d, const SolveCaps& sc, T* X, int nrhs, int ld, int bwd, cudaStream_t s) {
+static void level_solve(const LevelDev& d, const SolveCaps& sc, T* X, int nrhs, VecLayout lay, int bwd, cudaStream_t s) {
   cudaFuncSetAttribute(seg_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.seg_smem);
   cudaFuncSetAttribute(sep_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.sep_smem);
   for (int c0 = 0; c0 < nrhs; c0 += SC) {
     const int nc = nrhs - c0 < SC ? nrhs - c0 : SC;
-    T* Xc = X + (size_t)ld * c0;
+    T* Xc = X + (size_t)(c0 / SC) * lay.chunk;
     auto seg_go = [&](int dir) {
       note_launch();
-      seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, ld, dir);
+      seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, lay, dir);
     };
     auto sep_go = [&](int dir) {
       note_launch();
-      sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, ld, dir);
+      sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, lay, dir);
     };
     if (!bwd) {
       if (d.g.nseg() > 0) seg_go(0);
@@ -1727,14 +1727,14 @@ static void level_solve(const LevelDev& d, const SolveCaps& sc, T* X, int nrhs, 
   }
 }
 
-void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, int ld, cudaStream_t s) {
-  if (d.fp32) level_solve<float>(d, c, static_cast<float*>(X), nrhs, ld, 0, s);
-  else level_solve<double>(d, c, static_cast<double*>(X), nrhs, ld, 0, s);
+void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, VecLayout lay, cudaStream_t s) {
+  if (d.fp32) level_solve<float>(d, c, static_cast<float*>(X), nrhs, lay, 0, s);
+  else level_solve<double>(d, c, static_cast<double*>(X), nrhs, lay, 0, s);
 }
 
-void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, int ld, cudaStream_t s) {
-  if (d.fp32) level_solve<float>(d, c, static_cast<float*>(X), nrhs, ld, 1, s);
-  else level_solve<double>(d, c, static_cast<double*>(X), nrhs, ld, 1, s);
+void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, VecLayout lay, cudaStream_t s) {
+  if (d.fp32) level_solve<float>(d, c, static_cast<float*>(X), nrhs, lay, 1, s);
+  else level_solve<double>(d, c, static_cast<double*>(X), nrhs, lay, 1, s);
 }
 
 }  // namespace spalu

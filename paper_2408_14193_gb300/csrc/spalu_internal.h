@@ -204,6 +204,18 @@ constexpr int LDAB = 2 * KL + KU + 1;  // band storage rows (LAPACK layout with 
 // Kernels launched by this library in this process (diagnostics, spalu_kernel_launches).
 void note_launch();
 
+// Placement of a solve vector: element (grid node u, right-hand side c) at X[u * rs + c * cs];
+// the solve kernels take the right-hand sides in chunks of 16, chunk k at X + k * chunk.
+// Column-major (ld): {1, ld, 16 ld}; chunk-interleaved (16 values per node): {16, 1, 16 N}.
+struct VecLayout {
+  long long rs, cs, chunk;
+  __host__ __device__ __forceinline__ size_t at(int u, int c) const { return (size_t)(u * rs + c * cs); }
+  // any right-hand side c (chunk c / 16, position c % 16 in it)
+  __host__ __device__ __forceinline__ size_t atc(int u, int c) const {
+    return (size_t)((c >> 4) * chunk + u * rs + (c & 15) * cs);
+  }
+};
+
 // launch helpers (defined in the .cu files).  The solve launchers take the vector in the
 // precision of the factors: float in the mixed path, double otherwise.
 void launch_leaf_factor(const LeafDev& d, cudaStream_t s);
@@ -212,13 +224,13 @@ void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
 void launch_merge(const LevelDev& d, const LevelPlan& p, cudaStream_t s);
 
 cudaError_t leaf_init_tables();
-void launch_leaf_solve(const LeafDev& d, void* X, int nrhs, int ld, int bwd, int kumax, cudaStream_t s);
-void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, int ld, cudaStream_t s);
+void launch_leaf_solve(const LeafDev& d, void* X, int nrhs, VecLayout lay, int bwd, int kumax, cudaStream_t s);
+void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, VecLayout lay, cudaStream_t s);
 // Capacities for the level-solve kernels from the level maxima {e, kp, |dP|}; false when
 // the right-hand-side blocks alone do not fit in shared memory.
 bool level_solve_caps(const LevelDev& d, const int* lstat, SolveCaps* out);
-void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, int ld, cudaStream_t s);
-void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, int ld, cudaStream_t s);
+void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, VecLayout lay, cudaStream_t s);
+void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, VecLayout lay, cudaStream_t s);
 
 void launch_node_stats(const int* rowptr, const int* colind, const double* val, int n, float4* out,
                        cudaStream_t s);
