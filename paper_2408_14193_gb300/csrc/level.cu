@@ -1390,6 +1390,83 @@ __device__ __forceinline__ void upper_sweep(T* y, int ldy, int n, const T* LU, s
 }
 
 
+// Triangular blocks of order up to INV_MAX are inverted after the factorization (factor
+// kernels below), so that the solve applies them as one product per right-hand side instead of
+// a sequential sweep: [L\U] becomes [L~^{-1}\U^{-1}] with L~ the multipliers after all later
+// interchanges, and the pivot sequence becomes the permutation q, (P b)_i = b_{q_i}.
+constexpr int INV_MAX = 64;
+
+// v[:, c] = L~^{-1} v[q, c] (lower) or U^{-1} v[:, c] (upper) for c < nc, n <= INV_MAX, A the
+// inverted block (ld lda) in shared or global memory.  256 threads, at most 4 outputs each.
+template <typename T, bool LOWER>
+__device__ __forceinline__ void tri_apply(T* v, int ldv, int n, const T* A, size_t lda, const int* q, int nc) {
+  T acc[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int x = threadIdx.x + 256 * t;
+    acc[t] = T(0);
+    if (x < n * nc) {
+      const int i = x % n, c = x / n;
+      const T* vc = v + (size_t)ldv * c;
+      T s;
+      if constexpr (LOWER) {
+        s = vc[q[i]];
+        for (int k = 0; k < i; ++k) s += A[i + lda * k] * vc[q[k]];
+      } else {
+        s = T(0);
+        for (int k = i; k < n; ++k) s += A[i + lda * k] * vc[k];
+      }
+      acc[t] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int x = threadIdx.x + 256 * t;
+    if (x < n * nc) v[(x % n) + (size_t)ldv * (x / n)] = acc[t];
+  }
+  __syncthreads();
+}
+
+// In place on one GEPP block (n <= INV_MAX, column-major, ld lda; interchanges not applied to
+// earlier multipliers; rinv the reciprocal pivots): thread j moves column j's multipliers
+// through the later interchanges, then forms column j of L~^{-1} (below the diagonal) and of
+// U^{-1} (on and above it) from a shared-memory copy.  S and X: n * n each; q: n.
+template <typename T>
+__device__ void invert_lu_block(T* A, size_t lda, int n, const T* rinv, int* piv, T* S, T* X, int* q) {
+  for (int x = threadIdx.x; x < n * n; x += blockDim.x) S[x] = A[(x % n) + lda * (x / n)];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) q[i] = i;
+    for (int j = 0; j < n; ++j) { const int p = piv[j], t = q[j]; q[j] = q[p]; q[p] = t; }
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    T* sc = S + (size_t)n * j;
+    for (int t = j + 1; t < n; ++t) {
+      const int p = piv[t];
+      if (p != t) { const T a = sc[t]; sc[t] = sc[p]; sc[p] = a; }
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    T* xc = X + (size_t)n * j;
+    for (int i = j + 1; i < n; ++i) {          // L~ x = e_j (unit diagonal)
+      T s = S[i + (size_t)n * j];
+      for (int m = j + 1; m < i; ++m) s += S[i + (size_t)n * m] * xc[m];
+      xc[i] = -s;
+    }
+    xc[j] = rinv[j];                           // U x = e_j
+    for (int i = j - 1; i >= 0; --i) {
+      T s = T(0);
+      for (int m = i + 1; m <= j; ++m) s += S[i + (size_t)n * m] * xc[m];
+      xc[i] = -s * rinv[i];
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < n * n; x += blockDim.x) A[(x % n) + lda * (x / n)] = X[x];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) piv[i] = q[i];
+}
+
 template <typename T>
 __device__ __forceinline__ void gather_panel(T* dst, int nr, int ncl, const T* src, size_t ldsrc,
                                              const int* rowidx, size_t colbase) {
@@ -1399,6 +1476,42 @@ __device__ __forceinline__ void gather_panel(T* dst, int nr, int ncl, const T* s
     dst[x] = src[(size_t)rowidx[i] + ldsrc * (colbase + j)];
   }
 }
+
+// Inverse of each segment's remainder block (after the level's sparsification).
+template <typename T>
+__global__ void __launch_bounds__(64) seg_invert_kernel(LevelDev d) {
+  extern __shared__ double ism[];
+  const int sid = blockIdx.x;
+  const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
+  if (r <= 0 || r > INV_MAX) return;
+  const size_t capS = d.capS;
+  T* S = reinterpret_cast<T*>(ism);
+  T* X = S + (size_t)r * r;
+  int* q = reinterpret_cast<int*>(X + (size_t)r * r);
+  T* Dg = static_cast<T*>(d.Dm) + (size_t)sid * capS * capS;
+  invert_lu_block<T>(Dg + k + capS * k, capS, r, static_cast<const T*>(d.Dinv) + (size_t)sid * capS,
+                     d.piv + (size_t)sid * capS, S, X, q);
+}
+
+// Inverse of each parent's separator block (after its elimination in the merge).
+template <typename T>
+__global__ void __launch_bounds__(64) sep_invert_kernel(LevelDev d) {
+  extern __shared__ double ism[];
+  const int P = blockIdx.x;
+  const int kp = d.pcount[2 * P + 1];
+  if (kp <= 0 || kp > INV_MAX) return;
+  const size_t ldp = d.ldFp;
+  const int Dp = d.gp.D();
+  T* S = reinterpret_cast<T*>(ism);
+  T* X = S + (size_t)kp * kp;
+  int* q = reinterpret_cast<int*>(X + (size_t)kp * kp);
+  T* M = static_cast<T*>(d.Fp) + (size_t)P * ldp * ldp;
+  invert_lu_block<T>(M + Dp + ldp * Dp, ldp, kp, static_cast<const T*>(d.Pinv) + (size_t)P * d.sepcap,
+                     d.ppiv + (size_t)P * d.sepcap, S, X, q);
+}
+
+template <typename T>
+size_t invert_smem() { return 2 * sizeof(T) * INV_MAX * INV_MAX + sizeof(int) * INV_MAX; }
 
 // Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
@@ -1458,7 +1571,8 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
                     [&](int a, int c, T acc) { vr[a + e * c] -= acc; });
       __syncthreads();
     }
-    lower_sweep<T>(vr, e, r, LUs, ldl, pvs, nc);
+    if (r <= INV_MAX) tri_apply<T, true>(vr, e, r, LUs, ldl, pvs, nc);
+    else lower_sweep<T>(vr, e, r, LUs, ldl, pvs, nc);
     __syncthreads();
     if (k > 0) {      // b_s -= Z y_r
       const T* Zp = pstaged ? Ps : Dg + (size_t)capS * k;
@@ -1474,7 +1588,8 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
                     [&](int a, int c, T acc) { vr[a + e * c] -= acc; });
       __syncthreads();
     }
-    upper_sweep<T>(vr, e, r, LUs, ldl, ivs, nc);
+    if (r <= INV_MAX) tri_apply<T, false>(vr, e, r, LUs, ldl, pvs, nc);
+    else upper_sweep<T>(vr, e, r, LUs, ldl, ivs, nc);
     __syncthreads();
     if (k > 0) {      // x_s -= T x_r
       gemv_pairs<T>(k, r, [&](int a) { return Tp + a; }, ldt, vr, e, nc,
@@ -1538,7 +1653,8 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
   if (!bwd) stage_lu();
   __syncthreads();          // rows_sm, y (and the LU block) are read by other threads below
   if (!bwd) {
-    lower_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
+    if (kp <= INV_MAX) tri_apply<T, true>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
+    else lower_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
     __syncthreads();
     // b_dP -= Z y_p, Z = M[dP rows, separator columns]
     if (pstaged) {
@@ -1583,7 +1699,8 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
     __syncthreads();
     stage_lu();             // the panel is consumed: U takes the LU block
     __syncthreads();
-    upper_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, ivs, nc);
+    if (kp <= INV_MAX) tri_apply<T, false>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
+    else upper_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, ivs, nc);
   }
   __syncthreads();
   for (int x = threadIdx.x; x < kp * nc; x += blockDim.x) {
@@ -1629,6 +1746,10 @@ static void sparsify_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t 
     cudaFuncSetAttribute(sparsify_kernel<T, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     sparsify_kernel<T, NW><<<d.g.nseg(), NW * 32, smem, s>>>(d, smem);
   }
+  const int ism = (int)invert_smem<T>();
+  cudaFuncSetAttribute(seg_invert_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ism);
+  note_launch();
+  seg_invert_kernel<T><<<d.g.nseg(), 64, ism, s>>>(d);
 }
 
 void launch_sparsify(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
@@ -1652,6 +1773,12 @@ static void merge_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) 
   }
   note_launch();
   merge_panel_kernel<T><<<np, 256, 0, s>>>(d);
+  {
+    const int ism = (int)invert_smem<T>();
+    cudaFuncSetAttribute(sep_invert_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ism);
+    note_launch();
+    sep_invert_kernel<T><<<np, 64, ism, s>>>(d);
+  }
   {
     int tiles = (p.ldFp + 63) / 64;
     dim3 grid(tiles, tiles, np);
