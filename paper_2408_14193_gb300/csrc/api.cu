@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int*
                                                   const double* b, int ldb, double* y, int ldy,
                                                   const double* d, int ldd, double* part,
                                                   unsigned* cnt, double* out, int sq) {
+  pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
   double s[RC];
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int*
 __global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const double* h, const double* p, int ldp,
                                                  double* w, int ldw, const double* q, int ldq,
                                                  double* part, unsigned* cnt, double* out, int sq) {
+  pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
   double s[RC], hc[RC];
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const doubl
 // X_c += sum_i y[i][c] Z_i,c for i = 0..k-1, in that order (Z_i = Z + i * ldz * nrhs)
 __global__ void __launch_bounds__(VB, 4) combine_kernel(int n, int nrhs, int k, const double* y,
                                                      const double* Z, size_t ldz, double* X, int ldx) {
+  pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
   for (long long r = blockIdx.x * (long long)VB + threadIdx.x; r < n; r += (long long)gridDim.x * VB) {
@@ -296,6 +299,7 @@ __global__ void __launch_bounds__(VB, 4) combine_kernel(int n, int nrhs, int k, 
 // y[:, c] = x[:, c] / s[c] (zero when s[c] == 0); blockIdx.y = column, one reciprocal per thread
 __global__ void scale_kernel(int n, int nrhs, const double* s, const double* x, int ldx, double* y,
                              int ldy) {
+  pdl_enter();
   const int c = blockIdx.y;
   const double d = s[c];
   const double di = d != 0.0 ? 1.0 / d : 0.0;
@@ -320,6 +324,7 @@ __global__ void convert_kernel(long long n, int nc, const S* src, int lds, D* ds
 // that both sides are read and written in whole sectors.  grid = (ceil(n / 64), chunks).
 constexpr int CT = 64;
 __global__ void __launch_bounds__(256) to_chunked_kernel(int n, int nrhs, const double* B, int ldb, float* xf) {
+  pdl_enter();
   __shared__ float tile[16][CT + 1];
   const int u0 = blockIdx.x * CT, k = blockIdx.y;
   for (int i = threadIdx.x; i < 16 * CT; i += 256) {
@@ -335,6 +340,7 @@ __global__ void __launch_bounds__(256) to_chunked_kernel(int n, int nrhs, const 
 }
 
 __global__ void __launch_bounds__(256) from_chunked_kernel(int n, int nrhs, const float* xf, double* X, int ldx) {
+  pdl_enter();
   __shared__ float tile[16][CT + 1];
   const int u0 = blockIdx.x * CT, k = blockIdx.y;
   const float* src = xf + ((size_t)k * n + u0) * 16;
@@ -703,7 +709,7 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
       f->xf_cols = 16 * nch;
     }
     note_launch();
-    to_chunked_kernel<<<cgrid, 256, 0, s>>>(N, nrhs, B, ld, f->xf);
+    launch_pdl(to_chunked_kernel, cgrid, dim3(256), 0, s, N, nrhs, B, ld, f->xf);
     W = f->xf;
     lay = VecLayout{16, 1, 16LL * N};
   } else if (X != B) {
@@ -725,7 +731,7 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
   tm.end(t, s);
   if (f->leaf.fp32) {
     note_launch();
-    from_chunked_kernel<<<cgrid, 256, 0, s>>>(N, nrhs, f->xf, X, ld);
+    launch_pdl(from_chunked_kernel, cgrid, dim3(256), 0, s, N, nrhs, (const float*)f->xf, X, ld);
   }
   tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());
@@ -774,17 +780,16 @@ static dim3 vec_grid(int n, int nrhs) {
 static void vec_mgs(spalu_factor_t f, int nrhs, const double* h, const double* p, int ldp, double* w,
                     int ldw, const double* q, int ldq, double* out, int sq, cudaStream_t s) {
   note_launch();
-  mgs_kernel<<<vec_grid(f->N, nrhs), VB, 0, s>>>(f->N, nrhs, h, p, ldp, w, ldw, q, ldq, f->gw.part,
-                                                 f->gw.cnt, out, sq);
+  launch_pdl(mgs_kernel, vec_grid(f->N, nrhs), dim3(VB), 0, s, f->N, nrhs, h, p, ldp, w, ldw, q, ldq,
+             f->gw.part, f->gw.cnt, out, sq);
 }
 
 // y = b - A x (b null: A x); out set: out[c] = <y_c, d_c> (d null: ||y_c||, sq)
 static void vec_spmv(spalu_factor_t f, int nrhs, const double* x, int ldx, const double* b, int ldb,
                      double* y, int ldy, const double* d, int ldd, double* out, int sq, cudaStream_t s) {
   note_launch();
-  spmv_kernel<<<vec_grid(f->N, nrhs), VB, 0, s>>>(f->N, nrhs, f->rowptr, f->colind, f->val, x, ldx, b, ldb,
-                                                  y, ldy, d, ldd, out ? f->gw.part : nullptr, f->gw.cnt,
-                                                  out, sq);
+  launch_pdl(spmv_kernel, vec_grid(f->N, nrhs), dim3(VB), 0, s, f->N, nrhs, f->rowptr, f->colind, f->val, x,
+             ldx, b, ldb, y, ldy, d, ldd, out ? f->gw.part : nullptr, f->gw.cnt, out, sq);
 }
 
 static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
@@ -840,7 +845,8 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     for (int c = 0; c < nrhs; ++c) bsc[c] = done(c) ? 0.0 : beta[c];
     CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, bsc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     note_launch();
-    scale_kernel<<<dim3(grid_for(N) / nrhs + 1, nrhs), 256, 0, s>>>(N, nrhs, dvec + nrhs, w.R, (int)ldv, Vj(0), (int)ldv);
+    launch_pdl(scale_kernel, dim3(grid_for(N) / nrhs + 1, nrhs), dim3(256), 0, s, N, nrhs, (const double*)(dvec + nrhs),
+               (const double*)w.R, (int)ldv, Vj(0), (int)ldv);
     for (int c = 0; c < nrhs; ++c) {
       std::fill(H[c].begin(), H[c].end(), 0.0);
       std::fill(g[c].begin(), g[c].end(), 0.0);
@@ -857,7 +863,8 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
         vec_mgs(f, nrhs, w.hcol + (size_t)(i - 1) * nrhs, Vj(i - 1), (int)ldv, Vj(j + 1), (int)ldv,
                 i <= j ? Vj(i) : nullptr, (int)ldv, w.hcol + (size_t)i * nrhs, i > j, s);
       note_launch();
-      scale_kernel<<<dim3(grid_for(N) / nrhs + 1, nrhs), 256, 0, s>>>(N, nrhs, w.hcol + (size_t)(j + 1) * nrhs, Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
+      launch_pdl(scale_kernel, dim3(grid_for(N) / nrhs + 1, nrhs), dim3(256), 0, s, N, nrhs,
+                 (const double*)(w.hcol + (size_t)(j + 1) * nrhs), (const double*)Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
       CUDA_TRY(cudaMemcpyAsync(hh.data(), w.hcol, sizeof(double) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
       ++it;
@@ -897,7 +904,8 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     // X += M^{-1} V y = sum_i y_i Z_i
     CUDA_TRY(cudaMemcpyAsync(w.hcol, ycoef.data(), sizeof(double) * kdim * nrhs, cudaMemcpyHostToDevice, s));
     note_launch();
-    combine_kernel<<<vec_grid(N, nrhs), VB, 0, s>>>(N, nrhs, kdim, w.hcol, w.Z, ldv, X, ld);
+    launch_pdl(combine_kernel, vec_grid(N, nrhs), dim3(VB), 0, s, N, nrhs, kdim, (const double*)w.hcol,
+               (const double*)w.Z, ldv, X, ld);
     if ((st = residual()) != SPALU_OK) return st;
   }
   bool conv = true;

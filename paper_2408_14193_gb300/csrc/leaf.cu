@@ -379,6 +379,7 @@ __device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
 // memory would otherwise cost resident CTAs).
 template <typename T, int KUW, int LPB, bool bwd>
 __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) {
+  pdl_enter();
   extern __shared__ double lsm[];
   constexpr int NT = LPB * SLOT;
   constexpr int LST = SLOT * SLOT;                    // L stage per leaf: 16 columns x 16 (L(j+r, j) at r - 1)
@@ -571,6 +572,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 
 __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X, int nrhs, VecLayout lay) {
+  pdl_enter();
   extern __shared__ float4 gsm4[];
   float* Gs = reinterpret_cast<float*>(gsm4);    // NI x NQ
   float* xd = Gs + NI * NQ;                      // NQ x GRC
@@ -625,6 +627,7 @@ __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X,
 // the remaining rows.
 template <typename T>
 __global__ void sep_update_fwd_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) {
+  pdl_enter();
   const int nx = d.nx, ny = d.ny;
   const int R = (ny + 1) / (LEAF + 1) - 1, C = (nx + 1) / (LEAF + 1) - 1;
   const long long nrow = (long long)R * nx;
@@ -711,10 +714,10 @@ static void leaf_solve_go(const LeafDev& d, T* X, int nrhs, VecLayout lay, int b
   note_launch();
   if (!bwd) {
     cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    leaf_solve_kernel<T, KUW, LPB, false><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, lay);
+    launch_pdl(leaf_solve_kernel<T, KUW, LPB, false>, dim3(grid), dim3(LPB * SLOT), smem, s, d, X, nrhs, lay);
   } else {
     cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    leaf_solve_kernel<T, KUW, LPB, true><<<grid, LPB * SLOT, smem, s>>>(d, X, nrhs, lay);
+    launch_pdl(leaf_solve_kernel<T, KUW, LPB, true>, dim3(grid), dim3(LPB * SLOT), smem, s, d, X, nrhs, lay);
   }
 }
 
@@ -725,7 +728,8 @@ void launch_leaf_solve(const LeafDev& d, void* Xv, int nrhs, VecLayout lay, int 
     for (int c0 = 0; c0 < nrhs; c0 += GRC) {
       const int nc = nrhs - c0 < GRC ? nrhs - c0 : GRC;
       note_launch();
-      leaf_bwd_g_kernel<<<d.g.nbox(), GTH, smem, s>>>(d, static_cast<float*>(Xv) + (size_t)(c0 / GRC) * lay.chunk, nc, lay);
+      launch_pdl(leaf_bwd_g_kernel, dim3(d.g.nbox()), dim3(GTH), smem, s, d,
+                 static_cast<float*>(Xv) + (size_t)(c0 / GRC) * lay.chunk, nc, lay);
     }
     return;
   }
@@ -751,8 +755,8 @@ void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, VecLayout lay, c
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
   note_launch();
-  if (d.fp32) sep_update_fwd_kernel<float><<<blocks, 256, 0, s>>>(d, static_cast<float*>(X), nrhs, lay);
-  else sep_update_fwd_kernel<double><<<blocks, 256, 0, s>>>(d, static_cast<double*>(X), nrhs, lay);
+  if (d.fp32) launch_pdl(sep_update_fwd_kernel<float>, dim3(blocks), dim3(256), 0, s, d, static_cast<float*>(X), nrhs, lay);
+  else launch_pdl(sep_update_fwd_kernel<double>, dim3(blocks), dim3(256), 0, s, d, static_cast<double*>(X), nrhs, lay);
 }
 
 }  // namespace spalu

@@ -1517,6 +1517,7 @@ size_t invert_smem() { return 2 * sizeof(T) * INV_MAX * INV_MAX + sizeof(int) * 
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
+  pdl_enter();
   extern __shared__ double smd[];
   const int sid = blockIdx.x;
   const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
@@ -1608,6 +1609,7 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
 // not fixed); backward x_p = U^{-1} (y_p - W x_dP).
 template <typename T>
 __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
+  pdl_enter();
   extern __shared__ double smd[];
   const int P = blockIdx.x;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
@@ -1838,11 +1840,11 @@ static void level_solve(const LevelDev& d, const SolveCaps& sc, T* X, int nrhs, 
     T* Xc = X + (size_t)(c0 / SC) * lay.chunk;
     auto seg_go = [&](int dir) {
       note_launch();
-      seg_solve_kernel<T><<<d.g.nseg(), 256, sc.seg_smem, s>>>(d, sc, Xc, nc, lay, dir);
+      launch_pdl(seg_solve_kernel<T>, dim3(d.g.nseg()), dim3(256), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
     };
     auto sep_go = [&](int dir) {
       note_launch();
-      sep_solve_kernel<T><<<d.gp.nbox(), 256, sc.sep_smem, s>>>(d, sc, Xc, nc, lay, dir);
+      launch_pdl(sep_solve_kernel<T>, dim3(d.gp.nbox()), dim3(256), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
     };
     if (!bwd) {
       if (d.g.nseg() > 0) seg_go(0);

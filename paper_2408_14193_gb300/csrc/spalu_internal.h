@@ -204,6 +204,31 @@ constexpr int LDAB = 2 * KL + KU + 1;  // band storage rows (LAPACK layout with 
 // Kernels launched by this library in this process (diagnostics, spalu_kernel_launches).
 void note_launch();
 
+// Programmatic dependent launch: kernels of the solve and refinement sequences are launched
+// with launch_pdl, so that a kernel's blocks are set up while its predecessor finishes; each
+// such kernel calls pdl_enter() first, which waits until the predecessor grid has completed
+// and its writes are visible, then lets the successor launch.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Placement of a solve vector: element (grid node u, right-hand side c) at X[u * rs + c * cs];
 // the solve kernels take the right-hand sides in chunks of 16, chunk k at X + k * chunk.
 // Column-major (ld): {1, ld, 16 ld}; chunk-interleaved (16 values per node): {16, 1, 16 N}.
