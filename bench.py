@@ -187,8 +187,14 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU leg
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the same
-# workload, keyed by (kernel, mixed precision); a kernel missing here reports null traffic
-PROFILED_TRAFFIC = {}
+# workload (profiles/leaf_elimination_diffusion1023_mixed.md, profiles/leaf_solve_diffusion1023_mixed.md),
+# keyed by (kernel, mixed precision); a kernel missing here reports null traffic.  Re-capture
+# after changing one of these kernels.
+PROFILED_TRAFFIC = {
+    ("leaf_lu_kernel+leaf_schur_kernel", True): 831_956_958,   # per launch pair
+    ("leaf_solve_kernel", True): 569_567_744,
+    ("leaf_bwd_g_kernel", True): 327_993_344,
+}
 
 
 def _leaf_flops_split():
