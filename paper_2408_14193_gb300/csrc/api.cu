@@ -102,7 +102,6 @@ struct spalu_factor_s {
   int xf_cols = 0;
   cudaStream_t last_stream = nullptr;
   GmresWork gw;
-  std::vector<int> host_rowptr_cache;
   PhaseTimer timer;
   int kumax = 30;            // upper bandwidth of the leaf U factors (read after each factor)
   int* d_lstat = nullptr;    // [LS_N * (L + 1)] per-level counters (factor kernels)
@@ -671,14 +670,9 @@ spalu_status spalu_factor_numeric_host(spalu_factor_t f, const int* rowptr, cons
                                        const double* val, int nnz, spalu_stream_t stream) {
   if (!f || !rowptr || !colind || !val || nnz < 0 || nnz > f->nnz_cap) return SPALU_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  bool same = f->nnz == nnz && (int)f->host_rowptr_cache.size() == f->N + 1 &&
-              std::memcmp(f->host_rowptr_cache.data(), rowptr, (f->N + 1) * sizeof(int)) == 0;
   f->nnz = nnz;
-  if (!same) {
-    CUDA_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (f->N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, s));
-    f->host_rowptr_cache.assign(rowptr, rowptr + f->N + 1);
-  }
+  CUDA_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (f->N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyHostToDevice, s));
   return factor_run(f, s);
 }

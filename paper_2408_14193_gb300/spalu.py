@@ -234,11 +234,18 @@ class Factor:
             _check(st, "spalu_refine")
         return it.value, rel
 
-    def solve_host(self, B: np.ndarray, refine: bool = False, stream=None):
-        """Host arrays in and out (copies inside the call); B has shape (nrhs, N)."""
+    def solve_host(self, B: np.ndarray, refine: bool = False, stream=None, out: np.ndarray | None = None):
+        """Host arrays in and out (copies inside the call); B has shape (nrhs, N).  ``out``
+        (same shape, float64, C-contiguous; page-locked for full copy bandwidth) receives the
+        solution; a new array otherwise."""
         B = np.ascontiguousarray(B, dtype=np.float64)
         nrhs = 1 if B.ndim == 1 else B.shape[0]
-        X = np.empty_like(B)
+        if out is not None:
+            if out.shape != B.shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous float64 array shaped like B")
+            X = out
+        else:
+            X = np.empty_like(B)
         it = ctypes.c_int(0)
         rel = np.zeros(nrhs)
         _check(self.lib.spalu_solve_host(self.handle, B.ctypes.data, X.ctypes.data, nrhs, self.N,
