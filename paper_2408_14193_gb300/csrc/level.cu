@@ -1170,9 +1170,12 @@ __global__ void merge_assemble_kernel(LevelDev d) {
 }
 
 // LU of the separator block with the row operations over every column (W = L^{-1} P A_pd),
-// then Z = A_dp U^{-1}.
+// then Z = A_dp U^{-1}.  When the kp separator rows over all nM columns fit in the dynamic
+// shared memory (smem_bytes), they are staged there: the elimination then runs on shared
+// memory with the same operations in the same order, and the rows are written back once.
 template <typename T>
-__global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
+__global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d, int smem_bytes) {
+  extern __shared__ double pm_sm[];
   __shared__ int shi[4];
   const int P = blockIdx.x;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
@@ -1185,6 +1188,73 @@ __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d) {
   const int Dp = d.gp.D();
   int* piv = d.ppiv + (size_t)P * d.sepcap;
   bool ok = true;
+  if ((size_t)kp * nM * sizeof(T) + (size_t)nM * sizeof(int) <= (size_t)smem_bytes) {
+    // staged rows: Pn[r + kp c] = M[Dp + r, column of table entry c]; entries [ndP, nM) are
+    // the separator itself (positions Dp + j), [0, ndP) the parent boundary
+    T* Pn = reinterpret_cast<T*>(pm_sm);
+    int* colp = reinterpret_cast<int*>(Pn + (size_t)kp * nM);
+    for (int c = threadIdx.x; c < nM; c += blockDim.x) colp[c] = tab[(size_t)c * TABW];
+    __syncthreads();
+    for (int x = threadIdx.x; x < kp * nM; x += blockDim.x)
+      Pn[x] = M[(Dp + x % kp) + ldp * colp[x / kp]];
+    __syncthreads();
+    auto at = [&](int r, int c) -> T& { return Pn[r + (size_t)kp * c]; };
+    for (int j = 0; j < kp; ++j) {
+      const int cs = ndP + j;                   // staged column of separator unknown j
+      if (threadIdx.x < 32) {
+        int lane = threadIdx.x;
+        double best = -1.0;
+        int bi = kp;
+        for (int r = j + lane; r < kp; r += 32) {
+          double v = fabs((double)at(r, cs));
+          if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { shi[0] = bi; shi[1] = best == 0.0; piv[j] = bi; }
+      }
+      __syncthreads();
+      const int p = shi[0];
+      if (shi[1]) { ok = false; if (threadIdx.x == 0) inv[j] = T(0); __syncthreads(); continue; }
+      if (p != j) {
+        for (int c = threadIdx.x; c < nM; c += blockDim.x) {
+          if (c >= ndP && c < cs) continue;     // multipliers of earlier steps
+          T a = at(j, c);
+          at(j, c) = at(p, c);
+          at(p, c) = a;
+        }
+        __syncthreads();
+      }
+      const T ipv = T(1) / at(j, cs);
+      if (threadIdx.x == 0) inv[j] = ipv;
+      for (int r = j + 1 + threadIdx.x; r < kp; r += blockDim.x) at(r, cs) *= ipv;
+      __syncthreads();
+      const int nr = kp - j - 1;
+      const int ncols = (kp - j - 1) + ndP;
+      for (int x = threadIdx.x; x < nr * ncols; x += blockDim.x) {
+        int r = j + 1 + x % nr, cc = x / nr;
+        int c = cc < kp - j - 1 ? (cs + 1 + cc) : (cc - (kp - j - 1));
+        at(r, c) -= at(r, cs) * at(j, c);
+      }
+      __syncthreads();
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(d.err, ERR_SINGULAR);
+    for (int x = threadIdx.x; x < kp * nM; x += blockDim.x)
+      M[(Dp + x % kp) + ldp * colp[x / kp]] = Pn[x];
+    // Z = A_dp U^{-1}: each dP row solved left to right, U from the staged rows
+    for (int a = threadIdx.x; a < ndP; a += blockDim.x) {
+      size_t row = colp[a];
+      for (int j = 0; j < kp; ++j) {
+        T s = M[row + ldp * (Dp + j)];
+        for (int i = 0; i < j; ++i) s -= M[row + ldp * (Dp + i)] * at(i, ndP + j);
+        M[row + ldp * (Dp + j)] = s * inv[j];
+      }
+    }
+    return;
+  }
   for (int j = 0; j < kp; ++j) {
     const int cj = Dp + j;
     if (threadIdx.x < 32) {
@@ -1773,8 +1843,15 @@ static void merge_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) 
     note_launch();
     merge_assemble_kernel<T><<<grid, 256, 0, s>>>(d);
   }
-  note_launch();
-  merge_panel_kernel<T><<<np, 256, 0, s>>>(d);
+  {
+    // shared memory for the staged separator rows: the geometric bound, at most 96 KB (larger
+    // parents take the global-memory path inside the kernel)
+    const size_t geo = (size_t)p.sepcap * p.ldFp * sizeof(T) + (size_t)p.ldFp * sizeof(int);
+    const int pm = (int)(geo < 96 * 1024 ? geo : 96 * 1024);
+    if (pm > 48 * 1024) cudaFuncSetAttribute(merge_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pm);
+    note_launch();
+    merge_panel_kernel<T><<<np, 256, pm, s>>>(d, pm);
+  }
   {
     const int ism = (int)invert_smem<T>();
     cudaFuncSetAttribute(sep_invert_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ism);
