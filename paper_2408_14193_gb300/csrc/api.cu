@@ -626,7 +626,7 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
     note_launch();
     convert_kernel<double, float><<<grid_for(f->nnz), 256, 0, s>>>(f->nnz, 1, f->val, 0, f->fval, 0);
   }
-  if (f->pred_mode != PRED_OFF) launch_node_stats(f->rowptr, f->colind, f->val, f->N, f->d_nstat, s);
+  if (f->pred_mode != PRED_OFF) launch_node_stats(f->rowptr, f->colind, f->val, f->fval, f->N, f->d_nstat, s);
   int t = tm.begin("leaf_factor", s);
   launch_leaf_factor(f->leaf, s);
   tm.end(t, s);

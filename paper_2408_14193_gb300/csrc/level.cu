@@ -693,6 +693,122 @@ __device__ bool id_error_ok(const SegCtx& S, BGet bget, int halves, int e, int k
 }
 
 // ------------------------------------------------------------ sparsify: one CTA per segment
+// The same column-pivoted Householder QR by one warp, for the 8-warp CTAs when the sketch sits
+// in shared memory (odd pitch) and e <= 64: lane l owns columns l and l + 32, keeps their
+// squared norms in registers and downdates them itself, so a step needs no barrier; the
+// pivot, the Householder scalars and the rank decision are warp-uniform (xor reductions).
+// Same arithmetic as block_cpqr up to the order of the sums.  All threads call it.
+template <typename T>
+__device__ int warp_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1, double* vn2,
+                         int* shi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < e; j += blockDim.x) perm[j] = j;
+  if (m == 0 || e == 0) { __syncthreads(); return 0; }
+  for (int j = warp; j < e; j += nw) {
+    T s = T(0);
+    for (int r = lane; r < m; r += 32) { T v = Y[r + (size_t)ldy * j]; s += v * v; }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) { vn1[j] = (double)s; vn2[j] = (double)s; }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double n1[2], n2[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int j = lane + 32 * t;
+      n1[t] = j < e ? vn1[j] : 0.0;
+      n2[t] = j < e ? vn2[j] : 0.0;
+    }
+    const double tol3z = sqrt(DBL_EPSILON);
+    const double tie = (1.0 - TIE_RTOL) * (1.0 - TIE_RTOL);
+    const int kmax = min(m, e);
+    double ref = 0.0;
+    int k = kmax;
+    for (int i = 0; i < kmax; ++i) {
+      long long mx = -1;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int j = lane + 32 * t;
+        if (j >= i && j < e) mx = max(mx, dbits(n1[t]));
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const long long thr = dbits(__longlong_as_double(mx) * tie);
+      int p = e;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int j = lane + 32 * t;
+        if (j >= i && j < e && dbits(n1[t]) >= thr && j < p) p = j;
+      }
+      for (int o = 16; o > 0; o >>= 1) p = min(p, __shfl_xor_sync(0xffffffffu, p, o));
+      if (p != i) {
+        for (int r = lane; r < m; r += 32) {
+          const T a = Y[r + (size_t)ldy * i];
+          Y[r + (size_t)ldy * i] = Y[r + (size_t)ldy * p];
+          Y[r + (size_t)ldy * p] = a;
+        }
+        const int si = i >> 5, sp = p >> 5;
+        const double i1 = __shfl_sync(0xffffffffu, si ? n1[1] : n1[0], i & 31);
+        const double i2 = __shfl_sync(0xffffffffu, si ? n2[1] : n2[0], i & 31);
+        const double p1 = __shfl_sync(0xffffffffu, sp ? n1[1] : n1[0], p & 31);
+        const double p2 = __shfl_sync(0xffffffffu, sp ? n2[1] : n2[0], p & 31);
+        if (lane == (i & 31)) { if (si) { n1[1] = p1; n2[1] = p2; } else { n1[0] = p1; n2[0] = p2; } }
+        if (lane == (p & 31)) { if (sp) { n1[1] = i1; n2[1] = i2; } else { n1[0] = i1; n2[0] = i2; } }
+        if (lane == 0) { const int t = perm[i]; perm[i] = perm[p]; perm[p] = t; }
+        __syncwarp();
+      }
+      T s = T(0);
+      for (int r = i + lane; r < m; r += 32) { const T v = Y[r + (size_t)ldy * i]; s += v * v; }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const T normx = sqrt(s);
+      const T x0 = Y[i + (size_t)ldy * i];
+      const T alpha = x0 >= T(0) ? -normx : normx;
+      const T v0 = x0 - alpha;
+      const T vv = v0 * v0 + (s - x0 * x0);
+      const T c2 = vv > T(0) ? T(2) / vv : T(0);
+      if (i == 0) ref = (double)normx;
+      if (ref == 0.0) { k = 0; break; }
+      if ((double)normx <= eps * ref || normx == T(0)) { k = i; break; }
+      const T* yi = Y + (size_t)ldy * i;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int j = lane + 32 * t;
+        if (j <= i || j >= e) continue;
+        T* yj = Y + (size_t)ldy * j;
+        T d0 = v0 * yj[i], d1 = T(0), d2 = T(0), d3 = T(0);
+        int r = i + 1;
+        for (; r + 3 < m; r += 4) {
+          d0 += yi[r] * yj[r];
+          d1 += yi[r + 1] * yj[r + 1];
+          d2 += yi[r + 2] * yj[r + 2];
+          d3 += yi[r + 3] * yj[r + 3];
+        }
+        for (; r < m; ++r) d0 += yi[r] * yj[r];
+        const T cj = ((d0 + d1) + (d2 + d3)) * c2;
+        yj[i] -= cj * v0;
+        for (r = i + 1; r < m; ++r) yj[r] -= cj * yi[r];
+        const double sq = n1[t];
+        if (sq != 0.0) {
+          const double rij = (double)yj[i];
+          const double sn = fmax(sq - rij * rij, 0.0);
+          if (sn <= tol3z * n2[t]) {
+            double s2 = 0.0;
+            for (r = i + 1; r < m; ++r) { const double v = (double)yj[r]; s2 += v * v; }
+            n1[t] = s2;
+            n2[t] = s2;
+          } else {
+            n1[t] = sn;
+          }
+        }
+      }
+      if (lane == 0) Y[i + (size_t)ldy * i] = alpha;
+      __syncwarp();
+    }
+    if (lane == 0) shi[0] = k;
+  }
+  __syncthreads();
+  return shi[0];
+}
+
 template <typename T, int NWT>
 __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(LevelDev d, int smem_bytes) {
   extern __shared__ double sm[];
@@ -785,7 +901,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
   const size_t TD = sizeof(T);
   const size_t small_b = (2 * (size_t)e) * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * TD + 64;
   const size_t per_ch_b = (size_t)halves * (e + hmax) * TD;
-  const size_t ydt_b = ((size_t)mmax * e + 2 * (size_t)e * e) * TD;
+  const size_t ydt_b = ((size_t)(mmax + 1) * e + 2 * (size_t)e * e) * TD;
   int ch = SK_CHUNK;
   bool in_smem = small_b + ch * per_ch_b + ydt_b <= (size_t)smem_bytes;
   if (!in_smem) {
@@ -811,7 +927,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     Bc = reinterpret_cast<T*>(q); q += (size_t)halves * ch * e * TD;
     Gc = reinterpret_cast<T*>(q); q += (size_t)hmax * halves * ch * TD;
     if (in_smem) {
-      Y = reinterpret_cast<T*>(q); q += (size_t)mmax * e * TD; ldy = mmax;
+      Y = reinterpret_cast<T*>(q); q += (size_t)(mmax + 1) * e * TD; ldy = mmax | 1;   // odd pitch
       Dw = reinterpret_cast<T*>(q); q += (size_t)e * e * TD; ldd = e;
       Tw = reinterpret_cast<T*>(q); q += (size_t)e * e * TD; ldt = e;
     } else {
@@ -901,7 +1017,8 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
       for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
     }
     __syncthreads();
-    k = block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
+    k = (NWT == NW && in_smem && e <= 64) ? warp_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shi)
+                                          : block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
     ++passes;
     if (predicted) {          // the one-pass ID stands if it passes the measured-error test
       predicted = false;
@@ -1791,7 +1908,7 @@ size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes) 
   const size_t small_b = 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
   // segments of at most 32 unknowns also stage their B block (<= 6 sides of e + 8 corners)
   const size_t bs = e <= 32 ? halves * (6 * (size_t)e + 8) * e + 4 : 0;
-  return small_b + (SK_CHUNK * halves * (e + hcap) + mmax * e + 2 * (size_t)e * e + bs) * tbytes;
+  return small_b + (SK_CHUNK * halves * (e + hcap) + (mmax + 1) * e + 2 * (size_t)e * e + bs) * tbytes;
 }
 
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes) {

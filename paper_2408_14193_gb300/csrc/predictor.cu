@@ -24,18 +24,20 @@ constexpr int NACC = PRED_NPARAM + 1;  // gradient entries + the loss sum
 
 // Per grid node u of the original matrix (features 5-10 of the segments): log d_u with
 // d_u = |A_uu|, log(d_u / s_u) with s_u = sum_{j != u} |A_uj|, |sum_j A_uj| / d_u, and
-// sum_{j!=u} |A_uj - A_ju| / sum_{j!=u} (|A_uj| + |A_ju|); computed in FP64, stored as float.
+// sum_{j!=u} |A_uj - A_ju| / sum_{j!=u} (|A_uj| + |A_ju|); computed in the precision of the
+// value array (FP64, or its FP32 copy in the mixed path), stored as float.
+template <typename V>
 __global__ void node_stats_kernel(const int* __restrict__ rowptr, const int* __restrict__ colind,
-                                  const double* __restrict__ val, int n, float4* __restrict__ out) {
+                                  const V* __restrict__ val, int n, float4* __restrict__ out) {
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-    double dd = 0.0, off = 0.0, rs = 0.0, num = 0.0, den = 0.0;
+    V dd = V(0), off = V(0), rs = V(0), num = V(0), den = V(0);
     for (int p = rowptr[u]; p < rowptr[u + 1]; ++p) {
       const int j = colind[p];
-      const double a = val[p];
+      const V a = val[p];
       rs += a;
       if (j == u) { dd += a; continue; }
       off += fabs(a);
-      double aj = 0.0;
+      V aj = V(0);
       for (int q = rowptr[j]; q < rowptr[j + 1]; ++q)
         if (colind[q] == u) aj += val[q];
       num += fabs(a - aj);
@@ -43,10 +45,17 @@ __global__ void node_stats_kernel(const int* __restrict__ rowptr, const int* __r
     }
     dd = fabs(dd);
     float4 r;
-    r.x = (float)(dd > 0.0 ? log(dd) : log(1e-300));
-    r.y = (float)((off > 0.0 && dd > 0.0) ? log(dd / off) : 0.0);
-    r.z = (float)(dd > 0.0 ? fabs(rs) / dd : 0.0);
-    r.w = (float)(den > 0.0 ? num / den : 0.0);
+    if constexpr (sizeof(V) == 4) {     // FP32 copy of the values (mixed path): FP32 logs
+      r.x = dd > 0.f ? logf(dd) : -690.7755f;              // log(1e-300) when dd vanishes
+      r.y = (off > 0.f && dd > 0.f) ? logf(dd / off) : 0.f;
+      r.z = dd > 0.f ? fabsf(rs) / dd : 0.f;
+      r.w = den > 0.f ? num / den : 0.f;
+    } else {
+      r.x = (float)(dd > 0.0 ? log(dd) : log(1e-300));
+      r.y = (float)((off > 0.0 && dd > 0.0) ? log(dd / off) : 0.0);
+      r.z = (float)(dd > 0.0 ? fabs(rs) / dd : 0.0);
+      r.w = (float)(den > 0.0 ? num / den : 0.0);
+    }
     out[u] = r;
   }
 }
@@ -238,13 +247,14 @@ int pred_grad_blocks(int nb) {
   return g < 1 ? 1 : (g > PRED_MAXBLK ? PRED_MAXBLK : g);
 }
 
-void launch_node_stats(const int* rowptr, const int* colind, const double* val, int n, float4* out,
-                       cudaStream_t s) {
+void launch_node_stats(const int* rowptr, const int* colind, const double* val, const float* fval, int n,
+                       float4* out, cudaStream_t s) {
   if (n <= 0) return;
   int g = (n + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   note_launch();
-  node_stats_kernel<<<g, 256, 0, s>>>(rowptr, colind, val, n, out);
+  if (fval) node_stats_kernel<float><<<g, 256, 0, s>>>(rowptr, colind, fval, n, out);
+  else node_stats_kernel<double><<<g, 256, 0, s>>>(rowptr, colind, val, n, out);
 }
 
 void launch_pred_fit_norm(const float* X, int n, PredDev* P, cudaStream_t s) {

@@ -257,8 +257,8 @@ bool level_solve_caps(const LevelDev& d, const int* lstat, SolveCaps* out);
 void launch_level_solve_fwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, VecLayout lay, cudaStream_t s);
 void launch_level_solve_bwd(const LevelDev& d, const SolveCaps& c, void* X, int nrhs, VecLayout lay, cudaStream_t s);
 
-void launch_node_stats(const int* rowptr, const int* colind, const double* val, int n, float4* out,
-                       cudaStream_t s);
+void launch_node_stats(const int* rowptr, const int* colind, const double* val, const float* fval, int n,
+                       float4* out, cudaStream_t s);
 void launch_pred_fit_norm(const float* X, int n, PredDev* P, cudaStream_t s);
 void launch_pred_grad(const float* params, const PredDev* P, const float* X, const float* Y, int r0, int nb,
                       float* partial, float* grad, int* step, cudaStream_t s);
