@@ -78,6 +78,149 @@ struct Band {
   __device__ __forceinline__ T dinv(int j) const { return ld(invd + j); }
 };
 
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
+  if constexpr (sizeof(T) == 8) cp_async8(smem, gmem); else cp_async4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// 16 consecutive values of shared memory (16-byte aligned) into registers, 128-bit loads
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(p)[i];
+      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const double2 q = reinterpret_cast<const double2*>(p)[i];
+      v[2 * i] = q.x; v[2 * i + 1] = q.y;
+    }
+  }
+}
+
+// Warp-staged variants of the two sweeps for the leaf Schur kernel: every lane of the warp
+// takes part (act = this lane owns a column), the warp starts its forward sweep at the same
+// column j0, and the band entries of the next 16 columns are copied into a double-buffered
+// per-warp stage with cp.async while the current 16 columns are swept.  Stage layout, 16
+// values per column: forward L(j+1..j+15, j) then the pivot slot; backward 1/U_jj then
+// U(j-1..j-15, j).  Upper bandwidth <= 15 (no interchange widened U).
+template <typename T>
+struct WarpStage {
+  T* v;      // 2 x 16 x 16
+  int* p;    // 2 x 16 pivots
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_L(const WarpStage<T>& w, int buf, const T* ab, const int* piv, int jb, int lane) {
+  T* v = w.v + buf * 256;
+  for (int x = lane; x < 256; x += 32) {
+    const int u = x >> 4, r = x & 15, j = jb + u;
+    if (j < NI) {
+      if (r < 15) cp_async_t(v + x, ab + (KV + 1 + r) + (size_t)LDAB * j);
+      else cp_async4(w.p + buf * 16 + u, piv + j);
+    }
+  }
+  cp_async_commit();
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_U(const WarpStage<T>& w, int buf, const T* ab, const T* invd, int t0, int lane) {
+  T* v = w.v + buf * 256;
+  for (int x = lane; x < 256; x += 32) {
+    const int u = x >> 4, r = x & 15, j = NI - 1 - (t0 + u);
+    if (j >= 0) {
+      if (r == 0) cp_async_t(v + x, invd + j);
+      else cp_async_t(v + x, ab + (KV - r) + (size_t)LDAB * j);
+    }
+  }
+  cp_async_commit();
+}
+
+template <typename T, class In, class Out>
+__device__ __forceinline__ void sweep_L_staged(const WarpStage<T>& w, const T* ab, const int* piv, int j0, bool act,
+                                               In in, Out out) {
+  const int lane = threadIdx.x & 31;
+  T W[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) W[r] = (act && j0 + r < NI) ? in(j0 + r) : T(0);
+  const int nb = (NI - j0 + 15) / 16;
+  stage_L(w, 0, ab, piv, j0, lane);
+  for (int blk = 0; blk < nb; ++blk) {
+    if (blk + 1 < nb) { stage_L(w, (blk + 1) & 1, ab, piv, j0 + 16 * (blk + 1), lane); cp_async_wait<1>(); }
+    else cp_async_wait<0>();
+    __syncwarp();
+    const T* S = w.v + (blk & 1) * 256;
+    const int* P = w.p + (blk & 1) * 16;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int j = j0 + 16 * blk + u;
+      if (j < NI) {
+        const int dsw = P[u] - j;
+        T a = W[u], b = a;
+        if (__any_sync(0xffffffffu, dsw != 0)) {
+#pragma unroll
+          for (int r = 1; r < 16; ++r)
+            if (r == dsw) { b = W[(u + r) & 15]; W[(u + r) & 15] = a; }
+          W[u] = b;
+        }
+        T lv[16];
+        lds_vec(S + u * 16, lv);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= lv[r - 1] * b;
+        if (act) out(j, b);
+        W[u] = (act && j + 16 < NI) ? in(j + 16) : T(0);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, class In, class Out>
+__device__ __forceinline__ void sweep_U_staged(const WarpStage<T>& w, const T* ab, const T* invd, bool act, In in,
+                                               Out out) {
+  const int lane = threadIdx.x & 31;
+  T V[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) V[r] = act ? in(NI - 1 - r) : T(0);
+  const int nb = (NI + 15) / 16;
+  stage_U(w, 0, ab, invd, 0, lane);
+  for (int blk = 0; blk < nb; ++blk) {
+    if (blk + 1 < nb) { stage_U(w, (blk + 1) & 1, ab, invd, 16 * (blk + 1), lane); cp_async_wait<1>(); }
+    else cp_async_wait<0>();
+    __syncwarp();
+    const T* S = w.v + (blk & 1) * 256;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = 16 * blk + u;
+      if (t < NI) {
+        const int j = NI - 1 - t;
+        T uv[16];
+        lds_vec(S + u * 16, uv);
+        const T x = V[u] * uv[0];
+        if (act) out(j, x);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) V[(u + r) & 15] -= uv[r] * x;
+        V[u] = (act && j - 16 >= 0) ? in(j - 16) : T(0);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Forward sweep y = L^{-1} P x for one column held by this thread.  in(j) gives x_j,
 // out(j, y) receives y_j for j = j0..NI-1 (x_j = 0 for j < j0 is assumed).
 template <typename T, class BandT, class In, class Out>
@@ -267,7 +410,34 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
     }
   }
   __syncthreads();
-  if (live && tid < NQ) {
+  __shared__ __align__(16) T stv[FTH / 32][512];
+  __shared__ int stp[FTH / 32][32];
+  if (live && d.kur[b] <= 15) {     // warp-staged sweeps (all lanes; lanes >= NQ only stage)
+    const bool act = tid < NQ;
+    const int q = act ? c_qorder[tid] : 0;
+    const int j0 = c_qstart[tid >> 5];
+    const WarpStage<T> ws{stv[threadIdx.x >> 5], stp[threadIdx.x >> 5]};
+    const T* ab = reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI;
+    const int* pv = d.piv + (size_t)b * NI;
+    const T* iv = reinterpret_cast<const T*>(d.invd) + (size_t)b * NI;
+    T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
+    T* Gb = d.G ? reinterpret_cast<T*>(d.G) + (size_t)b * NI * NQ : nullptr;
+    const int mq = act ? qm[sub][q] : -1;
+    const T cq = (act && qex[sub][q]) ? (T)qc[sub][q] : T(0);
+    sweep_L_staged<T>(ws, ab, pv, j0, act, [&](int j) { return j == mq ? cq : T(0); },
+                      [&](int j, T y) { yb[(size_t)j * QL + tid] = y; });
+    const size_t ldF = d.ldF;
+    auto yin = [&](int j) { return j < j0 ? T(0) : yb[(size_t)j * QL + tid]; };
+    auto ring_out = [&](int j, T x) {
+      if (Gb) Gb[(size_t)j * NQ + q] = x;                   // column q of A_II^{-1} A_Id
+      const int lx = j % LEAF, ly = j / LEAF;
+      if (ly == 0 && qex[sub][lx]) F[lx + ldF * q] = -(T)qa[sub][lx] * x;
+      if (ly == LEAF - 1 && qex[sub][LEAF + lx]) F[(LEAF + lx) + ldF * q] = -(T)qa[sub][LEAF + lx] * x;
+      if (lx == 0 && qex[sub][2 * LEAF + ly]) F[(2 * LEAF + ly) + ldF * q] = -(T)qa[sub][2 * LEAF + ly] * x;
+      if (lx == LEAF - 1 && qex[sub][3 * LEAF + ly]) F[(3 * LEAF + ly) + ldF * q] = -(T)qa[sub][3 * LEAF + ly] * x;
+    };
+    sweep_U_staged<T>(ws, ab, iv, act, yin, ring_out);
+  } else if (live && tid < NQ) {    // widened U: sweeps reading the band from global memory
     const int q = c_qorder[tid];
     const int j0 = c_qstart[tid >> 5];
     Band<T, true> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
@@ -288,8 +458,7 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
       if (lx == 0 && qex[sub][2 * LEAF + ly]) F[(2 * LEAF + ly) + ldF * q] = -(T)qa[sub][2 * LEAF + ly] * x;
       if (lx == LEAF - 1 && qex[sub][3 * LEAF + ly]) F[(3 * LEAF + ly) + ldF * q] = -(T)qa[sub][3 * LEAF + ly] * x;
     };
-    if (d.kur[b] <= 15) sweep_U<T, 16>(Bd, yin, ring_out);   // no interchange widened U
-    else sweep_U<T, 32>(Bd, yin, ring_out);
+    sweep_U<T, 32>(Bd, yin, ring_out);
   }
   __syncthreads();
   const bool active = live;
@@ -336,40 +505,6 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
 // shared-memory stage with cp.async while the current block is swept, so the sequential
 // sweeps read their factor entries from shared memory without waiting on L2.
 constexpr int SLOT = 16;   // right-hand-side slots per leaf and launch
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-}
-template <typename T>
-__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
-  if constexpr (sizeof(T) == 8) cp_async8(smem, gmem); else cp_async4(smem, gmem);
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-// 16 consecutive values of shared memory (16-byte aligned) into registers, 128-bit loads
-template <typename T, int N>
-__device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) {
-      const float4 q = reinterpret_cast<const float4*>(p)[i];
-      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < N / 2; ++i) {
-      const double2 q = reinterpret_cast<const double2*>(p)[i];
-      v[2 * i] = q.x; v[2 * i + 1] = q.y;
-    }
-  }
-}
 
 // Band sweeps of LPB leaves x 16 right-hand sides per CTA, thread (leaf, rhs): forward
 // x_I = U^{-1} L^{-1} P b_I; backward x_I -= U^{-1} L^{-1} P (A_Id x_d).  The factors of the
