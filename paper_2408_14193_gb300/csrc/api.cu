@@ -28,9 +28,9 @@ struct GmresWork {
   double* V = nullptr;      // (m+1) * N * nrhs   Krylov basis
   double* Z = nullptr;      // m * N * nrhs       M^{-1} V_j, kept for the update (no final solve)
   unsigned* cnt = nullptr;  // ticket counters of the column sums, one per column chunk
-  double* R = nullptr;      // N * nrhs
   double* part = nullptr;   // partial sums
   double* hcol = nullptr;   // device coefficients (m+2) * nrhs
+  double* vs = nullptr;     // (m+2) * nrhs: basis vector j is vs[j] x V_j (stored unnormalized)
   double* vec = nullptr;    // nrhs scalars
 };
 
@@ -183,7 +183,7 @@ constexpr int VNB = 1024;                // most blocks per column chunk (partia
 
 static_assert(VB == 32 * RC, "one warp per column of a chunk in the block sums");
 __device__ void column_sums(double (&s)[RC], int c0, int nrhs, double* part, unsigned* cnt,
-                            double* out, int sq) {
+                            double* out, int sq, const double* oscale = nullptr, double* inv_out = nullptr) {
   __shared__ double red[RC][VB];
   __shared__ int last;
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;   // warp k sums column c0 + k
@@ -209,7 +209,12 @@ __device__ void column_sums(double (&s)[RC], int c0, int nrhs, double* part, uns
   if (valid)
     for (int i = lane; i < nb; i += 32) t += __ldcg(part + (size_t)(c0 + k) * nb + i);
   for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  if (lane == 0 && valid) out[c0 + k] = sq ? sqrt(t) : t;
+  if (lane == 0 && valid) {
+    double o = sq ? sqrt(t) : t;
+    if (oscale) o *= oscale[c0 + k];
+    out[c0 + k] = o;
+    if (inv_out) inv_out[c0 + k] = o != 0.0 ? 1.0 / o : 0.0;
+  }
   if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
@@ -217,8 +222,8 @@ __device__ void column_sums(double (&s)[RC], int c0, int nrhs, double* part, uns
 __global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int* rowptr, const int* colind,
                                                   const double* val, const double* x, int ldx,
                                                   const double* b, int ldb, double* y, int ldy,
-                                                  const double* d, int ldd, double* part,
-                                                  unsigned* cnt, double* out, int sq) {
+                                                  const double* d, int ldd, const double* dscale,
+                                                  double* part, unsigned* cnt, double* out, int sq) {
   pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
@@ -245,14 +250,16 @@ __global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int*
         s[k] += yv * (d ? d[r + (size_t)ldd * (c0 + k)] : yv);
       }
   }
-  if (part) column_sums(s, c0, nrhs, part, cnt, out, sq);
+  if (part) column_sums(s, c0, nrhs, part, cnt, out, sq, dscale);
 }
 
-// One modified Gram-Schmidt pass: w_c -= h_c p_c (skipped when p is null), then
-// out[c] = <w_c, q_c> (q null: ||w_c||, sq)
+// One modified Gram-Schmidt pass on unnormalized basis vectors (vector i stands for
+// scale_i x stored_i): w_c -= h_c ps_c p_c (skipped when p is null), then
+// out[c] = qs_c <w_c, q_c> (q null: ||w_c|| (sq) and inv_out[c] = 1 / out[c])
 __global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const double* h, const double* p, int ldp,
-                                                 double* w, int ldw, const double* q, int ldq,
-                                                 double* part, unsigned* cnt, double* out, int sq) {
+                                                 const double* ps, double* w, int ldw, const double* q,
+                                                 int ldq, const double* qs, double* part, unsigned* cnt,
+                                                 double* out, int sq, double* inv_out) {
   pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const doubl
 #pragma unroll
   for (int k = 0; k < RC; ++k) {
     s[k] = 0.0;
-    hc[k] = (p && k < nc) ? h[c0 + k] : 0.0;
+    hc[k] = (p && k < nc) ? (ps ? h[c0 + k] * ps[c0 + k] : h[c0 + k]) : 0.0;
   }
   for (long long r = blockIdx.x * (long long)VB + threadIdx.x; r < n; r += (long long)gridDim.x * VB) {
 #pragma unroll
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const doubl
         s[k] += wv * (q ? q[r + (size_t)ldq * (c0 + k)] : wv);
       }
   }
-  column_sums(s, c0, nrhs, part, cnt, out, sq);
+  column_sums(s, c0, nrhs, part, cnt, out, sq, q ? qs : nullptr, inv_out);
 }
 
 // X_c += sum_i y[i][c] Z_i,c for i = 0..k-1, in that order (Z_i = Z + i * ldz * nrhs)
@@ -295,18 +302,6 @@ __global__ void __launch_bounds__(VB, 4) combine_kernel(int n, int nrhs, int k, 
   }
 }
 
-// y[:, c] = x[:, c] / s[c] (zero when s[c] == 0); blockIdx.y = column, one reciprocal per thread
-__global__ void scale_kernel(int n, int nrhs, const double* s, const double* x, int ldx, double* y,
-                             int ldy) {
-  pdl_enter();
-  const int c = blockIdx.y;
-  const double d = s[c];
-  const double di = d != 0.0 ? 1.0 / d : 0.0;
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
-       r += (long long)gridDim.x * blockDim.x)
-    y[r + (size_t)ldy * c] = x[r + (size_t)ldx * c] * di;
-}
-
 // dst[:, c] = src[:, c] in the other precision (round to nearest), n rows, nc columns
 template <typename S, typename D>
 __global__ void convert_kernel(long long n, int nc, const S* src, int lds, D* dst, int ldd) {
@@ -322,13 +317,16 @@ __global__ void convert_kernel(long long n, int nc, const S* src, int lds, D* ds
 // 16 consecutive values per grid node), through a 64-node x 16-column tile in shared memory so
 // that both sides are read and written in whole sectors.  grid = (ceil(n / 64), chunks).
 constexpr int CT = 64;
-__global__ void __launch_bounds__(256) to_chunked_kernel(int n, int nrhs, const double* B, int ldb, float* xf) {
+__global__ void __launch_bounds__(256) to_chunked_kernel(int n, int nrhs, const double* B, int ldb,
+                                                         const double* bscale, float* xf) {
   pdl_enter();
   __shared__ float tile[16][CT + 1];
   const int u0 = blockIdx.x * CT, k = blockIdx.y;
   for (int i = threadIdx.x; i < 16 * CT; i += 256) {
     const int cc = i / CT, uu = i % CT, c = 16 * k + cc;
-    tile[cc][uu] = (u0 + uu < n && c < nrhs) ? (float)B[(size_t)(u0 + uu) + (size_t)ldb * c] : 0.f;
+    float v = (u0 + uu < n && c < nrhs) ? (float)B[(size_t)(u0 + uu) + (size_t)ldb * c] : 0.f;
+    if (bscale && c < nrhs) v *= (float)bscale[c];
+    tile[cc][uu] = v;
   }
   __syncthreads();
   float* dst = xf + ((size_t)k * n + u0) * 16;
@@ -351,6 +349,16 @@ __global__ void __launch_bounds__(256) from_chunked_kernel(int n, int nrhs, cons
   for (int i = threadIdx.x; i < 16 * CT; i += 256) {
     const int cc = i / CT, uu = i % CT, c = 16 * k + cc;
     if (u0 + uu < n && c < nrhs) X[(size_t)(u0 + uu) + (size_t)ldx * c] = (double)tile[cc][uu];
+  }
+}
+
+// X[:, c] = s_c B[:, c]
+__global__ void scaled_copy_kernel(int n, int nrhs, const double* B, int ldb, const double* sc, double* X, int ldx) {
+  pdl_enter();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * nrhs;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % n), c = (int)(e / n);
+    X[r + (size_t)ldx * c] = B[r + (size_t)ldb * c] * sc[c];
   }
 }
 
@@ -677,8 +685,17 @@ spalu_status spalu_factor_numeric_host(spalu_factor_t f, const int* rowptr, cons
   return factor_run(f, s);
 }
 
+// X = spaLU^{-1} (B diag(bscale)) (bscale: device, one factor per column, or null)
+static spalu_status solve_impl(spalu_factor_t f, const double* B, const double* bscale, double* X, int nrhs,
+                               int ld, spalu_stream_t stream);
+
 spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
                          spalu_stream_t stream) {
+  return solve_impl(f, B, nullptr, X, nrhs, ld, stream);
+}
+
+static spalu_status solve_impl(spalu_factor_t f, const double* B, const double* bscale, double* X, int nrhs,
+                               int ld, spalu_stream_t stream) {
   if (!f || !B || !X || nrhs < 0 || ld < f->N) return SPALU_ERR_ARG;
   if (!f->factored) return SPALU_ERR_STATE;
   if (nrhs == 0) return SPALU_OK;
@@ -703,9 +720,12 @@ spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs,
       f->xf_cols = 16 * nch;
     }
     note_launch();
-    launch_pdl(to_chunked_kernel, cgrid, dim3(256), 0, s, N, nrhs, B, ld, f->xf);
+    launch_pdl(to_chunked_kernel, cgrid, dim3(256), 0, s, N, nrhs, B, ld, bscale, f->xf);
     W = f->xf;
     lay = VecLayout{16, 1, 16LL * N};
+  } else if (bscale) {
+    note_launch();
+    launch_pdl(scaled_copy_kernel, dim3(grid_for((long long)N * nrhs)), dim3(256), 0, s, N, nrhs, B, ld, bscale, X, ld);
   } else if (X != B) {
     CUDA_TRY(cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), B, (size_t)ld * sizeof(double),
                                (size_t)N * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
@@ -736,16 +756,16 @@ static spalu_status gmres_alloc(spalu_factor_t f, int nrhs) {
   GmresWork& w = f->gw;
   const int m = f->o.gmres_m;
   if (w.nrhs >= nrhs && w.m == m) return SPALU_OK;
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vs); cudaFree(w.vec);
   w = GmresWork();
   size_t N = f->N;
   if (cudaMalloc(&w.V, sizeof(double) * (m + 1) * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.Z, sizeof(double) * (size_t)m * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.cnt, sizeof(unsigned) * ((nrhs + RC - 1) / RC)) != cudaSuccess ||
       cudaMemset(w.cnt, 0, sizeof(unsigned) * ((nrhs + RC - 1) / RC)) != cudaSuccess ||
-      cudaMalloc(&w.R, sizeof(double) * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.part, sizeof(double) * VNB * nrhs) != cudaSuccess ||
       cudaMalloc(&w.hcol, sizeof(double) * (m + 2) * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.vs, sizeof(double) * (m + 2) * nrhs) != cudaSuccess ||
       cudaMalloc(&w.vec, sizeof(double) * 4 * nrhs) != cudaSuccess)
     return SPALU_ERR_ALLOC;
   w.nrhs = nrhs;
@@ -770,20 +790,22 @@ static dim3 vec_grid(int n, int nrhs) {
   return dim3(nb > 0 ? nb : 1, nch);
 }
 
-// w -= h p (p null: w unchanged), out[c] = <w_c, q_c> (q null: ||w_c||, sq)
-static void vec_mgs(spalu_factor_t f, int nrhs, const double* h, const double* p, int ldp, double* w,
-                    int ldw, const double* q, int ldq, double* out, int sq, cudaStream_t s) {
+// w -= h ps p (p null: w unchanged), out[c] = qs <w_c, q_c> (q null: ||w_c||, sq; inv_out = 1 / out)
+static void vec_mgs(spalu_factor_t f, int nrhs, const double* h, const double* p, int ldp, const double* ps,
+                    double* w, int ldw, const double* q, int ldq, const double* qs, double* out, int sq,
+                    double* inv_out, cudaStream_t s) {
   note_launch();
-  launch_pdl(mgs_kernel, vec_grid(f->N, nrhs), dim3(VB), 0, s, f->N, nrhs, h, p, ldp, w, ldw, q, ldq,
-             f->gw.part, f->gw.cnt, out, sq);
+  launch_pdl(mgs_kernel, vec_grid(f->N, nrhs), dim3(VB), 0, s, f->N, nrhs, h, p, ldp, ps, w, ldw, q, ldq, qs,
+             f->gw.part, f->gw.cnt, out, sq, inv_out);
 }
 
-// y = b - A x (b null: A x); out set: out[c] = <y_c, d_c> (d null: ||y_c||, sq)
+// y = b - A x (b null: A x); out set: out[c] = ds_c <y_c, d_c> (d null: ||y_c||, sq)
 static void vec_spmv(spalu_factor_t f, int nrhs, const double* x, int ldx, const double* b, int ldb,
-                     double* y, int ldy, const double* d, int ldd, double* out, int sq, cudaStream_t s) {
+                     double* y, int ldy, const double* d, int ldd, const double* ds, double* out, int sq,
+                     cudaStream_t s) {
   note_launch();
   launch_pdl(spmv_kernel, vec_grid(f->N, nrhs), dim3(VB), 0, s, f->N, nrhs, f->rowptr, f->colind, f->val, x,
-             ldx, b, ldb, y, ldy, d, ldd, out ? f->gw.part : nullptr, f->gw.cnt, out, sq);
+             ldx, b, ldb, y, ldy, d, ldd, ds, out ? f->gw.part : nullptr, f->gw.cnt, out, sq);
 }
 
 static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
@@ -815,10 +837,12 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
   auto Zj = [&](int j) { return w.Z + (size_t)j * ldv * nrhs; };
   std::vector<double> bn(nrhs), beta(nrhs), hh((size_t)(m + 2) * nrhs);
   double* dvec = w.vec;   // [0, nrhs): norms; [nrhs, 2 nrhs): scratch
-  vec_mgs(f, nrhs, nullptr, nullptr, 0, const_cast<double*>(B), ld, nullptr, 0, dvec, 1, s);
+  vec_mgs(f, nrhs, nullptr, nullptr, 0, nullptr, const_cast<double*>(B), ld, nullptr, 0, nullptr, dvec, 1,
+          nullptr, s);
   CUDA_TRY(cudaMemcpyAsync(bn.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  // the residual goes straight into V_0 (stored unnormalized, scale 1 / beta)
   auto residual = [&]() -> spalu_status {
-    vec_spmv(f, nrhs, X, ld, B, ld, w.R, (int)ldv, nullptr, 0, dvec, 1, s);
+    vec_spmv(f, nrhs, X, ld, B, ld, Vj(0), (int)ldv, nullptr, 0, nullptr, dvec, 1, s);
     CUDA_TRY(cudaMemcpyAsync(beta.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SPALU_OK;
@@ -834,13 +858,13 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     bool all = true;
     for (int c = 0; c < nrhs; ++c) all = all && done(c);
     if (all) break;
-    // V_0 = r / beta (finished columns carry zeros)
-    std::vector<double> bsc(nrhs);
-    for (int c = 0; c < nrhs; ++c) bsc[c] = done(c) ? 0.0 : beta[c];
-    CUDA_TRY(cudaMemcpyAsync(dvec + nrhs, bsc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-    note_launch();
-    launch_pdl(scale_kernel, dim3(grid_for(N) / nrhs + 1, nrhs), dim3(256), 0, s, N, nrhs, (const double*)(dvec + nrhs),
-               (const double*)w.R, (int)ldv, Vj(0), (int)ldv);
+    // V_0 = r / beta: r is in V_0, its scale 1 / beta (finished columns: scale 0)
+    std::vector<double> bsc(nrhs), isc(nrhs);
+    for (int c = 0; c < nrhs; ++c) {
+      bsc[c] = done(c) ? 0.0 : beta[c];
+      isc[c] = bsc[c] != 0.0 ? 1.0 / bsc[c] : 0.0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(w.vs, isc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     for (int c = 0; c < nrhs; ++c) {
       std::fill(H[c].begin(), H[c].end(), 0.0);
       std::fill(g[c].begin(), g[c].end(), 0.0);
@@ -849,16 +873,16 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     int jl = -1;
     for (int j = 0; j < m; ++j) {
       // Z_j = M^{-1} V_j (kept), V_{j+1} = A Z_j
-      if ((st = spalu_solve(f, Vj(j), Zj(j), nrhs, (int)ldv, stream)) != SPALU_OK) return st;
-      // modified Gram-Schmidt, each subtraction fused with the next inner product:
-      // h_0 = <A Z_j, V_0> in the product's pass, then w -= h_{i-1} V_{i-1}, h_i = <w, V_i>
-      vec_spmv(f, nrhs, Zj(j), (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, Vj(0), (int)ldv, w.hcol, 0, s);
+      const double* sj = w.vs + (size_t)j * nrhs;
+      if ((st = solve_impl(f, Vj(j), sj, Zj(j), nrhs, (int)ldv, stream)) != SPALU_OK) return st;
+      // modified Gram-Schmidt on the unnormalized basis (vector i = vs_i x V_i), each subtraction
+      // fused with the next inner product: h_0 = <A Z_j, V_0> in the product's pass, then
+      // w -= h_{i-1} V_{i-1}, h_i = <w, V_i>; the last pass gives ||w|| and vs_{j+1} = 1 / ||w||
+      vec_spmv(f, nrhs, Zj(j), (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, Vj(0), (int)ldv, w.vs, w.hcol, 0, s);
       for (int i = 1; i <= j + 1; ++i)
-        vec_mgs(f, nrhs, w.hcol + (size_t)(i - 1) * nrhs, Vj(i - 1), (int)ldv, Vj(j + 1), (int)ldv,
-                i <= j ? Vj(i) : nullptr, (int)ldv, w.hcol + (size_t)i * nrhs, i > j, s);
-      note_launch();
-      launch_pdl(scale_kernel, dim3(grid_for(N) / nrhs + 1, nrhs), dim3(256), 0, s, N, nrhs,
-                 (const double*)(w.hcol + (size_t)(j + 1) * nrhs), (const double*)Vj(j + 1), (int)ldv, Vj(j + 1), (int)ldv);
+        vec_mgs(f, nrhs, w.hcol + (size_t)(i - 1) * nrhs, Vj(i - 1), (int)ldv, w.vs + (size_t)(i - 1) * nrhs,
+                Vj(j + 1), (int)ldv, i <= j ? Vj(i) : nullptr, (int)ldv, w.vs + (size_t)i * nrhs,
+                w.hcol + (size_t)i * nrhs, i > j, i > j ? w.vs + (size_t)(j + 1) * nrhs : nullptr, s);
       CUDA_TRY(cudaMemcpyAsync(hh.data(), w.hcol, sizeof(double) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
       ++it;
@@ -1182,7 +1206,7 @@ void spalu_factor_destroy(spalu_factor_t f) {
   cudaFree(f->arena);
   cudaFree(f->xf);
   GmresWork& w = f->gw;
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.R); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vec);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vs); cudaFree(w.vec);
   delete f;
 }
 
