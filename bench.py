@@ -191,6 +191,7 @@ def run_reference(args):
 # keyed by (kernel, mixed precision); a kernel missing here reports null traffic.  Re-capture
 # after changing one of these kernels.
 PROFILED_TRAFFIC = {
+    ("leaf_lu_kernel+leaf_schur_kernel", True): 835_925_788,   # per launch pair
     ("leaf_solve_kernel", True): 569_567_744,
     ("leaf_bwd_g_kernel", True): 327_993_344,
 }
