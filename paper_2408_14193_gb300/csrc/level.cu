@@ -1150,99 +1150,124 @@ __device__ void parent_ctx(const LevelDev& d, int P, ParentCtx& C) {
   C.kp = d.kk[C.sep];
 }
 
-// Unknowns of a child side restricted to its skeleton, appended to the table.
-__device__ int add_side(const LevelDev& d, int* tab, int n, int posM, int child, int I, int J, int side) {
-  int sg = d.g.box_side(I, J, side);
-  if (sg < 0) return n;
-  int k = d.kk[sg];
-  for (int t = 0; t < k; ++t) {
-    int* e = tab + (size_t)(n + t) * TABW;
-    int pc = d.g.side_pos(side) + d.perm[(size_t)sg * d.capS + t];
-    e[0] = posM + t;
-    e[1] = e[2] = e[3] = e[4] = e[5] = e[6] = -1;
-    e[child == 1 ? 1 : 4] = pc;
-    e[child == 1 ? 2 : 5] = side;
-    e[child == 1 ? 3 : 6] = t;
-    e[7] = d.nodes[(size_t)sg * d.capS + d.perm[(size_t)sg * d.capS + t]];
-  }
-  return n + k;
-}
-
-__device__ int add_corner(const LevelDev& d, int* tab, int n, int posM, int I1, int J1, int c1,
-                          int I2, int J2, int c2) {
-  int cid = c1 >= 0 ? d.g.box_corner(I1, J1, c1) : d.g.box_corner(I2, J2, c2);
-  if (cid < 0) return n;
-  int* e = tab + (size_t)n * TABW;
-  e[0] = posM;
-  e[1] = c1 >= 0 ? d.g.corner_pos(c1) : -1;
-  e[2] = c1 >= 0 ? 4 : -1;
-  e[3] = 0;
-  e[4] = c2 >= 0 ? d.g.corner_pos(c2) : -1;
-  e[5] = c2 >= 0 ? 4 : -1;
-  e[6] = 0;
-  e[7] = d.g.junction_node(cid, d.nx);
-  return n + 1;
-}
+// The table is built in two passes: thread 0 lists the runs of entries (a child side's
+// skeleton, a junction or corner, the separator skeleton) with their first table index and
+// first position in the parent block, then all threads fill the entries.
+struct TabRun {
+  int kind;            // 0: side of child `child`, 1: corner / junction, 2: separator skeleton
+  int n0, cnt, pos;    // first table index, entries, first position in the parent block
+  int child, I, J, side;
+  int I1, J1, c1, I2, J2, c2;
+};
+constexpr int TRUN_MAX = 16;
 
 __global__ void merge_table_kernel(LevelDev d) {
+  __shared__ TabRun runs[TRUN_MAX];
+  __shared__ int nrun_sh, total_sh;
   const int P = blockIdx.x;
-  if (threadIdx.x != 0) return;
   ParentCtx C;
   parent_ctx(d, P, C);
   int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
   const Geo gp = d.gp;
   const int Dp = gp.D();
-  const bool root = gp.bx * gp.by == 1;
-  int n = 0;
-  // sides of P (merged or inherited), then its corners, then the separator skeleton
-  for (int side = 0; side < 4 && !root; ++side) {
-    if (gp.box_side(C.Ip, C.Jp, side) < 0) continue;
-    int pos = gp.side_pos(side);
-    bool split = d.vcut ? (side == SIDE_BOTTOM || side == SIDE_TOP) : (side == SIDE_LEFT || side == SIDE_RIGHT);
-    if (!split) {
-      int child = d.vcut ? (side == SIDE_LEFT ? 1 : 2) : (side == SIDE_BOTTOM ? 1 : 2);
-      int I = child == 1 ? C.I1 : C.I2, J = child == 1 ? C.J1 : C.J2;
-      n = add_side(d, tab, n, pos, child, I, J, side);
-    } else {
-      int n0 = n;
-      n = add_side(d, tab, n, pos, 1, C.I1, C.J1, side);
-      int k1 = n - n0;
-      // junction: vertical cut: bottom -> b1.BR = b2.BL, top -> b1.TR = b2.TL;
-      //           horizontal cut: left -> b1.TL = b2.BL, right -> b1.TR = b2.BR
-      int jc1, jc2;
-      if (d.vcut) { jc1 = side == SIDE_BOTTOM ? C_BR : C_TR; jc2 = side == SIDE_BOTTOM ? C_BL : C_TL; }
-      else { jc1 = side == SIDE_LEFT ? C_TL : C_TR; jc2 = side == SIDE_LEFT ? C_BL : C_BR; }
-      n = add_corner(d, tab, n, pos + k1, C.I1, C.J1, jc1, C.I2, C.J2, jc2);
-      int n1 = n;
-      n = add_side(d, tab, n, pos + (n1 - n0), 2, C.I2, C.J2, side);
+  if (threadIdx.x == 0) {
+    const bool root = gp.bx * gp.by == 1;
+    int n = 0, nr = 0;
+    auto side_run = [&](int pos, int child, int I, int J, int side) {
+      const int sg = d.g.box_side(I, J, side);
+      if (sg < 0) return 0;
+      TabRun& R = runs[nr++];
+      R.kind = 0; R.n0 = n; R.cnt = d.kk[sg]; R.pos = pos; R.child = child; R.I = I; R.J = J; R.side = side;
+      n += R.cnt;
+      return R.cnt;
+    };
+    auto corner_run = [&](int pos, int I1, int J1, int c1, int I2, int J2, int c2) {
+      const int cid = c1 >= 0 ? d.g.box_corner(I1, J1, c1) : d.g.box_corner(I2, J2, c2);
+      if (cid < 0) return 0;
+      TabRun& R = runs[nr++];
+      R.kind = 1; R.n0 = n; R.cnt = 1; R.pos = pos;
+      R.I1 = I1; R.J1 = J1; R.c1 = c1; R.I2 = I2; R.J2 = J2; R.c2 = c2;
+      n += 1;
+      return 1;
+    };
+    // sides of P (merged or inherited), then its corners, then the separator skeleton
+    for (int side = 0; side < 4 && !root; ++side) {
+      if (gp.box_side(C.Ip, C.Jp, side) < 0) continue;
+      const int pos = gp.side_pos(side);
+      const bool split = d.vcut ? (side == SIDE_BOTTOM || side == SIDE_TOP) : (side == SIDE_LEFT || side == SIDE_RIGHT);
+      if (!split) {
+        const int child = d.vcut ? (side == SIDE_LEFT ? 1 : 2) : (side == SIDE_BOTTOM ? 1 : 2);
+        side_run(pos, child, child == 1 ? C.I1 : C.I2, child == 1 ? C.J1 : C.J2, side);
+      } else {
+        const int k1 = side_run(pos, 1, C.I1, C.J1, side);
+        // junction: vertical cut: bottom -> b1.BR = b2.BL, top -> b1.TR = b2.TL;
+        //           horizontal cut: left -> b1.TL = b2.BL, right -> b1.TR = b2.BR
+        int jc1, jc2;
+        if (d.vcut) { jc1 = side == SIDE_BOTTOM ? C_BR : C_TR; jc2 = side == SIDE_BOTTOM ? C_BL : C_TL; }
+        else { jc1 = side == SIDE_LEFT ? C_TL : C_TR; jc2 = side == SIDE_LEFT ? C_BL : C_BR; }
+        const int kj = corner_run(pos + k1, C.I1, C.J1, jc1, C.I2, C.J2, jc2);
+        side_run(pos + k1 + kj, 2, C.I2, C.J2, side);
+      }
     }
+    for (int c = 0; c < 4 && !root; ++c) {
+      if (gp.box_corner(C.Ip, C.Jp, c) < 0) continue;
+      // vertical cut: BL,TL from b1; BR,TR from b2.  horizontal: BL,BR from b1; TL,TR from b2
+      const bool from1 = d.vcut ? (c == C_BL || c == C_TL) : (c == C_BL || c == C_BR);
+      if (from1) corner_run(gp.corner_pos(c), C.I1, C.J1, c, 0, 0, -1);
+      else corner_run(gp.corner_pos(c), 0, 0, -1, C.I2, C.J2, c);
+    }
+    const int ndP = n;
+    {
+      TabRun& R = runs[nr++];
+      R.kind = 2; R.n0 = n; R.cnt = C.kp; R.pos = Dp;
+      n += C.kp;
+    }
+    nrun_sh = nr;
+    total_sh = n;
+    d.pcount[2 * P] = ndP;
+    d.pcount[2 * P + 1] = C.kp;
+    atomicMax(d.lstat + LS_KPMAX, C.kp);
+    atomicMax(d.lstat + LS_DPMAX, ndP);
   }
-  for (int c = 0; c < 4 && !root; ++c) {
-    if (gp.box_corner(C.Ip, C.Jp, c) < 0) continue;
-    // vertical cut: BL,TL from b1; BR,TR from b2.  horizontal: BL,BR from b1; TL,TR from b2
-    bool from1 = d.vcut ? (c == C_BL || c == C_TL) : (c == C_BL || c == C_BR);
-    if (from1) n = add_corner(d, tab, n, gp.corner_pos(c), C.I1, C.J1, c, 0, 0, -1);
-    else n = add_corner(d, tab, n, gp.corner_pos(c), 0, 0, -1, C.I2, C.J2, c);
-  }
-  const int ndP = n;
-  // separator skeleton: side RIGHT/TOP of child 1 (owner) = LEFT/BOTTOM of child 2
-  {
-    int s1 = d.vcut ? SIDE_RIGHT : SIDE_TOP, s2 = d.vcut ? SIDE_LEFT : SIDE_BOTTOM;
-    int sg = C.sep;
-    for (int t = 0; t < C.kp; ++t) {
-      int* e = tab + (size_t)(n + t) * TABW;
-      int q = d.perm[(size_t)sg * d.capS + t];
+  __syncthreads();
+  const int nr = nrun_sh, total = total_sh;
+  for (int x = threadIdx.x; x < total; x += blockDim.x) {
+    int ri = 0;
+    while (ri + 1 < nr && x >= runs[ri + 1].n0) ++ri;
+    const TabRun& R = runs[ri];
+    const int t = x - R.n0;
+    int* e = tab + (size_t)x * TABW;
+    if (R.kind == 0) {
+      const int sg = d.g.box_side(R.I, R.J, R.side);
+      const int q = d.perm[(size_t)sg * d.capS + t];
+      const int pc = d.g.side_pos(R.side) + q;
+      e[0] = R.pos + t;
+      e[1] = e[2] = e[3] = e[4] = e[5] = e[6] = -1;
+      e[R.child == 1 ? 1 : 4] = pc;
+      e[R.child == 1 ? 2 : 5] = R.side;
+      e[R.child == 1 ? 3 : 6] = t;
+      e[7] = d.nodes[(size_t)sg * d.capS + q];
+    } else if (R.kind == 1) {
+      const int cid = R.c1 >= 0 ? d.g.box_corner(R.I1, R.J1, R.c1) : d.g.box_corner(R.I2, R.J2, R.c2);
+      e[0] = R.pos;
+      e[1] = R.c1 >= 0 ? d.g.corner_pos(R.c1) : -1;
+      e[2] = R.c1 >= 0 ? 4 : -1;
+      e[3] = 0;
+      e[4] = R.c2 >= 0 ? d.g.corner_pos(R.c2) : -1;
+      e[5] = R.c2 >= 0 ? 4 : -1;
+      e[6] = 0;
+      e[7] = d.g.junction_node(cid, d.nx);
+    } else {
+      // separator skeleton: side RIGHT/TOP of child 1 (owner) = LEFT/BOTTOM of child 2
+      const int s1 = d.vcut ? SIDE_RIGHT : SIDE_TOP, s2 = d.vcut ? SIDE_LEFT : SIDE_BOTTOM;
+      const int sg = C.sep;
+      const int q = d.perm[(size_t)sg * d.capS + t];
       e[0] = Dp + t;
       e[1] = d.g.side_pos(s1) + q; e[2] = s1; e[3] = t;
       e[4] = d.g.side_pos(s2) + q; e[5] = s2; e[6] = t;
       e[7] = d.nodes[(size_t)sg * d.capS + q];
     }
-    n += C.kp;
   }
-  d.pcount[2 * P] = ndP;
-  d.pcount[2 * P + 1] = C.kp;
-  atomicMax(d.lstat + LS_KPMAX, C.kp);
-  atomicMax(d.lstat + LS_DPMAX, ndP);
 }
 
 // M[a][b] = sum over the children holding both unknowns of the child's block, where the
@@ -1951,7 +1976,7 @@ template <typename T>
 static void merge_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   const int np = d.gp.nbox();
   note_launch();
-  merge_table_kernel<<<np, 32, 0, s>>>(d);
+  merge_table_kernel<<<np, 128, 0, s>>>(d);
   {
     long long nmax = (long long)p.ldFp;
     int gx = (int)((nmax * nmax + 255) / 256);
