@@ -106,8 +106,8 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
 spalu_status spalu_factor_numeric(spalu_factor_t f, const int* rowptr, const int* colind,
                                   const double* val, int nnz, spalu_stream_t stream);
 
-/* Same, with rowptr / colind / val in host memory: the values are copied to the device
- * inside the call (the pattern is copied only when it changed). */
+/* Same, with rowptr / colind / val in host memory, copied to the device inside the call
+ * (page-locked host memory gives full copy bandwidth). */
 spalu_status spalu_factor_numeric_host(spalu_factor_t f, const int* rowptr, const int* colind,
                                        const double* val, int nnz, spalu_stream_t stream);
 
@@ -115,6 +115,24 @@ spalu_status spalu_factor_numeric_host(spalu_factor_t f, const int* rowptr, cons
  * leading dimension ld).  X may alias B.  Does not synchronise. */
 spalu_status spalu_solve(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
                          spalu_stream_t stream);
+
+/* Batched numeric factorization of n independent problems (Sec. 4.3 per problem): problem i
+ * factors f[i] (created for its own grid) from the device CSR arrays rowptr[i], colind[i],
+ * val[i] (nnz[i] entries) on streams[i].  Every problem's copies and kernels are enqueued
+ * first, then each stream is synchronised and its factor finished, so problems on different
+ * streams run concurrently.  Host arrays of n pointers / counts; the handles and the CSR
+ * arrays stay owned by the caller; a stream may serve several problems (they then run in
+ * order).  Returns the first non-OK status (SPALU_ERR_ARG before anything is enqueued when an
+ * argument is invalid); every problem that was enqueued is finished either way. */
+spalu_status spalu_factor_numeric_batch(int n, const spalu_factor_t* f, const int* const* rowptr,
+                                        const int* const* colind, const double* const* val,
+                                        const int* nnz, spalu_stream_t const* streams);
+
+/* Batched direct solve: spalu_solve(f[i], B[i], X[i], nrhs[i], ld[i], streams[i]) for
+ * i < n, enqueued in order; does not synchronise.  Returns the first non-OK status (the
+ * problems after it are not enqueued). */
+spalu_status spalu_solve_batch(int n, const spalu_factor_t* f, const double* const* B, double* const* X,
+                               const int* nrhs, const int* ld, spalu_stream_t const* streams);
 
 /* Iterative refinement by right-preconditioned GMRES(m) with the factor as preconditioner
  * and an FP64 residual with the last factored matrix: every column is iterated until

@@ -100,6 +100,7 @@ struct spalu_factor_s {
   bool factored = false;
   float* xf = nullptr;       // FP32 solve vector of the mixed path, N x xf_cols
   int xf_cols = 0;
+  int* hpin = nullptr;       // page-locked readback after a factorization: err, kumax, lstat
   cudaStream_t last_stream = nullptr;
   GmresWork gw;
   PhaseTimer timer;
@@ -160,17 +161,6 @@ struct Carver {
     return p;
   }
 };
-
-spalu_status read_err(spalu_factor_t f, cudaStream_t s) {
-  int h = 0;
-  CUDA_TRY(cudaMemcpyAsync(&h, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  if (h & ERR_SINGULAR) return SPALU_ERR_SINGULAR;
-  if (h & ERR_NONFINITE) return SPALU_ERR_NONFINITE;
-  if (h & ERR_TIMEOUT) return SPALU_ERR_TIMEOUT;
-  if (h & ERR_CAPACITY) return SPALU_ERR_UNSUPPORTED;
-  return SPALU_OK;
-}
 
 // ------------------------------------------------------------ GMRES helper kernels
 // Vector kernels over N rows x nrhs columns: one thread per row and RC columns (blockIdx.y =
@@ -600,6 +590,11 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
         delete f;
         return SPALU_ERR_ALLOC;
       }
+      if (cudaMallocHost(&f->hpin, sizeof(int) * (2 + LS_N * (L + 1))) != cudaSuccess) {
+        cudaFree(f->arena);
+        delete f;
+        return SPALU_ERR_ALLOC;
+      }
     }
   }
   f->leaf.rowptr = f->rowptr;
@@ -620,7 +615,10 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   return SPALU_OK;
 }
 
-static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
+// A factorization in two halves: enqueue() puts every kernel and the readback of the error
+// word, the leaf bandwidth and the level counters on the stream; finish() waits for that
+// stream and sets the solve capacities.  A batch enqueues all problems before finishing any.
+static spalu_status factor_enqueue(spalu_factor_t f, cudaStream_t s) {
   const int L = f->nd->L;
   PhaseTimer& tm = f->timer;
   int t_all = tm.begin("factor", s);
@@ -648,19 +646,35 @@ static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
   }
   tm.end(t_all, s);
   CUDA_TRY(cudaGetLastError());
-  spalu_status st = read_err(f, s);
-  int ku = 30;
-  if (cudaMemcpy(&ku, f->leaf.kumax, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SPALU_ERR_CUDA;
-  f->kumax = ku;
-  f->lstat.assign((size_t)LS_N * (L + 1), 0);
-  if (cudaMemcpy(f->lstat.data(), f->d_lstat, sizeof(int) * f->lstat.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return SPALU_ERR_CUDA;
+  CUDA_TRY(cudaMemcpyAsync(f->hpin, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(f->hpin + 1, f->leaf.kumax, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(f->hpin + 2, f->d_lstat, sizeof(int) * LS_N * (L + 1), cudaMemcpyDeviceToHost, s));
+  return SPALU_OK;
+}
+
+static spalu_status factor_finish(spalu_factor_t f, cudaStream_t s) {
+  const int L = f->nd->L;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const int h = f->hpin[0];
+  spalu_status st = SPALU_OK;
+  if (h & ERR_SINGULAR) st = SPALU_ERR_SINGULAR;
+  else if (h & ERR_NONFINITE) st = SPALU_ERR_NONFINITE;
+  else if (h & ERR_TIMEOUT) st = SPALU_ERR_TIMEOUT;
+  else if (h & ERR_CAPACITY) st = SPALU_ERR_UNSUPPORTED;
+  f->kumax = f->hpin[1];
+  f->lstat.assign(f->hpin + 2, f->hpin + 2 + LS_N * (L + 1));
   // the solve kernels hold a segment's (or separator's) right-hand-side block in shared memory
   for (int l = 1; l <= L && st == SPALU_OK; ++l)
     if (!level_solve_caps(f->lev[l], f->lstat.data() + LS_N * l, &f->caps[l])) st = SPALU_ERR_UNSUPPORTED;
   f->factored = (st == SPALU_OK);
   f->last_stream = s;
   return st;
+}
+
+static spalu_status factor_run(spalu_factor_t f, cudaStream_t s) {
+  spalu_status st = factor_enqueue(f, s);
+  if (st != SPALU_OK) return st;
+  return factor_finish(f, s);
 }
 
 spalu_status spalu_factor_numeric(spalu_factor_t f, const int* rowptr, const int* colind,
@@ -672,6 +686,45 @@ spalu_status spalu_factor_numeric(spalu_factor_t f, const int* rowptr, const int
   CUDA_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return factor_run(f, s);
+}
+
+spalu_status spalu_factor_numeric_batch(int n, const spalu_factor_t* f, const int* const* rowptr,
+                                        const int* const* colind, const double* const* val, const int* nnz,
+                                        spalu_stream_t const* streams) {
+  if (n < 0 || (n > 0 && (!f || !rowptr || !colind || !val || !nnz || !streams))) return SPALU_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!f[i] || !rowptr[i] || !colind[i] || !val[i] || nnz[i] < 0 || nnz[i] > f[i]->nnz_cap) return SPALU_ERR_ARG;
+  spalu_status first = SPALU_OK;
+  std::vector<char> queued(n, 0);
+  for (int i = 0; i < n; ++i) {          // every problem's copies and kernels, on its stream
+    spalu_factor_t g = f[i];
+    cudaStream_t s = (cudaStream_t)streams[i];
+    g->nnz = nnz[i];
+    spalu_status st = SPALU_OK;
+    if (cudaMemcpyAsync(g->rowptr, rowptr[i], (g->N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(g->colind, colind[i], (size_t)nnz[i] * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(g->val, val[i], (size_t)nnz[i] * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      st = SPALU_ERR_CUDA;
+    if (st == SPALU_OK) st = factor_enqueue(g, s);
+    if (st == SPALU_OK) queued[i] = 1;
+    else { g->factored = false; if (first == SPALU_OK) first = st; }
+  }
+  for (int i = 0; i < n; ++i) {          // then wait for each and set its solve capacities
+    if (!queued[i]) continue;
+    const spalu_status st = factor_finish(f[i], (cudaStream_t)streams[i]);
+    if (st != SPALU_OK && first == SPALU_OK) first = st;
+  }
+  return first;
+}
+
+spalu_status spalu_solve_batch(int n, const spalu_factor_t* f, const double* const* B, double* const* X,
+                               const int* nrhs, const int* ld, spalu_stream_t const* streams) {
+  if (n < 0 || (n > 0 && (!f || !B || !X || !nrhs || !ld || !streams))) return SPALU_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    const spalu_status st = spalu_solve(f[i], B[i], X[i], nrhs[i], ld[i], streams[i]);
+    if (st != SPALU_OK) return st;
+  }
+  return SPALU_OK;
 }
 
 spalu_status spalu_factor_numeric_host(spalu_factor_t f, const int* rowptr, const int* colind,
@@ -1205,6 +1258,7 @@ void spalu_factor_destroy(spalu_factor_t f) {
   if (!f) return;
   cudaFree(f->arena);
   cudaFree(f->xf);
+  cudaFreeHost(f->hpin);
   GmresWork& w = f->gw;
   cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vs); cudaFree(w.vec);
   delete f;

@@ -77,6 +77,8 @@ SIGNATURES = [
     ("spalu_nd_destroy", None, [_P]),
     ("spalu_factor_create", _I, [_P, _P, _P]),
     ("spalu_factor_numeric", _I, [_P, _P, _P, _P, _I, _P]),
+    ("spalu_factor_numeric_batch", _I, [_I, _P, _P, _P, _P, _P, _P]),
+    ("spalu_solve_batch", _I, [_I, _P, _P, _P, _P, _P, _P]),
     ("spalu_factor_numeric_host", _I, [_P, _P, _P, _P, _I, _P]),
     ("spalu_solve", _I, [_P, _P, _P, _I, _I, _P]),
     ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
@@ -298,6 +300,40 @@ class Factor:
         if h:
             self.lib.spalu_factor_destroy(h)
             self.handle = None
+
+
+def factor_batch(factors, csrs, streams):
+    """Numeric factorization of independent problems: factors[i] from csrs[i] = (rowptr, colind,
+    val) device tensors on streams[i]; all problems are enqueued before any is waited for."""
+    import torch
+    n = len(factors)
+    if not (len(csrs) == n and len(streams) == n):
+        raise ValueError("factors, csrs and streams must have the same length")
+    P = ctypes.c_void_p * n
+    hs = P(*[f.handle for f in factors])
+    rp = P(*[_dev_ptr(c[0], torch.int32).value for c in csrs])
+    ci = P(*[_dev_ptr(c[1], torch.int32).value for c in csrs])
+    va = P(*[_dev_ptr(c[2], torch.float64).value for c in csrs])
+    nz = (ctypes.c_int * n)(*[int(c[2].numel()) for c in csrs])
+    st = P(*[_stream_ptr(s).value for s in streams])
+    _check(load_library().spalu_factor_numeric_batch(n, hs, rp, ci, va, nz, st), "spalu_factor_numeric_batch")
+
+
+def solve_batch(factors, Bs, Xs, streams):
+    """X_i = spaLU_i^{-1} B_i on streams[i] for every problem (device float64 tensors shaped
+    (nrhs, N) or (N,)); enqueued only, not synchronised."""
+    import torch
+    n = len(factors)
+    if not (len(Bs) == n and len(Xs) == n and len(streams) == n):
+        raise ValueError("factors, Bs, Xs and streams must have the same length")
+    P = ctypes.c_void_p * n
+    hs = P(*[f.handle for f in factors])
+    bp = P(*[_dev_ptr(B, torch.float64).value for B in Bs])
+    xp = P(*[_dev_ptr(X, torch.float64).value for X in Xs])
+    nr = (ctypes.c_int * n)(*[1 if B.dim() == 1 else int(B.shape[0]) for B in Bs])
+    ld = (ctypes.c_int * n)(*[f.N for f in factors])
+    st = P(*[_stream_ptr(s).value for s in streams])
+    _check(load_library().spalu_solve_batch(n, hs, bp, xp, nr, ld, st), "spalu_solve_batch")
 
 
 class Predictor:

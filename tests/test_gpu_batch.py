@@ -1,0 +1,75 @@
+"""Batched factorization and solve (independent problems of different sizes on several
+streams, through spalu_factor_numeric_batch / spalu_solve_batch) against the same problems
+factored and solved one at a time, and one of them against the CPU oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.nd import nested_dissection
+from oracle.spalu import Options as OOpts, factor as ofactor, solve as osolve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _problem(n, seed, dev):
+    P = W.make_problem("diffusion", n, seed=seed, nrhs=1)
+    A = P.A
+    csr = (torch.from_numpy(A.indptr).to(dev), torch.from_numpy(A.indices).to(dev), torch.from_numpy(A.data).to(dev))
+    return P, csr, torch.from_numpy(np.ascontiguousarray(P.B.T)).to(dev)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_one_at_a_time(precision):
+    from paper_2408_14193_gb300 import Factor, NestedDissection, factor_batch, solve_batch
+    dev = torch.device("cuda:0")
+    sizes = [63, 127, 63, 255, 127, 63, 31]
+    nds = {n: NestedDissection(n) for n in set(sizes)}
+    probs = [_problem(n, 100 + i, dev) for i, n in enumerate(sizes)]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    fs = [Factor(nds[n], eps_id=1e-8, symmetric=1, precision=precision) for n in sizes]
+    st = [streams[i % 3] for i in range(len(sizes))]
+    torch.cuda.synchronize()
+    factor_batch(fs, [p[1] for p in probs], st)
+    Xs = [torch.empty_like(p[2]) for p in probs]
+    solve_batch(fs, [p[2] for p in probs], Xs, st)
+    torch.cuda.synchronize()
+    for i, n in enumerate(sizes):
+        g = Factor(nds[n], eps_id=1e-8, symmetric=1, precision=precision)
+        g.factor(*probs[i][1])
+        Y = g.solve(probs[i][2])
+        torch.cuda.synchronize()
+        x, y = Xs[i].cpu().numpy(), Y.cpu().numpy()
+        # the solve adds separator contributions with atomics, in a run-dependent order: FP64
+        # rounding for the plain form; FP32 rounding of an FP32 factor for the mixed one (its
+        # direct solve is only accurate to ~1e-4 at this eps, refinement restores 1e-10)
+        tol = 1e-12 if precision == 0 else 1e-3
+        assert np.linalg.norm(x - y) <= tol * np.linalg.norm(y), (i, n)
+    # one problem of the batch against the oracle (FP64 parity bar)
+    if precision == 0:
+        P = probs[3][0]
+        xo = osolve(ofactor(P.A, nested_dissection(255, 255), OOpts(eps=1e-8, symmetric=True)), P.B)
+        x = Xs[3].cpu().numpy().T
+        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_batch_rejects_bad_arguments():
+    from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError, factor_batch
+    dev = torch.device("cuda:0")
+    nd = NestedDissection(63)
+    f = Factor(nd, eps_id=1e-8, symmetric=1)
+    _, csr, _ = _problem(63, 5, dev)
+    with pytest.raises(ValueError):
+        factor_batch([f], [csr, csr], [torch.cuda.current_stream()])
+    big = torch.zeros(csr[2].numel() * 10, dtype=torch.float64, device=dev)
+    with pytest.raises(SpaluError):
+        factor_batch([f], [(csr[0], csr[1], big)], [torch.cuda.current_stream()])
