@@ -212,3 +212,45 @@ def test_mixed_precision_refined(kind, n, eps):
     x = X.cpu().numpy().T
     res = np.linalg.norm(P.B - P.A.matvec(x), axis=0) / np.linalg.norm(P.B, axis=0)
     assert np.all(res <= 1e-10), res
+
+
+# ------------------------------------------------------------------ right-hand-side chunks
+@pytest.mark.parametrize("nrhs", [17, 20])
+def test_many_rhs_ragged_chunks(nrhs):
+    """More right-hand sides than one solve chunk (16) and one GMRES vector chunk (8), with a
+    ragged last chunk: the FP64 form against the oracle, the mixed form refined to 1e-10."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    n = 63
+    P = W.make_problem("diffusion", n, seed=41, nrhs=nrhs)
+    X, _, _ = _gpu_solve(P, 1e-8)
+    Xo = osolve(ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-8, symmetric=True)), P.B)
+    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+    rp, ci, va, B = _dev(P)
+    f = Factor(NestedDissection(n), eps_id=1e-6, symmetric=1, precision=1)
+    f.factor(rp, ci, va)
+    Xm = f.solve(B)
+    it, rel = f.refine(B, Xm)
+    x = Xm.cpu().numpy().T
+    res = np.linalg.norm(P.B - P.A.matvec(x), axis=0) / np.linalg.norm(P.B, axis=0)
+    assert res.shape == (nrhs,) and np.all(res <= 1e-10), res
+    # every column solved as if alone: column 17 of the batch against a one-column solve
+    c = nrhs - 1
+    g = Factor(NestedDissection(n), eps_id=1e-8, symmetric=1)
+    g.factor(rp, ci, va)
+    Y = g.solve(B[c:c + 1].contiguous())
+    torch.cuda.synchronize()
+    assert np.linalg.norm(Y.cpu().numpy()[0] - X[:, c]) <= 1e-12 * np.linalg.norm(X[:, c])
+
+
+def test_zero_rhs_is_a_no_op():
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    P = W.make_problem("diffusion", 31, seed=42, nrhs=1)
+    rp, ci, va, _ = _dev(P)
+    f = Factor(NestedDissection(31), eps_id=1e-8, symmetric=1)
+    f.factor(rp, ci, va)
+    lib = f.lib
+    dummy = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    import ctypes
+    st = lib.spalu_solve(f.handle, ctypes.c_void_p(dummy.data_ptr()), ctypes.c_void_p(dummy.data_ptr()), 0,
+                         f.N, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
