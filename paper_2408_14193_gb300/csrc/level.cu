@@ -1609,13 +1609,15 @@ __device__ __forceinline__ void upper_sweep(T* y, int ldy, int n, const T* LU, s
 constexpr int INV_MAX = 64;
 
 // v[:, c] = L~^{-1} v[q, c] (lower) or U^{-1} v[:, c] (upper) for c < nc, n <= INV_MAX, A the
-// inverted block (ld lda) in shared or global memory.  256 threads, at most 4 outputs each.
-template <typename T, bool LOWER>
+// inverted block (ld lda) in shared or global memory.  NT threads (the CTA), each holding at
+// most INV_MAX x 16 / NT outputs.
+template <typename T, bool LOWER, int NT = 256>
 __device__ __forceinline__ void tri_apply(T* v, int ldv, int n, const T* A, size_t lda, const int* q, int nc) {
-  T acc[4];
+  constexpr int PER = (INV_MAX * 16 + NT - 1) / NT;   // outputs per thread (nc <= 16)
+  T acc[PER];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int x = threadIdx.x + 256 * t;
+  for (int t = 0; t < PER; ++t) {
+    const int x = threadIdx.x + NT * t;
     acc[t] = T(0);
     if (x < n * nc) {
       const int i = x % n, c = x / n;
@@ -1633,8 +1635,8 @@ __device__ __forceinline__ void tri_apply(T* v, int ldv, int n, const T* A, size
   }
   __syncthreads();
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int x = threadIdx.x + 256 * t;
+  for (int t = 0; t < PER; ++t) {
+    const int x = threadIdx.x + NT * t;
     if (x < n * nc) v[(x % n) + (size_t)ldv * (x / n)] = acc[t];
   }
   __syncthreads();
@@ -1727,8 +1729,8 @@ size_t invert_smem() { return 2 * sizeof(T) * INV_MAX * INV_MAX + sizeof(int) * 
 
 // Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
-template <typename T>
-__global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
   pdl_enter();
   extern __shared__ double smd[];
   const int sid = blockIdx.x;
@@ -1784,7 +1786,7 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
                     [&](int a, int c, T acc) { vr[a + e * c] -= acc; });
       __syncthreads();
     }
-    if (r <= INV_MAX) tri_apply<T, true>(vr, e, r, LUs, ldl, pvs, nc);
+    if (r <= INV_MAX) tri_apply<T, true, NT>(vr, e, r, LUs, ldl, pvs, nc);
     else lower_sweep<T>(vr, e, r, LUs, ldl, pvs, nc);
     __syncthreads();
     if (k > 0) {      // b_s -= Z y_r
@@ -1801,7 +1803,7 @@ __global__ void __launch_bounds__(256, 4) seg_solve_kernel(LevelDev d, SolveCaps
                     [&](int a, int c, T acc) { vr[a + e * c] -= acc; });
       __syncthreads();
     }
-    if (r <= INV_MAX) tri_apply<T, false>(vr, e, r, LUs, ldl, pvs, nc);
+    if (r <= INV_MAX) tri_apply<T, false, NT>(vr, e, r, LUs, ldl, pvs, nc);
     else upper_sweep<T>(vr, e, r, LUs, ldl, ivs, nc);
     __syncthreads();
     if (k > 0) {      // x_s -= T x_r
@@ -2052,14 +2054,18 @@ bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
 
 template <typename T>
 static void level_solve(const LevelDev& d, const SolveCaps& sc, T* X, int nrhs, VecLayout lay, int bwd, cudaStream_t s) {
-  cudaFuncSetAttribute(seg_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.seg_smem);
+  cudaFuncSetAttribute(seg_solve_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.seg_smem);
+  cudaFuncSetAttribute(seg_solve_kernel<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.seg_smem);
   cudaFuncSetAttribute(sep_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.sep_smem);
   for (int c0 = 0; c0 < nrhs; c0 += SC) {
     const int nc = nrhs - c0 < SC ? nrhs - c0 : SC;
     T* Xc = X + (size_t)(c0 / SC) * lay.chunk;
     auto seg_go = [&](int dir) {
       note_launch();
-      launch_pdl(seg_solve_kernel<T>, dim3(d.g.nseg()), dim3(256), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
+      if (d.capS <= 32)     // small segments: 2-warp CTAs, four times as many resident per SM
+        launch_pdl(seg_solve_kernel<T, 64>, dim3(d.g.nseg()), dim3(64), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
+      else
+        launch_pdl(seg_solve_kernel<T, 256>, dim3(d.g.nseg()), dim3(256), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
     };
     auto sep_go = [&](int dir) {
       note_launch();
