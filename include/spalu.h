@@ -128,6 +128,14 @@ spalu_status spalu_factor_numeric_batch(int n, const spalu_factor_t* f, const in
                                         const int* const* colind, const double* const* val,
                                         const int* nnz, spalu_stream_t const* streams);
 
+/* Autotuning of the level solves (scheduling, not in the paper): for every level, time the
+ * segment and separator solve kernels with 2-warp and 8-warp CTAs (the four combinations, on
+ * a zero vector of nrhs columns, 1 <= nrhs <= 16, CUDA events on stream) and keep the fastest
+ * for later solves of this handle, also across re-factorizations.  Requires a factored
+ * handle (SPALU_ERR_STATE otherwise); synchronises the stream.  Results do not depend on the
+ * choice beyond the order of the atomic separator updates. */
+spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream);
+
 /* Batched direct solve: spalu_solve(f[i], B[i], X[i], nrhs[i], ld[i], streams[i]) for
  * i < n, enqueued in order; does not synchronise.  Returns the first non-OK status (the
  * problems after it are not enqueued). */

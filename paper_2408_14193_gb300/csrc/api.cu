@@ -101,6 +101,7 @@ struct spalu_factor_s {
   float* xf = nullptr;       // FP32 solve vector of the mixed path, N x xf_cols
   int xf_cols = 0;
   int* hpin = nullptr;       // page-locked readback after a factorization: err, kumax, lstat
+  std::vector<int> tuned_nt; // [2 * (L + 1)] solve CTA widths chosen by spalu_tune_solve (0: none)
   cudaStream_t last_stream = nullptr;
   GmresWork gw;
   PhaseTimer timer;
@@ -664,8 +665,13 @@ static spalu_status factor_finish(spalu_factor_t f, cudaStream_t s) {
   f->kumax = f->hpin[1];
   f->lstat.assign(f->hpin + 2, f->hpin + 2 + LS_N * (L + 1));
   // the solve kernels hold a segment's (or separator's) right-hand-side block in shared memory
-  for (int l = 1; l <= L && st == SPALU_OK; ++l)
+  for (int l = 1; l <= L && st == SPALU_OK; ++l) {
     if (!level_solve_caps(f->lev[l], f->lstat.data() + LS_N * l, &f->caps[l])) st = SPALU_ERR_UNSUPPORTED;
+    if ((int)f->tuned_nt.size() == 2 * (L + 1) && f->tuned_nt[2 * l] > 0) {
+      f->caps[l].seg_nt = f->tuned_nt[2 * l];
+      f->caps[l].sep_nt = f->tuned_nt[2 * l + 1];
+    }
+  }
   f->factored = (st == SPALU_OK);
   f->last_stream = s;
   return st;
@@ -715,6 +721,69 @@ spalu_status spalu_factor_numeric_batch(int n, const spalu_factor_t* f, const in
     if (st != SPALU_OK && first == SPALU_OK) first = st;
   }
   return first;
+}
+
+spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream) {
+  if (!f || nrhs < 1 || nrhs > 16) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = f->nd->L, N = f->N;
+  // the solve's working vector (zeros: the timing does not depend on the values)
+  void* W = nullptr;
+  VecLayout lay{1, N, 16LL * N};
+  double* tmp = nullptr;
+  if (f->leaf.fp32) {
+    if (f->xf_cols < 16) {
+      cudaFree(f->xf);
+      f->xf = nullptr;
+      f->xf_cols = 0;
+      if (cudaMalloc(&f->xf, sizeof(float) * (size_t)N * 16) != cudaSuccess) return SPALU_ERR_ALLOC;
+      f->xf_cols = 16;
+    }
+    CUDA_TRY(cudaMemsetAsync(f->xf, 0, sizeof(float) * (size_t)N * 16, s));
+    W = f->xf;
+    lay = VecLayout{16, 1, 16LL * N};
+  } else {
+    if (cudaMalloc(&tmp, sizeof(double) * (size_t)N * nrhs) != cudaSuccess) return SPALU_ERR_ALLOC;
+    CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(double) * (size_t)N * nrhs, s));
+    W = tmp;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  f->tuned_nt.assign(2 * (L + 1), 0);
+  const int cand[4][2] = {{256, 256}, {64, 256}, {256, 64}, {64, 64}};
+  spalu_status st = SPALU_OK;
+  for (int l = 1; l <= L && st == SPALU_OK; ++l) {
+    float best = 1e30f;
+    int bi = 0;
+    for (int c = 0; c < 4; ++c) {
+      SolveCaps sc = f->caps[l];
+      sc.seg_nt = cand[c][0];
+      sc.sep_nt = cand[c][1];
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {        // the first repetition warms up
+        cudaEventRecord(e0, s);
+        launch_level_solve_fwd(f->lev[l], sc, W, nrhs, lay, s);
+        launch_level_solve_bwd(f->lev[l], sc, W, nrhs, lay, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = SPALU_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tmin = ms < tmin ? ms : tmin;
+      }
+      if (tmin < best) { best = tmin; bi = c; }
+    }
+    f->tuned_nt[2 * l] = cand[bi][0];
+    f->tuned_nt[2 * l + 1] = cand[bi][1];
+    f->caps[l].seg_nt = cand[bi][0];
+    f->caps[l].sep_nt = cand[bi][1];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(tmp);
+  CUDA_TRY(cudaGetLastError());
+  return st;
 }
 
 spalu_status spalu_solve_batch(int n, const spalu_factor_t* f, const double* const* B, double* const* X,

@@ -1821,8 +1821,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(Level
 // Separator of each parent: forward y_p = L^{-1} P b_p, then b_dP -= Z y_p added atomically
 // (a boundary unknown is shared by up to four parents; the order of their contributions is
 // not fixed); backward x_p = U^{-1} (y_p - W x_dP).
-template <typename T>
-__global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
   pdl_enter();
   extern __shared__ double smd[];
   const int P = blockIdx.x;
@@ -1869,7 +1869,7 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
   if (!bwd) stage_lu();
   __syncthreads();          // rows_sm, y (and the LU block) are read by other threads below
   if (!bwd) {
-    if (kp <= INV_MAX) tri_apply<T, true>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
+    if (kp <= INV_MAX) tri_apply<T, true, NT>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
     else lower_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
     __syncthreads();
     // b_dP -= Z y_p, Z = M[dP rows, separator columns]
@@ -1915,7 +1915,7 @@ __global__ void __launch_bounds__(256, 4) sep_solve_kernel(LevelDev d, SolveCaps
     __syncthreads();
     stage_lu();             // the panel is consumed: U takes the LU block
     __syncthreads();
-    if (kp <= INV_MAX) tri_apply<T, false>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
+    if (kp <= INV_MAX) tri_apply<T, false, NT>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
     else upper_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, ivs, nc);
   }
   __syncthreads();
@@ -2047,6 +2047,9 @@ bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
   sc.pcap = (int)mx(0, mn((long long)(sc.vrows / 2 + 1) * (sc.vrows / 2 + 1), (budget - seg_fixed) / (2 * TB)));
   sc.qcap = (int)mx(0, mn((long long)(sc.drows | 1) * sc.yrows, (budget - sep_fixed) / TB));
   sc.seg_smem = (size_t)(seg_fixed + 2 * TB * sc.pcap);
+  // CTA widths before any tuning: 2-warp segment CTAs where segments have at most 32 unknowns
+  sc.seg_nt = d.capS <= 32 ? 64 : 256;
+  sc.sep_nt = 256;
   sc.sep_smem = (size_t)(sep_fixed + TB * mx((long long)sc.lucap * sc.lucap, sc.qcap));
   *out = sc;
   return true;
@@ -2056,20 +2059,24 @@ template <typename T>
 static void level_solve(const LevelDev& d, const SolveCaps& sc, T* X, int nrhs, VecLayout lay, int bwd, cudaStream_t s) {
   cudaFuncSetAttribute(seg_solve_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.seg_smem);
   cudaFuncSetAttribute(seg_solve_kernel<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.seg_smem);
-  cudaFuncSetAttribute(sep_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.sep_smem);
+  cudaFuncSetAttribute(sep_solve_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.sep_smem);
+  cudaFuncSetAttribute(sep_solve_kernel<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.sep_smem);
   for (int c0 = 0; c0 < nrhs; c0 += SC) {
     const int nc = nrhs - c0 < SC ? nrhs - c0 : SC;
     T* Xc = X + (size_t)(c0 / SC) * lay.chunk;
     auto seg_go = [&](int dir) {
       note_launch();
-      if (d.capS <= 32)     // small segments: 2-warp CTAs, four times as many resident per SM
+      if (sc.seg_nt == 64)  // 2-warp CTAs: four times as many resident per SM
         launch_pdl(seg_solve_kernel<T, 64>, dim3(d.g.nseg()), dim3(64), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
       else
         launch_pdl(seg_solve_kernel<T, 256>, dim3(d.g.nseg()), dim3(256), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
     };
     auto sep_go = [&](int dir) {
       note_launch();
-      launch_pdl(sep_solve_kernel<T>, dim3(d.gp.nbox()), dim3(256), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
+      if (sc.sep_nt == 64)
+        launch_pdl(sep_solve_kernel<T, 64>, dim3(d.gp.nbox()), dim3(64), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
+      else
+        launch_pdl(sep_solve_kernel<T, 256>, dim3(d.gp.nbox()), dim3(256), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
     };
     if (!bwd) {
       if (d.g.nseg() > 0) seg_go(0);

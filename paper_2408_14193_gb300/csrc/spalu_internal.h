@@ -172,6 +172,7 @@ struct SolveCaps {
   int drows;     // separator: parent-boundary rows staged
   int yrows;     // separator: skeleton rows of the right-hand-side block (>= every kp)
   size_t seg_smem, sep_smem;
+  int seg_nt, sep_nt;   // CTA widths of the segment / separator solve kernels (64 or 256)
 };
 
 struct LeafDev {

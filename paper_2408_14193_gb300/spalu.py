@@ -79,6 +79,7 @@ SIGNATURES = [
     ("spalu_factor_numeric", _I, [_P, _P, _P, _P, _I, _P]),
     ("spalu_factor_numeric_batch", _I, [_I, _P, _P, _P, _P, _P, _P]),
     ("spalu_solve_batch", _I, [_I, _P, _P, _P, _P, _P, _P]),
+    ("spalu_tune_solve", _I, [_P, _I, _P]),
     ("spalu_factor_numeric_host", _I, [_P, _P, _P, _P, _I, _P]),
     ("spalu_solve", _I, [_P, _P, _P, _I, _I, _P]),
     ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
@@ -223,6 +224,10 @@ class Factor:
         _check(self.lib.spalu_solve(self.handle, _dev_ptr(B, torch.float64), _dev_ptr(X, torch.float64),
                                     nrhs, self.N, _stream_ptr(stream)), "spalu_solve")
         return X
+
+    def tune_solve(self, nrhs: int = 16, stream=None):
+        """Time the level-solve kernels with 2- and 8-warp CTAs per level and keep the fastest."""
+        _check(self.lib.spalu_tune_solve(self.handle, nrhs, _stream_ptr(stream)), "spalu_tune_solve")
 
     def refine(self, B, X, stream=None, check=True):
         """GMRES refinement of X in place; returns (iterations, relative residuals)."""

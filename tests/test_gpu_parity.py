@@ -254,3 +254,31 @@ def test_zero_rhs_is_a_no_op():
     st = lib.spalu_solve(f.handle, ctypes.c_void_p(dummy.data_ptr()), ctypes.c_void_p(dummy.data_ptr()), 0,
                          f.N, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tuned_solve_matches_default(precision):
+    """spalu_tune_solve only changes CTA widths of the level solves: same solution (up to the
+    order of the atomic separator updates), kept across a re-factorization."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    n = 255
+    P = W.make_problem("diffusion", n, seed=43, nrhs=4)
+    rp, ci, va, B = _dev(P)
+    f = Factor(NestedDissection(n), eps_id=1e-8, symmetric=1, precision=precision)
+    f.factor(rp, ci, va)
+    X0 = f.solve(B)
+    f.tune_solve(4)
+    X1 = f.solve(B)
+    f.factor(rp, ci, va)
+    X2 = f.solve(B)
+    torch.cuda.synchronize()
+    tol = 1e-12 if precision == 0 else 1e-3
+    for X in (X1, X2):
+        assert torch.linalg.norm(X - X0) <= tol * torch.linalg.norm(X0)
+
+
+def test_tune_requires_a_factor():
+    from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError
+    f = Factor(NestedDissection(31), eps_id=1e-8, symmetric=1)
+    with pytest.raises(SpaluError):
+        f.tune_solve(1)
