@@ -536,7 +536,7 @@ def run_ours(args):
         "mixed_adaptive": {"value": noml_value, "unit": "DOF/s", "ms_per_step": noml["ms"] / args.steps,
                            "relres_max": noml["relres"], "gmres_iters": noml["iters"],
                            "id_passes": sum(lv["passes"] for lv in noml["st"]["levels"])},
-        "predictor": dict(pred_info, id_passes=sum(lv["passes"] for lv in st["levels"]),
+        "predictor": dict(pred_info, margin=PRED_MARGIN, id_passes=sum(lv["passes"] for lv in st["levels"]),
                           predicted=sum(lv["predicted"] for lv in st["levels"]),
                           fallbacks=sum(lv["fallbacks"] for lv in st["levels"])),
         "speedup_vs_fp64": value / base_value,
