@@ -70,6 +70,13 @@ typedef struct {
   int gmres_m;                /* restart length of the refinement, default 30 */
   int gmres_maxit;            /* total iteration cap of the refinement, default 200 */
   double gmres_tol;           /* target ||b - A x|| / ||b||, default 1e-10 */
+  int spars_ctas;             /* performance only: the sparsification's per-segment shared
+                                 memory is cut to what lets min(spars_ctas, ceil(segments of
+                                 the level / SMs)) segments (at most what the register file
+                                 holds) run at once on an SM; a segment that does not fit
+                                 keeps its sketch and frontal rows in global memory (results
+                                 agree up to rounding).  0 = size for the largest segment the
+                                 geometry allows.  Default 4. */
 } spalu_opts;
 
 /* Fill *o with the defaults listed above (eps_id = 1e-8, precision 0, symmetric 0). */
@@ -135,6 +142,17 @@ spalu_status spalu_factor_numeric_batch(int n, const spalu_factor_t* f, const in
  * handle (SPALU_ERR_STATE otherwise); synchronises the stream.  Results do not depend on the
  * choice beyond the order of the atomic separator updates. */
 spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream);
+
+/* Autotuning of the sparsification's occupancy (scheduling, not in the paper): re-factor the
+ * handle's last matrix once per candidate shared-memory budget of the sparsify kernel (the
+ * uncut worst case, then budgets for 2, 3, 4, 6, 8 and 12 resident segments per SM, see
+ * spars_ctas), time every level's sparsification with CUDA events on stream, and keep the
+ * fastest budget per level for later factorizations of this handle.  Ends with one more
+ * factorization under the chosen budgets, so the handle is factored on return.  Requires a
+ * factored handle (SPALU_ERR_STATE otherwise); synchronises the stream; leaves the phase
+ * timings of spalu_factor_stats as they were.  The factors agree with untuned ones up to
+ * rounding. */
+spalu_status spalu_tune_factor(spalu_factor_t f, spalu_stream_t stream);
 
 /* Batched direct solve: spalu_solve(f[i], B[i], X[i], nrhs[i], ld[i], streams[i]) for
  * i < n, enqueued in order; does not synchronise.  Returns the first non-OK status (the

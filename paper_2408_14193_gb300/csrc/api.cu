@@ -376,6 +376,7 @@ void spalu_default_opts(spalu_opts* o) {
   o->gmres_m = 30;
   o->gmres_maxit = 200;
   o->gmres_tol = 1e-10;
+  o->spars_ctas = 4;
 }
 
 const char* spalu_status_string(spalu_status s) {
@@ -472,7 +473,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   if (!nd || !o || !out) return SPALU_ERR_ARG;
   *out = nullptr;
   if (!(o->eps_id >= 0.0) || o->p_oversample < 0 || o->h0 < 1 || o->near_radius < 0 ||
-      o->gmres_m < 1 || o->gmres_maxit < 0)
+      o->gmres_m < 1 || o->gmres_maxit < 0 || o->spars_ctas < 0 || o->spars_ctas > 32)
     return SPALU_ERR_ARG;
   if (o->precision != 0 && o->precision != 1) return SPALU_ERR_ARG;
   if (leaf_init_tables() != cudaSuccess) return SPALU_ERR_CUDA;
@@ -507,8 +508,25 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     size_t need = sparsify_smem_need(p.capS, o->symmetric, o->h0, o->p_oversample, tb);
     size_t lim = 160 * 1024;
     size_t mn = sparsify_smem_min(p.capS, o->symmetric, o->h0, o->p_oversample, tb);
-    p.spars_smem = std::min(need, std::max(lim, mn));
-    p.spars_global = need > p.spars_smem;
+    const size_t full = std::min(need, std::max(lim, mn));
+    // trade worst-case room for resident segments (the phases of one segment are
+    // latency-bound): as many per SM as the level has segments per SM, up to spars_ctas;
+    // segments that do not fit the budget fall back to global scratch inside the kernel
+    auto budget = [&](int ctas) {
+      const size_t b = ctas > 0 ? sparsify_smem_budget(tb == 4, p.capS, ctas) : 0;
+      return b >= mn ? std::min(full, b) : full;
+    };
+    p.spars_smem = full;
+    if (o->spars_ctas > 0 && p.g.nseg() > 0) {
+      const int nsm = sm_count();
+      p.spars_smem = budget((int)std::min<long long>(o->spars_ctas, ((long long)p.g.nseg() + nsm - 1) / nsm));
+    }
+    size_t least = p.spars_smem;
+    for (int c = 0; c < SPARS_NCAND; ++c) {
+      p.spars_cand[c] = budget(SPARS_CAND_CTAS[c]);
+      least = std::min(least, p.spars_cand[c]);
+    }
+    p.spars_global = need > least;   // global scratch for every budget the tuner may pick
   }
   // plan the arena (two passes: sizes, then pointers)
   for (int pass = 0; pass < 2; ++pass) {
@@ -783,6 +801,55 @@ spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream)
   cudaEventDestroy(e1);
   cudaFree(tmp);
   CUDA_TRY(cudaGetLastError());
+  return st;
+}
+
+spalu_status spalu_tune_factor(spalu_factor_t f, spalu_stream_t stream) {
+  if (!f) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = f->nd->L;
+  PhaseTimer& tm = f->timer;
+  tm.collect();
+  const bool was_on = tm.on;
+  const auto keep_ms = tm.ms;
+  const auto keep_count = tm.count;
+  std::vector<size_t> best_smem(L + 1, 0);
+  std::vector<double> best_ms(L + 1, 1e30);
+  for (int l = 1; l <= L; ++l) best_smem[l] = f->plan[l].spars_smem;
+  spalu_status st = SPALU_OK;
+  for (int c = 0; c < SPARS_NCAND && st == SPALU_OK; ++c) {
+    bool fresh = false;                  // skip budgets that repeat an earlier one everywhere
+    for (int l = 1; l <= L && !fresh; ++l) {
+      bool seen = false;
+      for (int c2 = 0; c2 < c; ++c2) seen = seen || f->plan[l].spars_cand[c2] == f->plan[l].spars_cand[c];
+      fresh = !seen;
+    }
+    if (!fresh) continue;
+    for (int l = 1; l <= L; ++l) f->plan[l].spars_smem = f->plan[l].spars_cand[c];
+    std::vector<double> tmin(L + 1, 1e30);
+    for (int rep = 0; rep < 3 && st == SPALU_OK; ++rep) {   // the first repetition warms up
+      tm.on = true;
+      tm.ms.clear();
+      tm.count.clear();
+      st = factor_run(f, s);
+      tm.collect();
+      if (st != SPALU_OK || rep == 0) continue;
+      for (int l = 1; l <= L; ++l) {
+        auto it = tm.ms.find("sparsify_l" + std::to_string(l));
+        if (it != tm.ms.end()) tmin[l] = std::min(tmin[l], it->second);
+      }
+    }
+    for (int l = 1; l <= L; ++l)
+      if (tmin[l] < best_ms[l]) { best_ms[l] = tmin[l]; best_smem[l] = f->plan[l].spars_cand[c]; }
+  }
+  for (int l = 1; l <= L; ++l) f->plan[l].spars_smem = best_smem[l];
+  tm.on = false;
+  if (st == SPALU_OK) st = factor_run(f, s);
+  tm.collect();
+  tm.on = was_on;
+  tm.ms = keep_ms;
+  tm.count = keep_count;
   return st;
 }
 

@@ -1944,6 +1944,38 @@ size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes) {
   return 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64 + halves * (e + hcap) * tbytes;
 }
 
+int sm_count() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+size_t sparsify_smem_budget(int fp32, int capS, int ctas) {
+  if (ctas < 1) return 0;
+  int dev = 0, per_sm = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaFuncAttributes fa{};
+  cudaError_t e;
+  const int threads = (capS <= 16 ? NW_SMALL : NW) * 32;
+  if (capS <= 16)
+    e = fp32 ? cudaFuncGetAttributes(&fa, sparsify_kernel<float, NW_SMALL>)
+             : cudaFuncGetAttributes(&fa, sparsify_kernel<double, NW_SMALL>);
+  else
+    e = fp32 ? cudaFuncGetAttributes(&fa, sparsify_kernel<float, NW>)
+             : cudaFuncGetAttributes(&fa, sparsify_kernel<double, NW>);
+  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+  // no more CTAs than the register file holds: shared memory beyond that buys nothing
+  const int regs = fa.numRegs > 0 ? fa.numRegs : 64;
+  const int by_regs = 65536 / (regs * threads);
+  if (by_regs >= 1 && ctas > by_regs) ctas = by_regs;
+  const long long share = ((long long)per_sm / ctas) & ~255LL;   // allocation granularity
+  const long long dyn = share - reserved - (long long)fa.sharedSizeBytes;
+  return dyn > 0 ? (size_t)(dyn & ~255LL) : 0;
+}
+
 void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
   int n = d.g.nseg() * LEAF;
   if (n == 0) return;
@@ -1957,9 +1989,13 @@ static void sparsify_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t 
   note_launch();
   if (d.capS <= 16) {       // finest segments: two warps each, many segments per SM
     cudaFuncSetAttribute(sparsify_kernel<T, NW_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(sparsify_kernel<T, NW_SMALL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     sparsify_kernel<T, NW_SMALL><<<d.g.nseg(), NW_SMALL * 32, smem, s>>>(d, smem);
   } else {
     cudaFuncSetAttribute(sparsify_kernel<T, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(sparsify_kernel<T, NW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     sparsify_kernel<T, NW><<<d.g.nseg(), NW * 32, smem, s>>>(d, smem);
   }
   const int ism = (int)invert_smem<T>();

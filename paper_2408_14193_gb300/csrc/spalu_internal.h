@@ -102,6 +102,10 @@ struct Geo {
   }
 };
 
+// Resident sparsify CTAs per SM that the occupancy autotuner tries (0: the uncut worst case)
+constexpr int SPARS_NCAND = 7;
+constexpr int SPARS_CAND_CTAS[SPARS_NCAND] = {0, 2, 3, 4, 6, 8, 12};
+
 struct LevelPlan {          // host-side description of level l (1..L)
   int l;
   int vcut;                 // level-l cut is vertical (children left/right)
@@ -114,6 +118,7 @@ struct LevelPlan {          // host-side description of level l (1..L)
   int Ycap;                 // rows of the per-segment sketch buffer
   size_t spars_smem;        // dynamic shared memory of the sparsify kernel
   int spars_global;         // 1 when the worst case needs global scratch
+  size_t spars_cand[SPARS_NCAND];   // candidate values of spars_smem (autotuner)
 };
 
 // Device view of one level, passed by value to the kernels.
@@ -272,6 +277,11 @@ void launch_pred_export(const float* feat, const int* tgt, int nseg, int p, floa
 
 size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes);
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes);
+// Dynamic shared memory per sparsify CTA that lets `ctas` of them be resident on one SM
+// (the variant that a level of segment capacity capS launches; 0 when that many cannot fit)
+size_t sparsify_smem_budget(int fp32, int capS, int ctas);
+// Streaming multiprocessors of the current device
+int sm_count();
 
 spalu_status residual_noalloc(int n, const int* rowptr, const int* colind, const double* val,
                               const double* B, const double* X, int nrhs, int ld, double* relres,

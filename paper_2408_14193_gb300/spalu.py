@@ -50,6 +50,7 @@ class Options(ctypes.Structure):
         ("gmres_m", ctypes.c_int),
         ("gmres_maxit", ctypes.c_int),
         ("gmres_tol", ctypes.c_double),
+        ("spars_ctas", ctypes.c_int),
     ]
 
     @classmethod
@@ -80,6 +81,7 @@ SIGNATURES = [
     ("spalu_factor_numeric_batch", _I, [_I, _P, _P, _P, _P, _P, _P]),
     ("spalu_solve_batch", _I, [_I, _P, _P, _P, _P, _P, _P]),
     ("spalu_tune_solve", _I, [_P, _I, _P]),
+    ("spalu_tune_factor", _I, [_P, _P]),
     ("spalu_factor_numeric_host", _I, [_P, _P, _P, _P, _I, _P]),
     ("spalu_solve", _I, [_P, _P, _P, _I, _I, _P]),
     ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
@@ -228,6 +230,11 @@ class Factor:
     def tune_solve(self, nrhs: int = 16, stream=None):
         """Time the level-solve kernels with 2- and 8-warp CTAs per level and keep the fastest."""
         _check(self.lib.spalu_tune_solve(self.handle, nrhs, _stream_ptr(stream)), "spalu_tune_solve")
+
+    def tune_factor(self, stream=None):
+        """Re-factor the last matrix under each candidate shared-memory budget of the sparsify
+        kernel and keep the fastest per level (the handle is factored on return)."""
+        _check(self.lib.spalu_tune_factor(self.handle, _stream_ptr(stream)), "spalu_tune_factor")
 
     def refine(self, B, X, stream=None, check=True):
         """GMRES refinement of X in place; returns (iterations, relative residuals)."""

@@ -277,8 +277,53 @@ def test_tuned_solve_matches_default(precision):
         assert torch.linalg.norm(X - X0) <= tol * torch.linalg.norm(X0)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sparsify_budgets_and_tuning_match_oracle(precision):
+    """The sparsify kernel's shared-memory budget (spars_ctas, and the per-level choice of
+    spalu_tune_factor) only moves segments between shared and global scratch: under every
+    budget, including ones that push the finest level's sketch into global memory, the FP64
+    form stays within the oracle parity bar and the mixed form within its FP32 bound; the
+    tuned choice is kept across a re-factorization."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    n = 255
+    eps = 1e-8 if precision == 0 else 1e-6
+    P = W.make_problem("diffusion", n, seed=44, nrhs=2)
+    rp, ci, va, B = _dev(P)
+    nd = NestedDissection(n)
+    Xo = osolve(ofactor(P.A, nested_dissection(n, n), OOpts(eps=eps, symmetric=True)), P.B)
+    bar = 1e-6 if precision == 0 else 1e-2
+
+    def err(f):
+        x = f.solve(B).cpu().numpy().T
+        return np.linalg.norm(x - Xo) / np.linalg.norm(Xo)
+
+    for ctas in (0, 4, 12, 16):
+        f = Factor(nd, eps_id=eps, symmetric=1, precision=precision, spars_ctas=ctas)
+        f.factor(rp, ci, va)
+        assert err(f) <= bar, ctas
+        if ctas == 4:
+            f.set_timing(True)
+            f.factor(rp, ci, va)
+            before = f.stats()["timing_ms"]
+            f.tune_factor()
+            assert f.stats()["timing_ms"] == before        # the tuner leaves the timings alone
+            f.set_timing(False)
+            assert err(f) <= bar
+            f.factor(rp, ci, va)
+            assert err(f) <= bar
+
+
+def test_bad_sparsify_budget_is_rejected():
+    from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError
+    for ctas in (-1, 33):
+        with pytest.raises(SpaluError):
+            Factor(NestedDissection(31), eps_id=1e-8, symmetric=1, spars_ctas=ctas)
+
+
 def test_tune_requires_a_factor():
     from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError
     f = Factor(NestedDissection(31), eps_id=1e-8, symmetric=1)
     with pytest.raises(SpaluError):
         f.tune_solve(1)
+    with pytest.raises(SpaluError):
+        f.tune_factor()
