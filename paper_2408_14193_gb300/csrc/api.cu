@@ -209,12 +209,15 @@ __device__ void column_sums(double (&s)[RC], int c0, int nrhs, double* part, uns
   if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
-// y = b - A x (b null: y = A x); when part is set, out[c] = <y_c, d_c> (d null: ||y_c||, sq)
-__global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int* rowptr, const int* colind,
-                                                  const double* val, const double* x, int ldx,
-                                                  const double* b, int ldb, double* y, int ldy,
-                                                  const double* d, int ldd, const double* dscale,
-                                                  double* part, unsigned* cnt, double* out, int sq) {
+// y = b - A x (b null: y = A x); when part is set, out[c] = <y_c, d_c> (d null: ||y_c||, sq).
+// No array aliases another, so the loads of b and d need not wait for the stores of y.
+__global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int* __restrict__ rowptr,
+                                                  const int* __restrict__ colind,
+                                                  const double* __restrict__ val, const double* __restrict__ x,
+                                                  int ldx, const double* __restrict__ b, int ldb,
+                                                  double* __restrict__ y, int ldy, const double* __restrict__ d,
+                                                  int ldd, const double* dscale, double* part, unsigned* cnt,
+                                                  double* out, int sq) {
   pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
@@ -225,20 +228,20 @@ __global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int*
     double acc[RC];
 #pragma unroll
     for (int k = 0; k < RC; ++k) acc[k] = 0.0;
-    const int p1 = rowptr[r + 1];
-    for (int p = rowptr[r]; p < p1; ++p) {
-      const int col = colind[p];
-      const double v = val[p];
+    const int p0 = __ldg(rowptr + r), p1 = __ldg(rowptr + r + 1);
+    for (int p = p0; p < p1; ++p) {
+      const int col = __ldg(colind + p);
+      const double v = __ldg(val + p);
 #pragma unroll
       for (int k = 0; k < RC; ++k)
-        if (k < nc) acc[k] += v * x[col + (size_t)ldx * (c0 + k)];
+        if (k < nc) acc[k] += v * __ldg(x + col + (size_t)ldx * (c0 + k));
     }
 #pragma unroll
     for (int k = 0; k < RC; ++k)
       if (k < nc) {
-        const double yv = b ? b[r + (size_t)ldb * (c0 + k)] - acc[k] : acc[k];
+        const double yv = b ? __ldcs(b + r + (size_t)ldb * (c0 + k)) - acc[k] : acc[k];
         y[r + (size_t)ldy * (c0 + k)] = yv;
-        s[k] += yv * (d ? d[r + (size_t)ldd * (c0 + k)] : yv);
+        s[k] += yv * (d ? __ldcs(d + r + (size_t)ldd * (c0 + k)) : yv);
       }
   }
   if (part) column_sums(s, c0, nrhs, part, cnt, out, sq, dscale);
@@ -246,9 +249,13 @@ __global__ void __launch_bounds__(VB, 4) spmv_kernel(int n, int nrhs, const int*
 
 // One modified Gram-Schmidt pass on unnormalized basis vectors (vector i stands for
 // scale_i x stored_i): w_c -= h_c ps_c p_c (skipped when p is null), then
-// out[c] = qs_c <w_c, q_c> (q null: ||w_c|| (sq) and inv_out[c] = 1 / out[c])
-__global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const double* h, const double* p, int ldp,
-                                                 const double* ps, double* w, int ldw, const double* q,
+// out[c] = qs_c <w_c, q_c> (q null: ||w_c|| (sq) and inv_out[c] = 1 / out[c]).  The operands
+// of four columns of a row are loaded before their stores (w, p and q never alias), so a row
+// costs two memory round trips rather than two per column.
+constexpr int RH = RC / 2;
+__global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const double* h,
+                                                 const double* __restrict__ p, int ldp, const double* ps,
+                                                 double* __restrict__ w, int ldw, const double* __restrict__ q,
                                                  int ldq, const double* qs, double* part, unsigned* cnt,
                                                  double* out, int sq, double* inv_out) {
   pdl_enter();
@@ -262,22 +269,35 @@ __global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const doubl
   }
   for (long long r = blockIdx.x * (long long)VB + threadIdx.x; r < n; r += (long long)gridDim.x * VB) {
 #pragma unroll
-    for (int k = 0; k < RC; ++k)
-      if (k < nc) {
-        double wv = w[r + (size_t)ldw * (c0 + k)];
-        if (p) {
-          wv -= hc[k] * p[r + (size_t)ldp * (c0 + k)];
-          w[r + (size_t)ldw * (c0 + k)] = wv;
-        }
-        s[k] += wv * (q ? q[r + (size_t)ldq * (c0 + k)] : wv);
+    for (int k0 = 0; k0 < RC; k0 += RH) {
+      double wv[RH], pv[RH], qv[RH];
+#pragma unroll
+      for (int j = 0; j < RH; ++j) {
+        const int k = k0 + j;
+        wv[j] = k < nc ? w[r + (size_t)ldw * (c0 + k)] : 0.0;
+        pv[j] = (p && k < nc) ? __ldcs(p + r + (size_t)ldp * (c0 + k)) : 0.0;
+        qv[j] = (q && k < nc) ? __ldcs(q + r + (size_t)ldq * (c0 + k)) : 0.0;
       }
+#pragma unroll
+      for (int j = 0; j < RH; ++j) {
+        const int k = k0 + j;
+        if (k < nc) {
+          if (p) {
+            wv[j] -= hc[k] * pv[j];
+            w[r + (size_t)ldw * (c0 + k)] = wv[j];
+          }
+          s[k] += wv[j] * (q ? qv[j] : wv[j]);
+        }
+      }
+    }
   }
   column_sums(s, c0, nrhs, part, cnt, out, sq, q ? qs : nullptr, inv_out);
 }
 
 // X_c += sum_i y[i][c] Z_i,c for i = 0..k-1, in that order (Z_i = Z + i * ldz * nrhs)
-__global__ void __launch_bounds__(VB, 4) combine_kernel(int n, int nrhs, int k, const double* y,
-                                                     const double* Z, size_t ldz, double* X, int ldx) {
+__global__ void __launch_bounds__(VB, 4) combine_kernel(int n, int nrhs, int k, const double* __restrict__ y,
+                                                     const double* __restrict__ Z, size_t ldz,
+                                                     double* __restrict__ X, int ldx) {
   pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
