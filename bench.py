@@ -488,13 +488,12 @@ def run_ours(args):
     g.factor_host(rp_h, ci_h, val_h)
     g.tune_factor()
     g.tune_solve(NRHS)
-    g.solve_host(B_h, refine=True, out=X_h)
+    g.factor_solve_host(rp_h, ci_h, val_h, B_h, refine=True, out=X_h)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_rel = 0.0
     for _ in range(args.steps):
-        g.factor_host(rp_h, ci_h, val_h)
-        Xh, _, rel = g.solve_host(B_h, refine=True, out=X_h)
+        Xh, _, rel = g.factor_solve_host(rp_h, ci_h, val_h, B_h, refine=True, out=X_h)
         e2e_rel = max(e2e_rel, float(np.max(rel)))
     e2e_s = time.perf_counter() - t0
     del g

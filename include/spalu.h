@@ -175,6 +175,20 @@ spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs
 spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
                               int refine, int* iters, double* relres, spalu_stream_t stream);
 
+/* Factor and solve from host memory in one call (Secs. 4.3-4.4): the numeric factorization of
+ * the host CSR arrays (as spalu_factor_numeric_host), then X = spaLU^{-1} B refined as
+ * spalu_refine when refine != 0 (as spalu_solve_host).  The upload of B runs on a second
+ * stream owned by the handle while the factorization's kernels run; B and X live in device
+ * buffers the handle keeps (grown on demand, freed with it), so a repeated call allocates
+ * nothing.  Host arrays: rowptr (N + 1), colind and val (nnz), B and X (nrhs columns of
+ * leading dimension ld >= N; page-locked memory gives full copy bandwidth).  Synchronises
+ * stream.  Returns the factorization's status if it fails (nothing is solved), else the
+ * solve's (SPALU_ERR_NOCONV still fills X). */
+spalu_status spalu_factor_solve_host(spalu_factor_t f, const int* rowptr, const int* colind,
+                                     const double* val, int nnz, const double* B, double* X, int nrhs,
+                                     int ld, int refine, int* iters, double* relres,
+                                     spalu_stream_t stream);
+
 /* JSON summary of the last factorization: per level the segment sizes and ranks, the
  * largest separator skeleton, the number of IDs computed ("passes"), of predicted one-pass
  * IDs and of those that fell back to the adaptive schedule; q~ (Sec. 6); device bytes

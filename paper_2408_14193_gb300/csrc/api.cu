@@ -102,6 +102,11 @@ struct spalu_factor_s {
   int xf_cols = 0;
   int* hpin = nullptr;       // page-locked readback after a factorization: err, kumax, lstat
   std::vector<int> tuned_nt; // [2 * (L + 1)] solve CTA widths chosen by spalu_tune_solve (0: none)
+  cudaStream_t up = nullptr; // second stream of spalu_factor_solve_host (right-hand-side upload)
+  cudaEvent_t up_go = nullptr, up_done = nullptr;
+  double* hB = nullptr;      // device B and X of spalu_factor_solve_host, hcap doubles each
+  double* hX = nullptr;
+  size_t hcap = 0;
   cudaStream_t last_stream = nullptr;
   GmresWork gw;
   PhaseTimer timer;
@@ -1172,6 +1177,61 @@ spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int 
   return st != SPALU_OK ? st : st2;
 }
 
+spalu_status spalu_factor_solve_host(spalu_factor_t f, const int* rowptr, const int* colind,
+                                     const double* val, int nnz, const double* B, double* X, int nrhs,
+                                     int ld, int refine, int* iters, double* relres,
+                                     spalu_stream_t stream) {
+  if (!f || !rowptr || !colind || !val || nnz < 0 || nnz > f->nnz_cap || !B || !X || nrhs < 0 || ld < f->N)
+    return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)f->N, need = N * (size_t)nrhs;
+  if (!f->up) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&f->up, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&f->up_go, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&f->up_done, cudaEventDisableTiming));
+  }
+  if (need > f->hcap) {
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaStreamSynchronize(f->up));
+    cudaFree(f->hB);
+    cudaFree(f->hX);
+    f->hB = f->hX = nullptr;
+    f->hcap = 0;
+    if (cudaMalloc(&f->hB, need * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&f->hX, need * sizeof(double)) != cudaSuccess)
+      return SPALU_ERR_ALLOC;
+    f->hcap = need;
+  }
+  f->nnz = nnz;
+  CUDA_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+  // B follows the matrix (so that it does not slow the matrix upload) on the second stream,
+  // after everything earlier on stream (an earlier call's solve may still read hB)
+  CUDA_TRY(cudaEventRecord(f->up_go, s));
+  CUDA_TRY(cudaStreamWaitEvent(f->up, f->up_go, 0));
+  if (nrhs > 0)
+    CUDA_TRY(cudaMemcpy2DAsync(f->hB, N * sizeof(double), B, (size_t)ld * sizeof(double), N * sizeof(double),
+                               nrhs, cudaMemcpyHostToDevice, f->up));
+  CUDA_TRY(cudaEventRecord(f->up_done, f->up));
+  spalu_status st = factor_enqueue(f, s);
+  if (st == SPALU_OK) st = factor_finish(f, s);
+  if (st != SPALU_OK) {
+    cudaStreamSynchronize(f->up);
+    return st;
+  }
+  if (nrhs == 0) return SPALU_OK;
+  CUDA_TRY(cudaStreamWaitEvent(s, f->up_done, 0));
+  st = spalu_solve(f, f->hB, f->hX, nrhs, f->N, stream);
+  if (st == SPALU_OK && refine) st = spalu_refine(f, f->hB, f->hX, nrhs, f->N, iters, relres, stream);
+  if (st != SPALU_OK && st != SPALU_ERR_NOCONV) return st;
+  if (cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), f->hX, N * sizeof(double), N * sizeof(double), nrhs,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return SPALU_ERR_CUDA;
+  return st;
+}
+
 spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
   if (!f || !json || cap == 0) return SPALU_ERR_ARG;
   if (!f->factored) return SPALU_ERR_STATE;
@@ -1417,6 +1477,14 @@ void spalu_factor_destroy(spalu_factor_t f) {
   cudaFreeHost(f->hpin);
   GmresWork& w = f->gw;
   cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vs); cudaFree(w.vec);
+  if (f->up) {
+    cudaStreamSynchronize(f->up);
+    cudaStreamDestroy(f->up);
+    cudaEventDestroy(f->up_go);
+    cudaEventDestroy(f->up_done);
+  }
+  cudaFree(f->hB);
+  cudaFree(f->hX);
   delete f;
 }
 

@@ -86,6 +86,7 @@ SIGNATURES = [
     ("spalu_solve", _I, [_P, _P, _P, _I, _I, _P]),
     ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     ("spalu_solve_host", _I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    ("spalu_factor_solve_host", _I, [_P, _P, _P, _P, _I, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_stats", _I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     ("spalu_residual_noalloc", _I, [_P, _P, _P, _I, _I, _P, _P]),
     ("spalu_set_timing", _I, [_P, _I]),
@@ -265,6 +266,31 @@ class Factor:
         _check(self.lib.spalu_solve_host(self.handle, B.ctypes.data, X.ctypes.data, nrhs, self.N,
                                          1 if refine else 0, ctypes.byref(it), rel.ctypes.data,
                                          _stream_ptr(stream)), "spalu_solve_host")
+        return X, it.value, rel
+
+    def factor_solve_host(self, rowptr: np.ndarray, colind: np.ndarray, val: np.ndarray, B: np.ndarray,
+                          refine: bool = False, stream=None, out: np.ndarray | None = None):
+        """spalu_factor_solve_host: factor the host CSR matrix and solve for the host B (shape
+        (nrhs, N)) in one call, the upload of B overlapping the factorization.  Returns
+        (X, iterations, relative residuals); ``out`` as in solve_host."""
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        colind = np.ascontiguousarray(colind, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        nrhs = 1 if B.ndim == 1 else B.shape[0]
+        if out is not None:
+            if out.shape != B.shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous float64 array shaped like B")
+            X = out
+        else:
+            X = np.empty_like(B)
+        it = ctypes.c_int(0)
+        rel = np.zeros(nrhs)
+        _check(self.lib.spalu_factor_solve_host(self.handle, rowptr.ctypes.data, colind.ctypes.data,
+                                                val.ctypes.data, int(val.size), B.ctypes.data, X.ctypes.data,
+                                                nrhs, self.N, 1 if refine else 0, ctypes.byref(it),
+                                                rel.ctypes.data, _stream_ptr(stream)),
+               "spalu_factor_solve_host")
         return X, it.value, rel
 
     def residual_noalloc(self, B, X, stream=None):

@@ -152,6 +152,36 @@ def test_solve_aliasing_and_host_entry_points():
     assert np.all(res <= 1e-10)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_factor_solve_host_matches_separate_calls(precision):
+    """spalu_factor_solve_host (B uploaded on a second stream during the factorization, device
+    buffers kept by the handle) gives what spalu_factor_numeric_host + spalu_solve_host give:
+    the direct solve to rounding (atomic separator updates), the refined one to 1e-10; repeated
+    calls with more right-hand sides grow the buffers; no right-hand sides only factors."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError
+    n = 127
+    P = W.make_problem("diffusion", n, seed=45, nrhs=3)
+    nd = NestedDissection(n)
+    eps = 1e-8 if precision == 0 else 1e-6
+    Bh = np.ascontiguousarray(P.B.T)
+    g = Factor(nd, eps_id=eps, symmetric=1, precision=precision)
+    g.factor_host(P.A.indptr, P.A.indices, P.A.data)
+    X0, _, _ = g.solve_host(Bh)
+    f = Factor(nd, eps_id=eps, symmetric=1, precision=precision)
+    X1, _, _ = f.factor_solve_host(P.A.indptr, P.A.indices, P.A.data, Bh[:1])
+    X2, _, _ = f.factor_solve_host(P.A.indptr, P.A.indices, P.A.data, Bh)
+    tol = 1e-12 if precision == 0 else 1e-3      # mixed: FP32 atomic order
+    assert np.linalg.norm(X2 - X0) <= tol * np.linalg.norm(X0)
+    assert np.linalg.norm(X1 - X0[:1]) <= tol * np.linalg.norm(X0[:1])
+    X3, it, rel = f.factor_solve_host(P.A.indptr, P.A.indices, P.A.data, Bh, refine=True)
+    res = np.linalg.norm(P.B - P.A.matvec(X3.T), axis=0) / np.linalg.norm(P.B, axis=0)
+    assert it >= 1 and np.all(res <= 1e-10) and np.allclose(rel, res, rtol=1e-3, atol=1e-13)
+    X4, _, _ = f.factor_solve_host(P.A.indptr, P.A.indices, P.A.data, np.zeros((0, n * n)))
+    assert X4.shape == (0, n * n)
+    with pytest.raises(SpaluError):                 # nnz above the handle's capacity
+        f.factor_solve_host(P.A.indptr, P.A.indices, np.zeros(6 * n * n), Bh)
+
+
 def test_errors_are_reported_not_raised_on_device():
     from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError
     nd = NestedDissection(31)
