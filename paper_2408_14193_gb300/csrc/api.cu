@@ -596,6 +596,11 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
       d.g = p.g; d.gp = p.gp;
       d.capS = p.capS; d.ldF = p.ldF; d.ldFp = p.ldFp; d.Ycap = p.Ycap; d.sepcap = p.sepcap;
       d.cnt = cv.take<int>(nseg);
+      d.order = cv.take<int>(nseg);
+      // levels with at least two segments per SM and segments that can exceed 16 unknowns:
+      // the sparsify CTAs take the largest first (the finest level's segments are all alike,
+      // and there index order keeps neighbouring segments' reads together)
+      d.use_order = (long long)nseg >= 2LL * sm_count() && p.capS > 16 ? 1 : 0;
       d.kk = cv.take<int>(nseg);
       d.hs = cv.take<int>(nseg);
       d.nodes = cv.take<int>((size_t)nseg * p.capS);
@@ -1022,8 +1027,17 @@ static void vec_spmv(spalu_factor_t f, int nrhs, const double* x, int ldx, const
              ldx, b, ldb, y, ldy, d, ldd, ds, out ? f->gw.part : nullptr, f->gw.cnt, out, sq);
 }
 
+// dl (optional): after every update of X, X is also copied to the host array dl->h on the
+// stream dl->s, so the copy of the final X overlaps the last residual; dl->n counts the copies
+struct HostDownload {
+  double* h;
+  int ldh;
+  cudaStream_t s;
+  cudaEvent_t ev;
+  int n;
+};
 static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
-                                int* iters, double* relres, spalu_stream_t stream);
+                                int* iters, double* relres, spalu_stream_t stream, HostDownload* dl = nullptr);
 
 spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
                           int* iters, double* relres, spalu_stream_t stream) {
@@ -1035,7 +1049,7 @@ spalu_status spalu_refine(spalu_factor_t f, const double* B, double* X, int nrhs
 }
 
 static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
-                                int* iters, double* relres, spalu_stream_t stream) {
+                                int* iters, double* relres, spalu_stream_t stream, HostDownload* dl) {
   if (!f || !B || !X || nrhs < 0 || ld < f->N) return SPALU_ERR_ARG;
   if (!f->factored) return SPALU_ERR_STATE;
   if (nrhs == 0) return SPALU_OK;
@@ -1138,6 +1152,13 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     note_launch();
     launch_pdl(combine_kernel, vec_grid(N, nrhs), dim3(VB), 0, s, N, nrhs, kdim, (const double*)w.hcol,
                (const double*)w.Z, ldv, X, ld);
+    if (dl) {        // X changes only here: its copy runs while the residual is checked
+      CUDA_TRY(cudaEventRecord(dl->ev, s));
+      CUDA_TRY(cudaStreamWaitEvent(dl->s, dl->ev, 0));
+      CUDA_TRY(cudaMemcpy2DAsync(dl->h, (size_t)dl->ldh * sizeof(double), X, (size_t)ld * sizeof(double),
+                                 (size_t)N * sizeof(double), nrhs, cudaMemcpyDeviceToHost, dl->s));
+      ++dl->n;
+    }
     if ((st = residual()) != SPALU_OK) return st;
   }
   bool conv = true;
@@ -1223,12 +1244,19 @@ spalu_status spalu_factor_solve_host(spalu_factor_t f, const int* rowptr, const 
   if (nrhs == 0) return SPALU_OK;
   CUDA_TRY(cudaStreamWaitEvent(s, f->up_done, 0));
   st = spalu_solve(f, f->hB, f->hX, nrhs, f->N, stream);
-  if (st == SPALU_OK && refine) st = spalu_refine(f, f->hB, f->hX, nrhs, f->N, iters, relres, stream);
+  HostDownload dl{X, ld, f->up, f->up_go, 0};
+  if (st == SPALU_OK && refine) {
+    const int t = f->timer.begin("refine", s);
+    st = refine_impl(f, f->hB, f->hX, nrhs, f->N, iters, relres, stream, &dl);
+    f->timer.end(t, s);
+  }
+  const bool ok = cudaStreamSynchronize(f->up) == cudaSuccess;
   if (st != SPALU_OK && st != SPALU_ERR_NOCONV) return st;
-  if (cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), f->hX, N * sizeof(double), N * sizeof(double), nrhs,
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+  if (dl.n == 0 &&           // no update of X in the refinement: copy the direct solve
+      cudaMemcpy2DAsync(X, (size_t)ld * sizeof(double), f->hX, N * sizeof(double), N * sizeof(double), nrhs,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return SPALU_ERR_CUDA;
+  if (!ok || cudaStreamSynchronize(s) != cudaSuccess) return SPALU_ERR_CUDA;
   return st;
 }
 

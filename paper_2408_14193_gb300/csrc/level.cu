@@ -809,6 +809,38 @@ __device__ int warp_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, dou
   return shi[0];
 }
 
+// Largest-first work list of a level (scheduling, not in the paper): a counting sort of the
+// segment ids by decreasing unknown count, so that the sparsify CTAs, which the hardware
+// starts roughly in index order, begin with the longest segments and the last wave holds the
+// shortest.  Ids of equal count land in any order: every CTA writes only its own segment's
+// outputs and keys its sketch by the segment id, so the order changes no result.
+constexpr int ORD_B = 256;
+__global__ void __launch_bounds__(1024) seg_order_kernel(const int* cnt, int nseg, int* order) {
+  __shared__ int start[ORD_B];
+  auto key = [](int e) { return ORD_B - 1 - min(max(e, 0), ORD_B - 1); };
+  for (int i = threadIdx.x; i < ORD_B; i += blockDim.x) start[i] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nseg; s += blockDim.x) atomicAdd(&start[key(cnt[s])], 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {            // exclusive scan of the 256 bucket sizes by one warp
+    constexpr int PER = ORD_B / 32;
+    const int lane = threadIdx.x;
+    int v[PER], t = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) { v[j] = start[lane * PER + j]; t += v[j]; }
+    int incl = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    int run = incl - t;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) { start[lane * PER + j] = run; run += v[j]; }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < nseg; s += blockDim.x) order[atomicAdd(&start[key(cnt[s])], 1)] = s;
+}
+
 template <typename T, int NWT>
 __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(LevelDev d, int smem_bytes) {
   extern __shared__ double sm[];
@@ -818,7 +850,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
   __shared__ int nearlist[NEAR_MAX];
   __shared__ int nnear_sh, nfar_sh;
 
-  const int sid = blockIdx.x;
+  const int sid = d.use_order ? d.order[blockIdx.x] : blockIdx.x;
   if (threadIdx.x == 0) seg_context(d, sid, S);
   __syncthreads();
   const int e = S.e;
@@ -1986,6 +2018,10 @@ void launch_level_init_L(const LevelDev& d, cudaStream_t s) {
 template <typename T>
 static void sparsify_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) {
   int smem = (int)p.spars_smem;
+  if (d.use_order && d.g.nseg() > 0) {
+    note_launch();
+    seg_order_kernel<<<1, 1024, 0, s>>>(d.cnt, d.g.nseg(), d.order);
+  }
   note_launch();
   if (d.capS <= 16) {       // finest segments: two warps each, many segments per SM
     cudaFuncSetAttribute(sparsify_kernel<T, NW_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

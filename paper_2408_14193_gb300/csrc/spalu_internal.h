@@ -142,6 +142,8 @@ struct LevelDev {
   void* Yg;         // global sketch scratch (nseg * Ycap * capS) or null
   void* Pinv;       // [gp.nbox * sepcap] reciprocal pivots of the separator U
   int* ptab;        // merge tables: gp.nbox * ldFp * 8 ints
+  int* order;       // [nseg] launch order of the sparsify CTAs (largest segments first)
+  int use_order;    // 1: order is built before each sparsify launch; 0: CTA b is segment b
   int* pcount;      // [gp.nbox * 2]: unknowns of dP, skeleton size of the separator
   int* ppiv;        // [gp.nbox * sepcap] pivots of the separator LU
   int* cnt_up;      // level-(l-1) segment counts (merge target) or null at l = 1
