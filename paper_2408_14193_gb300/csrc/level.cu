@@ -1763,7 +1763,7 @@ size_t invert_smem() { return 2 * sizeof(T) * INV_MAX * INV_MAX + sizeof(int) * 
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
-  pdl_enter();
+  pdl_trigger();
   extern __shared__ double smd[];
   const int sid = blockIdx.x;
   const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
@@ -1782,10 +1782,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(Level
   const T* Tm = static_cast<const T*>(d.T) + (size_t)sid * capS * capS;
   const T* Dg = static_cast<const T*>(d.Dm) + (size_t)sid * capS * capS;
   const T* inv = static_cast<const T*>(d.Dinv) + (size_t)sid * capS;
-  for (int x = threadIdx.x; x < e * SC; x += blockDim.x) {
-    int a = x % e, c = x / e;
-    v[x] = c < nc ? X[lay.at(snodes[a], c)] : T(0);
-  }
+  // factor data first (it overlaps the preceding kernel), the right-hand side after the wait
   if (staged) {
     for (int x = threadIdx.x; x < r * r; x += blockDim.x)
       LUsm[x] = Dg[(k + x % r) + (size_t)capS * (k + x / r)];
@@ -1802,6 +1799,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(Level
     }
     if (bwd)
       for (int x = threadIdx.x; x < r * k; x += blockDim.x) Ps[x] = Dg[(k + x % r) + (size_t)capS * (x / r)];
+  }
+  pdl_wait();
+  for (int x = threadIdx.x; x < e * SC; x += blockDim.x) {
+    int a = x % e, c = x / e;
+    v[x] = c < nc ? X[lay.at(snodes[a], c)] : T(0);
   }
   __syncthreads();
   const T* LUs = staged ? LUsm : Dg + k + (size_t)capS * k;
@@ -1855,7 +1857,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(Level
 // not fixed); backward x_p = U^{-1} (y_p - W x_dP).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
-  pdl_enter();
+  pdl_trigger();
   extern __shared__ double smd[];
   const int P = blockIdx.x;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
@@ -1886,10 +1888,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
   }
   auto rowpos = [&](int a) { return dstage ? rows_sm[a] : tab[(size_t)a * TABW]; };
   auto rownode = [&](int a) { return dstage ? rows_sm[cap.drows + a] : tab[(size_t)a * TABW + 7]; };
-  for (int x = threadIdx.x; x < kp * SC; x += blockDim.x) {
-    int a = x % kp, c = x / kp;
-    y[x] = c < nc ? X[lay.at(tab[(size_t)(ndP + a) * TABW + 7], c)] : T(0);
-  }
   if (staged) for (int x = threadIdx.x; x < kp; x += blockDim.x) { invs[x] = inv[x]; pivs[x] = piv[x]; }
   const size_t ldl = staged ? (size_t)kp : ldp;
   const T* ivs = staged ? invs : inv;
@@ -1898,7 +1896,22 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
     if (staged)
       for (int x = threadIdx.x; x < kp * kp; x += blockDim.x) U[x] = M[(Dp + x % kp) + ldp * (Dp + x / kp)];
   };
+  // factor data first (it overlaps the preceding kernel): the LU block (forward) or the W^T
+  // panel (backward); the solve vector after the wait
+  T* Wt = U;                                            // W^T panel, pitch ldw
   if (!bwd) stage_lu();
+  else if (pstaged) {
+    __syncthreads();                                    // rows_sm
+    for (int x = threadIdx.x; x < ndP * kp; x += blockDim.x) {
+      const int j = x % kp, b = x / kp;
+      Wt[b + (size_t)ldw * j] = M[(Dp + j) + ldp * rows_sm[b]];
+    }
+  }
+  pdl_wait();
+  for (int x = threadIdx.x; x < kp * SC; x += blockDim.x) {
+    int a = x % kp, c = x / kp;
+    y[x] = c < nc ? X[lay.at(tab[(size_t)(ndP + a) * TABW + 7], c)] : T(0);
+  }
   __syncthreads();          // rows_sm, y (and the LU block) are read by other threads below
   if (!bwd) {
     if (kp <= INV_MAX) tri_apply<T, true, NT>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
@@ -1920,12 +1933,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
         xd[x] = c < nc ? X[lay.at(rows_sm[cap.drows + b], c)] : T(0);
       }
     }
-    T* Wt = U;                                            // W^T panel, pitch ldw
-    if (pstaged)
-      for (int x = threadIdx.x; x < ndP * kp; x += blockDim.x) {
-        const int j = x % kp, b = x / kp;
-        Wt[b + (size_t)ldw * j] = M[(Dp + j) + ldp * rows_sm[b]];
-      }
     __syncthreads();
     // y_p -= W x_dP, one thread per (row a, right-hand side c)
     for (int x = threadIdx.x; x < kp * nc; x += blockDim.x) {

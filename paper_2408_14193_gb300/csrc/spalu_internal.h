@@ -215,10 +215,15 @@ void note_launch();
 // Programmatic dependent launch: kernels of the solve and refinement sequences are launched
 // with launch_pdl, so that a kernel's blocks are set up while its predecessor finishes; each
 // such kernel calls pdl_enter() first, which waits until the predecessor grid has completed
-// and its writes are visible, then lets the successor launch.
+// and its writes are visible, then lets the successor launch.  The level-solve kernels split
+// the two: pdl_trigger() at entry, then they stage their factor data (written by the
+// factorization, whose kernels are launched plainly and so have completed before any solve
+// kernel starts), and pdl_wait() before their first read of the solve vector.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  pdl_wait();
+  pdl_trigger();
 }
 
 template <typename... KArgs, typename... Args>
