@@ -514,7 +514,7 @@ constexpr int SLOT = 16;   // right-hand-side slots per leaf and launch
 // memory would otherwise cost resident CTAs).
 template <typename T, int KUW, int LPB, bool bwd>
 __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) {
-  pdl_enter();
+  pdl_trigger();
   extern __shared__ double lsm[];
   constexpr int NT = LPB * SLOT;
   constexpr int LST = SLOT * SLOT;                    // L stage per leaf: 16 columns x 16 (L(j+r, j) at r - 1)
@@ -543,8 +543,10 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
   constexpr bool XPF = !bwd && sizeof(T) == 4;       // stage the right-hand-side rows
   T* xst = stg + 2 * bufsz + (size_t)threadIdx.x * 2 * SLOT;   // own rows, 2 x 16
 
-  // ---- L sweep: y = L^{-1} P x, blocks of 16 steps
-  auto issue_L = [&](int blk, int buf) {
+  // ---- L sweep: y = L^{-1} P x, blocks of 16 steps.  The band part of a block's stage
+  //      (factor data) and its right-hand-side part are issued separately so that the first
+  //      block's band can be requested before the wait on the preceding kernel.
+  auto issue_L_band = [&](int blk, int buf) {
     T* S = stg + (size_t)buf * bufsz;
     const int j0 = blk * SLOT;
     {
@@ -563,6 +565,9 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
         }
       }
     }
+  };
+  auto issue_L_x = [&](int blk, int buf) {
+    const int j0 = blk * SLOT;
     if (XPF && active) {                              // rows j0 + 16 .. j0 + 31 of this thread's rhs
       T* xs = xst + (buf & 1) * SLOT;
       int j = j0 + SLOT;
@@ -575,7 +580,13 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
     }
     cp_async_commit();
   };
+  auto issue_L = [&](int blk, int buf) {
+    issue_L_band(blk, buf);
+    issue_L_x(blk, buf);
+  };
   const int nbl = (NI + SLOT - 1) / SLOT;
+  issue_L_band(0, 0);
+  pdl_wait();                             // the solve vector is written by the preceding kernel
   T W[16];
   if (active) {
     if (!bwd) {
@@ -603,7 +614,7 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
 #pragma unroll
     for (int r = 0; r < 16; ++r) W[r] = coupling(r);
   }
-  issue_L(0, 0);
+  issue_L_x(0, 0);
   for (int blk = 0; blk < nbl; ++blk) {
     if (blk + 1 < nbl) { issue_L(blk + 1, (blk + 1) & 1); cp_async_wait<1>(); }
     else cp_async_wait<0>();
@@ -707,7 +718,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 
 __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X, int nrhs, VecLayout lay) {
-  pdl_enter();
+  pdl_trigger();
   extern __shared__ float4 gsm4[];
   float* Gs = reinterpret_cast<float*>(gsm4);    // NI x NQ
   float* xd = Gs + NI * NQ;                      // NQ x GRC
@@ -715,6 +726,7 @@ __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X,
   const float* Gg = reinterpret_cast<const float*>(d.G) + (size_t)b * NI * NQ;
   for (int i = threadIdx.x; i < NI * NQ / 4; i += GTH) cp_async16(Gs + 4 * i, Gg + 4 * i);
   cp_async_commit();
+  pdl_wait();              // G is the factorization's; the solve vector is the preceding kernel's
   const int I = b % d.g.bx, J = b / d.g.bx;
   const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
   const int nx = d.nx;
