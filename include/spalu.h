@@ -50,7 +50,7 @@ typedef enum {
   SPALU_ERR_NOCONV = -4,       /* refinement did not reach the tolerance */
   SPALU_ERR_TIMEOUT = -5,      /* a bounded device wait expired */
   SPALU_ERR_CUDA = -6,         /* a CUDA runtime call failed */
-  SPALU_ERR_UNSUPPORTED = -7,  /* valid request this build does not implement */
+  SPALU_ERR_UNSUPPORTED = -7,  /* valid request the library does not implement */
   SPALU_ERR_NONFINITE = -8,    /* a NaN or Inf appeared in the factor */
   SPALU_ERR_STATE = -9         /* call made on a handle in the wrong state */
 } spalu_status;
