@@ -135,6 +135,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(pg, x: float) -> float:
+    """The largest x over all ranks (every rank gets it); x itself without a process group."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t[0])
+
+
+def job_value(ws: int, steps: int, n: int, seconds: float) -> float:
+    """Whole-job throughput in DOF/s: every one of ws ranks solved steps problems of n unknowns
+    (weak scaling), and the slowest rank took seconds."""
+    return ws * steps * n / seconds
+
+
 # ------------------------------------------------------------------ CPU oracle leg
 def oracle_sample(n: int, nrhs: int, seed: int = 1):
     """Factor + solve + GMRES refinement of one instance with the CPU oracle; returns
@@ -461,10 +477,7 @@ def run_ours(args):
         st = f.stats()
         f.set_timing(False)
         del f
-        if pg:
-            t = torch.tensor([ms], dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t[0])
+        ms = max_over_ranks(pg, ms)
         return {"ms": ms, "iters": max(iters), "relres": max(rels), "launches": launches,
                 "st": st, "clocks": clocks}
 
@@ -497,19 +510,16 @@ def run_ours(args):
         e2e_rel = max(e2e_rel, float(np.max(rel)))
     e2e_s = time.perf_counter() - t0
     del g
-    if pg:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = max_over_ranks(pg, e2e_s)
     if rank != 0:
         pg.destroy_process_group()
         return 0
-    value = ws * args.steps * N / (head["ms"] / 1e3)
-    base_value = ws * args.steps * N / (base["ms"] / 1e3)
-    noml_value = ws * args.steps * N / (noml["ms"] / 1e3)
+    value = job_value(ws, args.steps, N, head["ms"] / 1e3)
+    base_value = job_value(ws, args.steps, N, base["ms"] / 1e3)
+    noml_value = job_value(ws, args.steps, N, noml["ms"] / 1e3)
     pk = peaks()
     hbm = pk.get("hbm_gbs") or 6800.0
-    e2e_value = ws * args.steps * N / e2e_s
+    e2e_value = job_value(ws, args.steps, N, e2e_s)
 
     cpu = None
     if ws == 1 and not args.no_cpu:
