@@ -223,6 +223,19 @@ def _leaf_flops_split():
     return lu, leaf_algorithmic_flops() - lu
 
 
+def _dominant(st, steps, ms_per_step: float):
+    """The kernel with the largest share of the step: the sparsification (all levels).  Its
+    phases are chains of short dependent steps per segment (barriers, shared-memory latency,
+    instruction fetch at the finest level), so no FLOP or byte roof applies; the captures in
+    profiles/ show every pipe below a fifth of its peak and DRAM below 1 %."""
+    tms = st["timing_ms"]
+    sp = sum(v for k, v in tms.items() if k.startswith("sparsify_l")) / steps
+    return {"kernel": "sparsify_kernel (all levels, with seg_order_kernel and seg_invert_kernel)",
+            "bound": "latency", "ms_per_step": sp, "share_of_step": sp / ms_per_step,
+            "evidence": ["profiles/sparsify_kernel_l11_diffusion1023_mixed.md",
+                         "profiles/sparsify_kernel_l12_diffusion1023_mixed.md"]}
+
+
 def _roofline(st, steps, fp32: bool, hbm_gbs: float):
     """Roofline of the dominant kernel among those timed alone in a phase: achieved =
     algorithmic work per launch / average launch time.
@@ -558,6 +571,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(P.B.nbytes), "relres_max": e2e_rel},
         "gpu_launches": int(head["launches"]),
         "roofline": _roofline(st, args.steps, True, hbm),
+        "dominant": _dominant(st, args.steps, head["ms"] / args.steps),
         "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(st["timing_ms"].items())},
         "factor_stats": {"q_tilde": st["q_tilde"], "levels": st["levels"]},
         "cpu_baseline": cpu,
