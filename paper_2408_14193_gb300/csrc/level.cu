@@ -457,12 +457,16 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // ------------------------------------------------------------ far-row sketch
-// Yr[rr, c] = sum over far neighbour rows f of G[rr, f] B_F[f, c] for rr < hh (unscaled),
+// Yr[rr, c] = sum over far neighbour rows f of G[rr, f] B_F[f, c] for r0 <= rr < hh (unscaled),
 // neighbours taken in chunks of ch (near ones get zero weight).  Yr has leading dimension ldy.
+// Rows below r0 are left alone (the one-pass sketch takes them from the probe, whose rows are
+// the same rows of G).
 template <typename T, class BGet>
 __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const NbrTab& tb, BGet bget,
-                           int sid, int halves, int e, int hh, T* Yr, int ldy, T* Bc, T* Gc, int ch) {
-  for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Yr[(x % hh) + (size_t)ldy * (x / hh)] = T(0);
+                           int sid, int halves, int e, int r0, int hh, T* Yr, int ldy, T* Bc, T* Gc,
+                           int ch) {
+  const int nr = hh - r0;
+  for (int x = threadIdx.x; x < nr * e; x += blockDim.x) Yr[(r0 + x % nr) + (size_t)ldy * (x / nr)] = T(0);
   __syncthreads();
   for (int f0 = 0; f0 < S.nb; f0 += ch) {
     const int nc = min(ch, S.nb - f0);
@@ -472,18 +476,18 @@ __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const NbrTab& tb,
       int t = row / nc, jj = row % nc;
       Bc[row + (size_t)rows * c] = bget(t, f0 + jj, c);
     }
-    for (int x = threadIdx.x; x < hh * rows; x += blockDim.x) {
-      int rr = x % hh, row = x / hh;
+    for (int x = threadIdx.x; x < nr * rows; x += blockDim.x) {
+      int rr = x % nr, row = x / nr;
       int t = row / nc, jj = row % nc;
       const Nbr q = nbr_get(d, S, tb, f0 + jj);
-      Gc[rr + (size_t)hh * row] = q.nearf ? T(0) : (T)sketch_gauss(d.seed, d.l, sid, rr, q.node, t);
+      Gc[rr + (size_t)nr * row] = q.nearf ? T(0) : (T)sketch_gauss(d.seed, d.l, sid, r0 + rr, q.node, t);
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < hh * e; x += blockDim.x) {
-      int rr = x % hh, c = x / hh;
+    for (int x = threadIdx.x; x < nr * e; x += blockDim.x) {
+      int rr = x % nr, c = x / nr;
       T acc = T(0);
-      for (int row = 0; row < rows; ++row) acc += Gc[rr + (size_t)hh * row] * Bc[row + (size_t)rows * c];
-      Yr[rr + (size_t)ldy * c] += acc;
+      for (int row = 0; row < rows; ++row) acc += Gc[rr + (size_t)nr * row] * Bc[row + (size_t)rows * c];
+      Yr[(r0 + rr) + (size_t)ldy * c] += acc;
     }
     __syncthreads();
   }
@@ -1001,6 +1005,12 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     __syncthreads();
     probe_sketch<T>(d, S, tb, bget, sid, halves, e, Y);
     __syncthreads();
+    if (d.pred_mode == PRED_PREDICT && e >= PRED_PROBE) {
+      // keep the probe (the first PRED_PROBE rows of this segment's G times B_F, unscaled) for
+      // the one-pass sketch: the features' QR overwrites it, and T is free until the ID
+      for (int x = threadIdx.x; x < PRED_PROBE * e; x += blockDim.x) Tw[x] = Y[x];
+      __syncthreads();
+    }
     probe_features<T>(d, sid, e, nnear, nfar_sh, S.nb, Y, xf);
     if (d.pred_mode == PRED_RECORD) {
       if (threadIdx.x < PRED_NFEAT) d.feat[(size_t)sid * PRED_NFEAT + threadIdx.x] = xf[threadIdx.x];
@@ -1043,10 +1053,16 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
             Y[(nN + t * nfar_sh + j) + (size_t)ldy * c] = bget(t, f, c);
       }
     } else {
-      // Y_F = G B_F, chunks of neighbours (near ones get zero weight)
-      sketch_far<T>(d, S, tb, bget, sid, halves, e, hh, Y + nN, ldy, Bc, Gc, ch);
+      // Y_F = G B_F, chunks of neighbours (near ones get zero weight); the one-pass sketch of
+      // a predicted segment takes its first PRED_PROBE rows from the probe
+      const int r0 = (predicted && e >= PRED_PROBE) ? min(PRED_PROBE, hh) : 0;
+      if (r0 < hh) sketch_far<T>(d, S, tb, bget, sid, halves, e, r0, hh, Y + nN, ldy, Bc, Gc, ch);
       const T sc = (T)(1.0 / sqrt((double)hh));
-      for (int x = threadIdx.x; x < hh * e; x += blockDim.x) Y[(nN + x % hh) + (size_t)ldy * (x / hh)] *= sc;
+      for (int x = threadIdx.x; x < hh * e; x += blockDim.x) {
+        const int rr = x % hh, c = x / hh;
+        T* yv = Y + (nN + rr) + (size_t)ldy * c;
+        *yv = (rr < r0 ? Tw[rr + PRED_PROBE * c] : *yv) * sc;
+      }
     }
     __syncthreads();
     k = (NWT == NW && in_smem && e <= 64) ? warp_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shi)
