@@ -178,7 +178,9 @@ spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int 
 /* Factor and solve from host memory in one call (Secs. 4.3-4.4): the numeric factorization of
  * the host CSR arrays (as spalu_factor_numeric_host), then X = spaLU^{-1} B refined as
  * spalu_refine when refine != 0 (as spalu_solve_host).  The upload of B runs on a second
- * stream owned by the handle while the factorization's kernels run; B and X live in device
+ * stream owned by the handle while the factorization's kernels run, and the copy of X back
+ * runs there too, after each update of X, while the refinement checks its residual; B and X
+ * live in device
  * buffers the handle keeps (grown on demand, freed with it), so a repeated call allocates
  * nothing.  Host arrays: rowptr (N + 1), colind and val (nnz), B and X (nrhs columns of
  * leading dimension ld >= N; page-locked memory gives full copy bandwidth).  Synchronises
