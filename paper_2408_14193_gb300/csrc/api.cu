@@ -337,11 +337,14 @@ __global__ void __launch_bounds__(256) to_chunked_kernel(int n, int nrhs, const 
                                                          const double* bscale, float* xf) {
   pdl_enter();
   __shared__ float tile[16][CT + 1];
+  __shared__ float bs[16];                    // the column scales, converted once per block
   const int u0 = blockIdx.x * CT, k = blockIdx.y;
+  if (bscale && threadIdx.x < 16) bs[threadIdx.x] = 16 * k + threadIdx.x < nrhs ? (float)bscale[16 * k + threadIdx.x] : 0.f;
+  __syncthreads();
   for (int i = threadIdx.x; i < 16 * CT; i += 256) {
     const int cc = i / CT, uu = i % CT, c = 16 * k + cc;
     float v = (u0 + uu < n && c < nrhs) ? (float)B[(size_t)(u0 + uu) + (size_t)ldb * c] : 0.f;
-    if (bscale && c < nrhs) v *= (float)bscale[c];
+    if (bscale && c < nrhs) v *= bs[cc];
     tile[cc][uu] = v;
   }
   __syncthreads();
