@@ -1,7 +1,8 @@
-"""The multi-rank host logic of bench.py on the CPU, world size 2: the max-over-ranks timing
+"""Host logic of bench.py on the CPU.  Multi-rank, world size 2: the max-over-ranks timing
 reduction over gloo (each rank its own spawned process, rendezvous on 127.0.0.1, as under
 torchrun), the whole-job (weak-scaling) throughput, and the reference arm's rule that rank 0
-alone runs and prints.  No GPU is touched."""
+alone runs and prints.  Measurement: the roofline and dominant-kernel arithmetic of the bench
+line.  No GPU is touched."""
 import json
 import os
 import socket
@@ -72,3 +73,30 @@ def test_reference_arm_runs_on_rank0_only():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_roofline_and_dominant_arithmetic():
+    """The bench line's roofline and dominant-kernel entries from synthetic phase timings:
+    the largest timed phase among those with a roof is chosen, achieved = algorithmic work /
+    average launch time, frac = achieved / peak; the dominant entry is the sparsification's
+    share of the step."""
+    sys.path.insert(0, ROOT)
+    import bench
+    steps = 5
+    st = {"timing_ms": {"leaf_factor": 5 * 1.6, "leaf_solve_fwd": 20 * 0.25, "leaf_solve_bwd": 20 * 0.14,
+                        "sparsify_l12": 5 * 2.0, "sparsify_l11": 5 * 1.5},
+          "timing_count": {"leaf_factor": 5, "leaf_solve_fwd": 20, "leaf_solve_bwd": 20,
+                           "sparsify_l12": 5, "sparsify_l11": 5}}
+    r = bench._roofline(st, steps, True, 6800.0)
+    assert r["kernel"] == "leaf_lu_kernel+leaf_schur_kernel" and r["bound"] == "alu"
+    assert r["launch_ms"] == pytest.approx(1.6) and r["share_of_step_ms"] == pytest.approx(1.6)
+    assert r["achieved"] == pytest.approx(r["algorithmic_flops"] / 1.6e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"]) and 0 < r["frac"] < 1
+    # with the leaf elimination faster, the forward sweeps (HBM-bound) are the largest phase
+    st2 = {"timing_ms": dict(st["timing_ms"], leaf_factor=5 * 0.5), "timing_count": st["timing_count"]}
+    r2 = bench._roofline(st2, steps, True, 6800.0)
+    assert r2["kernel"] == "leaf_solve_kernel" and r2["unit"] == "GB/s" and r2["peak"] == 6800.0
+    assert r2["achieved"] == pytest.approx(r2["algorithmic_bytes"] / 0.25e-3 / 1e9)
+    dmn = bench._dominant(st, steps, 18.0)
+    assert dmn["ms_per_step"] == pytest.approx(3.5) and dmn["share_of_step"] == pytest.approx(3.5 / 18.0)
+    assert dmn["bound"] == "latency"
