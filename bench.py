@@ -309,7 +309,6 @@ def train_predictor(dev, prec, eps, epochs: int = 200):
     import torch
 
     import workloads as W
-    from oracle import predictor as opr
     from paper_2408_14193_gb300 import Factor, NestedDissection, Predictor
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -327,7 +326,7 @@ def train_predictor(dev, prec, eps, epochs: int = 200):
     Y = torch.cat(Ys).contiguous()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    p = Predictor(opr.init_params(0))
+    p = Predictor(W.predictor_init_params(0))
     p.fit_norm(X)
     loss0, _ = p.loss_grad(X, Y)
     loss = p.train(X, Y, epochs=epochs, batch=256, lr=3e-3)

@@ -197,11 +197,39 @@ spalu_status spalu_factor_solve_host(spalu_factor_t f, const int* rowptr, const 
  * held.  Synchronises the factor's stream. */
 spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap);
 
+/* Index tables of level l (1 <= l <= L) as the last factorization left them, for parity
+ * checks of the segment bookkeeping (Secs. 2.3.1, 3.2), the IDs (Sec. 4.2) and the merge
+ * E_(l) (Sec. 4.3).  info (host, 4 ints) receives {nseg, capS, nparent, ldFp}; call once with
+ * only info to size the arrays.  Every other pointer is a host array and may be NULL:
+ *   cnt   [nseg]           unknowns of segment s entering level l;
+ *   kk    [nseg]           skeleton size k of segment s (k = cnt when eps_id = 0);
+ *   nodes [nseg * capS]    grid nodes of segment s entering level l (first cnt[s] valid):
+ *                          at the finest level the side in increasing coordinate, above it
+ *                          the merge of the finer level's skeletons and junction;
+ *   skel  [nseg * capS]    the same nodes in ID order: the first kk[s] are the skeleton in
+ *                          pivot order, the rest the remainders;
+ *   pcnt  [2 * nparent]    per depth-(l-1) box P (row-major in its tiling): |dP| (unknowns on
+ *                          P's boundary after the merge) and k_p (skeleton size of the
+ *                          level-l separator that cuts P);
+ *   pmap  [2 * nparent * ldFp]  per box P, its first |dP| + k_p entries: pairs (position in
+ *                          P's frontal block, grid node) in merge order: P's sides (bottom,
+ *                          top, left, right; a side cut by the separator is skeleton of child
+ *                          1, the junction, skeleton of child 2), P's corners (BL, BR, TL,
+ *                          TR, those that exist), then the separator's skeleton; positions:
+ *                          bottom [0, w), top [w, 2w), left [2w, 2w + h), right
+ *                          [2w + h, 2w + 2h), corners 2w + 2h + {0..3}, separator from
+ *                          2w + 2h + 4 (from 0 at l = 1, where P is the whole grid);
+ *                          w x h is the box size of depth l - 1.
+ * SPALU_ERR_STATE when f is not factored.  Synchronises the stream of the last factorization. */
+spalu_status spalu_factor_export_level(spalu_factor_t f, int l, int* info, int* cnt, int* kk, int* nodes,
+                                       int* skel, int* pcnt, int* pmap);
+
 /* Relative residual norms relres[c] = ||B_c - A X_c||_2 / ||B_c||_2 (0 when B_c = 0) of nrhs
  * columns against the matrix of the last factorization, computed without allocating any
  * device memory.  The paper has no counterpart: this serves callers that cannot let the
- * library allocate when they check a solution, such as code running while a stream is
- * captured into a CUDA graph, or hosts that give all device memory to their own pool.
+ * library allocate when they check a solution, such as hosts that give all device memory to
+ * their own pool and forbid later allocations by libraries, or processes so close to the
+ * device-memory limit that a new allocation would fail.
  * B, X: device, column-major, leading dimension ld >= N; relres: host, nrhs entries.
  * The reduction goes through one fixed scratch array of 64 * 512 * 2 + 64 doubles
  * (about 0.5 MB) held by every GPU that loads the library until the process exits, so
@@ -209,7 +237,8 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap);
  * The first call on a device looks the array's address up (with that device current) and
  * should come before any stream capture.  All calls share the array: calls whose work
  * overlaps on the GPU (other streams, other threads) race and must be serialised by the
- * caller.  Synchronises the stream to return relres. */
+ * caller.  The looked-up address is kept for the life of the process, so the call must not
+ * be used across a cudaDeviceReset.  Synchronises the stream to return relres. */
 spalu_status spalu_residual_noalloc(spalu_factor_t f, const double* B, const double* X, int nrhs,
                                     int ld, double* relres, spalu_stream_t stream);
 
@@ -223,6 +252,13 @@ spalu_status spalu_set_timing(spalu_factor_t f, int on);
 /* Number of CUDA kernels this library has launched so far in the calling process, over all
  * handles (a diagnostic counter; never reset). */
 unsigned long long spalu_kernel_launches(void);
+
+/* Measured FMA throughput of the current device's CUDA cores (a diagnostic; not in the paper):
+ * precision 0 = FP64, 1 = FP32.  Runs a kernel of independent fused multiply-add chains on
+ * every SM, timed with CUDA events on stream (best of three after a warm-up launch), and
+ * writes the rate in FLOP/s (an FMA counts 2) to *flops.  These rates bound the small dense
+ * kernels of the factorization (leaf LU, ID, block eliminations).  Synchronises the stream. */
+spalu_status spalu_measure_fma_peak(int precision, double* flops, spalu_stream_t stream);
 
 void spalu_factor_destroy(spalu_factor_t f);
 

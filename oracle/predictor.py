@@ -84,11 +84,10 @@ def pack(W1, b1, W2, b2, dtype=np.float64):
 
 
 def init_params(seed: int) -> np.ndarray:
-    """He-normal weights, zero biases (float32); the seeded draw is an input to both sides."""
-    rng = np.random.default_rng(seed)
-    W1 = rng.standard_normal((NHID, NFEAT)) * math.sqrt(2.0 / NFEAT)
-    W2 = rng.standard_normal((NOUT, NHID)) * math.sqrt(2.0 / NHID)
-    return pack(W1, np.zeros(NHID), W2, np.zeros(NOUT), np.float32)
+    """He-normal weights, zero biases (float32): the seeded draw of ``workloads``, an input
+    to both sides."""
+    from workloads import predictor_init_params
+    return predictor_init_params(seed, NFEAT, NHID, NOUT)
 
 
 def fit_norm(X):

@@ -35,6 +35,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .dense import gepp, interp_decomp, lu_solve
+from . import flops as fl
 from .nd import NestedDissection, box_corners, chebyshev_to_segment, _sides
 from .philox import sketch_matrix
 from . import predictor as pred
@@ -186,7 +187,7 @@ def factor(A, nd: NestedDissection, opts: Options = Options()) -> Factor:
         seg_g = {k: ("S", l, k) for k in keys}
         ids = {}
         e_max, k_max = 0, 0
-        cnt = {"passes": 0, "fallbacks": 0, "predicted": 0}
+        cnt = {"passes": 0, "fallbacks": 0, "predicted": 0, "flops_sparsify": 0}
         # 1. one ID per segment, all from A^(l) as it stands (Eqs. (RRQR sample), (ID [A_ni; A_in]))
         for key in keys:
             g = seg_g[key]
@@ -200,9 +201,17 @@ def factor(A, nd: NestedDissection, opts: Options = Options()) -> Factor:
             ids[key] = _segment_id(blk, g, key, nbr, nodes, l, lev.segments[key].sid, nx, opts,
                                    A, L, cnt)
             k_max = max(k_max, ids[key][1])
+        for key in keys:             # transforms and remainder eliminations of this level
+            e = nodes[seg_g[key]].size
+            k = int(ids[key][1])
+            cnt["flops_sparsify"] += fl.apply(e, k) + (fl.elim(e - k, k) if e > k else 0)
         stats["levels"][l] = {"e_max": e_max, "k_max": k_max, **cnt,
                               "ranks": [int(ids[k][1]) for k in keys],
-                              "sizes": [int(nodes[seg_g[k]].size) for k in keys]}
+                              "sizes": [int(nodes[seg_g[k]].size) for k in keys],
+                              # index tables: segment nodes entering the level and in ID order
+                              # (skeleton first, in pivot order), keyed by segment id
+                              "nodes": {lev.segments[k].sid: nodes[seg_g[k]].copy() for k in keys},
+                              "skel": {lev.segments[k].sid: nodes[seg_g[k]][ids[k][0]] for k in keys}}
 
         # 2. apply U_T^(l) A^(l) L_T^(l) (Eq. (U_T * A * LT)): transformed diagonal blocks,
         #    neighbour couplings restricted to skeletons, remainder couplings dropped.
@@ -257,14 +266,24 @@ def factor(A, nd: NestedDissection, opts: Options = Options()) -> Factor:
             _eliminate(blk, rg, nodes, tape)
 
         # 4. eliminate the level-l separators (their skeletons)
+        kps = []
         for key in lev.separators:
             kg = ("K", l, key)
+            kps.append(nodes[kg].size if kg in nodes else 0)
             if kg in nodes:
                 _eliminate(blk, kg, nodes, tape)
 
         # 5. merge skeletons into the segments of level l-1 (E_(l))
         if l > 1:
             nodes, blk = _merge(nd, l, nodes, blk)
+        # work of the separator eliminations, counted against every unknown on the boundary of
+        # the parent box after the merge (its sides and its existing corners)
+        fm = 0
+        for parent, kp in zip(lev.parents, kps):
+            dP = sum(nodes[("S", l - 1, key)].size for key, _ in _sides(parent, nx, nd.ny)) if l > 1 else 0
+            dP += len(box_corners(parent, nx, nd.ny)) if l > 1 else 0
+            fm += fl.elim(kp, dP) if kp else 0
+        stats["levels"][l]["flops_merge"] = fm
 
     assert not blk.d, "unknowns left after level 1"
     ks = [v["k_max"] / v["e_max"] for v in stats["levels"].values() if v["e_max"] > 0]
@@ -294,7 +313,7 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0,
     """Sampled ID of one segment (Secs. 4.1-4.2, 4.5): returns (perm, k, T).  With a
     predictor, the first sketch has the predicted size and is kept only if it passes the
     measured-error test; otherwise the adaptive schedule continues."""
-    cnt = cnt if cnt is not None else {"passes": 0, "fallbacks": 0, "predicted": 0}
+    cnt = cnt if cnt is not None else {"passes": 0, "fallbacks": 0, "predicted": 0, "flops_sparsify": 0}
     e = nodes[g].size
     rows_n, rows_t, labels = [], [], []
     for gn in nbr:
@@ -324,11 +343,17 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0,
     nF = BF.shape[0]
 
     def ident():
-        return interp_decomp(np.vstack([BN, BF]), opts.eps)
+        r = interp_decomp(np.vstack([BN, BF]), opts.eps)
+        cnt["flops_sparsify"] += fl.qr(BN.shape[0] + nF, e, r[1])
+        return r
+
+    def done(r):
+        cnt["flops_sparsify"] += fl.interp(r[1], e)
+        return r
 
     cnt["passes"] += 1
     if nF <= opts.h0:
-        return ident()
+        return done(ident())
     p = opts.p_oversample
     h = min(nF, opts.h0)
     use_pred = (opts.predictor is not None or opts.record is not None) and A is not None \
@@ -352,6 +377,7 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0,
         G = sketch_matrix(opts.seed, l, sid, h, f_nodes, f_half)
         Y = np.vstack([BN, (G @ BF) / math.sqrt(h)])
         perm, k, T = interp_decomp(Y, opts.eps)
+        cnt["flops_sparsify"] += fl.sketch(h, nF, e) + fl.qr(Y.shape[0], e, k)
         if predicted:
             predicted = False
             if k <= h - p and pred.id_error_ok(Bx, perm, k, T, opts.eps):
@@ -369,7 +395,7 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0,
         break
     if use_pred and opts.record is not None:
         opts.record.append((x, int(res[1]), int(nF), int(e), int(l)))
-    return res
+    return done(res)
 
 
 def _eliminate(blk: _Blocks, p, nodes, tape):

@@ -112,6 +112,8 @@ struct spalu_factor_s {
   PhaseTimer timer;
   int kumax = 30;            // upper bandwidth of the leaf U factors (read after each factor)
   int* d_lstat = nullptr;    // [LS_N * (L + 1)] per-level counters (factor kernels)
+  unsigned long long* d_flops = nullptr;   // [4 * (L + 1)] per level: algorithmic FLOPs of the sparsify
+                                           // and merge phases, bytes of the segment and separator factors
   std::vector<int> lstat;    // host copy after the last factor
   std::vector<SolveCaps> caps;   // [1..L] solve-kernel capacities from the last factor
   int* d_tgt_all = nullptr;  // recorded targets of all levels (4 ints per segment)
@@ -562,6 +564,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     cv.base = pass ? f->arena : nullptr;
     f->d_err = cv.take<int>(4);
     f->d_lstat = cv.take<int>((size_t)LS_N * (L + 1));
+    f->d_flops = cv.take<unsigned long long>((size_t)4 * (L + 1));
     {
       size_t nt = 0;
       for (int l = 1; l <= L; ++l) nt += (size_t)f->plan[l].g.nseg() * 4;
@@ -657,6 +660,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   for (int l = 1; l <= L; ++l) {
     f->lev[l].err = f->d_err;
     f->lev[l].lstat = f->d_lstat + LS_N * l;
+    f->lev[l].flops = f->d_flops + 4 * l;
     f->lev[l].rowptr = f->rowptr;
     f->lev[l].colind = f->colind;
     f->lev[l].val = f->val;
@@ -677,6 +681,7 @@ static spalu_status factor_enqueue(spalu_factor_t f, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(f->d_err, 0, sizeof(int), s));
   CUDA_TRY(cudaMemsetAsync(f->leaf.kumax, 0, sizeof(int), s));
   CUDA_TRY(cudaMemsetAsync(f->d_lstat, 0, sizeof(int) * LS_N * (L + 1), s));
+  CUDA_TRY(cudaMemsetAsync(f->d_flops, 0, sizeof(unsigned long long) * 4 * (L + 1), s));
   if (f->pred_mode == PRED_RECORD && f->tgt_ints)
     CUDA_TRY(cudaMemsetAsync(f->d_tgt_all, 0, sizeof(int) * f->tgt_ints, s));
   if (L >= 1) launch_level_init_L(f->lev[L], s);
@@ -1269,6 +1274,8 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
   const int L = f->nd->L;
   std::string out = "{\"L\": " + std::to_string(L) + ", \"arena_bytes\": " + std::to_string(f->arena_bytes) + ", \"levels\": [";
   double qt = 0.0;
+  std::vector<unsigned long long> fl(4 * (size_t)(L + 1));
+  CUDA_TRY(cudaMemcpy(fl.data(), f->d_flops, sizeof(unsigned long long) * fl.size(), cudaMemcpyDeviceToHost));
   for (int l = 1; l <= L; ++l) {
     const LevelDev& d = f->lev[l];
     int n = d.g.nseg();
@@ -1285,11 +1292,11 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
       ksum += kk[i];
     }
     if (emax > 0) qt = std::max(qt, (double)kmax / emax);
-    char buf[512];
+    char buf[640];
     const int* ls = f->lstat.data() + LS_N * l;
-    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld, \"sep_k_max\": %d, \"passes\": %d, \"fallbacks\": %d, \"predicted\": %d}",
+    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld, \"sep_k_max\": %d, \"passes\": %d, \"fallbacks\": %d, \"predicted\": %d, \"flops_sparsify\": %llu, \"flops_merge\": %llu, \"bytes_seg\": %llu, \"bytes_sep\": %llu}",
                   l == 1 ? "" : ", ", l, n, emax, kmax, esum, ksum, ls[LS_KPMAX], ls[LS_PASSES],
-                  ls[LS_FALLBACK], ls[LS_PREDICTED]);
+                  ls[LS_FALLBACK], ls[LS_PREDICTED], fl[4 * l], fl[4 * l + 1], fl[4 * l + 2], fl[4 * l + 3]);
     out += buf;
   }
   char buf[64];
@@ -1315,6 +1322,46 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
   out += "}}";
   if (out.size() + 1 > cap) return SPALU_ERR_ARG;
   std::memcpy(json, out.c_str(), out.size() + 1);
+  return SPALU_OK;
+}
+
+spalu_status spalu_factor_export_level(spalu_factor_t f, int l, int* info, int* cnt, int* kk, int* nodes,
+                                       int* skel, int* pcnt, int* pmap) {
+  if (!f || !info) return SPALU_ERR_ARG;
+  if (!f->factored) return SPALU_ERR_STATE;
+  const int L = f->nd->L;
+  if (l < 1 || l > L) return SPALU_ERR_ARG;
+  const LevelDev& d = f->lev[l];
+  const int nseg = d.g.nseg(), np = d.gp.nbox();
+  info[0] = nseg;
+  info[1] = d.capS;
+  info[2] = np;
+  info[3] = d.ldFp;
+  cudaStream_t s = f->last_stream;
+  const size_t segs = (size_t)nseg * d.capS;
+  if (cnt) CUDA_TRY(cudaMemcpyAsync(cnt, d.cnt, sizeof(int) * nseg, cudaMemcpyDeviceToHost, s));
+  if (kk) CUDA_TRY(cudaMemcpyAsync(kk, d.kk, sizeof(int) * nseg, cudaMemcpyDeviceToHost, s));
+  if (nodes) CUDA_TRY(cudaMemcpyAsync(nodes, d.nodes, sizeof(int) * segs, cudaMemcpyDeviceToHost, s));
+  if (skel) CUDA_TRY(cudaMemcpyAsync(skel, d.snodes, sizeof(int) * segs, cudaMemcpyDeviceToHost, s));
+  std::vector<int> pc(2 * (size_t)np), tab;
+  CUDA_TRY(cudaMemcpyAsync(pc.data(), d.pcount, sizeof(int) * 2 * np, cudaMemcpyDeviceToHost, s));
+  if (pmap) {
+    tab.resize((size_t)np * d.ldFp * MERGE_TABW);
+    CUDA_TRY(cudaMemcpyAsync(tab.data(), d.ptab, sizeof(int) * tab.size(), cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (pcnt) std::memcpy(pcnt, pc.data(), sizeof(int) * 2 * np);
+  if (pmap) {
+    for (int P = 0; P < np; ++P) {
+      const int n = pc[2 * P] + pc[2 * P + 1];
+      if (n < 0 || n > d.ldFp) return SPALU_ERR_CUDA;
+      for (int x = 0; x < n; ++x) {
+        const int* e = tab.data() + ((size_t)P * d.ldFp + x) * MERGE_TABW;
+        pmap[((size_t)P * d.ldFp + x) * 2] = e[0];
+        pmap[((size_t)P * d.ldFp + x) * 2 + 1] = e[7];
+      }
+    }
+  }
   return SPALU_OK;
 }
 

@@ -26,6 +26,7 @@
 
 #include "pred_infer.cuh"
 #include "spalu_internal.h"
+#include "work.cuh"
 
 namespace spalu {
 namespace {
@@ -883,7 +884,11 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
       perm_out[j] = j;
       d.snodes[(size_t)sid * capS + j] = d.nodes[(size_t)sid * capS + j];
     }
-    if (threadIdx.x == 0) { d.kk[sid] = e; d.hs[sid] = 0; }
+    if (threadIdx.x == 0) {
+      d.kk[sid] = e;
+      d.hs[sid] = 0;
+      atomicAdd(d.flops + 2, (unsigned long long)(e * e * sizeof(T) + 2 * e * sizeof(int)));
+    }
     return;
   }
 
@@ -1026,10 +1031,12 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
   int passes = 0;
   bool fellback = false, have_t = false;
   const bool was_predicted = predicted;
+  unsigned long long work_done = 0;       // algorithmic FLOPs of this segment (thread 0)
   while (true) {
     const bool full = (h >= nF);
     const int hh = full ? nF : h;
     const int m = nN + hh;
+    if (threadIdx.x == 0 && !full) work_done += work::sketch(hh, nF, e);
     // near rows
     for (int x = threadIdx.x; x < nN * e; x += blockDim.x) {
       int row = x % nN, c = x / nN;
@@ -1068,6 +1075,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     k = (NWT == NW && in_smem && e <= 64) ? warp_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shi)
                                           : block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
     ++passes;
+    if (threadIdx.x == 0) work_done += work::qr(m, e, k);
     if (predicted) {          // the one-pass ID stands if it passes the measured-error test
       predicted = false;
       if (full) break;
@@ -1164,7 +1172,13 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     d.piv[(size_t)sid * capS + j] = piv[j];
     Ig[j] = rinv[j];
   }
-  if (threadIdx.x == 0) { d.kk[sid] = k; d.hs[sid] = h; }
+  if (threadIdx.x == 0) {
+    d.kk[sid] = k;
+    d.hs[sid] = h;
+    work_done += work::interp(k, e) + work::apply(e, k) + (r > 0 ? work::elim(r, k) : 0ull);
+    atomicAdd(d.flops, work_done);
+    atomicAdd(d.flops + 2, (unsigned long long)((k * r + e * e) * sizeof(T) + 2 * e * sizeof(int)));
+  }
 }
 
 // ------------------------------------------------------------ level-L segment tables
@@ -1178,10 +1192,8 @@ __global__ void level_init_L_kernel(LevelDev d) {
 }
 
 // ------------------------------------------------------------ merge (Sec. 4.3, E_(l))
-// Table entry per unknown of the parent's extended block [dP | p]:
-//   [0] position in the parent block, [1..3] (position, side, skeleton index) in child 1,
-//   [4..6] the same in child 2 (-1 when absent; side 4 = corner), [7] grid node.
-constexpr int TABW = 8;
+// Table entry per unknown of the parent's extended block [dP | p]: see MERGE_TABW.
+constexpr int TABW = MERGE_TABW;
 
 struct ParentCtx {
   int Ip, Jp, c1, c2, I1, J1, I2, J2, sep, kp;
@@ -1274,6 +1286,12 @@ __global__ void merge_table_kernel(LevelDev d) {
     total_sh = n;
     d.pcount[2 * P] = ndP;
     d.pcount[2 * P + 1] = C.kp;
+    if (C.kp > 0) {
+      atomicAdd(d.flops + 1, work::elim(C.kp, ndP));
+      const size_t tb = d.fp32 ? sizeof(float) : sizeof(double);
+      atomicAdd(d.flops + 3, (unsigned long long)(((size_t)C.kp * C.kp + 2 * (size_t)C.kp * ndP) * tb +
+                                                  (size_t)C.kp * sizeof(int)));
+    }
     atomicMax(d.lstat + LS_KPMAX, C.kp);
     atomicMax(d.lstat + LS_DPMAX, ndP);
   }

@@ -2,11 +2,16 @@
 //
 // spalu_refine measures ||b - A x|| / ||b|| with buffers it allocates on first use (the
 // residual vectors and the partial sums of its reductions).  Some callers cannot let the
-// library allocate at that point: code that runs while a stream is being captured into a
-// CUDA graph (cudaMalloc is not allowed during capture), and hosts that hand every byte of
-// device memory to their own pool and forbid allocations from libraries after start-up.
-// spalu_residual_noalloc serves them: the residual is formed on the fly and reduced through
-// a fixed scratch array that lives in this file for the whole life of the process.
+// library allocate at that point: hosts that hand every byte of device memory to their own
+// pool (a framework's caching allocator, a serving runtime with a fixed memory budget) and
+// forbid allocations from libraries after start-up, and processes already at the edge of
+// device memory, where a new cudaMalloc would fail.  spalu_residual_noalloc serves them: the
+// residual is formed on the fly and reduced through a fixed scratch array that lives in this
+// file for the whole life of the process.
+//
+// The array's device address is looked up once per device and kept.  A cudaDeviceReset (or
+// any reset of the primary context) unloads this module and makes that address stale, so
+// the entry point must not be used across such a reset.
 #include <mutex>
 
 #include "spalu_internal.h"

@@ -102,6 +102,12 @@ struct Geo {
   }
 };
 
+// Merge table (Sec. 4.3, E_(l)) of a depth-(l-1) parent box: one entry of MERGE_TABW ints per
+// unknown of its extended block [dP | p]: [0] position in the parent block, [1..3]
+// (position, side, skeleton index) in child 1, [4..6] the same in child 2 (-1 when absent;
+// side 4 = corner), [7] grid node.
+constexpr int MERGE_TABW = 8;
+
 // Resident sparsify CTAs per SM that the occupancy autotuner tries (0: the uncut worst case)
 constexpr int SPARS_NCAND = 7;
 constexpr int SPARS_CAND_CTAS[SPARS_NCAND] = {0, 2, 3, 4, 6, 8, 12};
@@ -155,6 +161,10 @@ struct LevelDev {
   unsigned long long seed;
   int* err;
   int* lstat;       // [LS_N] counters of this level (maxima of e, kp, |dP|; ID passes, ...)
+  unsigned long long* flops;   // [4] of this level: algorithmic FLOPs of the sparsification and of
+                               // the separator eliminations (work.cuh), and the bytes of the
+                               // segment factors (T, transformed block, remainder LU, pivots)
+                               // and of the separator factors (LU, W, Z, pivots) the solve reads
   int L;            // number of levels of the dissection
   // learned rank predictor
   int pred_mode;            // PRED_OFF / PRED_RECORD / PRED_PREDICT

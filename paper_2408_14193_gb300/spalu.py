@@ -88,9 +88,11 @@ SIGNATURES = [
     ("spalu_solve_host", _I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_factor_solve_host", _I, [_P, _P, _P, _P, _I, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_stats", _I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    ("spalu_factor_export_level", _I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     ("spalu_residual_noalloc", _I, [_P, _P, _P, _I, _I, _P, _P]),
     ("spalu_set_timing", _I, [_P, _I]),
     ("spalu_kernel_launches", ctypes.c_ulonglong, []),
+    ("spalu_measure_fma_peak", _I, [_I, _P, _P]),
     ("spalu_factor_destroy", None, [_P]),
     ("spalu_predictor_create", _I, [_P, _P]),
     ("spalu_predictor_get_params", _I, [_P, _P, _P]),
@@ -132,6 +134,14 @@ def load_library(path: str | None = None):
 
 def kernel_launches() -> int:
     return int(load_library().spalu_kernel_launches())
+
+
+def measure_fma_peak(precision: int, stream=None) -> float:
+    """spalu_measure_fma_peak: FP64 (0) or FP32 (1) FMA throughput of the device in FLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(load_library().spalu_measure_fma_peak(precision, ctypes.byref(v), _stream_ptr(stream)),
+           "spalu_measure_fma_peak")
+    return v.value
 
 
 def _stream_ptr(stream=None):
@@ -204,18 +214,34 @@ class Factor:
     def factor(self, rowptr, colind, val, stream=None):
         """Numeric factorization of a device CSR matrix (torch int32/int32/float64)."""
         import torch
+        self._csr_shape(rowptr, colind, val)
         _check(self.lib.spalu_factor_numeric(self.handle, _dev_ptr(rowptr, torch.int32),
                                              _dev_ptr(colind, torch.int32), _dev_ptr(val, torch.float64),
                                              int(val.numel()), _stream_ptr(stream)),
                "spalu_factor_numeric")
 
+    def _csr_shape(self, rowptr, colind, val):
+        if len(rowptr) != self.N + 1 or len(colind) != len(val):
+            raise ValueError(f"CSR arrays must have N + 1 = {self.N + 1} row pointers and as many column "
+                             f"indices as values, got {len(rowptr)}, {len(colind)}, {len(val)}")
+
     def factor_host(self, rowptr: np.ndarray, colind: np.ndarray, val: np.ndarray, stream=None):
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
         colind = np.ascontiguousarray(colind, dtype=np.int32)
         val = np.ascontiguousarray(val, dtype=np.float64)
+        self._csr_shape(rowptr, colind, val)
         _check(self.lib.spalu_factor_numeric_host(self.handle, rowptr.ctypes.data, colind.ctypes.data,
                                                   val.ctypes.data, int(val.size), _stream_ptr(stream)),
                "spalu_factor_numeric_host")
+
+    def _nrhs(self, B, X):
+        """Right-hand-side count of B, shaped (N,) or (nrhs, N), with X shaped like B; the
+        kernels index both with leading dimension N, so a short tensor is refused here."""
+        if B.dim() not in (1, 2) or B.shape[-1] != self.N:
+            raise ValueError(f"B must have shape (N,) or (nrhs, N) with N = {self.N}, got {tuple(B.shape)}")
+        if X is not None and tuple(X.shape) != tuple(B.shape):
+            raise ValueError(f"X must have the shape of B {tuple(B.shape)}, got {tuple(X.shape)}")
+        return 1 if B.dim() == 1 else B.shape[0]
 
     def solve(self, B, X=None, stream=None):
         """X = spaLU^{-1} B for a device float64 tensor B of shape (N,) or (nrhs, N) laid
@@ -223,7 +249,7 @@ class Factor:
         import torch
         if X is None:
             X = torch.empty_like(B)
-        nrhs = 1 if B.dim() == 1 else B.shape[0]
+        nrhs = self._nrhs(B, X)
         _check(self.lib.spalu_solve(self.handle, _dev_ptr(B, torch.float64), _dev_ptr(X, torch.float64),
                                     nrhs, self.N, _stream_ptr(stream)), "spalu_solve")
         return X
@@ -240,7 +266,7 @@ class Factor:
     def refine(self, B, X, stream=None, check=True):
         """GMRES refinement of X in place; returns (iterations, relative residuals)."""
         import torch
-        nrhs = 1 if B.dim() == 1 else B.shape[0]
+        nrhs = self._nrhs(B, X)
         it = ctypes.c_int(0)
         rel = np.zeros(nrhs)
         st = self.lib.spalu_refine(self.handle, _dev_ptr(B, torch.float64), _dev_ptr(X, torch.float64),
@@ -254,6 +280,8 @@ class Factor:
         (same shape, float64, C-contiguous; page-locked for full copy bandwidth) receives the
         solution; a new array otherwise."""
         B = np.ascontiguousarray(B, dtype=np.float64)
+        if B.ndim not in (1, 2) or B.shape[-1] != self.N:
+            raise ValueError(f"B must have shape (N,) or (nrhs, N) with N = {self.N}, got {B.shape}")
         nrhs = 1 if B.ndim == 1 else B.shape[0]
         if out is not None:
             if out.shape != B.shape or out.dtype != np.float64 or not out.flags.c_contiguous:
@@ -276,7 +304,10 @@ class Factor:
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
         colind = np.ascontiguousarray(colind, dtype=np.int32)
         val = np.ascontiguousarray(val, dtype=np.float64)
+        self._csr_shape(rowptr, colind, val)
         B = np.ascontiguousarray(B, dtype=np.float64)
+        if B.ndim not in (1, 2) or B.shape[-1] != self.N:
+            raise ValueError(f"B must have shape (N,) or (nrhs, N) with N = {self.N}, got {B.shape}")
         nrhs = 1 if B.ndim == 1 else B.shape[0]
         if out is not None:
             if out.shape != B.shape or out.dtype != np.float64 or not out.flags.c_contiguous:
@@ -296,13 +327,30 @@ class Factor:
     def residual_noalloc(self, B, X, stream=None):
         """||B - A X|| / ||B|| per column without any device allocation (nrhs <= 64)."""
         import torch
-        nrhs = 1 if B.dim() == 1 else B.shape[0]
+        nrhs = self._nrhs(B, X)
         rel = np.zeros(nrhs)
         _check(self.lib.spalu_residual_noalloc(self.handle, _dev_ptr(B, torch.float64),
                                                _dev_ptr(X, torch.float64), nrhs, self.N,
                                                rel.ctypes.data, _stream_ptr(stream)),
                "spalu_residual_noalloc")
         return rel
+
+    def export_level(self, l: int) -> dict:
+        """spalu_factor_export_level: the index tables of level l as numpy arrays: cnt, kk,
+        nodes and skel (nseg x capS), pcnt (nparent x 2) and pmap (nparent x ldFp x 2)."""
+        info = np.zeros(4, dtype=np.int32)
+        _check(self.lib.spalu_factor_export_level(self.handle, l, info.ctypes.data, None, None, None, None,
+                                                  None, None), "spalu_factor_export_level")
+        nseg, cap, npar, ldp = (int(v) for v in info)
+        out = {"cnt": np.zeros(nseg, np.int32), "kk": np.zeros(nseg, np.int32),
+               "nodes": np.zeros((nseg, cap), np.int32), "skel": np.zeros((nseg, cap), np.int32),
+               "pcnt": np.zeros((npar, 2), np.int32), "pmap": np.full((npar, ldp, 2), -1, np.int32)}
+        _check(self.lib.spalu_factor_export_level(self.handle, l, info.ctypes.data,
+                                                  *[out[k].ctypes.data for k in
+                                                    ("cnt", "kk", "nodes", "skel", "pcnt", "pmap")]),
+               "spalu_factor_export_level")
+        out["info"] = info
+        return out
 
     def set_timing(self, on: bool = True):
         _check(self.lib.spalu_set_timing(self.handle, 1 if on else 0), "spalu_set_timing")
@@ -368,7 +416,7 @@ def solve_batch(factors, Bs, Xs, streams):
     hs = P(*[f.handle for f in factors])
     bp = P(*[_dev_ptr(B, torch.float64).value for B in Bs])
     xp = P(*[_dev_ptr(X, torch.float64).value for X in Xs])
-    nr = (ctypes.c_int * n)(*[1 if B.dim() == 1 else int(B.shape[0]) for B in Bs])
+    nr = (ctypes.c_int * n)(*[f._nrhs(B, X) for f, B, X in zip(factors, Bs, Xs)])
     ld = (ctypes.c_int * n)(*[f.N for f in factors])
     st = P(*[_stream_ptr(s).value for s in streams])
     _check(load_library().spalu_solve_batch(n, hs, bp, xp, nr, ld, st), "spalu_solve_batch")

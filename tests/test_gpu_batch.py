@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import assert_close
 from oracle.nd import nested_dissection
 from oracle.spalu import Options as OOpts, factor as ofactor, solve as osolve
 
@@ -53,13 +54,13 @@ def test_batch_matches_one_at_a_time(precision):
         # rounding for the plain form; FP32 rounding of an FP32 factor for the mixed one (its
         # direct solve is only accurate to ~1e-4 at this eps, refinement restores 1e-10)
         tol = 1e-12 if precision == 0 else 1e-3
-        assert np.linalg.norm(x - y) <= tol * np.linalg.norm(y), (i, n)
+        assert_close(x, y, tol, f"problem {i}, n {n}")
     # one problem of the batch against the oracle (FP64 parity bar)
     if precision == 0:
         P = probs[3][0]
         xo = osolve(ofactor(P.A, nested_dissection(255, 255), OOpts(eps=1e-8, symmetric=True)), P.B)
         x = Xs[3].cpu().numpy().T
-        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert_close(x, xo, 1e-6, f"oracle, n {n}")
 
 
 def test_batch_rejects_bad_arguments():

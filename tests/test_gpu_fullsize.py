@@ -1,0 +1,117 @@
+"""Parity at the larger sizes: FP64 against the oracle at 511 x 511 (L = 10), against the
+stored 1023 x 1023 oracle solution (the golden file written by a script that calls only the
+oracle), and the headline path at 1023 x 1023 (mixed precision, learned ranks, eps_ID 5e-7)
+bounded against the FP64 GPU path, with its GMRES iteration count asserted."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.nd import nested_dissection
+from oracle.spalu import Options as OOpts, factor as ofactor, solve as osolve
+from parity import assert_close, rel_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "diffusion1023_seed1_eps1e-8.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _dev(P):
+    d = torch.device("cuda:0")
+    A = P.A
+    return (torch.from_numpy(A.indptr).to(d), torch.from_numpy(A.indices).to(d),
+            torch.from_numpy(A.data).to(d), torch.from_numpy(np.ascontiguousarray(P.B.T)).to(d))
+
+
+def test_fp64_matches_oracle_511():
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    n = 511
+    P = W.make_problem("diffusion", n, seed=61, nrhs=2)
+    rp, ci, va, B = _dev(P)
+    f = Factor(NestedDissection(n), eps_id=1e-8, symmetric=1)
+    f.factor(rp, ci, va)
+    X = f.solve(B).cpu().numpy().T
+    F = ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-8, symmetric=True))
+    nrm, ent = assert_close(X, osolve(F, P.B), 1e-6, "diffusion 511")
+    print(f"511^2 FP64 vs oracle: norm-wise {nrm:.2e}, entry-wise {ent:.2e}")
+    for lv in f.stats()["levels"]:
+        o = F.stats["levels"][lv["level"]]
+        assert abs(lv["e_max"] - o["e_max"]) <= 2 and abs(lv["k_max"] - o["k_max"]) <= 2
+
+
+def test_fp64_matches_golden_1023():
+    """The full-size workload against the oracle's stored solution: the sampled unknowns (one
+    per leaf box, the level-1 separator, 1024 more separator nodes) entry by entry, the
+    norms, and the per-level sizes, ranks and work counts."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    with open(GOLDEN) as fh:
+        g = json.load(fh)
+    n = g["n"]
+    P = W.make_problem("diffusion", n, seed=g["seed"], nrhs=1)
+    assert abs(np.linalg.norm(P.B[:, 0]) - g["b_norm2"]) <= 1e-12 * g["b_norm2"]    # same input
+    rp, ci, va, B = _dev(P)
+    f = Factor(NestedDissection(n), eps_id=g["eps_id"], symmetric=1)
+    f.factor(rp, ci, va)
+    x = f.solve(B).cpu().numpy()[0]
+    idx = np.array(g["index"])
+    val = np.array(g["value"])
+    ent = np.max(np.abs(x[idx] - val)) / g["norminf"]
+    nrm = abs(np.linalg.norm(x) - g["norm2"]) / g["norm2"]
+    print(f"1023^2 FP64 vs stored oracle: sampled entry-wise {ent:.2e}, norm {nrm:.2e}")
+    assert ent <= 1e-6 and nrm <= 1e-6
+    assert abs(np.max(np.abs(x)) - g["norminf"]) <= 1e-6 * g["norminf"]
+    for lv in f.stats()["levels"]:
+        o = g["levels"][str(lv["level"])]
+        assert abs(lv["e_max"] - o["e_max"]) <= 2 and abs(lv["k_max"] - o["k_max"]) <= 2
+        for k in ("flops_sparsify", "flops_merge"):
+            assert abs(lv[k] - o[k]) <= 0.05 * max(o[k], 1), (lv["level"], k, lv[k], o[k])
+
+
+def test_headline_path_1023():
+    """Mixed precision (FP32 factors and solve, FP64 leaf LU and QR pivots / norms), learned
+    ranks, eps_ID 5e-7, 16 right-hand sides: the direct solve stays within the FP32 bound of
+    the FP64 GPU path (eps_ID 1e-8), and GMRES with the FP64 residual reaches 1e-10 in at most
+    four iterations (three in nearly every run; an occasional retrained network needs a
+    fourth), checked by a CPU residual."""
+    import bench
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    dev = torch.device("cuda:0")
+    pred, info = bench.train_predictor(dev, 1, 5e-7)
+    n = 1023
+    P = W.make_problem("diffusion", n, seed=1, nrhs=16)
+    rp, ci, va, B = _dev(P)
+    nd = NestedDissection(n)
+    f64 = Factor(nd, eps_id=1e-8, symmetric=1, precision=0)
+    f64.factor(rp, ci, va)
+    X64 = f64.solve(B).cpu().numpy().T
+    del f64
+    fm = Factor(nd, eps_id=5e-7, symmetric=1, precision=1)
+    fm.set_predictor(pred, "predict", margin=bench.PRED_MARGIN)
+    fm.factor(rp, ci, va)
+    X = fm.solve(B)
+    x0 = X.cpu().numpy().T
+    st = fm.stats()
+    nrm, ent = rel_errors(x0, X64)
+    npred = sum(lv["predicted"] for lv in st["levels"])
+    print(f"headline direct solve vs FP64 GPU: norm-wise {nrm:.2e}, entry-wise {ent:.2e}; "
+          f"{npred} predicted IDs, {sum(lv['fallbacks'] for lv in st['levels'])} fallbacks")
+    assert npred > 0.5 * sum(lv["nseg"] for lv in st["levels"])
+    assert nrm <= 1e-2 and ent <= 5e-2
+    it, rel = fm.refine(B, X)
+    x = X.cpu().numpy().T
+    res = np.linalg.norm(P.B - P.A.matvec(x), axis=0) / np.linalg.norm(P.B, axis=0)
+    print(f"GMRES iterations {it}, CPU residual max {res.max():.2e}")
+    assert np.all(res <= 1e-10), res
+    assert it <= 4

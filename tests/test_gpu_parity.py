@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle.nd import nested_dissection
+from oracle.nd import nested_dissection, _sides
+from parity import assert_close, rel_errors
 from oracle.spalu import Options as OOpts, factor as ofactor, solve as osolve
 
 torch = pytest.importorskip("torch")
@@ -78,7 +79,7 @@ def test_eps0_equals_dense_solve(kind, n):
     P = W.make_problem(kind, n, seed=21, nrhs=3)
     X, _, _ = _gpu_solve(P, 0.0)
     Xd = np.linalg.solve(P.A.to_dense(), P.B)
-    assert np.linalg.norm(X - Xd) <= 1e-11 * np.linalg.norm(Xd)
+    assert_close(X, Xd, 1e-11, f"{kind} {n} eps 0")
 
 
 # ------------------------------------------------------------------ FP64 parity with the oracle
@@ -90,8 +91,7 @@ def test_fp64_matches_oracle(kind, n, nrhs):
     X, f, _ = _gpu_solve(P, 1e-8)
     F = ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-8, symmetric=P.symmetric))
     Xo = osolve(F, P.B)
-    rel = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
-    assert rel <= 1e-6, rel
+    assert_close(X, Xo, 1e-6, f"{kind} {n}")
     # rank statistics agree level by level (pivot ties may move a rank by one)
     st = f.stats()
     for lv in st["levels"]:
@@ -105,7 +105,7 @@ def test_rectangular_grids(nx, ny):
     P = W.make_problem("diffusion", nx, seed=23, nrhs=2, ny=ny)
     X, _, _ = _gpu_solve(P, 1e-8, nx=nx, ny=ny)
     Xo = osolve(ofactor(P.A, nested_dissection(nx, ny), OOpts(eps=1e-8, symmetric=True)), P.B)
-    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+    assert_close(X, Xo, 1e-6, f"{nx}x{ny}")
 
 
 def test_nonsymmetric_flag_on_symmetric_matrix():
@@ -115,7 +115,7 @@ def test_nonsymmetric_flag_on_symmetric_matrix():
     X2, _, _ = _gpu_solve(P, 1e-8, symmetric=False)
     Xd = np.linalg.solve(P.A.to_dense(), P.B)
     for X in (X1, X2):
-        assert np.linalg.norm(X - Xd) <= 1e-5 * np.linalg.norm(Xd)
+        assert_close(X, Xd, 1e-5)
 
 
 # ------------------------------------------------------------------ refinement
@@ -179,7 +179,9 @@ def test_factor_solve_host_matches_separate_calls(precision):
     X4, _, _ = f.factor_solve_host(P.A.indptr, P.A.indices, P.A.data, np.zeros((0, n * n)))
     assert X4.shape == (0, n * n)
     with pytest.raises(SpaluError):                 # nnz above the handle's capacity
-        f.factor_solve_host(P.A.indptr, P.A.indices, np.zeros(6 * n * n), Bh)
+        f.factor_solve_host(P.A.indptr, np.zeros(6 * n * n, np.int32), np.zeros(6 * n * n), Bh)
+    with pytest.raises(ValueError):                 # a short right-hand side is refused before the call
+        f.factor_solve_host(P.A.indptr, P.A.indices, P.A.data, Bh[:, :-1])
 
 
 def test_errors_are_reported_not_raised_on_device():
@@ -230,8 +232,9 @@ def test_mixed_precision_refined(kind, n, eps):
     torch.cuda.synchronize()
     x0 = X.cpu().numpy().T
     Xo = osolve(ofactor(P.A, nested_dissection(n, n), OOpts(eps=eps, symmetric=P.symmetric)), P.B)
-    err = np.linalg.norm(x0 - Xo) / np.linalg.norm(Xo)
-    print(f"mixed {kind} {n}: direct-solve error vs FP64 oracle {err:.2e}")
+    err_n, err = rel_errors(x0, Xo)
+    print(f"mixed {kind} {n}: direct-solve error vs FP64 oracle {err_n:.2e} (norm-wise), "
+          f"{err:.2e} (entry-wise)")
     # FP32 factors: forward error ~ cond x 6e-8.  The k^2-shifted Helmholtz operator is
     # indefinite and far worse conditioned than the others: over seeds 28-30 its 63^2 direct
     # solve lands anywhere in 5e-4..2e-2, so it gets a wider bound; the refinement to 1e-10
@@ -254,7 +257,7 @@ def test_many_rhs_ragged_chunks(nrhs):
     P = W.make_problem("diffusion", n, seed=41, nrhs=nrhs)
     X, _, _ = _gpu_solve(P, 1e-8)
     Xo = osolve(ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-8, symmetric=True)), P.B)
-    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+    assert_close(X, Xo, 1e-6, f"{nrhs} RHS")
     rp, ci, va, B = _dev(P)
     f = Factor(NestedDissection(n), eps_id=1e-6, symmetric=1, precision=1)
     f.factor(rp, ci, va)
@@ -325,7 +328,7 @@ def test_sparsify_budgets_and_tuning_match_oracle(precision):
 
     def err(f):
         x = f.solve(B).cpu().numpy().T
-        return np.linalg.norm(x - Xo) / np.linalg.norm(Xo)
+        return max(rel_errors(x, Xo))
 
     for ctas in (0, 4, 12, 16):
         f = Factor(nd, eps_id=eps, symmetric=1, precision=precision, spars_ctas=ctas)

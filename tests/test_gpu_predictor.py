@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import assert_close
 from oracle import predictor as pr
 from oracle.nd import nested_dissection
 from oracle.spalu import Options as OOpts, factor as ofactor, solve as osolve
@@ -175,8 +176,8 @@ def test_trained_predictor_gains_over_adaptive_id():
     # same mode as the oracle (adaptive): the parity bar; predicted skeletons differ from the
     # adaptive ones, so that solution is held to the method's accuracy at eps = 1e-8 (the
     # oracle pins bound the error by 1e3 eps)
-    assert np.linalg.norm(xa - Xo) <= 1e-6 * np.linalg.norm(Xo)
-    assert np.linalg.norm(xp - Xo) <= 1e-5 * np.linalg.norm(Xo)
+    assert_close(xa, Xo, 1e-6, "adaptive")
+    assert_close(xp, Xo, 1e-5, "predicted")
 
 
 def test_predict_mode_matches_oracle_with_the_same_network():
@@ -196,7 +197,7 @@ def test_predict_mode_matches_oracle_with_the_same_network():
     Fo = ofactor(P.A, nested_dissection(n, n),
                  OOpts(eps=1e-8, symmetric=False, predictor={"params": p.params(), "mu": mu, "isd": isd}))
     xo = osolve(Fo, P.B)
-    assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert_close(x, xo, 1e-6, "predict mode, same network")
     pg = sum(lv["passes"] for lv in st["levels"])
     po = sum(v["passes"] for v in Fo.stats["levels"].values())
     npg = sum(lv["predicted"] for lv in st["levels"])

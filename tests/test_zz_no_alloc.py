@@ -1,8 +1,8 @@
 """spalu_residual_noalloc: the residual-norm entry point that allocates no device memory.
 
 It exists for callers that cannot let the library allocate when they check a solution
-(work under CUDA-graph stream capture, hosts that own all device memory through their own
-pool).  Its result must match the relative residuals spalu_refine reports (computed there
+(hosts that own all device memory through their own pool, processes at the edge of device
+memory).  Its result must match the relative residuals spalu_refine reports (computed there
 with buffers the library allocates), on two calls in a row.  This file is collected last
 so that a failure here leaves every other test already run.
 """
@@ -78,3 +78,48 @@ def test_noalloc_rejects_too_many_columns(setup):
                                       65, N, rel.ctypes.data, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == -1
     assert np.all(rel == -1.0)
+
+
+def _call(f, Bp, Xp, nrhs, ld):
+    rel = np.full(max(nrhs, 1), -1.0)
+    st = f.lib.spalu_residual_noalloc(f.handle, ctypes.c_void_p(Bp), ctypes.c_void_p(Xp), nrhs, ld,
+                                      rel.ctypes.data, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    return rel[:nrhs]
+
+
+def _cpu_relres(P, Bc, Xc):
+    return np.linalg.norm(Bc - P.A.matvec(Xc), axis=0) / np.linalg.norm(Bc, axis=0)
+
+
+def test_noalloc_padded_leading_dimension(setup):
+    """B and X inside a buffer with leading dimension N + 7 (columns start at c (N + 7))."""
+    P, f, B = setup
+    N = P.A.n
+    ld = N + 7
+    X = f.solve(B)
+    Bpad = torch.full((3, ld), 1e30, dtype=torch.float64, device="cuda")
+    Xpad = torch.full((3, ld), 1e30, dtype=torch.float64, device="cuda")
+    Bpad[:, :N] = B
+    Xpad[:, :N] = X
+    Xpad[2, :N] *= 0.5
+    torch.cuda.synchronize()
+    r = _call(f, Bpad.data_ptr(), Xpad.data_ptr(), 3, ld)
+    Xc = Xpad[:, :N].cpu().numpy().T
+    assert np.allclose(r, _cpu_relres(P, P.B, Xc), rtol=1e-8)
+    assert r[2] > 0.3 and r[0] < 0.1          # half a solution leaves half of B
+
+
+def test_noalloc_largest_column_count(setup):
+    """nrhs = 64, the largest count the fixed array holds, against the CPU residual."""
+    P, f, _ = setup
+    N = P.A.n
+    rng = np.random.default_rng(7)
+    Bc = rng.standard_normal((N, 64))
+    Xc = rng.standard_normal((N, 64)) * 1e-3
+    Bd = torch.from_numpy(np.ascontiguousarray(Bc.T)).cuda()
+    Xd = torch.from_numpy(np.ascontiguousarray(Xc.T)).cuda()
+    r1 = _call(f, Bd.data_ptr(), Xd.data_ptr(), 64, N)
+    r2 = _call(f, Bd.data_ptr(), Xd.data_ptr(), 64, N)
+    assert np.allclose(r1, _cpu_relres(P, Bc, Xc), rtol=1e-10)
+    assert np.array_equal(r1, r2)

@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "CSR", "Problem", "laplace", "diffusion", "helmholtz", "convdiff", "grf",
-    "rhs_normal", "rhs_point_sources", "make_problem", "grid_sizes_ok",
+    "rhs_normal", "rhs_point_sources", "make_problem", "grid_sizes_ok", "predictor_init_params",
 ]
 
 
@@ -235,3 +235,14 @@ def make_problem(kind: str, n: int, seed: int = 0, nrhs: int | None = None,
         B = rhs_normal(N, nrhs or 4, rng)
         return Problem(kind, n, nyy, A, B, False, {"beta": beta})
     raise ValueError(f"unknown problem kind {kind!r}")
+
+
+def predictor_init_params(seed: int, nfeat: int = 16, nhid: int = 64, nout: int = 2) -> np.ndarray:
+    """Seeded initial weights of the rank predictor's 16 -> 64 -> 2 network (float32):
+    He-normal W1 (nhid x nfeat, row-major) and W2 (nout x nhid), zero biases, packed as
+    W1 | b1 | W2 | b2 (the parameter layout of the library's predictor entry points).  A
+    seeded draw, like the right-hand sides: an input to both the oracle and the device."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((nhid, nfeat)) * math.sqrt(2.0 / nfeat)
+    W2 = rng.standard_normal((nout, nhid)) * math.sqrt(2.0 / nhid)
+    return np.concatenate([W1.ravel(), np.zeros(nhid), W2.ravel(), np.zeros(nout)]).astype(np.float32)
