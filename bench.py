@@ -205,17 +205,6 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
-# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the same
-# workload (profiles/leaf_elimination_diffusion1023_mixed.md, profiles/leaf_solve_diffusion1023_mixed.md),
-# keyed by (kernel, mixed precision); a kernel missing here reports null traffic.  Re-capture
-# after changing one of these kernels.
-PROFILED_TRAFFIC = {
-    ("leaf_lu_kernel+leaf_schur_kernel", True): 835_925_788,   # per launch pair
-    ("leaf_solve_kernel", True): 569_761_536,
-    ("leaf_bwd_g_kernel", True): 328_024_576,
-}
-
-
 def _leaf_flops_split():
     """(FP64 FLOPs of the band LU, FLOPs of the 60 band solves) of one leaf elimination."""
     n, b = 225, 15
@@ -223,72 +212,89 @@ def _leaf_flops_split():
     return lu, leaf_algorithmic_flops() - lu
 
 
-def _dominant(st, steps, ms_per_step: float):
-    """The kernel with the largest share of the step: the sparsification (all levels).  Its
-    phases are chains of short dependent steps per segment (barriers, shared-memory latency,
-    instruction fetch at the finest level), so no FLOP or byte roof applies; the captures in
-    profiles/ show every pipe below a fifth of its peak and DRAM below 1 %."""
-    tms = st["timing_ms"]
-    sp = sum(v for k, v in tms.items() if k.startswith("sparsify_l")) / steps
-    return {"kernel": "sparsify_kernel (all levels, with seg_order_kernel and seg_invert_kernel)",
-            "bound": "latency", "ms_per_step": sp, "share_of_step": sp / ms_per_step,
-            "evidence": ["profiles/sparsify_kernel_l11_diffusion1023_mixed.md",
-                         "profiles/sparsify_kernel_l12_diffusion1023_mixed.md"]}
+def measured_alu_peaks() -> dict:
+    """FP64 and FP32 FMA rates of this GPU's CUDA cores, measured by the library's probe
+    kernel (FLOP/s); the unit-count figures (152 SMs x 4 / 256 FLOP per clock x 2070 MHz)
+    only where the probe cannot run."""
+    try:
+        from paper_2408_14193_gb300.spalu import measure_fma_peak
+        return {"fp64": measure_fma_peak(0), "fp32": measure_fma_peak(1), "source": "measured (FMA probe kernel)"}
+    except Exception as exc:                 # noqa: BLE001
+        clk = SM_MAX_MHZ * 1e6
+        return {"fp64": N_SM * FP64_FLOP_PER_CLK_SM * clk, "fp32": N_SM * FP32_FLOP_PER_CLK_SM * clk,
+                "source": f"derived from unit counts ({exc})"}
 
 
-def _roofline(st, steps, fp32: bool, hbm_gbs: float):
-    """Roofline of the dominant kernel among those timed alone in a phase: achieved =
-    algorithmic work per launch / average launch time.
+def _sum_levels(st, key):
+    return float(sum(lv.get(key, 0) for lv in st["levels"]))
 
-    * leaf_factor (leaf_lu_kernel + leaf_schur_kernel): bound by the FP64 pipe (band LU) plus,
-      in mixed mode, the FP32 pipe (band solves);
-    * leaf_solve_kernel (forward band sweeps, one launch = 4096 leaves x 16 right-hand sides):
-      HBM bytes = the L multipliers (15 per column), U rows (15 superdiagonals and the
-      reciprocal pivot), the pivots, and the 225 interior values read and written;
-    * leaf_bwd_g_kernel (mixed backward step): the FP32 A_II^{-1} A_Id (225 x 60), the 60 side
-      values gathered and the 225 interior values read and written;
-      in FP64 the backward step is the band sweep again, with the side couplings."""
+
+def _roofline(st, steps, fp32: bool, hbm_gbs: float, alu: dict):
+    """Roofline of the dominant kernel of the step: the sparsification (sparsify_kernel, all
+    levels; its launches carry the ID, the transforms and the remainder eliminations).
+    achieved = the algorithmic FLOPs its launches counted (per level: sketch 2 h |F| e,
+    pivoted QR, interpolation, transforms, remainder eliminations; work.cuh) / their CUDA-event
+    time inside the timed steps; peak = the measured FMA rate of the precision its arithmetic
+    runs in (FP32 in the mixed path, FP64 otherwise)."""
     tms, tcount = st["timing_ms"], st["timing_count"]
+    sp_ms = sum(v for k, v in tms.items() if k.startswith("sparsify_l"))
+    launches = sum(v for k, v in tcount.items() if k.startswith("sparsify_l"))
+    flops = _sum_levels(st, "flops_sparsify")          # per factorization = per step
+    peak = alu["fp32" if fp32 else "fp64"]
+    ach = flops / (sp_ms / steps / 1e3)
+    per_level = []
+    for lv in st["levels"]:
+        t = tms.get(f"sparsify_l{lv['level']}", 0.0) / steps
+        if t > 0:
+            per_level.append({"level": lv["level"], "ms": round(t, 4), "gflop": round(lv["flops_sparsify"] / 1e9, 4),
+                              "tflops": round(lv["flops_sparsify"] / (t / 1e3) / 1e12, 4)})
+    return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "kernel": "sparsify_kernel (all levels)",
+            "algorithmic_flops": flops, "launches_per_step": launches / steps,
+            "launch_ms": sp_ms / launches if launches else None, "share_of_step_ms": sp_ms / steps,
+            "peak_source": f"{alu['source']}, {'FP32' if fp32 else 'FP64'} CUDA cores",
+            "per_level": per_level}
+
+
+def _step_roofline(st, steps, ms_per_step: float, fp32: bool, nrhs: int, n_solves: int, gmres_iters: int,
+                   hbm_gbs: float, alu: dict):
+    """Whole-step roofline: T_roof = sum over phases of max(FP64 FLOPs / P64 + FP32 FLOPs /
+    P32, bytes / HBM), against the measured step time.  Work per phase:
+      leaf elimination   band LU (FP64) + 60 band solves per leaf (FP32 in the mixed path);
+      sparsify, merge    the counted algorithmic FLOPs (precision of the path);
+      each solve         bytes: the leaf factors (band L/U, pivots; the mixed path's backward
+                         step reads the 225 x 60 operator), the segment and separator factors
+                         twice (forward, backward), and the solve vector read and written per
+                         sweep (leaf sweeps, the 2 level sweeps);
+      GMRES              per iteration: SpMV (5 FMA per row and column) and modified
+                         Gram-Schmidt against j + 1 basis vectors (2 FMA each), FP64."""
+    N = N_SIDE * N_SIDE
     nleaf = ((N_SIDE + 1) // 16) ** 2
-    clk = SM_MAX_MHZ * 1e6
-    p64 = N_SM * FP64_FLOP_PER_CLK_SM * clk
-    p32 = N_SM * FP32_FLOP_PER_CLK_SM * clk
-    tb = 4 if fp32 else 8                  # factors and solve vectors share the precision
-    sweep = 225 * (15 + 15 + 1) * tb + 225 * 4 + 2 * 225 * NRHS * tb
-    cand = {}
-    if "leaf_factor" in tms:
-        lu, sv = _leaf_flops_split()
-        t_roof = nleaf * (lu / p64 + sv / (p32 if fp32 else p64))
-        cand["leaf_lu_kernel+leaf_schur_kernel"] = ("alu", tms["leaf_factor"], tcount["leaf_factor"],
-                                                    nleaf * (lu + sv), t_roof)
-    if "leaf_solve_fwd" in tms:
-        byts = nleaf * sweep
-        cand["leaf_solve_kernel"] = ("hbm", tms["leaf_solve_fwd"], tcount["leaf_solve_fwd"], byts,
-                                     byts / (hbm_gbs * 1e9))
-    if "leaf_solve_bwd" in tms:
-        if fp32:
-            byts = nleaf * (225 * 60 * 4 + 60 * NRHS * 4 + 2 * 225 * NRHS * 4)
-            name = "leaf_bwd_g_kernel"
-        else:
-            byts = nleaf * sweep
-            name = "leaf_solve_kernel(backward)"
-        cand[name] = ("hbm", tms["leaf_solve_bwd"], tcount["leaf_solve_bwd"], byts, byts / (hbm_gbs * 1e9))
-    dom = max(cand, key=lambda k: cand[k][1])
-    bound, tot, cnt, work, t_roof = cand[dom]
-    dur_s = tot / cnt / 1e3
-    if bound == "hbm":
-        ach = work / dur_s / 1e9
-        peak, unit, src = hbm_gbs, "GB/s", "measured (MEASURED_PEAKS.json hbm_gbs)"
-    else:
-        ach = work / dur_s / 1e12
-        peak = work / t_roof / 1e12
-        unit = "TFLOP/s"
-        src = ("derived: FP64 band LU at 152 SMs x 4 FLOP/clk x 2070 MHz" +
-               (" + FP32 band solves at 152 x 256 FLOP/clk x 2070 MHz" if fp32 else ""))
-    traffic = PROFILED_TRAFFIC.get((dom, fp32))
-    return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-            "traffic": traffic, "kernel": dom, "algorithmic_bytes" if bound == "hbm" else "algorithmic_flops": work,
-            "launch_ms": dur_s * 1e3, "share_of_step_ms": tot / steps, "peak_source": src}
+    p64, p32 = alu["fp64"], alu["fp32"]
+    pa = p32 if fp32 else p64
+    hb = hbm_gbs * 1e9
+    tb = 4 if fp32 else 8
+    lu, sv = _leaf_flops_split()
+    phases = {}
+    phases["leaf_factor"] = nleaf * (lu / p64 + sv / pa)
+    phases["sparsify"] = _sum_levels(st, "flops_sparsify") / pa
+    phases["merge"] = _sum_levels(st, "flops_merge") / pa
+    tape = _sum_levels(st, "bytes_seg") + _sum_levels(st, "bytes_sep")
+    leaf_f = nleaf * (225 * 31 * tb + 225 * 4)
+    leaf_b = nleaf * 225 * 60 * 4 if fp32 else leaf_f
+    vec = N * nrhs * tb
+    solve_bytes = leaf_f + leaf_b + 2 * tape + 8 * vec
+    phases["solves"] = n_solves * solve_bytes / hb
+    g64 = 0.0
+    for j in range(gmres_iters):
+        g64 += N * nrhs * (10 + 4 * (j + 1))
+    g64 += N * nrhs * 10                            # the residual of the initial guess
+    phases["gmres"] = g64 / p64
+    t_roof = sum(phases.values())
+    return {"t_roof_ms": t_roof * 1e3, "t_measured_ms": ms_per_step, "frac": t_roof * 1e3 / ms_per_step,
+            "phases_roof_ms": {k: round(v * 1e3, 4) for k, v in phases.items()},
+            "solve_bytes": solve_bytes, "peaks": {"fp64_tflops": p64 / 1e12, "fp32_tflops": p32 / 1e12,
+                                                  "hbm_gbs": hbm_gbs, "alu_source": alu["source"]}}
 
 
 def _nvtx(push: bool):
@@ -493,6 +499,7 @@ def run_ours(args):
         return {"ms": ms, "iters": max(iters), "relres": max(rels), "launches": launches,
                 "st": st, "clocks": clocks}
 
+    alu = measured_alu_peaks()
     pred, pred_info = train_predictor(dev, 1, args.mixed_eps, args.pred_epochs)
     head = measure(1, args.mixed_eps, True, pred)  # mixed precision + learned ranks: the headline
     if args.only_mixed:                           # profiling runs: the headline path alone
@@ -500,6 +507,7 @@ def run_ours(args):
                           "gmres_iters": head["iters"]}), flush=True)
         return 0
     base = measure(0, EPS_ID, False)              # plain FP64 GPU form
+    base_loose = measure(0, args.mixed_eps, False)   # FP64 at the mixed path's eps_ID
     noml = measure(1, args.mixed_eps, False)      # ablation: mixed precision, adaptive ID
 
     # end to end through the host-memory entry points (pinned host buffers), headline path
@@ -555,7 +563,10 @@ def run_ours(args):
         "fp64_plain": {"value": base_value, "unit": "DOF/s", "ms_per_step": base["ms"] / args.steps,
                        "eps_id": EPS_ID, "relres_max": base["relres"], "gmres_iters": base["iters"],
                        "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(base["st"]["timing_ms"].items())},
-                       "roofline": _roofline(base["st"], args.steps, False, hbm)},
+                       "roofline": _roofline(base["st"], args.steps, False, hbm, alu)},
+        "fp64_plain_same_eps": {"value": job_value(ws, args.steps, N, base_loose["ms"] / 1e3), "unit": "DOF/s",
+                                "ms_per_step": base_loose["ms"] / args.steps, "eps_id": args.mixed_eps,
+                                "relres_max": base_loose["relres"], "gmres_iters": base_loose["iters"]},
         "mixed_adaptive": {"value": noml_value, "unit": "DOF/s", "ms_per_step": noml["ms"] / args.steps,
                            "relres_max": noml["relres"], "gmres_iters": noml["iters"],
                            "id_passes": sum(lv["passes"] for lv in noml["st"]["levels"])},
@@ -569,8 +580,9 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(A.data.nbytes + A.indptr.nbytes + A.indices.nbytes + P.B.nbytes),
                 "d2h_bytes_per_step": int(P.B.nbytes), "relres_max": e2e_rel},
         "gpu_launches": int(head["launches"]),
-        "roofline": _roofline(st, args.steps, True, hbm),
-        "dominant": _dominant(st, args.steps, head["ms"] / args.steps),
+        "roofline": _roofline(st, args.steps, True, hbm, alu),
+        "step_roofline": _step_roofline(st, args.steps, head["ms"] / args.steps, True, NRHS, 1 + head["iters"],
+                                        head["iters"], hbm, alu),
         "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(st["timing_ms"].items())},
         "factor_stats": {"q_tilde": st["q_tilde"], "levels": st["levels"]},
         "cpu_baseline": cpu,

@@ -1,8 +1,8 @@
 """Host logic of bench.py on the CPU.  Multi-rank, world size 2: the max-over-ranks timing
 reduction over gloo (each rank its own spawned process, rendezvous on 127.0.0.1, as under
 torchrun), the whole-job (weak-scaling) throughput, and the reference arm's rule that rank 0
-alone runs and prints.  Measurement: the roofline and dominant-kernel arithmetic of the bench
-line.  No GPU is touched."""
+alone runs and prints.  Measurement: the roofline arithmetic of the bench line (the
+sparsification against the measured FMA peak, the whole-step roofline).  No GPU is touched."""
 import json
 import os
 import socket
@@ -75,28 +75,28 @@ def test_reference_arm_runs_on_rank0_only():
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["h2d_bytes_per_step"] == 0
 
 
-def test_roofline_and_dominant_arithmetic():
-    """The bench line's roofline and dominant-kernel entries from synthetic phase timings:
-    the largest timed phase among those with a roof is chosen, achieved = algorithmic work /
-    average launch time, frac = achieved / peak; the dominant entry is the sparsification's
-    share of the step."""
+def test_roofline_arithmetic():
+    """The bench line's roofline of the sparsification from synthetic timings and counters:
+    achieved = counted algorithmic FLOPs per step / sparsify time per step, frac = achieved /
+    measured FMA peak of the path's precision; the whole-step roofline adds up its phases."""
     sys.path.insert(0, ROOT)
     import bench
     steps = 5
-    st = {"timing_ms": {"leaf_factor": 5 * 1.6, "leaf_solve_fwd": 20 * 0.25, "leaf_solve_bwd": 20 * 0.14,
-                        "sparsify_l12": 5 * 2.0, "sparsify_l11": 5 * 1.5},
-          "timing_count": {"leaf_factor": 5, "leaf_solve_fwd": 20, "leaf_solve_bwd": 20,
-                           "sparsify_l12": 5, "sparsify_l11": 5}}
-    r = bench._roofline(st, steps, True, 6800.0)
-    assert r["kernel"] == "leaf_lu_kernel+leaf_schur_kernel" and r["bound"] == "alu"
-    assert r["launch_ms"] == pytest.approx(1.6) and r["share_of_step_ms"] == pytest.approx(1.6)
-    assert r["achieved"] == pytest.approx(r["algorithmic_flops"] / 1.6e-3 / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"]) and 0 < r["frac"] < 1
-    # with the leaf elimination faster, the forward sweeps (HBM-bound) are the largest phase
-    st2 = {"timing_ms": dict(st["timing_ms"], leaf_factor=5 * 0.5), "timing_count": st["timing_count"]}
-    r2 = bench._roofline(st2, steps, True, 6800.0)
-    assert r2["kernel"] == "leaf_solve_kernel" and r2["unit"] == "GB/s" and r2["peak"] == 6800.0
-    assert r2["achieved"] == pytest.approx(r2["algorithmic_bytes"] / 0.25e-3 / 1e9)
-    dmn = bench._dominant(st, steps, 18.0)
-    assert dmn["ms_per_step"] == pytest.approx(3.5) and dmn["share_of_step"] == pytest.approx(3.5 / 18.0)
-    assert dmn["bound"] == "latency"
+    st = {"timing_ms": {"leaf_factor": 5 * 1.6, "sparsify_l12": 5 * 2.0, "sparsify_l11": 5 * 1.5},
+          "timing_count": {"leaf_factor": 5, "sparsify_l12": 5, "sparsify_l11": 5},
+          "levels": [{"level": 11, "flops_sparsify": 3e9, "flops_merge": 1e8, "bytes_seg": 2e7, "bytes_sep": 4e6},
+                     {"level": 12, "flops_sparsify": 4e9, "flops_merge": 2e8, "bytes_seg": 3e7, "bytes_sep": 5e6}]}
+    alu = {"fp64": 1.2e12, "fp32": 75e12, "source": "synthetic"}
+    r = bench._roofline(st, steps, True, 6800.0, alu)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["algorithmic_flops"] == pytest.approx(7e9)
+    assert r["achieved"] == pytest.approx(7e9 / 3.5e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 75.0)
+    assert r["launch_ms"] == pytest.approx(3.5 / 2) and r["share_of_step_ms"] == pytest.approx(3.5)
+    assert [p["level"] for p in r["per_level"]] == [11, 12]
+    r64 = bench._roofline(st, steps, False, 6800.0, alu)
+    assert r64["peak"] == pytest.approx(1.2) and r64["frac"] == pytest.approx(r64["achieved"] / 1.2)
+    sr = bench._step_roofline(st, steps, 18.0, True, 16, 4, 3, 6800.0, alu)
+    assert sr["t_roof_ms"] == pytest.approx(sum(sr["phases_roof_ms"].values()), rel=1e-3)
+    assert sr["phases_roof_ms"]["sparsify"] == pytest.approx(7e9 / 75e12 * 1e3, rel=1e-3)
+    assert 0 < sr["frac"] < 1 and sr["frac"] == pytest.approx(sr["t_roof_ms"] / 18.0)
