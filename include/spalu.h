@@ -191,6 +191,26 @@ spalu_status spalu_factor_solve_host(spalu_factor_t f, const int* rowptr, const 
                                      int ld, int refine, int* iters, double* relres,
                                      spalu_stream_t stream);
 
+/* The whole step as one CUDA graph (scheduling; not in the paper): the numeric factorization
+ * of the device CSR arrays (as spalu_factor_numeric), the direct solve X = spaLU^{-1} B (as
+ * spalu_solve) and GMRES refinement of X (as spalu_refine), with one host synchronisation at
+ * the end.  The first call for a given set of arguments (the same pointers, nnz, nrhs, ld)
+ * runs the three calls plainly and then captures the step; later calls with the same
+ * arguments replay the graph.  Inside it, a guard kernel after the factorization checks that
+ * the new factor still fits the solve kernels' capacities fixed at capture (per-level largest
+ * segment, separator skeleton and separator boundary, leaf upper bandwidth); when it does not,
+ * the solve and refinement are skipped in the graph and redone outside it (the next call
+ * captures again).  The refinement inside the graph is one GMRES cycle of up to K =
+ * min(m, max(4, steps of the last plain refinement + 2)) Arnoldi steps, each a conditional
+ * node that runs only while a column is above the tolerance; columns still above it after
+ * the graph continue with spalu_refine.  B and X: device, column-major, leading dimension ld;
+ * X must not alias B; 1 <= nrhs.  The arrays must stay valid between calls that reuse them.
+ * iters / relres (host, may be NULL) as in spalu_refine.  Per-phase timing
+ * (spalu_set_timing) records nothing inside the graph.  Synchronises the stream. */
+spalu_status spalu_factor_solve_graph(spalu_factor_t f, const int* rowptr, const int* colind, const double* val,
+                                      int nnz, const double* B, double* X, int nrhs, int ld, int* iters,
+                                      double* relres, spalu_stream_t stream);
+
 /* JSON summary of the last factorization: per level the segment sizes and ranks, the
  * largest separator skeleton, the number of IDs computed ("passes"), of predicted one-pass
  * IDs and of those that fell back to the adaptive schedule; q~ (Sec. 6); device bytes

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <map>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -32,6 +33,17 @@ struct GmresWork {
   double* hcol = nullptr;   // device coefficients (m+2) * nrhs
   double* vs = nullptr;     // (m+2) * nrhs: basis vector j is vs[j] x V_j (stored unnormalized)
   double* vec = nullptr;    // nrhs scalars
+  // device-side least-squares state of the Arnoldi cycle (one column per right-hand side)
+  double* H = nullptr;      // nrhs * (m+1) * m  rotated Hessenberg columns
+  double* cs = nullptr;     // nrhs * m          Givens cosines
+  double* sn = nullptr;     // nrhs * m          Givens sines
+  double* g = nullptr;      // nrhs * (m+1)      rotated right-hand side
+  double* y = nullptr;      // m * nrhs          coefficients of the update
+  double* bn = nullptr;     // nrhs              ||b_c||
+  double* beta = nullptr;   // nrhs              ||b_c - A x_c||
+  int* st = nullptr;        // 4 * nrhs: [active, kdim, its, converged-at-start] per column
+  int* flag = nullptr;      // [0]: some column still active
+  int* hflag = nullptr;     // page-locked copy of flag[0]
 };
 
 namespace {
@@ -53,9 +65,23 @@ struct PhaseTimer {
     cudaEventCreate(&e);
     return e;
   }
-  // open an interval on stream s; returns its index (or -1 when timing is off)
+  // While the step graph is captured, intervals on its top-level stream become event nodes of
+  // the graph (kept in grecs and read after every replay); other capturing streams (the bodies
+  // of conditional nodes, which cannot hold event nodes) record nothing.
+  cudaStream_t cap_top = nullptr;
+  std::vector<Rec> grecs;
+  // open an interval on stream s; returns its index (-1 when timing is off or not possible)
   int begin(const std::string& name, cudaStream_t s) {
     if (!on) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return -1;
+    if (cs != cudaStreamCaptureStatusNone) {
+      if (s != cap_top) return -1;
+      Rec r{name, take(), take()};
+      if (cudaEventRecord(r.a, s) != cudaSuccess) return -1;
+      grecs.push_back(r);
+      return -2 - ((int)grecs.size() - 1);
+    }
     Rec r{name, take(), take()};
     cudaEventRecord(r.a, s);
     recs.push_back(r);
@@ -63,6 +89,19 @@ struct PhaseTimer {
   }
   void end(int i, cudaStream_t s) {
     if (i >= 0) cudaEventRecord(recs[i].b, s);
+    else if (i <= -2) cudaEventRecord(grecs[-2 - i].b, s);
+  }
+  // add the intervals of the last replay of the step graph to the sums (events kept)
+  void collect_graph() {
+    for (auto& r : grecs) {
+      float t = 0.f;
+      cudaEventSynchronize(r.b);
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) { ms[r.name] += t; count[r.name] += 1; }
+    }
+  }
+  void drop_graph() {
+    for (auto& r : grecs) { pool.push_back(r.a); pool.push_back(r.b); }
+    grecs.clear();
   }
   // fold the finished intervals into the sums
   void collect() {
@@ -78,6 +117,7 @@ struct PhaseTimer {
   void reset() { collect(); ms.clear(); count.clear(); }
   ~PhaseTimer() {
     for (auto& r : recs) { pool.push_back(r.a); pool.push_back(r.b); }
+    drop_graph();
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
@@ -111,6 +151,18 @@ struct spalu_factor_s {
   GmresWork gw;
   PhaseTimer timer;
   int kumax = 30;            // upper bandwidth of the leaf U factors (read after each factor)
+  int gmres_hint = 1;        // Arnoldi steps the last single-cycle refinement needed
+  struct StepGraph {         // spalu_factor_solve_graph: the captured step and what it was captured for
+    cudaGraphExec_t exec = nullptr;
+    const void* key[6] = {};
+    int nnz = -1, nrhs = -1, ld = -1, K = 0;
+    bool timed = false;      // captured with per-phase timing on (event nodes in the graph)
+    int* d_ref = nullptr;    // guard references: captured level maxima (3 per level) and kumax
+    int* d_ok = nullptr;     // guard result
+    int* h_out = nullptr;    // page-locked: guard result, some column active
+    long long n_pre = 0, n_ok = 0;   // kernels of the graph: before the guard's node, in its body
+    std::vector<long long> n_step;   // ... and in each Arnoldi step's node
+  } sg;
   int* d_lstat = nullptr;    // [LS_N * (L + 1)] per-level counters (factor kernels)
   unsigned long long* d_flops = nullptr;   // [4 * (L + 1)] per level: algorithmic FLOPs of the sparsify
                                            // and merge phases, bytes of the segment and separator factors
@@ -150,10 +202,19 @@ bool side_ok(int n) {
   return (q & (q - 1)) == 0;
 }
 
+// With SPALU_DEBUG set in the environment, a failing CUDA call is reported on stderr.
+void report_cuda(const char* what, cudaError_t e, int line) {
+  static const bool on = std::getenv("SPALU_DEBUG") != nullptr;
+  if (on) std::fprintf(stderr, "spalu: %s failed at api.cu:%d: %s\n", what, line, cudaGetErrorString(e));
+}
+
 #define CUDA_TRY(x)                                   \
   do {                                                \
     cudaError_t _e = (x);                             \
-    if (_e != cudaSuccess) return SPALU_ERR_CUDA;     \
+    if (_e != cudaSuccess) {                          \
+      report_cuda(#x, _e, __LINE__);                  \
+      return SPALU_ERR_CUDA;                          \
+    }                                                 \
   } while (0)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -301,22 +362,135 @@ __global__ void __launch_bounds__(VB, 4) mgs_kernel(int n, int nrhs, const doubl
   column_sums(s, c0, nrhs, part, cnt, out, sq, q ? qs : nullptr, inv_out);
 }
 
-// X_c += sum_i y[i][c] Z_i,c for i = 0..k-1, in that order (Z_i = Z + i * ldz * nrhs)
+// X_c += sum_i y[i][c] Z_i,c for i = 0..k_c-1, in that order (Z_i = Z + i * ldz * nrhs); k_c = k,
+// or with st the steps column c took in the cycle (later Z_i were not written for it)
 __global__ void __launch_bounds__(VB, 4) combine_kernel(int n, int nrhs, int k, const double* __restrict__ y,
                                                      const double* __restrict__ Z, size_t ldz,
-                                                     double* __restrict__ X, int ldx) {
+                                                     double* __restrict__ X, int ldx, const int* st) {
   pdl_enter();
   const int c0 = blockIdx.y * RC;
   const int nc = nrhs - c0 < RC ? nrhs - c0 : RC;
+  int kc[RC];
+#pragma unroll
+  for (int kk = 0; kk < RC; ++kk) {
+    const int c = c0 + kk;
+    kc[kk] = (st && kk < nc) ? (st[4 * c + 3] ? 0 : min(k, st[4 * c + 1])) : k;
+  }
   for (long long r = blockIdx.x * (long long)VB + threadIdx.x; r < n; r += (long long)gridDim.x * VB) {
 #pragma unroll
     for (int kk = 0; kk < RC; ++kk)
       if (kk < nc) {
         const int c = c0 + kk;
         double xv = X[r + (size_t)ldx * c];
-        for (int i = 0; i < k; ++i) xv += y[(size_t)i * nrhs + c] * Z[(size_t)i * ldz * nrhs + r + ldz * c];
+        for (int i = 0; i < kc[kk]; ++i) xv += y[(size_t)i * nrhs + c] * Z[(size_t)i * ldz * nrhs + r + ldz * c];
         X[r + (size_t)ldx * c] = xv;
       }
+  }
+}
+
+// ---- least-squares side of GMRES on the device (one thread per column, one block): the
+// Givens rotations that keep the Hessenberg matrix upper triangular, the residual estimate
+// |g_{j+1}| (the stop test) and the back substitution for the update coefficients, so the
+// Arnoldi loop needs no host round trip.  Column c's state st[4c..4c+3] = {active, steps of
+// this cycle, steps in all, converged when the cycle began}; flag[0] = some column active,
+// also passed to a graph conditional node when one is given.
+constexpr int GB = 256;
+
+__device__ __forceinline__ void publish_active(int any, int* flag, cudaGraphConditionalHandle h, int use_h) {
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    flag[0] = any;
+    if (use_h) cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
+}
+
+// start of a cycle: beta = ||b - A x|| is in; V_0 = r / beta (scale vs_0), g = beta e_1;
+// columns already at the tolerance stay out of the cycle (scale 0)
+__global__ void __launch_bounds__(GB) gmres_begin_kernel(int nrhs, int m, double tol, const double* bn,
+                                                       const double* beta, double* vs, double* g, int* st,
+                                                       int first, int* flag, cudaGraphConditionalHandle h,
+                                                       int use_h) {
+  int any = 0;
+  for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+    const double b = bn[c], r = beta[c];
+    const bool done = b == 0.0 || r <= tol * b;
+    const double bsc = done ? 0.0 : r;
+    vs[c] = bsc != 0.0 ? 1.0 / bsc : 0.0;
+    g[(size_t)c * (m + 1)] = bsc;
+    int* sc = st + 4 * c;
+    sc[0] = done ? 0 : 1;
+    sc[1] = 0;
+    if (first) sc[2] = 0;
+    sc[3] = done ? 1 : 0;
+    any |= done ? 0 : 1;
+  }
+  publish_active(any, flag, h, use_h);
+}
+
+// after Arnoldi step j: the new Hessenberg column h_0..h_{j+1} (hcol) is rotated by the
+// previous rotations, a new rotation zeroes h_{j+1}, and g follows; a column whose |g_{j+1}|
+// reaches tol ||b|| leaves the cycle (its later basis vectors get scale 0)
+__global__ void __launch_bounds__(GB) gmres_givens_kernel(int nrhs, int m, int j, double tol, const double* hcol,
+                                                        const double* bn, double* H, double* cs, double* sn,
+                                                        double* g, double* vs, int* st, int* flag,
+                                                        cudaGraphConditionalHandle h, int use_h) {
+  pdl_enter();
+  int any = 0;
+  for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+    int* sc = st + 4 * c;
+    if (!sc[0]) {
+      vs[(size_t)(j + 1) * nrhs + c] = 0.0;
+      continue;
+    }
+    double* Hc = H + (size_t)c * (m + 1) * m + (size_t)(m + 1) * j;
+    double* csc = cs + (size_t)c * m;
+    double* snc = sn + (size_t)c * m;
+    double* gc = g + (size_t)c * (m + 1);
+    for (int i = 0; i <= j + 1; ++i) Hc[i] = hcol[(size_t)i * nrhs + c];
+    for (int i = 0; i < j; ++i) {
+      const double a = Hc[i], b = Hc[i + 1];
+      Hc[i] = csc[i] * a + snc[i] * b;
+      Hc[i + 1] = -snc[i] * a + csc[i] * b;
+    }
+    const double a = Hc[j], b = Hc[j + 1];
+    const double den = hypot(a, b);
+    csc[j] = den == 0.0 ? 1.0 : a / den;
+    snc[j] = den == 0.0 ? 0.0 : b / den;
+    Hc[j] = den;
+    Hc[j + 1] = 0.0;
+    gc[j + 1] = -snc[j] * gc[j];
+    gc[j] = csc[j] * gc[j];
+    sc[1] = j + 1;
+    if (fabs(gc[j + 1]) <= tol * bn[c]) {
+      sc[0] = 0;
+      vs[(size_t)(j + 1) * nrhs + c] = 0.0;
+    }
+    any |= sc[0];
+  }
+  publish_active(any, flag, h, use_h);
+}
+
+// end of a cycle: y (kmax x nrhs, row-major by step) from the triangular system R y = g
+// over each column's own steps; zero beyond them and for columns that sat the cycle out
+__global__ void __launch_bounds__(GB) gmres_ysolve_kernel(int nrhs, int m, int kmax, const double* H,
+                                                        const double* g, double* y, int* st) {
+  pdl_enter();
+  for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+    int* sc = st + 4 * c;
+    const int k = sc[3] ? 0 : sc[1];
+    const double* Hc = H + (size_t)c * (m + 1) * m;
+    const double* gc = g + (size_t)c * (m + 1);
+    for (int i = kmax - 1; i >= 0; --i) {
+      if (i >= k) {
+        y[(size_t)i * nrhs + c] = 0.0;
+        continue;
+      }
+      double sum = gc[i];
+      for (int q = i + 1; q < k; ++q) sum -= Hc[i + (size_t)(m + 1) * q] * y[(size_t)q * nrhs + c];
+      const double d = Hc[i + (size_t)(m + 1) * i];
+      y[(size_t)i * nrhs + c] = d == 0.0 ? 0.0 : sum / d;
+    }
+    sc[2] += k;
   }
 }
 
@@ -779,9 +953,12 @@ spalu_status spalu_factor_numeric_batch(int n, const spalu_factor_t* f, const in
   return first;
 }
 
+static void step_graph_free(spalu_factor_t f);
+
 spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream) {
   if (!f || nrhs < 1 || nrhs > 16) return SPALU_ERR_ARG;
   if (!f->factored) return SPALU_ERR_STATE;
+  step_graph_free(f);        // a captured step holds the old CTA widths
   cudaStream_t s = (cudaStream_t)stream;
   const int L = f->nd->L, N = f->N;
   // the solve's working vector (zeros: the timing does not depend on the values)
@@ -845,6 +1022,7 @@ spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream)
 spalu_status spalu_tune_factor(spalu_factor_t f, spalu_stream_t stream) {
   if (!f) return SPALU_ERR_ARG;
   if (!f->factored) return SPALU_ERR_STATE;
+  step_graph_free(f);        // a captured step holds the old shared-memory budgets
   cudaStream_t s = (cudaStream_t)stream;
   const int L = f->nd->L;
   PhaseTimer& tm = f->timer;
@@ -979,12 +1157,18 @@ static spalu_status solve_impl(spalu_factor_t f, const double* B, const double* 
   return SPALU_OK;
 }
 
+static void gmres_free(GmresWork& w) {
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vs); cudaFree(w.vec);
+  cudaFree(w.H); cudaFree(w.cs); cudaFree(w.sn); cudaFree(w.g); cudaFree(w.y); cudaFree(w.bn); cudaFree(w.beta);
+  cudaFree(w.st); cudaFree(w.flag); cudaFreeHost(w.hflag);
+  w = GmresWork();
+}
+
 static spalu_status gmres_alloc(spalu_factor_t f, int nrhs) {
   GmresWork& w = f->gw;
   const int m = f->o.gmres_m;
   if (w.nrhs >= nrhs && w.m == m) return SPALU_OK;
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vs); cudaFree(w.vec);
-  w = GmresWork();
+  gmres_free(w);
   size_t N = f->N;
   if (cudaMalloc(&w.V, sizeof(double) * (m + 1) * N * nrhs) != cudaSuccess ||
       cudaMalloc(&w.Z, sizeof(double) * (size_t)m * N * nrhs) != cudaSuccess ||
@@ -993,8 +1177,20 @@ static spalu_status gmres_alloc(spalu_factor_t f, int nrhs) {
       cudaMalloc(&w.part, sizeof(double) * VNB * nrhs) != cudaSuccess ||
       cudaMalloc(&w.hcol, sizeof(double) * (m + 2) * nrhs) != cudaSuccess ||
       cudaMalloc(&w.vs, sizeof(double) * (m + 2) * nrhs) != cudaSuccess ||
-      cudaMalloc(&w.vec, sizeof(double) * 4 * nrhs) != cudaSuccess)
+      cudaMalloc(&w.vec, sizeof(double) * 4 * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.H, sizeof(double) * (size_t)nrhs * (m + 1) * m) != cudaSuccess ||
+      cudaMalloc(&w.cs, sizeof(double) * (size_t)nrhs * m) != cudaSuccess ||
+      cudaMalloc(&w.sn, sizeof(double) * (size_t)nrhs * m) != cudaSuccess ||
+      cudaMalloc(&w.g, sizeof(double) * (size_t)nrhs * (m + 1)) != cudaSuccess ||
+      cudaMalloc(&w.y, sizeof(double) * (size_t)nrhs * m) != cudaSuccess ||
+      cudaMalloc(&w.bn, sizeof(double) * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.beta, sizeof(double) * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.st, sizeof(int) * 4 * nrhs) != cudaSuccess ||
+      cudaMalloc(&w.flag, sizeof(int) * 4) != cudaSuccess ||
+      cudaMallocHost(&w.hflag, sizeof(int) * 4) != cudaSuccess) {
+    gmres_free(w);
     return SPALU_ERR_ALLOC;
+  }
   w.nrhs = nrhs;
   w.m = m;
   return SPALU_OK;
@@ -1071,43 +1267,30 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
   const size_t ldv = (size_t)N;
   auto Vj = [&](int j) { return w.V + (size_t)j * ldv * nrhs; };
   auto Zj = [&](int j) { return w.Z + (size_t)j * ldv * nrhs; };
-  std::vector<double> bn(nrhs), beta(nrhs), hh((size_t)(m + 2) * nrhs);
-  double* dvec = w.vec;   // [0, nrhs): norms; [nrhs, 2 nrhs): scratch
-  vec_mgs(f, nrhs, nullptr, nullptr, 0, nullptr, const_cast<double*>(B), ld, nullptr, 0, nullptr, dvec, 1,
+  vec_mgs(f, nrhs, nullptr, nullptr, 0, nullptr, const_cast<double*>(B), ld, nullptr, 0, nullptr, w.bn, 1,
           nullptr, s);
-  CUDA_TRY(cudaMemcpyAsync(bn.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
-  // the residual goes straight into V_0 (stored unnormalized, scale 1 / beta)
+  bool first = true;
+  // the residual goes straight into V_0 (stored unnormalized, scale 1 / beta); then the cycle
+  // set-up on the device, and one read of "some column still active"
   auto residual = [&]() -> spalu_status {
-    vec_spmv(f, nrhs, X, ld, B, ld, Vj(0), (int)ldv, nullptr, 0, nullptr, dvec, 1, s);
-    CUDA_TRY(cudaMemcpyAsync(beta.data(), dvec, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    vec_spmv(f, nrhs, X, ld, B, ld, Vj(0), (int)ldv, nullptr, 0, nullptr, w.beta, 1, s);
+    note_launch();
+    gmres_begin_kernel<<<1, GB, 0, s>>>(nrhs, m, tol, w.bn, w.beta, w.vs, w.g, w.st, first ? 1 : 0, w.flag,
+                                        cudaGraphConditionalHandle{}, 0);
+    first = false;
+    CUDA_TRY(cudaMemcpyAsync(w.hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SPALU_OK;
   };
   if ((st = residual()) != SPALU_OK) return st;
   int it = 0;
-  auto done = [&](int c) { return bn[c] == 0.0 || beta[c] <= tol * bn[c]; };
-  std::vector<std::vector<double>> H(nrhs, std::vector<double>((size_t)(m + 1) * m, 0.0));
-  std::vector<std::vector<double>> cs(nrhs, std::vector<double>(m)), sn(nrhs, std::vector<double>(m)),
-      g(nrhs, std::vector<double>(m + 1));
-  std::vector<double> ycoef((size_t)m * nrhs);
-  while (it < maxit) {
-    bool all = true;
-    for (int c = 0; c < nrhs; ++c) all = all && done(c);
-    if (all) break;
-    // V_0 = r / beta: r is in V_0, its scale 1 / beta (finished columns: scale 0)
-    std::vector<double> bsc(nrhs), isc(nrhs);
-    for (int c = 0; c < nrhs; ++c) {
-      bsc[c] = done(c) ? 0.0 : beta[c];
-      isc[c] = bsc[c] != 0.0 ? 1.0 / bsc[c] : 0.0;
-    }
-    CUDA_TRY(cudaMemcpyAsync(w.vs, isc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-    for (int c = 0; c < nrhs; ++c) {
-      std::fill(H[c].begin(), H[c].end(), 0.0);
-      std::fill(g[c].begin(), g[c].end(), 0.0);
-      g[c][0] = bsc[c];
-    }
-    int jl = -1;
-    for (int j = 0; j < m; ++j) {
+  int cycles = 0, first_cycle_steps = 0;
+  while (it < maxit && w.hflag[0]) {
+    // the first check of the cycle comes after one step fewer than the last call needed (it
+    // cannot have converged before); later checks after every step
+    int batch = cycles == 0 ? std::max(1, f->gmres_hint - 1) : 1;
+    int jl = -1, since = 0;
+    for (int j = 0; j < m && it < maxit; ++j) {
       // Z_j = M^{-1} V_j (kept), V_{j+1} = A Z_j
       const double* sj = w.vs + (size_t)j * nrhs;
       if ((st = solve_impl(f, Vj(j), sj, Zj(j), nrhs, (int)ldv, stream)) != SPALU_OK) return st;
@@ -1119,47 +1302,29 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
         vec_mgs(f, nrhs, w.hcol + (size_t)(i - 1) * nrhs, Vj(i - 1), (int)ldv, w.vs + (size_t)(i - 1) * nrhs,
                 Vj(j + 1), (int)ldv, i <= j ? Vj(i) : nullptr, (int)ldv, w.vs + (size_t)i * nrhs,
                 w.hcol + (size_t)i * nrhs, i > j, i > j ? w.vs + (size_t)(j + 1) * nrhs : nullptr, s);
-      CUDA_TRY(cudaMemcpyAsync(hh.data(), w.hcol, sizeof(double) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
-      CUDA_TRY(cudaStreamSynchronize(s));
+      note_launch();
+      launch_pdl(gmres_givens_kernel, dim3(1), dim3(GB), 0, s, nrhs, m, j, tol, (const double*)w.hcol,
+                 (const double*)w.bn, w.H, w.cs, w.sn, w.g, w.vs, w.st, w.flag, cudaGraphConditionalHandle{}, 0);
       ++it;
       jl = j;
-      bool allc = true;
-      for (int c = 0; c < nrhs; ++c) {
-        double* Hc = H[c].data();
-        for (int i = 0; i <= j; ++i) Hc[i + (m + 1) * j] = hh[(size_t)i * nrhs + c];
-        Hc[(j + 1) + (m + 1) * j] = hh[(size_t)(j + 1) * nrhs + c];
-        for (int i = 0; i < j; ++i) {
-          double a = Hc[i + (m + 1) * j], b = Hc[i + 1 + (m + 1) * j];
-          Hc[i + (m + 1) * j] = cs[c][i] * a + sn[c][i] * b;
-          Hc[i + 1 + (m + 1) * j] = -sn[c][i] * a + cs[c][i] * b;
-        }
-        double a = Hc[j + (m + 1) * j], b = Hc[j + 1 + (m + 1) * j];
-        double den = std::hypot(a, b);
-        cs[c][j] = den == 0.0 ? 1.0 : a / den;
-        sn[c][j] = den == 0.0 ? 0.0 : b / den;
-        Hc[j + (m + 1) * j] = den;
-        Hc[j + 1 + (m + 1) * j] = 0.0;
-        g[c][j + 1] = -sn[c][j] * g[c][j];
-        g[c][j] = cs[c][j] * g[c][j];
-        if (!(done(c) || std::fabs(g[c][j + 1]) <= tol * bn[c])) allc = false;
+      if (++since >= batch || it >= maxit || j == m - 1) {
+        CUDA_TRY(cudaMemcpyAsync(w.hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        since = 0;
+        batch = 1;
+        if (!w.hflag[0]) break;
       }
-      if (allc || it >= maxit) break;
     }
-    // y from the triangular system, U = V y, X += M^{-1} U
+    if (cycles == 0) first_cycle_steps = jl + 1;
+    ++cycles;
+    // y from the triangular system, X += M^{-1} V y = sum_i y_i Z_i
     const int kdim = jl + 1;
-    for (int c = 0; c < nrhs; ++c) {
-      double* Hc = H[c].data();
-      for (int i = kdim - 1; i >= 0; --i) {
-        double sum = g[c][i];
-        for (int q = i + 1; q < kdim; ++q) sum -= Hc[i + (m + 1) * q] * ycoef[(size_t)q * nrhs + c];
-        ycoef[(size_t)i * nrhs + c] = (done(c) || Hc[i + (m + 1) * i] == 0.0) ? 0.0 : sum / Hc[i + (m + 1) * i];
-      }
-    }
-    // X += M^{-1} V y = sum_i y_i Z_i
-    CUDA_TRY(cudaMemcpyAsync(w.hcol, ycoef.data(), sizeof(double) * kdim * nrhs, cudaMemcpyHostToDevice, s));
     note_launch();
-    launch_pdl(combine_kernel, vec_grid(N, nrhs), dim3(VB), 0, s, N, nrhs, kdim, (const double*)w.hcol,
-               (const double*)w.Z, ldv, X, ld);
+    launch_pdl(gmres_ysolve_kernel, dim3(1), dim3(GB), 0, s, nrhs, m, kdim, (const double*)w.H,
+               (const double*)w.g, w.y, w.st);
+    note_launch();
+    launch_pdl(combine_kernel, vec_grid(N, nrhs), dim3(VB), 0, s, N, nrhs, kdim, (const double*)w.y,
+               (const double*)w.Z, ldv, X, ld, (const int*)w.st);
     if (dl) {        // X changes only here: its copy runs while the residual is checked
       CUDA_TRY(cudaEventRecord(dl->ev, s));
       CUDA_TRY(cudaStreamWaitEvent(dl->s, dl->ev, 0));
@@ -1169,14 +1334,329 @@ static spalu_status refine_impl(spalu_factor_t f, const double* B, double* X, in
     }
     if ((st = residual()) != SPALU_OK) return st;
   }
+  if (cycles == 1) f->gmres_hint = first_cycle_steps;
+  std::vector<double> bn(nrhs), beta(nrhs);
+  std::vector<int> stc(4 * (size_t)nrhs);
+  CUDA_TRY(cudaMemcpyAsync(bn.data(), w.bn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(beta.data(), w.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(stc.data(), w.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
   bool conv = true;
+  int its = 0;
   for (int c = 0; c < nrhs; ++c) {
     if (relres) relres[c] = bn[c] == 0.0 ? 0.0 : beta[c] / bn[c];
-    conv = conv && done(c);
+    conv = conv && stc[4 * c + 3] == 1;
+    its = std::max(its, stc[4 * c + 2]);
   }
-  if (iters) *iters = it;
+  if (iters) *iters = its;
   CUDA_TRY(cudaGetLastError());
   return conv ? SPALU_OK : SPALU_ERR_NOCONV;
+}
+
+// ------------------------------------------------------------ one graph over the whole step
+// Factorization, direct solve and GMRES refinement captured once as a CUDA graph and replayed
+// (scheduling; not in the paper).  The solve kernels' shared-memory capacities and the leaf
+// sweep variant are fixed by the factorization the graph was captured after, so a guard kernel
+// after the factorization checks the new factor's level maxima and leaf bandwidth against
+// those: the solve and refinement run inside a conditional node only when they still fit (else
+// the host redoes them outside the graph).  The refinement inside the graph is one GMRES cycle
+// of at most K Arnoldi steps, each in a conditional node that the previous step's Givens
+// kernel switches off once every column has converged.
+__global__ void step_guard_kernel(const int* err, const int* kumax, int kumax_ref, const int* lstat,
+                                  const int* ref, int L, int* ok_out, cudaGraphConditionalHandle h,
+                                  cudaGraphConditionalHandle h2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int ok = (*err == 0 && *kumax <= kumax_ref) ? 1 : 0;
+  for (int l = 1; l <= L; ++l)
+    for (int q = 0; q < 3; ++q)
+      if (lstat[LS_N * l + q] > ref[3 * l + q]) ok = 0;      // LS_EMAX, LS_KPMAX, LS_DPMAX
+  *ok_out = ok;
+  cudaGraphSetConditional(h, ok ? 1u : 0u);
+  cudaGraphSetConditional(h2, ok ? 1u : 0u);
+}
+
+static void step_graph_free(spalu_factor_t f) {
+  auto& g = f->sg;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  f->timer.drop_graph();
+  cudaFree(g.d_ref);
+  cudaFree(g.d_ok);
+  cudaFreeHost(g.h_out);
+  g = spalu_factor_s::StepGraph();
+}
+
+// add an IF node on handle h after what stream s (capturing) has so far; returns its body
+static cudaError_t add_if_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) { report_cuda("cudaStreamGetCaptureInfo", e, __LINE__); return e; }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp)) != cudaSuccess) {
+    report_cuda("cudaGraphAddNode", e, __LINE__);
+    return e;
+  }
+  *body = cp.conditional.phGraph_out[0];
+  e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) report_cuda("cudaStreamUpdateCaptureDependencies", e, __LINE__);
+  return e;
+}
+
+// the cycle's Arnoldi step j (as in refine_impl), enqueued on s
+static spalu_status arnoldi_step(spalu_factor_t f, int nrhs, int j, cudaGraphConditionalHandle h, int use_h,
+                                 cudaStream_t s) {
+  GmresWork& w = f->gw;
+  const int m = f->o.gmres_m;
+  const size_t ldv = (size_t)f->N;
+  auto Vj = [&](int i) { return w.V + (size_t)i * ldv * nrhs; };
+  auto Zj = [&](int i) { return w.Z + (size_t)i * ldv * nrhs; };
+  spalu_status st = solve_impl(f, Vj(j), w.vs + (size_t)j * nrhs, Zj(j), nrhs, (int)ldv, (spalu_stream_t)s);
+  if (st != SPALU_OK) return st;
+  vec_spmv(f, nrhs, Zj(j), (int)ldv, nullptr, 0, Vj(j + 1), (int)ldv, Vj(0), (int)ldv, w.vs, w.hcol, 0, s);
+  for (int i = 1; i <= j + 1; ++i)
+    vec_mgs(f, nrhs, w.hcol + (size_t)(i - 1) * nrhs, Vj(i - 1), (int)ldv, w.vs + (size_t)(i - 1) * nrhs,
+            Vj(j + 1), (int)ldv, i <= j ? Vj(i) : nullptr, (int)ldv, w.vs + (size_t)i * nrhs,
+            w.hcol + (size_t)i * nrhs, i > j, i > j ? w.vs + (size_t)(j + 1) * nrhs : nullptr, s);
+  note_launch();
+  launch_pdl(gmres_givens_kernel, dim3(1), dim3(GB), 0, s, nrhs, m, j, f->o.gmres_tol, (const double*)w.hcol,
+             (const double*)w.bn, w.H, w.cs, w.sn, w.g, w.vs, w.st, w.flag, h, use_h);
+  return SPALU_OK;
+}
+
+static spalu_status capture_step(spalu_factor_t f, const int* rowptr, const int* colind, const double* val,
+                                 int nnz, const double* B, double* X, int nrhs, int ld, cudaStream_t s) {
+  // captured on a stream of the handle's own (the caller's may be the legacy default stream,
+  // which cannot be captured); the graph is launched on the caller's stream
+  auto& G = f->sg;
+  const int L = f->nd->L;
+  const int N = f->N, m = f->o.gmres_m;
+  const int K = std::min(m, std::max(4, f->gmres_hint + 2));
+  GmresWork& w = f->gw;
+  const size_t ldv = (size_t)N;
+  // guard references: the maxima the current solve capacities were set from
+  std::vector<int> ref(3 * (L + 1), 0);
+  for (int l = 1; l <= L; ++l)
+    for (int q = 0; q < 3; ++q) ref[3 * l + q] = f->lstat[LS_N * l + q];
+  CUDA_TRY(cudaMemcpy(G.d_ref, ref.data(), sizeof(int) * ref.size(), cudaMemcpyHostToDevice));
+  cudaStream_t s2 = nullptr, s3 = nullptr;
+  CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+  if (cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStreamDestroy(s2);
+    return SPALU_ERR_CUDA;
+  }
+  cudaStream_t s1 = nullptr;
+  if (cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStreamDestroy(s2);
+    cudaStreamDestroy(s3);
+    return SPALU_ERR_CUDA;
+  }
+  (void)s;
+  s = s1;
+  spalu_status st = SPALU_OK;
+  cudaGraph_t graph = nullptr;
+  auto fail = [&](spalu_status e) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(s3, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    junk = nullptr;
+    cudaStreamEndCapture(s2, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    junk = nullptr;
+    cudaStreamEndCapture(s, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    cudaGetLastError();
+    return e;
+  };
+#define CAP_TRY(x)                                   \
+  do {                                               \
+    cudaError_t _e = (x);                            \
+    if (_e != cudaSuccess) { report_cuda(#x, _e, __LINE__); st = fail(SPALU_ERR_CUDA); goto done; } \
+  } while (0)
+  G.n_step.assign(K, 0);
+  f->timer.drop_graph();
+  f->timer.cap_top = s;
+  {
+    unsigned long long c0 = g_launches.load();
+    CAP_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    cudaGraph_t top = nullptr;
+    {
+      cudaStreamCaptureStatus cs;
+      CAP_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &top, nullptr, nullptr, nullptr));
+    }
+    // every conditional node sits in the top-level graph; the handles are reset to 0 at each
+    // launch, so when the guard fails nothing after it runs
+    // one handle per conditional node: h_act[j] (set by the set-up or by step j-1) opens step j
+    cudaGraphConditionalHandle h_ok, h_ok2;
+    std::vector<cudaGraphConditionalHandle> h_act(K + 1);
+    CAP_TRY(cudaGraphConditionalHandleCreate(&h_ok, top, 0, cudaGraphCondAssignDefault));
+    CAP_TRY(cudaGraphConditionalHandleCreate(&h_ok2, top, 0, cudaGraphCondAssignDefault));
+    for (int j = 0; j < K; ++j) CAP_TRY(cudaGraphConditionalHandleCreate(&h_act[j], top, 0, cudaGraphCondAssignDefault));
+    CAP_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CAP_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CAP_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if ((st = factor_enqueue(f, s)) != SPALU_OK) { st = fail(st); goto done; }
+    note_launch();
+    step_guard_kernel<<<1, 32, 0, s>>>(f->d_err, f->leaf.kumax, f->kumax, f->d_lstat, G.d_ref, L, G.d_ok, h_ok,
+                                       h_ok2);
+    CAP_TRY(cudaGetLastError());
+    G.n_pre = (long long)(g_launches.load() - c0);
+    c0 = g_launches.load();
+    // solve, then the cycle's set-up
+    cudaGraph_t body;
+    CAP_TRY(add_if_node(s, h_ok, &body));
+    CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    if ((st = solve_impl(f, B, nullptr, X, nrhs, ld, (spalu_stream_t)s2)) != SPALU_OK) { st = fail(st); goto done; }
+    vec_mgs(f, nrhs, nullptr, nullptr, 0, nullptr, const_cast<double*>(B), ld, nullptr, 0, nullptr, w.bn, 1,
+            nullptr, s2);
+    vec_spmv(f, nrhs, X, ld, B, ld, w.V, (int)ldv, nullptr, 0, nullptr, w.beta, 1, s2);
+    note_launch();
+    gmres_begin_kernel<<<1, GB, 0, s2>>>(nrhs, m, f->o.gmres_tol, w.bn, w.beta, w.vs, w.g, w.st, 1, w.flag, h_act[0], 1);
+    {
+      cudaGraph_t out2 = nullptr;
+      CAP_TRY(cudaStreamEndCapture(s2, &out2));
+    }
+    // the Arnoldi steps, each while some column is active
+    for (int j = 0; j < K; ++j) {
+      CAP_TRY(add_if_node(s, h_act[j], &body));
+      CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      const unsigned long long cj = g_launches.load();
+      if ((st = arnoldi_step(f, nrhs, j, h_act[j + 1], j + 1 < K ? 1 : 0, s2)) != SPALU_OK) { st = fail(st); goto done; }
+      G.n_step[j] = (long long)(g_launches.load() - cj);
+      c0 += G.n_step[j];
+      cudaGraph_t out2 = nullptr;
+      CAP_TRY(cudaStreamEndCapture(s2, &out2));
+    }
+    // the update of X and the residual of the result
+    CAP_TRY(add_if_node(s, h_ok2, &body));
+    CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    note_launch();
+    launch_pdl(gmres_ysolve_kernel, dim3(1), dim3(GB), 0, s2, nrhs, m, K, (const double*)w.H, (const double*)w.g,
+               w.y, w.st);
+    note_launch();
+    launch_pdl(combine_kernel, vec_grid(N, nrhs), dim3(VB), 0, s2, N, nrhs, K, (const double*)w.y,
+               (const double*)w.Z, ldv, X, ld, (const int*)w.st);
+    vec_spmv(f, nrhs, X, ld, B, ld, w.V, (int)ldv, nullptr, 0, nullptr, w.beta, 1, s2);
+    note_launch();
+    gmres_begin_kernel<<<1, GB, 0, s2>>>(nrhs, m, f->o.gmres_tol, w.bn, w.beta, w.vs, w.g, w.st, 0, w.flag,
+                                         cudaGraphConditionalHandle{}, 0);
+    {
+      cudaGraph_t out2 = nullptr;
+      CAP_TRY(cudaStreamEndCapture(s2, &out2));
+    }
+    G.n_ok = (long long)(g_launches.load() - c0);
+    CAP_TRY(cudaMemcpyAsync(G.h_out, G.d_ok, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CAP_TRY(cudaMemcpyAsync(G.h_out + 1, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CAP_TRY(cudaStreamEndCapture(s, &graph));
+    if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
+      G.exec = nullptr;
+      st = SPALU_ERR_CUDA;
+    }
+  }
+done:
+#undef CAP_TRY
+  f->timer.cap_top = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(s1);
+  cudaStreamDestroy(s2);
+  cudaStreamDestroy(s3);
+  if (st != SPALU_OK) return st;
+  G.key[0] = rowptr; G.key[1] = colind; G.key[2] = val; G.key[3] = B; G.key[4] = X; G.key[5] = w.V;
+  G.nnz = nnz; G.nrhs = nrhs; G.ld = ld; G.K = K; G.timed = f->timer.on;
+  return SPALU_OK;
+}
+
+spalu_status spalu_factor_solve_graph(spalu_factor_t f, const int* rowptr, const int* colind, const double* val,
+                                      int nnz, const double* B, double* X, int nrhs, int ld, int* iters,
+                                      double* relres, spalu_stream_t stream) {
+  if (!f || !rowptr || !colind || !val || nnz < 0 || nnz > f->nnz_cap || !B || !X || nrhs < 1 || ld < f->N ||
+      X == B)
+    return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto& G = f->sg;
+  const bool fits = G.exec && G.key[0] == rowptr && G.key[1] == colind && G.key[2] == val && G.key[3] == B &&
+                    G.key[4] == X && G.nnz == nnz && G.nrhs == nrhs && G.ld == ld && f->gw.nrhs >= nrhs &&
+                    G.key[5] == f->gw.V && f->factored && G.timed == f->timer.on;
+  if (!fits) {
+    // the plain path once (it sets the capacities, the allocations and the step count), then
+    // capture the step for the next calls
+    if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
+    f->timer.drop_graph();
+    spalu_status st = spalu_factor_numeric(f, rowptr, colind, val, nnz, stream);
+    if (st != SPALU_OK) return st;
+    if ((st = spalu_solve(f, B, X, nrhs, ld, stream)) != SPALU_OK) return st;
+    st = spalu_refine(f, B, X, nrhs, ld, iters, relres, stream);
+    if (st != SPALU_OK && st != SPALU_ERR_NOCONV) return st;
+    if (!G.d_ref) {
+      const int L = f->nd->L;
+      if (cudaMalloc(&G.d_ref, sizeof(int) * 3 * (L + 1)) != cudaSuccess ||
+          cudaMalloc(&G.d_ok, sizeof(int)) != cudaSuccess || cudaMallocHost(&G.h_out, sizeof(int) * 2) != cudaSuccess) {
+        step_graph_free(f);
+        return SPALU_ERR_ALLOC;
+      }
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const spalu_status cst = capture_step(f, rowptr, colind, val, nnz, B, X, nrhs, ld, s);
+    if (cst != SPALU_OK) step_graph_free(f);
+    return cst != SPALU_OK ? cst : st;
+  }
+  f->nnz = nnz;
+  int t_step = f->timer.begin("step_graph", s);
+  CUDA_TRY(cudaGraphLaunch(G.exec, s));
+  f->timer.end(t_step, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (G.timed) f->timer.collect_graph();
+  // the factorization's readback (error word, leaf bandwidth, level counters) came with the graph
+  note_launches(G.n_pre);
+  spalu_status st = factor_finish(f, s);
+  if (st != SPALU_OK) return st;
+  if (G.h_out[0]) {          // kernels that ran inside the conditional nodes
+    int steps = 0;
+    std::vector<int> stc(4 * (size_t)nrhs);
+    CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < nrhs; ++c) steps = std::max(steps, stc[4 * c + 2]);
+    long long n = G.n_ok;
+    for (int j = 0; j < steps && j < G.K; ++j) n += G.n_step[j];
+    note_launches(n);
+  }
+  if (!G.h_out[0]) {
+    // the new factor outgrew the captured capacities: solve and refine outside the graph, and
+    // capture again next time
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    f->timer.drop_graph();
+    if ((st = spalu_solve(f, B, X, nrhs, ld, stream)) != SPALU_OK) return st;
+    return spalu_refine(f, B, X, nrhs, ld, iters, relres, stream);
+  }
+  if (G.h_out[1]) {
+    // not converged within the captured steps: continue with more cycles outside the graph
+    int it2 = 0;
+    std::vector<int> stc(4 * (size_t)nrhs);
+    CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
+    int its = 0;
+    for (int c = 0; c < nrhs; ++c) its = std::max(its, stc[4 * c + 2]);
+    st = spalu_refine(f, B, X, nrhs, ld, &it2, relres, stream);
+    if (iters) *iters = its + it2;
+    return st;
+  }
+  std::vector<double> bn(nrhs), beta(nrhs);
+  std::vector<int> stc(4 * (size_t)nrhs);
+  CUDA_TRY(cudaMemcpy(bn.data(), f->gw.bn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(beta.data(), f->gw.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
+  int its = 0;
+  for (int c = 0; c < nrhs; ++c) {
+    if (relres) relres[c] = bn[c] == 0.0 ? 0.0 : beta[c] / bn[c];
+    its = std::max(its, stc[4 * c + 2]);
+  }
+  if (iters) *iters = its;
+  return SPALU_OK;
 }
 
 spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,
@@ -1522,6 +2002,7 @@ spalu_status spalu_predictor_infer(spalu_predictor_t p, const float* X, int n, f
 spalu_status spalu_factor_set_predictor(spalu_factor_t f, spalu_predictor_t p, int mode, double margin) {
   if (!f || mode < PRED_OFF || mode > PRED_PREDICT || !(margin >= 0.0)) return SPALU_ERR_ARG;
   if (mode == PRED_PREDICT && !p) return SPALU_ERR_ARG;
+  step_graph_free(f);        // a captured step holds the old predictor settings
   f->pred = p;
   f->pred_mode = mode;
   for (int l = 1; l <= f->nd->L; ++l) {
@@ -1553,8 +2034,8 @@ void spalu_factor_destroy(spalu_factor_t f) {
   cudaFree(f->arena);
   cudaFree(f->xf);
   cudaFreeHost(f->hpin);
-  GmresWork& w = f->gw;
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.cnt); cudaFree(w.part); cudaFree(w.hcol); cudaFree(w.vs); cudaFree(w.vec);
+  gmres_free(f->gw);
+  step_graph_free(f);
   if (f->up) {
     cudaStreamSynchronize(f->up);
     cudaStreamDestroy(f->up);

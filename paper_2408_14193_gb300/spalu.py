@@ -87,6 +87,7 @@ SIGNATURES = [
     ("spalu_refine", _I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     ("spalu_solve_host", _I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_factor_solve_host", _I, [_P, _P, _P, _P, _I, _P, _P, _I, _I, _I, _P, _P, _P]),
+    ("spalu_factor_solve_graph", _I, [_P, _P, _P, _P, _I, _P, _P, _I, _I, _P, _P, _P]),
     ("spalu_stats", _I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     ("spalu_factor_export_level", _I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     ("spalu_residual_noalloc", _I, [_P, _P, _P, _I, _I, _P, _P]),
@@ -253,6 +254,22 @@ class Factor:
         _check(self.lib.spalu_solve(self.handle, _dev_ptr(B, torch.float64), _dev_ptr(X, torch.float64),
                                     nrhs, self.N, _stream_ptr(stream)), "spalu_solve")
         return X
+
+    def factor_solve_graph(self, rowptr, colind, val, B, X, stream=None, check=True):
+        """spalu_factor_solve_graph: factor (device CSR), solve B into X and refine X, as one
+        CUDA graph after the first call; returns (iterations, relative residuals)."""
+        import torch
+        self._csr_shape(rowptr, colind, val)
+        nrhs = self._nrhs(B, X)
+        it = ctypes.c_int(0)
+        rel = np.zeros(nrhs)
+        st = self.lib.spalu_factor_solve_graph(
+            self.handle, _dev_ptr(rowptr, torch.int32), _dev_ptr(colind, torch.int32), _dev_ptr(val, torch.float64),
+            int(val.numel()), _dev_ptr(B, torch.float64), _dev_ptr(X, torch.float64), nrhs, self.N,
+            ctypes.byref(it), rel.ctypes.data, _stream_ptr(stream))
+        if check:
+            _check(st, "spalu_factor_solve_graph")
+        return it.value, rel
 
     def tune_solve(self, nrhs: int = 16, stream=None):
         """Time the level-solve kernels with 2- and 8-warp CTAs per level and keep the fastest."""

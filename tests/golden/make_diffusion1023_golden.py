@@ -3,7 +3,7 @@
 The problem is the full-size variable-coefficient workload (a = exp(GRF), length 0.05,
 variance 1) with seed 1 and one standard-normal right-hand side; the oracle factors it at
 eps_ID = 1e-8 (FP64, adaptive ID) and solves.  Stored: the solution's 2-norm, max-norm and
-sum, its values at a fixed sample of unknowns (one interior node of every leaf box, every
+sum, the input's digest (sum and 2-norm of the matrix values, norm of B), its values at a fixed sample of unknowns (one interior node of every leaf box, every
 node of the level-1 separator, 1024 further separator nodes), and per level the oracle's
 largest segment, largest rank and work counts.  The vector itself (8 MB) is not stored.
 
@@ -54,6 +54,7 @@ def main():
         "n": N_SIDE, "seed": SEED, "eps_id": EPS, "nrhs": 1,
         "norm2": float(np.linalg.norm(x)), "norminf": float(np.max(np.abs(x))), "sum": float(x.sum()),
         "b_norm2": float(np.linalg.norm(P.B[:, 0])),
+        "a_sum": float(P.A.data.sum()), "a_norm2": float(np.linalg.norm(P.A.data)),
         "index": idx.tolist(), "value": [float(v) for v in x[idx]],
         "levels": {str(l): {k: int(v[k]) for k in ("e_max", "k_max", "flops_sparsify", "flops_merge", "passes")}
                    for l, v in F.stats["levels"].items()},

@@ -49,7 +49,7 @@ def test_batch_matches_one_at_a_time(precision):
         g.factor(*probs[i][1])
         Y = g.solve(probs[i][2])
         torch.cuda.synchronize()
-        x, y = Xs[i].cpu().numpy(), Y.cpu().numpy()
+        x, y = Xs[i].cpu().numpy().T, Y.cpu().numpy().T       # (N, nrhs): one column per RHS
         # the solve adds separator contributions with atomics, in a run-dependent order: FP64
         # rounding for the plain form; FP32 rounding of an FP32 factor for the mixed one (its
         # direct solve is only accurate to ~1e-4 at this eps, refinement restores 1e-10)
