@@ -590,6 +590,7 @@ def run_ours(args):
                                         head["iters"], hbm, alu),
         "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(st["timing_ms"].items())},
         "factor_stats": {"q_tilde": st["q_tilde"], "levels": st["levels"]},
+        "step_graph": st.get("step_graph"),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -78,7 +78,14 @@ struct PhaseTimer {
     if (cs != cudaStreamCaptureStatusNone) {
       if (s != cap_top) return -1;
       Rec r{name, take(), take()};
-      if (cudaEventRecord(r.a, s) != cudaSuccess) return -1;
+      // external: an event-record node of the graph (a plain record in a capture only orders
+      // the captured work)
+      if (cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal) != cudaSuccess) {
+        cudaGetLastError();
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+        return -1;
+      }
       grecs.push_back(r);
       return -2 - ((int)grecs.size() - 1);
     }
@@ -89,7 +96,7 @@ struct PhaseTimer {
   }
   void end(int i, cudaStream_t s) {
     if (i >= 0) cudaEventRecord(recs[i].b, s);
-    else if (i <= -2) cudaEventRecord(grecs[-2 - i].b, s);
+    else if (i <= -2) cudaEventRecordWithFlags(grecs[-2 - i].b, s, cudaEventRecordExternal);
   }
   // add the intervals of the last replay of the step graph to the sums (events kept)
   void collect_graph() {
@@ -97,6 +104,7 @@ struct PhaseTimer {
       float t = 0.f;
       cudaEventSynchronize(r.b);
       if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) { ms[r.name] += t; count[r.name] += 1; }
+      else cudaGetLastError();
     }
   }
   void drop_graph() {
@@ -161,6 +169,7 @@ struct spalu_factor_s {
     int* d_ok = nullptr;     // guard result
     int* h_out = nullptr;    // page-locked: guard result, some column active
     long long n_pre = 0, n_ok = 0;   // kernels of the graph: before the guard's node, in its body
+    long long captures = 0, replays = 0, refits = 0, continued = 0;   // statistics (spalu_stats)
     std::vector<long long> n_step;   // ... and in each Arnoldi step's node
   } sg;
   int* d_lstat = nullptr;    // [LS_N * (L + 1)] per-level counters (factor kernels)
@@ -1382,7 +1391,9 @@ static void step_graph_free(spalu_factor_t f) {
   cudaFree(g.d_ref);
   cudaFree(g.d_ok);
   cudaFreeHost(g.h_out);
+  const long long c = g.captures, r = g.replays, rf = g.refits, ct = g.continued;
   g = spalu_factor_s::StepGraph();
+  g.captures = c; g.replays = r; g.refits = rf; g.continued = ct;
 }
 
 // add an IF node on handle h after what stream s (capturing) has so far; returns its body
@@ -1440,10 +1451,27 @@ static spalu_status capture_step(spalu_factor_t f, const int* rowptr, const int*
   const int K = std::min(m, std::max(4, f->gmres_hint + 2));
   GmresWork& w = f->gw;
   const size_t ldv = (size_t)N;
-  // guard references: the maxima the current solve capacities were set from
+  // guard references: the level maxima with some headroom (skeleton sizes move by a few
+  // unknowns between factorizations of the same matrix: FP32 rounding, learned sketch sizes),
+  // and the solve capacities of the captured kernels set from them
   std::vector<int> ref(3 * (L + 1), 0);
-  for (int l = 1; l <= L; ++l)
-    for (int q = 0; q < 3; ++q) ref[3 * l + q] = f->lstat[LS_N * l + q];
+  for (int l = 1; l <= L; ++l) {
+    int lm[LS_N] = {};
+    for (int q = 0; q < 3; ++q) {
+      const int v = f->lstat[LS_N * l + q];
+      lm[q] = v + std::max(4, v / 4);
+    }
+    SolveCaps c;
+    if (level_solve_caps(f->lev[l], lm, &c)) {
+      c.seg_nt = f->caps[l].seg_nt;
+      c.sep_nt = f->caps[l].sep_nt;
+      f->caps[l] = c;
+    } else {
+      for (int q = 0; q < 3; ++q) lm[q] = f->lstat[LS_N * l + q];
+    }
+    for (int q = 0; q < 3; ++q) ref[3 * l + q] = lm[q];
+  }
+  f->kumax = f->kumax <= 15 ? 15 : 30;       // the two leaf-sweep variants
   CUDA_TRY(cudaMemcpy(G.d_ref, ref.data(), sizeof(int) * ref.size(), cudaMemcpyHostToDevice));
   cudaStream_t s2 = nullptr, s3 = nullptr;
   CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
@@ -1569,6 +1597,7 @@ done:
   if (st != SPALU_OK) return st;
   G.key[0] = rowptr; G.key[1] = colind; G.key[2] = val; G.key[3] = B; G.key[4] = X; G.key[5] = w.V;
   G.nnz = nnz; G.nrhs = nrhs; G.ld = ld; G.K = K; G.timed = f->timer.on;
+  ++G.captures;
   return SPALU_OK;
 }
 
@@ -1612,6 +1641,7 @@ spalu_status spalu_factor_solve_graph(spalu_factor_t f, const int* rowptr, const
   f->timer.end(t_step, s);
   CUDA_TRY(cudaStreamSynchronize(s));
   if (G.timed) f->timer.collect_graph();
+  ++G.replays;
   // the factorization's readback (error word, leaf bandwidth, level counters) came with the graph
   note_launches(G.n_pre);
   spalu_status st = factor_finish(f, s);
@@ -1631,11 +1661,13 @@ spalu_status spalu_factor_solve_graph(spalu_factor_t f, const int* rowptr, const
     cudaGraphExecDestroy(G.exec);
     G.exec = nullptr;
     f->timer.drop_graph();
+    ++G.refits;
     if ((st = spalu_solve(f, B, X, nrhs, ld, stream)) != SPALU_OK) return st;
     return spalu_refine(f, B, X, nrhs, ld, iters, relres, stream);
   }
   if (G.h_out[1]) {
     // not converged within the captured steps: continue with more cycles outside the graph
+    ++G.continued;
     int it2 = 0;
     std::vector<int> stc(4 * (size_t)nrhs);
     CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
@@ -1779,8 +1811,10 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
                   ls[LS_FALLBACK], ls[LS_PREDICTED], fl[4 * l], fl[4 * l + 1], fl[4 * l + 2], fl[4 * l + 3]);
     out += buf;
   }
-  char buf[64];
-  std::snprintf(buf, sizeof buf, "], \"q_tilde\": %.6f", qt);
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "], \"q_tilde\": %.6f, \"step_graph\": {\"captures\": %lld, \"replays\": %lld, "
+                "\"refits\": %lld, \"continued\": %lld}", qt, f->sg.captures, f->sg.replays, f->sg.refits,
+                f->sg.continued);
   out += buf;
   f->timer.collect();
   out += ", \"timing_ms\": {";

@@ -540,12 +540,19 @@ __device__ void probe_sketch(const LevelDev& d, const SegCtx& S, const NbrTab& t
         }
       }
     }
+    // the warps add their partial sums in warp order (a fixed summation order: the probe, and
+    // through it the predicted sketch size, is the same in every factorization)
+    for (int w = 0; w < nw; ++w) {
+      if (warp == w) {
 #pragma unroll
-    for (int qc = 0; qc < 2; ++qc) {
-      const int c = c0 + 32 * qc + lane;
-      if (c < e)
+        for (int qc = 0; qc < 2; ++qc) {
+          const int c = c0 + 32 * qc + lane;
+          if (c < e)
 #pragma unroll
-        for (int r = 0; r < PRED_PROBE; ++r) atomicAdd(&Y8[r + PRED_PROBE * c], acc[qc][r]);
+            for (int r = 0; r < PRED_PROBE; ++r) Y8[r + PRED_PROBE * c] += acc[qc][r];
+        }
+      }
+      __syncthreads();
     }
   }
 }

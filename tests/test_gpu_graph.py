@@ -57,6 +57,8 @@ def test_graph_step_matches_plain_calls(precision, eps):
         assert np.allclose(rel, res, rtol=1e-3, atol=1e-13)
         assert abs(it - itp) <= 1, (call, it, itp)
         assert launched > 50
+    sg = g.stats()["step_graph"]
+    assert sg["captures"] == 1 and sg["replays"] == 2 and sg["refits"] == 0, sg
     # the refined solutions agree to the refinement's accuracy
     d = (X - Xp).cpu().numpy()
     assert np.linalg.norm(d) <= 1e-8 * np.linalg.norm(Xp.cpu().numpy())
