@@ -65,7 +65,8 @@ typedef struct {
                                  0: B = [A_{n,i}; A_{i,n}^T] (Sec. 4.5, Eq. (ID [A_ni; A_in])) */
   int p_oversample;           /* p of h = k + p (Sec. 4.2.3), default 5 */
   int near_radius;            /* Chebyshev radius of the near field, default 2 */
-  int h0;                     /* first sketch size, default 16 */
+  int h0;                     /* first sketch size, default 16 (segments with e + p <= 2 h0 are
+                                 sketched once with h = 2 h0: their rank is <= e <= h - p) */
   unsigned long long seed;    /* key of the Philox4x32-10 stream of the sketch */
   int gmres_m;                /* restart length of the refinement, default 30 */
   int gmres_maxit;            /* total iteration cap of the refinement, default 200 */
@@ -301,7 +302,9 @@ void spalu_factor_destroy(spalu_factor_t f);
  *   targets   y0 = log2(1 + k), y1 = log2(min(far rows, k + p));
  *   sketch    h = max(ceil(2^o1 (1 + margin)), ceil((2^o0 - 1)(1 + margin)) + p), clamped
  *             to [1, min(far rows, max(h0, 2 (e + p)))];
- *   applies   to segments whose far rows exceed max(h0, 8) and with e <= 128.
+ *   applies   to segments whose far rows exceed max(h0, 8), with e + p > 2 h0 and e <= 128
+ *             (a segment with e + p <= 2 h0 is sketched once with h = 2 h0 whatever the
+ *             mode: its rank is at most e <= h - p).
  * Parameter vector (float32, SPALU_PRED_NPARAM): W1 (64 x 16 row-major) | b1 (64) |
  * W2 (2 x 64) | b2 (2).  Inference rounds the standardised features, the parameters and
  * the hidden activations to bfloat16 and accumulates in float32. */

@@ -8,11 +8,14 @@ Weyl constants between rounds.  Written here from that published definition.
 Entry of G (the reading of the paper used by this project; the paper only says "a Gaussian
 random matrix"): for level ``l``, segment id ``sid``, sketch row ``r`` and far row labelled by
 its grid node ``v`` and half ``t`` (t=0 for a row of A_{n,i}, t=1 for a row of A_{i,n}^T),
-    counter = (r, v, 2*l + t, sid),   key = (seed mod 2^32, seed div 2^32 mod 2^32)
-and the first two output words give u1, u2 in (0,1) as odd multiples of 2^-24; the entry is
-the float32 Box-Muller value sqrt(-2 log u1) cos(2 pi u2) computed with the platform's own
-float32 log/sqrt/cos.  Because each entry is addressed by (r, v, t), the sketch does not
-depend on the order in which far rows are enumerated.
+    counter = (r div 4, v, 2*l + t, sid),   key = (seed mod 2^32, seed div 2^32 mod 2^32);
+the four output words give u1..u4 in (0,1) as odd multiples of 2^-24, and Box-Muller turns
+each pair into two independent standard normals:
+    z0 = R1 cos(2 pi u2), z1 = R1 sin(2 pi u2), z2 = R2 cos(2 pi u4), z3 = R2 sin(2 pi u4),
+    R1 = sqrt(-2 log u1), R2 = sqrt(-2 log u3)
+(float32, the platform's own log/sqrt/cos/sin); row r takes z_(r mod 4).  One counter thus
+serves four consecutive rows.  Because each entry is addressed by (r, v, t), the sketch does
+not depend on the order in which far rows are enumerated.
 """
 from __future__ import annotations
 
@@ -50,16 +53,19 @@ def _unit_f32(x):
             .astype(np.float32) * np.float32(2.0 ** -24))
 
 
-def gaussian_f32(c0, c1, c2, c3, seed: int):
-    """Box-Muller normal in float32 from the first two Philox words of each counter."""
+def gaussian4_f32(c0, c1, c2, c3, seed: int):
+    """Four Box-Muller normals in float32 per counter (last axis: z0..z3), two from each pair
+    of Philox output words."""
     k0 = seed & 0xFFFFFFFF
     k1 = (seed >> 32) & 0xFFFFFFFF
-    x0, x1, _, _ = philox4x32_10(c0, c1, c2, c3, k0, k1)
-    u1 = _unit_f32(x0)
-    u2 = _unit_f32(x1)
-    rad = np.sqrt(np.float32(-2.0) * np.log(u1))
-    ang = np.float32(6.283185307179586) * u2
-    return (rad * np.cos(ang)).astype(np.float32)
+    x = philox4x32_10(c0, c1, c2, c3, k0, k1)
+    u = [_unit_f32(w) for w in x]
+    two_pi = np.float32(6.283185307179586)
+    r1 = np.sqrt(np.float32(-2.0) * np.log(u[0]))
+    r2 = np.sqrt(np.float32(-2.0) * np.log(u[2]))
+    a1 = two_pi * u[1]
+    a2 = two_pi * u[3]
+    return np.stack([r1 * np.cos(a1), r1 * np.sin(a1), r2 * np.cos(a2), r2 * np.sin(a2)], axis=-1).astype(np.float32)
 
 
 def sketch_matrix(seed: int, level: int, sid: int, h: int, far_nodes, far_half) -> np.ndarray:
@@ -70,8 +76,10 @@ def sketch_matrix(seed: int, level: int, sid: int, h: int, far_nodes, far_half) 
     r = np.arange(h, dtype=np.int64)[:, None]
     v = far_nodes[None, :]
     t = far_half[None, :]
-    c0 = np.broadcast_to(r, (h, far_nodes.size))
+    c0 = np.broadcast_to(r // 4, (h, far_nodes.size))
     c1 = np.broadcast_to(v, (h, far_nodes.size))
     c2 = np.broadcast_to(2 * level + t, (h, far_nodes.size))
     c3 = np.full((h, far_nodes.size), sid, dtype=np.int64)
-    return gaussian_f32(c0, c1, c2, c3, seed).astype(np.float64)
+    z = gaussian4_f32(c0, c1, c2, c3, seed)
+    comp = np.broadcast_to(r % 4, (h, far_nodes.size))
+    return np.take_along_axis(z, comp[..., None], axis=-1)[..., 0].astype(np.float64)

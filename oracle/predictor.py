@@ -44,8 +44,10 @@ Parameters are one float32 vector: W1 (64 x 16, row-major) | b1 | W2 (2 x 64) | 
  * Acceptance of the one-pass ID: k <= h - p and ||B_r - B_s T||_F <= 10 eps ||B||_F on the
    exact B; otherwise the adaptive schedule continues from h <- min(2h, |F_rows|,
    max(h0, 2 (e + p))) (at that bound k <= e < h - p, so the schedule ends).
-The predictor is used for a segment only when the adaptive method would sketch it, the probe
-fits and the segment is not too large: |F_rows| > max(h0, PROBE) and e <= EMAX.
+The predictor is used for a segment only when the adaptive method would sketch it more than
+once, the probe fits and the segment is not too large: |F_rows| > max(h0, PROBE),
+e + p > 2 h0 (smaller segments are sketched once with h = 2 h0 >= e + p, the rank bound) and
+e <= EMAX.
 """
 from __future__ import annotations
 

@@ -13,9 +13,13 @@ Readings of the paper used here (the paper is silent or loose on these points):
     distance ``near_radius`` (2) of the segment (this includes both end junctions); the
     far rows are replaced by G B_F / sqrt(h) with G from ``philox.sketch_matrix``; when the
     far block has no more than h rows it is taken whole (Phi = I).
-  * Sketch size (h = k + p, p = 5 in Sec. 4.2.3; k unknown in advance): start with
-    h = min(|F|, 16); after the ID, while k > h - p and h < |F|, double h (capped at |F|)
-    and redo the sketch and the ID.
+  * Sketch size (h = k + p, p = 5 in Sec. 4.2.3; k unknown in advance): the rank is at most
+    the segment's size e, so a segment with e + p <= 2 h0 is sketched once with
+    h = min(|F|, 2 h0, max(h0, 2 (e + p))) (the size the adaptive schedule below reaches at its
+    second pass, within the schedule's own cap), and k <= e <= h - p holds at once (or h = |F|
+    and the far block is taken whole); a larger one starts with h = min(|F|, h0 = 16), and after
+    the ID, while k > h - p and h < |F|, h doubles (capped at |F|) and the sketch and the ID
+    are redone.
   * Truncation (Sec. 4.1): relative, the first k with |R_{k+1,k+1}| <= eps |R_{11}|.
     eps = 0 skips sparsification altogether (k = e), which makes the method exact block LU.
   * Order inside a level (Alg. 2 loops "for each segment"): every ID of level l is taken
@@ -356,8 +360,13 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0,
         return done(ident())
     p = opts.p_oversample
     h = min(nF, opts.h0)
+    # rank bound: k <= e, so a segment with e + p <= 2 h0 is sketched once with h = 2 h0 (the
+    # size the adaptive schedule reaches at its second pass), and that pass always stands
+    small = e + p <= 2 * opts.h0
+    if small:
+        h = min(nF, 2 * opts.h0, max(opts.h0, 2 * (e + p)))
     use_pred = (opts.predictor is not None or opts.record is not None) and A is not None \
-        and nF > max(opts.h0, pred.PROBE) and e <= pred.EMAX
+        and nF > max(opts.h0, pred.PROBE) and e <= pred.EMAX and not small
     predicted = False
     if use_pred:
         probe = sketch_matrix(opts.seed, l, sid, pred.PROBE, f_nodes, f_half) @ BF

@@ -52,16 +52,23 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
   }
 }
 
-// Entry of the sampling matrix G: counter (r, node, 2l+t, sid), key = seed; float32
-// Box-Muller from the first two words, u = odd multiple of 2^-24.
-__device__ __forceinline__ float sketch_gauss(unsigned long long seed, int l, int sid, int r, int node, int t) {
-  uint32_t c[4] = {(uint32_t)r, (uint32_t)node, (uint32_t)(2 * l + t), (uint32_t)sid};
+// Entries of the sampling matrix G for sketch rows 4 g .. 4 g + 3 of one far row: counter
+// (g, node, 2l+t, sid), key = seed; the four output words give u1..u4 (odd multiples of
+// 2^-24), and float32 Box-Muller turns each pair into two normals:
+// z = {R1 cos(2 pi u2), R1 sin(2 pi u2), R2 cos(2 pi u4), R2 sin(2 pi u4)}, R = sqrt(-2 log u).
+__device__ __forceinline__ void sketch_gauss4(unsigned long long seed, int l, int sid, int g, int node, int t,
+                                              float (&z)[4]) {
+  uint32_t c[4] = {(uint32_t)g, (uint32_t)node, (uint32_t)(2 * l + t), (uint32_t)sid};
   philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
-  float u1 = (float)(((c[0] >> 9) << 1) | 1u) * 0x1p-24f;
-  float u2 = (float)(((c[1] >> 9) << 1) | 1u) * 0x1p-24f;
-  float rad = sqrtf(-2.0f * logf(u1));
-  float ang = 6.283185307179586f * u2;
-  return rad * cosf(ang);
+  float u[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) u[i] = (float)(((c[i] >> 9) << 1) | 1u) * 0x1p-24f;
+  const float r1 = sqrtf(-2.0f * logf(u[0])), r2 = sqrtf(-2.0f * logf(u[2]));
+  const float a1 = 6.283185307179586f * u[1], a2 = 6.283185307179586f * u[3];
+  z[0] = r1 * cosf(a1);
+  z[1] = r1 * sinf(a1);
+  z[2] = r2 * cosf(a2);
+  z[3] = r2 * sinf(a2);
 }
 
 // ------------------------------------------------------------ neighbour runs of a segment
@@ -477,11 +484,19 @@ __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const NbrTab& tb,
       int t = row / nc, jj = row % nc;
       Bc[row + (size_t)rows * c] = bget(t, f0 + jj, c);
     }
-    for (int x = threadIdx.x; x < nr * rows; x += blockDim.x) {
-      int rr = x % nr, row = x / nr;
-      int t = row / nc, jj = row % nc;
+    // one Philox counter per group of four sketch rows (r0 is a multiple of 4)
+    const int g0 = r0 >> 2, ng = ((hh + 3) >> 2) - g0;
+    for (int x = threadIdx.x; x < ng * rows; x += blockDim.x) {
+      const int gi = x % ng, row = x / ng;
+      const int t = row / nc, jj = row % nc;
       const Nbr q = nbr_get(d, S, tb, f0 + jj);
-      Gc[rr + (size_t)nr * row] = q.nearf ? T(0) : (T)sketch_gauss(d.seed, d.l, sid, r0 + rr, q.node, t);
+      float z[4] = {0.f, 0.f, 0.f, 0.f};
+      if (!q.nearf) sketch_gauss4(d.seed, d.l, sid, g0 + gi, q.node, t, z);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int rr = 4 * (g0 + gi) + i - r0;
+        if (rr < nr) Gc[rr + (size_t)nr * row] = (T)z[i];
+      }
     }
     __syncthreads();
     for (int x = threadIdx.x; x < nr * e; x += blockDim.x) {
@@ -520,7 +535,18 @@ __device__ void probe_sketch(const LevelDev& d, const SegCtx& S, const NbrTab& t
         t = row / S.nb;
         q = nbr_get(d, S, tb, row % S.nb);
       }
-      const T g = q.nearf ? T(0) : (T)sketch_gauss(d.seed, d.l, sid, r8, q.node, t);
+      // lanes r8 = 0 and 4 of each node row draw the two counters (rows 0-3, 4-7); the
+      // others take their component by shuffle
+      float z[4] = {0.f, 0.f, 0.f, 0.f};
+      if (!q.nearf && (r8 & 3) == 0) sketch_gauss4(d.seed, d.l, sid, r8 >> 2, q.node, t, z);
+      const int srcl = lane & ~3;
+      float zc = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float v = __shfl_sync(0xffffffffu, z[i], srcl);
+        if ((r8 & 3) == i) zc = v;
+      }
+      const T g = q.nearf ? T(0) : (T)zc;
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int src = 8 * rr;
@@ -1009,8 +1035,13 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
   //      far rows, then the network's one-pass sketch size (PRED_PREDICT) or a training
   //      record of the features and the adaptive rank (PRED_RECORD)
   __shared__ float xf[PRED_NFEAT], zs[PRED_NFEAT], hid[PRED_NHID], pout[PRED_NOUT];
-  const bool use_pred = d.pred_mode != PRED_OFF && nF > max(d.h0, PRED_PROBE) && e <= PRED_EMAX;
-  int h = (nF <= d.h0) ? nF : d.h0;
+  // rank bound (k <= e): a segment with e + p <= 2 h0 is sketched once with
+  // h = min(2 h0, hmax) >= min(|F|, e + p), the size the adaptive schedule reaches at its
+  // second pass, and that pass always stands; the predictor serves the larger segments.
+  // Every h stays <= hmax, the rows the sketch buffer was sized for.
+  const bool small = e + d.p_over <= 2 * d.h0;
+  const bool use_pred = d.pred_mode != PRED_OFF && nF > max(d.h0, PRED_PROBE) && e <= PRED_EMAX && !small;
+  int h = (nF <= d.h0) ? nF : small ? min(hmax, 2 * d.h0) : min(hmax, d.h0);
   bool predicted = false;
   if (use_pred) {
     for (int x = threadIdx.x; x < PRED_PROBE * e; x += blockDim.x) Y[x] = T(0);   // Y8, pitch 8
@@ -1033,6 +1064,7 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     }
   }
 
+  h = min(h, hmax);          // the sketch buffer holds nN + hmax rows
   // ---- adaptive sketch + ID (Sec. 4.2.3; h = k + p with k unknown: double h until k <= h - p)
   int k = 0;
   int passes = 0;

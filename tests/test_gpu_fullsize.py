@@ -110,7 +110,9 @@ def test_headline_path_1023():
     npred = sum(lv["predicted"] for lv in st["levels"])
     print(f"headline direct solve vs FP64 GPU: norm-wise {nrm:.2e}, entry-wise {ent:.2e}; "
           f"{npred} predicted IDs, {sum(lv['fallbacks'] for lv in st['levels'])} fallbacks")
-    assert npred > 0.5 * sum(lv["nseg"] for lv in st["levels"])
+    # the network serves the segments past the rank bound (e + p > 2 h0: the coarser levels)
+    big = sum(lv["nseg"] for lv in st["levels"] if lv["e_max"] + 5 > 32)
+    assert 0 < npred <= big
     assert nrm <= 1e-2 and ent <= 5e-2
     it, rel = fm.refine(B, X)
     x = X.cpu().numpy().T

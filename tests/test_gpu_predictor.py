@@ -172,7 +172,9 @@ def test_trained_predictor_gains_over_adaptive_id():
     (xa, pa, _, _, ta), (xp, pp, npred, nfb, tp) = res["off"], res["predict"]
     print(f"ID passes adaptive {pa}, predicted {pp} ({npred} predicted, {nfb} fallbacks); "
           f"sparsify ms adaptive {ta:.3f}, predicted {tp:.3f}")
-    assert npred > 0 and pp <= 0.75 * pa and nfb <= 0.25 * npred
+    # every predicted segment would have taken at least two adaptive passes (smaller ones are
+    # sketched once by the rank bound); most of them save one
+    assert npred > 0 and pa - pp >= 0.4 * npred and nfb <= 0.25 * npred
     # same mode as the oracle (adaptive): the parity bar; predicted skeletons differ from the
     # adaptive ones, so that solution is held to the method's accuracy at eps = 1e-8 (the
     # oracle pins bound the error by 1e3 eps)

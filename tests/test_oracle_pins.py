@@ -16,7 +16,7 @@ import workloads as W
 from oracle.dense import cpqr, gepp, interp_decomp, lu_solve
 from oracle.gmres import gmres
 from oracle.nd import nested_dissection, separator_walk
-from oracle.philox import gaussian_f32, philox4x32_10, sketch_matrix
+from oracle.philox import gaussian4_f32, philox4x32_10, sketch_matrix
 from oracle.spalu import Elim, Options, Sparsify, factor, solve
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -36,12 +36,18 @@ def test_philox_known_answers():
 
 def test_gaussian_moments_and_independence():
     n = 200_000
-    z = gaussian_f32(np.arange(n), 7, 3, 11, seed=12345).astype(np.float64)
-    assert abs(z.mean()) < 0.01
-    assert abs(z.var() - 1.0) < 0.01
-    assert abs(np.mean(z**4) - 3.0) < 0.06           # Gaussian kurtosis
-    z2 = gaussian_f32(np.arange(n), 7, 3, 12, seed=12345).astype(np.float64)
-    assert abs(np.corrcoef(z, z2)[0, 1]) < 0.01       # different segment -> independent
+    Z = gaussian4_f32(np.arange(n), 7, 3, 11, seed=12345).astype(np.float64)
+    for i in range(4):                                # each of the four Box-Muller outputs
+        z = Z[:, i]
+        assert abs(z.mean()) < 0.01
+        assert abs(z.var() - 1.0) < 0.01
+        assert abs(np.mean(z**4) - 3.0) < 0.06       # Gaussian kurtosis
+    C = np.corrcoef(Z.T)                              # the four are uncorrelated (cos / sin of
+    assert np.all(np.abs(C - np.eye(4)) < 0.01)       # one pair, and different pairs)
+    r2 = Z[:, 0] ** 2 + Z[:, 1] ** 2                  # Box-Muller: z0^2 + z1^2 = -2 log u1 ~ chi^2_2
+    assert abs(np.mean(r2) - 2.0) < 0.02 and abs(np.mean(np.exp(-r2 / 2)) - 0.5) < 0.005
+    Z2 = gaussian4_f32(np.arange(n), 7, 3, 12, seed=12345).astype(np.float64)
+    assert abs(np.corrcoef(Z[:, 0], Z2[:, 0])[0, 1]) < 0.01   # different segment -> independent
 
 
 def test_sketch_is_order_free():

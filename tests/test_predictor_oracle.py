@@ -131,9 +131,10 @@ def _records(kind, n, seed, eps=1e-8):
 
 
 def test_feature_invariants():
-    _, lap = _records("laplace", 63, 1)
-    _, hel = _records("helmholtz", 63, 2)
-    _, cdf = _records("convdiff", 63, 3)
+    # records come from the segments the predictor serves (e + p > 2 h0): 127^2 has a few dozen
+    _, lap = _records("laplace", 127, 1)
+    _, hel = _records("helmholtz", 127, 2)
+    _, cdf = _records("convdiff", 127, 3)
     for recs in (lap, hel, cdf):
         X = np.array([r[0] for r in recs])
         assert np.all(np.isfinite(X))
@@ -151,16 +152,16 @@ def test_feature_invariants():
     assert np.all(Xc[:, 10] > 0.0)                             # convection shows
     for r in lap:                                              # targets are well defined
         k, nF, e, l = r[1:]
-        assert 0 <= k <= e and nF > 16
+        assert 0 <= k <= e and nF > 16 and e + 5 > 2 * 16     # only segments past the rank bound
 
 
 def test_oracle_predictor_saves_passes_and_keeps_the_solution():
     """Train the oracle network on adaptive records of small problems; on a held-out problem
-    the predicted one-pass IDs need fewer ID passes and the solution stays within the ID
-    tolerance of the adaptive one."""
+    the predicted one-pass IDs save ID passes (most predicted segments save the second
+    adaptive pass) and the solution stays within the ID tolerance of the adaptive one."""
     rec = []
-    for kind, n, seed in [("diffusion", 63, 1), ("diffusion", 127, 2), ("laplace", 63, 3),
-                          ("convdiff", 63, 4)]:
+    for kind, n, seed in [("diffusion", 127, 1), ("diffusion", 255, 2), ("laplace", 127, 3),
+                          ("convdiff", 127, 4)]:
         rec += _records(kind, n, seed)[1]
     X = np.array([r[0] for r in rec])
     Y = np.array([pr.targets(r[1], r[2], 5) for r in rec])
@@ -176,6 +177,6 @@ def test_oracle_predictor_saves_passes_and_keeps_the_solution():
     pp = sum(v["passes"] for v in Fp.stats["levels"].values())
     npred = sum(v["predicted"] for v in Fp.stats["levels"].values())
     nfb = sum(v["fallbacks"] for v in Fp.stats["levels"].values())
-    assert npred > 0 and pp < 0.8 * pa and nfb <= 0.3 * npred, (pa, pp, npred, nfb)
+    assert npred > 0 and pa - pp >= 0.4 * npred and nfb <= 0.3 * npred, (pa, pp, npred, nfb)
     xa, xp = solve(Fa, P.B), solve(Fp, P.B)
     assert np.linalg.norm(xp - xa) <= 1e-5 * np.linalg.norm(xa)
