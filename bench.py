@@ -39,7 +39,7 @@ N_SIDE = 1023
 NRHS = 16
 # relative margin of the learned sketch size h = (k^ + p)(1 + margin): 0.5 measured slightly
 # faster than the library default 0.35 at eps_ID 5e-7 (fewer fallbacks outweigh the larger sketches)
-PRED_MARGIN = 0.5
+PRED_MARGIN = 0.7
 EPS_ID = 1e-8
 FP64_FLOP_PER_CLK_SM = 4          # 2 FP64 FMA per clock per SM on GB300 (measured: 1.19 TFLOP/s)
 FP32_FLOP_PER_CLK_SM = 256        # 128 FP32 lanes x FMA per clock per SM
@@ -448,8 +448,8 @@ def run_ours(args):
     gpu_id = str(getattr(props, "uuid", "") or "")
     gpu_id = ("GPU-" + gpu_id) if gpu_id and not gpu_id.startswith("GPU-") else (gpu_id or str(local))
 
-    def measure(prec, eps, sample_clocks, pred=None, graph=not args.no_graph):
-        f = Factor(nd, eps_id=eps, symmetric=1, precision=prec)
+    def measure(prec, eps, sample_clocks, pred=None, graph=not args.no_graph, near_radius=2):
+        f = Factor(nd, eps_id=eps, symmetric=1, precision=prec, near_radius=near_radius)
         if pred is not None:
             f.set_predictor(pred, "predict", margin=PRED_MARGIN)
 
@@ -501,7 +501,9 @@ def run_ours(args):
         del f
         ms = max_over_ranks(pg, ms)
         return {"ms": ms, "iters": max(iters), "relres": max(rels), "launches": launches,
-                "st": st, "clocks": clocks}
+                "st": st, "clocks": clocks,
+                "sparsify_ms_per_level": {str(lv["level"]): round(st["timing_ms"].get(f"sparsify_l{lv['level']}", 0.0)
+                                                                 / args.steps, 4) for lv in st["levels"]}}
 
     alu = measured_alu_peaks()
     pred, pred_info = train_predictor(dev, 1, args.mixed_eps, args.pred_epochs)
@@ -513,6 +515,7 @@ def run_ours(args):
     base = measure(0, EPS_ID, False)              # plain FP64 GPU form
     base_loose = measure(0, args.mixed_eps, False)   # FP64 at the mixed path's eps_ID
     noml = measure(1, args.mixed_eps, False)      # ablation: mixed precision, adaptive ID
+    prnd = measure(1, args.mixed_eps, False, near_radius=-1)   # ablation: pure randomized sampling
 
     # end to end through the host-memory entry points (pinned host buffers), headline path
     val_h = torch.from_numpy(A.data).pin_memory().numpy()
@@ -574,10 +577,23 @@ def run_ours(args):
                                 "relres_max": base_loose["relres"], "gmres_iters": base_loose["iters"]},
         "mixed_adaptive": {"value": noml_value, "unit": "DOF/s", "ms_per_step": noml["ms"] / args.steps,
                            "relres_max": noml["relres"], "gmres_iters": noml["iters"],
-                           "id_passes": sum(lv["passes"] for lv in noml["st"]["levels"])},
+                           "id_passes": sum(lv["passes"] for lv in noml["st"]["levels"]),
+                           "sparsify_ms_per_level": noml["sparsify_ms_per_level"]},
+        "sampling_ablation": {"what": "mixed, adaptive ID, pure randomized sampling (every neighbour row "
+                                      "sketched, Sec. 4.2.1) against the hybrid sampling of mixed_adaptive",
+                              "value": job_value(ws, args.steps, N, prnd["ms"] / 1e3), "unit": "DOF/s",
+                              "ms_per_step": prnd["ms"] / args.steps, "relres_max": prnd["relres"],
+                              "gmres_iters": prnd["iters"],
+                              "k_sum": sum(lv["k_sum"] for lv in prnd["st"]["levels"]),
+                              "k_sum_hybrid": sum(lv["k_sum"] for lv in noml["st"]["levels"]),
+                              "sparsify_gflop": sum(lv["flops_sparsify"] for lv in prnd["st"]["levels"]) / 1e9,
+                              "sparsify_gflop_hybrid": sum(lv["flops_sparsify"] for lv in noml["st"]["levels"]) / 1e9,
+                              "sparsify_ms_per_level": prnd["sparsify_ms_per_level"]},
         "predictor": dict(pred_info, margin=PRED_MARGIN, id_passes=sum(lv["passes"] for lv in st["levels"]),
                           predicted=sum(lv["predicted"] for lv in st["levels"]),
-                          fallbacks=sum(lv["fallbacks"] for lv in st["levels"])),
+                          fallbacks=sum(lv["fallbacks"] for lv in st["levels"]),
+                          levels_on=[lv["level"] for lv in st["levels"] if lv.get("predictor") == 2],
+                          sparsify_ms_per_level=head["sparsify_ms_per_level"]),
         "speedup_vs_fp64": value / base_value,
         "nd_build_s": nd_s,
         "clocks": head["clocks"],

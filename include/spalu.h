@@ -64,7 +64,10 @@ typedef struct {
   int symmetric;              /* 1: caller asserts A = A^T and B = A_{n,i} is sampled;
                                  0: B = [A_{n,i}; A_{i,n}^T] (Sec. 4.5, Eq. (ID [A_ni; A_in])) */
   int p_oversample;           /* p of h = k + p (Sec. 4.2.3), default 5 */
-  int near_radius;            /* Chebyshev radius of the near field, default 2 */
+  int near_radius;            /* Chebyshev radius of the near field, default 2 (hybrid
+                                 sampling, Sec. 4.2.3: near rows kept exactly, far rows
+                                 sketched); -1: no near field, every neighbour row is
+                                 sketched (pure randomized sampling, Sec. 4.2.1) */
   int h0;                     /* first sketch size, default 16 (segments with e + p <= 2 h0 are
                                  sketched once with h = 2 h0: their rank is <= e <= h - p) */
   unsigned long long seed;    /* key of the Philox4x32-10 stream of the sketch */
@@ -149,10 +152,13 @@ spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream)
  * uncut worst case, then budgets for 2, 3, 4, 6, 8 and 12 resident segments per SM, see
  * spars_ctas), time every level's sparsification with CUDA events on stream, and keep the
  * fastest budget per level for later factorizations of this handle.  Ends with one more
- * factorization under the chosen budgets, so the handle is factored on return.  Requires a
+ * factorization under the chosen budgets, so the handle is factored on return.  In predict
+ * mode (spalu_factor_set_predictor) it also times every level with and without the network
+ * and keeps the network only on the levels where it was faster (per-level "predictor" in
+ * spalu_stats; the next spalu_factor_set_predictor call resets the choice).  Requires a
  * factored handle (SPALU_ERR_STATE otherwise); synchronises the stream; leaves the phase
- * timings of spalu_factor_stats as they were.  The factors agree with untuned ones up to
- * rounding. */
+ * timings of spalu_factor_stats as they were.  With the predictor choice unchanged the
+ * factors agree with untuned ones up to rounding. */
 spalu_status spalu_tune_factor(spalu_factor_t f, spalu_stream_t stream);
 
 /* Batched direct solve: spalu_solve(f[i], B[i], X[i], nrhs[i], ld[i], streams[i]) for

@@ -50,7 +50,7 @@ class Options:
     eps: float = 1e-8
     symmetric: bool = False
     p_oversample: int = 5
-    near_radius: int = 2
+    near_radius: int = 2          # -1: no near rows (pure randomized sampling, Sec. 4.2.1)
     h0: int = 16
     seed: int = 0
     # learned rank predictor (not in the paper; see oracle/predictor.py): a dict with

@@ -685,7 +685,7 @@ void spalu_nd_destroy(spalu_nd_t nd) {
 spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_factor_t* out) {
   if (!nd || !o || !out) return SPALU_ERR_ARG;
   *out = nullptr;
-  if (!(o->eps_id >= 0.0) || o->p_oversample < 0 || o->h0 < 1 || o->near_radius < 0 ||
+  if (!(o->eps_id >= 0.0) || o->p_oversample < 0 || o->h0 < 1 || o->near_radius < -1 ||
       o->gmres_m < 1 || o->gmres_maxit < 0 || o->spars_ctas < 0 || o->spars_ctas > 32)
     return SPALU_ERR_ARG;
   if (o->precision != 0 && o->precision != 1) return SPALU_ERR_ARG;
@@ -1069,6 +1069,30 @@ spalu_status spalu_tune_factor(spalu_factor_t f, spalu_stream_t stream) {
       if (tmin[l] < best_ms[l]) { best_ms[l] = tmin[l]; best_smem[l] = f->plan[l].spars_cand[c]; }
   }
   for (int l = 1; l <= L; ++l) f->plan[l].spars_smem = best_smem[l];
+  // predict mode: keep the network only on the levels where it measured faster than the
+  // adaptive schedule (its one-pass sketches against the probe, network and error-test
+  // overhead and the fallbacks)
+  if (st == SPALU_OK && f->pred_mode == PRED_PREDICT) {
+    std::vector<double> lt[2];
+    for (int on = 0; on < 2 && st == SPALU_OK; ++on) {
+      for (int l = 1; l <= L; ++l) f->lev[l].pred_mode = on ? PRED_PREDICT : PRED_OFF;
+      lt[on].assign(L + 1, 1e30);
+      for (int rep = 0; rep < 3 && st == SPALU_OK; ++rep) {
+        tm.on = true;
+        tm.ms.clear();
+        tm.count.clear();
+        st = factor_run(f, s);
+        tm.collect();
+        if (st != SPALU_OK || rep == 0) continue;
+        for (int l = 1; l <= L; ++l) {
+          auto it = tm.ms.find("sparsify_l" + std::to_string(l));
+          if (it != tm.ms.end()) lt[on][l] = std::min(lt[on][l], it->second);
+        }
+      }
+    }
+    for (int l = 1; l <= L; ++l)
+      f->lev[l].pred_mode = (st == SPALU_OK && lt[1][l] < lt[0][l]) ? PRED_PREDICT : PRED_OFF;
+  }
   tm.on = false;
   if (st == SPALU_OK) st = factor_run(f, s);
   tm.collect();
@@ -1806,9 +1830,10 @@ spalu_status spalu_stats(spalu_factor_t f, char* json, size_t cap) {
     if (emax > 0) qt = std::max(qt, (double)kmax / emax);
     char buf[640];
     const int* ls = f->lstat.data() + LS_N * l;
-    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld, \"sep_k_max\": %d, \"passes\": %d, \"fallbacks\": %d, \"predicted\": %d, \"flops_sparsify\": %llu, \"flops_merge\": %llu, \"bytes_seg\": %llu, \"bytes_sep\": %llu}",
+    std::snprintf(buf, sizeof buf, "%s{\"level\": %d, \"nseg\": %d, \"e_max\": %d, \"k_max\": %d, \"e_sum\": %lld, \"k_sum\": %lld, \"sep_k_max\": %d, \"passes\": %d, \"fallbacks\": %d, \"predicted\": %d, \"flops_sparsify\": %llu, \"flops_merge\": %llu, \"bytes_seg\": %llu, \"bytes_sep\": %llu, \"predictor\": %d}",
                   l == 1 ? "" : ", ", l, n, emax, kmax, esum, ksum, ls[LS_KPMAX], ls[LS_PASSES],
-                  ls[LS_FALLBACK], ls[LS_PREDICTED], fl[4 * l], fl[4 * l + 1], fl[4 * l + 2], fl[4 * l + 3]);
+                  ls[LS_FALLBACK], ls[LS_PREDICTED], fl[4 * l], fl[4 * l + 1], fl[4 * l + 2], fl[4 * l + 3],
+                  d.pred_mode);
     out += buf;
   }
   char buf[256];

@@ -100,6 +100,24 @@ def test_fp64_matches_oracle(kind, n, nrhs):
         assert abs(lv["k_max"] - o["k_max"]) <= 2
 
 
+@pytest.mark.parametrize("kind", ["diffusion", "convdiff"])
+def test_pure_randomized_sampling_matches_oracle(kind):
+    """near_radius = -1: no near field, every neighbour row is sketched (Sec. 4.2.1), against
+    the oracle in the same mode."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    n = 127
+    P = W.make_problem(kind, n, seed=36, nrhs=2)
+    rp, ci, va, B = _dev(P)
+    f = Factor(NestedDissection(n), eps_id=1e-8, symmetric=1 if P.symmetric else 0, near_radius=-1)
+    f.factor(rp, ci, va)
+    X = f.solve(B).cpu().numpy().T
+    F = ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-8, symmetric=P.symmetric, near_radius=-1))
+    assert_close(X, osolve(F, P.B), 1e-6, f"pure randomized {kind}")
+    for lv in f.stats()["levels"]:
+        o = F.stats["levels"][lv["level"]]
+        assert abs(lv["k_max"] - o["k_max"]) <= 2
+
+
 @pytest.mark.parametrize("nx,ny", [(127, 31), (31, 63)])
 def test_rectangular_grids(nx, ny):
     P = W.make_problem("diffusion", nx, seed=23, nrhs=2, ny=ny)

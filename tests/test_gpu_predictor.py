@@ -255,3 +255,28 @@ def test_factorization_is_deterministic():
     assert out[0][0] == out[1][0]
     # the separator updates of the solve are atomic additions (order free): rounding only
     assert np.linalg.norm(out[0][1] - out[1][1]) <= 1e-5 * np.linalg.norm(out[0][1])
+
+
+def test_tuner_keeps_the_network_where_it_is_faster():
+    """spalu_tune_factor in predict mode times each level with and without the network and
+    keeps it where it was faster; the factorization stays within the refinement's reach and a
+    new set_predictor call switches every level back on."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    p, _, _, _, _ = _train_on_recorded([("diffusion", 127, 1), ("diffusion", 255, 2)], precision=1,
+                                       eps=5e-7, epochs=100)
+    n = 255
+    P = W.make_problem("diffusion", n, seed=33, nrhs=2)
+    rp, ci, va, B = _dev(P)
+    f = Factor(NestedDissection(n), eps_id=5e-7, symmetric=1, precision=1)
+    f.set_predictor(p, "predict", margin=0.5)
+    f.factor(rp, ci, va)
+    f.tune_factor()
+    modes = [lv["predictor"] for lv in f.stats()["levels"]]
+    assert set(modes) <= {0, 2}
+    X = f.solve(B)
+    it, rel = f.refine(B, X)
+    x = X.cpu().numpy().T
+    res = np.linalg.norm(P.B - P.A.matvec(x), axis=0) / np.linalg.norm(P.B, axis=0)
+    assert np.all(res <= 1e-10)
+    f.set_predictor(p, "predict", margin=0.5)
+    assert all(lv["predictor"] == 2 for lv in f.stats()["levels"])

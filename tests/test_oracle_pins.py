@@ -243,14 +243,16 @@ def test_manufactured_solution_convergence_order(kind, order):
     assert 0.75 * 2**order < ratio < 1.3 * 2**order, ratio
 
 
-@pytest.mark.parametrize("kind", ["laplace", "diffusion", "convdiff"])
-def test_residual_tracks_eps(kind):
-    """R_es ~ eps with about one digit lost (Sec. 6.2); bound it by 1e3 eps."""
+@pytest.mark.parametrize("kind,near", [("laplace", 2), ("diffusion", 2), ("convdiff", 2), ("diffusion", -1),
+                                       ("convdiff", -1)])
+def test_residual_tracks_eps(kind, near):
+    """R_es ~ eps with about one digit lost (Sec. 6.2); bound it by 1e3 eps.  Also for pure
+    randomized sampling (near = -1: every neighbour row sketched, Sec. 4.2.1)."""
     n = 127
     P = W.make_problem(kind, n, seed=4, nrhs=1)
     nd = nested_dissection(n, n)
     eps = 1e-8
-    F = factor(P.A, nd, Options(eps=eps, symmetric=P.symmetric))
+    F = factor(P.A, nd, Options(eps=eps, symmetric=P.symmetric, near_radius=near))
     X = solve(F, P.B)
     res = np.linalg.norm(P.B - P.A.matvec(X)) / np.linalg.norm(P.B)
     assert res <= 1e3 * eps, res
