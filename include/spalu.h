@@ -41,6 +41,7 @@ typedef struct CUstream_st* spalu_stream_t;          /* same type as cudaStream_
 typedef struct spalu_nd_s* spalu_nd_t;               /* opaque, library-owned */
 typedef struct spalu_factor_s* spalu_factor_t;       /* opaque, library-owned, owns device memory */
 typedef struct spalu_predictor_s* spalu_predictor_t; /* opaque, library-owned, owns device memory */
+typedef struct spalu_batch_s* spalu_batch_t;         /* opaque, library-owned */
 
 typedef enum {
   SPALU_OK = 0,
@@ -217,6 +218,30 @@ spalu_status spalu_factor_solve_host(spalu_factor_t f, const int* rowptr, const 
 spalu_status spalu_factor_solve_graph(spalu_factor_t f, const int* rowptr, const int* colind, const double* val,
                                       int nnz, const double* B, double* X, int nrhs, int ld, int* iters,
                                       double* relres, spalu_stream_t stream);
+
+/* Many independent problems as one CUDA graph (scheduling; not in the paper): problem i is
+ * the step of spalu_factor_solve_graph for handle f[i] (its own grid and options), CSR matrix
+ * rowptr[i] / colind[i] / val[i] (nnz[i] entries), right-hand sides B[i] and solution X[i]
+ * (nrhs[i] >= 1 columns, leading dimension ld[i], X[i] != B[i]): numeric factorization, direct
+ * solve and, with refine != 0, one GMRES cycle in conditional nodes.  The problems' nodes are
+ * spread over nstreams branches of the one graph so that they run concurrently.  create runs
+ * every problem once plainly on stream (setting capacities, allocations and step counts),
+ * then captures; *out receives the handle.  The handles f[i] must be distinct, stay alive and
+ * unused by other calls while the batch exists, and every array must stay valid and in place
+ * (new values may be written into them between runs).  SPALU_ERR_ARG on an invalid argument
+ * (nothing is run). */
+spalu_status spalu_batch_graph_create(int n, const spalu_factor_t* f, const int* const* rowptr,
+                                      const int* const* colind, const double* const* val, const int* nnz,
+                                      const double* const* B, double* const* X, const int* nrhs, const int* ld,
+                                      int nstreams, int refine, spalu_stream_t stream, spalu_batch_t* out);
+/* Launch the batch graph on stream and wait for it.  iters[i] / relres[i] (host arrays of n,
+ * may be NULL): the GMRES steps and the largest relative residual of problem i (with
+ * refine).  A problem whose new factor outgrew the captured solve capacities is solved and
+ * refined outside the graph (the batch is captured again afterwards); columns still above
+ * the tolerance after the graph's cycle continue with spalu_refine.  Returns the first
+ * non-OK status of the problems (every problem is finished either way). */
+spalu_status spalu_batch_graph_run(spalu_batch_t b, int* iters, double* relres, spalu_stream_t stream);
+void spalu_batch_graph_destroy(spalu_batch_t b);
 
 /* JSON summary of the last factorization: per level the segment sizes and ranks, the
  * largest separator skeleton, the number of IDs computed ("passes"), of predicted one-pass

@@ -3,8 +3,8 @@
 The compute path lives in the CUDA library built from ``csrc/`` into ``_build/libspalu.so``
 (C ABI: ``include/spalu.h``); ``spalu`` is a thin ctypes binding with the same names.
 """
-from .spalu import (Factor, NestedDissection, Options, Predictor, SpaluError, factor_batch,
+from .spalu import (BatchGraph, Factor, NestedDissection, Options, Predictor, SpaluError, factor_batch,
                     library_path, load_library, solve_batch, status_string)
 
-__all__ = ["Factor", "NestedDissection", "Options", "Predictor", "SpaluError", "factor_batch",
+__all__ = ["BatchGraph", "Factor", "NestedDissection", "Options", "Predictor", "SpaluError", "factor_batch",
            "library_path", "load_library", "solve_batch", "status_string"]

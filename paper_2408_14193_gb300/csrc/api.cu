@@ -1465,19 +1465,17 @@ static spalu_status arnoldi_step(spalu_factor_t f, int nrhs, int j, cudaGraphCon
   return SPALU_OK;
 }
 
-static spalu_status capture_step(spalu_factor_t f, const int* rowptr, const int* colind, const double* val,
-                                 int nnz, const double* B, double* X, int nrhs, int ld, cudaStream_t s) {
-  // captured on a stream of the handle's own (the caller's may be the legacy default stream,
-  // which cannot be captured); the graph is launched on the caller's stream
-  auto& G = f->sg;
+// Guard references and solve capacities for a capture: the level maxima with some headroom
+// (skeleton sizes move by a few unknowns between factorizations of the same matrix: FP32
+// rounding, learned sketch sizes), the solve capacities of the captured kernels set from them,
+// and the leaf-sweep variant; uploaded before the capture starts.
+static spalu_status step_prepare(spalu_factor_t f, spalu_factor_s::StepGraph& G) {
   const int L = f->nd->L;
-  const int N = f->N, m = f->o.gmres_m;
-  const int K = std::min(m, std::max(4, f->gmres_hint + 2));
-  GmresWork& w = f->gw;
-  const size_t ldv = (size_t)N;
-  // guard references: the level maxima with some headroom (skeleton sizes move by a few
-  // unknowns between factorizations of the same matrix: FP32 rounding, learned sketch sizes),
-  // and the solve capacities of the captured kernels set from them
+  if (!G.d_ref) {
+    if (cudaMalloc(&G.d_ref, sizeof(int) * 3 * (L + 1)) != cudaSuccess || cudaMalloc(&G.d_ok, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&G.h_out, sizeof(int) * 2) != cudaSuccess)
+      return SPALU_ERR_ALLOC;
+  }
   std::vector<int> ref(3 * (L + 1), 0);
   for (int l = 1; l <= L; ++l) {
     int lm[LS_N] = {};
@@ -1497,94 +1495,86 @@ static spalu_status capture_step(spalu_factor_t f, const int* rowptr, const int*
   }
   f->kumax = f->kumax <= 15 ? 15 : 30;       // the two leaf-sweep variants
   CUDA_TRY(cudaMemcpy(G.d_ref, ref.data(), sizeof(int) * ref.size(), cudaMemcpyHostToDevice));
-  cudaStream_t s2 = nullptr, s3 = nullptr;
-  CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
-  if (cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaStreamDestroy(s2);
-    return SPALU_ERR_CUDA;
-  }
-  cudaStream_t s1 = nullptr;
-  if (cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaStreamDestroy(s2);
-    cudaStreamDestroy(s3);
-    return SPALU_ERR_CUDA;
-  }
-  (void)s;
-  s = s1;
-  spalu_status st = SPALU_OK;
-  cudaGraph_t graph = nullptr;
-  auto fail = [&](spalu_status e) {
-    cudaGraph_t junk = nullptr;
-    cudaStreamEndCapture(s3, &junk);
-    if (junk) cudaGraphDestroy(junk);
-    junk = nullptr;
-    cudaStreamEndCapture(s2, &junk);
-    if (junk) cudaGraphDestroy(junk);
-    junk = nullptr;
-    cudaStreamEndCapture(s, &junk);
-    if (junk) cudaGraphDestroy(junk);
-    cudaGetLastError();
-    return e;
-  };
-#define CAP_TRY(x)                                   \
-  do {                                               \
-    cudaError_t _e = (x);                            \
-    if (_e != cudaSuccess) { report_cuda(#x, _e, __LINE__); st = fail(SPALU_ERR_CUDA); goto done; } \
-  } while (0)
+  G.K = std::min(f->o.gmres_m, std::max(4, f->gmres_hint + 2));
+  return SPALU_OK;
+}
+
+// One problem's step enqueued into the capture in progress on stream s (its top-level graph
+// takes every node; s2 captures the bodies of the conditional nodes): the matrix copy, the
+// factorization, the guard, then in conditional nodes the solve and (refine != 0) one GMRES
+// cycle of G.K steps and the update of X; finally the guard result and the "still active" flag
+// copied to G.h_out.
+static spalu_status capture_step_into(spalu_factor_t f, spalu_factor_s::StepGraph& G, const int* rowptr,
+                                      const int* colind, const double* val, int nnz, const double* B, double* X,
+                                      int nrhs, int ld, int refine, cudaStream_t s, cudaStream_t s2) {
+  const int L = f->nd->L;
+  const int N = f->N, m = f->o.gmres_m;
+  const int K = refine ? G.K : 0;
+  GmresWork& w = f->gw;
+  const size_t ldv = (size_t)N;
   G.n_step.assign(K, 0);
-  f->timer.drop_graph();
-  f->timer.cap_top = s;
+  unsigned long long c0 = g_launches.load();
+  cudaGraph_t top = nullptr;
+#define CAP_TRY(x)                                        \
+  do {                                                    \
+    cudaError_t _e = (x);                                 \
+    if (_e != cudaSuccess) { report_cuda(#x, _e, __LINE__); return SPALU_ERR_CUDA; } \
+  } while (0)
   {
-    unsigned long long c0 = g_launches.load();
-    CAP_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    cudaGraph_t top = nullptr;
-    {
-      cudaStreamCaptureStatus cs;
-      CAP_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &top, nullptr, nullptr, nullptr));
-    }
-    // every conditional node sits in the top-level graph; the handles are reset to 0 at each
-    // launch, so when the guard fails nothing after it runs
-    // one handle per conditional node: h_act[j] (set by the set-up or by step j-1) opens step j
-    cudaGraphConditionalHandle h_ok, h_ok2;
-    std::vector<cudaGraphConditionalHandle> h_act(K + 1);
-    CAP_TRY(cudaGraphConditionalHandleCreate(&h_ok, top, 0, cudaGraphCondAssignDefault));
-    CAP_TRY(cudaGraphConditionalHandleCreate(&h_ok2, top, 0, cudaGraphCondAssignDefault));
-    for (int j = 0; j < K; ++j) CAP_TRY(cudaGraphConditionalHandleCreate(&h_act[j], top, 0, cudaGraphCondAssignDefault));
-    CAP_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
-    CAP_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
-    CAP_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if ((st = factor_enqueue(f, s)) != SPALU_OK) { st = fail(st); goto done; }
-    note_launch();
-    step_guard_kernel<<<1, 32, 0, s>>>(f->d_err, f->leaf.kumax, f->kumax, f->d_lstat, G.d_ref, L, G.d_ok, h_ok,
-                                       h_ok2);
-    CAP_TRY(cudaGetLastError());
-    G.n_pre = (long long)(g_launches.load() - c0);
-    c0 = g_launches.load();
-    // solve, then the cycle's set-up
-    cudaGraph_t body;
-    CAP_TRY(add_if_node(s, h_ok, &body));
-    CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    if ((st = solve_impl(f, B, nullptr, X, nrhs, ld, (spalu_stream_t)s2)) != SPALU_OK) { st = fail(st); goto done; }
+    cudaStreamCaptureStatus cs;
+    CAP_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &top, nullptr, nullptr, nullptr));
+  }
+  // every conditional node sits in the top-level graph with a handle of its own (a handle
+  // serves one node), reset to 0 at each launch: when the guard fails nothing after it runs;
+  // h_act[j] (set by the cycle's set-up or by step j-1) opens Arnoldi step j
+  cudaGraphConditionalHandle h_ok, h_ok2;
+  std::vector<cudaGraphConditionalHandle> h_act(K + 1);
+  CAP_TRY(cudaGraphConditionalHandleCreate(&h_ok, top, 0, cudaGraphCondAssignDefault));
+  CAP_TRY(cudaGraphConditionalHandleCreate(&h_ok2, top, 0, cudaGraphCondAssignDefault));
+  for (int j = 0; j < K; ++j) CAP_TRY(cudaGraphConditionalHandleCreate(&h_act[j], top, 0, cudaGraphCondAssignDefault));
+  CAP_TRY(cudaMemcpyAsync(f->rowptr, rowptr, (N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CAP_TRY(cudaMemcpyAsync(f->colind, colind, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CAP_TRY(cudaMemcpyAsync(f->val, val, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  spalu_status st = factor_enqueue(f, s);
+  if (st != SPALU_OK) return st;
+  note_launch();
+  step_guard_kernel<<<1, 32, 0, s>>>(f->d_err, f->leaf.kumax, f->kumax, f->d_lstat, G.d_ref, L, G.d_ok, h_ok, h_ok2);
+  CAP_TRY(cudaGetLastError());
+  G.n_pre = (long long)(g_launches.load() - c0);
+  c0 = g_launches.load();
+  // solve, then the cycle's set-up
+  cudaGraph_t body;
+  CAP_TRY(add_if_node(s, h_ok, &body));
+  CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  st = solve_impl(f, B, nullptr, X, nrhs, ld, (spalu_stream_t)s2);
+  if (st == SPALU_OK && refine) {
     vec_mgs(f, nrhs, nullptr, nullptr, 0, nullptr, const_cast<double*>(B), ld, nullptr, 0, nullptr, w.bn, 1,
             nullptr, s2);
     vec_spmv(f, nrhs, X, ld, B, ld, w.V, (int)ldv, nullptr, 0, nullptr, w.beta, 1, s2);
     note_launch();
-    gmres_begin_kernel<<<1, GB, 0, s2>>>(nrhs, m, f->o.gmres_tol, w.bn, w.beta, w.vs, w.g, w.st, 1, w.flag, h_act[0], 1);
-    {
-      cudaGraph_t out2 = nullptr;
-      CAP_TRY(cudaStreamEndCapture(s2, &out2));
-    }
-    // the Arnoldi steps, each while some column is active
-    for (int j = 0; j < K; ++j) {
-      CAP_TRY(add_if_node(s, h_act[j], &body));
-      CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      const unsigned long long cj = g_launches.load();
-      if ((st = arnoldi_step(f, nrhs, j, h_act[j + 1], j + 1 < K ? 1 : 0, s2)) != SPALU_OK) { st = fail(st); goto done; }
-      G.n_step[j] = (long long)(g_launches.load() - cj);
-      c0 += G.n_step[j];
-      cudaGraph_t out2 = nullptr;
-      CAP_TRY(cudaStreamEndCapture(s2, &out2));
-    }
+    gmres_begin_kernel<<<1, GB, 0, s2>>>(nrhs, m, f->o.gmres_tol, w.bn, w.beta, w.vs, w.g, w.st, 1, w.flag, h_act[0],
+                                         1);
+  }
+  {
+    cudaGraph_t out2 = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s2, &out2);
+    if (st != SPALU_OK) return st;
+    CAP_TRY(e);
+  }
+  // the Arnoldi steps, each while some column is active
+  for (int j = 0; j < K; ++j) {
+    CAP_TRY(add_if_node(s, h_act[j], &body));
+    CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const unsigned long long cj = g_launches.load();
+    st = arnoldi_step(f, nrhs, j, h_act[j + 1], j + 1 < K ? 1 : 0, s2);
+    G.n_step[j] = (long long)(g_launches.load() - cj);
+    c0 += G.n_step[j];
+    cudaGraph_t out2 = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s2, &out2);
+    if (st != SPALU_OK) return st;
+    CAP_TRY(e);
+  }
+  if (refine) {
     // the update of X and the residual of the result
     CAP_TRY(add_if_node(s, h_ok2, &body));
     CAP_TRY(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
@@ -1598,30 +1588,107 @@ static spalu_status capture_step(spalu_factor_t f, const int* rowptr, const int*
     note_launch();
     gmres_begin_kernel<<<1, GB, 0, s2>>>(nrhs, m, f->o.gmres_tol, w.bn, w.beta, w.vs, w.g, w.st, 0, w.flag,
                                          cudaGraphConditionalHandle{}, 0);
-    {
-      cudaGraph_t out2 = nullptr;
-      CAP_TRY(cudaStreamEndCapture(s2, &out2));
-    }
-    G.n_ok = (long long)(g_launches.load() - c0);
-    CAP_TRY(cudaMemcpyAsync(G.h_out, G.d_ok, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CAP_TRY(cudaMemcpyAsync(G.h_out + 1, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CAP_TRY(cudaStreamEndCapture(s, &graph));
-    if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
-      G.exec = nullptr;
-      st = SPALU_ERR_CUDA;
+    cudaGraph_t out2 = nullptr;
+    CAP_TRY(cudaStreamEndCapture(s2, &out2));
+  }
+  G.n_ok = (long long)(g_launches.load() - c0);
+  CAP_TRY(cudaMemcpyAsync(G.h_out, G.d_ok, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (refine) CAP_TRY(cudaMemcpyAsync(G.h_out + 1, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+#undef CAP_TRY
+  return SPALU_OK;
+}
+
+// End every capture still open on the given streams (after a failure) and clear the error.
+static void abandon_capture(std::initializer_list<cudaStream_t> ss) {
+  for (cudaStream_t x : ss) {
+    if (!x) continue;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(x, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(x, &junk);
+      if (junk) cudaGraphDestroy(junk);
     }
   }
-done:
-#undef CAP_TRY
+  cudaGetLastError();
+}
+
+static spalu_status capture_step(spalu_factor_t f, const int* rowptr, const int* colind, const double* val,
+                                 int nnz, const double* B, double* X, int nrhs, int ld) {
+  // captured on streams of the call's own (the caller's may be the legacy default stream,
+  // which cannot be captured); the graph is launched on the caller's stream
+  auto& G = f->sg;
+  spalu_status st = step_prepare(f, G);
+  if (st != SPALU_OK) return st;
+  cudaStream_t s1 = nullptr, s2 = nullptr;
+  if (cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+    if (s1) cudaStreamDestroy(s1);
+    return SPALU_ERR_CUDA;
+  }
+  f->timer.drop_graph();
+  f->timer.cap_top = s1;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s1, cudaStreamCaptureModeRelaxed) != cudaSuccess) st = SPALU_ERR_CUDA;
+  if (st == SPALU_OK) st = capture_step_into(f, G, rowptr, colind, val, nnz, B, X, nrhs, ld, 1, s1, s2);
+  if (st == SPALU_OK && cudaStreamEndCapture(s1, &graph) != cudaSuccess) st = SPALU_ERR_CUDA;
+  if (st != SPALU_OK) abandon_capture({s2, s1});
+  if (st == SPALU_OK && cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
+    G.exec = nullptr;
+    st = SPALU_ERR_CUDA;
+  }
   f->timer.cap_top = nullptr;
   if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(s1);
   cudaStreamDestroy(s2);
-  cudaStreamDestroy(s3);
   if (st != SPALU_OK) return st;
-  G.key[0] = rowptr; G.key[1] = colind; G.key[2] = val; G.key[3] = B; G.key[4] = X; G.key[5] = w.V;
-  G.nnz = nnz; G.nrhs = nrhs; G.ld = ld; G.K = K; G.timed = f->timer.on;
+  G.key[0] = rowptr; G.key[1] = colind; G.key[2] = val; G.key[3] = B; G.key[4] = X; G.key[5] = f->gw.V;
+  G.nnz = nnz; G.nrhs = nrhs; G.ld = ld; G.timed = f->timer.on;
   ++G.captures;
+  return SPALU_OK;
+}
+
+// After a replay (stream synchronised): the factorization's readback, the launch count of what
+// ran, and the cases the graph left open: a failed guard (solve and refine redone outside;
+// *refit = true) and columns still above the tolerance (more cycles outside).
+static spalu_status step_finish(spalu_factor_t f, spalu_factor_s::StepGraph& G, const double* B, double* X,
+                                int nrhs, int ld, int refine, int* iters, double* relres, spalu_stream_t stream,
+                                bool* refit) {
+  cudaStream_t s = (cudaStream_t)stream;
+  *refit = false;
+  note_launches(G.n_pre);
+  spalu_status st = factor_finish(f, s);
+  if (st != SPALU_OK) return st;
+  if (!G.h_out[0]) {
+    *refit = true;
+    if ((st = spalu_solve(f, B, X, nrhs, ld, stream)) != SPALU_OK) return st;
+    if (!refine) return SPALU_OK;
+    return spalu_refine(f, B, X, nrhs, ld, iters, relres, stream);
+  }
+  if (!refine) {
+    note_launches(G.n_ok);
+    return SPALU_OK;
+  }
+  std::vector<double> bn(nrhs), beta(nrhs);
+  std::vector<int> stc(4 * (size_t)nrhs);
+  CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
+  int its = 0;
+  for (int c = 0; c < nrhs; ++c) its = std::max(its, stc[4 * c + 2]);
+  long long n = G.n_ok;                      // kernels that ran inside the conditional nodes
+  for (int j = 0; j < its && j < G.K; ++j) n += G.n_step[j];
+  note_launches(n);
+  if (G.h_out[1]) {
+    // not converged within the captured steps: continue with more cycles outside the graph
+    ++G.continued;
+    int it2 = 0;
+    st = spalu_refine(f, B, X, nrhs, ld, &it2, relres, stream);
+    if (iters) *iters = its + it2;
+    return st;
+  }
+  CUDA_TRY(cudaMemcpy(bn.data(), f->gw.bn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(beta.data(), f->gw.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+  for (int c = 0; c < nrhs; ++c)
+    if (relres) relres[c] = bn[c] == 0.0 ? 0.0 : beta[c] / bn[c];
+  if (iters) *iters = its;
   return SPALU_OK;
 }
 
@@ -1646,16 +1713,8 @@ spalu_status spalu_factor_solve_graph(spalu_factor_t f, const int* rowptr, const
     if ((st = spalu_solve(f, B, X, nrhs, ld, stream)) != SPALU_OK) return st;
     st = spalu_refine(f, B, X, nrhs, ld, iters, relres, stream);
     if (st != SPALU_OK && st != SPALU_ERR_NOCONV) return st;
-    if (!G.d_ref) {
-      const int L = f->nd->L;
-      if (cudaMalloc(&G.d_ref, sizeof(int) * 3 * (L + 1)) != cudaSuccess ||
-          cudaMalloc(&G.d_ok, sizeof(int)) != cudaSuccess || cudaMallocHost(&G.h_out, sizeof(int) * 2) != cudaSuccess) {
-        step_graph_free(f);
-        return SPALU_ERR_ALLOC;
-      }
-    }
     CUDA_TRY(cudaStreamSynchronize(s));
-    const spalu_status cst = capture_step(f, rowptr, colind, val, nnz, B, X, nrhs, ld, s);
+    const spalu_status cst = capture_step(f, rowptr, colind, val, nnz, B, X, nrhs, ld);
     if (cst != SPALU_OK) step_graph_free(f);
     return cst != SPALU_OK ? cst : st;
   }
@@ -1666,53 +1725,168 @@ spalu_status spalu_factor_solve_graph(spalu_factor_t f, const int* rowptr, const
   CUDA_TRY(cudaStreamSynchronize(s));
   if (G.timed) f->timer.collect_graph();
   ++G.replays;
-  // the factorization's readback (error word, leaf bandwidth, level counters) came with the graph
-  note_launches(G.n_pre);
-  spalu_status st = factor_finish(f, s);
-  if (st != SPALU_OK) return st;
-  if (G.h_out[0]) {          // kernels that ran inside the conditional nodes
-    int steps = 0;
-    std::vector<int> stc(4 * (size_t)nrhs);
-    CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
-    for (int c = 0; c < nrhs; ++c) steps = std::max(steps, stc[4 * c + 2]);
-    long long n = G.n_ok;
-    for (int j = 0; j < steps && j < G.K; ++j) n += G.n_step[j];
-    note_launches(n);
-  }
-  if (!G.h_out[0]) {
-    // the new factor outgrew the captured capacities: solve and refine outside the graph, and
-    // capture again next time
+  bool refit = false;
+  const spalu_status st = step_finish(f, G, B, X, nrhs, ld, 1, iters, relres, stream, &refit);
+  if (refit) {
+    // the new factor outgrew the captured capacities: capture again next time
     cudaGraphExecDestroy(G.exec);
     G.exec = nullptr;
     f->timer.drop_graph();
     ++G.refits;
-    if ((st = spalu_solve(f, B, X, nrhs, ld, stream)) != SPALU_OK) return st;
-    return spalu_refine(f, B, X, nrhs, ld, iters, relres, stream);
   }
-  if (G.h_out[1]) {
-    // not converged within the captured steps: continue with more cycles outside the graph
-    ++G.continued;
-    int it2 = 0;
-    std::vector<int> stc(4 * (size_t)nrhs);
-    CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
-    int its = 0;
-    for (int c = 0; c < nrhs; ++c) its = std::max(its, stc[4 * c + 2]);
-    st = spalu_refine(f, B, X, nrhs, ld, &it2, relres, stream);
-    if (iters) *iters = its + it2;
+  return st;
+}
+
+// ------------------------------------------------------------ many problems as one graph
+struct spalu_batch_s {
+  int n = 0, refine = 0, nstreams = 1;
+  std::vector<spalu_factor_t> f;
+  std::vector<spalu_factor_s::StepGraph> G;
+  std::vector<const int*> rowptr, colind;
+  std::vector<const double*> val, B;
+  std::vector<double*> X;
+  std::vector<int> nnz, nrhs, ld;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+
+static void batch_release(spalu_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  for (auto& g : b->G) {
+    cudaFree(g.d_ref);
+    cudaFree(g.d_ok);
+    cudaFreeHost(g.h_out);
+    g.d_ref = nullptr; g.d_ok = nullptr; g.h_out = nullptr;
+  }
+}
+
+// capture every problem's step into one graph: each on one of nstreams forked streams
+static spalu_status batch_capture(spalu_batch_s* b) {
+  const int n = b->n, K = std::max(1, std::min(b->nstreams, n));
+  for (int i = 0; i < n; ++i) {
+    const spalu_status st = step_prepare(b->f[i], b->G[i]);
+    if (st != SPALU_OK) return st;
+  }
+  std::vector<cudaStream_t> ss(K, nullptr);
+  std::vector<cudaEvent_t> ev(K + 1, nullptr);
+  cudaStream_t s0 = nullptr, s2 = nullptr;
+  spalu_status st = SPALU_OK;
+  if (cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess)
+    st = SPALU_ERR_CUDA;
+  for (int k = 0; k < K && st == SPALU_OK; ++k)
+    if (cudaStreamCreateWithFlags(&ss[k], cudaStreamNonBlocking) != cudaSuccess) st = SPALU_ERR_CUDA;
+  for (int k = 0; k <= K && st == SPALU_OK; ++k)
+    if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) st = SPALU_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  const unsigned long long c0 = g_launches.load();
+  if (st == SPALU_OK && cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed) != cudaSuccess) st = SPALU_ERR_CUDA;
+  if (st == SPALU_OK && cudaEventRecord(ev[K], s0) != cudaSuccess) st = SPALU_ERR_CUDA;
+  for (int k = 0; k < K && st == SPALU_OK; ++k)
+    if (cudaStreamWaitEvent(ss[k], ev[K], 0) != cudaSuccess) st = SPALU_ERR_CUDA;
+  for (int i = 0; i < n && st == SPALU_OK; ++i)
+    st = capture_step_into(b->f[i], b->G[i], b->rowptr[i], b->colind[i], b->val[i], b->nnz[i], b->B[i], b->X[i],
+                           b->nrhs[i], b->ld[i], b->refine, ss[i % K], s2);
+  for (int k = 0; k < K && st == SPALU_OK; ++k)
+    if (cudaEventRecord(ev[k], ss[k]) != cudaSuccess || cudaStreamWaitEvent(s0, ev[k], 0) != cudaSuccess)
+      st = SPALU_ERR_CUDA;
+  if (st == SPALU_OK && cudaStreamEndCapture(s0, &graph) != cudaSuccess) st = SPALU_ERR_CUDA;
+  if (st != SPALU_OK) {
+    std::vector<cudaStream_t> all(ss);
+    all.push_back(s2);
+    all.push_back(s0);
+    for (cudaStream_t x : all) abandon_capture({x});
+  }
+  if (st == SPALU_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+    b->exec = nullptr;
+    st = SPALU_ERR_CUDA;
+  }
+  b->kernels = (long long)(g_launches.load() - c0);
+  if (graph) cudaGraphDestroy(graph);
+  for (auto e : ev) if (e) cudaEventDestroy(e);
+  for (auto x : ss) if (x) cudaStreamDestroy(x);
+  if (s2) cudaStreamDestroy(s2);
+  if (s0) cudaStreamDestroy(s0);
+  return st;
+}
+
+spalu_status spalu_batch_graph_create(int n, const spalu_factor_t* f, const int* const* rowptr,
+                                      const int* const* colind, const double* const* val, const int* nnz,
+                                      const double* const* B, double* const* X, const int* nrhs, const int* ld,
+                                      int nstreams, int refine, spalu_stream_t stream, spalu_batch_t* out) {
+  if (!out) return SPALU_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || !f || !rowptr || !colind || !val || !nnz || !B || !X || !nrhs || !ld || nstreams < 1)
+    return SPALU_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!f[i] || !rowptr[i] || !colind[i] || !val[i] || nnz[i] < 0 || nnz[i] > f[i]->nnz_cap || !B[i] || !X[i] ||
+        nrhs[i] < 1 || ld[i] < f[i]->N || B[i] == X[i])
+      return SPALU_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (f[j] == f[i]) return SPALU_ERR_ARG;       // a handle's buffers serve one problem
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  auto* b = new spalu_batch_s();
+  b->n = n; b->refine = refine ? 1 : 0; b->nstreams = nstreams;
+  b->f.assign(f, f + n);
+  b->G.resize(n);
+  b->rowptr.assign(rowptr, rowptr + n); b->colind.assign(colind, colind + n); b->val.assign(val, val + n);
+  b->B.assign(B, B + n); b->X.assign(X, X + n);
+  b->nnz.assign(nnz, nnz + n); b->nrhs.assign(nrhs, nrhs + n); b->ld.assign(ld, ld + n);
+  // the plain path once per problem (capacities, allocations, step counts)
+  spalu_status st = SPALU_OK;
+  for (int i = 0; i < n && st == SPALU_OK; ++i) {
+    step_graph_free(f[i]);                   // a single-step graph of the handle is given up
+    st = spalu_factor_numeric(f[i], rowptr[i], colind[i], val[i], nnz[i], stream);
+    if (st == SPALU_OK) st = spalu_solve(f[i], B[i], X[i], nrhs[i], ld[i], stream);
+    if (st == SPALU_OK && refine) {
+      st = spalu_refine(f[i], B[i], X[i], nrhs[i], ld[i], nullptr, nullptr, stream);
+      if (st == SPALU_ERR_NOCONV) st = SPALU_OK;
+    }
+  }
+  if (st == SPALU_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SPALU_ERR_CUDA;
+  if (st == SPALU_OK) st = batch_capture(b);
+  if (st != SPALU_OK) {
+    batch_release(b);
+    delete b;
     return st;
   }
-  std::vector<double> bn(nrhs), beta(nrhs);
-  std::vector<int> stc(4 * (size_t)nrhs);
-  CUDA_TRY(cudaMemcpy(bn.data(), f->gw.bn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
-  CUDA_TRY(cudaMemcpy(beta.data(), f->gw.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
-  CUDA_TRY(cudaMemcpy(stc.data(), f->gw.st, sizeof(int) * 4 * nrhs, cudaMemcpyDeviceToHost));
-  int its = 0;
-  for (int c = 0; c < nrhs; ++c) {
-    if (relres) relres[c] = bn[c] == 0.0 ? 0.0 : beta[c] / bn[c];
-    its = std::max(its, stc[4 * c + 2]);
-  }
-  if (iters) *iters = its;
+  *out = b;
   return SPALU_OK;
+}
+
+spalu_status spalu_batch_graph_run(spalu_batch_t b, int* iters, double* relres, spalu_stream_t stream) {
+  if (!b || !b->exec) return SPALU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaGraphLaunch(b->exec, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  spalu_status first = SPALU_OK;
+  bool any_refit = false;
+  std::vector<double> rel;
+  for (int i = 0; i < b->n; ++i) {
+    rel.assign(b->nrhs[i], 0.0);
+    int it = 0;
+    bool refit = false;
+    spalu_status st = step_finish(b->f[i], b->G[i], b->B[i], b->X[i], b->nrhs[i], b->ld[i], b->refine, &it,
+                                  rel.data(), stream, &refit);
+    any_refit = any_refit || refit;
+    if (iters) iters[i] = it;
+    if (relres) relres[i] = rel.empty() ? 0.0 : *std::max_element(rel.begin(), rel.end());
+    if (st != SPALU_OK && first == SPALU_OK) first = st;
+  }
+  if (any_refit && first == SPALU_OK) {        // some factor outgrew its captured capacities
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    first = batch_capture(b);
+  }
+  return first;
+}
+
+void spalu_batch_graph_destroy(spalu_batch_t b) {
+  if (!b) return;
+  batch_release(b);
+  delete b;
 }
 
 spalu_status spalu_solve_host(spalu_factor_t f, const double* B, double* X, int nrhs, int ld,

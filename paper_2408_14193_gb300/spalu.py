@@ -88,6 +88,9 @@ SIGNATURES = [
     ("spalu_solve_host", _I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_factor_solve_host", _I, [_P, _P, _P, _P, _I, _P, _P, _I, _I, _I, _P, _P, _P]),
     ("spalu_factor_solve_graph", _I, [_P, _P, _P, _P, _I, _P, _P, _I, _I, _P, _P, _P]),
+    ("spalu_batch_graph_create", _I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P, _P]),
+    ("spalu_batch_graph_run", _I, [_P, _P, _P, _P]),
+    ("spalu_batch_graph_destroy", None, [_P]),
     ("spalu_stats", _I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     ("spalu_factor_export_level", _I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     ("spalu_residual_noalloc", _I, [_P, _P, _P, _I, _I, _P, _P]),
@@ -507,4 +510,51 @@ class Predictor:
         h = getattr(self, "handle", None)
         if h:
             self.lib.spalu_predictor_destroy(h)
+            self.handle = None
+
+
+class BatchGraph:
+    """spalu_batch_graph_*: the steps (factor, solve, optionally one GMRES cycle) of many
+    independent problems captured as one CUDA graph; run() replays it."""
+
+    def __init__(self, factors, csrs, Bs, Xs, nstreams: int = 16, refine: bool = True, stream=None):
+        import torch
+        n = len(factors)
+        if not (len(csrs) == n and len(Bs) == n and len(Xs) == n):
+            raise ValueError("factors, csrs, Bs and Xs must have the same length")
+        self.lib = load_library()
+        self.factors = list(factors)
+        self._keep = (list(csrs), list(Bs), list(Xs))
+        P = ctypes.c_void_p * n
+        for f, (rp, ci, va) in zip(factors, csrs):
+            f._csr_shape(rp, ci, va)
+        self.nrhs = [f._nrhs(B, X) for f, B, X in zip(factors, Bs, Xs)]
+        args = [P(*[f.handle for f in factors]),
+                P(*[_dev_ptr(c[0], torch.int32).value for c in csrs]),
+                P(*[_dev_ptr(c[1], torch.int32).value for c in csrs]),
+                P(*[_dev_ptr(c[2], torch.float64).value for c in csrs]),
+                (ctypes.c_int * n)(*[int(c[2].numel()) for c in csrs]),
+                P(*[_dev_ptr(B, torch.float64).value for B in Bs]),
+                P(*[_dev_ptr(X, torch.float64).value for X in Xs]),
+                (ctypes.c_int * n)(*self.nrhs),
+                (ctypes.c_int * n)(*[f.N for f in factors])]
+        h = ctypes.c_void_p()
+        _check(self.lib.spalu_batch_graph_create(n, *args, int(nstreams), 1 if refine else 0, _stream_ptr(stream),
+                                                 ctypes.byref(h)), "spalu_batch_graph_create")
+        self.handle = h
+        self.n = n
+
+    def run(self, stream=None, check=True):
+        """Replay the graph; returns (iterations per problem, largest relative residual per problem)."""
+        it = np.zeros(self.n, dtype=np.int32)
+        rel = np.zeros(self.n)
+        st = self.lib.spalu_batch_graph_run(self.handle, it.ctypes.data, rel.ctypes.data, _stream_ptr(stream))
+        if check:
+            _check(st, "spalu_batch_graph_run")
+        return it, rel
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.lib.spalu_batch_graph_destroy(h)
             self.handle = None

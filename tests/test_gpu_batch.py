@@ -74,3 +74,53 @@ def test_batch_rejects_bad_arguments():
     big = torch.zeros(csr[2].numel() * 10, dtype=torch.float64, device=dev)
     with pytest.raises(SpaluError):
         factor_batch([f], [(csr[0], csr[1], big)], [torch.cuda.current_stream()])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_graph_matches_one_at_a_time(precision):
+    """Independent problems of different sizes as one CUDA graph (factor, solve, one GMRES
+    cycle each, spread over 3 branches): every problem refined to 1e-10 (CPU residual), the
+    replay follows new values written into the same buffers."""
+    from paper_2408_14193_gb300 import BatchGraph, Factor, NestedDissection
+    dev = torch.device("cuda:0")
+    sizes = [63, 127, 63, 255, 31]
+    nds = {n: NestedDissection(n) for n in set(sizes)}
+    probs = [_problem(n, 200 + i, dev) for i, n in enumerate(sizes)]
+    eps = 1e-8 if precision == 0 else 5e-7
+    fs = [Factor(nds[n], eps_id=eps, symmetric=1, precision=precision) for n in sizes]
+    Xs = [torch.zeros_like(p[2]) for p in probs]
+    bg = BatchGraph(fs, [p[1] for p in probs], [p[2] for p in probs], Xs, nstreams=3)
+
+    def check(Ps):
+        for P, X in zip(Ps, Xs):
+            x = X.cpu().numpy().T
+            res = np.linalg.norm(P.B - P.A.matvec(x), axis=0) / np.linalg.norm(P.B, axis=0)
+            assert np.all(res <= 1e-10), res
+
+    for _ in range(2):
+        for X in Xs:
+            X.zero_()
+        it, rel = bg.run()
+        assert np.all(rel <= 1e-10) and np.all(it >= 1)
+        check([p[0] for p in probs])
+    # new matrices (other seeds) in the same buffers, same right-hand sides
+    new = []
+    for i, (n, p) in enumerate(zip(sizes, probs)):
+        Q = W.make_problem("diffusion", n, seed=300 + i, nrhs=1)
+        Q.B = p[0].B
+        p[1][2].copy_(torch.from_numpy(Q.A.data).to(dev))
+        new.append(Q)
+    it, rel = bg.run()
+    check(new)
+
+
+def test_batch_graph_rejects_bad_arguments():
+    from paper_2408_14193_gb300 import BatchGraph, Factor, NestedDissection, SpaluError
+    dev = torch.device("cuda:0")
+    nd = NestedDissection(31)
+    f = Factor(nd, eps_id=1e-8, symmetric=1)
+    P, csr, B = _problem(31, 5, dev)
+    with pytest.raises(SpaluError):                 # the same handle twice
+        BatchGraph([f, f], [csr, csr], [B, B.clone()], [torch.zeros_like(B), torch.zeros_like(B)])
+    with pytest.raises(SpaluError):                 # X aliasing B
+        BatchGraph([f], [csr], [B], [B])
