@@ -482,23 +482,27 @@ def run_ours(args):
     gpu_id = str(getattr(props, "uuid", "") or "")
     gpu_id = ("GPU-" + gpu_id) if gpu_id and not gpu_id.startswith("GPU-") else (gpu_id or str(local))
 
-    def measure(prec, eps, sample_clocks, pred=None, graph=not args.no_graph, near_radius=2):
-        f = Factor(nd, eps_id=eps, symmetric=1, precision=prec, near_radius=near_radius)
+    def measure(prec, eps, sample_clocks, pred=None, graph=not args.no_graph, near_radius=2, prob=None,
+                steps=None, tune=True):
+        pnd, prp, pci, pva, pB, pX, psym = prob or (nd, rp, ci, va, B, X, 1)
+        nsteps = steps or args.steps
+        f = Factor(pnd, eps_id=eps, symmetric=psym, precision=prec, near_radius=near_radius)
         if pred is not None:
             f.set_predictor(pred, "predict", margin=PRED_MARGIN)
 
         def step():
             if graph:                             # factor + solve + refine as one CUDA graph
-                return f.factor_solve_graph(rp, ci, va, B, X)
-            f.factor(rp, ci, va)
-            f.solve(B, X)
-            return f.refine(B, X)
+                return f.factor_solve_graph(prp, pci, pva, pB, pX)
+            f.factor(prp, pci, pva)
+            f.solve(pB, pX)
+            return f.refine(pB, pX)
 
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        f.tune_factor()                           # sparsify occupancy per level (untimed)
-        f.tune_solve(NRHS)                        # CTA widths of the level solves (untimed)
+        if tune:
+            f.tune_factor()                       # sparsify occupancy per level (untimed)
+            f.tune_solve(min(16, int(pB.shape[0])))   # CTA widths of the level solves (untimed)
         f.set_timing(True)                        # phase events (captured into the graph too)
         step()                                    # plain run + capture after the tuners
         step()
@@ -512,7 +516,7 @@ def run_ours(args):
         l0 = kernel_launches()
         ms = 0.0
         iters, rels = [], []
-        for _ in range(args.steps):
+        for _ in range(nsteps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -537,7 +541,23 @@ def run_ours(args):
         return {"ms": ms, "iters": max(iters), "relres": max(rels), "launches": launches,
                 "st": st, "clocks": clocks,
                 "sparsify_ms_per_level": {str(lv["level"]): round(st["timing_ms"].get(f"sparsify_l{lv['level']}", 0.0)
-                                                                 / args.steps, 4) for lv in st["levels"]}}
+                                                                 / nsteps, 4) for lv in st["levels"]}}
+
+    def other_config(kind, n, nrhs, prec, eps, sym, steps, tune, pred=None):
+        """One more workload of the configuration list (its own generated problem)."""
+        Q = W.make_problem(kind, n, seed=2 + rank, nrhs=nrhs)
+        qd = (NestedDissection(n), torch.from_numpy(Q.A.indptr).to(dev), torch.from_numpy(Q.A.indices).to(dev),
+              torch.from_numpy(Q.A.data).to(dev))
+        QB = torch.from_numpy(np.ascontiguousarray(Q.B.T)).to(dev)
+        r = measure(prec, eps, False, pred=pred, prob=qd + (QB, torch.zeros_like(QB), sym), steps=steps, tune=tune)
+        out = {"value": job_value(ws, steps, n * n, r["ms"] / 1e3), "unit": "DOF/s", "ms_per_step": r["ms"] / steps,
+               "N": n * n, "nrhs": nrhs, "precision": "mixed" if prec else "fp64", "eps_id": eps,
+               "relres_max": r["relres"], "gmres_iters": r["iters"], "steps": steps,
+               "k_max": max(lv["k_max"] for lv in r["st"]["levels"]),
+               "e_max": max(lv["e_max"] for lv in r["st"]["levels"])}
+        del qd, QB
+        torch.cuda.empty_cache()
+        return out
 
     alu = measured_alu_peaks()
     pred, pred_info = train_predictor(dev, 1, args.mixed_eps, args.pred_epochs)
@@ -550,6 +570,17 @@ def run_ours(args):
     base_loose = measure(0, args.mixed_eps, False)   # FP64 at the mixed path's eps_ID
     noml = measure(1, args.mixed_eps, False)      # ablation: mixed precision, adaptive ID
     prnd = measure(1, args.mixed_eps, False, near_radius=-1)   # ablation: pure randomized sampling
+    cfg3 = cfg2 = None
+    if not args.no_configs:
+        # convection-diffusion 1023^2, 4 RHS, learned predictor on (the non-symmetric family)
+        cfg3 = dict(other_config("convdiff", N_SIDE, 4, 1, args.mixed_eps, 0, args.steps, True, pred),
+                    workload=f"convection-diffusion {N_SIDE}x{N_SIDE}, beta=50(cos t, sin t), first-order upwind, "
+                             "4 normal RHS, mixed precision, learned ranks, GMRES to 1e-10")
+        # Helmholtz 2047^2 at 10 points per wavelength, 8 point sources: the FP32 factor of this
+        # indefinite operator leaves GMRES without convergence, so the factor is FP64
+        cfg2 = dict(other_config("helmholtz", 2047, 8, 0, EPS_ID, 1, 3, False),
+                    workload="Helmholtz 2047x2047, k0 = 2 pi / (10 h), k^2 (1 + 0.2 GRF), 8 Gaussian point "
+                             "sources, FP64 factor (the mixed one does not converge), eps_ID=1e-8, GMRES to 1e-10")
 
     # end to end through the host-memory entry points (pinned host buffers), headline path
     val_h = torch.from_numpy(A.data).pin_memory().numpy()
@@ -646,6 +677,8 @@ def run_ours(args):
         "step_graph": st.get("step_graph"),
         "cpu_baseline": cpu,
         "batch": batch,
+        "config3_convdiff": cfg3,
+        "config2_helmholtz": cfg2,
     }
     print(json.dumps(line), flush=True)
     if pg:
@@ -673,6 +706,8 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="the batched workload (256 independent problems) instead of the headline")
     ap.add_argument("--batch-n", type=int, default=256, dest="batch_n")
+    ap.add_argument("--no-configs", action="store_true", dest="no_configs",
+                    help="leave the convection-diffusion and Helmholtz workloads out of the headline run")
     ap.add_argument("--no-batch", action="store_true", dest="no_batch",
                     help="leave the batched workload out of the headline run")
     args = ap.parse_args()
