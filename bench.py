@@ -483,10 +483,10 @@ def run_ours(args):
     gpu_id = ("GPU-" + gpu_id) if gpu_id and not gpu_id.startswith("GPU-") else (gpu_id or str(local))
 
     def measure(prec, eps, sample_clocks, pred=None, graph=not args.no_graph, near_radius=2, prob=None,
-                steps=None, tune=True):
+                steps=None, tune=True, schur_tc=1):
         pnd, prp, pci, pva, pB, pX, psym = prob or (nd, rp, ci, va, B, X, 1)
         nsteps = steps or args.steps
-        f = Factor(pnd, eps_id=eps, symmetric=psym, precision=prec, near_radius=near_radius)
+        f = Factor(pnd, eps_id=eps, symmetric=psym, precision=prec, near_radius=near_radius, schur_tc=schur_tc)
         if pred is not None:
             f.set_predictor(pred, "predict", margin=PRED_MARGIN)
 
@@ -541,7 +541,8 @@ def run_ours(args):
         return {"ms": ms, "iters": max(iters), "relres": max(rels), "launches": launches,
                 "st": st, "clocks": clocks,
                 "sparsify_ms_per_level": {str(lv["level"]): round(st["timing_ms"].get(f"sparsify_l{lv['level']}", 0.0)
-                                                                 / nsteps, 4) for lv in st["levels"]}}
+                                                                 / nsteps, 4) for lv in st["levels"]},
+                "merge_ms": sum(v for k, v in st["timing_ms"].items() if k.startswith("merge_l")) / nsteps}
 
     def other_config(kind, n, nrhs, prec, eps, sym, steps, tune, pred=None):
         """One more workload of the configuration list (its own generated problem)."""
@@ -564,7 +565,7 @@ def run_ours(args):
     if args.factor_only:
         # profiling runs: the headline matrix factored (mixed precision, learned ranks) warmup +
         # steps times, nothing else on the device (no solve vectors, no GMRES basis)
-        f = Factor(nd, eps_id=args.mixed_eps, symmetric=1, precision=1)
+        f = Factor(nd, eps_id=args.mixed_eps, symmetric=1, precision=1, schur_tc=1 if args.schur_tc else 0)
         f.set_predictor(pred, "predict", margin=PRED_MARGIN)
         for _ in range(args.warmup + args.steps):
             f.factor(rp, ci, va)
@@ -581,6 +582,7 @@ def run_ours(args):
     base_loose = measure(0, args.mixed_eps, False)   # FP64 at the mixed path's eps_ID
     noml = measure(1, args.mixed_eps, False)      # ablation: mixed precision, adaptive ID
     prnd = measure(1, args.mixed_eps, False, near_radius=-1)   # ablation: pure randomized sampling
+    scc = measure(1, args.mixed_eps, False, schur_tc=0)      # ablation: Schur updates on the CUDA cores
     cfg3 = cfg2 = None
     if not args.no_configs:
         # convection-diffusion 1023^2, 4 RHS, learned predictor on (the non-symmetric family)
@@ -668,6 +670,13 @@ def run_ours(args):
                               "sparsify_gflop": sum(lv["flops_sparsify"] for lv in prnd["st"]["levels"]) / 1e9,
                               "sparsify_gflop_hybrid": sum(lv["flops_sparsify"] for lv in noml["st"]["levels"]) / 1e9,
                               "sparsify_ms_per_level": prnd["sparsify_ms_per_level"]},
+        "schur_cuda_cores": {"what": "mixed, adaptive ID, separator Schur updates M -= Z W in FP32 on the CUDA "
+                                     "cores, against the tensor-core updates (mma.sync TF32, operands split into "
+                                     "high and low parts, 3 products) of mixed_adaptive and the headline",
+                             "value": job_value(ws, args.steps, N, scc["ms"] / 1e3), "unit": "DOF/s",
+                             "ms_per_step": scc["ms"] / args.steps, "gmres_iters": scc["iters"],
+                             "relres_max": scc["relres"], "merge_ms_per_step": scc["merge_ms"],
+                             "merge_ms_per_step_tensor_cores": noml["merge_ms"]},
         "predictor": dict(pred_info, margin=PRED_MARGIN, id_passes=sum(lv["passes"] for lv in st["levels"]),
                           predicted=sum(lv["predicted"] for lv in st["levels"]),
                           fallbacks=sum(lv["fallbacks"] for lv in st["levels"]),
@@ -712,6 +721,8 @@ def main():
     ap.add_argument("--pred-epochs", type=int, default=200, dest="pred_epochs")
     ap.add_argument("--no-graph", action="store_true", dest="no_graph",
                     help="time the plain calls (factor, solve, refine) instead of the captured step graph")
+    ap.add_argument("--schur-cuda-cores", action="store_false", dest="schur_tc",
+                    help="with --factor-only: separator Schur updates on the CUDA cores")
     ap.add_argument("--factor-only", action="store_true", dest="factor_only",
                     help="factor the headline matrix warmup + steps times and exit (profiler runs)")
     ap.add_argument("--only-mixed", action="store_true", dest="only_mixed",

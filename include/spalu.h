@@ -82,6 +82,11 @@ typedef struct {
                                  keeps its sketch and frontal rows in global memory (results
                                  agree up to rounding).  0 = size for the largest segment the
                                  geometry allows.  Default 4. */
+  int schur_tc;               /* mixed precision only: 1 (default) = the separators' Schur
+                                 updates M -= Z W run on the tensor cores (mma.sync TF32 with
+                                 the operands split into high and low TF32 parts, three
+                                 products per tile: FP32-level accuracy); 0 = FP32 FMA on the
+                                 CUDA cores.  Ignored in FP64 mode. */
 } spalu_opts;
 
 /* Fill *o with the defaults listed above (eps_id = 1e-8, precision 0, symmetric 0). */

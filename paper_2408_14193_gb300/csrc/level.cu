@@ -1612,6 +1612,92 @@ __global__ void __launch_bounds__(256) merge_schur_kernel(LevelDev d) {
     }
 }
 
+// The same update on the tensor cores (mixed path, schur_tc): mma.sync m16n8k8 with TF32
+// operands and FP32 accumulation.  TF32 keeps 10 mantissa bits, so each operand is split into
+// a high part tf32(x) and a low part tf32(x - hi) and three products are accumulated (the two
+// cross terms first, then hi*hi): the result matches an FP32 product to about FP32 rounding
+// (the lo*lo term, below 2^-22 relative, is dropped).  64 x 64 tile per CTA: warp w owns rows
+// 16 (w % 4) .. +16 and columns 32 (w / 4) .. +32 (four 16 x 8 accumulator tiles).
+// Fragment layouts of m16n8k8 (PTX ISA, tf32): g = lane / 4, q = lane % 4;
+//   A (16 x 8, row major): a0 (g, q), a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4);
+//   B (8 x 8, column major): b0 (q, g), b1 (q + 4, g);
+//   C (16 x 8): c0 (g, 2q), c1 (g, 2q + 1), c2 (g + 8, 2q), c3 (g + 8, 2q + 1).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(256) merge_schur_tc_kernel(LevelDev d) {
+  __shared__ float Zs[64][17];
+  __shared__ float Ws[16][65];
+  __shared__ int ra[64], cb[64];
+  const int P = blockIdx.z;
+  const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
+  if (kp == 0 || ndP == 0) return;
+  const int tiles = (ndP + 63) / 64;
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti >= tiles || tj >= tiles) return;
+  const int* tab = d.ptab + (size_t)P * d.ldFp * TABW;
+  const size_t ldp = d.ldFp;
+  float* M = static_cast<float*>(d.Fp) + (size_t)P * ldp * ldp;
+  const int Dp = d.gp.D();
+  for (int x = threadIdx.x; x < 64; x += blockDim.x) {
+    int a = ti * 64 + x, b = tj * 64 + x;
+    ra[x] = a < ndP ? tab[(size_t)a * TABW] : -1;
+    cb[x] = b < ndP ? tab[(size_t)b * TABW] : -1;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int r0 = 16 * (warp & 3), c0 = 32 * (warp >> 2);
+  float acc[4][4] = {};
+  for (int j0 = 0; j0 < kp; j0 += 16) {
+    for (int x = threadIdx.x; x < 64 * 16; x += blockDim.x) {
+      int i = x % 64, j = x / 64;
+      Zs[i][j] = (ra[i] >= 0 && j0 + j < kp) ? M[ra[i] + ldp * (Dp + j0 + j)] : 0.f;
+      Ws[j][i] = (cb[i] >= 0 && j0 + j < kp) ? M[(Dp + j0 + j) + ldp * cb[i]] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      uint32_t ah[4], al[4];
+      split_tf32(Zs[r0 + g][8 * ks + q], ah[0], al[0]);
+      split_tf32(Zs[r0 + g + 8][8 * ks + q], ah[1], al[1]);
+      split_tf32(Zs[r0 + g][8 * ks + q + 4], ah[2], al[2]);
+      split_tf32(Zs[r0 + g + 8][8 * ks + q + 4], ah[3], al[3]);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        uint32_t bh[2], bl[2];
+        split_tf32(Ws[8 * ks + q][c0 + 8 * t + g], bh[0], bl[0]);
+        split_tf32(Ws[8 * ks + q + 4][c0 + 8 * t + g], bh[1], bl[1]);
+        mma_tf32(acc[t], al, bh);
+        mma_tf32(acc[t], ah, bl);
+        mma_tf32(acc[t], ah, bh);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = r0 + g + 8 * (u >> 1), c = c0 + 8 * t + 2 * q + (u & 1);
+      if (ra[i] >= 0 && cb[c] >= 0) M[ra[i] + ldp * cb[c]] -= acc[t][u];
+    }
+}
+
 // Level-(l-1) segment tables: counts and grid nodes (merged sides: [skel 1, junction, skel 2]).
 __global__ void seg_merge_kernel(LevelDev d) {
   const Geo gp = d.gp, g = d.g;
@@ -2158,7 +2244,8 @@ static void merge_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) 
     int tiles = (p.ldFp + 63) / 64;
     dim3 grid(tiles, tiles, np);
     note_launch();
-    merge_schur_kernel<T><<<grid, 256, 0, s>>>(d);
+    if (d.schur_tc && d.fp32) merge_schur_tc_kernel<<<grid, 256, 0, s>>>(d);
+    else merge_schur_kernel<T><<<grid, 256, 0, s>>>(d);
   }
   if (d.l > 1 && d.gp.nseg() > 0) {
     note_launch();

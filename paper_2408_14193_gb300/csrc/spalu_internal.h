@@ -158,6 +158,7 @@ struct LevelDev {
   // options
   double eps;
   int symmetric, p_over, near_radius, h0;
+  int schur_tc;     // separator Schur updates on the tensor cores (mixed path only)
   unsigned long long seed;
   int* err;
   int* lstat;       // [LS_N] counters of this level (maxima of e, kp, |dP|; ID passes, ...)

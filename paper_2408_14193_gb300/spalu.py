@@ -51,6 +51,7 @@ class Options(ctypes.Structure):
         ("gmres_maxit", ctypes.c_int),
         ("gmres_tol", ctypes.c_double),
         ("spars_ctas", ctypes.c_int),
+        ("schur_tc", ctypes.c_int),
     ]
 
     @classmethod
