@@ -483,10 +483,11 @@ def run_ours(args):
     gpu_id = ("GPU-" + gpu_id) if gpu_id and not gpu_id.startswith("GPU-") else (gpu_id or str(local))
 
     def measure(prec, eps, sample_clocks, pred=None, graph=not args.no_graph, near_radius=2, prob=None,
-                steps=None, tune=True, schur_tc=1):
+                steps=None, tune=True, schur_tc=1, sketch_tc=0):
         pnd, prp, pci, pva, pB, pX, psym = prob or (nd, rp, ci, va, B, X, 1)
         nsteps = steps or args.steps
-        f = Factor(pnd, eps_id=eps, symmetric=psym, precision=prec, near_radius=near_radius, schur_tc=schur_tc)
+        f = Factor(pnd, eps_id=eps, symmetric=psym, precision=prec, near_radius=near_radius, schur_tc=schur_tc,
+                   sketch_tc=sketch_tc)
         if pred is not None:
             f.set_predictor(pred, "predict", margin=PRED_MARGIN)
 
@@ -583,6 +584,7 @@ def run_ours(args):
     noml = measure(1, args.mixed_eps, False)      # ablation: mixed precision, adaptive ID
     prnd = measure(1, args.mixed_eps, False, near_radius=-1)   # ablation: pure randomized sampling
     scc = measure(1, args.mixed_eps, False, schur_tc=0)      # ablation: Schur updates on the CUDA cores
+    sktc = measure(1, args.mixed_eps, False, sketch_tc=1)    # ablation: sketch products on the tensor cores
     cfg3 = cfg2 = None
     if not args.no_configs:
         # convection-diffusion 1023^2, 4 RHS, learned predictor on (the non-symmetric family)
@@ -677,6 +679,13 @@ def run_ours(args):
                              "ms_per_step": scc["ms"] / args.steps, "gmres_iters": scc["iters"],
                              "relres_max": scc["relres"], "merge_ms_per_step": scc["merge_ms"],
                              "merge_ms_per_step_tensor_cores": noml["merge_ms"]},
+        "sketch_tensor_cores": {"what": "mixed, adaptive ID, sketch products G B_F on the tensor cores (split-TF32 "
+                                        "mma.sync) against the FP32 CUDA-core products of mixed_adaptive",
+                                "value": job_value(ws, args.steps, N, sktc["ms"] / 1e3), "unit": "DOF/s",
+                                "ms_per_step": sktc["ms"] / args.steps, "gmres_iters": sktc["iters"],
+                                "relres_max": sktc["relres"],
+                                "sparsify_ms_per_step": sum(sktc["sparsify_ms_per_level"].values()),
+                                "sparsify_ms_per_step_cuda_cores": sum(noml["sparsify_ms_per_level"].values())},
         "predictor": dict(pred_info, margin=PRED_MARGIN, id_passes=sum(lv["passes"] for lv in st["levels"]),
                           predicted=sum(lv["predicted"] for lv in st["levels"]),
                           fallbacks=sum(lv["fallbacks"] for lv in st["levels"]),

@@ -87,6 +87,11 @@ typedef struct {
                                  the operands split into high and low TF32 parts, three
                                  products per tile: FP32-level accuracy); 0 = FP32 FMA on the
                                  CUDA cores.  Ignored in FP64 mode. */
+  int sketch_tc;              /* mixed precision only: 1 = the sketch products G B_F
+                                 (Sec. 4.2.3) on the tensor cores (the same split-TF32
+                                 mma.sync); 0 (default) = FP32 FMA on the CUDA cores (the
+                                 random entries of G, not the product, dominate the sketch's
+                                 cost).  Ignored in FP64 mode. */
 } spalu_opts;
 
 /* Fill *o with the defaults listed above (eps_id = 1e-8, precision 0, symmetric 0). */

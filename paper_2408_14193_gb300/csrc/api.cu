@@ -591,6 +591,7 @@ void spalu_default_opts(spalu_opts* o) {
   o->gmres_tol = 1e-10;
   o->spars_ctas = 4;
   o->schur_tc = 1;
+  o->sketch_tc = 0;
 }
 
 const char* spalu_status_string(spalu_status s) {
@@ -688,7 +689,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   *out = nullptr;
   if (!(o->eps_id >= 0.0) || o->p_oversample < 0 || o->h0 < 1 || o->near_radius < -1 ||
       o->gmres_m < 1 || o->gmres_maxit < 0 || o->spars_ctas < 0 || o->spars_ctas > 32 ||
-      (o->schur_tc != 0 && o->schur_tc != 1))
+      (o->schur_tc != 0 && o->schur_tc != 1) || (o->sketch_tc != 0 && o->sketch_tc != 1))
     return SPALU_ERR_ARG;
   if (o->precision != 0 && o->precision != 1) return SPALU_ERR_ARG;
   if (leaf_init_tables() != cudaSuccess) return SPALU_ERR_CUDA;
@@ -813,6 +814,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
       d.eps = o->eps_id; d.symmetric = o->symmetric; d.p_over = o->p_oversample;
       d.near_radius = o->near_radius; d.h0 = o->h0; d.seed = o->seed;
       d.schur_tc = (o->schur_tc && f32) ? 1 : 0;
+      d.sketch_tc = (o->sketch_tc && f32) ? 1 : 0;
       d.L = L;
       d.pred_mode = PRED_OFF; d.pred_margin = 0.35; d.pred = nullptr;
       d.log10eps = o->eps_id > 0.0 ? std::log10(o->eps_id) : -16.0;

@@ -464,6 +464,33 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// ------------------------------------------------------------ tensor-core helpers (TF32)
+// mma.sync m16n8k8 with TF32 operands and FP32 accumulation.  TF32 keeps 10 mantissa bits, so
+// each operand is split into a high part tf32(x) and a low part tf32(x - hi) and three products
+// are accumulated (the two cross terms first, then hi*hi): the result matches an FP32 product
+// to about FP32 rounding (the lo*lo term, below 2^-22 relative, is dropped).
+// Fragment layouts of m16n8k8 (PTX ISA, tf32): g = lane / 4, q = lane % 4;
+//   A (16 x 8, row major): a0 (g, q), a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4);
+//   B (8 x 8, column major): b0 (q, g), b1 (q + 4, g);
+//   C (16 x 8): c0 (g, 2q), c1 (g, 2q + 1), c2 (g + 8, 2q), c3 (g + 8, 2q + 1).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+
 // ------------------------------------------------------------ far-row sketch
 // Yr[rr, c] = sum over far neighbour rows f of G[rr, f] B_F[f, c] for r0 <= rr < hh (unscaled),
 // neighbours taken in chunks of ch (near ones get zero weight).  Yr has leading dimension ldy.
@@ -499,6 +526,40 @@ __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const NbrTab& tb,
       }
     }
     __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+      if (d.sketch_tc) {
+        // Y_chunk (nr x e) += G_chunk (nr x rows) B_chunk (rows x e) on the tensor cores: the
+        // warps take 16 x 8 output tiles in turn, k in steps of 8 rows (zero past the end)
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int g = lane >> 2, q = lane & 3;
+        const int mt = (nr + 15) >> 4, nt = (e + 7) >> 3;
+        auto Ga = [&](int r, int k) { return (r < nr && k < rows) ? (float)Gc[r + (size_t)nr * k] : 0.f; };
+        auto Bb = [&](int k, int c) { return (k < rows && c < e) ? (float)Bc[k + (size_t)rows * c] : 0.f; };
+        for (int t = warp; t < mt * nt; t += nw) {
+          const int m0 = 16 * (t % mt), n0 = 8 * (t / mt);
+          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int k0 = 0; k0 < rows; k0 += 8) {
+            uint32_t ah[4], al[4], bh[2], bl[2];
+            split_tf32(Ga(m0 + g, k0 + q), ah[0], al[0]);
+            split_tf32(Ga(m0 + g + 8, k0 + q), ah[1], al[1]);
+            split_tf32(Ga(m0 + g, k0 + q + 4), ah[2], al[2]);
+            split_tf32(Ga(m0 + g + 8, k0 + q + 4), ah[3], al[3]);
+            split_tf32(Bb(k0 + q, n0 + g), bh[0], bl[0]);
+            split_tf32(Bb(k0 + q + 4, n0 + g), bh[1], bl[1]);
+            mma_tf32(acc, al, bh);
+            mma_tf32(acc, ah, bl);
+            mma_tf32(acc, ah, bh);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int rr = m0 + g + 8 * (u >> 1), c = n0 + 2 * q + (u & 1);
+            if (rr < nr && c < e) Yr[(r0 + rr) + (size_t)ldy * c] += (T)acc[u];
+          }
+        }
+        __syncthreads();
+        continue;
+      }
+    }
     for (int x = threadIdx.x; x < nr * e; x += blockDim.x) {
       int rr = x % nr, c = x / nr;
       T acc = T(0);
@@ -1612,33 +1673,9 @@ __global__ void __launch_bounds__(256) merge_schur_kernel(LevelDev d) {
     }
 }
 
-// The same update on the tensor cores (mixed path, schur_tc): mma.sync m16n8k8 with TF32
-// operands and FP32 accumulation.  TF32 keeps 10 mantissa bits, so each operand is split into
-// a high part tf32(x) and a low part tf32(x - hi) and three products are accumulated (the two
-// cross terms first, then hi*hi): the result matches an FP32 product to about FP32 rounding
-// (the lo*lo term, below 2^-22 relative, is dropped).  64 x 64 tile per CTA: warp w owns rows
-// 16 (w % 4) .. +16 and columns 32 (w / 4) .. +32 (four 16 x 8 accumulator tiles).
-// Fragment layouts of m16n8k8 (PTX ISA, tf32): g = lane / 4, q = lane % 4;
-//   A (16 x 8, row major): a0 (g, q), a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4);
-//   B (8 x 8, column major): b0 (q, g), b1 (q + 4, g);
-//   C (16 x 8): c0 (g, 2q), c1 (g, 2q + 1), c2 (g + 8, 2q), c3 (g + 8, 2q + 1).
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
+// The same update on the tensor cores (mixed path, schur_tc): 3xTF32 mma.sync (helpers above).
+// 64 x 64 tile per CTA: warp w owns rows 16 (w % 4) .. +16 and columns 32 (w / 4) .. +32
+// (four 16 x 8 accumulator tiles).
 __global__ void __launch_bounds__(256) merge_schur_tc_kernel(LevelDev d) {
   __shared__ float Zs[64][17];
   __shared__ float Ws[16][65];

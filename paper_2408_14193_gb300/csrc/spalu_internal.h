@@ -159,6 +159,7 @@ struct LevelDev {
   double eps;
   int symmetric, p_over, near_radius, h0;
   int schur_tc;     // separator Schur updates on the tensor cores (mixed path only)
+  int sketch_tc;    // sketch products G B_F on the tensor cores (mixed path only)
   unsigned long long seed;
   int* err;
   int* lstat;       // [LS_N] counters of this level (maxima of e, kp, |dP|; ID passes, ...)

@@ -52,6 +52,7 @@ class Options(ctypes.Structure):
         ("gmres_tol", ctypes.c_double),
         ("spars_ctas", ctypes.c_int),
         ("schur_tc", ctypes.c_int),
+        ("sketch_tc", ctypes.c_int),
     ]
 
     @classmethod

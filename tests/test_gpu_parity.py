@@ -265,11 +265,13 @@ def test_mixed_precision_refined(kind, n, eps):
     assert np.all(res <= 1e-10), res
 
 
-@pytest.mark.parametrize("kind,n", [("diffusion", 255), ("convdiff", 127)])
-def test_schur_updates_on_tensor_cores(kind, n):
-    """schur_tc = 1: the separators' Schur updates on the tensor cores (3xTF32 mma.sync) give
-    the FP32 CUDA-core result to FP32 rounding, the mixed bar against the FP64 oracle, and the
-    refinement to 1e-10."""
+@pytest.mark.parametrize("kind,n,which", [("diffusion", 255, "schur_tc"), ("convdiff", 127, "schur_tc"),
+                                          ("diffusion", 255, "sketch_tc"), ("convdiff", 127, "sketch_tc")])
+def test_contractions_on_tensor_cores(kind, n, which):
+    """schur_tc / sketch_tc = 1: the separators' Schur updates / the sketch products on the
+    tensor cores (3xTF32 mma.sync) give the FP32 CUDA-core result to FP32 rounding (through the
+    factorization: the skeleton choices may move), the mixed bar against the FP64 oracle, and
+    the refinement to 1e-10."""
     from paper_2408_14193_gb300 import Factor, NestedDissection
     P = W.make_problem(kind, n, seed=37, nrhs=2)
     rp, ci, va, B = _dev(P)
@@ -277,11 +279,13 @@ def test_schur_updates_on_tensor_cores(kind, n):
     sym = 1 if P.symmetric else 0
     out = []
     for tc in (0, 1):
-        f = Factor(nd, eps_id=1e-6, symmetric=sym, precision=1, schur_tc=tc)
+        kw = {"schur_tc": 0, "sketch_tc": 0}
+        kw[which] = tc
+        f = Factor(nd, eps_id=1e-6, symmetric=sym, precision=1, **kw)
         f.factor(rp, ci, va)
         out.append((f, f.solve(B).cpu().numpy().T))
     nrm, ent = rel_errors(out[1][1], out[0][1])
-    print(f"{kind} {n}: tensor-core Schur vs CUDA-core Schur: {nrm:.2e} (norm-wise), {ent:.2e} (entry-wise)")
+    print(f"{kind} {n} {which}: tensor cores vs CUDA cores: {nrm:.2e} (norm-wise), {ent:.2e} (entry-wise)")
     assert nrm <= 1e-3
     Xo = osolve(ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-6, symmetric=P.symmetric)), P.B)
     assert rel_errors(out[1][1], Xo)[0] <= 1e-2
