@@ -85,7 +85,7 @@ def test_eps0_equals_dense_solve(kind, n):
 # ------------------------------------------------------------------ FP64 parity with the oracle
 @pytest.mark.parametrize("kind,n,nrhs", [("laplace", 127, 1), ("diffusion", 127, 4),
                                          ("convdiff", 127, 2), ("diffusion", 255, 2),
-                                         ("helmholtz", 63, 2)])
+                                         ("helmholtz", 63, 2), ("aniso", 127, 2)])
 def test_fp64_matches_oracle(kind, n, nrhs):
     P = W.make_problem(kind, n, seed=22, nrhs=nrhs)
     X, f, _ = _gpu_solve(P, 1e-8)
@@ -235,7 +235,7 @@ def test_full_size_diffusion_1023_refined():
 # ------------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("kind,n,eps", [("diffusion", 127, 1e-6), ("diffusion", 255, 1e-6),
                                         ("convdiff", 127, 1e-6), ("laplace", 127, 1e-6),
-                                        ("helmholtz", 63, 1e-6)])
+                                        ("helmholtz", 63, 1e-6), ("aniso", 127, 1e-6)])
 def test_mixed_precision_refined(kind, n, eps):
     """Mixed mode (FP32 factors / solve, FP64 leaf LU, FP64 QR pivots and norms) refined by
     GMRES with an FP64 residual to 1e-10; the direct solve's error against the FP64 oracle

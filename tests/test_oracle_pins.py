@@ -179,7 +179,7 @@ def test_interp_decomp_rank_and_error():
 
 
 # ----------------------------------------------------------------------------- whole method
-@pytest.mark.parametrize("kind", ["laplace", "diffusion", "helmholtz", "convdiff"])
+@pytest.mark.parametrize("kind", ["laplace", "diffusion", "helmholtz", "convdiff", "aniso"])
 @pytest.mark.parametrize("n", [15, 31, 63])
 def test_eps0_equals_dense_solve(kind, n):
     """With eps = 0 nothing is truncated: the method is exact block LU (special case)."""
@@ -243,7 +243,7 @@ def test_manufactured_solution_convergence_order(kind, order):
     assert 0.75 * 2**order < ratio < 1.3 * 2**order, ratio
 
 
-@pytest.mark.parametrize("kind,near", [("laplace", 2), ("diffusion", 2), ("convdiff", 2), ("diffusion", -1),
+@pytest.mark.parametrize("kind,near", [("laplace", 2), ("diffusion", 2), ("convdiff", 2), ("aniso", 2), ("diffusion", -1),
                                        ("convdiff", -1)])
 def test_residual_tracks_eps(kind, near):
     """R_es ~ eps with about one digit lost (Sec. 6.2); bound it by 1e3 eps.  Also for pure

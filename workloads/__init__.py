@@ -18,6 +18,10 @@ The paper's experiments use FEM meshes and random fields that are not available
   * ``diffusion``   : -div(a grad u) = f, a = exp(GRF)       (symmetric positive definite)
   * ``helmholtz``   : -Lap_h u - k^2(x) u = f                (symmetric indefinite)
   * ``convdiff``    : -Lap_h u + beta . grad u = f, upwind   (non-symmetric)
+  * ``aniso``       : -d/dx(a1 du/dx) - d/dy(a2 du/dy) + beta . grad u = f, a1 = exp(GRF),
+                      a2 = 10 exp(GRF') (a diagonal anisotropic coefficient, a tenfold
+                      contrast between the directions), first-order upwind convection
+                      (non-symmetric; the 5-point analogue of Sec. 6.4's problem)
 """
 from __future__ import annotations
 
@@ -29,6 +33,7 @@ import numpy as np
 __all__ = [
     "CSR", "Problem", "laplace", "diffusion", "helmholtz", "convdiff", "grf",
     "rhs_normal", "rhs_point_sources", "make_problem", "grid_sizes_ok", "predictor_init_params",
+    "aniso",
 ]
 
 
@@ -138,6 +143,30 @@ def helmholtz(nx: int, ny: int, k2_interior: np.ndarray) -> CSR:
                      np.full(shape, -ax), np.full(shape, -ay), np.full(shape, -ay))
 
 
+def aniso(nx: int, ny: int, a1_nodes: np.ndarray, a2_nodes: np.ndarray, beta: tuple[float, float]) -> CSR:
+    """-d/dx(a1 du/dx) - d/dy(a2 du/dy) + beta . grad u with a1, a2 on the (ny+2) x (nx+2) node
+    lattice (x faces take the mean of a1 over their two nodes, y faces the mean of a2) and
+    first-order upwind convection (non-symmetric)."""
+    assert a1_nodes.shape == (ny + 2, nx + 2) and a2_nodes.shape == (ny + 2, nx + 2)
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    P1, P2 = a1_nodes[1:-1, 1:-1], a2_nodes[1:-1, 1:-1]
+    w = -0.5 * (P1 + a1_nodes[1:-1, :-2]) / hx**2
+    e = -0.5 * (P1 + a1_nodes[1:-1, 2:]) / hx**2
+    s_ = -0.5 * (P2 + a2_nodes[:-2, 1:-1]) / hy**2
+    n = -0.5 * (P2 + a2_nodes[2:, 1:-1]) / hy**2
+    d = -(w + e + s_ + n)
+    bx, by = beta
+    if bx > 0:
+        d, w = d + bx / hx, w - bx / hx
+    else:
+        d, e = d - bx / hx, e + bx / hx
+    if by > 0:
+        d, s_ = d + by / hy, s_ - by / hy
+    else:
+        d, n = d - by / hy, n + by / hy
+    return _assemble(nx, ny, d, w, e, s_, n)
+
+
 def convdiff(nx: int, ny: int, beta: tuple[float, float]) -> CSR:
     """-Lap_h u + beta . grad u with first-order upwind differences (non-symmetric)."""
     hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
@@ -237,6 +266,14 @@ def make_problem(kind: str, n: int, seed: int = 0, nrhs: int | None = None,
         A = convdiff(n, nyy, beta)
         B = rhs_normal(N, nrhs or 4, rng)
         return Problem(kind, n, nyy, A, B, False, {"beta": beta})
+    if kind == "aniso":
+        g1 = grf(n, nyy, 0.05, 1.0, rng)
+        g2 = grf(n, nyy, 0.05, 1.0, rng)
+        theta = rng.uniform(0, 2 * math.pi)
+        beta = (50 * math.cos(theta), 50 * math.sin(theta))
+        A = aniso(n, nyy, np.exp(g1), 10.0 * np.exp(g2), beta)
+        B = rhs_normal(N, nrhs or 4, rng)
+        return Problem(kind, n, nyy, A, B, False, {"beta": beta, "ratio": 10.0})
     raise ValueError(f"unknown problem kind {kind!r}")
 
 
