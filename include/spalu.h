@@ -116,6 +116,24 @@ spalu_status spalu_nd_export(spalu_nd_t nd, int* perm, int* iperm, int* levels, 
  * segment-id order, 15 each in increasing coordinate; nodes must hold 15 * nseg(L) ints. */
 spalu_status spalu_nd_export_segments(spalu_nd_t nd, int* nodes, int cap);
 
+/* Nested dissection of a general graph with vertex coordinates (Sec. 3.1, Alg. 1; the
+ * separator walk of Eq. (degreebias) with theta = 0.1), computed on the host: the ordering
+ * only (the factorization takes regular grids, spalu_nd_build_grid).  Host arrays: rowptr
+ * (n + 1) and colind, the symmetric sparsity pattern of the matrix (diagonal entries
+ * ignored); xy (2n doubles: x, y of vertex v at xy[2v], xy[2v + 1]); boundary (n flags for
+ * the domain's boundary vertices, may be NULL: then the vertices with fewer neighbours than
+ * the most connected one, the boundary of a grid).  A part with at most leaf_size >= 1
+ * vertices is a leaf.  Out: perm (n) = order I (leaves in depth-first order, each in
+ * increasing vertex id, then the separators by level L..1, each in walk order); level (n,
+ * may be NULL) = 0 for a leaf vertex, l for a vertex of a level-l separator.  The walk ends
+ * at D <= 0, at a dead end or at the first vertex on the part's boundary; D values within
+ * 1e-12 count as equal (first neighbour in adjacency order wins); the rest of a part goes to
+ * the separator's sides by connected component.  On a grid with leaf_size 225 the result is
+ * the order of spalu_nd_build_grid.  Errors: SPALU_ERR_ARG (sizes, indices out of range,
+ * non-finite coordinates). */
+spalu_status spalu_nd_order_csr(int n, const int* rowptr, const int* colind, const double* xy,
+                                const unsigned char* boundary, int leaf_size, int* perm, int* level);
+
 void spalu_nd_destroy(spalu_nd_t nd);
 
 /* Allocate a factor for the grid of nd with options o (all device memory is allocated here,

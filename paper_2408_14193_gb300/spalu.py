@@ -78,6 +78,7 @@ SIGNATURES = [
     ("spalu_nd_export", _I, [_P, _P, _P, _P, _I]),
     ("spalu_nd_export_segments", _I, [_P, _P, _I]),
     ("spalu_nd_destroy", None, [_P]),
+    ("spalu_nd_order_csr", _I, [_I, _P, _P, _P, _P, _I, _P, _P]),
     ("spalu_factor_create", _I, [_P, _P, _P]),
     ("spalu_factor_numeric", _I, [_P, _P, _P, _P, _I, _P]),
     ("spalu_factor_numeric_batch", _I, [_I, _P, _P, _P, _P, _P, _P]),
@@ -166,6 +167,26 @@ def _dev_ptr(t, dtype):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
         raise TypeError(f"expected a contiguous CUDA tensor of {dtype}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def nd_order_csr(rowptr, colind, xy, leaf_size: int, boundary=None):
+    """spalu_nd_order_csr: nested dissection of a general graph with coordinates (host
+    computation); returns (perm, level) as int32 arrays."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    n = rowptr.size - 1
+    if xy.shape != (n, 2):
+        raise ValueError("xy must have shape (n, 2)")
+    bd = None if boundary is None else np.ascontiguousarray(boundary, dtype=np.uint8)
+    if bd is not None and bd.size != n:
+        raise ValueError("boundary must have n entries")
+    perm = np.empty(n, dtype=np.int32)
+    level = np.empty(n, dtype=np.int32)
+    _check(load_library().spalu_nd_order_csr(n, rowptr.ctypes.data, colind.ctypes.data, xy.ctypes.data,
+                                             None if bd is None else bd.ctypes.data, int(leaf_size),
+                                             perm.ctypes.data, level.ctypes.data), "spalu_nd_order_csr")
+    return perm, level
 
 
 class NestedDissection:
