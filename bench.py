@@ -577,7 +577,9 @@ def run_ours(args):
     head = measure(1, args.mixed_eps, True, pred)  # mixed precision + learned ranks: the headline
     if args.only_mixed:                           # profiling runs: the headline path alone
         print(json.dumps({"ms_per_step": head["ms"] / args.steps, "relres_max": head["relres"],
-                          "gmres_iters": head["iters"]}), flush=True)
+                          "gmres_iters": head["iters"],
+                          "phase_ms_per_step": {k: round(v / args.steps, 4)
+                                                for k, v in sorted(head["st"]["timing_ms"].items())}}), flush=True)
         return 0
     base = measure(0, EPS_ID, False)              # plain FP64 GPU form
     base_loose = measure(0, args.mixed_eps, False)   # FP64 at the mixed path's eps_ID

@@ -771,11 +771,11 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     auto real = [&](size_t n) -> void* { return f32 ? (void*)cv.take<float>(n) : (void*)cv.take<double>(n); };
     lf.fp32 = f32 ? 1 : 0;
     lf.F = real((size_t)gl.nbox() * ldF[L] * ldF[L]);
-    lf.band = real((size_t)gl.nbox() * LDAB * NI);
-    lf.invd = real((size_t)gl.nbox() * NI);
+    lf.lrec = real((size_t)gl.nbox() * NI * 16);
+    lf.urec = real((size_t)gl.nbox() * NI * 16);
+    lf.uext = real((size_t)gl.nbox() * NI * 16);
     lf.ybuf = real((size_t)gl.nbox() * NI * 64);
     lf.G = f32 ? (void*)cv.take<float>((size_t)gl.nbox() * NI * 4 * LEAF) : nullptr;
-    lf.piv = cv.take<int>((size_t)gl.nbox() * NI);
     lf.kumax = cv.take<int>(4);
     lf.kur = cv.take<int>((size_t)gl.nbox());
     std::vector<void*> Fst(L + 1, nullptr);

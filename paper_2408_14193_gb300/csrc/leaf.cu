@@ -64,35 +64,39 @@ __device__ __forceinline__ double csr_entry(const int* rowptr, const int* colind
 __constant__ int c_qorder[NQ];
 __constant__ int c_qstart[2];   // first sweep step of the two solve warps of a leaf
 
-// Read-only view of one leaf's factors in precision T: RO = true reads global memory through
-// the read-only path (factors written by an earlier kernel); false reads plain (shared) memory.
-template <typename T, bool RO>
+// Read-only view of one leaf's factor records in precision T (written by an earlier kernel,
+// read through the read-only path).
+template <typename T>
 struct Band {
-  const T* __restrict__ ab;     // LDAB x NI
-  const int* __restrict__ piv;
-  const T* __restrict__ invd;
-  __device__ __forceinline__ T ld(const T* q) const { if constexpr (RO) return __ldg(q); else return *q; }
-  __device__ __forceinline__ T l(int r, int j) const { return ld(ab + (KV + r) + LDAB * j); }   // L(j+r, j)
-  __device__ __forceinline__ T u(int r, int j) const { return ld(ab + (KV - r) + LDAB * j); }   // U(j-r, j)
-  __device__ __forceinline__ int p(int j) const { if constexpr (RO) return __ldg(piv + j); else return piv[j]; }
-  __device__ __forceinline__ T dinv(int j) const { return ld(invd + j); }
+  const T* __restrict__ lr;     // NI x 16: L(j+1+r, j) at r, pivot offset at 15
+  const T* __restrict__ ur;     // NI x 16: 1/U_jj at 0, U(j-r, j) at r <= 15
+  const T* __restrict__ ux;     // NI x 16: U(j-r, j) at r - 16 for r >= 16
+  __device__ __forceinline__ T l(int r, int j) const { return __ldg(lr + 16 * j + r - 1); }   // L(j+r, j)
+  __device__ __forceinline__ T u(int r, int j) const {                                        // U(j-r, j)
+    return r < 16 ? __ldg(ur + 16 * j + r) : __ldg(ux + 16 * j + r - 16);
+  }
+  __device__ __forceinline__ int p(int j) const { return j + (int)__ldg(lr + 16 * j + 15); }
+  __device__ __forceinline__ T dinv(int j) const { return __ldg(ur + 16 * j); }
 };
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-}
-template <typename T>
-__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
-  if constexpr (sizeof(T) == 8) cp_async8(smem, gmem); else cp_async4(smem, gmem);
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+// L2 policy for data read once per pass (the factor records of the sweeps): first to be evicted,
+// so that the solve vector, written and read back within the pass, stays in L2
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void cp_async16_ef(void* smem, const void* gmem, unsigned long long pol) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "l"(pol));
+}
 
 // 16 consecutive values of shared memory (16-byte aligned) into registers, 128-bit loads
 template <typename T, int N>
@@ -114,71 +118,65 @@ __device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
 
 // Warp-staged variants of the two sweeps for the leaf Schur kernel: every lane of the warp
 // takes part (act = this lane owns a column), the warp starts its forward sweep at the same
-// column j0, and the band entries of the next 16 columns are copied into a double-buffered
-// per-warp stage with cp.async while the current 16 columns are swept.  Stage layout, 16
-// values per column: forward L(j+1..j+15, j) then the pivot slot; backward 1/U_jj then
-// U(j-1..j-15, j).  Upper bandwidth <= 15 (no interchange widened U).
+// column j0, and the records of the next 16 columns are copied into a double-buffered per-warp
+// stage with 16-byte cp.async while the current 16 columns are swept.  A stage holds 16
+// records of 16 values: the L records of columns jb..jb+15, or the U records of columns
+// NI-1-t0 down to NI-16-t0.  Upper bandwidth <= 15 (no interchange widened U).
 template <typename T>
 struct WarpStage {
-  T* v;      // 2 x 16 x 16
-  int* p;    // 2 x 16 pivots
+  T* v;      // 2 x 16 x 16, 16-byte aligned
 };
 
 template <typename T>
-__device__ __forceinline__ void stage_L(const WarpStage<T>& w, int buf, const T* ab, const int* piv, int jb, int lane) {
+__device__ __forceinline__ void stage_L(const WarpStage<T>& w, int buf, const T* lr, int jb, int lane) {
+  constexpr int EPC = 16 / sizeof(T), CPR = 16 / EPC;   // values per chunk, chunks per record
   T* v = w.v + buf * 256;
-  for (int x = lane; x < 256; x += 32) {
-    const int u = x >> 4, r = x & 15, j = jb + u;
-    if (j < NI) {
-      if (r < 15) cp_async_t(v + x, ab + (KV + 1 + r) + (size_t)LDAB * j);
-      else cp_async4(w.p + buf * 16 + u, piv + j);
-    }
+  for (int x = lane; x < 16 * CPR; x += 32) {
+    const int u = x / CPR, k = x % CPR, j = jb + u;
+    if (j < NI) cp_async16(v + u * 16 + k * EPC, lr + (size_t)16 * j + k * EPC);
   }
   cp_async_commit();
 }
 
 template <typename T>
-__device__ __forceinline__ void stage_U(const WarpStage<T>& w, int buf, const T* ab, const T* invd, int t0, int lane) {
+__device__ __forceinline__ void stage_U(const WarpStage<T>& w, int buf, const T* ur, int t0, int lane) {
+  constexpr int EPC = 16 / sizeof(T), CPR = 16 / EPC;
   T* v = w.v + buf * 256;
-  for (int x = lane; x < 256; x += 32) {
-    const int u = x >> 4, r = x & 15, j = NI - 1 - (t0 + u);
-    if (j >= 0) {
-      if (r == 0) cp_async_t(v + x, invd + j);
-      else cp_async_t(v + x, ab + (KV - r) + (size_t)LDAB * j);
-    }
+  for (int x = lane; x < 16 * CPR; x += 32) {
+    const int u = x / CPR, k = x % CPR, j = NI - 1 - (t0 + u);
+    if (j >= 0) cp_async16(v + u * 16 + k * EPC, ur + (size_t)16 * j + k * EPC);
   }
   cp_async_commit();
 }
 
 template <typename T, class In, class Out>
-__device__ __forceinline__ void sweep_L_staged(const WarpStage<T>& w, const T* ab, const int* piv, int j0, bool act,
-                                               In in, Out out) {
+__device__ __forceinline__ void sweep_L_staged(const WarpStage<T>& w, const T* lr, int j0, bool act, In in,
+                                               Out out) {
   const int lane = threadIdx.x & 31;
   T W[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) W[r] = (act && j0 + r < NI) ? in(j0 + r) : T(0);
   const int nb = (NI - j0 + 15) / 16;
-  stage_L(w, 0, ab, piv, j0, lane);
+  stage_L(w, 0, lr, j0, lane);
   for (int blk = 0; blk < nb; ++blk) {
-    if (blk + 1 < nb) { stage_L(w, (blk + 1) & 1, ab, piv, j0 + 16 * (blk + 1), lane); cp_async_wait<1>(); }
+    if (blk + 1 < nb) { stage_L(w, (blk + 1) & 1, lr, j0 + 16 * (blk + 1), lane); cp_async_wait<1>(); }
     else cp_async_wait<0>();
     __syncwarp();
     const T* S = w.v + (blk & 1) * 256;
-    const int* P = w.p + (blk & 1) * 16;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int j = j0 + 16 * blk + u;
       if (j < NI) {
-        const int dsw = P[u] - j;
+        T lv[16];
+        lds_vec(S + u * 16, lv);
+        const int dsw = (int)lv[15];   // the same for the whole warp (one leaf)
         T a = W[u], b = a;
-        if (__any_sync(0xffffffffu, dsw != 0)) {
+        if (dsw != 0) {
 #pragma unroll
           for (int r = 1; r < 16; ++r)
             if (r == dsw) { b = W[(u + r) & 15]; W[(u + r) & 15] = a; }
           W[u] = b;
         }
-        T lv[16];
-        lds_vec(S + u * 16, lv);
 #pragma unroll
         for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= lv[r - 1] * b;
         if (act) out(j, b);
@@ -190,16 +188,15 @@ __device__ __forceinline__ void sweep_L_staged(const WarpStage<T>& w, const T* a
 }
 
 template <typename T, class In, class Out>
-__device__ __forceinline__ void sweep_U_staged(const WarpStage<T>& w, const T* ab, const T* invd, bool act, In in,
-                                               Out out) {
+__device__ __forceinline__ void sweep_U_staged(const WarpStage<T>& w, const T* ur, bool act, In in, Out out) {
   const int lane = threadIdx.x & 31;
   T V[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) V[r] = act ? in(NI - 1 - r) : T(0);
   const int nb = (NI + 15) / 16;
-  stage_U(w, 0, ab, invd, 0, lane);
+  stage_U(w, 0, ur, 0, lane);
   for (int blk = 0; blk < nb; ++blk) {
-    if (blk + 1 < nb) { stage_U(w, (blk + 1) & 1, ab, invd, 16 * (blk + 1), lane); cp_async_wait<1>(); }
+    if (blk + 1 < nb) { stage_U(w, (blk + 1) & 1, ur, 16 * (blk + 1), lane); cp_async_wait<1>(); }
     else cp_async_wait<0>();
     __syncwarp();
     const T* S = w.v + (blk & 1) * 256;
@@ -299,9 +296,9 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
     const int D = g.D();
     for (int e = tid; e < D * D; e += LUT) F[(e % D) + (size_t)d.ldF * (e / D)] = T(0);
   }
-  T* bandg = reinterpret_cast<T*>(d.band) + (size_t)b * LDAB * NI;
-  T* invg = reinterpret_cast<T*>(d.invd) + (size_t)b * NI;
-  int* pivg = d.piv + (size_t)b * NI;
+  T* lrg = reinterpret_cast<T*>(d.lrec) + (size_t)b * NI * 16;
+  T* urg = reinterpret_cast<T*>(d.urec) + (size_t)b * NI * 16;
+  T* uxg = reinterpret_cast<T*>(d.uext) + (size_t)b * NI * 16;
   auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
   // band row r of column c of A_II from the CSR: A(i, c), i = c + r - KV (5-point stencil)
   auto assemble = [&](int r, int c) -> double {
@@ -316,7 +313,7 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
   for (int x = tid; x < LDAB * WS; x += LUT) W[x] = assemble(x % LDAB, x / LDAB);
   __syncthreads();
   int ju = 0, kureach = KU;
-  bool ok = true;
+  bool ok = true, swapped = false;
   const int ur = 1 + (tid & 15), ucg = tid >> 4;       // rank-1 update: row, column group
   for (int j = 0; j < NI; ++j) {
     const int km = min(KL, NI - 1 - j);
@@ -332,13 +329,14 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
       if (lane == 0) {
         sh[0] = bi;
         sh[1] = best == 0 ? 1 : 0;
-        pivg[j] = j + bi;
+        lrg[16 * j + 15] = (T)bi;      // pivot offset 0..15, exact in T
       }
     }
     __syncthreads();
     const int jp = sh[0];
     const bool zero = sh[1] != 0;
     if (zero) ok = false;
+    swapped |= jp != 0;
     ju = max(ju, min(j + KU + jp, NI - 1));
     kureach = max(kureach, ju - j);
     if (!zero && jp != 0)
@@ -351,7 +349,7 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
     if (tid < 32) {           // one reciprocal per pivot; multipliers scaled by it
       const double rp = zero ? 0.0 : 1.0 / w(j, j);
       if (!zero && tid < km) w(j + 1 + tid, j) *= rp;
-      if (tid == 0) invg[j] = (T)rp;
+      if (tid == 0) urg[16 * j] = (T)rp;
     }
     __syncthreads();
     if (!zero && ur <= km) {
@@ -359,9 +357,13 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
       for (int c = j + 1 + ucg; c <= ju; c += LUT / 16) w(j + ur, c) -= m * w(j, c);
     }
     __syncthreads();
-    if (tid < LDAB) {         // column j is final: store it, refill its slot with column j + WS
+    if (tid < LDAB) {         // column j is final: store its records, refill its slot with column j + WS
       double& slot = W[tid + LDAB * (j & (WS - 1))];
-      bandg[tid + LDAB * j] = (T)slot;
+      const T v = (T)slot;
+      if (tid > KV) lrg[16 * j + (tid - KV - 1)] = v;              // L(j+1+r, j), r = tid - KV - 1
+      else if (tid > KV - 16) { if (tid < KV) urg[16 * j + (KV - tid)] = v; }   // U(j-r, j), r = KV - tid <= 15
+      else uxg[16 * j + (KV - 16 - tid)] = v;                      // U(j-r, j), r = 16..30
+      if (tid == KV) uxg[16 * j + 15] = T(0);
       slot = assemble(tid, j + WS);
     }
   }
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
   if (tid == 0) {
     const int ku = min(kureach, KV);
     d.kur[b] = ku;
-    atomicMax(d.kumax, ku);
+    atomicMax(d.kumax, swapped && ku < 16 ? 16 : ku);   // <= 15: no leaf made an interchange
   }
 }
 
@@ -411,20 +413,18 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
   }
   __syncthreads();
   __shared__ __align__(16) T stv[FTH / 32][512];
-  __shared__ int stp[FTH / 32][32];
   if (live && d.kur[b] <= 15) {     // warp-staged sweeps (all lanes; lanes >= NQ only stage)
     const bool act = tid < NQ;
     const int q = act ? c_qorder[tid] : 0;
     const int j0 = c_qstart[tid >> 5];
-    const WarpStage<T> ws{stv[threadIdx.x >> 5], stp[threadIdx.x >> 5]};
-    const T* ab = reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI;
-    const int* pv = d.piv + (size_t)b * NI;
-    const T* iv = reinterpret_cast<const T*>(d.invd) + (size_t)b * NI;
+    const WarpStage<T> ws{stv[threadIdx.x >> 5]};
+    const T* lr = reinterpret_cast<const T*>(d.lrec) + (size_t)b * NI * 16;
+    const T* ur = reinterpret_cast<const T*>(d.urec) + (size_t)b * NI * 16;
     T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
     T* Gb = d.G ? reinterpret_cast<T*>(d.G) + (size_t)b * NI * NQ : nullptr;
     const int mq = act ? qm[sub][q] : -1;
     const T cq = (act && qex[sub][q]) ? (T)qc[sub][q] : T(0);
-    sweep_L_staged<T>(ws, ab, pv, j0, act, [&](int j) { return j == mq ? cq : T(0); },
+    sweep_L_staged<T>(ws, lr, j0, act, [&](int j) { return j == mq ? cq : T(0); },
                       [&](int j, T y) { yb[(size_t)j * QL + tid] = y; });
     const size_t ldF = d.ldF;
     auto yin = [&](int j) { return j < j0 ? T(0) : yb[(size_t)j * QL + tid]; };
@@ -436,12 +436,13 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
       if (lx == 0 && qex[sub][2 * LEAF + ly]) F[(2 * LEAF + ly) + ldF * q] = -(T)qa[sub][2 * LEAF + ly] * x;
       if (lx == LEAF - 1 && qex[sub][3 * LEAF + ly]) F[(3 * LEAF + ly) + ldF * q] = -(T)qa[sub][3 * LEAF + ly] * x;
     };
-    sweep_U_staged<T>(ws, ab, iv, act, yin, ring_out);
+    sweep_U_staged<T>(ws, ur, act, yin, ring_out);
   } else if (live && tid < NQ) {    // widened U: sweeps reading the band from global memory
     const int q = c_qorder[tid];
     const int j0 = c_qstart[tid >> 5];
-    Band<T, true> Bd{reinterpret_cast<const T*>(d.band) + (size_t)b * LDAB * NI, d.piv + (size_t)b * NI,
-                     reinterpret_cast<const T*>(d.invd) + (size_t)b * NI};
+    Band<T> Bd{reinterpret_cast<const T*>(d.lrec) + (size_t)b * NI * 16,
+               reinterpret_cast<const T*>(d.urec) + (size_t)b * NI * 16,
+               reinterpret_cast<const T*>(d.uext) + (size_t)b * NI * 16};
     T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)b * NI * QL;
     T* Gb = d.G ? reinterpret_cast<T*>(d.G) + (size_t)b * NI * NQ : nullptr;
     const int mq = qm[sub][q];
@@ -499,108 +500,122 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
 // ---------------------------------------------------------------- solve
 // One thread per (leaf, right-hand side).  Forward (leaf part of W~): X[I] <- A_II^{-1} X[I];
 // the side unknowns are updated afterwards by sep_update_fwd_kernel.  Backward (leaf part of
-// V~): X[I] <- X[I] - A_II^{-1} (A_Id x_d).  The intermediate L^{-1} P b goes through ybuf.
-// One thread per (leaf, right-hand side slot), LPB leaves x 16 slots per CTA.  The band
-// columns of the next block of steps (16 for L, KUW for U) are copied into a double-buffered
-// shared-memory stage with cp.async while the current block is swept, so the sequential
-// sweeps read their factor entries from shared memory without waiting on L2.
+// V~): X[I] <- X[I] - A_II^{-1} (A_Id x_d).
 constexpr int SLOT = 16;   // right-hand-side slots per leaf and launch
+constexpr int SWPB = 4;    // warps per CTA of the solve sweeps (two leaves per warp)
 
-// Band sweeps of LPB leaves x 16 right-hand sides per CTA, thread (leaf, rhs): forward
-// x_I = U^{-1} L^{-1} P b_I; backward x_I -= U^{-1} L^{-1} P (A_Id x_d).  The factors of the
-// next block of 16 (L) or KUW (U) steps are staged by cp.async while the current block runs,
-// a half-warp per band column; in the FP32 forward L sweep each thread also stages its own
-// right-hand-side rows one block ahead (the FP64 variant loads them directly: its shared
-// memory would otherwise cost resident CTAs).
-template <typename T, int KUW, int LPB, bool bwd>
-__global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) {
+// Per-warp shared-memory stage of leaf_solve_kernel (values of T, two buffers): for each of
+// the warp's two leaves 16 L records and, in the FP32 forward solve, the 16 right-hand-side
+// rows of the next block (16 values each); in the U phase KUW columns of KUW values (the U
+// record, and for KUW = 32 its extension) and, FP32 forward, the KUW rows y of the block after.
+// The pads put the two leaves of a warp on different banks.
+template <typename T, int KUW, bool bwd>
+struct SolveStage {
+  static constexpr int EPC = 16 / (int)sizeof(T);      // values per 16-byte chunk
+  static constexpr int CPR = SLOT / EPC;                // chunks per 16-value record
+  static constexpr int LSTP = SLOT * SLOT + EPC;
+  static constexpr int USTP = KUW * KUW + EPC;
+  static constexpr int XSTP = SLOT * SLOT + 16;
+  static constexpr int YSTP = KUW * SLOT + 16;
+  static constexpr bool XPF = !bwd && sizeof(T) == 4;
+  static constexpr int bufL = 2 * (LSTP + (XPF ? XSTP : 0));
+  static constexpr int bufU = 2 * (USTP + (XPF ? YSTP : 0));
+  static constexpr int bufsz = bufL > bufU ? bufL : bufU;   // one buffer of one warp
+  static constexpr size_t bytes = (size_t)SWPB * 2 * bufsz * sizeof(T);
+};
+
+// Band sweeps, one warp per two leaves x 16 right-hand sides, thread (leaf, rhs): forward
+// x_I = U^{-1} L^{-1} P b_I; backward x_I -= U^{-1} L^{-1} P (A_Id x_d).
+// - Warp-synchronous: a warp stages the factor records of its own two leaves for the next
+//   block of 16 (L) or KUW (U) steps with 16-byte cp.async (L2 evict-first: read once per
+//   pass) into its double-buffered stage while it sweeps the current block; no CTA barrier.
+// - Forward: y = L^{-1} P b overwrites b in the solve vector (row j is written at step j,
+//   after the last read of b_j) and the U sweep reads it back from there, so the intermediate
+//   costs no scratch traffic and stays in L2 between the sweeps.  Backward: x_I is needed
+//   until the last step, so y goes through the sweep buffer.
+// - FP32: the solve vector is chunked (a node's 16 right-hand sides are one 64-byte run); the
+//   right-hand-side rows of the next L block and the y rows of the next U block are staged
+//   with the records, so no global load is outstanding at a warp barrier.
+// - KUW = 16 is launched only when no leaf made an interchange (the step has no swap).
+// All lanes run the sweep arithmetic (lanes without a right-hand side or leaf on values that
+// are never stored), so the warp votes and barriers are full-warp.
+template <typename T, int KUW, bool bwd>
+__global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) {
   pdl_trigger();
-  extern __shared__ double lsm[];
-  constexpr int NT = LPB * SLOT;
-  constexpr int LST = SLOT * SLOT;                    // L stage per leaf: 16 columns x 16 (L(j+r, j) at r - 1)
-  constexpr int UST = KUW * KUW;                      // U stage per leaf: KUW columns x KUW (r = 0 -> 1/U_jj)
+  extern __shared__ float4 lsm4[];
+  using St = SolveStage<T, KUW, bwd>;
+  constexpr int EPC = St::EPC, CPR = St::CPR;
+  constexpr int LSTP = St::LSTP, USTP = St::USTP, XSTP = St::XSTP, YSTP = St::YSTP, bufsz = St::bufsz;
   constexpr int RMAX = KUW - 1 < KV ? KUW - 1 : KV;
-  T* stg = reinterpret_cast<T*>(lsm);                 // 2 buffers
+  constexpr bool XPF = St::XPF;
+  constexpr bool CHK = sizeof(T) == 4;
+  constexpr bool PIV = KUW > 16;
+  constexpr int RPC = SLOT * CPR;                     // chunks of one leaf's 16 records
+  constexpr int CPC = (KUW / SLOT) * CPR;             // chunks of one U column
+  static_assert(RPC % 32 == 0 && (KUW * CPC) % 32 == 0, "a leaf's stage is a whole number of warp copies");
+  const int lane = threadIdx.x & 31;
+  const int sub = lane >> 4, c = lane & 15;
   const int nbox = d.g.nbox();
-  const int sub = threadIdx.x / SLOT, c = threadIdx.x % SLOT;
-  const int b0 = blockIdx.x * LPB;
+  const int b0 = (blockIdx.x * SWPB + (threadIdx.x >> 5)) * 2;   // the warp's first leaf
+  if (b0 >= nbox) return;                             // whole warp: no leaf
   const int b = b0 + sub;
-  const bool active = b < nbox && c < nrhs;
+  const bool act = b < nbox && c < nrhs;
+  T* stg = reinterpret_cast<T*>(lsm4) + (size_t)(threadIdx.x >> 5) * 2 * bufsz;
+  const T* lrec = reinterpret_cast<const T*>(d.lrec);
+  const T* urec = reinterpret_cast<const T*>(d.urec);
+  const T* uext = reinterpret_cast<const T*>(d.uext);
+  const unsigned long long pol = evict_first_policy();
+  const int bx = d.g.bx, nx = d.nx;
   const int bb = b < nbox ? b : nbox - 1;
-  const T* gband = reinterpret_cast<const T*>(d.band);
-  const T* ginv = reinterpret_cast<const T*>(d.invd);
-  constexpr size_t bufL = (size_t)LPB * (LST + SLOT); // values + pivots (pivots stored as T slots)
-  constexpr size_t bufU = (size_t)LPB * UST;
-  constexpr size_t bufsz = bufL > bufU ? bufL : bufU;
-  const int I = bb % d.g.bx, J = bb / d.g.bx;
-  const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
-  const int nx = d.nx;
-  T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)bb * NI * QL;
+  const int bl1 = b0 + 1 < nbox ? b0 + 1 : b0;       // the warp's second leaf (clamped)
+  const int x0 = (bb % bx) * (LEAF + 1), y0 = (bb / bx) * (LEAF + 1);
+  const int o0 = x0 + nx * y0;                        // grid node of this lane's leaf interior (0, 0)
+  const int og[2] = {(b0 % bx) * (LEAF + 1) + nx * ((b0 / bx) * (LEAF + 1)),
+                     (bl1 % bx) * (LEAF + 1) + nx * ((bl1 / bx) * (LEAF + 1))};
+  auto node_of = [&](int j) { return o0 + j % LEAF + nx * (j / LEAF); };
+  T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)bb * NI * QL;   // backward only
   T* Xc = X + (size_t)c * lay.cs;
   const long long rs = lay.rs;
-  auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
-  auto xat = [&](int node) -> T& { return Xc[(size_t)(node * rs)]; };
-  constexpr bool XPF = !bwd && sizeof(T) == 4;       // stage the right-hand-side rows
-  T* xst = stg + 2 * bufsz + (size_t)threadIdx.x * 2 * SLOT;   // own rows, 2 x 16
+  auto xat = [&](int node) -> T& {
+    if constexpr (CHK) return X[(size_t)node * SLOT + c];
+    else return Xc[(size_t)(node * rs)];
+  };
+  // 16 values of row r of the warp's leaf s (FP32 chunked vector), chunk k of 4
+  auto row_chunk = [&](T* dst, int s, int r, int k) {
+    cp_async16(dst, X + (size_t)(og[s] + r % LEAF + nx * (r / LEAF)) * SLOT + 4 * k);
+  };
 
-  // ---- L sweep: y = L^{-1} P x, blocks of 16 steps.  The band part of a block's stage
-  //      (factor data) and its right-hand-side part are issued separately so that the first
-  //      block's band can be requested before the wait on the preceding kernel.
-  auto issue_L_band = [&](int blk, int buf) {
+  // ---- L sweep: y = L^{-1} P x, blocks of 16 steps.  Stage of block blk: its records and
+  //      (FP32 forward) right-hand-side rows blk * 16 + 16 .. + 31, the refills of its steps.
+  auto issue_L_rec = [&](int blk, int buf) {
     T* S = stg + (size_t)buf * bufsz;
     const int j0 = blk * SLOT;
-    {
-      // half-warps over band columns (col = leaf * 16 + u), lane r < 15 copies L(j+1+r, j):
-      // contiguous in the band, so each half-warp reads one run of 15 values
-      const int r = threadIdx.x & 15;
-#pragma unroll 4
-      for (int col = threadIdx.x >> 4; col < LPB * SLOT; col += NT / 16) {
-        const int sl = col / SLOT, u = col % SLOT;
-        const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
-        if (j0 + u < NI) {
-          if (r < SLOT - 1)
-            cp_async_t(S + (size_t)sl * LST + u * SLOT + r, gband + (size_t)lb * LDAB * NI + (KV + 1 + r) + (size_t)LDAB * (j0 + u));
-          else
-            cp_async4(reinterpret_cast<int*>(S + (size_t)LPB * LST) + col, d.piv + (size_t)lb * NI + j0 + u);
-        }
-      }
+    const int nch = (NI - j0 < SLOT ? NI - j0 : SLOT) * CPR;
+#pragma unroll
+    for (int i = 0; i < 2 * RPC / 32; ++i) {
+      const int s = i / (RPC / 32), k = lane + 32 * (i % (RPC / 32));
+      if (k < nch) cp_async16_ef(S + s * LSTP + k * EPC, lrec + ((size_t)(s ? bl1 : b0) * NI + j0) * SLOT + k * EPC, pol);
     }
   };
   auto issue_L_x = [&](int blk, int buf) {
-    const int j0 = blk * SLOT;
-    if (XPF && active) {                              // rows j0 + 16 .. j0 + 31 of this thread's rhs
-      T* xs = xst + (buf & 1) * SLOT;
-      int j = j0 + SLOT;
-      int lx = j % LEAF, node = node_of(j);
+    if constexpr (XPF) {
+      T* S = stg + (size_t)buf * bufsz + 2 * LSTP;
 #pragma unroll
-      for (int u = 0; u < SLOT; ++u, ++j) {
-        if (j < NI) cp_async_t(xs + u, &xat(node));
-        if (++lx == LEAF) { lx = 0; node += nx - (LEAF - 1); } else ++node;
+      for (int i = 0; i < 2 * SLOT * 4 / 32; ++i) {
+        const int s = i / (SLOT * 4 / 32), u = (lane + 32 * (i % (SLOT * 4 / 32))) / 4, k = lane % 4;
+        const int r = blk * SLOT + SLOT + u;
+        if (r < NI) row_chunk(S + s * XSTP + u * SLOT + 4 * k, s, r, k);
       }
     }
     cp_async_commit();
   };
-  auto issue_L = [&](int blk, int buf) {
-    issue_L_band(blk, buf);
-    issue_L_x(blk, buf);
-  };
   const int nbl = (NI + SLOT - 1) / SLOT;
-  issue_L_band(0, 0);
+  issue_L_rec(0, 0);
   pdl_wait();                             // the solve vector is written by the preceding kernel
-  T W[16];
-  if (active) {
-    if (!bwd) {
-#pragma unroll
-      for (int r = 0; r < 16; ++r) W[r] = xat(node_of(r));
-    } else {
-#pragma unroll
-      for (int r = 0; r < 16; ++r) W[r] = T(0);
-    }
-  }
   auto coupling = [&](int j) {            // (A_Id x_d)_j for the backward sweep
     T v = T(0);
     const int lx = j % LEAF, ly = j / LEAF;
-    if (lx == 0 || ly == 0 || lx == LEAF - 1 || ly == LEAF - 1) {
+    if (act && (lx == 0 || ly == 0 || lx == LEAF - 1 || ly == LEAF - 1)) {
       const int node = node_of(j);
       for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
         const int cc = d.colind[p];
@@ -610,99 +625,129 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
     }
     return v;
   };
-  if (active && bwd) {
+  T W[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) W[r] = coupling(r);
-  }
+  for (int r = 0; r < 16; ++r) W[r] = bwd ? coupling(r) : (act ? xat(node_of(r)) : T(0));
   issue_L_x(0, 0);
   for (int blk = 0; blk < nbl; ++blk) {
-    if (blk + 1 < nbl) { issue_L(blk + 1, (blk + 1) & 1); cp_async_wait<1>(); }
-    else cp_async_wait<0>();
-    __syncthreads();
-    const T* S = stg + (size_t)(blk & 1) * bufsz + (size_t)sub * LST;
-    const int* P = reinterpret_cast<const int*>(stg + (size_t)(blk & 1) * bufsz + (size_t)LPB * LST) + sub * SLOT;
-    const T* xs = xst + (blk & 1) * SLOT;
-    if (active) {
+    if (blk + 1 < nbl) {
+      issue_L_rec(blk + 1, (blk + 1) & 1);
+      issue_L_x(blk + 1, (blk + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const T* S = stg + (size_t)(blk & 1) * bufsz + sub * LSTP;
+    const T* xs = stg + (size_t)(blk & 1) * bufsz + 2 * LSTP + sub * XSTP + c;
+    int lx = (blk * SLOT) % LEAF, node = node_of(blk * SLOT);   // grid node of step j
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int j = blk * SLOT + u;
-        if (j < NI) {
-          const int dsw = P[u] - j;
-          T a = W[u], bv = a;
-          if (__any_sync(__activemask(), dsw != 0)) {
+    for (int u = 0; u < 16; ++u) {
+      const int j = blk * SLOT + u;
+      if (j < NI) {
+        T lv[16];
+        lds_vec(S + u * SLOT, lv);
+        T bv = W[u];
+        if constexpr (PIV) {
+          const int dsw = (int)lv[15];     // 0..15: the interchange stays in the window
+          if (__any_sync(0xffffffffu, dsw != 0)) {
+            const T a = bv;
 #pragma unroll
             for (int r = 1; r < 16; ++r)
               if (r == dsw) { bv = W[(u + r) & 15]; W[(u + r) & 15] = a; }
-            W[u] = bv;
           }
-          T lv[16];
-          lds_vec(S + u * SLOT, lv);
-#pragma unroll
-          for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= lv[r - 1] * bv;
-          yb[(size_t)j * QL + c] = bv;
-          T nv = T(0);
-          if (j + 16 < NI) {
-            if constexpr (XPF) nv = xs[u];
-            else if constexpr (!bwd) nv = xat(node_of(j + 16));
-            else nv = coupling(j + 16);
-          }
-          W[u] = nv;
         }
+#pragma unroll
+        for (int r = 1; r < 16; ++r) W[(u + r) & 15] -= lv[r - 1] * bv;
+        if (act) {
+          if constexpr (!bwd) xat(node) = bv;    // y_j over b_j
+          else yb[(size_t)j * SLOT + c] = bv;
+        }
+        T nv = T(0);
+        if (j + 16 < NI) {
+          if constexpr (XPF) nv = xs[u * SLOT];
+          else if constexpr (!bwd) nv = act ? xat(node_of(j + 16)) : T(0);
+          else nv = coupling(j + 16);
+        }
+        W[u] = nv;
+        const bool wrap = lx == LEAF - 1;
+        lx = wrap ? 0 : lx + 1;
+        node += wrap ? nx - (LEAF - 1) : 1;
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 
-  // ---- U sweep: x = U^{-1} y, blocks of KUW steps from the bottom
+  // ---- U sweep: x = U^{-1} y, blocks of KUW steps from the bottom.  Stage of block blk: its
+  //      U columns and (FP32 forward) the y rows of block blk + 1, the refills of its steps.
   auto issue_U = [&](int blk, int buf) {
     T* S = stg + (size_t)buf * bufsz;
     const int t0 = blk * KUW;
-    // half-warps over band columns; lane r copies 1/U_jj (r = 0) or U(j-r, j) (r <= RMAX)
-    const int r0 = threadIdx.x & 15;
-#pragma unroll 4
-    for (int cr = threadIdx.x >> 4; cr < LPB * KUW * (KUW / 16); cr += NT / 16) {
-      const int col = cr / (KUW / 16), r = r0 + 16 * (cr % (KUW / 16));
-      const int sl = col / KUW, u = col % KUW;
-      const int lb = b0 + sl < nbox ? b0 + sl : nbox - 1;
+#pragma unroll
+    for (int i = 0; i < 2 * KUW * CPC / 32; ++i) {
+      const int s = i / (KUW * CPC / 32), rem = lane + 32 * (i % (KUW * CPC / 32)), u = rem / CPC, k = rem % CPC;
       const int j = NI - 1 - (t0 + u);
-      if (j >= 0 && r <= RMAX) {
-        T* dst = S + (size_t)sl * UST + u * KUW + r;
-        if (r == 0) cp_async_t(dst, ginv + (size_t)lb * NI + j);
-        else cp_async_t(dst, gband + (size_t)lb * LDAB * NI + (KV - r) + (size_t)LDAB * j);
+      if (j >= 0) {
+        const size_t rec = ((size_t)(s ? bl1 : b0) * NI + j) * SLOT;
+        const T* src = k < CPR ? urec + rec + k * EPC : uext + rec + (k - CPR) * EPC;
+        cp_async16_ef(S + s * USTP + u * KUW + k * EPC, src, pol);
+      }
+    }
+    if constexpr (XPF) {
+      T* Y = S + 2 * USTP;
+#pragma unroll
+      for (int i = 0; i < 2 * KUW * 4 / 32; ++i) {
+        const int s = i / (KUW * 4 / 32), u = (lane + 32 * (i % (KUW * 4 / 32))) / 4, k = lane % 4;
+        const int r = NI - 1 - (t0 + KUW + u);
+        if (r >= 0) row_chunk(Y + s * YSTP + u * SLOT + 4 * k, s, r, k);
       }
     }
     cp_async_commit();
   };
+  // (FP64 forward) row j - KUW from row j: KUW = 15 q + m, so q leaf rows down and m nodes
+  // left, one more row down (and LEAF nodes right) when fewer than m nodes are left of j
+  constexpr int QD = KUW / LEAF, MD = KUW % LEAF;
   const int nbu = (NI + KUW - 1) / KUW;
   T V[KUW];
-  if (active) {
 #pragma unroll
-    for (int r = 0; r < KUW; ++r) V[r] = (NI - 1 - r >= 0) ? yb[(size_t)(NI - 1 - r) * QL + c] : T(0);
-  }
+  for (int r = 0; r < KUW; ++r)
+    V[r] = (act && NI - 1 - r >= 0) ? (bwd ? yb[(size_t)(NI - 1 - r) * SLOT + c] : xat(node_of(NI - 1 - r))) : T(0);
   issue_U(0, 0);
   for (int blk = 0; blk < nbu; ++blk) {
     if (blk + 1 < nbu) { issue_U(blk + 1, (blk + 1) & 1); cp_async_wait<1>(); }
     else cp_async_wait<0>();
-    __syncthreads();
-    const T* S = stg + (size_t)(blk & 1) * bufsz + (size_t)sub * UST;
-    if (active) {
+    __syncwarp();
+    const T* S = stg + (size_t)(blk & 1) * bufsz + sub * USTP;
+    const T* ys = stg + (size_t)(blk & 1) * bufsz + 2 * USTP + sub * YSTP + c;
+    const int jt = NI - 1 - blk * KUW;
+    int lx = jt % LEAF, node = node_of(jt);      // grid node of step j (descending)
 #pragma unroll
-      for (int u = 0; u < KUW; ++u) {
-        const int t = blk * KUW + u;
-        if (t < NI) {
-          const int j = NI - 1 - t;
-          T uv[KUW];
-          lds_vec(S + u * KUW, uv);
-          const T x = V[u] * uv[0];
-          if (!bwd) xat(node_of(j)) = x;
-          else xat(node_of(j)) -= x;
-#pragma unroll
-          for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= uv[r] * x;
-          V[u] = (j - KUW >= 0) ? yb[(size_t)(j - KUW) * QL + c] : T(0);
+    for (int u = 0; u < KUW; ++u) {
+      const int t = blk * KUW + u;
+      if (t < NI) {
+        const int j = NI - 1 - t;
+        T uv[KUW];
+        lds_vec(S + u * KUW, uv);
+        const T x = V[u] * uv[0];
+        if (act) {
+          if (!bwd) xat(node) = x;
+          else xat(node) -= x;
         }
+#pragma unroll
+        for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= uv[r] * x;
+        T nv = T(0);
+        if (j - KUW >= 0) {
+          if constexpr (XPF) nv = ys[u * SLOT];
+          else if constexpr (bwd) nv = act ? yb[(size_t)(j - KUW) * SLOT + c] : T(0);
+          else nv = act ? xat(node - QD * nx - MD + (lx < MD ? LEAF - nx : 0)) : T(0);
+        }
+        V[u] = nv;
+        const bool wrap = lx == 0;
+        lx = wrap ? LEAF - 1 : lx - 1;
+        node -= wrap ? nx - (LEAF - 1) : 1;
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -712,11 +757,6 @@ __global__ void __launch_bounds__(LPB * SLOT) leaf_solve_kernel(LeafDev d, T* X,
 // all right-hand sides of the chunk (up to 16) and updates the interior unknown j.
 constexpr int GTH = 256;
 constexpr int GRC = 16;                          // right-hand sides per launch
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-
 __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X, int nrhs, VecLayout lay) {
   pdl_trigger();
   extern __shared__ float4 gsm4[];
@@ -852,22 +892,23 @@ void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
   else leaf_schur_kernel<double><<<(nbox + LPC - 1) / LPC, FTH, 0, s>>>(d);
 }
 
-template <typename T, int KUW, int LPB>
+template <typename T, int KUW>
 static void leaf_solve_go(const LeafDev& d, T* X, int nrhs, VecLayout lay, int bwd, cudaStream_t s) {
-  const size_t bufL = (size_t)LPB * (SLOT * SLOT + SLOT), bufU = (size_t)LPB * KUW * KUW;
-  const bool xpf = !bwd && sizeof(T) == 4;
-  const size_t smem = sizeof(T) * (2 * (bufL > bufU ? bufL : bufU) + (xpf ? (size_t)LPB * SLOT * 2 * SLOT : 0));
-  const int grid = (d.g.nbox() + LPB - 1) / LPB;
+  const int grid = (d.g.nbox() + 2 * SWPB - 1) / (2 * SWPB);
   note_launch();
   if (!bwd) {
-    cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    launch_pdl(leaf_solve_kernel<T, KUW, LPB, false>, dim3(grid), dim3(LPB * SLOT), smem, s, d, X, nrhs, lay);
+    const int smem = (int)SolveStage<T, KUW, false>::bytes;
+    cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    launch_pdl(leaf_solve_kernel<T, KUW, false>, dim3(grid), dim3(SWPB * 32), smem, s, d, X, nrhs, lay);
   } else {
-    cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, LPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    launch_pdl(leaf_solve_kernel<T, KUW, LPB, true>, dim3(grid), dim3(LPB * SLOT), smem, s, d, X, nrhs, lay);
+    const int smem = (int)SolveStage<T, KUW, true>::bytes;
+    cudaFuncSetAttribute(leaf_solve_kernel<T, KUW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    launch_pdl(leaf_solve_kernel<T, KUW, true>, dim3(grid), dim3(SWPB * 32), smem, s, d, X, nrhs, lay);
   }
 }
 
+// The FP32 solve vector is always chunked (VecLayout{16, 1, 16 N}: a node's 16 right-hand
+// sides contiguous, every chunk 64-byte aligned); the FP32 forward sweep stages its rows as such.
 void launch_leaf_solve(const LeafDev& d, void* Xv, int nrhs, VecLayout lay, int bwd, int kumax, cudaStream_t s) {
   if (bwd && d.fp32 && d.G) {
     const int smem = (int)(sizeof(float) * (NI * NQ + NQ * GRC));
@@ -884,12 +925,12 @@ void launch_leaf_solve(const LeafDev& d, void* Xv, int nrhs, VecLayout lay, int 
     const int nc = nrhs - c0 < SLOT ? nrhs - c0 : SLOT;
     if (d.fp32) {
       float* Xc = static_cast<float*>(Xv) + (size_t)(c0 / SLOT) * lay.chunk;
-      if (kumax <= 15) leaf_solve_go<float, 16, 8>(d, Xc, nc, lay, bwd, s);
-      else leaf_solve_go<float, 32, 8>(d, Xc, nc, lay, bwd, s);
+      if (kumax <= 15) leaf_solve_go<float, 16>(d, Xc, nc, lay, bwd, s);
+      else leaf_solve_go<float, 32>(d, Xc, nc, lay, bwd, s);
     } else {
       double* Xc = static_cast<double*>(Xv) + (size_t)(c0 / SLOT) * lay.chunk;
-      if (kumax <= 15) leaf_solve_go<double, 16, 4>(d, Xc, nc, lay, bwd, s);
-      else leaf_solve_go<double, 32, 4>(d, Xc, nc, lay, bwd, s);
+      if (kumax <= 15) leaf_solve_go<double, 16>(d, Xc, nc, lay, bwd, s);
+      else leaf_solve_go<double, 32>(d, Xc, nc, lay, bwd, s);
     }
   }
 }

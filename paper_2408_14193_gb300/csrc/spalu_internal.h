@@ -200,13 +200,16 @@ struct LeafDev {
   Geo g;            // depth-L tiling (leaf boxes, 15 x 15)
   int ldF;          // = g.D()
   void* F;          // depth-L frontals (FP64 or FP32)
-  void* band;       // [nbox * LDAB * 225] band LU of the leaf interiors (FP64 or FP32)
-  void* invd;       // [nbox * 225] reciprocal pivots of U
+  // Band LU of the leaf interiors (FP64 or FP32), one 16-value record per column j of a leaf
+  // (leaf b's records start at b * 225 * 16):
+  void* lrec;       //   L(j+1+r, j) at slot r = 0..14, slot 15 = pivot row - j (0..15, exact)
+  void* urec;       //   1/U_jj at slot 0, U(j-r, j) at slot r = 1..15
+  void* uext;       //   U(j-r, j) at slot r - 16 for r = 16..30 (fill of the interchanges), slot 15 = 0
   void* ybuf;       // [nbox * 225 * 64] intermediate vectors of the band sweeps
   void* G;          // [nbox * 225 * 60] FP32 A_II^{-1} A_Id per leaf (row-major, column = side
                     // unknown); set in the mixed path only, where it replaces the backward sweeps
-  int* piv;         // [nbox * 225]
-  int* kumax;       // largest upper bandwidth of U produced by the interchanges
+  int* kumax;       // largest upper bandwidth of U produced by the interchanges, at least 16
+                    // when any leaf made one (<= 15: the sweeps need no interchange step)
   int* kur;         // [nbox] upper bandwidth of each leaf's U
   const int* rowptr;
   const int* colind;
