@@ -92,6 +92,13 @@ typedef struct {
                                  mma.sync); 0 (default) = FP32 FMA on the CUDA cores (the
                                  random entries of G, not the product, dominate the sketch's
                                  cost).  Ignored in FP64 mode. */
+  int leaf_bwd;               /* mixed precision only, performance only: the backward leaf
+                                 step x_I -= A_II^{-1} A_Id x_d (Eq. (WV)) as 0 = one product
+                                 with G = A_II^{-1} A_Id, stored by the factorization (225 x 60
+                                 FP32 per leaf, independent rows); 1 = a band sweep pair per
+                                 leaf on the stored factors (no G: less memory and traffic, but
+                                 225 dependent steps); -1 (default) = G on grids of fewer than
+                                 2048 leaves, the sweeps otherwise.  FP64 mode always sweeps. */
 } spalu_opts;
 
 /* Fill *o with the defaults listed above (eps_id = 1e-8, precision 0, symmetric 0). */
@@ -169,11 +176,13 @@ spalu_status spalu_factor_numeric_batch(int n, const spalu_factor_t* f, const in
                                         const int* nnz, spalu_stream_t const* streams);
 
 /* Autotuning of the level solves (scheduling, not in the paper): for every level, time the
- * segment and separator solve kernels with 2-warp and 8-warp CTAs (the four combinations, on
- * a zero vector of nrhs columns, 1 <= nrhs <= 16, CUDA events on stream) and keep the fastest
- * for later solves of this handle, also across re-factorizations.  Requires a factored
- * handle (SPALU_ERR_STATE otherwise); synchronises the stream.  Results do not depend on the
- * choice beyond the order of the atomic separator updates. */
+ * segment and separator solve kernels with 2-warp and 8-warp CTAs and with the right-hand
+ * sides split into 1, 2, 4 or 8 groups of one CTA each (more CTAs on levels with few
+ * segments or separators) -- every combination, on a zero vector of nrhs columns,
+ * 1 <= nrhs <= 16, CUDA events on stream -- and keep the fastest for later solves of this
+ * handle, also across re-factorizations.  Requires a factored handle (SPALU_ERR_STATE
+ * otherwise); synchronises the stream.  Results do not depend on the choice beyond the order
+ * of the atomic separator updates. */
 spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream);
 
 /* Autotuning of the sparsification's occupancy (scheduling, not in the paper): re-factor the

@@ -149,7 +149,8 @@ struct spalu_factor_s {
   float* xf = nullptr;       // FP32 solve vector of the mixed path, N x xf_cols
   int xf_cols = 0;
   int* hpin = nullptr;       // page-locked readback after a factorization: err, kumax, lstat
-  std::vector<int> tuned_nt; // [2 * (L + 1)] solve CTA widths chosen by spalu_tune_solve (0: none)
+  std::vector<int> tuned_nt; // [4 * (L + 1)] per level: segment / separator solve CTA widths and
+                             // right-hand-side groups chosen by spalu_tune_solve (0: none)
   cudaStream_t up = nullptr; // second stream of spalu_factor_solve_host (right-hand-side upload)
   cudaEvent_t up_go = nullptr, up_done = nullptr;
   double* hB = nullptr;      // device B and X of spalu_factor_solve_host, hcap doubles each
@@ -592,6 +593,7 @@ void spalu_default_opts(spalu_opts* o) {
   o->spars_ctas = 4;
   o->schur_tc = 1;
   o->sketch_tc = 0;
+  o->leaf_bwd = -1;
 }
 
 const char* spalu_status_string(spalu_status s) {
@@ -689,7 +691,8 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
   *out = nullptr;
   if (!(o->eps_id >= 0.0) || o->p_oversample < 0 || o->h0 < 1 || o->near_radius < -1 ||
       o->gmres_m < 1 || o->gmres_maxit < 0 || o->spars_ctas < 0 || o->spars_ctas > 32 ||
-      (o->schur_tc != 0 && o->schur_tc != 1) || (o->sketch_tc != 0 && o->sketch_tc != 1))
+      (o->schur_tc != 0 && o->schur_tc != 1) || (o->sketch_tc != 0 && o->sketch_tc != 1) ||
+      o->leaf_bwd < -1 || o->leaf_bwd > 1)
     return SPALU_ERR_ARG;
   if (o->precision != 0 && o->precision != 1) return SPALU_ERR_ARG;
   if (leaf_init_tables() != cudaSuccess) return SPALU_ERR_CUDA;
@@ -775,7 +778,9 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     lf.urec = real((size_t)gl.nbox() * NI * 16);
     lf.uext = real((size_t)gl.nbox() * NI * 16);
     lf.ybuf = real((size_t)gl.nbox() * NI * 64);
-    lf.G = f32 ? (void*)cv.take<float>((size_t)gl.nbox() * NI * 4 * LEAF) : nullptr;
+    lf.cpl = real((size_t)gl.nbox() * 4 * LEAF);
+    const bool useG = f32 && (o->leaf_bwd == 0 || (o->leaf_bwd < 0 && gl.nbox() < LEAF_G_MAX));
+    lf.G = useG ? (void*)cv.take<float>((size_t)gl.nbox() * NI * 4 * LEAF) : nullptr;
     lf.kumax = cv.take<int>(4);
     lf.kur = cv.take<int>((size_t)gl.nbox());
     std::vector<void*> Fst(L + 1, nullptr);
@@ -911,9 +916,11 @@ static spalu_status factor_finish(spalu_factor_t f, cudaStream_t s) {
   // the solve kernels hold a segment's (or separator's) right-hand-side block in shared memory
   for (int l = 1; l <= L && st == SPALU_OK; ++l) {
     if (!level_solve_caps(f->lev[l], f->lstat.data() + LS_N * l, &f->caps[l])) st = SPALU_ERR_UNSUPPORTED;
-    if ((int)f->tuned_nt.size() == 2 * (L + 1) && f->tuned_nt[2 * l] > 0) {
-      f->caps[l].seg_nt = f->tuned_nt[2 * l];
-      f->caps[l].sep_nt = f->tuned_nt[2 * l + 1];
+    if ((int)f->tuned_nt.size() == 4 * (L + 1) && f->tuned_nt[4 * l] > 0) {
+      f->caps[l].seg_nt = f->tuned_nt[4 * l];
+      f->caps[l].sep_nt = f->tuned_nt[4 * l + 1];
+      f->caps[l].seg_split = f->tuned_nt[4 * l + 2];
+      f->caps[l].sep_split = f->tuned_nt[4 * l + 3];
     }
   }
   f->factored = (st == SPALU_OK);
@@ -998,33 +1005,49 @@ spalu_status spalu_tune_solve(spalu_factor_t f, int nrhs, spalu_stream_t stream)
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  f->tuned_nt.assign(2 * (L + 1), 0);
-  const int cand[4][2] = {{256, 256}, {64, 256}, {256, 64}, {64, 64}};
+  f->tuned_nt.assign(4 * (L + 1), 0);
+  // per level: the CTA widths (64 or 256) and the right-hand-side groups (1, 2, 4, 8: more
+  // CTAs per segment or separator on levels with few of them) of the two solve kernels, the
+  // fastest forward + backward pass; the first repetition of each candidate warms up
+  auto time_cfg = [&](int l, const SolveCaps& sc, float* out) -> bool {
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, s);
+      launch_level_solve_fwd(f->lev[l], sc, W, nrhs, lay, s);
+      launch_level_solve_bwd(f->lev[l], sc, W, nrhs, lay, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = ms < tmin ? ms : tmin;
+    }
+    *out = tmin;
+    return true;
+  };
+  const int nts[2] = {64, 256}, splits[4] = {1, 2, 4, 8};
   spalu_status st = SPALU_OK;
   for (int l = 1; l <= L && st == SPALU_OK; ++l) {
-    float best = 1e30f;
-    int bi = 0;
-    for (int c = 0; c < 4; ++c) {
-      SolveCaps sc = f->caps[l];
-      sc.seg_nt = cand[c][0];
-      sc.sep_nt = cand[c][1];
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 4; ++rep) {        // the first repetition warms up
-        cudaEventRecord(e0, s);
-        launch_level_solve_fwd(f->lev[l], sc, W, nrhs, lay, s);
-        launch_level_solve_bwd(f->lev[l], sc, W, nrhs, lay, s);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { st = SPALU_ERR_CUDA; break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) tmin = ms < tmin ? ms : tmin;
-      }
-      if (tmin < best) { best = tmin; bi = c; }
-    }
-    f->tuned_nt[2 * l] = cand[bi][0];
-    f->tuned_nt[2 * l + 1] = cand[bi][1];
-    f->caps[l].seg_nt = cand[bi][0];
-    f->caps[l].sep_nt = cand[bi][1];
+    SolveCaps best = f->caps[l];
+    float tbest = 1e30f;
+    for (int a = 0; a < 2 && st == SPALU_OK; ++a)
+      for (int b = 0; b < 2 && st == SPALU_OK; ++b)
+        for (int g = 0; g < 4 && st == SPALU_OK; ++g)
+          for (int h = 0; h < 4 && st == SPALU_OK; ++h) {
+            if (splits[g] > nrhs || splits[h] > nrhs) continue;
+            SolveCaps sc = f->caps[l];
+            sc.seg_nt = nts[a];
+            sc.sep_nt = nts[b];
+            sc.seg_split = splits[g];
+            sc.sep_split = splits[h];
+            float t = 0.f;
+            if (!time_cfg(l, sc, &t)) { st = SPALU_ERR_CUDA; break; }
+            if (t < tbest) { tbest = t; best = sc; }
+          }
+    f->caps[l] = best;
+    f->tuned_nt[4 * l] = best.seg_nt;
+    f->tuned_nt[4 * l + 1] = best.sep_nt;
+    f->tuned_nt[4 * l + 2] = best.seg_split;
+    f->tuned_nt[4 * l + 3] = best.sep_split;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1492,6 +1515,8 @@ static spalu_status step_prepare(spalu_factor_t f, spalu_factor_s::StepGraph& G)
     if (level_solve_caps(f->lev[l], lm, &c)) {
       c.seg_nt = f->caps[l].seg_nt;
       c.sep_nt = f->caps[l].sep_nt;
+      c.seg_split = f->caps[l].seg_split;
+      c.sep_split = f->caps[l].sep_split;
       f->caps[l] = c;
     } else {
       for (int q = 0; q < 3; ++q) lm[q] = f->lstat[LS_N * l + q];

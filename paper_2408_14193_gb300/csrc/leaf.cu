@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
       }
       qa[sub][q] = a;
       qc[sub][q] = c;
+      reinterpret_cast<T*>(d.cpl)[(size_t)b * NQ + q] = (T)c;   // A(m, side unknown q), 0 outside the grid
     }
   }
   __syncthreads();
@@ -504,24 +505,31 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
 constexpr int SLOT = 16;   // right-hand-side slots per leaf and launch
 constexpr int SWPB = 4;    // warps per CTA of the solve sweeps (two leaves per warp)
 
-// Per-warp shared-memory stage of leaf_solve_kernel (values of T, two buffers): for each of
-// the warp's two leaves 16 L records and, in the FP32 forward solve, the 16 right-hand-side
-// rows of the next block (16 values each); in the U phase KUW columns of KUW values (the U
-// record, and for KUW = 32 its extension) and, FP32 forward, the KUW rows y of the block after.
-// The pads put the two leaves of a warp on different banks.
+// Per-warp shared-memory stage of leaf_solve_kernel (values of T).  L phase, two buffers of:
+// for each of the warp's two leaves 16 L records and (FP32 forward) the right-hand-side rows
+// of the next block; backward also the leaves' 60 side values x_d and coupling coefficients.
+// U phase, two buffers of: KUW columns of KUW values (the U record, and for KUW = 32 its
+// extension) and (FP32) the KUW rows y of the next block and (FP32 backward) the KUW rows of x
+// this block updates.  Rows hold 16 values (the right-hand sides); the pads put the two
+// leaves of a warp on different banks.
 template <typename T, int KUW, bool bwd>
 struct SolveStage {
   static constexpr int EPC = 16 / (int)sizeof(T);      // values per 16-byte chunk
   static constexpr int CPR = SLOT / EPC;                // chunks per 16-value record
+  static constexpr bool CHKV = sizeof(T) == 4;          // FP32: the chunked solve vector
+  static constexpr bool XPF = !bwd && CHKV;
+  static constexpr bool YPF = CHKV;
+  static constexpr bool XOPF = bwd && CHKV;
   static constexpr int LSTP = SLOT * SLOT + EPC;
   static constexpr int USTP = KUW * KUW + EPC;
   static constexpr int XSTP = SLOT * SLOT + 16;
   static constexpr int YSTP = KUW * SLOT + 16;
-  static constexpr bool XPF = !bwd && sizeof(T) == 4;
+  static constexpr int XDSTP = NQ * SLOT + 16;
   static constexpr int bufL = 2 * (LSTP + (XPF ? XSTP : 0));
-  static constexpr int bufU = 2 * (USTP + (XPF ? YSTP : 0));
-  static constexpr int bufsz = bufL > bufU ? bufL : bufU;   // one buffer of one warp
-  static constexpr size_t bytes = (size_t)SWPB * 2 * bufsz * sizeof(T);
+  static constexpr int bufU = 2 * (USTP + (YPF ? YSTP : 0) + (XOPF ? YSTP : 0));
+  static constexpr int xdsz = bwd ? 2 * XDSTP + 2 * 64 : 0;
+  static constexpr int warpsz = 2 * bufL + xdsz > 2 * bufU ? 2 * bufL + xdsz : 2 * bufU;
+  static constexpr size_t bytes = (size_t)SWPB * warpsz * sizeof(T);
 };
 
 // Band sweeps, one warp per two leaves x 16 right-hand sides, thread (leaf, rhs): forward
@@ -533,9 +541,13 @@ struct SolveStage {
 //   after the last read of b_j) and the U sweep reads it back from there, so the intermediate
 //   costs no scratch traffic and stays in L2 between the sweeps.  Backward: x_I is needed
 //   until the last step, so y goes through the sweep buffer.
+// - Backward input: (A_Id x_d)_j is nonzero on the leaf's boundary rows only, one term per
+//   side the node touches: the coupling coefficient (stored by the factorization) times the
+//   side value, both staged once per warp.
 // - FP32: the solve vector is chunked (a node's 16 right-hand sides are one 64-byte run); the
-//   right-hand-side rows of the next L block and the y rows of the next U block are staged
-//   with the records, so no global load is outstanding at a warp barrier.
+//   right-hand-side rows of the next L block, the y rows of the next U block and (backward)
+//   the rows a U block updates are staged with the records, so no global load is
+//   outstanding at a warp barrier.  FP64 reads them directly.
 // - KUW = 16 is launched only when no leaf made an interchange (the step has no swap).
 // All lanes run the sweep arithmetic (lanes without a right-hand side or leaf on values that
 // are never stored), so the warp votes and barriers are full-warp.
@@ -545,10 +557,10 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
   extern __shared__ float4 lsm4[];
   using St = SolveStage<T, KUW, bwd>;
   constexpr int EPC = St::EPC, CPR = St::CPR;
-  constexpr int LSTP = St::LSTP, USTP = St::USTP, XSTP = St::XSTP, YSTP = St::YSTP, bufsz = St::bufsz;
+  constexpr int LSTP = St::LSTP, USTP = St::USTP, XSTP = St::XSTP, YSTP = St::YSTP, XDSTP = St::XDSTP;
+  constexpr int bufL = St::bufL, bufU = St::bufU;
   constexpr int RMAX = KUW - 1 < KV ? KUW - 1 : KV;
-  constexpr bool XPF = St::XPF;
-  constexpr bool CHK = sizeof(T) == 4;
+  constexpr bool CHK = St::CHKV, XPF = St::XPF, YPF = St::YPF, XOPF = St::XOPF;
   constexpr bool PIV = KUW > 16;
   constexpr int RPC = SLOT * CPR;                     // chunks of one leaf's 16 records
   constexpr int CPC = (KUW / SLOT) * CPR;             // chunks of one U column
@@ -560,51 +572,84 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
   if (b0 >= nbox) return;                             // whole warp: no leaf
   const int b = b0 + sub;
   const bool act = b < nbox && c < nrhs;
-  T* stg = reinterpret_cast<T*>(lsm4) + (size_t)(threadIdx.x >> 5) * 2 * bufsz;
+  T* stg = reinterpret_cast<T*>(lsm4) + (size_t)(threadIdx.x >> 5) * St::warpsz;
   const T* lrec = reinterpret_cast<const T*>(d.lrec);
   const T* urec = reinterpret_cast<const T*>(d.urec);
   const T* uext = reinterpret_cast<const T*>(d.uext);
   const unsigned long long pol = evict_first_policy();
   const int bx = d.g.bx, nx = d.nx;
   const int bb = b < nbox ? b : nbox - 1;
-  const int bl1 = b0 + 1 < nbox ? b0 + 1 : b0;       // the warp's second leaf (clamped)
-  const int x0 = (bb % bx) * (LEAF + 1), y0 = (bb / bx) * (LEAF + 1);
-  const int o0 = x0 + nx * y0;                        // grid node of this lane's leaf interior (0, 0)
-  const int og[2] = {(b0 % bx) * (LEAF + 1) + nx * ((b0 / bx) * (LEAF + 1)),
-                     (bl1 % bx) * (LEAF + 1) + nx * ((bl1 / bx) * (LEAF + 1))};
+  // the warp's two leaves (the second clamped) and the grid nodes of their interiors' (0, 0)
+  const int bl0 = b0, bl1 = b0 + 1 < nbox ? b0 + 1 : b0;
+  const int og0 = (bl0 % bx) * (LEAF + 1) + nx * ((bl0 / bx) * (LEAF + 1));
+  const int og1 = (bl1 % bx) * (LEAF + 1) + nx * ((bl1 / bx) * (LEAF + 1));
+  auto bl = [&](int s) { return s ? bl1 : bl0; };
+  auto og = [&](int s) { return s ? og1 : og0; };
+  const int o0 = og(sub);                             // this lane's leaf
   auto node_of = [&](int j) { return o0 + j % LEAF + nx * (j / LEAF); };
-  T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)bb * NI * QL;   // backward only
+  T* yb = reinterpret_cast<T*>(d.ybuf) + (size_t)bb * NI * QL;   // backward only, rows of 16
   T* Xc = X + (size_t)c * lay.cs;
   const long long rs = lay.rs;
   auto xat = [&](int node) -> T& {
     if constexpr (CHK) return X[(size_t)node * SLOT + c];
     else return Xc[(size_t)(node * rs)];
   };
-  // 16 values of row r of the warp's leaf s (FP32 chunked vector), chunk k of 4
-  auto row_chunk = [&](T* dst, int s, int r, int k) {
-    cp_async16(dst, X + (size_t)(og[s] + r % LEAF + nx * (r / LEAF)) * SLOT + 4 * k);
+  // chunk k (4 values) of the 16-value row of grid node `node` (FP32 chunked vector)
+  auto node_chunk = [&](T* dst, int node, int k) { cp_async16(dst, X + (size_t)node * SLOT + 4 * k); };
+
+  // ---- backward input: side values x_d (60 per leaf: BOTTOM, TOP, LEFT, RIGHT, 15 each, the
+  //      grid neighbours of the boundary rows) and their coupling coefficients
+  T* xd = stg + 2 * bufL;                             // [leaf][q][16], pitch XDSTP
+  T* cf = xd + 2 * XDSTP;                             // [leaf][q], pitch 64
+  auto side_node = [&](int s, int q) {
+    const int t = q % LEAF, o = og(s);
+    switch (q / LEAF) {
+      case SIDE_BOTTOM: return o - nx + t;
+      case SIDE_TOP: return o + LEAF * nx + t;
+      case SIDE_LEFT: return o - 1 + nx * t;
+      default: return o + LEAF + nx * t;
+    }
+  };
+  if constexpr (bwd) {
+    // a side exists unless the leaf touches the grid boundary there (coefficient 0)
+    for (int x = lane; x < 2 * NQ; x += 32) {
+      const int s = x / NQ, q = x % NQ;
+      cf[s * 64 + q] = reinterpret_cast<const T*>(d.cpl)[(size_t)bl(s) * NQ + q];
+    }
+    __syncwarp();
+  }
+  // (A_Id x_d)_j of row j = (lx, ly), terms in the order of the CSR columns
+  auto cplin = [&](int lx, int ly) -> T {
+    const T* xs = xd + sub * XDSTP + c;
+    const T* cs = cf + sub * 64;
+    T v = T(0);
+    if (ly == 0) v += cs[lx] * xs[lx * SLOT];
+    if (lx == 0) v += cs[2 * LEAF + ly] * xs[(2 * LEAF + ly) * SLOT];
+    if (lx == LEAF - 1) v += cs[3 * LEAF + ly] * xs[(3 * LEAF + ly) * SLOT];
+    if (ly == LEAF - 1) v += cs[LEAF + lx] * xs[(LEAF + lx) * SLOT];
+    return v;
   };
 
   // ---- L sweep: y = L^{-1} P x, blocks of 16 steps.  Stage of block blk: its records and
   //      (FP32 forward) right-hand-side rows blk * 16 + 16 .. + 31, the refills of its steps.
   auto issue_L_rec = [&](int blk, int buf) {
-    T* S = stg + (size_t)buf * bufsz;
+    T* S = stg + (size_t)buf * bufL;
     const int j0 = blk * SLOT;
     const int nch = (NI - j0 < SLOT ? NI - j0 : SLOT) * CPR;
 #pragma unroll
     for (int i = 0; i < 2 * RPC / 32; ++i) {
       const int s = i / (RPC / 32), k = lane + 32 * (i % (RPC / 32));
-      if (k < nch) cp_async16_ef(S + s * LSTP + k * EPC, lrec + ((size_t)(s ? bl1 : b0) * NI + j0) * SLOT + k * EPC, pol);
+      if (k < nch) cp_async16_ef(S + s * LSTP + k * EPC, lrec + ((size_t)bl(s) * NI + j0) * SLOT + k * EPC, pol);
     }
   };
   auto issue_L_x = [&](int blk, int buf) {
     if constexpr (XPF) {
-      T* S = stg + (size_t)buf * bufsz + 2 * LSTP;
+      T* S = stg + (size_t)buf * bufL + 2 * LSTP;
 #pragma unroll
       for (int i = 0; i < 2 * SLOT * 4 / 32; ++i) {
         const int s = i / (SLOT * 4 / 32), u = (lane + 32 * (i % (SLOT * 4 / 32))) / 4, k = lane % 4;
         const int r = blk * SLOT + SLOT + u;
-        if (r < NI) row_chunk(S + s * XSTP + u * SLOT + 4 * k, s, r, k);
+        if (r < NI) node_chunk(S + s * XSTP + u * SLOT + 4 * k, og(s) + r % LEAF + nx * (r / LEAF), k);
       }
     }
     cp_async_commit();
@@ -612,23 +657,32 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
   const int nbl = (NI + SLOT - 1) / SLOT;
   issue_L_rec(0, 0);
   pdl_wait();                             // the solve vector is written by the preceding kernel
-  auto coupling = [&](int j) {            // (A_Id x_d)_j for the backward sweep
-    T v = T(0);
-    const int lx = j % LEAF, ly = j / LEAF;
-    if (act && (lx == 0 || ly == 0 || lx == LEAF - 1 || ly == LEAF - 1)) {
-      const int node = node_of(j);
-      for (int p = d.rowptr[node]; p < d.rowptr[node + 1]; ++p) {
-        const int cc = d.colind[p];
-        const int cx = cc % nx - x0, cy = cc / nx - y0;
-        if (!(cx >= 0 && cx < LEAF && cy >= 0 && cy < LEAF)) v += (T)d.val[p] * xat(cc);
+  if constexpr (bwd) {
+    if constexpr (CHK) {
+      for (int x = lane; x < 2 * NQ * 4; x += 32) {
+        const int s = x / (NQ * 4), q = (x / 4) % NQ, k = x % 4;
+        T* dst = xd + s * XDSTP + q * SLOT + 4 * k;
+        if (cf[s * 64 + q] != T(0)) node_chunk(dst, side_node(s, q), k);
+        else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+      for (int q = 0; q < NQ; ++q) {
+        const T a = cf[sub * 64 + q];
+        xd[sub * XDSTP + q * SLOT + c] = (act && a != T(0)) ? xat(side_node(sub, q)) : T(0);
       }
     }
-    return v;
-  };
-  T W[16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) W[r] = bwd ? coupling(r) : (act ? xat(node_of(r)) : T(0));
+  }
   issue_L_x(0, 0);
+  T W[16];
+  if constexpr (bwd) {
+    cp_async_wait<0>();
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) W[r] = cplin(r % LEAF, r / LEAF);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) W[r] = act ? xat(node_of(r)) : T(0);
+  }
   for (int blk = 0; blk < nbl; ++blk) {
     if (blk + 1 < nbl) {
       issue_L_rec(blk + 1, (blk + 1) & 1);
@@ -638,9 +692,10 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
       cp_async_wait<0>();
     }
     __syncwarp();
-    const T* S = stg + (size_t)(blk & 1) * bufsz + sub * LSTP;
-    const T* xs = stg + (size_t)(blk & 1) * bufsz + 2 * LSTP + sub * XSTP + c;
+    const T* S = stg + (size_t)(blk & 1) * bufL + sub * LSTP;
+    const T* xs = stg + (size_t)(blk & 1) * bufL + 2 * LSTP + sub * XSTP + c;
     int lx = (blk * SLOT) % LEAF, node = node_of(blk * SLOT);   // grid node of step j
+    int rx = (blk * SLOT + SLOT) % LEAF, ry = (blk * SLOT + SLOT) / LEAF;   // row j + 16 (backward)
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int j = blk * SLOT + u;
@@ -665,41 +720,62 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
         }
         T nv = T(0);
         if (j + 16 < NI) {
-          if constexpr (XPF) nv = xs[u * SLOT];
-          else if constexpr (!bwd) nv = act ? xat(node_of(j + 16)) : T(0);
-          else nv = coupling(j + 16);
+          if constexpr (bwd) nv = cplin(rx, ry);
+          else if constexpr (XPF) nv = xs[u * SLOT];
+          else nv = act ? xat(node_of(j + 16)) : T(0);
         }
         W[u] = nv;
         const bool wrap = lx == LEAF - 1;
         lx = wrap ? 0 : lx + 1;
         node += wrap ? nx - (LEAF - 1) : 1;
+        if constexpr (bwd) {
+          const bool rw = rx == LEAF - 1;
+          rx = rw ? 0 : rx + 1;
+          ry += rw ? 1 : 0;
+        }
       }
     }
     __syncwarp();
   }
 
   // ---- U sweep: x = U^{-1} y, blocks of KUW steps from the bottom.  Stage of block blk: its
-  //      U columns and (FP32 forward) the y rows of block blk + 1, the refills of its steps.
+  //      U columns, (FP32) the y rows of block blk + 1 (the refills of its steps) and
+  //      (FP32 backward) the x rows of block blk.
   auto issue_U = [&](int blk, int buf) {
-    T* S = stg + (size_t)buf * bufsz;
+    T* S = stg + (size_t)buf * bufU;
     const int t0 = blk * KUW;
 #pragma unroll
     for (int i = 0; i < 2 * KUW * CPC / 32; ++i) {
       const int s = i / (KUW * CPC / 32), rem = lane + 32 * (i % (KUW * CPC / 32)), u = rem / CPC, k = rem % CPC;
       const int j = NI - 1 - (t0 + u);
       if (j >= 0) {
-        const size_t rec = ((size_t)(s ? bl1 : b0) * NI + j) * SLOT;
+        const size_t rec = ((size_t)bl(s) * NI + j) * SLOT;
         const T* src = k < CPR ? urec + rec + k * EPC : uext + rec + (k - CPR) * EPC;
         cp_async16_ef(S + s * USTP + u * KUW + k * EPC, src, pol);
       }
     }
-    if constexpr (XPF) {
+    if constexpr (YPF) {
       T* Y = S + 2 * USTP;
 #pragma unroll
       for (int i = 0; i < 2 * KUW * 4 / 32; ++i) {
         const int s = i / (KUW * 4 / 32), u = (lane + 32 * (i % (KUW * 4 / 32))) / 4, k = lane % 4;
         const int r = NI - 1 - (t0 + KUW + u);
-        if (r >= 0) row_chunk(Y + s * YSTP + u * SLOT + 4 * k, s, r, k);
+        if (r >= 0) {
+          if constexpr (bwd)
+            cp_async16(Y + s * YSTP + u * SLOT + 4 * k,
+                       reinterpret_cast<const T*>(d.ybuf) + ((size_t)bl(s) * NI * QL + (size_t)r * SLOT) + 4 * k);
+          else
+            node_chunk(Y + s * YSTP + u * SLOT + 4 * k, og(s) + r % LEAF + nx * (r / LEAF), k);
+        }
+      }
+    }
+    if constexpr (XOPF) {
+      T* XO = S + 2 * USTP + 2 * YSTP;
+#pragma unroll
+      for (int i = 0; i < 2 * KUW * 4 / 32; ++i) {
+        const int s = i / (KUW * 4 / 32), u = (lane + 32 * (i % (KUW * 4 / 32))) / 4, k = lane % 4;
+        const int r = NI - 1 - (t0 + u);
+        if (r >= 0) node_chunk(XO + s * YSTP + u * SLOT + 4 * k, og(s) + r % LEAF + nx * (r / LEAF), k);
       }
     }
     cp_async_commit();
@@ -717,8 +793,9 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
     if (blk + 1 < nbu) { issue_U(blk + 1, (blk + 1) & 1); cp_async_wait<1>(); }
     else cp_async_wait<0>();
     __syncwarp();
-    const T* S = stg + (size_t)(blk & 1) * bufsz + sub * USTP;
-    const T* ys = stg + (size_t)(blk & 1) * bufsz + 2 * USTP + sub * YSTP + c;
+    const T* S = stg + (size_t)(blk & 1) * bufU + sub * USTP;
+    const T* ys = stg + (size_t)(blk & 1) * bufU + 2 * USTP + sub * YSTP + c;
+    const T* xo = stg + (size_t)(blk & 1) * bufU + 2 * USTP + 2 * YSTP + sub * YSTP + c;
     const int jt = NI - 1 - blk * KUW;
     int lx = jt % LEAF, node = node_of(jt);      // grid node of step j (descending)
 #pragma unroll
@@ -730,14 +807,15 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
         lds_vec(S + u * KUW, uv);
         const T x = V[u] * uv[0];
         if (act) {
-          if (!bwd) xat(node) = x;
+          if constexpr (!bwd) xat(node) = x;
+          else if constexpr (XOPF) xat(node) = xo[u * SLOT] - x;
           else xat(node) -= x;
         }
 #pragma unroll
         for (int r = 1; r <= RMAX; ++r) V[(u + r) & (KUW - 1)] -= uv[r] * x;
         T nv = T(0);
         if (j - KUW >= 0) {
-          if constexpr (XPF) nv = ys[u * SLOT];
+          if constexpr (YPF) nv = ys[u * SLOT];
           else if constexpr (bwd) nv = act ? yb[(size_t)(j - KUW) * SLOT + c] : T(0);
           else nv = act ? xat(node - QD * nx - MD + (lx < MD ? LEAF - nx : 0)) : T(0);
         }
@@ -751,10 +829,12 @@ __global__ void __launch_bounds__(SWPB * 32) leaf_solve_kernel(LeafDev d, T* X, 
   }
 }
 
-// Backward leaf step of the mixed path: x_I -= G x_d with G = A_II^{-1} A_Id (FP32, stored by
-// the factorization) and x_d the 60 side unknowns of the leaf.  One leaf per CTA: G is staged
-// in shared memory by cp.async while x_d is gathered, then thread j forms row j of G x_d for
-// all right-hand sides of the chunk (up to 16) and updates the interior unknown j.
+// Backward leaf step of the mixed path on grids of few leaves: x_I -= G x_d with
+// G = A_II^{-1} A_Id (FP32, stored by the factorization) and x_d the 60 side unknowns of the
+// leaf.  One leaf per CTA: G is staged in shared memory by cp.async while x_d is gathered,
+// then thread j forms row j of G x_d for all right-hand sides of the chunk (up to 16) and
+// updates the interior unknown j.  225 independent rows per leaf instead of one sequential
+// sweep pair: on a grid of few leaves the sweeps' step latency, not traffic, bounds the time.
 constexpr int GTH = 256;
 constexpr int GRC = 16;                          // right-hand sides per launch
 __global__ void __launch_bounds__(GTH, 3) leaf_bwd_g_kernel(LeafDev d, float* X, int nrhs, VecLayout lay) {

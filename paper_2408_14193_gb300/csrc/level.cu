@@ -1955,12 +1955,25 @@ __global__ void __launch_bounds__(64) sep_invert_kernel(LevelDev d) {
 template <typename T>
 size_t invert_smem() { return 2 * sizeof(T) * INV_MAX * INV_MAX + sizeof(int) * INV_MAX; }
 
+// The right-hand sides of a launch are split into gridDim.y groups (one CTA per group and
+// segment or separator: more CTAs where a level has few segments); this CTA's group becomes
+// columns 0 .. nc-1 of X.  False when the group is empty.
+template <typename T>
+__device__ __forceinline__ bool rhs_group(T*& X, int& nc, const VecLayout& lay) {
+  const int per = (nc + (int)gridDim.y - 1) / (int)gridDim.y, c0 = (int)blockIdx.y * per;
+  if (c0 >= nc) return false;
+  X += (size_t)c0 * (size_t)lay.cs;
+  nc = nc - c0 < per ? nc - c0 : per;
+  return true;
+}
+
 // Forward, per segment: b_r -= T^T b_s; y_r = L^{-1} P b_r; b_s -= Z y_r.
 // Backward, per segment: x_r = U^{-1} (y_r - W x_s); x_s -= T x_r.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
   pdl_trigger();
   extern __shared__ double smd[];
+  if (!rhs_group(X, nc, lay)) return;
   const int sid = blockIdx.x;
   const int e = d.cnt[sid], k = d.kk[sid], r = e - k;
   if (r == 0 || e == 0) return;
@@ -2055,6 +2068,7 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(LevelDev d, SolveCaps cap, T* X, int nc, VecLayout lay, int bwd) {
   pdl_trigger();
   extern __shared__ double smd[];
+  if (!rhs_group(X, nc, lay)) return;
   const int P = blockIdx.x;
   const int ndP = d.pcount[2 * P], kp = d.pcount[2 * P + 1];
   if (kp == 0) return;
@@ -2326,6 +2340,7 @@ bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
   // CTA widths before any tuning: 2-warp segment CTAs where segments have at most 32 unknowns
   sc.seg_nt = d.capS <= 32 ? 64 : 256;
   sc.sep_nt = 256;
+  sc.seg_split = sc.sep_split = 1;
   sc.sep_smem = (size_t)(sep_fixed + TB * mx((long long)sc.lucap * sc.lucap, sc.qcap));
   *out = sc;
   return true;
@@ -2342,17 +2357,19 @@ static void level_solve(const LevelDev& d, const SolveCaps& sc, T* X, int nrhs, 
     T* Xc = X + (size_t)(c0 / SC) * lay.chunk;
     auto seg_go = [&](int dir) {
       note_launch();
+      const dim3 grid(d.g.nseg(), sc.seg_split < nc ? sc.seg_split : nc);
       if (sc.seg_nt == 64)  // 2-warp CTAs: four times as many resident per SM
-        launch_pdl(seg_solve_kernel<T, 64>, dim3(d.g.nseg()), dim3(64), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
+        launch_pdl(seg_solve_kernel<T, 64>, grid, dim3(64), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
       else
-        launch_pdl(seg_solve_kernel<T, 256>, dim3(d.g.nseg()), dim3(256), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
+        launch_pdl(seg_solve_kernel<T, 256>, grid, dim3(256), sc.seg_smem, s, d, sc, Xc, nc, lay, dir);
     };
     auto sep_go = [&](int dir) {
       note_launch();
+      const dim3 grid(d.gp.nbox(), sc.sep_split < nc ? sc.sep_split : nc);
       if (sc.sep_nt == 64)
-        launch_pdl(sep_solve_kernel<T, 64>, dim3(d.gp.nbox()), dim3(64), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
+        launch_pdl(sep_solve_kernel<T, 64>, grid, dim3(64), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
       else
-        launch_pdl(sep_solve_kernel<T, 256>, dim3(d.gp.nbox()), dim3(256), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
+        launch_pdl(sep_solve_kernel<T, 256>, grid, dim3(256), sc.sep_smem, s, d, sc, Xc, nc, lay, dir);
     };
     if (!bwd) {
       if (d.g.nseg() > 0) seg_go(0);

@@ -192,6 +192,7 @@ struct SolveCaps {
   int yrows;     // separator: skeleton rows of the right-hand-side block (>= every kp)
   size_t seg_smem, sep_smem;
   int seg_nt, sep_nt;   // CTA widths of the segment / separator solve kernels (64 or 256)
+  int seg_split, sep_split;   // right-hand-side groups per segment / separator (CTAs along y)
 };
 
 struct LeafDev {
@@ -207,7 +208,10 @@ struct LeafDev {
   void* uext;       //   U(j-r, j) at slot r - 16 for r = 16..30 (fill of the interchanges), slot 15 = 0
   void* ybuf;       // [nbox * 225 * 64] intermediate vectors of the band sweeps
   void* G;          // [nbox * 225 * 60] FP32 A_II^{-1} A_Id per leaf (row-major, column = side
-                    // unknown); set in the mixed path only, where it replaces the backward sweeps
+                    // unknown); mixed path on grids of fewer than LEAF_G_MAX leaves only, where
+                    // it replaces the backward sweeps
+  void* cpl;        // [nbox * 60] coupling of each side unknown q to its interior neighbour m,
+                    // A(m, q) (FP64 or FP32; 0 where the side node is outside the grid)
   int* kumax;       // largest upper bandwidth of U produced by the interchanges, at least 16
                     // when any leaf made one (<= 15: the sweeps need no interchange step)
   int* kur;         // [nbox] upper bandwidth of each leaf's U
@@ -219,6 +223,7 @@ struct LeafDev {
 };
 
 constexpr int LEAF = 15;
+constexpr int LEAF_G_MAX = 2048;       // leaves below which the mixed backward leaf step uses G
 constexpr int NI = LEAF * LEAF;        // interior unknowns of a leaf
 constexpr int KL = LEAF;               // lower bandwidth of the leaf matrix (natural order)
 constexpr int KU = LEAF;               // upper bandwidth

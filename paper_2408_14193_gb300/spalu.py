@@ -53,6 +53,7 @@ class Options(ctypes.Structure):
         ("spars_ctas", ctypes.c_int),
         ("schur_tc", ctypes.c_int),
         ("sketch_tc", ctypes.c_int),
+        ("leaf_bwd", ctypes.c_int),
     ]
 
     @classmethod

@@ -44,7 +44,7 @@ def test_status_strings_and_defaults(lib):
     assert lib.spalu_status_string(-3) == b"zero pivot in an LU"
     o = Options.default()
     assert o.eps_id == 1e-8 and o.p_oversample == 5 and o.h0 == 16 and o.near_radius == 2
-    assert o.gmres_tol == 1e-10 and o.spars_ctas == 4 and o.schur_tc == 1
+    assert o.gmres_tol == 1e-10 and o.spars_ctas == 4 and o.schur_tc == 1 and o.leaf_bwd == -1
     # argument checks that need no device: bad grid shape, bad leaf pitch, null output
     h = ctypes.c_void_p()
     assert lib.spalu_nd_build_grid(20, 31, 16, None, ctypes.byref(h)) == -1

@@ -265,6 +265,32 @@ def test_mixed_precision_refined(kind, n, eps):
     assert np.all(res <= 1e-10), res
 
 
+@pytest.mark.parametrize("kind,n,nrhs", [("diffusion", 255, 16), ("helmholtz", 127, 3), ("convdiff", 127, 16)])
+def test_leaf_backward_forms(kind, n, nrhs):
+    """The two forms of the mixed backward leaf step x_I -= A_II^{-1} A_Id x_d (Eq. (WV)):
+    leaf_bwd = 0 (one product with the stored G = A_II^{-1} A_Id) and leaf_bwd = 1 (a band
+    sweep pair on the stored factors with the coupling table; the interchange variant on the
+    Helmholtz leaves, idle lanes with 3 right-hand sides) agree to FP32 rounding on the same
+    factorization, and both meet the mixed bar against the FP64 oracle."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    P = W.make_problem(kind, n, seed=41, nrhs=nrhs)
+    rp, ci, va, B = _dev(P)
+    nd = NestedDissection(n)
+    sym = 1 if P.symmetric else 0
+    xs = []
+    for form in (0, 1):
+        f = Factor(nd, eps_id=1e-6, symmetric=sym, precision=1, leaf_bwd=form)
+        f.factor(rp, ci, va)
+        xs.append(f.solve(B).cpu().numpy().T)
+    nrm, ent = rel_errors(xs[1], xs[0])
+    print(f"{kind} {n}: sweeps vs G: {nrm:.2e} (norm-wise), {ent:.2e} (entry-wise)")
+    assert nrm <= (1e-3 if kind == "helmholtz" else 1e-4) and ent <= (1e-2 if kind == "helmholtz" else 1e-3)
+    Xo = osolve(ofactor(P.A, nested_dissection(n, n), OOpts(eps=1e-6, symmetric=P.symmetric)), P.B)
+    bar = 1e-1 if kind == "helmholtz" else 1e-2
+    for x in xs:
+        assert rel_errors(x, Xo)[0] <= bar
+
+
 @pytest.mark.parametrize("kind,n,which", [("diffusion", 255, "schur_tc"), ("convdiff", 127, "schur_tc"),
                                           ("diffusion", 255, "sketch_tc"), ("convdiff", 127, "sketch_tc")])
 def test_contractions_on_tensor_cores(kind, n, which):
@@ -341,8 +367,9 @@ def test_zero_rhs_is_a_no_op():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tuned_solve_matches_default(precision):
-    """spalu_tune_solve only changes CTA widths of the level solves: same solution (up to the
-    order of the atomic separator updates), kept across a re-factorization."""
+    """spalu_tune_solve only changes CTA widths and right-hand-side groups of the level solves:
+    same solution (up to the order of the atomic separator updates), kept across a
+    re-factorization."""
     from paper_2408_14193_gb300 import Factor, NestedDissection
     n = 255
     P = W.make_problem("diffusion", n, seed=43, nrhs=4)
