@@ -386,7 +386,9 @@ def _segment_id(blk, g, key, nbr, nodes, l, sid, nx, opts: Options, A=None, L=0,
         G = sketch_matrix(opts.seed, l, sid, h, f_nodes, f_half)
         Y = np.vstack([BN, (G @ BF) / math.sqrt(h)])
         perm, k, T = interp_decomp(Y, opts.eps)
-        cnt["flops_sparsify"] += fl.sketch(h, nF, e) + fl.qr(Y.shape[0], e, k)
+        # work count: a pass that may still double h only has to establish k > h - p, so its
+        # QR counts min(k, h - p + 1) steps (the library stops there; the results are the same)
+        cnt["flops_sparsify"] += fl.sketch(h, nF, e) + fl.qr(Y.shape[0], e, min(k, max(1, h - p + 1)))
         if predicted:
             predicted = False
             if k <= h - p and pred.id_error_ok(Bx, perm, k, T, opts.eps):

@@ -238,11 +238,12 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 // Drmac-Bujanovic guard written for squared norms: no division or square root per column and
 // step) — and the pivot is chosen from them; the Householder products and their column sums
 // run in T.  perm receives the column order; on exit the first k rows of Y hold [R_1 R_2] in
-// the permuted order.  Returns k.  sh: >= NWT*32 + 3*64 doubles of shared scratch; flags: >= e.
-// NWT = warps of the CTA.
+// the permuted order.  Returns k.  The factorization also stops after kstop steps (returning
+// kstop): a caller that only needs to know whether k exceeds kstop - 1 skips the rest.
+// sh: >= NWT*32 + 3*64 doubles of shared scratch; flags: >= e.  NWT = warps of the CTA.
 template <typename T, int NWT>
 __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1,
-                          double* vn2, double* sh, int* flags, int* shi) {
+                          double* vn2, double* sh, int* flags, int* shi, int kstop) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* part = reinterpret_cast<T*>(sh);                   // [NWT][32] partial dots
   T* coef = reinterpret_cast<T*>(sh + NWT * 32);         // [64]
@@ -262,7 +263,7 @@ __device__ int block_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, do
   __syncthreads();
   const double tol3z = sqrt(DBL_EPSILON);
   const double tie = (1.0 - TIE_RTOL) * (1.0 - TIE_RTOL);   // on squared norms
-  const int kmax = min(m, e);
+  const int kmax = min(min(m, e), kstop);
   double ref = 0.0;
   int k = kmax;
   for (int i = 0; i < kmax; ++i) {
@@ -799,7 +800,7 @@ __device__ bool id_error_ok(const SegCtx& S, BGet bget, int halves, int e, int k
 // Same arithmetic as block_cpqr up to the order of the sums.  All threads call it.
 template <typename T>
 __device__ int warp_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1, double* vn2,
-                         int* shi) {
+                         int* shi, int kstop) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = threadIdx.x; j < e; j += blockDim.x) perm[j] = j;
   if (m == 0 || e == 0) { __syncthreads(); return 0; }
@@ -820,7 +821,7 @@ __device__ int warp_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, dou
     }
     const double tol3z = sqrt(DBL_EPSILON);
     const double tie = (1.0 - TIE_RTOL) * (1.0 - TIE_RTOL);
-    const int kmax = min(m, e);
+    const int kmax = min(min(m, e), kstop);
     double ref = 0.0;
     int k = kmax;
     for (int i = 0; i < kmax; ++i) {
@@ -1172,8 +1173,11 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
       }
     }
     __syncthreads();
-    k = (NWT == NW && in_smem && e <= 64) ? warp_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shi)
-                                          : block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi);
+    // a pass that can still double h only needs to know whether k > h - p: its QR stops at
+    // step h - p + 1 (the same decision, the remaining steps skipped)
+    const int kstop = (!full && h < nF) ? max(1, hh - d.p_over + 1) : e;
+    k = (NWT == NW && in_smem && e <= 64) ? warp_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shi, kstop)
+                                          : block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi, kstop);
     ++passes;
     if (threadIdx.x == 0) work_done += work::qr(m, e, k);
     if (predicted) {          // the one-pass ID stands if it passes the measured-error test
