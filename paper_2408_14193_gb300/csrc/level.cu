@@ -33,7 +33,8 @@ namespace {
 
 constexpr int NEAR_MAX = 16;      // near unknowns per segment (the geometry gives <= 10)
 constexpr int RUN_MAX = 16;
-constexpr int SK_CHUNK = 16;      // far unknowns per chunk of the sketch product
+constexpr int SK_CHUNK = 16;      // far unknowns per chunk of the sketch product (at least)
+constexpr int SK_CHUNK_MAX = 64;  // ... and at most, where the shared-memory budget has room
 constexpr int NW = 8;             // warps per CTA of the sparsify kernel (segments with e > 32)
 constexpr int NW_SMALL = 2;       // ... and for levels whose segments have at most 16 unknowns
 constexpr double TIE_RTOL = 1e-12;
@@ -1038,7 +1039,16 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
   const size_t small_b = (2 * (size_t)e) * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * TD + 64;
   const size_t per_ch_b = (size_t)halves * (e + hmax) * TD;
   const size_t ydt_b = ((size_t)(mmax + 1) * e + 2 * (size_t)e * e) * TD;
+  // chunk of the sketch product: the largest of 64, 32 and 16 far unknowns whose working set
+  // fits the budget together with the staged B block (or without it, where B never fits):
+  // fewer chunks, fewer barriers on the coarse levels' long far fields
   int ch = SK_CHUNK;
+  {
+    const size_t bsz = (size_t)halves * S.nb * e * TD + 48;
+    const bool keep_b = small_b + SK_CHUNK * per_ch_b + ydt_b + bsz <= (size_t)smem_bytes;
+    for (int c = SK_CHUNK_MAX; c > SK_CHUNK; c >>= 1)
+      if (small_b + c * per_ch_b + ydt_b + (keep_b ? bsz : 0) <= (size_t)smem_bytes) { ch = c; break; }
+  }
   bool in_smem = small_b + ch * per_ch_b + ydt_b <= (size_t)smem_bytes;
   if (!in_smem) {
     size_t room = (size_t)smem_bytes > small_b ? (size_t)smem_bytes - small_b : 0;
@@ -2181,14 +2191,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
 
 }  // namespace
 
-size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes) {
+size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes, int chunk) {
   const size_t halves = symmetric ? 1 : 2;
   const size_t hcap = (size_t)(h0 > 2 * (e + p_over) ? h0 : 2 * (e + p_over));
   const size_t mmax = halves * NEAR_MAX + hcap;
   const size_t small_b = 2 * (size_t)e * 8 + (3 * (size_t)e + 4) * 4 + (size_t)e * tbytes + 64;
   // segments of at most 32 unknowns also stage their B block (<= 6 sides of e + 8 corners)
   const size_t bs = e <= 32 ? halves * (6 * (size_t)e + 8) * e + 4 : 0;
-  return small_b + (SK_CHUNK * halves * (e + hcap) + (mmax + 1) * e + 2 * (size_t)e * e + bs) * tbytes;
+  return small_b + ((size_t)chunk * halves * (e + hcap) + (mmax + 1) * e + 2 * (size_t)e * e + bs) * tbytes;
 }
 
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes) {

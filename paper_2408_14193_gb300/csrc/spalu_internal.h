@@ -302,7 +302,7 @@ void launch_pred_infer(const PredDev* P, const float* X, int n, float* out, cuda
 void launch_pred_export(const float* feat, const int* tgt, int nseg, int p, float* X, float* Y, int cap,
                         int* count, cudaStream_t s);
 
-size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes);
+size_t sparsify_smem_need(int e, int symmetric, int h0, int p_over, int tbytes, int chunk);
 size_t sparsify_smem_min(int e, int symmetric, int h0, int p_over, int tbytes);
 // Dynamic shared memory per sparsify CTA that lets `ctas` of them be resident on one SM
 // (the variant that a level of segment capacity capS launches; 0 when that many cannot fit)
