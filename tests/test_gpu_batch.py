@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from parity import assert_close
+from parity import assert_close, rel_errors
 from oracle.nd import nested_dissection
 from oracle.spalu import Options as OOpts, factor as ofactor, solve as osolve
 
@@ -52,9 +52,13 @@ def test_batch_matches_one_at_a_time(precision):
         x, y = Xs[i].cpu().numpy().T, Y.cpu().numpy().T       # (N, nrhs): one column per RHS
         # the solve adds separator contributions with atomics, in a run-dependent order: FP64
         # rounding for the plain form; FP32 rounding of an FP32 factor for the mixed one (its
-        # direct solve is only accurate to ~1e-4 at this eps, refinement restores 1e-10)
-        tol = 1e-12 if precision == 0 else 1e-3
-        assert_close(x, y, tol, f"problem {i}, n {n}")
+        # direct solve is only accurate to ~1e-4 at this eps, refinement restores 1e-10; single
+        # entries near a zero of the solution move by up to ~1e-3 of its largest entry)
+        if precision == 0:
+            assert_close(x, y, 1e-12, f"problem {i}, n {n}")
+        else:
+            nrm, ent = rel_errors(x, y)
+            assert nrm <= 1e-4 and ent <= 5e-3, f"problem {i}, n {n}: {nrm:.3e}, {ent:.3e}"
     # one problem of the batch against the oracle (FP64 parity bar)
     if precision == 0:
         P = probs[3][0]
