@@ -784,6 +784,7 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     lf.cpl = real((size_t)gl.nbox() * 4 * LEAF);
     const bool useG = f32 && (o->leaf_bwd == 0 || (o->leaf_bwd < 0 && gl.nbox() < LEAF_G_MAX));
     lf.G = useG ? (void*)cv.take<float>((size_t)gl.nbox() * NI * 4 * LEAF) : nullptr;
+    lf.band5 = cv.take<double>((size_t)gl.nbox() * NI * 5);
     lf.kumax = cv.take<int>(4);
     lf.kur = cv.take<int>((size_t)gl.nbox());
     std::vector<void*> Fst(L + 1, nullptr);

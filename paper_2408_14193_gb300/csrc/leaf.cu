@@ -276,10 +276,32 @@ __device__ __forceinline__ void sweep_U(const BandT& B, In in, Out out) {
 // factor can reach; multipliers scaled by the reciprocal pivot) of one leaf per 64-thread
 // CTA, in FP64, on a sliding window of WS band columns in shared memory: column c sits in
 // slot c mod WS; after step j column j is final, goes to global memory in precision T and its
-// slot is refilled with column j + WS assembled from the CSR (first touched at step j + 2).
+// slot is refilled with column j + WS (first touched at step j + 2) from the gathered nonzeros
+// (leaf_band5_kernel), loaded one step before.
 // Also zeroes the leaf's frontal block and records the upper bandwidth reached.
 constexpr int WS = 32;       // window columns (> KV)
 constexpr int LUT = 64;      // threads per leaf LU
+
+// The leaf matrices' nonzeros by column, gathered from the CSR once for all leaves (one thread
+// per leaf, column and stencil offset, every lookup independent), so that the LU's window
+// refills read them with plain loads issued a step ahead instead of searching the CSR on the
+// critical path of every step.
+__global__ void leaf_band5_kernel(LeafDev d) {
+  const int nbox = d.g.nbox();
+  const long long n = (long long)nbox * NI * 5;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(x % 5), c = (int)((x / 5) % NI), b = (int)(x / (5 * NI));
+    const int o = k == 0 ? -LEAF : k == 1 ? -1 : k == 2 ? 0 : k == 3 ? 1 : LEAF;
+    const int i = c + o;
+    double v = 0.0;
+    if (i >= 0 && i < NI && (o == 0 || o == LEAF || o == -LEAF || i / LEAF == c / LEAF)) {
+      const int x0 = (b % d.g.bx) * (LEAF + 1), y0 = (b / d.g.bx) * (LEAF + 1);
+      v = csr_entry(d.rowptr, d.colind, d.val, (x0 + i % LEAF) + d.nx * (y0 + i / LEAF),
+                    (x0 + c % LEAF) + d.nx * (y0 + c / LEAF));
+    }
+    d.band5[x] = v;
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
@@ -288,9 +310,6 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
   const Geo g = d.g;
-  const int I = b % g.bx, J = b / g.bx;
-  const int x0 = I * (LEAF + 1), y0 = J * (LEAF + 1);
-  const int nx = d.nx;
   {
     T* F = reinterpret_cast<T*>(d.F) + (size_t)b * d.ldF * d.ldF;
     const int D = g.D();
@@ -299,18 +318,16 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
   T* lrg = reinterpret_cast<T*>(d.lrec) + (size_t)b * NI * 16;
   T* urg = reinterpret_cast<T*>(d.urec) + (size_t)b * NI * 16;
   T* uxg = reinterpret_cast<T*>(d.uext) + (size_t)b * NI * 16;
-  auto node_of = [&](int j) { return (x0 + j % LEAF) + nx * (y0 + j / LEAF); };
-  // band row r of column c of A_II from the CSR: A(i, c), i = c + r - KV (5-point stencil)
+  // band row r of column c of A_II: A(c + r - KV, c), nonzero for the five stencil offsets only
+  const double* b5 = d.band5 + (size_t)b * NI * 5;
   auto assemble = [&](int r, int c) -> double {
-    const int i = c + r - KV;
-    if (c >= NI || i < 0 || i >= NI) return 0.0;
-    const int di = i - c;
-    const bool adj = di == 0 || di == LEAF || di == -LEAF || ((di == 1 || di == -1) && i / LEAF == c / LEAF);
-    if (!adj) return 0.0;
-    return csr_entry(d.rowptr, d.colind, d.val, node_of(i), node_of(c));
+    const int o = r - KV;
+    const int k = o == -LEAF ? 0 : o == -1 ? 1 : o == 0 ? 2 : o == 1 ? 3 : o == LEAF ? 4 : -1;
+    return (c < NI && k >= 0) ? b5[5 * c + k] : 0.0;
   };
   auto w = [&](int i, int c) -> double& { return W[(KV + i - c) + LDAB * (c & (WS - 1))]; };
   for (int x = tid; x < LDAB * WS; x += LUT) W[x] = assemble(x % LDAB, x / LDAB);
+  double pre = tid < LDAB ? assemble(tid, WS) : 0.0;     // the refill of the next slot, a step ahead
   __syncthreads();
   int ju = 0, kureach = KU;
   bool ok = true, swapped = false;
@@ -364,7 +381,8 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
       else if (tid > KV - 16) { if (tid < KV) urg[16 * j + (KV - tid)] = v; }   // U(j-r, j), r = KV - tid <= 15
       else uxg[16 * j + (KV - 16 - tid)] = v;                      // U(j-r, j), r = 16..30
       if (tid == KV) uxg[16 * j + 15] = T(0);
-      slot = assemble(tid, j + WS);
+      slot = pre;                          // column j + WS
+      pre = assemble(tid, j + WS + 1);     // consumed at step j + 1
     }
   }
   if (!ok && tid == 0) atomicOr(d.err, ERR_SINGULAR);
@@ -964,6 +982,13 @@ cudaError_t leaf_init_tables() {
 
 void launch_leaf_factor(const LeafDev& d, cudaStream_t s) {
   const int nbox = d.g.nbox();
+  note_launch();
+  {
+    const long long n = (long long)nbox * NI * 5;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    leaf_band5_kernel<<<(int)blocks, 256, 0, s>>>(d);
+  }
   note_launch();
   if (d.fp32) leaf_lu_kernel<float><<<nbox, LUT, 0, s>>>(d);
   else leaf_lu_kernel<double><<<nbox, LUT, 0, s>>>(d);

@@ -212,6 +212,8 @@ struct LeafDev {
                     // it replaces the backward sweeps
   void* cpl;        // [nbox * 60] coupling of each side unknown q to its interior neighbour m,
                     // A(m, q) (FP64 or FP32; 0 where the side node is outside the grid)
+  double* band5;    // [nbox * 225 * 5] the leaf matrix's nonzeros by column c: A(c + o, c) for
+                    // o = -15, -1, 0, 1, 15 (0 where the stencil neighbour is outside the leaf)
   int* kumax;       // largest upper bandwidth of U produced by the interchanges, at least 16
                     // when any leaf made one (<= 15: the sweeps need no interchange step)
   int* kur;         // [nbox] upper bandwidth of each leaf's U
