@@ -794,38 +794,70 @@ __device__ bool id_error_ok(const SegCtx& S, BGet bget, int halves, int e, int k
 }
 
 // ------------------------------------------------------------ sparsify: one CTA per segment
-// The same column-pivoted Householder QR by one warp, for the 8-warp CTAs when the sketch sits
-// in shared memory (odd pitch) and e <= 64: lane l owns columns l and l + 32, keeps their
-// squared norms in registers and downdates them itself, so a step needs no barrier; the
-// pivot, the Householder scalars and the rank decision are warp-uniform (xor reductions).
-// Same arithmetic as block_cpqr up to the order of the sums.  All threads call it.
-template <typename T>
-__device__ int warp_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, double* vn1, double* vn2,
-                         int* shi, int kstop) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// The same column-pivoted Householder QR for CTAs of NWT warps when e <= 64, with the row work
+// spread over the warps and the scalar work on warp 0; three barriers per step.  Lanes own
+// columns (lane l: columns l and l + 32), warps own rows (warp w: rows r = w mod NWT).  Per
+// step i: warp 0 downdates the FP64 squared norms by the row of step i - 1 (recomputing below
+// the guard), chooses the pivot and forms the Householder scalars from the pivot column
+// (before it moves), and publishes them; then every warp swaps columns i and p on its rows and
+// forms its partial dots v^T y_j over its rows; then every warp sums the partial dots in warp
+// order and updates its rows.  Same arithmetic as block_cpqr up to the order of the sums.
+// part: >= NWT * 64 values of T; pub: >= 4 values of T.  All threads call it.
+template <typename T, int NWT>
+__device__ int rows_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, T* part, T* pub, int* shi,
+                         int kstop) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < e; j += blockDim.x) perm[j] = j;
   if (m == 0 || e == 0) { __syncthreads(); return 0; }
-  for (int j = warp; j < e; j += nw) {
+  // initial squared norms: partial sums over each warp's rows, added in warp order by warp 0
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int j = lane + 32 * t;
     T s = T(0);
-    for (int r = lane; r < m; r += 32) { T v = Y[r + (size_t)ldy * j]; s += v * v; }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) { vn1[j] = (double)s; vn2[j] = (double)s; }
+    if (j < e)
+      for (int r = warp; r < m; r += NWT) { const T v = Y[r + (size_t)ldy * j]; s += v * v; }
+    part[warp * 64 + j] = s;
   }
   __syncthreads();
+  const double tol3z = sqrt(DBL_EPSILON);
+  const double tie = (1.0 - TIE_RTOL) * (1.0 - TIE_RTOL);
+  const int kmax = min(min(m, e), kstop);
+  double n1[2] = {0.0, 0.0}, n2[2] = {0.0, 0.0};       // warp 0: squared norms of lane's columns
+  double ref = 0.0;
   if (warp == 0) {
-    double n1[2], n2[2];
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-      const int j = lane + 32 * t;
-      n1[t] = j < e ? vn1[j] : 0.0;
-      n2[t] = j < e ? vn2[j] : 0.0;
+      T s = T(0);
+      for (int w = 0; w < NWT; ++w) s += part[w * 64 + lane + 32 * t];
+      n1[t] = n2[t] = lane + 32 * t < e ? (double)s : 0.0;
     }
-    const double tol3z = sqrt(DBL_EPSILON);
-    const double tie = (1.0 - TIE_RTOL) * (1.0 - TIE_RTOL);
-    const int kmax = min(min(m, e), kstop);
-    double ref = 0.0;
-    int k = kmax;
-    for (int i = 0; i < kmax; ++i) {
+  }
+  int k = kmax;
+  for (int i = 0; i < kmax; ++i) {
+    // ---- warp 0: downdates by row i - 1, pivot, Householder scalars of the pivot column
+    if (warp == 0) {
+      if (i > 0) {
+        unsigned fl = 0;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int j = lane + 32 * t;
+          if (j > i - 1 && j < e && n1[t] != 0.0) {
+            const double rij = (double)Y[(i - 1) + (size_t)ldy * j];
+            const double sn = fmax(n1[t] - rij * rij, 0.0);
+            if (sn <= tol3z * n2[t]) fl |= 1u << t;
+            else n1[t] = sn;
+          }
+        }
+        unsigned f0 = __ballot_sync(0xffffffffu, fl & 1u), f1 = __ballot_sync(0xffffffffu, (fl >> 1) & 1u);
+        while (f0 | f1) {          // recompute from rows i.. (rare)
+          int j;
+          if (f0) { j = __ffs(f0) - 1; f0 &= f0 - 1; } else { j = 32 + __ffs(f1) - 1; f1 &= f1 - 1; }
+          double s2 = 0.0;
+          for (int r = i + lane; r < m; r += 32) { const double v = (double)Y[r + (size_t)ldy * j]; s2 += v * v; }
+          for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+          if (lane == (j & 31)) { if (j >> 5) { n1[1] = s2; n2[1] = s2; } else { n1[0] = s2; n2[0] = s2; } }
+        }
+      }
       long long mx = -1;
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
@@ -842,11 +874,6 @@ __device__ int warp_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, dou
       }
       for (int o = 16; o > 0; o >>= 1) p = min(p, __shfl_xor_sync(0xffffffffu, p, o));
       if (p != i) {
-        for (int r = lane; r < m; r += 32) {
-          const T a = Y[r + (size_t)ldy * i];
-          Y[r + (size_t)ldy * i] = Y[r + (size_t)ldy * p];
-          Y[r + (size_t)ldy * p] = a;
-        }
         const int si = i >> 5, sp = p >> 5;
         const double i1 = __shfl_sync(0xffffffffu, si ? n1[1] : n1[0], i & 31);
         const double i2 = __shfl_sync(0xffffffffu, si ? n2[1] : n2[0], i & 31);
@@ -855,59 +882,74 @@ __device__ int warp_cpqr(T* Y, int ldy, int m, int e, double eps, int* perm, dou
         if (lane == (i & 31)) { if (si) { n1[1] = p1; n2[1] = p2; } else { n1[0] = p1; n2[0] = p2; } }
         if (lane == (p & 31)) { if (sp) { n1[1] = i1; n2[1] = i2; } else { n1[0] = i1; n2[0] = i2; } }
         if (lane == 0) { const int t = perm[i]; perm[i] = perm[p]; perm[p] = t; }
-        __syncwarp();
       }
+      const T* yp = Y + (size_t)ldy * p;
       T s = T(0);
-      for (int r = i + lane; r < m; r += 32) { const T v = Y[r + (size_t)ldy * i]; s += v * v; }
+      for (int r = i + lane; r < m; r += 32) { const T v = yp[r]; s += v * v; }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      const T normx = sqrt(s);
-      const T x0 = Y[i + (size_t)ldy * i];
-      const T alpha = x0 >= T(0) ? -normx : normx;
-      const T v0 = x0 - alpha;
-      const T vv = v0 * v0 + (s - x0 * x0);
-      const T c2 = vv > T(0) ? T(2) / vv : T(0);
-      if (i == 0) ref = (double)normx;
-      if (ref == 0.0) { k = 0; break; }
-      if ((double)normx <= eps * ref || normx == T(0)) { k = i; break; }
-      const T* yi = Y + (size_t)ldy * i;
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int j = lane + 32 * t;
-        if (j <= i || j >= e) continue;
-        T* yj = Y + (size_t)ldy * j;
-        T d0 = v0 * yj[i], d1 = T(0), d2 = T(0), d3 = T(0);
-        int r = i + 1;
-        for (; r + 3 < m; r += 4) {
-          d0 += yi[r] * yj[r];
-          d1 += yi[r + 1] * yj[r + 1];
-          d2 += yi[r + 2] * yj[r + 2];
-          d3 += yi[r + 3] * yj[r + 3];
-        }
-        for (; r < m; ++r) d0 += yi[r] * yj[r];
-        const T cj = ((d0 + d1) + (d2 + d3)) * c2;
-        yj[i] -= cj * v0;
-        for (r = i + 1; r < m; ++r) yj[r] -= cj * yi[r];
-        const double sq = n1[t];
-        if (sq != 0.0) {
-          const double rij = (double)yj[i];
-          const double sn = fmax(sq - rij * rij, 0.0);
-          if (sn <= tol3z * n2[t]) {
-            double s2 = 0.0;
-            for (r = i + 1; r < m; ++r) { const double v = (double)yj[r]; s2 += v * v; }
-            n1[t] = s2;
-            n2[t] = s2;
-          } else {
-            n1[t] = sn;
-          }
-        }
+      if (lane == 0) {
+        const T normx = sqrt(s);
+        const T x0 = yp[i];
+        const T alpha = x0 >= T(0) ? -normx : normx;
+        const T v0 = x0 - alpha;
+        const T vv = v0 * v0 + (s - x0 * x0);
+        if (i == 0) ref = (double)normx;
+        int stop = 0;
+        if (ref == 0.0) stop = 2;
+        else if ((double)normx <= eps * ref || normx == T(0)) stop = 1;
+        pub[0] = alpha;
+        pub[1] = v0;
+        pub[2] = vv > T(0) ? T(2) / vv : T(0);
+        shi[0] = p;
+        shi[1] = stop;
       }
-      if (lane == 0) Y[i + (size_t)ldy * i] = alpha;
-      __syncwarp();
     }
-    if (lane == 0) shi[0] = k;
+    __syncthreads();
+    const int p = shi[0], stop = shi[1];
+    // ---- every warp, its rows (one per lane): swap columns i and p (also on the stopping step,
+    //      as perm already has)
+    if (p != i)
+      for (int r = warp + NWT * lane; r < m; r += NWT * 32) {
+        T* a = Y + r + (size_t)ldy * i;
+        T* b = Y + r + (size_t)ldy * p;
+        const T tmp = *a; *a = *b; *b = tmp;
+      }
+    if (stop) { __syncthreads(); k = stop == 2 ? 0 : i; break; }
+    __syncwarp();
+    const T v0 = pub[1], c2 = pub[2];
+    // ---- every warp, its rows: partial dots with v (v_i = v0)
+    const int r0 = i + ((warp - i % NWT) + NWT) % NWT;   // this warp's first row >= i
+    T acc[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int j = lane + 32 * t;
+      acc[t] = T(0);
+      if (j > i && j < e) {
+        const T* yj = Y + (size_t)ldy * j;
+        const T* yi = Y + (size_t)ldy * i;
+        for (int r = r0; r < m; r += NWT) acc[t] += (r == i ? v0 : yi[r]) * yj[r];
+      }
+      part[warp * 64 + j] = acc[t];
+    }
+    __syncthreads();
+    // ---- every warp, its rows: y_j -= c2 (v^T y_j) v
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int j = lane + 32 * t;
+      if (j > i && j < e) {
+        T d = T(0);
+        for (int w = 0; w < NWT; ++w) d += part[w * 64 + j];
+        const T cj = d * c2;
+        T* yj = Y + (size_t)ldy * j;
+        const T* yi = Y + (size_t)ldy * i;
+        for (int r = r0; r < m; r += NWT) yj[r] -= cj * (r == i ? v0 : yi[r]);
+      }
+    }
+    if (r0 == i && lane == 0) Y[i + (size_t)ldy * i] = pub[0];   // R_ii, by the warp owning row i
+    __syncthreads();
   }
   __syncthreads();
-  return shi[0];
+  return k;
 }
 
 // Largest-first work list of a level (scheduling, not in the paper): a counting sort of the
@@ -946,7 +988,7 @@ template <typename T, int NWT>
 __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(LevelDev d, int smem_bytes) {
   extern __shared__ double sm[];
   __shared__ SegCtx S;
-  __shared__ double shr[NWT * 32 + 3 * 64];
+  __shared__ double shr[NWT * 64 + 3 * 64];
   __shared__ int shi[8];
   __shared__ int nearlist[NEAR_MAX];
   __shared__ int nnear_sh, nfar_sh;
@@ -1186,8 +1228,10 @@ __global__ void __launch_bounds__(NWT * 32, NWT == NW ? 4 : 16) sparsify_kernel(
     // a pass that can still double h only needs to know whether k > h - p: its QR stops at
     // step h - p + 1 (the same decision, the remaining steps skipped)
     const int kstop = (!full && h < nF) ? max(1, hh - d.p_over + 1) : e;
-    k = (NWT == NW && in_smem && e <= 64) ? warp_cpqr<T>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shi, kstop)
-                                          : block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi, kstop);
+    k = (NWT == NW && e <= 64)
+            ? rows_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, reinterpret_cast<T*>(shr),
+                                reinterpret_cast<T*>(shr) + NWT * 64, shi, kstop)
+            : block_cpqr<T, NWT>(Y, ldy, m, e, d.eps, perm, vn1, vn2, shr, flags, shi, kstop);
     ++passes;
     if (threadIdx.x == 0) work_done += work::qr(m, e, k);
     if (predicted) {          // the one-pass ID stands if it passes the measured-error test
