@@ -562,11 +562,26 @@ __device__ void sketch_far(const LevelDev& d, const SegCtx& S, const NbrTab& tb,
         continue;
       }
     }
+    // sums over blocks of SK_CHUNK far unknowns (both halves of a block, then the next block):
+    // the same order of operations for every chunk size, so that the sketch does not depend on
+    // the shared-memory budget the level runs with
     for (int x = threadIdx.x; x < nr * e; x += blockDim.x) {
-      int rr = x % nr, c = x / nr;
-      T acc = T(0);
-      for (int row = 0; row < rows; ++row) acc += Gc[rr + (size_t)nr * row] * Bc[row + (size_t)rows * c];
-      Yr[(r0 + rr) + (size_t)ldy * c] += acc;
+      const int rr = x % nr, c = x / nr;
+      const T* g = Gc + rr;
+      const T* bc = Bc + (size_t)rows * c;
+      T y = Yr[(r0 + rr) + (size_t)ldy * c];
+      for (int b0 = 0; b0 < nc; b0 += SK_CHUNK) {
+        const int b1 = min(nc, b0 + SK_CHUNK);
+        T acc = T(0);
+#pragma unroll 4
+        for (int row = b0; row < b1; ++row) acc += g[(size_t)nr * row] * bc[row];
+        if (halves == 2) {
+#pragma unroll 4
+          for (int row = nc + b0; row < nc + b1; ++row) acc += g[(size_t)nr * row] * bc[row];
+        }
+        y += acc;
+      }
+      Yr[(r0 + rr) + (size_t)ldy * c] = y;
     }
     __syncthreads();
   }
