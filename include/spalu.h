@@ -79,8 +79,10 @@ typedef struct {
                                  memory is cut to what lets min(spars_ctas, ceil(segments of
                                  the level / SMs)) segments (at most what the register file
                                  holds) run at once on an SM; a segment that does not fit
-                                 keeps its sketch and frontal rows in global memory (results
-                                 agree up to rounding).  0 = size for the largest segment the
+                                 keeps its sketch rows in global memory (results agree up to
+                                 rounding).  A level with at most one segment per SM gets
+                                 160 KB (room for larger sketch chunks and the staged
+                                 neighbour block).  0 = size for the largest segment the
                                  geometry allows.  Default 4. */
   int schur_tc;               /* mixed precision only: 1 (default) = the separators' Schur
                                  updates M -= Z W run on the tensor cores (mma.sync TF32 with

@@ -725,17 +725,20 @@ spalu_status spalu_factor_create(spalu_nd_t nd, const spalu_opts* o, spalu_facto
     p.Ycap = 2 * 16 + std::max(o->h0, 2 * (p.capS + o->p_oversample));
     const int tb = o->precision == 1 ? 4 : 8;
     // need: the uncut working set with the smallest sketch chunk (below it the kernel keeps
-    // its sketch rows in global scratch).  The uncut budget is 160 KB: what a segment does not
-    // need for its working set goes to larger sketch chunks and the staged B block
+    // its sketch rows in global scratch).  A level that runs one segment per SM (or the uncut
+    // candidate of the tuner) gets 160 KB: what a segment does not need for its working set
+    // goes to larger sketch chunks and the staged B block
     size_t need = sparsify_smem_need(p.capS, o->symmetric, o->h0, o->p_oversample, tb, 16);
     size_t lim = 160 * 1024;
     size_t mn = sparsify_smem_min(p.capS, o->symmetric, o->h0, o->p_oversample, tb);
-    const size_t full = std::max(lim, mn);
+    const size_t roomy = std::max(lim, mn);
+    const size_t full = std::min(need, roomy);
     // trade worst-case room for resident segments (the phases of one segment are
     // latency-bound): as many per SM as the level has segments per SM, up to spars_ctas;
     // segments that do not fit the budget fall back to global scratch inside the kernel
     auto budget = [&](int ctas) {
-      const size_t b = ctas > 0 ? sparsify_smem_budget(tb == 4, p.capS, ctas) : 0;
+      if (ctas <= 1) return roomy;
+      const size_t b = sparsify_smem_budget(tb == 4, p.capS, ctas);
       return b >= mn ? std::min(full, b) : full;
     };
     p.spars_smem = full;
