@@ -1554,7 +1554,7 @@ __global__ void merge_assemble_kernel(LevelDev d) {
 // then Z = A_dp U^{-1}.  When the kp separator rows over all nM columns fit in the dynamic
 // shared memory (smem_bytes), they are staged there: the elimination then runs on shared
 // memory with the same operations in the same order, and the rows are written back once.
-template <typename T>
+template <typename T, bool ZREG>
 __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d, int smem_bytes) {
   extern __shared__ double pm_sm[];
   __shared__ int shi[4];
@@ -1625,7 +1625,32 @@ __global__ void __launch_bounds__(256) merge_panel_kernel(LevelDev d, int smem_b
     if (!ok && threadIdx.x == 0) atomicOr(d.err, ERR_SINGULAR);
     for (int x = threadIdx.x; x < kp * nM; x += blockDim.x)
       M[(Dp + x % kp) + ldp * colp[x / kp]] = Pn[x];
-    // Z = A_dp U^{-1}: each dP row solved left to right, U from the staged rows
+    // Z = A_dp U^{-1}: each dP row solved left to right, U from the staged rows; ZREG (levels of
+    // few parents, where this chain is the latency): a separator of at most 32 unknowns keeps
+    // the row in registers (one load and one store per entry, the same operations in the same
+    // order)
+    if (ZREG && kp <= 32) {
+      for (int a = threadIdx.x; a < ndP; a += blockDim.x) {
+        const size_t row = colp[a];
+        T z[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < kp) z[j] = M[row + ldp * (Dp + j)];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j < kp) {
+            T s = z[j];
+#pragma unroll
+            for (int i = 0; i < j; ++i) s -= z[i] * at(i, ndP + j);
+            z[j] = s * inv[j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < kp) M[row + ldp * (Dp + j)] = z[j];
+      }
+      return;
+    }
     for (int a = threadIdx.x; a < ndP; a += blockDim.x) {
       size_t row = colp[a];
       for (int j = 0; j < kp; ++j) {
@@ -2354,9 +2379,14 @@ static void merge_launch(const LevelDev& d, const LevelPlan& p, cudaStream_t s) 
     // parents take the global-memory path inside the kernel)
     const size_t geo = (size_t)p.sepcap * p.ldFp * sizeof(T) + (size_t)p.ldFp * sizeof(int);
     const int pm = (int)(geo < 96 * 1024 ? geo : 96 * 1024);
-    if (pm > 48 * 1024) cudaFuncSetAttribute(merge_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pm);
     note_launch();
-    merge_panel_kernel<T><<<np, 256, pm, s>>>(d, pm);
+    if (np <= 2 * sm_count()) {      // at most two parents per SM: latency-bound, rows in registers
+      if (pm > 48 * 1024) cudaFuncSetAttribute(merge_panel_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pm);
+      merge_panel_kernel<T, true><<<np, 256, pm, s>>>(d, pm);
+    } else {
+      if (pm > 48 * 1024) cudaFuncSetAttribute(merge_panel_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pm);
+      merge_panel_kernel<T, false><<<np, 256, pm, s>>>(d, pm);
+    }
   }
   {
     const int ism = (int)invert_smem<T>();
