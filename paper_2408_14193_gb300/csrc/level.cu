@@ -2082,6 +2082,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(Level
   T* Psm = LUsm + (size_t)cap.lucap * cap.lucap;         // two k x r panels (when k r <= pcap)
   T* invs = Psm + 2 * (size_t)cap.pcap;
   int* pivs = reinterpret_cast<int*>(invs + cap.lucap);
+  int* nds = pivs + cap.lucap;                           // the segment's nodes (vrows)
   const bool staged = r <= cap.lucap;
   const bool pstaged = (size_t)k * r <= (size_t)cap.pcap;
   const int* snodes = d.snodes + (size_t)sid * capS;     // nodes in [skeleton | remainder] order
@@ -2107,10 +2108,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(Level
     if (bwd)
       for (int x = threadIdx.x; x < r * k; x += blockDim.x) Ps[x] = Dg[(k + x % r) + (size_t)capS * (x / r)];
   }
+  for (int a = threadIdx.x; a < e; a += blockDim.x) nds[a] = snodes[a];
+  __syncthreads();
   pdl_wait();
-  for (int x = threadIdx.x; x < e * SC; x += blockDim.x) {
+  for (int x = threadIdx.x; x < e * nc; x += blockDim.x) {
     int a = x % e, c = x / e;
-    v[x] = c < nc ? X[lay.at(snodes[a], c)] : T(0);
+    v[x] = X[lay.at(nds[a], c)];
   }
   __syncthreads();
   const T* LUs = staged ? LUsm : Dg + k + (size_t)capS * k;
@@ -2155,7 +2158,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) seg_solve_kernel(Level
   __syncthreads();
   for (int x = threadIdx.x; x < e * nc; x += blockDim.x) {
     int a = x % e, c = x / e;
-    X[lay.at(snodes[a], c)] = v[x];
+    X[lay.at(nds[a], c)] = v[x];
   }
 }
 
@@ -2184,6 +2187,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
   T* invs = xd + (size_t)cap.drows * SC;
   int* pivs = reinterpret_cast<int*>(invs + cap.lucap);
   int* rows_sm = pivs + cap.lucap;                      // 2 * drows
+  int* ynode = rows_sm + 2 * cap.drows;                 // the separator skeleton's nodes (yrows)
   const bool staged = kp <= cap.lucap;
   const bool dstage = ndP <= cap.drows;
   const int ldw = ndP | 1;                              // odd pitch of the staged W^T panel
@@ -2197,6 +2201,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
   auto rowpos = [&](int a) { return dstage ? rows_sm[a] : tab[(size_t)a * TABW]; };
   auto rownode = [&](int a) { return dstage ? rows_sm[cap.drows + a] : tab[(size_t)a * TABW + 7]; };
   if (staged) for (int x = threadIdx.x; x < kp; x += blockDim.x) { invs[x] = inv[x]; pivs[x] = piv[x]; }
+  for (int a = threadIdx.x; a < kp; a += blockDim.x) ynode[a] = tab[(size_t)(ndP + a) * TABW + 7];
   const size_t ldl = staged ? (size_t)kp : ldp;
   const T* ivs = staged ? invs : inv;
   const int* pvs = staged ? pivs : piv;
@@ -2215,12 +2220,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
       Wt[b + (size_t)ldw * j] = M[(Dp + j) + ldp * rows_sm[b]];
     }
   }
+  __syncthreads();          // ynode, rows_sm
   pdl_wait();
-  for (int x = threadIdx.x; x < kp * SC; x += blockDim.x) {
+  for (int x = threadIdx.x; x < kp * nc; x += blockDim.x) {
     int a = x % kp, c = x / kp;
-    y[x] = c < nc ? X[lay.at(tab[(size_t)(ndP + a) * TABW + 7], c)] : T(0);
+    y[x] = X[lay.at(ynode[a], c)];
   }
-  __syncthreads();          // rows_sm, y (and the LU block) are read by other threads below
+  __syncthreads();          // y (and the LU block) are read by other threads below
   if (!bwd) {
     if (kp <= INV_MAX) tri_apply<T, true, NT>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
     else lower_sweep<T>(y, kp, kp, staged ? U : M + Dp + ldp * Dp, ldl, pvs, nc);
@@ -2236,9 +2242,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
                   [&](int a, int c, T acc) { atomicAdd(X + lay.at(rownode(a), c), -acc); });
   } else {
     if (dstage) {
-      for (int x = threadIdx.x; x < ndP * SC; x += blockDim.x) {
+      for (int x = threadIdx.x; x < ndP * nc; x += blockDim.x) {
         int b = x % ndP, c = x / ndP;
-        xd[x] = c < nc ? X[lay.at(rows_sm[cap.drows + b], c)] : T(0);
+        xd[x] = X[lay.at(rows_sm[cap.drows + b], c)];
       }
     }
     __syncthreads();
@@ -2268,7 +2274,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 16) sep_solve_kernel(Level
   __syncthreads();
   for (int x = threadIdx.x; x < kp * nc; x += blockDim.x) {
     int a = x % kp, c = x / kp;
-    X[lay.at(tab[(size_t)(ndP + a) * TABW + 7], c)] = y[x];
+    X[lay.at(ynode[a], c)] = y[x];
   }
 }
 
@@ -2425,10 +2431,11 @@ bool level_solve_caps(const LevelDev& d, const int* lmax, SolveCaps* out) {
   long long seg_fixed = 0, sep_fixed = 0;
   for (;;) {
     // segment: v, LU block, reciprocal pivots, pivots (panels come on top)
-    seg_fixed = TB * ((long long)sc.vrows * SC + (long long)sc.lucap * sc.lucap + sc.lucap) + 4LL * sc.lucap + 16;
+    seg_fixed = TB * ((long long)sc.vrows * SC + (long long)sc.lucap * sc.lucap + sc.lucap) +
+                4LL * (sc.lucap + sc.vrows) + 16;
     // separator: y, xd, reciprocal pivots, pivots, boundary rows (the LU block / panel union on top)
     sep_fixed = TB * ((long long)sc.yrows * SC + (long long)sc.drows * SC + sc.lucap) +
-                4LL * (sc.lucap + 2 * sc.drows) + 16;
+                4LL * (sc.lucap + 2 * sc.drows + sc.yrows) + 16;
     const long long lu = TB * (long long)sc.lucap * sc.lucap;
     if (seg_fixed <= budget && sep_fixed + lu <= budget) break;
     if (sc.lucap > 8) sc.lucap /= 2;
