@@ -949,6 +949,56 @@ __global__ void sep_update_fwd_kernel(LeafDev d, T* X, int nrhs, VecLayout lay) 
   }
 }
 
+// The same update for the chunked FP32 vector (a node's 16 right-hand sides contiguous): one
+// thread per separator node and all 16 right-hand sides, so that the row's CSR entries are
+// read and classified once instead of once per right-hand side, and the neighbour values move
+// as four 16-byte loads.  Same operations in the same order for every right-hand side.
+__global__ void sep_update_fwd16_kernel(LeafDev d, float* X) {
+  pdl_enter();
+  const int nx = d.nx, ny = d.ny;
+  const int R = (ny + 1) / (LEAF + 1) - 1, C = (nx + 1) / (LEAF + 1) - 1;
+  const long long nrow = (long long)R * nx;
+  const long long nsep = nrow + (long long)(ny - R) * C;
+  for (long long sidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; sidx < nsep;
+       sidx += (long long)gridDim.x * blockDim.x) {
+    int ux, uy;
+    if (sidx < nrow) {
+      uy = (int)(sidx / nx) * (LEAF + 1) + LEAF;
+      ux = (int)(sidx % nx);
+    } else {
+      const long long t = sidx - nrow;
+      const int yy = (int)(t / C);
+      ux = (int)(t % C) * (LEAF + 1) + LEAF;
+      uy = (yy / LEAF) * (LEAF + 1) + yy % LEAF;
+    }
+    const int u = ux + nx * uy;
+    float4 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int p = d.rowptr[u]; p < d.rowptr[u + 1]; ++p) {
+      const int v = d.colind[p];
+      const int vx = v % nx, vy = v / nx;
+      const bool vsep = ((vx + 1) % (LEAF + 1) == 0) || ((vy + 1) % (LEAF + 1) == 0);
+      if (!vsep) {
+        const float a = d.fval[p];
+        const float4* xv = reinterpret_cast<const float4*>(X + (size_t)v * 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 t = xv[q];
+          acc[q].x += a * t.x; acc[q].y += a * t.y; acc[q].z += a * t.z; acc[q].w += a * t.w;
+        }
+      }
+    }
+    float4* xu = reinterpret_cast<float4*>(X + (size_t)u * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float4 t = xu[q];
+      t.x -= acc[q].x; t.y -= acc[q].y; t.z -= acc[q].z; t.w -= acc[q].w;
+      xu[q] = t;
+    }
+  }
+}
+
 // side unknowns sorted by the in-leaf index of their interior neighbour, and the first
 // sweep step of each of the two warps that solve for them
 void qorder_tables(int* ord, int* start) {
@@ -1048,8 +1098,21 @@ void launch_sep_update_fwd(const LeafDev& d, void* X, int nrhs, VecLayout lay, c
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
   note_launch();
-  if (d.fp32) launch_pdl(sep_update_fwd_kernel<float>, dim3(blocks), dim3(256), 0, s, d, static_cast<float*>(X), nrhs, lay);
-  else launch_pdl(sep_update_fwd_kernel<double>, dim3(blocks), dim3(256), 0, s, d, static_cast<double*>(X), nrhs, lay);
+  if (d.fp32 && lay.cs == 1 && lay.rs == 16) {   // the chunked FP32 vector: a thread per node
+    const long long nsep = n / nrhs;
+    int b16 = (int)((nsep + 255) / 256);
+    if (b16 > 152 * 32) b16 = 152 * 32;
+    if (b16 < 1) b16 = 1;
+    for (int c0 = 0; c0 < nrhs; c0 += 16) {       // one launch per chunk of 16 right-hand sides
+      if (c0 > 0) note_launch();
+      launch_pdl(sep_update_fwd16_kernel, dim3(b16), dim3(256), 0, s, d,
+                 static_cast<float*>(X) + (size_t)(c0 / 16) * lay.chunk);
+    }
+  } else if (d.fp32) {
+    launch_pdl(sep_update_fwd_kernel<float>, dim3(blocks), dim3(256), 0, s, d, static_cast<float*>(X), nrhs, lay);
+  } else {
+    launch_pdl(sep_update_fwd_kernel<double>, dim3(blocks), dim3(256), 0, s, d, static_cast<double*>(X), nrhs, lay);
+  }
 }
 
 }  // namespace spalu
