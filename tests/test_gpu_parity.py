@@ -433,6 +433,27 @@ def test_sparsify_budgets_and_tuning_match_oracle(precision):
             assert err(f) <= bar
 
 
+def test_ranks_do_not_depend_on_the_sparsify_budget():
+    """The sketch is summed in blocks of 16 far unknowns whatever chunk the shared-memory
+    budget allows (and the pivoted QR is the same in shared or global memory), so the mixed
+    factorization takes the same skeletons under every budget: identical per-level ranks, and
+    solutions equal up to the run-dependent order of the solve's separator atomics."""
+    from paper_2408_14193_gb300 import Factor, NestedDissection
+    n = 255
+    P = W.make_problem("diffusion", n, seed=45, nrhs=2)
+    rp, ci, va, B = _dev(P)
+    nd = NestedDissection(n)
+    ranks, xs = [], []
+    for ctas in (0, 2, 4, 12):
+        f = Factor(nd, eps_id=5e-7, symmetric=1, precision=1, spars_ctas=ctas)
+        f.factor(rp, ci, va)
+        ranks.append([(lv["k_sum"], lv["k_max"], lv["passes"]) for lv in f.stats()["levels"]])
+        xs.append(f.solve(B).cpu().numpy().T)
+    for r, x in zip(ranks[1:], xs[1:]):
+        assert r == ranks[0]
+        assert rel_errors(x, xs[0])[0] <= 1e-5
+
+
 def test_bad_sparsify_budget_is_rejected():
     from paper_2408_14193_gb300 import Factor, NestedDissection, SpaluError
     for ctas in (-1, 33):
