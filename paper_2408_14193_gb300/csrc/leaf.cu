@@ -10,6 +10,11 @@
 // interior nodes next to the sides (every side unknown couples to one interior node), so it
 // comes from 60 solves with unit right-hand sides.
 //
+// The LU works on a window of band columns in shared memory (LAPACK band layout); each final
+// column leaves it as three 16-value records (L multipliers and pivot offset; reciprocal
+// pivot and U above the diagonal; U entries 16..30 that interchanges create), which the sweeps
+// stage 16 columns at a time as contiguous runs.
+//
 // GB300 mapping: FP64 runs at 2 FMA per clock per SM, so every FP64 warp instruction must
 // carry 32 useful lanes.  The solves therefore give one thread to one (leaf, right-hand side)
 // column and sweep the band with a register window (the interchanges stay inside it); the
