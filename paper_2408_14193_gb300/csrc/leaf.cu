@@ -223,6 +223,57 @@ __device__ __forceinline__ void sweep_U_staged(const WarpStage<T>& w, const T* u
   }
 }
 
+// The backward sweep of the leaf Schur kernel in FP32 with the y rows of the next block staged
+// too: row j of the warp's 32 columns is one 128-byte run of the sweep buffer (ybw + j QL),
+// written by this warp's forward sweep; the refill of step u of block blk reads row j - 16 from
+// the stage of block blk + 1 instead of a global load outstanding at the warp barriers.
+// Rows below j0 (where this warp's forward sweep started) are zero.
+template <typename T, class Out>
+__device__ __forceinline__ void sweep_U_staged_y(const WarpStage<T>& w, T* ys, const T* ur, const T* ybw, int j0,
+                                                 bool act, Out out) {
+  const int lane = threadIdx.x & 31;
+  T V[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) V[r] = (act && NI - 1 - r >= j0) ? ybw[(size_t)(NI - 1 - r) * QL + lane] : T(0);
+  auto stage_y = [&](int buf, int blk) {   // rows of block blk (no commit: stage_U commits)
+    T* Y = ys + buf * 512;
+    for (int x = lane; x < 16 * 8; x += 32) {
+      const int u = x >> 3, k = x & 7, j = NI - 1 - 16 * blk - u;
+      if (j >= j0) cp_async16(Y + u * 32 + 4 * k, ybw + (size_t)j * QL + 4 * k);
+    }
+  };
+  const int nb = (NI + 15) / 16;
+  stage_y(0, 1);
+  stage_U(w, 0, ur, 0, lane);
+  for (int blk = 0; blk < nb; ++blk) {
+    if (blk + 1 < nb) {
+      stage_y((blk + 1) & 1, blk + 2);
+      stage_U(w, (blk + 1) & 1, ur, 16 * (blk + 1), lane);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const T* S = w.v + (blk & 1) * 256;
+    const T* Ys = ys + (blk & 1) * 512 + lane;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = 16 * blk + u;
+      if (t < NI) {
+        const int j = NI - 1 - t;
+        T uv[16];
+        lds_vec(S + u * 16, uv);
+        const T x = V[u] * uv[0];
+        if (act) out(j, x);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) V[(u + r) & 15] -= uv[r] * x;
+        V[u] = (act && j - 16 >= j0) ? Ys[u * 32] : T(0);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Forward sweep y = L^{-1} P x for one column held by this thread.  in(j) gives x_j,
 // out(j, y) receives y_j for j = j0..NI-1 (x_j = 0 for j < j0 is assumed).
 template <typename T, class BandT, class In, class Out>
@@ -437,6 +488,7 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
   }
   __syncthreads();
   __shared__ __align__(16) T stv[FTH / 32][512];
+  __shared__ __align__(16) T sty[FTH / 32][sizeof(T) == 4 ? 1024 : 4];   // FP32: y rows of the U sweep
   if (live && d.kur[b] <= 15) {     // warp-staged sweeps (all lanes; lanes >= NQ only stage)
     const bool act = tid < NQ;
     const int q = act ? c_qorder[tid] : 0;
@@ -460,7 +512,10 @@ __global__ void __launch_bounds__(FTH) leaf_schur_kernel(LeafDev d) {
       if (lx == 0 && qex[sub][2 * LEAF + ly]) F[(2 * LEAF + ly) + ldF * q] = -(T)qa[sub][2 * LEAF + ly] * x;
       if (lx == LEAF - 1 && qex[sub][3 * LEAF + ly]) F[(3 * LEAF + ly) + ldF * q] = -(T)qa[sub][3 * LEAF + ly] * x;
     };
-    sweep_U_staged<T>(ws, ur, act, yin, ring_out);
+    if constexpr (sizeof(T) == 4)
+      sweep_U_staged_y<T>(ws, sty[threadIdx.x >> 5], ur, yb + 32 * (tid >> 5), j0, act, ring_out);
+    else
+      sweep_U_staged<T>(ws, ur, act, yin, ring_out);
   } else if (live && tid < NQ) {    // widened U: sweeps reading the band from global memory
     const int q = c_qorder[tid];
     const int j0 = c_qstart[tid >> 5];
