@@ -87,6 +87,10 @@ struct Band {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
@@ -333,7 +337,7 @@ __device__ __forceinline__ void sweep_U(const BandT& B, In in, Out out) {
 // CTA, in FP64, on a sliding window of WS band columns in shared memory: column c sits in
 // slot c mod WS; after step j column j is final, goes to global memory in precision T and its
 // slot is refilled with column j + WS (first touched at step j + 2) from the gathered nonzeros
-// (leaf_band5_kernel), loaded one step before.
+// (leaf_band5_kernel) by cp.async, waited for two steps later.
 // Also zeroes the leaf's frontal block and records the upper bandwidth reached.
 constexpr int WS = 32;       // window columns (> KV)
 constexpr int LUT = 64;      // threads per leaf LU
@@ -383,13 +387,16 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
   };
   auto w = [&](int i, int c) -> double& { return W[(KV + i - c) + LDAB * (c & (WS - 1))]; };
   for (int x = tid; x < LDAB * WS; x += LUT) W[x] = assemble(x % LDAB, x / LDAB);
-  double pre = tid < LDAB ? assemble(tid, WS) : 0.0;     // the refill of the next slot, a step ahead
+  // band row tid of a refilled column: stencil offset k of the gathered nonzeros, or none
+  const int ko = tid - KV;
+  const int kst = ko == -LEAF ? 0 : ko == -1 ? 1 : ko == 0 ? 2 : ko == 1 ? 3 : ko == LEAF ? 4 : -1;
   __syncthreads();
   int ju = 0, kureach = KU;
   bool ok = true, swapped = false;
   const int ur = 1 + (tid & 15), ucg = tid >> 4;       // rank-1 update: row, column group
   for (int j = 0; j < NI; ++j) {
     const int km = min(KL, NI - 1 - j);
+    cp_async_wait<1>();       // the refills issued up to step j - 2 (column j + 30 at the latest)
     if (tid < 32) {           // pivot: |entries| compared as bit patterns (no FP64 arithmetic)
       long long best = -1;
       int bi = 0;
@@ -437,10 +444,14 @@ __global__ void __launch_bounds__(LUT) leaf_lu_kernel(LeafDev d) {
       else if (tid > KV - 16) { if (tid < KV) urg[16 * j + (KV - tid)] = v; }   // U(j-r, j), r = KV - tid <= 15
       else uxg[16 * j + (KV - 16 - tid)] = v;                      // U(j-r, j), r = 16..30
       if (tid == KV) uxg[16 * j + 15] = T(0);
-      slot = pre;                          // column j + WS
-      pre = assemble(tid, j + WS + 1);     // consumed at step j + 1
+      // column j + WS (first touched at step j + 2): its stencil rows copied asynchronously, the
+      // rest zero, so that no global load is outstanding at the next barriers
+      if (j + WS < NI && kst >= 0) cp_async8(&slot, b5 + 5 * (j + WS) + kst);
+      else slot = 0.0;
     }
+    cp_async_commit();
   }
+  cp_async_wait<0>();
   if (!ok && tid == 0) atomicOr(d.err, ERR_SINGULAR);
   if (tid == 0) {
     const int ku = min(kureach, KV);
